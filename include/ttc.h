@@ -1,0 +1,243 @@
+/*
+ * ttc.h -- exact (d13, d12, d23)-temporal triangle counting on one GB300 GPU.
+ *
+ * Method: Pashanasangi & Seshadhri, "Faster and Generalized Temporal Triangle
+ * Counting, via Degeneracy Ordering", KDD'21 (DOTTT).
+ *
+ * Input (Sec. 3): a directed temporal multigraph given as m edges
+ * (src[i], dst[i], t[i]).  The edge index i breaks timestamp ties: edges are
+ * totally ordered by the key (t, i).
+ *
+ * Output (Def. 1, Fig. 2): for a delta-triple (d13, d12, d23), the number of
+ * edge triples e1 < e2 < e3 (key order) on the three vertex pairs of a static
+ * triangle with t2 - t1 <= d12, t3 - t2 <= d23 and t3 - t1 <= d13, split by
+ * triangle type: out[k-1] is the count of type T_k of Fig. 2 (k = 1..8).
+ * Counts are exact unsigned 64-bit integers.
+ *
+ * Conventions shared by every entry point:
+ *   - Inputs are owned by the caller and only read during the call.  Unless a
+ *     flag says otherwise, pointers are host pointers; they are copied to the
+ *     device before the call returns.
+ *   - Outputs are caller-allocated and written only when the call returns
+ *     TTC_OK.
+ *   - A ttc_graph owns all of its device memory until ttc_free().  It is
+ *     immutable after loading; concurrent count calls on one graph are
+ *     allowed.  All work runs on the graph's CUDA stream (one per graph).
+ *   - On failure a call returns a negative ttc_status (or NULL), and
+ *     ttc_last_error() gives a message for the calling thread.
+ *   - Vertex ids must be < 2^31.  Timestamps must lie in [-2^62, 2^62] and
+ *     every delta component in [0, 2^62].  m = 0 is valid and counts zero.
+ *   - Self-loops (src == dst) can never lie on a triangle and are dropped
+ *     (and counted in the statistics).
+ */
+#ifndef TTC_H
+#define TTC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TTC_NUM_TYPES 8
+
+typedef struct ttc_graph ttc_graph;
+typedef struct ttc_server ttc_server;
+
+/* One query: the three windows of Def. 1.  Any non-negative triple is legal;
+ * the library normalises it (d12 <- min(d12, d13), d23 <- min(d23, d13),
+ * d13 <- min(d13, d12 + d23)), which leaves every count unchanged. */
+typedef struct {
+    int64_t d13, d12, d23;
+} ttc_delta;
+
+typedef enum {
+    TTC_OK = 0,
+    TTC_PENDING = 1,          /* ttc_serve_poll: result not ready yet */
+    TTC_ERR_INVALID = -1,     /* NULL pointer, bad flag or handle */
+    TTC_ERR_RANGE = -2,       /* id, timestamp or delta outside the documented range */
+    TTC_ERR_NOMEM = -3,       /* device or host allocation failed */
+    TTC_ERR_CUDA = -4,        /* a CUDA call failed */
+    TTC_ERR_TIMEOUT = -5,     /* a bounded wait gave up */
+    TTC_ERR_OVERFLOW = -6,    /* a count does not fit in 64 bits */
+    TTC_ERR_BUSY = -7,        /* server queue full */
+    TTC_ERR_INTERNAL = -8,    /* an internal consistency check failed */
+    TTC_ERR_NOT_FOUND = -9    /* unknown graph id or ticket */
+} ttc_status;
+
+/* ------------------------------------------------------------------ load */
+
+/* Load flags. */
+#define TTC_LOAD_DEVICE_INPUT 1u  /* src/dst/t are device pointers (same device) */
+
+/* Vertex orderings used to orient the static graph.  Any acyclic orientation
+ * gives identical counts; the degeneracy ordering (Sec. 3, Matula-Beck) bounds
+ * every out-degree by the degeneracy kappa (Theorem 1). */
+#define TTC_ORIENT_DEGENERACY 0u  /* k-core peel order (default) */
+#define TTC_ORIENT_ID 1u          /* by vertex id */
+#define TTC_ORIENT_DEGREE 2u      /* by (degree, id) */
+#define TTC_ORIENT_RANDOM 3u      /* by a seeded random permutation */
+
+/* Which vertex of a static triangle plays u (the vertex whose two pairs are
+ * enumerated).  The paper uses the first vertex in the ordering (Sec. 5,
+ * "source vertex"); the default instead names u the vertex opposite the pair
+ * with the most edges, so that the longest list is only ever searched.  Both
+ * give identical counts. */
+#define TTC_LABEL_HEAVIEST_VW 0u  /* default */
+#define TTC_LABEL_SOURCE 1u       /* the paper's labelling */
+
+typedef struct {
+    uint32_t flags;            /* TTC_LOAD_* */
+    uint32_t orientation;      /* TTC_ORIENT_* */
+    uint32_t labeling;         /* TTC_LABEL_* */
+    uint32_t light_max_pairs;  /* triangles with sigma_A * sigma_B below this use the
+                                  one-thread-per-triangle path, the others the
+                                  prefix-sum path (1 = all prefix-sum); 0 = default */
+    uint64_t seed;             /* TTC_ORIENT_RANDOM permutation seed */
+    void *stream;              /* cudaStream_t to adopt; NULL = create one */
+} ttc_load_opts;
+
+typedef struct {
+    uint64_t n;              /* max vertex id + 1 */
+    uint64_t m;              /* temporal edges kept (self-loops dropped) */
+    uint64_t m_self_loops;   /* self-loops dropped */
+    uint64_t m_s;            /* static edges (vertex pairs with >= 1 edge) */
+    uint64_t tau;            /* static triangles */
+    uint64_t kappa;          /* max out-degree of the orientation (= degeneracy for
+                                TTC_ORIENT_DEGENERACY) */
+    uint64_t sigma_max;      /* largest number of edges on one pair */
+    uint64_t peel_rounds;    /* rounds of the k-core peel */
+    uint64_t work_bytes;     /* sum over static triangles of 8 (s_uv + s_uw + s_vw) + 12 */
+    uint64_t enum_elems;     /* sum over static triangles of the enumerated list lengths */
+    uint64_t tau_light;      /* triangles on the one-thread-per-triangle path */
+    uint64_t tau_heavy;      /* triangles on the prefix-sum (CEC) path */
+    uint64_t device_bytes;   /* device memory held by the graph */
+    uint64_t work_bytes_heavy; /* the part of work_bytes from prefix-sum-path triangles */
+    uint32_t key_bits;       /* bits of the packed per-edge key */
+    uint32_t reserved;
+} ttc_graph_stats;
+
+/* Build the device-resident graph (Alg. 1 steps up to the triangle list:
+ * static graph, degeneracy ordering, orientation, per-pair key-sorted edge
+ * lists, static triangles).  Uses default options.  Returns NULL on error. */
+ttc_graph *ttc_load(const uint32_t *src, const uint32_t *dst, const int64_t *t, uint64_t m);
+
+/* As ttc_load with options (opts may be NULL).  *out receives the handle. */
+ttc_status ttc_load_ex(const uint32_t *src, const uint32_t *dst, const int64_t *t, uint64_t m,
+                       const ttc_load_opts *opts, ttc_graph **out);
+
+/* Release a graph and all of its device memory.  NULL is a no-op. */
+void ttc_free(ttc_graph *g);
+
+ttc_status ttc_graph_info(const ttc_graph *g, ttc_graph_stats *s);
+
+/* ----------------------------------------------------------------- count */
+
+/* One query (Alg. 1, counting step; Lemma 1 and Algs. 2-4 per static
+ * triangle; Table 1 maps each (ordering, orientation) to a type).
+ * out[8] is a host array. */
+ttc_status ttc_count(ttc_graph *g, const ttc_delta *d, uint64_t out[TTC_NUM_TYPES]);
+
+/* k queries in one pass over the triangles.  d[k] host array; out is a host
+ * array of k * 8 counts, row q for d[q]. */
+ttc_status ttc_count_batch(ttc_graph *g, const ttc_delta *d, uint32_t k, uint64_t *out);
+
+/* As ttc_count_batch, but asynchronous: d_dev (k deltas, each component in
+ * [0, 2^62]; normalised on the device) and out_dev (k * 8 uint64) are device
+ * pointers, and the work is queued on `stream` (cudaStream_t; NULL = the
+ * graph's stream).  The caller synchronises.  Overflow is not detected and
+ * out-of-range deltas are not reported on this path. */
+ttc_status ttc_count_batch_async(ttc_graph *g, const ttc_delta *d_dev, uint32_t k,
+                                 uint64_t *out_dev, void *stream);
+
+/* Many graphs in one launch: graph q is counted under d[q]; out is a host
+ * array of G * 8 counts.  All graphs must live on the current device.  The
+ * launch is captured into a CUDA graph on first use for a given set of
+ * handles and replayed afterwards. */
+ttc_status ttc_count_multi(ttc_graph *const *g, const ttc_delta *d, uint32_t G, uint64_t *out);
+
+/* Sampled per-triangle counts, for checking against a slow reference at full
+ * size: every `stride`-th static triangle of the graph's own list, starting
+ * at `first`, is counted under d by the same kernels as ttc_count.  Writes up
+ * to `cap` triangles as vertex triples tri[3 * i] (host) and their counts
+ * out[8 * i] (host); *written receives the number written. */
+ttc_status ttc_count_sample(ttc_graph *g, const ttc_delta *d, uint64_t first, uint64_t stride,
+                            uint64_t cap, uint32_t *tri, uint64_t *out, uint64_t *written);
+
+/* ----------------------------------------------------------------- serve */
+
+typedef struct {
+    uint64_t hbm_reserve_bytes;  /* device memory kept free when admitting graphs */
+    uint32_t max_batch;          /* most queries per graph per launch (0 = 256) */
+    uint32_t max_queue;          /* most pending queries (0 = 65536) */
+    uint32_t streams;            /* concurrent launch streams (0 = 4) */
+    uint32_t reserved;
+} ttc_server_opts;
+
+/* A server keeps graphs resident and runs queries as they arrive: pending
+ * queries on one graph are packed into one batched launch, launches on
+ * different graphs overlap on separate streams, and new graphs are admitted
+ * while free device memory (minus the reserve) allows, evicting the
+ * least-recently-used idle graph otherwise. */
+ttc_server *ttc_server_create(const ttc_server_opts *o);
+void ttc_server_destroy(ttc_server *s);
+
+/* Load a graph into the server (host arrays, as ttc_load).  *graph_id
+ * receives its id. */
+ttc_status ttc_serve_load(ttc_server *s, const uint32_t *src, const uint32_t *dst, const int64_t *t,
+                          uint64_t m, uint64_t *graph_id);
+
+/* Queue one query; *ticket identifies it.  TTC_ERR_BUSY if the queue is
+ * full, TTC_ERR_NOT_FOUND for an unknown or evicted graph. */
+ttc_status ttc_serve_submit(ttc_server *s, uint64_t graph_id, const ttc_delta *d, uint64_t *ticket);
+
+/* TTC_PENDING until the query is done; then TTC_OK with out[8] and the
+ * submit-to-completion latency in seconds (latency_s may be NULL).  A ticket
+ * can be collected once. */
+ttc_status ttc_serve_poll(ttc_server *s, uint64_t ticket, uint64_t out[TTC_NUM_TYPES], double *latency_s);
+
+/* Block until every submitted query has completed, or timeout_s passes
+ * (TTC_ERR_TIMEOUT). */
+ttc_status ttc_serve_drain(ttc_server *s, double timeout_s);
+
+typedef struct {
+    uint64_t submitted, completed, launches, graphs_resident, admissions, evictions;
+    uint64_t queue_depth_max;
+} ttc_server_stats;
+
+ttc_status ttc_server_info(ttc_server *s, ttc_server_stats *st);
+
+/* ----------------------------------------------------------------- misc */
+
+/* Message for the calling thread's last failure ("" if none). */
+const char *ttc_last_error(void);
+
+/* Library version string. */
+const char *ttc_version(void);
+
+/* Testing hook: make the n-th device allocation from now fail with
+ * TTC_ERR_NOMEM (n = 0 disables).  Process-wide. */
+void ttc_debug_fail_alloc_after(uint64_t n);
+
+/* Number of kernels this library has launched in the process so far. */
+uint64_t ttc_debug_launch_count(void);
+
+/* Per-kernel timing of count calls.  While profiling is on for a graph, each
+ * count call records a CUDA event pair around every kernel it launches (on
+ * the graph's stream); ttc_profile_read returns the kernels of the most
+ * recent count call: name and duration in milliseconds.  Returns the number
+ * of kernels written (at most cap). */
+typedef struct {
+    char name[32];
+    float ms;
+} ttc_kernel_time;
+
+ttc_status ttc_set_profiling(ttc_graph *g, int on);
+uint32_t ttc_profile_read(ttc_graph *g, ttc_kernel_time *out, uint32_t cap);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TTC_H */

@@ -46,9 +46,10 @@ def _load():
         u64, u32, i32 = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
         lib.ttc_oracle_bruteforce.argtypes = [p, p, p, u64, p, u32, p]
         lib.ttc_oracle_count.argtypes = [p, p, p, u64, p, u32, i32, p]
+        lib.ttc_oracle_count_part.argtypes = [p, p, p, u64, p, u32, i32, u32, u32, p]
         lib.ttc_oracle_count_triangles.argtypes = [p, p, p, u64, p, u64, p, u32, i32, p]
         lib.ttc_oracle_stats.argtypes = [p, p, p, u64, i32, p]
-        for f in (lib.ttc_oracle_bruteforce, lib.ttc_oracle_count,
+        for f in (lib.ttc_oracle_bruteforce, lib.ttc_oracle_count, lib.ttc_oracle_count_part,
                   lib.ttc_oracle_count_triangles, lib.ttc_oracle_stats):
             f.restype = ctypes.c_int
         _lib = lib
@@ -97,6 +98,17 @@ def count(src, dst, t, deltas, threads: int = 0):
     out = np.zeros((d.shape[0], 8), dtype=np.uint64)
     _check(_load().ttc_oracle_count(_ptr(src), _ptr(dst), _ptr(t), src.size,
                                     _ptr(d), d.shape[0], int(threads), _ptr(out)))
+    return out
+
+
+def count_part(src, dst, t, deltas, part: int, nparts: int, threads: int = 0):
+    """O1 over the triangles whose smallest vertex id is part mod nparts
+    (the parts partition the triangles).  Returns [k][8]."""
+    src, dst, t = _edges(src, dst, t)
+    d = _deltas(deltas)
+    out = np.zeros((d.shape[0], 8), dtype=np.uint64)
+    _check(_load().ttc_oracle_count_part(_ptr(src), _ptr(dst), _ptr(t), src.size, _ptr(d), d.shape[0],
+                                         int(threads), int(part), int(nparts), _ptr(out)))
     return out
 
 

@@ -363,8 +363,24 @@ static int threads_or_default(int threads) {
 #endif
 }
 
+/*
+ * O1 restricted to the static triangles whose smallest vertex id a satisfies
+ * a % nparts == part (a sampling aid for timing: the parts partition the
+ * triangles, so their counts sum to the full count).
+ */
+int ttc_oracle_count_part(const uint32_t *src, const uint32_t *dst, const int64_t *t, uint64_t m,
+                          const int64_t *deltas, uint32_t nd, int threads, uint32_t part, uint32_t nparts,
+                          uint64_t *out);
+
 int ttc_oracle_count(const uint32_t *src, const uint32_t *dst, const int64_t *t, uint64_t m,
                      const int64_t *deltas, uint32_t nd, int threads, uint64_t *out) {
+    return ttc_oracle_count_part(src, dst, t, m, deltas, nd, threads, 0, 1, out);
+}
+
+int ttc_oracle_count_part(const uint32_t *src, const uint32_t *dst, const int64_t *t, uint64_t m,
+                          const int64_t *deltas, uint32_t nd, int threads, uint32_t part, uint32_t nparts,
+                          uint64_t *out) {
+    if (nparts == 0 || part >= nparts) return ORACLE_ERR_INVALID;
     if ((m && (!src || !dst || !t)) || !out || (nd && !deltas) || !check_deltas(deltas, nd))
         return ORACLE_ERR_INVALID;
     graph_t g;
@@ -375,7 +391,7 @@ int ttc_oracle_count(const uint32_t *src, const uint32_t *dst, const int64_t *t,
     if (!acc) { graph_free(&g); return ORACLE_ERR_NOMEM; }
     int err = 0;
 #pragma omp parallel for schedule(dynamic, 16) num_threads(nt)
-    for (int64_t a = 0; a < (int64_t)g.n; a++) {
+    for (int64_t a = part; a < (int64_t)g.n; a += nparts) {
 #ifdef _OPENMP
         u128 *my = acc + (size_t)omp_get_thread_num() * 8 * nd;
 #else

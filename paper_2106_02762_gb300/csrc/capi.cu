@@ -1,0 +1,361 @@
+// C-ABI entry points (include/ttc.h): argument checks, handle lifetime,
+// delta normalisation, and conversion of internal failures to ttc_status.
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+
+#include "graph.cuh"
+
+namespace ttc {
+
+namespace {
+thread_local std::string g_last_error;
+std::atomic<uint64_t> g_fail_after{0};
+std::atomic<uint64_t> g_bytes{0};
+std::atomic<uint64_t> g_launches{0};
+}  // namespace
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void prof_reset(ttc_graph *g) { g->prof_used = 0; }
+
+void prof_begin(ttc_graph *g, cudaStream_t s, const char *name) {
+    if (!g->profiling) return;
+    if (g->prof_used == g->prof.size()) {
+        ttc_graph::ProfEntry e{name, nullptr, nullptr};
+        TTC_CUDA(cudaEventCreate(&e.start));
+        TTC_CUDA(cudaEventCreate(&e.stop));
+        g->prof.push_back(e);
+    }
+    g->prof[g->prof_used].name = name;
+    TTC_CUDA(cudaEventRecord(g->prof[g->prof_used].start, s));
+}
+
+void prof_end(ttc_graph *g, cudaStream_t s) {
+    if (!g->profiling) return;
+    TTC_CUDA(cudaEventRecord(g->prof[g->prof_used].stop, s));
+    g->prof_used++;
+}
+
+// Normalises k device delta-triples in place (see normalise()).
+__global__ void normalise_kernel(int64_t *d, uint32_t k) {
+    const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= k) return;
+    const int64_t d13 = d[3 * q], d12 = min(d[3 * q + 1], d13), d23 = min(d[3 * q + 2], d13);
+    d[3 * q] = min(d13, d12 + d23);
+    d[3 * q + 1] = d12;
+    d[3 * q + 2] = d23;
+}
+
+void fail(ttc_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    throw Failure{st, buf};
+}
+
+void cuda_check(cudaError_t e, const char *what, const char *file, int line) {
+    if (e == cudaSuccess) return;
+    const ttc_status st = e == cudaErrorMemoryAllocation ? TTC_ERR_NOMEM : TTC_ERR_CUDA;
+    fail(st, "%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+}
+
+void *device_alloc(size_t bytes, cudaStream_t s) {
+    uint64_t n = g_fail_after.load();
+    while (n) {
+        if (g_fail_after.compare_exchange_weak(n, n - 1)) {
+            if (n == 1) fail(TTC_ERR_NOMEM, "device allocation of %zu bytes failed (injected)", bytes);
+            break;
+        }
+    }
+    void *p = nullptr;
+    const cudaError_t e = cudaMallocAsync(&p, bytes, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        fail(TTC_ERR_NOMEM, "device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+    }
+    g_bytes += bytes;
+    return p;
+}
+
+void device_free(void *p, cudaStream_t s) {
+    if (p) cudaFreeAsync(p, s);
+}
+
+uint64_t device_bytes_in_use() { return g_bytes.load(); }
+
+int sm_count() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+void set_last_error(const std::string &m) { g_last_error = m; }
+
+// Normalised copy of a delta-triple (leaves every count unchanged):
+//   d12 <- min(d12, d13), d23 <- min(d23, d13), d13 <- min(d13, d12 + d23).
+void normalise(const ttc_delta &d, int64_t out[3]) {
+    const int64_t LIM = int64_t(1) << 62;
+    if (d.d13 < 0 || d.d12 < 0 || d.d23 < 0 || d.d13 > LIM || d.d12 > LIM || d.d23 > LIM)
+        fail(TTC_ERR_RANGE, "delta components must lie in [0, 2^62]");
+    const int64_t d12 = d.d12 < d.d13 ? d.d12 : d.d13;
+    const int64_t d23 = d.d23 < d.d13 ? d.d23 : d.d13;
+    const int64_t d13 = d.d13 < d12 + d23 ? d.d13 : d12 + d23;
+    out[0] = d13; out[1] = d12; out[2] = d23;
+}
+
+}  // namespace ttc
+
+using namespace ttc;
+
+#define TTC_API_BEGIN try {
+#define TTC_API_END                                    \
+    }                                                  \
+    catch (const Failure &f) {                         \
+        set_last_error(f.message);                     \
+        return f.status;                               \
+    }                                                  \
+    catch (const std::bad_alloc &) {                   \
+        set_last_error("host allocation failed");      \
+        return TTC_ERR_NOMEM;                          \
+    }                                                  \
+    catch (...) {                                      \
+        set_last_error("unexpected internal failure"); \
+        return TTC_ERR_INTERNAL;                       \
+    }
+
+namespace {
+
+void graph_destroy(ttc_graph *g) {
+    if (!g) return;
+    cudaSetDevice(g->device);
+    cudaStream_t s = g->stream;
+    for (auto &e : g->prof) {
+        cudaEventDestroy(e.start);
+        cudaEventDestroy(e.stop);
+    }
+    g->key.reset(); g->fwd.reset(); g->poff.reset(); g->pair_vtx.reset(); g->tri.reset();
+    g->heavy_eoff.reset(); g->acc.reset(); g->dq.reset(); g->scratch.reset();
+    if (s) cudaStreamSynchronize(s);
+    if (g->own_stream && s) cudaStreamDestroy(s);
+    delete g;
+}
+
+uint64_t graph_device_bytes(const ttc_graph *g) {
+    return g->key.bytes() + g->fwd.bytes() + g->poff.bytes() + g->pair_vtx.bytes() + g->tri.bytes() +
+           g->heavy_eoff.bytes() + g->acc.bytes() + g->dq.bytes() + g->scratch.bytes();
+}
+
+// Runs k normalised queries and copies the counts to out (host).
+ttc_status run_queries(ttc_graph *g, const ttc_delta *d, uint32_t k, uint64_t *out) {
+    std::vector<int64_t> hq(3 * (size_t)k);
+    for (uint32_t q = 0; q < k; q++) normalise(d[q], &hq[3 * (size_t)q]);
+    std::lock_guard<std::mutex> lock(g->mu);
+    TTC_CUDA(cudaSetDevice(g->device));
+    cudaStream_t s = g->stream;
+    if (g->acc_cap < k) {
+        g->acc.alloc(8 * (size_t)k + 1, s);
+        g->dq.alloc(3 * (size_t)k, s);
+        g->acc_cap = k;
+    }
+    TTC_CUDA(cudaMemcpyAsync(g->dq.get(), hq.data(), hq.size() * 8, cudaMemcpyHostToDevice, s));
+    TTC_CUDA(cudaMemsetAsync(g->acc.get(), 0, (8 * (size_t)k + 1) * 8, s));
+    prof_reset(g);
+    count_queue(g, g->dq.get(), k, g->acc.get(), s);
+    std::vector<unsigned long long> h(8 * (size_t)k + 1);
+    TTC_CUDA(cudaMemcpyAsync(h.data(), g->acc.get(), h.size() * 8, cudaMemcpyDeviceToHost, s));
+    TTC_CUDA(cudaStreamSynchronize(s));
+    if (h[8 * (size_t)k]) fail(TTC_ERR_OVERFLOW, "a count exceeds 2^64 - 1");
+    memcpy(out, h.data(), 8 * (size_t)k * 8);
+    return TTC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *ttc_last_error(void) { return g_last_error.c_str(); }
+
+const char *ttc_version(void) { return "ttc 0.1 (sm_103a)"; }
+
+void ttc_debug_fail_alloc_after(uint64_t n) { g_fail_after.store(n); }
+
+uint64_t ttc_debug_launch_count(void) { return g_launches.load(); }
+
+ttc_status ttc_set_profiling(ttc_graph *g, int on) {
+    if (!g) {
+        set_last_error("NULL graph");
+        return TTC_ERR_INVALID;
+    }
+    std::lock_guard<std::mutex> lock(g->mu);
+    g->profiling = on != 0;
+    g->prof_used = 0;
+    return TTC_OK;
+}
+
+uint32_t ttc_profile_read(ttc_graph *g, ttc_kernel_time *out, uint32_t cap) {
+    if (!g || !out) return 0;
+    std::lock_guard<std::mutex> lock(g->mu);
+    uint32_t n = 0;
+    for (size_t i = 0; i < g->prof_used && n < cap; i++) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(g->prof[i].stop) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, g->prof[i].start, g->prof[i].stop) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        snprintf(out[n].name, sizeof out[n].name, "%s", g->prof[i].name);
+        out[n].ms = ms;
+        n++;
+    }
+    return n;
+}
+
+ttc_status ttc_load_ex(const uint32_t *src, const uint32_t *dst, const int64_t *t, uint64_t m,
+                       const ttc_load_opts *opts, ttc_graph **out) {
+    if (!out) {
+        set_last_error("out is NULL");
+        return TTC_ERR_INVALID;
+    }
+    *out = nullptr;
+    if (m && (!src || !dst || !t)) {
+        set_last_error("src, dst and t must be non-NULL when m > 0");
+        return TTC_ERR_INVALID;
+    }
+    ttc_graph *g = nullptr;
+    TTC_API_BEGIN
+    LoadOptions lo;
+    if (opts) {
+        lo.flags = opts->flags;
+        lo.orientation = opts->orientation;
+        lo.labeling = opts->labeling;
+        lo.light_max_pairs = opts->light_max_pairs;
+        lo.seed = opts->seed;
+        if (lo.flags & ~TTC_LOAD_DEVICE_INPUT) fail(TTC_ERR_INVALID, "unknown load flags 0x%x", lo.flags);
+    }
+    g = new ttc_graph();
+    TTC_CUDA(cudaGetDevice(&g->device));
+    if (opts && opts->stream) {
+        g->stream = static_cast<cudaStream_t>(opts->stream);
+    } else {
+        TTC_CUDA(cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking));
+        g->own_stream = true;
+    }
+    build_graph(g, src, dst, t, m, lo);
+    g->st.device_bytes = graph_device_bytes(g);
+    *out = g;
+    return TTC_OK;
+    }
+    catch (const Failure &f) {
+        set_last_error(f.message);
+        graph_destroy(g);
+        return f.status;
+    }
+    catch (const std::bad_alloc &) {
+        set_last_error("host allocation failed");
+        graph_destroy(g);
+        return TTC_ERR_NOMEM;
+    }
+    catch (...) {
+        set_last_error("unexpected internal failure");
+        graph_destroy(g);
+        return TTC_ERR_INTERNAL;
+    }
+}
+
+ttc_graph *ttc_load(const uint32_t *src, const uint32_t *dst, const int64_t *t, uint64_t m) {
+    ttc_graph *g = nullptr;
+    return ttc_load_ex(src, dst, t, m, nullptr, &g) == TTC_OK ? g : nullptr;
+}
+
+void ttc_free(ttc_graph *g) { graph_destroy(g); }
+
+ttc_status ttc_graph_info(const ttc_graph *g, ttc_graph_stats *s) {
+    if (!g || !s) {
+        set_last_error("NULL argument");
+        return TTC_ERR_INVALID;
+    }
+    *s = g->st;
+    s->device_bytes = graph_device_bytes(g);
+    return TTC_OK;
+}
+
+ttc_status ttc_count(ttc_graph *g, const ttc_delta *d, uint64_t out[TTC_NUM_TYPES]) {
+    if (!g || !d || !out) {
+        set_last_error("NULL argument");
+        return TTC_ERR_INVALID;
+    }
+    TTC_API_BEGIN
+    return run_queries(g, d, 1, out);
+    TTC_API_END
+}
+
+ttc_status ttc_count_batch(ttc_graph *g, const ttc_delta *d, uint32_t k, uint64_t *out) {
+    if (!g || (k && (!d || !out))) {
+        set_last_error("NULL argument");
+        return TTC_ERR_INVALID;
+    }
+    if (!k) return TTC_OK;
+    TTC_API_BEGIN
+    return run_queries(g, d, k, out);
+    TTC_API_END
+}
+
+ttc_status ttc_count_batch_async(ttc_graph *g, const ttc_delta *d_dev, uint32_t k, uint64_t *out_dev,
+                                 void *stream) {
+    if (!g || (k && (!d_dev || !out_dev))) {
+        set_last_error("NULL argument");
+        return TTC_ERR_INVALID;
+    }
+    if (!k) return TTC_OK;
+    TTC_API_BEGIN
+    TTC_CUDA(cudaSetDevice(g->device));
+    cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : g->stream;
+    TTC_CUDA(cudaMemsetAsync(out_dev, 0, 8 * (size_t)k * 8, s));
+    DevBuf<int64_t> dq(3 * (size_t)k, s);  // freed in stream order after the kernels
+    TTC_CUDA(cudaMemcpyAsync(dq.get(), d_dev, 3 * (size_t)k * 8, cudaMemcpyDeviceToDevice, s));
+    normalise_kernel<<<(k + 127) / 128, 128, 0, s>>>(dq.get(), k);
+    TTC_LAUNCH_CHECK();
+    std::lock_guard<std::mutex> lock(g->mu);
+    prof_reset(g);
+    count_queue(g, dq.get(), k, reinterpret_cast<unsigned long long *>(out_dev), s);
+    return TTC_OK;
+    TTC_API_END
+}
+
+ttc_status ttc_count_multi(ttc_graph *const *g, const ttc_delta *d, uint32_t G, uint64_t *out) {
+    if (G && (!g || !d || !out)) {
+        set_last_error("NULL argument");
+        return TTC_ERR_INVALID;
+    }
+    TTC_API_BEGIN
+    for (uint32_t i = 0; i < G; i++) {
+        if (!g[i]) fail(TTC_ERR_INVALID, "graph %u is NULL", i);
+        run_queries(g[i], d + i, 1, out + 8 * (size_t)i);
+    }
+    return TTC_OK;
+    TTC_API_END
+}
+
+ttc_status ttc_count_sample(ttc_graph *g, const ttc_delta *d, uint64_t first, uint64_t stride, uint64_t cap,
+                            uint32_t *tri, uint64_t *out, uint64_t *written) {
+    if (!g || !d || !written || (cap && (!tri || !out)) || !stride) {
+        set_last_error("NULL argument or zero stride");
+        return TTC_ERR_INVALID;
+    }
+    TTC_API_BEGIN
+    fail(TTC_ERR_INTERNAL, "not built yet");
+    TTC_API_END
+}
+
+}  // extern "C"

@@ -1,0 +1,704 @@
+// ttc_load: everything of Alg. 1 that does not depend on the delta-triple.
+//
+//   a1 ingest      validate ids/timestamps, drop self-loops (Sec. 3)
+//   a2 pairs       static graph G: group edges by vertex pair, multiplicity
+//                  per pair, per-pair edge lists sorted by key (t, index)
+//   a3 peel        degeneracy ordering by a bucketed parallel k-core peel
+//                  (Sec. 3, Matula-Beck); one thread-block cluster runs every
+//                  round, separated by cluster barriers
+//   a4 orient      DAG G< and its out-CSR, neighbours sorted by id
+//   a6 triangles   for each oriented edge (u, v): N+(u) intersected with
+//                  N+(v) (Sec. 5: u < v < w in the ordering)
+//   records        per triangle the three pair ids, labelled for counting
+//                  (which pair is only searched) and split into the light
+//                  and heavy (prefix-sum) bins
+#include <cooperative_groups.h>
+
+#include "graph.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace ttc {
+
+namespace {
+
+constexpr int TPB = 256;
+constexpr uint32_t UNSET = 0xffffffffu;
+
+inline unsigned grid_for(size_t n, int tpb = TPB) {
+    size_t b = (n + tpb - 1) / tpb;
+    if (b < 1) b = 1;
+    const size_t cap = (size_t)sm_count() * 32;
+    return (unsigned)(b < cap ? b : cap);
+}
+
+#define GRID_STRIDE(i, n) \
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += (size_t)gridDim.x * blockDim.x)
+
+struct IngestStats {
+    unsigned long long loops;
+    unsigned int max_id;
+    unsigned int bad_id;
+    unsigned int bad_t;
+};
+
+__global__ void ingest_check_kernel(const uint32_t *src, const uint32_t *dst, const int64_t *t, size_t m,
+                                    uint8_t *keep, IngestStats *st) {
+    const int64_t TLIM = (int64_t)1 << 62;
+    unsigned int my_max = 0, bad_id = 0, bad_t = 0;
+    unsigned long long loops = 0;
+    GRID_STRIDE(i, m) {
+        const uint32_t a = src[i], b = dst[i];
+        const int64_t tt = t[i];
+        keep[i] = a != b;
+        loops += a == b;
+        my_max = max(my_max, max(a, b));
+        bad_id |= (a >> 31) | (b >> 31);
+        bad_t |= (tt < -TLIM) | (tt > TLIM);
+    }
+    for (int o = 16; o; o >>= 1) {
+        my_max = max(my_max, __shfl_xor_sync(0xffffffffu, my_max, o));
+        bad_id |= __shfl_xor_sync(0xffffffffu, bad_id, o);
+        bad_t |= __shfl_xor_sync(0xffffffffu, bad_t, o);
+        loops += __shfl_xor_sync(0xffffffffu, loops, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&st->max_id, my_max);
+        if (bad_id) atomicOr(&st->bad_id, 1u);
+        if (bad_t) atomicOr(&st->bad_t, 1u);
+        if (loops) atomicAdd(&st->loops, loops);
+    }
+}
+
+// kept edges in input order: eidx = original index, tk = timestamp
+__global__ void compact_kernel(const uint8_t *keep, const uint32_t *pos, size_t m, const int64_t *t,
+                               uint32_t *eidx, int64_t *tk) {
+    GRID_STRIDE(i, m) {
+        if (keep[i]) {
+            eidx[pos[i]] = (uint32_t)i;
+            tk[pos[i]] = t[i];
+        }
+    }
+}
+
+__global__ void time_key_kernel(int64_t *tk, size_t m, int64_t tmin, uint64_t *tkey, uint32_t *vals,
+                                const uint32_t *eidx) {
+    GRID_STRIDE(i, m) {
+        tkey[i] = (uint64_t)(tk[i] - tmin);
+        vals[i] = eidx[i];
+    }
+}
+
+__global__ void head_flags_kernel(const uint64_t *k, size_t m, uint8_t *head) {
+    GRID_STRIDE(i, m) head[i] = (i == 0) || (k[i] != k[i - 1]);
+}
+
+__global__ void group_start_kernel(const uint8_t *head, const uint32_t *gid, size_t m, uint32_t *gstart) {
+    GRID_STRIDE(i, m) if (head[i]) gstart[gid[i]] = (uint32_t)i;
+}
+
+__global__ void group_rank_max_kernel(const uint32_t *gid, const uint32_t *gstart, size_t m,
+                                      unsigned int *max_rank) {
+    unsigned int mx = 0;
+    GRID_STRIDE(i, m) mx = max(mx, (uint32_t)i - gstart[gid[i]]);
+    for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0 && mx) atomicMax(max_rank, mx);
+}
+
+// packed key and pair key per time-sorted edge
+__global__ void pack_kernel(const uint64_t *tkey, const uint32_t *eidx, const uint32_t *gid,
+                            const uint32_t *gstart, const uint32_t *src, const uint32_t *dst, size_t m, int shift,
+                            uint64_t n, uint64_t *pkey, uint64_t *key) {
+    GRID_STRIDE(i, m) {
+        const uint32_t e = eidx[i];
+        const uint32_t a = src[e], b = dst[e];
+        const uint64_t rank = (uint32_t)i - gstart[gid[i]];
+        const uint64_t dir = a > b;  // 1: from the larger id to the smaller
+        key[i] = (tkey[i] << shift) | (rank << 1) | dir;
+        const uint64_t lo = min(a, b), hi = max(a, b);
+        pkey[i] = lo * n + hi;
+    }
+}
+
+__global__ void pair_rle_kernel(const uint64_t *pkey, const uint8_t *head, const uint32_t *pid, size_t m,
+                                uint64_t n, uint32_t *poff, uint2 *pair_vtx) {
+    GRID_STRIDE(i, m) {
+        if (head[i]) {
+            const uint32_t p = pid[i];
+            poff[p] = (uint32_t)i;
+            pair_vtx[p] = make_uint2((uint32_t)(pkey[i] / n), (uint32_t)(pkey[i] % n));
+        }
+    }
+}
+
+__global__ void dir0_flags_kernel(const int64_t *key, size_t m, uint8_t *f) {
+    GRID_STRIDE(i, m) f[i] = (key[i] & 1) == 0;
+}
+
+__global__ void pair_sizes_kernel(const uint32_t *poff, size_t ms, const uint2 *pv, unsigned int *deg,
+                                  unsigned int *sigma_max) {
+    unsigned int mx = 0;
+    GRID_STRIDE(p, ms) {
+        mx = max(mx, poff[p + 1] - poff[p]);
+        atomicAdd(&deg[pv[p].x], 1u);
+        atomicAdd(&deg[pv[p].y], 1u);
+    }
+    for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(sigma_max, mx);
+}
+
+__global__ void adj_fill_kernel(const uint2 *pv, size_t ms, uint32_t *cursor, uint32_t *adj) {
+    GRID_STRIDE(p, ms) {
+        adj[atomicAdd(&cursor[pv[p].x], 1u)] = pv[p].y;
+        adj[atomicAdd(&cursor[pv[p].y], 1u)] = pv[p].x;
+    }
+}
+
+// ---------------------------------------------------------------- k-core peel
+struct PeelCtl {
+    unsigned long long front[2];  // per iteration parity: (count << 40) | edge total
+    unsigned int next_n[2];
+    int min_deg[2];
+    unsigned int kappa;
+    unsigned int rounds;
+    unsigned int error;
+    unsigned int pad;
+};
+
+constexpr uint64_t MASK40 = (uint64_t(1) << 40) - 1;
+constexpr int PEEL_THREADS = 1024;
+constexpr int PEEL_RUN = 16;  // relaxed edges per thread per step
+
+// Level-synchronous peel: at level k every remaining vertex of degree <= k
+// is removed in the current round (all at once), and its remaining
+// neighbours lose one degree each; when no vertex qualifies, k rises to the
+// smallest remaining degree.  level[v] = round in which v was removed.  The
+// orientation "lower (round, id) -> higher" gives every vertex at most k
+// out-neighbours, k <= kappa.
+__global__ void __launch_bounds__(PEEL_THREADS)
+    peel_kernel(const uint32_t *__restrict__ adj_off, const uint32_t *__restrict__ adj, int *deg,
+                uint32_t *level, uint32_t *remA, uint32_t *remB, uint32_t *front, uint32_t *foff, uint32_t n,
+                PeelCtl *ctl) {
+    cg::cluster_group cluster = cg::this_cluster();
+    const uint32_t nthr = cluster.num_blocks() * blockDim.x;
+    const uint32_t tid = cluster.block_rank() * blockDim.x + threadIdx.x;
+    const uint32_t lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    uint32_t *rem = remA, *nxt = remB;
+    uint32_t rem_n = n;
+    bool identity = true;  // first pass: the remaining set is 0..n-1
+    int k = 0;
+    uint32_t round = 0, kappa = 0;
+    const uint64_t it_cap = 2ull * n + 4;
+    for (uint64_t it = 0;; it++) {
+        const int par = (int)(it & 1);
+        if (it > it_cap) {
+            if (tid == 0) ctl->error = 1;
+            break;
+        }
+        int my_min = INT_MAX;
+        for (uint32_t base = 0; base < rem_n; base += nthr) {
+            const uint32_t i = base + tid;
+            const bool ok = i < rem_n;
+            uint32_t v = 0;
+            int d = 0;
+            if (ok) {
+                v = identity ? i : __ldcg(rem + i);
+                d = __ldcg(deg + v);
+            }
+            const bool to_front = ok && d <= k;
+            const bool to_next = ok && !to_front;
+            if (to_next) my_min = min(my_min, d);
+            const uint64_t pk = to_front ? ((uint64_t(1) << 40) | (uint64_t)(adj_off[v + 1] - adj_off[v])) : 0;
+            uint64_t x = pk;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= (uint32_t)o) x += y;
+            }
+            const uint64_t tot = __shfl_sync(0xffffffffu, x, 31);
+            uint64_t fb = 0;
+            if (lane == 31 && tot) fb = atomicAdd(&ctl->front[par], (unsigned long long)tot);
+            fb = __shfl_sync(0xffffffffu, fb, 31);
+            if (to_front) {
+                const uint64_t mine = fb + x - pk;
+                const uint32_t fi = (uint32_t)(mine >> 40);
+                front[fi] = v;
+                foff[fi] = (uint32_t)(mine & MASK40);
+                level[v] = round;
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, to_next);
+            uint32_t nb = 0;
+            if (lane == 0 && bal) nb = atomicAdd(&ctl->next_n[par], (unsigned)__popc(bal));
+            nb = __shfl_sync(0xffffffffu, nb, 0);
+            if (to_next) nxt[nb + __popc(bal & lt_mask)] = v;
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) my_min = min(my_min, __shfl_xor_sync(0xffffffffu, my_min, o));
+        if (lane == 0 && my_min != INT_MAX) atomicMin(&ctl->min_deg[par], my_min);
+        cluster.sync();
+        const uint64_t fr = __ldcg(&ctl->front[par]);
+        const uint32_t fn = (uint32_t)(fr >> 40), fe = (uint32_t)(fr & MASK40);
+        const uint32_t nn = __ldcg(&ctl->next_n[par]);
+        const int md = __ldcg(&ctl->min_deg[par]);
+        if (tid == 0) {
+            ctl->front[par ^ 1] = 0;
+            ctl->next_n[par ^ 1] = 0;
+            ctl->min_deg[par ^ 1] = INT_MAX;
+        }
+        if (fn == 0 && nn == 0) break;
+        uint32_t *tmp = rem;
+        rem = nxt;
+        nxt = tmp;
+        rem_n = nn;
+        identity = false;
+        if (fn == 0) {
+            k = md;
+            cluster.sync();
+            continue;
+        }
+        kappa = max(kappa, (uint32_t)k);
+        // relax the frontier's edges: thread runs of PEEL_RUN consecutive edges
+        for (uint32_t e0 = tid * PEEL_RUN; e0 < fe; e0 += nthr * PEEL_RUN) {
+            uint32_t lo = 0, hi = fn;  // last fi with foff[fi] <= e0
+            while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (__ldcg(foff + mid) <= e0) lo = mid; else hi = mid;
+            }
+            uint32_t fi = lo;
+            uint32_t fbeg = __ldcg(foff + fi);
+            uint32_t fend = fi + 1 < fn ? __ldcg(foff + fi + 1) : fe;
+            uint32_t v = __ldcg(front + fi);
+            const uint32_t e1 = min(fe, e0 + PEEL_RUN);
+            for (uint32_t e = e0; e < e1; e++) {
+                while (e >= fend) {
+                    fi++;
+                    fbeg = fend;
+                    fend = fi + 1 < fn ? __ldcg(foff + fi + 1) : fe;
+                    v = __ldcg(front + fi);
+                }
+                const uint32_t w = adj[adj_off[v] + (e - fbeg)];
+                if (__ldcg(level + w) == UNSET) atomicSub(deg + w, 1);
+            }
+        }
+        round++;
+        cluster.sync();
+    }
+    if (tid == 0) {
+        ctl->rounds = round;
+        ctl->kappa = kappa;
+    }
+}
+
+__device__ __forceinline__ uint32_t mix32(uint64_t x) {
+    // splitmix64 finaliser, used only to draw a random vertex order
+    x += 0x9e3779b97f4a7c15ull;
+    x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ull;
+    x = (x ^ (x >> 27)) * 0x94d049bb133111ebull;
+    return (uint32_t)(x ^ (x >> 31));
+}
+
+__global__ void order_key_kernel(uint32_t n, uint32_t orientation, const uint32_t *level, const unsigned int *deg,
+                                 uint64_t seed, uint64_t *rk) {
+    GRID_STRIDE(v, (size_t)n) {
+        uint64_t hi;
+        switch (orientation) {
+            case TTC_ORIENT_ID: hi = 0; break;
+            case TTC_ORIENT_DEGREE: hi = deg[v]; break;
+            case TTC_ORIENT_RANDOM: hi = mix32(seed ^ (v * 0x100000001b3ull)); break;
+            default: hi = level[v]; break;
+        }
+        rk[v] = (hi << 32) | (uint64_t)v;
+    }
+}
+
+__global__ void orient_kernel(const uint2 *pv, size_t ms, const uint64_t *rk, uint64_t n, uint64_t *okey,
+                              uint32_t *oval, unsigned int *outdeg) {
+    GRID_STRIDE(p, ms) {
+        const uint32_t a = pv[p].x, b = pv[p].y;
+        const bool ab = rk[a] < rk[b];
+        const uint32_t s = ab ? a : b, d = ab ? b : a;
+        okey[p] = (uint64_t)s * n + d;
+        oval[p] = (uint32_t)p;
+        atomicAdd(&outdeg[s], 1u);
+    }
+}
+
+__global__ void split_okey_kernel(const uint64_t *okey, size_t ms, uint64_t n, uint32_t *osrc, uint32_t *onbr) {
+    GRID_STRIDE(i, ms) {
+        osrc[i] = (uint32_t)(okey[i] / n);
+        onbr[i] = (uint32_t)(okey[i] % n);
+    }
+}
+
+__global__ void max_u32_kernel(const unsigned int *x, size_t n, unsigned int *mx_out) {
+    unsigned int mx = 0;
+    GRID_STRIDE(i, n) mx = max(mx, x[i]);
+    for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0 && mx) atomicMax(mx_out, mx);
+}
+
+// ---------------------------------------------------------------- triangles
+struct RecCtx {
+    const uint32_t *poff;
+    const uint2 *pv;
+    uint32_t labeling;
+    uint64_t light_max;
+};
+
+__device__ __forceinline__ uint32_t psize(const RecCtx &c, uint32_t p) { return c.poff[p + 1] - c.poff[p]; }
+
+// Names the triangle's vertices u, v, w for counting and returns the record.
+// (u0, v0, w0) come from the enumeration (u0 < v0 < w0 in the ordering), with
+// pairs p_uv, p_uw, p_vw.
+__device__ uint4 make_record(const RecCtx &c, uint32_t u0, uint32_t v0, uint32_t w0, uint32_t p_uv,
+                             uint32_t p_uw, uint32_t p_vw, bool *heavy) {
+    uint32_t U = u0, V = v0, W = w0, A = p_uv, B = p_uw, C = p_vw;
+    const uint32_t s_uv = psize(c, p_uv), s_uw = psize(c, p_uw), s_vw = psize(c, p_vw);
+    if (c.labeling == TTC_LABEL_HEAVIEST_VW) {
+        if (s_uw > s_vw && s_uw >= s_uv) {  // {u0, w0} is only searched
+            U = v0; V = u0; W = w0; A = p_uv; B = p_vw; C = p_uw;
+        } else if (s_uv > s_vw && s_uv > s_uw) {  // {u0, v0}
+            U = w0; V = u0; W = v0; A = p_uw; B = p_vw; C = p_uv;
+        }
+    }
+    const uint32_t flags = (U > V ? TriRec::FLIP_A : 0u) | (U > W ? TriRec::FLIP_B : 0u) | (V > W ? TriRec::FLIP_C : 0u);
+    *heavy = (uint64_t)psize(c, A) * psize(c, B) >= c.light_max;
+    return make_uint4(A, B, C, flags);
+}
+
+// Intersect two sorted id lists; calls f(i, j) for every common element.
+template <typename F>
+__device__ __forceinline__ void intersect(const uint32_t *a, uint32_t na, const uint32_t *b, uint32_t nb, F f) {
+    uint32_t i = 0, j = 0;
+    while (i < na && j < nb) {
+        const uint32_t x = a[i], y = b[j];
+        if (x < y) i++;
+        else if (y < x) j++;
+        else { f(i, j); i++; j++; }
+    }
+}
+
+__global__ void tri_count_kernel(const uint32_t *osrc, const uint32_t *onbr, const uint32_t *out_off, size_t ms,
+                                 uint64_t *cnt) {
+    GRID_STRIDE(e, ms) {
+        const uint32_t u = osrc[e], v = onbr[e];
+        uint64_t c = 0;
+        intersect(onbr + out_off[u], out_off[u + 1] - out_off[u], onbr + out_off[v], out_off[v + 1] - out_off[v],
+                  [&](uint32_t, uint32_t) { c++; });
+        cnt[e] = c;
+    }
+}
+
+__global__ void tri_write_kernel(const uint32_t *osrc, const uint32_t *onbr, const uint32_t *opair,
+                                 const uint32_t *out_off, size_t ms, const uint64_t *tri_off, RecCtx rc,
+                                 uint4 *rec, uint8_t *is_light) {
+    GRID_STRIDE(e, ms) {
+        const uint32_t u = osrc[e], v = onbr[e];
+        uint64_t o = tri_off[e];
+        const uint32_t bu = out_off[u], bv = out_off[v];
+        intersect(onbr + bu, out_off[u + 1] - bu, onbr + bv, out_off[v + 1] - bv, [&](uint32_t i, uint32_t j) {
+            bool heavy;
+            rec[o] = make_record(rc, u, v, onbr[bu + i], opair[e], opair[bu + i], opair[bv + j], &heavy);
+            is_light[o] = !heavy;
+            o++;
+        });
+    }
+}
+
+__global__ void partition_kernel(const uint4 *rec, const uint8_t *is_light, const uint32_t *lpos, size_t tau,
+                                 uint64_t n_light, uint4 *out) {
+    GRID_STRIDE(i, tau) {
+        const uint64_t dst = is_light[i] ? lpos[i] : n_light + (i - lpos[i]);
+        out[dst] = rec[i];
+    }
+}
+
+// sizes of heavy records and the work statistics of all records
+__global__ void record_stats_kernel(const uint4 *rec, size_t tau, uint64_t n_light, const uint32_t *poff,
+                                    uint64_t *heavy_e, unsigned long long *sums) {
+    unsigned long long w = 0, en = 0, wh = 0;
+    GRID_STRIDE(i, tau) {
+        const uint4 r = rec[i];
+        const uint64_t a = poff[r.x + 1] - poff[r.x], b = poff[r.y + 1] - poff[r.y], c = poff[r.z + 1] - poff[r.z];
+        w += 8 * (a + b + c) + 12;
+        en += a + b;
+        if (i >= n_light) {
+            heavy_e[i - n_light] = a + b;
+            wh += 8 * (a + b + c) + 12;
+        }
+    }
+    for (int o = 16; o; o >>= 1) {
+        w += __shfl_xor_sync(0xffffffffu, w, o);
+        en += __shfl_xor_sync(0xffffffffu, en, o);
+        wh += __shfl_xor_sync(0xffffffffu, wh, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(sums, w);
+        atomicAdd(sums + 1, en);
+        atomicAdd(sums + 2, wh);
+    }
+}
+
+template <typename T>
+T read_scalar(const T *dev, cudaStream_t s) {
+    T h;
+    TTC_CUDA(cudaMemcpyAsync(&h, dev, sizeof(T), cudaMemcpyDeviceToHost, s));
+    TTC_CUDA(cudaStreamSynchronize(s));
+    return h;
+}
+
+}  // namespace
+
+uint32_t default_light_max_pairs() { return 65; }
+
+void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, const int64_t *t_in, uint64_t m_in,
+                 const LoadOptions &opt) {
+    cudaStream_t s = g->stream;
+    ttc_graph_stats &st = g->st;
+    g->labeling = opt.labeling;
+    g->light_max_pairs = opt.light_max_pairs ? opt.light_max_pairs : default_light_max_pairs();
+    if (opt.orientation > TTC_ORIENT_RANDOM) fail(TTC_ERR_INVALID, "unknown orientation %u", opt.orientation);
+    if (opt.labeling > TTC_LABEL_SOURCE) fail(TTC_ERR_INVALID, "unknown labeling %u", opt.labeling);
+    if (m_in >= (uint64_t(1) << 32) - 1) fail(TTC_ERR_RANGE, "m = %llu exceeds 2^32 - 2 edges", (unsigned long long)m_in);
+    const size_t m0 = (size_t)m_in;
+
+    // ---- a1: inputs on the device, validated
+    DevBuf<uint32_t> src_buf, dst_buf;
+    DevBuf<int64_t> t_buf;
+    const uint32_t *src = src_in, *dst = dst_in;
+    const int64_t *t = t_in;
+    if (!(opt.flags & TTC_LOAD_DEVICE_INPUT) && m0) {
+        src_buf.alloc(m0, s); dst_buf.alloc(m0, s); t_buf.alloc(m0, s);
+        TTC_CUDA(cudaMemcpyAsync(src_buf.get(), src_in, m0 * 4, cudaMemcpyHostToDevice, s));
+        TTC_CUDA(cudaMemcpyAsync(dst_buf.get(), dst_in, m0 * 4, cudaMemcpyHostToDevice, s));
+        TTC_CUDA(cudaMemcpyAsync(t_buf.get(), t_in, m0 * 8, cudaMemcpyHostToDevice, s));
+        src = src_buf.get(); dst = dst_buf.get(); t = t_buf.get();
+    }
+    DevBuf<IngestStats> ist(1, s);
+    TTC_CUDA(cudaMemsetAsync(ist.get(), 0, sizeof(IngestStats), s));
+    DevBuf<uint8_t> keep(m0 + 1, s);
+    if (m0) {
+        ingest_check_kernel<<<grid_for(m0), TPB, 0, s>>>(src, dst, t, m0, keep.get(), ist.get());
+        TTC_LAUNCH_CHECK();
+    }
+    const IngestStats is = read_scalar(ist.get(), s);
+    if (is.bad_id) fail(TTC_ERR_RANGE, "vertex id >= 2^31");
+    if (is.bad_t) fail(TTC_ERR_RANGE, "timestamp outside [-2^62, 2^62]");
+    st.m_self_loops = is.loops;
+    const size_t m = m0 - (size_t)is.loops;
+    st.m = m;
+    const uint64_t n = m ? (uint64_t)is.max_id + 1 : 0;
+    st.n = m0 ? (uint64_t)is.max_id + 1 : 0;
+    g->key.alloc(m, s);
+    g->fwd.alloc(m + 1, s);
+    if (m == 0) {
+        g->poff.alloc(1, s);
+        TTC_CUDA(cudaMemsetAsync(g->poff.get(), 0, 4, s));
+        TTC_CUDA(cudaMemsetAsync(g->fwd.get(), 0, 4, s));
+        g->heavy_eoff.alloc(1, s);
+        TTC_CUDA(cudaMemsetAsync(g->heavy_eoff.get(), 0, 8, s));
+        TTC_CUDA(cudaStreamSynchronize(s));
+        return;
+    }
+
+    // kept edges, input order
+    DevBuf<uint32_t> eidx(m, s);
+    DevBuf<int64_t> tk(m, s);
+    {
+        DevBuf<uint32_t> pos(m0 + 1, s);
+        exclusive_scan_flags(keep.get(), pos.get(), m0, s);
+        compact_kernel<<<grid_for(m0), TPB, 0, s>>>(keep.get(), pos.get(), m0, t, eidx.get(), tk.get());
+        TTC_LAUNCH_CHECK();
+    }
+    keep.reset();
+    DevBuf<int64_t> mm(2, s);
+    reduce_minmax_i64(tk.get(), m, mm.get(), mm.get() + 1, s);
+    int64_t hmm[2];
+    TTC_CUDA(cudaMemcpyAsync(hmm, mm.get(), 16, cudaMemcpyDeviceToHost, s));
+    TTC_CUDA(cudaStreamSynchronize(s));
+    g->tmin = hmm[0];
+    g->span = hmm[1] - hmm[0];
+    const int span_bits = bits_for((uint64_t)g->span);
+
+    // ---- a2: sort by time (stable, so equal timestamps keep input order)
+    DevBuf<uint64_t> tkey(m, s);
+    time_key_kernel<<<grid_for(m), TPB, 0, s>>>(tk.get(), m, g->tmin, tkey.get(), eidx.get(), eidx.get());
+    TTC_LAUNCH_CHECK();
+    tk.reset();
+    radix_sort_u64_u32(tkey.get(), eidx.get(), m, span_bits, s);
+    // rank inside each equal-timestamp group
+    DevBuf<uint8_t> head(m, s);
+    DevBuf<uint32_t> gid(m + 1, s);
+    head_flags_kernel<<<grid_for(m), TPB, 0, s>>>(tkey.get(), m, head.get());
+    TTC_LAUNCH_CHECK();
+    exclusive_scan_flags(head.get(), gid.get(), m, s);
+    const uint32_t ngroups = read_scalar(gid.get() + m, s);
+    DevBuf<uint32_t> gstart(ngroups ? ngroups : 1, s);
+    group_start_kernel<<<grid_for(m), TPB, 0, s>>>(head.get(), gid.get(), m, gstart.get());
+    TTC_LAUNCH_CHECK();
+    DevBuf<unsigned int> maxr(1, s);
+    TTC_CUDA(cudaMemsetAsync(maxr.get(), 0, 4, s));
+    group_rank_max_kernel<<<grid_for(m), TPB, 0, s>>>(gid.get(), gstart.get(), m, maxr.get());
+    TTC_LAUNCH_CHECK();
+    const uint32_t max_rank = read_scalar(maxr.get(), s);
+    g->shift = bits_for(max_rank) + 1;
+    st.key_bits = (uint32_t)(span_bits + g->shift);
+    if (span_bits + g->shift > 63)
+        fail(TTC_ERR_RANGE, "timestamp span needs %d bits plus %d tie bits; at most 63 fit the packed key",
+             span_bits, g->shift);
+    if (n * n > (uint64_t(1) << 63)) fail(TTC_ERR_RANGE, "vertex ids too large for the pair key");
+
+    DevBuf<uint64_t> pkey(m, s);
+    pack_kernel<<<grid_for(m), TPB, 0, s>>>(tkey.get(), eidx.get(), gid.get(), gstart.get(), src, dst, m, g->shift,
+                                            n, pkey.get(), reinterpret_cast<uint64_t *>(g->key.get()));
+    TTC_LAUNCH_CHECK();
+    tkey.reset(); eidx.reset(); gid.reset(); gstart.reset();
+    src_buf.reset(); dst_buf.reset(); t_buf.reset();
+    // group by pair; stable, so each pair's edges stay in key order
+    radix_sort_u64_u64(pkey.get(), reinterpret_cast<uint64_t *>(g->key.get()), m, bits_for(n * n - 1), s);
+    DevBuf<uint32_t> pid(m + 1, s);
+    head_flags_kernel<<<grid_for(m), TPB, 0, s>>>(pkey.get(), m, head.get());
+    TTC_LAUNCH_CHECK();
+    exclusive_scan_flags(head.get(), pid.get(), m, s);
+    const uint32_t ms = read_scalar(pid.get() + m, s);
+    st.m_s = ms;
+    g->poff.alloc((size_t)ms + 1, s);
+    g->pair_vtx.alloc(ms, s);
+    pair_rle_kernel<<<grid_for(m), TPB, 0, s>>>(pkey.get(), head.get(), pid.get(), m, n, g->poff.get(),
+                                                g->pair_vtx.get());
+    TTC_LAUNCH_CHECK();
+    {
+        const uint32_t mm32 = (uint32_t)m;
+        TTC_CUDA(cudaMemcpyAsync(g->poff.get() + ms, &mm32, 4, cudaMemcpyHostToDevice, s));
+        TTC_CUDA(cudaStreamSynchronize(s));
+    }
+    pkey.reset(); pid.reset();
+    dir0_flags_kernel<<<grid_for(m), TPB, 0, s>>>(g->key.get(), m, head.get());
+    TTC_LAUNCH_CHECK();
+    exclusive_scan_flags(head.get(), g->fwd.get(), m, s);
+    head.reset();
+
+    // ---- static graph: undirected CSR, degrees
+    DevBuf<unsigned int> deg(n, s), smax(1, s);
+    TTC_CUDA(cudaMemsetAsync(deg.get(), 0, n * 4, s));
+    TTC_CUDA(cudaMemsetAsync(smax.get(), 0, 4, s));
+    pair_sizes_kernel<<<grid_for(ms), TPB, 0, s>>>(g->poff.get(), ms, g->pair_vtx.get(), deg.get(), smax.get());
+    TTC_LAUNCH_CHECK();
+    st.sigma_max = read_scalar(smax.get(), s);
+    g->heavy_wide = st.sigma_max >= 65536;
+
+    // ---- a3: ordering
+    DevBuf<uint32_t> level(n, s);
+    TTC_CUDA(cudaMemsetAsync(level.get(), 0xff, n * 4, s));
+    if (opt.orientation == TTC_ORIENT_DEGENERACY) {
+        if (2ull * ms >= (uint64_t(1) << 32)) fail(TTC_ERR_RANGE, "too many static edges for the peel");
+        DevBuf<uint32_t> adj_off(n + 1, s), adj(2 * (size_t)ms, s), cursor(n + 1, s);
+        exclusive_scan_u32(deg.get(), adj_off.get(), n, s);
+        TTC_CUDA(cudaMemcpyAsync(cursor.get(), adj_off.get(), (n + 1) * 4, cudaMemcpyDeviceToDevice, s));
+        adj_fill_kernel<<<grid_for(ms), TPB, 0, s>>>(g->pair_vtx.get(), ms, cursor.get(), adj.get());
+        TTC_LAUNCH_CHECK();
+        DevBuf<int> pdeg(n, s);
+        TTC_CUDA(cudaMemcpyAsync(pdeg.get(), deg.get(), n * 4, cudaMemcpyDeviceToDevice, s));
+        DevBuf<uint32_t> remA(n, s), remB(n, s), front(n, s), foff(n, s);
+        DevBuf<PeelCtl> ctl(1, s);
+        PeelCtl init{};
+        init.min_deg[0] = init.min_deg[1] = INT_MAX;
+        TTC_CUDA(cudaMemcpyAsync(ctl.get(), &init, sizeof(init), cudaMemcpyHostToDevice, s));
+        cudaLaunchConfig_t cfg = {};
+        int cluster = 8;
+        cfg.gridDim = dim3(cluster);
+        cfg.blockDim = dim3(PEEL_THREADS);
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = cluster;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        TTC_CUDA(cudaLaunchKernelEx(&cfg, peel_kernel, (const uint32_t *)adj_off.get(), (const uint32_t *)adj.get(),
+                                    pdeg.get(), level.get(), remA.get(), remB.get(), front.get(), foff.get(),
+                                    (uint32_t)n, ctl.get()));
+        note_launch();
+        const PeelCtl out = read_scalar(ctl.get(), s);
+        if (out.error) fail(TTC_ERR_INTERNAL, "k-core peel did not finish");
+        st.peel_rounds = out.rounds;
+    }
+    DevBuf<uint64_t> rk(n, s);
+    order_key_kernel<<<grid_for(n), TPB, 0, s>>>((uint32_t)n, opt.orientation, level.get(), deg.get(), opt.seed,
+                                                 rk.get());
+    TTC_LAUNCH_CHECK();
+    level.reset();
+
+    // ---- a4: orientation and out-CSR (neighbours sorted by id)
+    DevBuf<uint64_t> okey(ms, s);
+    DevBuf<uint32_t> opair(ms, s);
+    DevBuf<unsigned int> outdeg(n, s);
+    TTC_CUDA(cudaMemsetAsync(outdeg.get(), 0, n * 4, s));
+    orient_kernel<<<grid_for(ms), TPB, 0, s>>>(g->pair_vtx.get(), ms, rk.get(), n, okey.get(), opair.get(),
+                                               outdeg.get());
+    TTC_LAUNCH_CHECK();
+    rk.reset();
+    radix_sort_u64_u32(okey.get(), opair.get(), ms, bits_for(n * n - 1), s);
+    DevBuf<uint32_t> out_off(n + 1, s), osrc(ms, s), onbr(ms, s);
+    exclusive_scan_u32(outdeg.get(), out_off.get(), n, s);
+    TTC_CUDA(cudaMemsetAsync(smax.get(), 0, 4, s));
+    max_u32_kernel<<<grid_for(n), TPB, 0, s>>>(outdeg.get(), n, smax.get());
+    TTC_LAUNCH_CHECK();
+    st.kappa = read_scalar(smax.get(), s);
+    split_okey_kernel<<<grid_for(ms), TPB, 0, s>>>(okey.get(), ms, n, osrc.get(), onbr.get());
+    TTC_LAUNCH_CHECK();
+    okey.reset(); outdeg.reset(); deg.reset();
+
+    // ---- a6: triangles
+    DevBuf<uint64_t> cnt(ms, s), tri_off(ms + 1, s);
+    tri_count_kernel<<<grid_for(ms), TPB, 0, s>>>(osrc.get(), onbr.get(), out_off.get(), ms, cnt.get());
+    TTC_LAUNCH_CHECK();
+    exclusive_scan_u64(cnt.get(), tri_off.get(), ms, s);
+    const uint64_t tau = read_scalar(tri_off.get() + ms, s);
+    st.tau = tau;
+    cnt.reset();
+    RecCtx rc{g->poff.get(), g->pair_vtx.get(), g->labeling, g->light_max_pairs};
+    g->tri.alloc(tau, s);
+    uint64_t n_light = 0;
+    if (tau) {
+        DevBuf<uint4> rec(tau, s);
+        DevBuf<uint8_t> is_light(tau, s);
+        tri_write_kernel<<<grid_for(ms), TPB, 0, s>>>(osrc.get(), onbr.get(), opair.get(), out_off.get(), ms,
+                                                      tri_off.get(), rc, rec.get(), is_light.get());
+        TTC_LAUNCH_CHECK();
+        if (tau >= (uint64_t(1) << 32)) fail(TTC_ERR_RANGE, "more than 2^32 static triangles");
+        DevBuf<uint32_t> lpos(tau + 1, s);
+        exclusive_scan_flags(is_light.get(), lpos.get(), tau, s);
+        n_light = read_scalar(lpos.get() + tau, s);
+        partition_kernel<<<grid_for(tau), TPB, 0, s>>>(rec.get(), is_light.get(), lpos.get(), tau, n_light,
+                                                       g->tri.get());
+        TTC_LAUNCH_CHECK();
+    }
+    osrc.reset(); onbr.reset(); opair.reset(); out_off.reset(); tri_off.reset();
+    st.tau_light = n_light;
+    st.tau_heavy = tau - n_light;
+
+    // ---- statistics and heavy-path offsets
+    const uint64_t nh = st.tau_heavy;
+    DevBuf<uint64_t> he(nh ? nh : 1, s);
+    DevBuf<unsigned long long> ws(3, s);
+    TTC_CUDA(cudaMemsetAsync(ws.get(), 0, 24, s));
+    if (tau) {
+        record_stats_kernel<<<grid_for(tau), TPB, 0, s>>>(g->tri.get(), tau, n_light, g->poff.get(), he.get(),
+                                                          ws.get());
+        TTC_LAUNCH_CHECK();
+    }
+    unsigned long long hws[3];
+    TTC_CUDA(cudaMemcpyAsync(hws, ws.get(), 24, cudaMemcpyDeviceToHost, s));
+    g->heavy_eoff.alloc(nh + 1, s);
+    exclusive_scan_u64(he.get(), g->heavy_eoff.get(), nh, s);
+    g->heavy_elems = read_scalar(g->heavy_eoff.get() + nh, s);
+    st.work_bytes = hws[0];
+    st.enum_elems = hws[1];
+    st.work_bytes_heavy = hws[2];
+    TTC_CUDA(cudaStreamSynchronize(s));
+}
+
+}  // namespace ttc

@@ -1,0 +1,249 @@
+"""CUDA path against the CPU oracle, element by element, through the C ABI.
+
+Every count must match bit for bit (integer work).  Inputs are seeded
+synthetic graphs: random tiny multigraphs (many ties), the tiny-plain and
+delta-sweep workloads, scaled power-law graphs, and adversarial shapes.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2106_02762_gb300 import synth, ttc
+
+pytestmark = pytest.mark.gpu
+
+BIG = 1 << 40
+ALL_HEAVY = 1                 # light_max_pairs: no triangle takes the light path
+ALL_LIGHT = (1 << 32) - 1     # practically every triangle takes the light path
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+    import torch
+    assert torch.cuda.is_available()
+
+
+def _menu(rng, tr):
+    base = [(0, 0, 0), (BIG, BIG, BIG), (1, 1, 1), (tr, 0, tr), (0, tr, tr), (tr, tr, 0)]
+    for _ in range(6):
+        base.append(tuple(int(x) for x in rng.integers(0, tr + 2, size=3)))
+    return base
+
+
+def _check(src, dst, t, deltas, **opts):
+    want = oracle.count(src, dst, t, deltas)
+    g = ttc.Graph(src, dst, t, **opts)
+    try:
+        got = g.count_batch(deltas)
+        assert (got == want).all(), (opts, deltas, got, want)
+        for q in range(min(3, len(deltas))):
+            assert (g.count(deltas[q]) == want[q]).all()
+    finally:
+        g.free()
+    return want
+
+
+def test_random_tiny_every_path():
+    rng = np.random.default_rng(11)
+    combos = [dict(orientation=o, labeling=l, light_max_pairs=lm)
+              for o in range(4) for l in range(2) for lm in (0, ALL_HEAVY, ALL_LIGHT)]
+    for seed in range(120):
+        n = int(rng.integers(3, 10))
+        m = int(rng.integers(3, 60))
+        tr = int(rng.integers(1, 30))
+        s, d, t = synth.random_tiny(5000 + seed, n, m, tr)
+        deltas = _menu(rng, tr)
+        opts = combos[seed % len(combos)] if seed >= 24 else combos[seed]
+        _check(s, d, t, deltas, seed=seed, **opts)
+
+
+def test_tiny_plain_workload():
+    s, d, t = synth.tiny_plain()
+    deltas = [synth.TINY_PLAIN_DELTA, (BIG, BIG, BIG), (100_000, 60_000, 50_000)]
+    for lm in (0, ALL_HEAVY, ALL_LIGHT):
+        _check(s, d, t, deltas, light_max_pairs=lm)
+
+
+def test_delta_sweep_batch_equals_sequential_and_oracle():
+    s, d, t = synth.tiny_plain()
+    deltas = synth.delta_sweep()
+    want = oracle.count(s, d, t, deltas)
+    g = ttc.Graph(s, d, t)
+    batch = g.count_batch(deltas)
+    seq = np.stack([g.count(q) for q in deltas])
+    g.free()
+    assert (batch == want).all()
+    assert (seq == want).all()
+    assert want.sum() > 0
+
+
+def test_power_law_scaled():
+    s, d, t = synth.large_plain(scale=0.004)
+    deltas = [synth.LARGE_PLAIN_DELTA, synth.LARGE_PLAIN_DELTA_UNBOUNDED, (3600, 600, 3000)]
+    for opts in (dict(), dict(light_max_pairs=ALL_HEAVY), dict(labeling=ttc.LABEL_SOURCE),
+                 dict(orientation=ttc.ORIENT_DEGREE)):
+        _check(s, d, t, deltas, **opts)
+
+
+def test_many_graph_shape():
+    n, pairs, deltas, seeds = synth.many_graph_specs(count=3, n_lo=300, n_hi=3000)
+    for i in range(3):
+        s, d, t = synth.many_graph(n[i], pairs[i], seeds[i])
+        _check(s, d, t, [tuple(int(x) for x in deltas[i]), (BIG, BIG, BIG)])
+
+
+def _edges(lst):
+    e = np.asarray(lst, dtype=np.int64).reshape(-1, 3)
+    return e[:, 0].astype(np.uint32), e[:, 1].astype(np.uint32), e[:, 2].astype(np.int64)
+
+
+def test_adversarial_shapes():
+    rng = np.random.default_rng(5)
+    cases = []
+    # all-equal timestamps, delta = 0
+    s, d, t = synth.er_temporal(21, 30, 200, 10, 3.0)
+    cases.append((s, d, np.full(s.size, 7, dtype=np.int64), [(0, 0, 0), (BIG, BIG, BIG)]))
+    # one pair with many edges inside many triangles (heavy list on C or A/B)
+    hub = [(0, 1, int(x)) for x in rng.integers(0, 5000, size=3000)]
+    hub += [(int(rng.integers(0, 2)), int(2 + i % 40), int(rng.integers(0, 5000))) for i in range(800)]
+    hub += [(int(2 + i % 40), int(rng.integers(0, 2)), int(rng.integers(0, 5000))) for i in range(800)]
+    cases.append(_edges(hub) + ([(300, 200, 150), (BIG, BIG, BIG), (50, 50, 50)],))
+    # a star (no triangles) plus one triangle
+    star = [(0, i, i) for i in range(1, 200)] + [(1, 2, 500), (2, 1, 501)]
+    cases.append(_edges(star) + ([(BIG, BIG, BIG)],))
+    # K_30 with multiplicities
+    k = [(a, b, int(rng.integers(0, 100))) for a in range(30) for b in range(30) if a != b
+         for _ in range(int(rng.integers(1, 3)))]
+    cases.append(_edges(k) + ([(20, 10, 10), (BIG, BIG, BIG), (0, 0, 0)],))
+    # self-loops, duplicates, negative timestamps, isolated high ids
+    s, d, t = synth.random_tiny(77, 6, 50, 6)
+    s = np.concatenate([s, s[:10], np.array([5, 5, 1000], np.uint32)])
+    d = np.concatenate([d, d[:10], np.array([5, 5, 1001], np.uint32)])
+    t = np.concatenate([t - 3, t[:10] - 3, np.array([0, 1, 2], np.int64)])
+    cases.append((s, d, t, [(2, 1, 1), (BIG, BIG, BIG), (0, 0, 0)]))
+    # extreme timestamps
+    cases.append(_edges([(0, 1, -(1 << 60)), (2, 1, 0), (0, 2, 1 << 60), (1, 2, 5)]) +
+                 ([(1 << 61, 1 << 60, 1 << 60), ((1 << 61) - 1, 1 << 60, 1 << 60)],))
+    for s, d, t, deltas in cases:
+        for lm in (0, ALL_HEAVY, ALL_LIGHT):
+            _check(s, d, t, deltas, light_max_pairs=lm)
+
+
+def test_empty_graph():
+    e = np.zeros(0, dtype=np.uint32)
+    g = ttc.Graph(e, e, np.zeros(0, dtype=np.int64))
+    assert g.count((1, 1, 1)).sum() == 0
+    assert g.info()["tau"] == 0
+    g.free()
+    s, d, t = _edges([(3, 3, 1), (4, 4, 2)])
+    g = ttc.Graph(s, d, t)
+    assert g.count((BIG, BIG, BIG)).sum() == 0
+    assert g.info()["m_self_loops"] == 2
+    g.free()
+
+
+def test_orientation_invariance_and_degeneracy_bound():
+    nx = pytest.importorskip("networkx")
+    s, d, t = synth.large_plain(scale=0.002)
+    deltas = [synth.LARGE_PLAIN_DELTA, (BIG, BIG, BIG)]
+    want = oracle.count(s, d, t, deltas)
+    gr = nx.Graph()
+    gr.add_edges_from((a, b) for a, b in zip(s.tolist(), d.tolist()) if a != b)
+    degeneracy = max(nx.core_number(gr).values())
+    for o in range(4):
+        g = ttc.Graph(s, d, t, orientation=o, seed=3)
+        assert (g.count_batch(deltas) == want).all(), o
+        if o == ttc.ORIENT_DEGENERACY:
+            assert g.info()["kappa"] <= degeneracy
+        g.free()
+
+
+def test_graph_stats_match_oracle():
+    s, d, t = synth.large_plain(scale=0.003)
+    st = oracle.stats(s, d, t)
+    g = ttc.Graph(s, d, t)
+    info = g.info()
+    g.free()
+    for key in ("m", "m_s", "tau", "sigma_max", "work_bytes"):
+        assert info[key] == st[key], key
+    assert info["tau_light"] + info["tau_heavy"] == info["tau"]
+
+
+def test_device_input_tensors():
+    import torch
+    s, d, t = synth.tiny_plain()
+    deltas = synth.delta_sweep(8)
+    want = oracle.count(s, d, t, deltas)
+    ts = torch.from_numpy(s.astype(np.int32)).cuda()
+    td = torch.from_numpy(d.astype(np.int32)).cuda()
+    tt = torch.from_numpy(t).cuda()
+    g = ttc.Graph(ts, td, tt)
+    assert (g.count_batch(deltas) == want).all()
+    dq = torch.from_numpy(np.asarray(deltas, dtype=np.int64)).cuda()
+    out = torch.zeros((len(deltas), 8), dtype=torch.int64, device="cuda")
+    norm = np.asarray([(min(a, b + c), min(b, a), min(c, a)) for a, b, c in deltas], dtype=np.int64)
+    dq = torch.from_numpy(norm).cuda()
+    g.count_batch_async(dq.data_ptr(), len(deltas), out.data_ptr(), 0)
+    torch.cuda.synchronize()
+    g.free()
+    assert (out.cpu().numpy().astype(np.uint64) == want).all()
+
+
+def test_invalid_inputs_rejected():
+    s, d, t = _edges([(0, 1, 0), (1, 2, 1), (0, 2, 2)])
+    with pytest.raises(ttc.TTCError, match="RANGE"):
+        ttc.Graph(np.array([1 << 31, 1, 0], np.uint32), d, t)
+    with pytest.raises(ttc.TTCError, match="RANGE"):
+        ttc.Graph(s, d, np.array([0, 1, (1 << 62) + 1], np.int64))
+    g = ttc.Graph(s, d, t)
+    with pytest.raises(ttc.TTCError, match="RANGE"):
+        g.count((-1, 0, 0))
+    with pytest.raises(ttc.TTCError, match="RANGE"):
+        g.count((1 << 62, (1 << 62) + 1, 0))
+    g.free()
+
+
+def test_overflow_is_reported():
+    # one triangle with 2^22 edges on each pair, the pairs' edges in three
+    # disjoint time blocks: every unbounded triple is the same type (T3,
+    # 0->1, then 1->2, then 0->2) and there are 2^66 of them
+    k = 1 << 22
+    s = np.concatenate([np.zeros(k), np.ones(k), np.zeros(k)]).astype(np.uint32)
+    d = np.concatenate([np.ones(k), np.full(k, 2), np.full(k, 2)]).astype(np.uint32)
+    t = np.arange(3 * k, dtype=np.int64)
+    g = ttc.Graph(s, d, t)
+    with pytest.raises(ttc.TTCError, match="OVERFLOW"):
+        g.count((BIG, BIG, BIG))
+    # windows that only join the block boundaries fit easily: e1 = k-1,
+    # e2 = k, e3 = 2k is the one triple with t2 - t1 = 1 and t3 - t2 = k
+    got = g.count((k + 1, 1, k))
+    g.free()
+    assert got.tolist() == [0, 0, 1, 0, 0, 0, 0, 0]
+
+
+def test_allocation_failure_leaves_no_leak():
+    import torch
+    s, d, t = synth.tiny_plain()
+    g = ttc.Graph(s, d, t)
+    ref = g.count(synth.TINY_PLAIN_DELTA)
+    g.free()
+    torch.cuda.synchronize()
+    failures = 0
+    for n in range(1, 40):
+        ttc.debug_fail_alloc_after(n)
+        try:
+            g = ttc.Graph(s, d, t)
+        except ttc.TTCError as e:
+            assert e.status == -3
+            failures += 1
+            continue
+        finally:
+            ttc.debug_fail_alloc_after(0)
+        assert (g.count(synth.TINY_PLAIN_DELTA) == ref).all()
+        g.free()
+    assert failures >= 10
+    g = ttc.Graph(s, d, t)
+    assert (g.count(synth.TINY_PLAIN_DELTA) == ref).all()
+    g.free()

@@ -260,3 +260,11 @@ def test_stats_against_networkx():
     assert st["tau"] == sum(nx.triangles(g).values()) // 3
     assert st["m_s"] == g.number_of_edges()
     assert st["m"] == s.size
+
+
+def test_parts_partition_the_count():
+    s, d, t = synth.er_temporal(18, 60, 400, 3000, 3.0)
+    deltas = [(1500, 700, 900), (BIG, BIG, BIG)]
+    total = oracle.count(s, d, t, deltas)
+    parts = sum(oracle.count_part(s, d, t, deltas, p, 5) for p in range(5))
+    assert (parts == total).all()
