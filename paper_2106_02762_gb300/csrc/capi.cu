@@ -354,7 +354,14 @@ ttc_status ttc_count_sample(ttc_graph *g, const ttc_delta *d, uint64_t first, ui
         return TTC_ERR_INVALID;
     }
     TTC_API_BEGIN
-    fail(TTC_ERR_INTERNAL, "not built yet");
+    int64_t hq[3];
+    normalise(*d, hq);
+    std::lock_guard<std::mutex> lock(g->mu);
+    TTC_CUDA(cudaSetDevice(g->device));
+    DevBuf<int64_t> dq(3, g->stream);
+    TTC_CUDA(cudaMemcpyAsync(dq.get(), hq, 24, cudaMemcpyHostToDevice, g->stream));
+    count_sample(g, dq.get(), first, stride, cap, tri, reinterpret_cast<unsigned long long *>(out), written);
+    return TTC_OK;
     TTC_API_END
 }
 

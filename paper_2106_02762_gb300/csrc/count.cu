@@ -30,6 +30,9 @@
 //
 // Deltas arrive normalised (d12, d23 <= d13 <= d12 + d23); all counts use
 // unsigned 64-bit sums with carry detection.
+#include <cstring>
+#include <vector>
+
 #include "graph.cuh"
 
 namespace ttc {
@@ -258,14 +261,39 @@ __global__ void __launch_bounds__(LIGHT_THREADS)
         if (s_bacc[i]) atomicAdd(acc + i, s_bacc[i]);
 }
 
-// Sample mode: one thread per sampled triangle, counts written per triangle.
-__global__ void light_kernel_sample(LightArgs a, const int64_t *dq, uint64_t count) {
+// Sample mode: one thread per sampled light triangle, counts written per
+// triangle (out[8 * i] for the i-th index of idx).
+__global__ void light_kernel_sample(LightArgs a, const int64_t *dq, const uint64_t *idx, uint64_t count,
+                                    unsigned long long *out) {
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
          i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t ti = a.first + i * a.stride;
-        unsigned long long *o = a.per_tri + 8 * i;
-        const uint4 r = __ldg(a.tri + ti);
+        unsigned long long *o = out + 8 * i;
+        const uint4 r = __ldg(a.tri + idx[i]);
         light_triangle(a, r, dq, 1, [&](uint32_t, int type, uint32_t n) { o[type] += n; });
+    }
+}
+
+// Vertex triple (u, v, w) of each sampled record: A = {u, v}, B = {u, w}.
+__global__ void record_vertices_kernel(const uint4 *tri, const uint2 *pv, const uint64_t *idx, uint64_t count,
+                                       uint32_t *out) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint4 r = tri[idx[i]];
+        const uint2 a = pv[r.x], b = pv[r.y];
+        const uint32_t u = (a.x == b.x || a.x == b.y) ? a.x : a.y;
+        out[3 * i] = u;
+        out[3 * i + 1] = a.x == u ? a.y : a.x;
+        out[3 * i + 2] = b.x == u ? b.y : b.x;
+    }
+}
+
+__global__ void gather_records_kernel(const uint4 *tri, const uint64_t *idx, uint64_t count, const uint32_t *poff,
+                                      uint4 *out, uint64_t *sizes) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint4 r = tri[idx[i]];
+        out[i] = r;
+        sizes[i] = (poff[r.x + 1] - poff[r.x]) + (poff[r.y + 1] - poff[r.y]);
     }
 }
 
@@ -572,9 +600,71 @@ void count_queue(ttc_graph *g, const int64_t *dq, uint32_t k, unsigned long long
 }
 
 void count_sample(ttc_graph *g, const int64_t *dq, uint64_t first, uint64_t stride, uint64_t cap,
-                  uint32_t *, unsigned long long *out_dev, cudaStream_t s) {
-    (void)first; (void)stride; (void)cap; (void)out_dev; (void)dq; (void)g; (void)s;
-    fail(TTC_ERR_INTERNAL, "count_sample: not built yet");
+                  uint32_t *tri_vtx_host, unsigned long long *out_host, uint64_t *written) {
+    cudaStream_t s = g->stream;
+    const uint64_t tau = g->st.tau, nl = g->st.tau_light;
+    std::vector<uint64_t> li, hi_, all;
+    for (uint64_t i = 0, ti = first; i < cap && ti < tau; i++, ti += stride) {
+        all.push_back(ti);
+        (ti < nl ? li : hi_).push_back(ti);
+    }
+    *written = all.size();
+    if (all.empty()) return;
+    const uint64_t n = all.size(), nlc = li.size(), nhc = hi_.size();
+    DevBuf<uint64_t> d_all(n, s), d_idx(n, s);
+    DevBuf<uint32_t> d_vtx(3 * n, s);
+    DevBuf<unsigned long long> d_out(8 * n, s);
+    TTC_CUDA(cudaMemcpyAsync(d_all.get(), all.data(), n * 8, cudaMemcpyHostToDevice, s));
+    TTC_CUDA(cudaMemsetAsync(d_out.get(), 0, 8 * n * 8, s));
+    record_vertices_kernel<<<ceil_div(n, 256), 256, 0, s>>>(g->tri.get(), g->pair_vtx.get(), d_all.get(), n,
+                                                            d_vtx.get());
+    TTC_LAUNCH_CHECK();
+    // light samples first, then heavy ones, in d_idx / d_out order
+    std::vector<uint64_t> order(li);
+    order.insert(order.end(), hi_.begin(), hi_.end());
+    TTC_CUDA(cudaMemcpyAsync(d_idx.get(), order.data(), n * 8, cudaMemcpyHostToDevice, s));
+    if (nlc) {
+        light_kernel_sample<<<ceil_div(nlc, 128), 128, 0, s>>>(light_args(g), dq, d_idx.get(), nlc, d_out.get());
+        TTC_LAUNCH_CHECK();
+    }
+    if (nhc) {
+        DevBuf<uint4> sub(nhc, s);
+        DevBuf<uint64_t> sizes(nhc, s), eoff(nhc + 1, s);
+        gather_records_kernel<<<ceil_div(nhc, 256), 256, 0, s>>>(g->tri.get(), d_idx.get() + nlc, nhc,
+                                                                 g->poff.get(), sub.get(), sizes.get());
+        TTC_LAUNCH_CHECK();
+        exclusive_scan_u64(sizes.get(), eoff.get(), nhc, s);
+        uint64_t total = 0;
+        TTC_CUDA(cudaMemcpyAsync(&total, eoff.get() + nhc, 8, cudaMemcpyDeviceToHost, s));
+        TTC_CUDA(cudaStreamSynchronize(s));
+        HeavyArgs ha{};
+        ha.k = KeyCtx{g->key.get(), g->fwd.get(), g->shift, g->span};
+        ha.poff = g->poff.get();
+        ha.tri = sub.get();
+        ha.eoff = eoff.get();
+        ha.nh = nhc;
+        ha.total = total;
+        const size_t bytes = ((size_t)total + 4 * nhc) * 8 * (g->heavy_wide ? 8 : 4);
+        DevBuf<uint8_t> pre(bytes, s);
+        ha.pre = pre.get();
+        ha.per_tri = d_out.get() + 8 * nlc;
+        const bool saved = g->profiling;
+        g->profiling = false;
+        if (g->heavy_wide) run_heavy<unsigned long long>(g, ha, dq, nullptr, s);
+        else run_heavy<uint32_t>(g, ha, dq, nullptr, s);
+        g->profiling = saved;
+    }
+    std::vector<unsigned long long> h(8 * n);
+    std::vector<uint32_t> hv(3 * n);
+    TTC_CUDA(cudaMemcpyAsync(h.data(), d_out.get(), 8 * n * 8, cudaMemcpyDeviceToHost, s));
+    TTC_CUDA(cudaMemcpyAsync(hv.data(), d_vtx.get(), 3 * n * 4, cudaMemcpyDeviceToHost, s));
+    TTC_CUDA(cudaStreamSynchronize(s));
+    // back to sample order
+    for (uint64_t i = 0, a = 0, b = 0; i < n; i++) {
+        const uint64_t slot = all[i] < nl ? a++ : nlc + b++;
+        memcpy(out_host + 8 * i, &h[8 * slot], 64);
+    }
+    memcpy(tri_vtx_host, hv.data(), 3 * n * 4);
 }
 
 }  // namespace ttc

@@ -83,8 +83,9 @@ void prof_end(ttc_graph *g, cudaStream_t s);
 void count_queue(ttc_graph *g, const int64_t *dq, uint32_t k, unsigned long long *acc, cudaStream_t s);
 
 // count.cu: per-triangle counts of a strided sample of the triangle list.
+// (host outputs; the sampled triangles run through the same light/heavy code)
 void count_sample(ttc_graph *g, const int64_t *dq, uint64_t first, uint64_t stride, uint64_t cap,
-                  uint32_t *tri_vtx_dev, unsigned long long *out_dev, cudaStream_t s);
+                  uint32_t *tri_vtx_host, unsigned long long *out_host, uint64_t *written);
 
 // count.cu: many graphs in one persistent launch.
 struct MultiGraphDesc;

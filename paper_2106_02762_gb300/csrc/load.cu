@@ -100,7 +100,8 @@ __global__ void group_start_kernel(const uint8_t *head, const uint32_t *gid, siz
 __global__ void group_rank_max_kernel(const uint32_t *gid, const uint32_t *gstart, size_t m,
                                       unsigned int *max_rank) {
     unsigned int mx = 0;
-    GRID_STRIDE(i, m) mx = max(mx, (uint32_t)i - gstart[gid[i]]);
+    // gid is the exclusive scan of head flags, so element i's group is gid[i + 1] - 1
+    GRID_STRIDE(i, m) mx = max(mx, (uint32_t)i - gstart[gid[i + 1] - 1]);
     for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if ((threadIdx.x & 31) == 0 && mx) atomicMax(max_rank, mx);
 }
@@ -112,7 +113,7 @@ __global__ void pack_kernel(const uint64_t *tkey, const uint32_t *eidx, const ui
     GRID_STRIDE(i, m) {
         const uint32_t e = eidx[i];
         const uint32_t a = src[e], b = dst[e];
-        const uint64_t rank = (uint32_t)i - gstart[gid[i]];
+        const uint64_t rank = (uint32_t)i - gstart[gid[i + 1] - 1];
         const uint64_t dir = a > b;  // 1: from the larger id to the smaller
         key[i] = (tkey[i] << shift) | (rank << 1) | dir;
         const uint64_t lo = min(a, b), hi = max(a, b);
