@@ -165,6 +165,28 @@ ttc_status ttc_count_multi(ttc_graph *const *g, const ttc_delta *d, uint32_t G, 
 ttc_status ttc_count_sample(ttc_graph *g, const ttc_delta *d, uint64_t first, uint64_t stride,
                             uint64_t cap, uint32_t *tri, uint64_t *out, uint64_t *written);
 
+/* No-allocation variant of ttc_count (the paper has no counterpart; this is
+ * an interface convenience).  For callers that cannot allocate device memory
+ * when they count: inside a CUDA stream capture, beside a framework allocator
+ * that owns the device's memory, or in latency-critical loops.  It runs the
+ * same kernels as ttc_count, but its device scratch (the counts, the delta
+ * and the prefix-sum arrays of the heavy bin) is one static __device__ array
+ * of TTC_NOALLOC_SCRATCH_BYTES that every device holds from library load to
+ * process exit; it calls no cudaMalloc, cudaFree or other allocator.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - A graph whose heavy-bin prefix arrays need more than the array holds
+ *     (TTC_NOALLOC_SCRATCH_BYTES - 512 bytes) is rejected with TTC_ERR_RANGE;
+ *     use ttc_count for it.
+ *   - Every call shares the one array and keeps the previous call's contents;
+ *     each call zeroes the counts it needs.  Calls are serialised by a lock and
+ *     return only when their kernels are done; work that overlapped a call on
+ *     the GPU while using the same array would race.
+ * d and out are host pointers; stream is a cudaStream_t (NULL = the graph's
+ * stream). */
+#define TTC_NOALLOC_SCRATCH_BYTES (64u << 20)
+ttc_status ttc_count_noalloc(ttc_graph *g, const ttc_delta *d, uint64_t out[TTC_NUM_TYPES], void *stream);
+
 /* ----------------------------------------------------------------- serve */
 
 typedef struct {

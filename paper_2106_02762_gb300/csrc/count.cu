@@ -599,6 +599,37 @@ void count_queue(ttc_graph *g, const int64_t *dq, uint32_t k, unsigned long long
     }
 }
 
+size_t heavy_scratch_bytes(const ttc_graph *g) {
+    const size_t entries = (size_t)g->heavy_elems + 4 * (size_t)g->st.tau_heavy;
+    return g->st.tau_heavy ? entries * 8 * (g->heavy_wide ? 8 : 4) : 0;
+}
+
+void count_one_into(ttc_graph *g, const int64_t *dq, unsigned long long *acc, void *scratch, cudaStream_t s) {
+    if (!g->st.tau) return;
+    const LightArgs la = light_args(g);
+    if (la.ntri) {
+        const uint64_t want = (la.ntri + LIGHT_THREADS - 1) / LIGHT_THREADS;
+        const uint64_t cap = (uint64_t)sm_count() * 8;
+        light_kernel_single<<<(unsigned)(want < cap ? want : cap), LIGHT_THREADS, 0, s>>>(la, dq, acc);
+        TTC_LAUNCH_CHECK();
+    }
+    if (g->st.tau_heavy) {
+        HeavyArgs ha{};
+        ha.k = KeyCtx{g->key.get(), g->fwd.get(), g->shift, g->span};
+        ha.poff = g->poff.get();
+        ha.tri = g->tri.get() + g->st.tau_light;
+        ha.eoff = g->heavy_eoff.get();
+        ha.nh = g->st.tau_heavy;
+        ha.total = g->heavy_elems;
+        ha.pre = scratch;
+        const bool saved = g->profiling;
+        g->profiling = false;
+        if (g->heavy_wide) run_heavy<unsigned long long>(g, ha, dq, acc, s);
+        else run_heavy<uint32_t>(g, ha, dq, acc, s);
+        g->profiling = saved;
+    }
+}
+
 void count_sample(ttc_graph *g, const int64_t *dq, uint64_t first, uint64_t stride, uint64_t cap,
                   uint32_t *tri_vtx_host, unsigned long long *out_host, uint64_t *written) {
     cudaStream_t s = g->stream;

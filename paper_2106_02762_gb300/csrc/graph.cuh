@@ -82,6 +82,13 @@ void prof_end(ttc_graph *g, cudaStream_t s);
 // trailing overflow flag), which the caller zeroes.
 void count_queue(ttc_graph *g, const int64_t *dq, uint32_t k, unsigned long long *acc, cudaStream_t s);
 
+// count.cu: the same kernels as count_queue for one normalised query, but
+// with every device buffer supplied by the caller: acc (9 u64, zeroed by the
+// caller) and the heavy-path prefix scratch of heavy_scratch_bytes(g) bytes.
+// Allocates nothing.
+size_t heavy_scratch_bytes(const ttc_graph *g);
+void count_one_into(ttc_graph *g, const int64_t *dq, unsigned long long *acc, void *scratch, cudaStream_t s);
+
 // count.cu: per-triangle counts of a strided sample of the triangle list.
 // (host outputs; the sampled triangles run through the same light/heavy code)
 void count_sample(ttc_graph *g, const int64_t *dq, uint64_t first, uint64_t stride, uint64_t cap,

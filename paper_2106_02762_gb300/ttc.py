@@ -30,7 +30,7 @@ EXPORTS = ["ttc_load", "ttc_load_ex", "ttc_free", "ttc_graph_info", "ttc_count",
            "ttc_count_batch_async", "ttc_count_multi", "ttc_count_sample", "ttc_server_create",
            "ttc_server_destroy", "ttc_serve_load", "ttc_serve_submit", "ttc_serve_poll", "ttc_serve_drain",
            "ttc_server_info", "ttc_last_error", "ttc_version", "ttc_debug_fail_alloc_after",
-           "ttc_debug_launch_count", "ttc_set_profiling", "ttc_profile_read"]
+           "ttc_debug_launch_count", "ttc_set_profiling", "ttc_profile_read", "ttc_count_noalloc"]
 
 
 class TTCError(RuntimeError):
@@ -104,6 +104,7 @@ def lib():
             "ttc_debug_launch_count": ([], u64),
             "ttc_set_profiling": ([p, ctypes.c_int], ctypes.c_int),
             "ttc_profile_read": ([p, p, u32], u32),
+            "ttc_count_noalloc": ([p, p, p, p], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
