@@ -196,80 +196,108 @@ __device__ __forceinline__ void light_pair(const KeyCtx &k, const List &C, const
     }
 }
 
-// Direct Lemma 1 over A x B for one triangle and the queries [q0, q0 + nq).
-template <typename Acc>
-__device__ __forceinline__ void light_triangle(const LightArgs &a, const uint4 r, const int64_t *dq, uint32_t nq,
-                                               Acc &&acc) {
+// ---------------------------------------------------------------------------
+// Warp-cooperative light kernel.  Each warp takes 32 consecutive triangle
+// records, flattens their A x B pairs (fewer than light_max_pairs each) into
+// one index space and gives every lane one pair per step, so lanes stay busy
+// whatever the per-triangle list sizes.  Per pair: the two keys, their
+// positions in C, and the three cases of light_pair.
+constexpr int LIGHT_WARPS = LIGHT_THREADS / 32;
+
+struct WarpTris {
+    uint32_t excl[LIGHT_WARPS][33];  // exclusive prefix of pair counts
+    uint4 lst[LIGHT_WARPS][32];      // A.b, B.b, C.b, C.n
+    uint32_t bn[LIGHT_WARPS][32];    // B.n
+    uint32_t fl[LIGHT_WARPS][32];    // flip flags
+};
+
+// MODE 0: one query, per-thread accumulators.  MODE 1: nq queries, block
+// accumulators.  MODE 2: one query, per-triangle output for the sampled
+// triangles idx[0 .. ntri) (acc is then [ntri][8]).
+template <int MODE>
+__global__ void __launch_bounds__(LIGHT_THREADS)
+    light_kernel_warp(LightArgs a, const int64_t *dq, uint32_t nq, unsigned long long *acc, const uint64_t *idx) {
+    __shared__ WarpTris wt;
+    __shared__ unsigned long long s_acc[MODE == 0 ? 8 : 1][MODE == 0 ? 256 : 1];
+    extern __shared__ unsigned long long s_bacc[];  // MODE 1: [nq * 8]
+    const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if constexpr (MODE == 0) {
+#pragma unroll
+        for (int j = 0; j < 8; j++) s_acc[j][threadIdx.x] = 0;
+    }
+    if (MODE == 1) {
+        for (uint32_t i = threadIdx.x; i < nq * 8; i += blockDim.x) s_bacc[i] = 0;
+        __syncthreads();
+    }
+    unsigned ovf = 0;
     const KeyCtx &k = a.k;
-    const List A = make_list(a.poff, r.x, r.w & TriRec::FLIP_A);
-    const List B = make_list(a.poff, r.y, (r.w & TriRec::FLIP_B) ? 1u : 0u);
-    const List C = make_list(a.poff, r.z, (r.w & TriRec::FLIP_C) ? 1u : 0u);
-    for (uint32_t i = 0; i < A.n; i++) {
-        const int64_t ka = __ldg(k.key + A.b + i);
-        const int64_t ra = ka >> k.shift;
-        const uint32_t dA = (uint32_t)(ka & 1) ^ A.flip;
-        const uint32_t pa = cnt_key(k, C, ka);
-        for (uint32_t j = 0; j < B.n; j++) {
-            const int64_t kb = __ldg(k.key + B.b + j);
-            const int64_t rb = kb >> k.shift;
-            const uint32_t dB = (uint32_t)(kb & 1) ^ B.flip;
-            const uint32_t pb = cnt_key(k, C, kb);
+    const uint64_t nchunks = (a.ntri + 31) / 32;
+    const uint64_t gw = (uint64_t)blockIdx.x * LIGHT_WARPS + w, nw = (uint64_t)gridDim.x * LIGHT_WARPS;
+    const Query Q0 = load_query(dq, 0);
+    int64_t gmax = Q0.d13;  // every case needs t_y - t_x <= d13 (normalised)
+    if (MODE == 1)
+        for (uint32_t q = 1; q < nq; q++) gmax = max(gmax, dq[3 * q]);
+    for (uint64_t c = gw; c < nchunks; c += nw) {
+        const uint64_t ti = c * 32 + lane;
+        uint32_t npairs = 0;
+        if (ti < a.ntri) {
+            const uint4 r = __ldg(a.tri + (MODE == 2 ? idx[ti] : ti));
+            const uint32_t ab = __ldg(a.poff + r.x), an = __ldg(a.poff + r.x + 1) - ab;
+            const uint32_t bb = __ldg(a.poff + r.y), bn = __ldg(a.poff + r.y + 1) - bb;
+            const uint32_t cb = __ldg(a.poff + r.z), cn = __ldg(a.poff + r.z + 1) - cb;
+            npairs = an * bn;
+            wt.lst[w][lane] = make_uint4(ab, bb, cb, cn);
+            wt.bn[w][lane] = bn;
+            wt.fl[w][lane] = r.w;
+        }
+        uint32_t x = npairs;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= (uint32_t)o) x += y;
+        }
+        wt.excl[w][lane] = x - npairs;
+        const uint32_t total = __shfl_sync(0xffffffffu, x, 31);
+        if (lane == 0) wt.excl[w][32] = total;
+        __syncwarp();
+        for (uint32_t base = 0; base < total; base += 32) {
+            const uint32_t j = base + lane;
+            if (j >= total) continue;
+            uint32_t o = 0;  // last slot with excl <= j (skips empty slots before it)
+#pragma unroll
+            for (uint32_t step = 16; step; step >>= 1)
+                if (wt.excl[w][o + step] <= j) o += step;
+            const uint4 L = wt.lst[w][o];
+            const uint32_t bn = wt.bn[w][o], fl = wt.fl[w][o];
+            const uint32_t loc = j - wt.excl[w][o];
+            const uint32_t ai = loc / bn, bi = loc - ai * bn;
+            const int64_t ka = __ldg(k.key + L.x + ai), kb = __ldg(k.key + L.y + bi);
+            const int64_t ra = ka >> k.shift, rb = kb >> k.shift;
             const bool a_first = ka < kb;
-            for (uint32_t q = 0; q < nq; q++) {
-                const Query Q = load_query(dq, q);
-                auto acc_q = [&](int type, uint32_t n) { acc(q, type, n); };
-                if (a_first) light_pair(k, C, Q, true, ra, rb, pa, pb, dA, dB, acc_q);
-                else light_pair(k, C, Q, false, rb, ra, pb, pa, dA, dB, acc_q);
+            const int64_t gap = a_first ? rb - ra : ra - rb;
+            if (gap > gmax) continue;
+            const List C{L.z, L.w, (fl & TriRec::FLIP_C) ? 1u : 0u};
+            const uint32_t dA = (uint32_t)(ka & 1) ^ (fl & TriRec::FLIP_A);
+            const uint32_t dB = (uint32_t)(kb & 1) ^ ((fl & TriRec::FLIP_B) ? 1u : 0u);
+            const uint32_t pa = cnt_key(k, C, ka), pb = cnt_key(k, C, kb);
+            for (uint32_t q = 0; q < (MODE == 1 ? nq : 1u); q++) {
+                const Query Q = MODE == 1 ? load_query(dq, q) : Q0;
+                auto accq = [&](int type, uint32_t n) {
+                    if constexpr (MODE == 0) add_checked(s_acc[type][threadIdx.x], n, ovf);
+                    else if constexpr (MODE == 1) atomicAdd(&s_bacc[q * 8 + type], (unsigned long long)n);
+                    else atomicAdd(acc + 8 * (c * 32 + o) + type, (unsigned long long)n);
+                };
+                if (a_first) light_pair(k, C, Q, true, ra, rb, pa, pb, dA, dB, accq);
+                else light_pair(k, C, Q, false, rb, ra, pb, pa, dA, dB, accq);
             }
         }
+        __syncwarp();
     }
-}
-
-// One query: per-thread accumulators in shared memory.
-__global__ void __launch_bounds__(LIGHT_THREADS)
-    light_kernel_single(LightArgs a, const int64_t *dq, unsigned long long *acc) {
-    __shared__ unsigned long long s_acc[8][256];
-#pragma unroll
-    for (int j = 0; j < 8; j++) s_acc[j][threadIdx.x] = 0;
-    unsigned ovf = 0;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.ntri;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint4 r = __ldg(a.tri + i);
-        light_triangle(a, r, dq, 1, [&](uint32_t, int type, uint32_t n) {
-            add_checked(s_acc[type][threadIdx.x], n, ovf);
-        });
-    }
-    flush_block(s_acc, LIGHT_THREADS, acc, ovf);
-}
-
-// Several queries: block accumulators [nq][8] in shared memory.
-constexpr int MAX_BATCH_SMEM_Q = 256;
-__global__ void __launch_bounds__(LIGHT_THREADS)
-    light_kernel_batch(LightArgs a, const int64_t *dq, uint32_t nq, unsigned long long *acc) {
-    extern __shared__ unsigned long long s_bacc[];  // [nq * 8]
-    for (uint32_t i = threadIdx.x; i < nq * 8; i += blockDim.x) s_bacc[i] = 0;
-    __syncthreads();
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.ntri;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint4 r = __ldg(a.tri + i);
-        light_triangle(a, r, dq, nq, [&](uint32_t q, int type, uint32_t n) {
-            atomicAdd(&s_bacc[q * 8 + type], (unsigned long long)n);
-        });
-    }
-    __syncthreads();
-    for (uint32_t i = threadIdx.x; i < nq * 8; i += blockDim.x)
-        if (s_bacc[i]) atomicAdd(acc + i, s_bacc[i]);
-}
-
-// Sample mode: one thread per sampled light triangle, counts written per
-// triangle (out[8 * i] for the i-th index of idx).
-__global__ void light_kernel_sample(LightArgs a, const int64_t *dq, const uint64_t *idx, uint64_t count,
-                                    unsigned long long *out) {
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-        unsigned long long *o = out + 8 * i;
-        const uint4 r = __ldg(a.tri + idx[i]);
-        light_triangle(a, r, dq, 1, [&](uint32_t, int type, uint32_t n) { o[type] += n; });
+    if constexpr (MODE == 0) flush_block(s_acc, LIGHT_THREADS, acc, ovf);
+    if constexpr (MODE == 1) {
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < nq * 8; i += blockDim.x)
+            if (s_bacc[i]) atomicAdd(acc + i, s_bacc[i]);
     }
 }
 
@@ -556,6 +584,14 @@ HeavyArgs heavy_args(ttc_graph *g, cudaStream_t s) {
     return ha;
 }
 
+constexpr int MAX_BATCH_SMEM_Q = 256;
+
+unsigned light_grid(uint64_t ntri) {
+    const uint64_t want = (ntri + LIGHT_THREADS - 1) / LIGHT_THREADS;
+    const uint64_t cap = (uint64_t)sm_count() * 8;
+    return (unsigned)(want < 1 ? 1 : want < cap ? want : cap);
+}
+
 LightArgs light_args(ttc_graph *g) {
     LightArgs la{};
     la.k = KeyCtx{g->key.get(), g->fwd.get(), g->shift, g->span};
@@ -571,20 +607,18 @@ void count_queue(ttc_graph *g, const int64_t *dq, uint32_t k, unsigned long long
     if (!g->st.tau || !k) return;
     const LightArgs la = light_args(g);
     if (la.ntri) {
-        const uint64_t want = (la.ntri + LIGHT_THREADS - 1) / LIGHT_THREADS;
-        const uint64_t cap = (uint64_t)sm_count() * 8;
-        const unsigned grid = (unsigned)(want < cap ? want : cap);
+        const unsigned grid = light_grid(la.ntri);
         if (k == 1) {
             prof_begin(g, s, "light");
-            light_kernel_single<<<grid, LIGHT_THREADS, 0, s>>>(la, dq, acc);
+            light_kernel_warp<0><<<grid, LIGHT_THREADS, 0, s>>>(la, dq, 1, acc, nullptr);
             TTC_LAUNCH_CHECK();
             prof_end(g, s);
         } else {
             for (uint32_t q0 = 0; q0 < k; q0 += MAX_BATCH_SMEM_Q) {
                 const uint32_t nq = k - q0 < (uint32_t)MAX_BATCH_SMEM_Q ? k - q0 : (uint32_t)MAX_BATCH_SMEM_Q;
                 prof_begin(g, s, "light_batch");
-                light_kernel_batch<<<grid, LIGHT_THREADS, nq * 8 * sizeof(unsigned long long), s>>>(
-                    la, dq + 3 * (size_t)q0, nq, acc + 8 * (size_t)q0);
+                light_kernel_warp<1><<<grid, LIGHT_THREADS, nq * 8 * sizeof(unsigned long long), s>>>(
+                    la, dq + 3 * (size_t)q0, nq, acc + 8 * (size_t)q0, nullptr);
                 TTC_LAUNCH_CHECK();
                 prof_end(g, s);
             }
@@ -608,9 +642,7 @@ void count_one_into(ttc_graph *g, const int64_t *dq, unsigned long long *acc, vo
     if (!g->st.tau) return;
     const LightArgs la = light_args(g);
     if (la.ntri) {
-        const uint64_t want = (la.ntri + LIGHT_THREADS - 1) / LIGHT_THREADS;
-        const uint64_t cap = (uint64_t)sm_count() * 8;
-        light_kernel_single<<<(unsigned)(want < cap ? want : cap), LIGHT_THREADS, 0, s>>>(la, dq, acc);
+        light_kernel_warp<0><<<light_grid(la.ntri), LIGHT_THREADS, 0, s>>>(la, dq, 1, acc, nullptr);
         TTC_LAUNCH_CHECK();
     }
     if (g->st.tau_heavy) {
@@ -655,7 +687,9 @@ void count_sample(ttc_graph *g, const int64_t *dq, uint64_t first, uint64_t stri
     order.insert(order.end(), hi_.begin(), hi_.end());
     TTC_CUDA(cudaMemcpyAsync(d_idx.get(), order.data(), n * 8, cudaMemcpyHostToDevice, s));
     if (nlc) {
-        light_kernel_sample<<<ceil_div(nlc, 128), 128, 0, s>>>(light_args(g), dq, d_idx.get(), nlc, d_out.get());
+        LightArgs la = light_args(g);
+        la.ntri = nlc;
+        light_kernel_warp<2><<<light_grid(nlc), LIGHT_THREADS, 0, s>>>(la, dq, 1, d_out.get(), d_idx.get());
         TTC_LAUNCH_CHECK();
     }
     if (nhc) {

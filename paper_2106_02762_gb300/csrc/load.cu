@@ -14,6 +14,8 @@
 //                  and heavy (prefix-sum) bins
 #include <cooperative_groups.h>
 
+#include <algorithm>
+
 #include "graph.cuh"
 
 namespace cg = cooperative_groups;
@@ -156,10 +158,17 @@ __global__ void adj_fill_kernel(const uint2 *pv, size_t ms, uint32_t *cursor, ui
 }
 
 // ---------------------------------------------------------------- k-core peel
+// Counters of one phase of the peel.  Phases rotate through three slots: the
+// slot of phase p is read by every thread after the barrier that ends p and
+// is zeroed again after the barrier that ends p + 1, two barriers before it
+// is written again.
+struct PeelSlot {
+    unsigned long long front;  // (vertices << 40) | their adjacency total
+    unsigned int rem_n;
+    int min_deg;
+};
 struct PeelCtl {
-    unsigned long long front[2];  // per iteration parity: (count << 40) | edge total
-    unsigned int next_n[2];
-    int min_deg[2];
+    PeelSlot slot[3];
     unsigned int kappa;
     unsigned int rounds;
     unsigned int error;
@@ -170,124 +179,176 @@ constexpr uint64_t MASK40 = (uint64_t(1) << 40) - 1;
 constexpr int PEEL_THREADS = 1024;
 constexpr int PEEL_RUN = 16;  // relaxed edges per thread per step
 
-// Level-synchronous peel: at level k every remaining vertex of degree <= k
-// is removed in the current round (all at once), and its remaining
-// neighbours lose one degree each; when no vertex qualifies, k rises to the
-// smallest remaining degree.  level[v] = round in which v was removed.  The
-// orientation "lower (round, id) -> higher" gives every vertex at most k
-// out-neighbours, k <= kappa.
+// Appends v (with its adjacency length) to a frontier list; warp-aggregated.
+// Every lane of the warp must call it (pred selects the appending lanes).
+__device__ __forceinline__ void push_frontier(bool pred, uint32_t v, uint32_t nadj, PeelSlot *sl, uint32_t *front,
+                                              uint32_t *foff, uint32_t lane) {
+    const uint64_t pk = pred ? ((uint64_t(1) << 40) | nadj) : 0;
+    uint64_t x = pk;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= (uint32_t)o) x += y;
+    }
+    const uint64_t tot = __shfl_sync(0xffffffffu, x, 31);
+    uint64_t base = 0;
+    if (lane == 31 && tot) base = atomicAdd(&sl->front, (unsigned long long)tot);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    if (pred) {
+        const uint64_t mine = base + x - pk;
+        const uint32_t fi = (uint32_t)(mine >> 40);
+        front[fi] = v;
+        foff[fi] = (uint32_t)(mine & MASK40);
+    }
+}
+
+// Level-synchronous bucketed peel (Sec. 3, degeneracy ordering).  At level k
+// the frontier is every remaining vertex of degree <= k; removing it lowers
+// its remaining neighbours' degrees, and a neighbour whose degree falls to k
+// (the decrement that returns k + 1) joins the next round's frontier.  When a
+// round empties the frontier, the remaining set is compacted and k rises to
+// its smallest degree.  level[v] = round of removal; orienting every pair
+// from the lower (round, id) to the higher gives each vertex at most k <=
+// kappa out-neighbours.  All rounds run in one thread-block cluster,
+// separated by cluster barriers; every control decision is uniform.
 __global__ void __launch_bounds__(PEEL_THREADS)
     peel_kernel(const uint32_t *__restrict__ adj_off, const uint32_t *__restrict__ adj, int *deg,
-                uint32_t *level, uint32_t *remA, uint32_t *remB, uint32_t *front, uint32_t *foff, uint32_t n,
-                PeelCtl *ctl) {
+                uint32_t *level, uint32_t *remA, uint32_t *remB, uint32_t *frontA, uint32_t *frontB,
+                uint32_t *foffA, uint32_t *foffB, uint32_t n, PeelCtl *ctl) {
     cg::cluster_group cluster = cg::this_cluster();
     const uint32_t nthr = cluster.num_blocks() * blockDim.x;
     const uint32_t tid = cluster.block_rank() * blockDim.x + threadIdx.x;
     const uint32_t lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
-    uint32_t *rem = remA, *nxt = remB;
-    uint32_t rem_n = n;
-    bool identity = true;  // first pass: the remaining set is 0..n-1
+    uint32_t *rem = remA, *rem_next = remB;
+    uint32_t *front = frontA, *front_next = frontB, *foff = foffA, *foff_next = foffB;
+    uint32_t rem_n = n, fn = 0, fe = 0;
+    bool identity = true;  // the remaining set is 0..n-1 until the first compaction
     int k = 0;
-    uint32_t round = 0, kappa = 0;
-    const uint64_t it_cap = 2ull * n + 4;
-    for (uint64_t it = 0;; it++) {
-        const int par = (int)(it & 1);
-        if (it > it_cap) {
-            if (tid == 0) ctl->error = 1;
-            break;
-        }
-        int my_min = INT_MAX;
-        for (uint32_t base = 0; base < rem_n; base += nthr) {
-            const uint32_t i = base + tid;
-            const bool ok = i < rem_n;
-            uint32_t v = 0;
-            int d = 0;
-            if (ok) {
-                v = identity ? i : __ldcg(rem + i);
-                d = __ldcg(deg + v);
-            }
-            const bool to_front = ok && d <= k;
-            const bool to_next = ok && !to_front;
-            if (to_next) my_min = min(my_min, d);
-            const uint64_t pk = to_front ? ((uint64_t(1) << 40) | (uint64_t)(adj_off[v + 1] - adj_off[v])) : 0;
-            uint64_t x = pk;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
-                if (lane >= (uint32_t)o) x += y;
-            }
-            const uint64_t tot = __shfl_sync(0xffffffffu, x, 31);
-            uint64_t fb = 0;
-            if (lane == 31 && tot) fb = atomicAdd(&ctl->front[par], (unsigned long long)tot);
-            fb = __shfl_sync(0xffffffffu, fb, 31);
-            if (to_front) {
-                const uint64_t mine = fb + x - pk;
-                const uint32_t fi = (uint32_t)(mine >> 40);
-                front[fi] = v;
-                foff[fi] = (uint32_t)(mine & MASK40);
-                level[v] = round;
-            }
-            const unsigned bal = __ballot_sync(0xffffffffu, to_next);
-            uint32_t nb = 0;
-            if (lane == 0 && bal) nb = atomicAdd(&ctl->next_n[par], (unsigned)__popc(bal));
-            nb = __shfl_sync(0xffffffffu, nb, 0);
-            if (to_next) nxt[nb + __popc(bal & lt_mask)] = v;
-        }
-#pragma unroll
-        for (int o = 16; o; o >>= 1) my_min = min(my_min, __shfl_xor_sync(0xffffffffu, my_min, o));
-        if (lane == 0 && my_min != INT_MAX) atomicMin(&ctl->min_deg[par], my_min);
+    uint32_t round = 0, kappa = 0, ph = 0;
+    const uint64_t ph_cap = 3ull * n + 8;
+    bool ok = true;
+    // ends phase ph: barrier, then zero the slot of phase ph + 2
+    auto end_phase = [&]() -> PeelSlot * {
         cluster.sync();
-        const uint64_t fr = __ldcg(&ctl->front[par]);
-        const uint32_t fn = (uint32_t)(fr >> 40), fe = (uint32_t)(fr & MASK40);
-        const uint32_t nn = __ldcg(&ctl->next_n[par]);
-        const int md = __ldcg(&ctl->min_deg[par]);
+        PeelSlot *cur = &ctl->slot[ph % 3];
         if (tid == 0) {
-            ctl->front[par ^ 1] = 0;
-            ctl->next_n[par ^ 1] = 0;
-            ctl->min_deg[par ^ 1] = INT_MAX;
+            PeelSlot *z = &ctl->slot[(ph + 2) % 3];
+            z->front = 0;
+            z->rem_n = 0;
+            z->min_deg = INT_MAX;
         }
-        if (fn == 0 && nn == 0) break;
-        uint32_t *tmp = rem;
-        rem = nxt;
-        nxt = tmp;
-        rem_n = nn;
-        identity = false;
+        ph++;
+        if (ph > ph_cap) ok = false;
+        return cur;
+    };
+    while (ok) {
         if (fn == 0) {
-            k = md;
-            cluster.sync();
-            continue;
-        }
-        kappa = max(kappa, (uint32_t)k);
-        // relax the frontier's edges: thread runs of PEEL_RUN consecutive edges
-        for (uint32_t e0 = tid * PEEL_RUN; e0 < fe; e0 += nthr * PEEL_RUN) {
-            uint32_t lo = 0, hi = fn;  // last fi with foff[fi] <= e0
-            while (hi - lo > 1) {
-                const uint32_t mid = (lo + hi) >> 1;
-                if (__ldcg(foff + mid) <= e0) lo = mid; else hi = mid;
-            }
-            uint32_t fi = lo;
-            uint32_t fbeg = __ldcg(foff + fi);
-            uint32_t fend = fi + 1 < fn ? __ldcg(foff + fi + 1) : fe;
-            uint32_t v = __ldcg(front + fi);
-            const uint32_t e1 = min(fe, e0 + PEEL_RUN);
-            for (uint32_t e = e0; e < e1; e++) {
-                while (e >= fend) {
-                    fi++;
-                    fbeg = fend;
-                    fend = fi + 1 < fn ? __ldcg(foff + fi + 1) : fe;
-                    v = __ldcg(front + fi);
+            // compaction: keep the unremoved vertices, find their smallest degree
+            PeelSlot *sl = &ctl->slot[ph % 3];
+            int my_min = INT_MAX;
+            for (uint32_t base = 0; base < rem_n; base += nthr) {
+                const uint32_t i = base + tid;
+                uint32_t v = 0;
+                bool keep = false;
+                if (i < rem_n) {
+                    v = identity ? i : __ldcg(rem + i);
+                    keep = __ldcg(level + v) == UNSET;
+                    if (keep) my_min = min(my_min, __ldcg(deg + v));
                 }
-                const uint32_t w = adj[adj_off[v] + (e - fbeg)];
-                if (__ldcg(level + w) == UNSET) atomicSub(deg + w, 1);
+                const unsigned bal = __ballot_sync(0xffffffffu, keep);
+                uint32_t b = 0;
+                if (lane == 0 && bal) b = atomicAdd(&sl->rem_n, (unsigned)__popc(bal));
+                b = __shfl_sync(0xffffffffu, b, 0);
+                if (keep) rem_next[b + __popc(bal & lt_mask)] = v;
+            }
+#pragma unroll
+            for (int o = 16; o; o >>= 1) my_min = min(my_min, __shfl_xor_sync(0xffffffffu, my_min, o));
+            if (lane == 0 && my_min != INT_MAX) atomicMin(&sl->min_deg, my_min);
+            const PeelSlot *r = end_phase();
+            rem_n = __ldcg(&r->rem_n);
+            const int md = __ldcg(&r->min_deg);
+            identity = false;
+            uint32_t *t = rem; rem = rem_next; rem_next = t;
+            if (rem_n == 0) break;
+            k = max(k, md);
+            kappa = max(kappa, (uint32_t)k);
+            // collection: the new level's frontier
+            sl = &ctl->slot[ph % 3];
+            for (uint32_t base = 0; base < rem_n; base += nthr) {
+                const uint32_t i = base + tid;
+                bool take = false;
+                uint32_t v = 0, na = 0;
+                if (i < rem_n) {
+                    v = __ldcg(rem + i);
+                    take = __ldcg(deg + v) <= k;
+                    if (take) {
+                        level[v] = round;
+                        na = adj_off[v + 1] - adj_off[v];
+                    }
+                }
+                push_frontier(take, v, na, sl, front, foff, lane);
+            }
+            r = end_phase();
+            const uint64_t f = __ldcg(&r->front);
+            fn = (uint32_t)(f >> 40);
+            fe = (uint32_t)(f & MASK40);
+        }
+        // relaxation: remove the frontier (round `round`)
+        PeelSlot *sl = &ctl->slot[ph % 3];
+        for (uint32_t e0 = tid * PEEL_RUN; e0 - tid * PEEL_RUN < fe; e0 += nthr * PEEL_RUN) {
+            // the loop bound keeps every lane of a warp iterating together
+            uint32_t e1 = min(fe, e0 + PEEL_RUN);
+            uint32_t fi = 0, fbeg = 0, fend = 0, v = 0;
+            if (e0 < fe) {
+                uint32_t lo = 0, hi = fn;  // last fi with foff[fi] <= e0
+                while (hi - lo > 1) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (__ldcg(foff + mid) <= e0) lo = mid; else hi = mid;
+                }
+                fi = lo;
+                fbeg = __ldcg(foff + fi);
+                fend = fi + 1 < fn ? __ldcg(foff + fi + 1) : fe;
+                v = __ldcg(front + fi);
+            } else {
+                e1 = e0;
+            }
+            for (uint32_t step = 0; step < PEEL_RUN; step++) {
+                const uint32_t e = e0 + step;
+                bool push = false;
+                uint32_t w = 0, na = 0;
+                if (e < e1) {
+                    while (e >= fend) {
+                        fi++;
+                        fbeg = fend;
+                        fend = fi + 1 < fn ? __ldcg(foff + fi + 1) : fe;
+                        v = __ldcg(front + fi);
+                    }
+                    w = adj[adj_off[v] + (e - fbeg)];
+                    if (__ldcg(level + w) == UNSET) {
+                        const int old = atomicSub(deg + w, 1);
+                        if (old == k + 1) {
+                            push = true;
+                            level[w] = round + 1;
+                            na = adj_off[w + 1] - adj_off[w];
+                        }
+                    }
+                }
+                push_frontier(push, w, na, sl, front_next, foff_next, lane);
             }
         }
+        const PeelSlot *r = end_phase();
+        const uint64_t f = __ldcg(&r->front);
+        fn = (uint32_t)(f >> 40);
+        fe = (uint32_t)(f & MASK40);
         round++;
-        cluster.sync();
+        uint32_t *t = front; front = front_next; front_next = t;
+        t = foff; foff = foff_next; foff_next = t;
     }
     if (tid == 0) {
         ctl->rounds = round;
         ctl->kappa = kappa;
+        if (!ok) ctl->error = 1;
     }
 }
 
@@ -339,6 +400,13 @@ __global__ void max_u32_kernel(const unsigned int *x, size_t n, unsigned int *mx
     if ((threadIdx.x & 31) == 0 && mx) atomicMax(mx_out, mx);
 }
 
+__global__ void widen_kernel(const uint32_t *a, const uint32_t *b, size_t n, uint64_t *a64, uint64_t *b64) {
+    GRID_STRIDE(i, n) {
+        a64[i] = a[i];
+        b64[i] = b[i];
+    }
+}
+
 // ---------------------------------------------------------------- triangles
 struct RecCtx {
     const uint32_t *poff;
@@ -368,52 +436,9 @@ __device__ uint4 make_record(const RecCtx &c, uint32_t u0, uint32_t v0, uint32_t
     return make_uint4(A, B, C, flags);
 }
 
-// Intersect two sorted id lists; calls f(i, j) for every common element.
-template <typename F>
-__device__ __forceinline__ void intersect(const uint32_t *a, uint32_t na, const uint32_t *b, uint32_t nb, F f) {
-    uint32_t i = 0, j = 0;
-    while (i < na && j < nb) {
-        const uint32_t x = a[i], y = b[j];
-        if (x < y) i++;
-        else if (y < x) j++;
-        else { f(i, j); i++; j++; }
-    }
-}
 
-__global__ void tri_count_kernel(const uint32_t *osrc, const uint32_t *onbr, const uint32_t *out_off, size_t ms,
-                                 uint64_t *cnt) {
-    GRID_STRIDE(e, ms) {
-        const uint32_t u = osrc[e], v = onbr[e];
-        uint64_t c = 0;
-        intersect(onbr + out_off[u], out_off[u + 1] - out_off[u], onbr + out_off[v], out_off[v + 1] - out_off[v],
-                  [&](uint32_t, uint32_t) { c++; });
-        cnt[e] = c;
-    }
-}
 
-__global__ void tri_write_kernel(const uint32_t *osrc, const uint32_t *onbr, const uint32_t *opair,
-                                 const uint32_t *out_off, size_t ms, const uint64_t *tri_off, RecCtx rc,
-                                 uint4 *rec, uint8_t *is_light) {
-    GRID_STRIDE(e, ms) {
-        const uint32_t u = osrc[e], v = onbr[e];
-        uint64_t o = tri_off[e];
-        const uint32_t bu = out_off[u], bv = out_off[v];
-        intersect(onbr + bu, out_off[u + 1] - bu, onbr + bv, out_off[v + 1] - bv, [&](uint32_t i, uint32_t j) {
-            bool heavy;
-            rec[o] = make_record(rc, u, v, onbr[bu + i], opair[e], opair[bu + i], opair[bv + j], &heavy);
-            is_light[o] = !heavy;
-            o++;
-        });
-    }
-}
 
-__global__ void partition_kernel(const uint4 *rec, const uint8_t *is_light, const uint32_t *lpos, size_t tau,
-                                 uint64_t n_light, uint4 *out) {
-    GRID_STRIDE(i, tau) {
-        const uint64_t dst = is_light[i] ? lpos[i] : n_light + (i - lpos[i]);
-        out[dst] = rec[i];
-    }
-}
 
 // sizes of heavy records and the work statistics of all records
 __global__ void record_stats_kernel(const uint4 *rec, size_t tau, uint64_t n_light, const uint32_t *poff,
@@ -441,6 +466,106 @@ __global__ void record_stats_kernel(const uint4 *rec, size_t tau, uint64_t n_lig
     }
 }
 
+// Triangle enumeration, warp-cooperative.  A warp takes 32 consecutive
+// oriented edges (u, v) and flattens the elements of their N+(v) lists into
+// one index space; each lane takes one element w per step and looks it up in
+// N+(u) by binary search (both lists sorted by id), so a hit is the triangle
+// <u, v, w> of Sec. 5.  COUNT pass: per edge, the number of light and heavy
+// records.  WRITE pass: the records, each at its edge's offset in its bin
+// plus its rank among the edge's hits of that bin (hits are ranked in
+// (step, lane) order, so the layout is deterministic).
+constexpr int TRI_THREADS = 256;
+constexpr int TRI_WARPS = TRI_THREADS / 32;
+
+template <bool WRITE>
+__global__ void __launch_bounds__(TRI_THREADS)
+    tri_enum_kernel(const uint32_t *__restrict__ osrc, const uint32_t *__restrict__ onbr,
+                    const uint32_t *__restrict__ opair, const uint32_t *__restrict__ out_off, size_t ms, RecCtx rc,
+                    uint32_t *cnt_light, uint32_t *cnt_heavy, const uint64_t *light_off, const uint64_t *heavy_off,
+                    uint64_t heavy_base, uint4 *rec) {
+    __shared__ uint32_t s_excl[TRI_WARPS][33];
+    __shared__ uint32_t s_u[TRI_WARPS][32], s_v[TRI_WARPS][32], s_vb[TRI_WARPS][32];
+    __shared__ uint32_t s_run[TRI_WARPS][64];  // per edge slot: light, heavy hits so far
+    const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const uint64_t nchunks = (ms + 31) / 32;
+    for (uint64_t c = (uint64_t)blockIdx.x * TRI_WARPS + w; c < nchunks; c += (uint64_t)gridDim.x * TRI_WARPS) {
+        const uint64_t e = c * 32 + lane;
+        uint32_t len = 0;
+        if (e < ms) {
+            const uint32_t u = osrc[e], v = onbr[e];
+            s_u[w][lane] = u;
+            s_v[w][lane] = v;
+            s_vb[w][lane] = out_off[v];
+            len = out_off[v + 1] - out_off[v];
+        }
+        s_run[w][2 * lane] = 0;
+        s_run[w][2 * lane + 1] = 0;
+        uint32_t x = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= (uint32_t)o) x += y;
+        }
+        s_excl[w][lane] = x - len;
+        const uint32_t total = __shfl_sync(0xffffffffu, x, 31);
+        if (lane == 0) s_excl[w][32] = total;
+        __syncwarp();
+        for (uint32_t base = 0; base < total; base += 32) {
+            const uint32_t j = base + lane;
+            bool hit = false, heavy = false;
+            uint32_t slot = 0;
+            uint4 r = make_uint4(0, 0, 0, 0);
+            if (j < total) {
+                uint32_t o = 0;
+#pragma unroll
+                for (uint32_t step = 16; step; step >>= 1)
+                    if (s_excl[w][o + step] <= j) o += step;
+                slot = o;
+                const uint32_t u = s_u[w][o];
+                const uint32_t jv = s_vb[w][o] + (j - s_excl[w][o]);
+                const uint32_t x3 = onbr[jv];
+                // binary search x3 in N+(u)
+                const uint32_t ub = out_off[u];
+                uint32_t lo = 0, n = out_off[u + 1] - ub;
+                while (n > 0) {
+                    const uint32_t half = n >> 1;
+                    if (onbr[ub + lo + half] < x3) {
+                        lo += half + 1;
+                        n -= half + 1;
+                    } else {
+                        n = half;
+                    }
+                }
+                if (lo < out_off[u + 1] - ub && onbr[ub + lo] == x3) {
+                    hit = true;
+                    r = make_record(rc, u, s_v[w][o], x3, opair[c * 32 + o], opair[ub + lo], opair[jv], &heavy);
+                }
+            }
+            const unsigned act = __ballot_sync(0xffffffffu, hit);
+            if (!act) continue;
+            const uint32_t key = slot * 2 + (heavy ? 1u : 0u);
+            const unsigned peers = __match_any_sync(0xffffffffu, hit ? key : 0xffffffffu) & act;
+            uint32_t rank = 0;
+            if (hit) rank = s_run[w][key] + __popc(peers & lt_mask);
+            __syncwarp();
+            if (hit && (peers & lt_mask) == 0) s_run[w][key] += __popc(peers);
+            __syncwarp();
+            if (WRITE && hit) {
+                const uint64_t ee = c * 32 + slot;
+                const uint64_t pos = heavy ? heavy_base + heavy_off[ee] + rank : light_off[ee] + rank;
+                rec[pos] = r;
+            }
+        }
+        __syncwarp();
+        if (!WRITE && e < ms) {
+            cnt_light[e] = s_run[w][2 * lane];
+            cnt_heavy[e] = s_run[w][2 * lane + 1];
+        }
+        __syncwarp();
+    }
+}
+
 template <typename T>
 T read_scalar(const T *dev, cudaStream_t s) {
     T h;
@@ -452,6 +577,33 @@ T read_scalar(const T *dev, cudaStream_t s) {
 }  // namespace
 
 uint32_t default_light_max_pairs() { return 65; }
+
+// Largest cluster (up to 16 CTAs of 1024 threads) the device can run for the peel.
+int peel_cluster_size() {
+    static int best = 0;
+    if (best) return best;
+    cudaFuncSetAttribute(peel_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    best = 8;
+    for (int c = 16; c > 8; c /= 2) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(c);
+        cfg.blockDim = dim3(PEEL_THREADS);
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = c;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int clusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&clusters, peel_kernel, &cfg) == cudaSuccess && clusters >= 1) {
+            best = c;
+            break;
+        }
+        cudaGetLastError();
+    }
+    return best;
+}
 
 void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, const int64_t *t_in, uint64_t m_in,
                  const LoadOptions &opt) {
@@ -601,13 +753,13 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
         TTC_LAUNCH_CHECK();
         DevBuf<int> pdeg(n, s);
         TTC_CUDA(cudaMemcpyAsync(pdeg.get(), deg.get(), n * 4, cudaMemcpyDeviceToDevice, s));
-        DevBuf<uint32_t> remA(n, s), remB(n, s), front(n, s), foff(n, s);
+        DevBuf<uint32_t> remA(n, s), remB(n, s), frontA(n, s), frontB(n, s), foffA(n, s), foffB(n, s);
         DevBuf<PeelCtl> ctl(1, s);
         PeelCtl init{};
-        init.min_deg[0] = init.min_deg[1] = INT_MAX;
+        for (auto &sl : init.slot) sl.min_deg = INT_MAX;
         TTC_CUDA(cudaMemcpyAsync(ctl.get(), &init, sizeof(init), cudaMemcpyHostToDevice, s));
+        int cluster = peel_cluster_size();
         cudaLaunchConfig_t cfg = {};
-        int cluster = 8;
         cfg.gridDim = dim3(cluster);
         cfg.blockDim = dim3(PEEL_THREADS);
         cfg.stream = s;
@@ -619,8 +771,8 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         TTC_CUDA(cudaLaunchKernelEx(&cfg, peel_kernel, (const uint32_t *)adj_off.get(), (const uint32_t *)adj.get(),
-                                    pdeg.get(), level.get(), remA.get(), remB.get(), front.get(), foff.get(),
-                                    (uint32_t)n, ctl.get()));
+                                    pdeg.get(), level.get(), remA.get(), remB.get(), frontA.get(), frontB.get(),
+                                    foffA.get(), foffB.get(), (uint32_t)n, ctl.get()));
         note_launch();
         const PeelCtl out = read_scalar(ctl.get(), s);
         if (out.error) fail(TTC_ERR_INTERNAL, "k-core peel did not finish");
@@ -652,32 +804,34 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
     TTC_LAUNCH_CHECK();
     okey.reset(); outdeg.reset(); deg.reset();
 
-    // ---- a6: triangles
-    DevBuf<uint64_t> cnt(ms, s), tri_off(ms + 1, s);
-    tri_count_kernel<<<grid_for(ms), TPB, 0, s>>>(osrc.get(), onbr.get(), out_off.get(), ms, cnt.get());
-    TTC_LAUNCH_CHECK();
-    exclusive_scan_u64(cnt.get(), tri_off.get(), ms, s);
-    const uint64_t tau = read_scalar(tri_off.get() + ms, s);
-    st.tau = tau;
-    cnt.reset();
+    // ---- a6: triangles, written straight into the light and heavy bins
     RecCtx rc{g->poff.get(), g->pair_vtx.get(), g->labeling, g->light_max_pairs};
+    const unsigned tgrid = (unsigned)std::min<uint64_t>((ms + 255) / 256 + 1, (uint64_t)sm_count() * 16);
+    DevBuf<uint32_t> cl(ms + 1, s), ch(ms + 1, s);
+    DevBuf<uint64_t> loff(ms + 1, s), hoff(ms + 1, s), cl64(ms + 1, s), ch64(ms + 1, s);
+    tri_enum_kernel<false><<<tgrid, TRI_THREADS, 0, s>>>(osrc.get(), onbr.get(), opair.get(), out_off.get(), ms, rc,
+                                                        cl.get(), ch.get(), nullptr, nullptr, 0, nullptr);
+    TTC_LAUNCH_CHECK();
+    widen_kernel<<<grid_for(ms), TPB, 0, s>>>(cl.get(), ch.get(), ms, cl64.get(), ch64.get());
+    TTC_LAUNCH_CHECK();
+    exclusive_scan_u64(cl64.get(), loff.get(), ms, s);
+    exclusive_scan_u64(ch64.get(), hoff.get(), ms, s);
+    uint64_t nlh[2];
+    TTC_CUDA(cudaMemcpyAsync(&nlh[0], loff.get() + ms, 8, cudaMemcpyDeviceToHost, s));
+    TTC_CUDA(cudaMemcpyAsync(&nlh[1], hoff.get() + ms, 8, cudaMemcpyDeviceToHost, s));
+    TTC_CUDA(cudaStreamSynchronize(s));
+    const uint64_t n_light = nlh[0], tau = nlh[0] + nlh[1];
+    if (tau >= (uint64_t(1) << 32)) fail(TTC_ERR_RANGE, "more than 2^32 static triangles");
+    st.tau = tau;
     g->tri.alloc(tau, s);
-    uint64_t n_light = 0;
     if (tau) {
-        DevBuf<uint4> rec(tau, s);
-        DevBuf<uint8_t> is_light(tau, s);
-        tri_write_kernel<<<grid_for(ms), TPB, 0, s>>>(osrc.get(), onbr.get(), opair.get(), out_off.get(), ms,
-                                                      tri_off.get(), rc, rec.get(), is_light.get());
-        TTC_LAUNCH_CHECK();
-        if (tau >= (uint64_t(1) << 32)) fail(TTC_ERR_RANGE, "more than 2^32 static triangles");
-        DevBuf<uint32_t> lpos(tau + 1, s);
-        exclusive_scan_flags(is_light.get(), lpos.get(), tau, s);
-        n_light = read_scalar(lpos.get() + tau, s);
-        partition_kernel<<<grid_for(tau), TPB, 0, s>>>(rec.get(), is_light.get(), lpos.get(), tau, n_light,
-                                                       g->tri.get());
+        tri_enum_kernel<true><<<tgrid, TRI_THREADS, 0, s>>>(osrc.get(), onbr.get(), opair.get(), out_off.get(), ms,
+                                                           rc, nullptr, nullptr, loff.get(), hoff.get(), n_light,
+                                                           g->tri.get());
         TTC_LAUNCH_CHECK();
     }
-    osrc.reset(); onbr.reset(); opair.reset(); out_off.reset(); tri_off.reset();
+    cl.reset(); ch.reset(); loff.reset(); hoff.reset(); cl64.reset(); ch64.reset();
+    osrc.reset(); onbr.reset(); opair.reset(); out_off.reset();
     st.tau_light = n_light;
     st.tau_heavy = tau - n_light;
 
