@@ -45,6 +45,12 @@ def parse():
     ap.add_argument("--query-iters", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--mode", choices=["plain", "multi", "serve"], default="plain",
+                    help="plain: the power-law workload (default line); multi: many graphs in one launch; "
+                         "serve: Poisson queries against a resident pool")
+    ap.add_argument("--graphs", type=int, default=4096, help="multi: number of graphs")
+    ap.add_argument("--rate", type=float, default=2000.0, help="serve: query arrivals per second")
+    ap.add_argument("--duration", type=float, default=20.0, help="serve: seconds of arrivals")
     return ap.parse_args()
 
 
@@ -197,6 +203,129 @@ def run_reference(args):
     barrier(ws)
 
 
+# ------------------------------------------------------------------ batched sweep
+def batched_sweep(ttc, torch, reps=20):
+    """64 delta-triples on the tiny-plain graph: one ttc_count_batch call
+    against 64 sequential ttc_count calls (queries per second each)."""
+    from paper_2106_02762_gb300 import synth
+    s, d, t = synth.tiny_plain()
+    deltas = synth.delta_sweep()
+    g = ttc.Graph(s, d, t)
+    ref = g.count_batch(deltas)
+    seq_t, bat_t = [], []
+    for _ in range(reps):
+        w = time.perf_counter()
+        seq = [g.count(q) for q in deltas]
+        seq_t.append(time.perf_counter() - w)
+        w = time.perf_counter()
+        b = g.count_batch(deltas)
+        bat_t.append(time.perf_counter() - w)
+    assert (np.stack(seq) == ref).all() and (b == ref).all()
+    g.free()
+    seq_s, bat_s = statistics.median(seq_t), statistics.median(bat_t)
+    return {"workload": "tiny plain graph (n=1000, 5000 pairs), 64 delta-triples log-spaced 60 s..30 d",
+            "batch_queries_per_s": len(deltas) / bat_s, "sequential_queries_per_s": len(deltas) / seq_s,
+            "speedup": seq_s / bat_s, "batch_ms": bat_s * 1e3, "sequential_ms": seq_s * 1e3}
+
+
+# ------------------------------------------------------------------ many graphs
+def _gen_many(item):
+    from paper_2106_02762_gb300 import synth
+    n, pairs, seed = item
+    return synth.many_graph(n, pairs, seed)
+
+
+def run_multi(args):
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    from paper_2106_02762_gb300 import synth
+    n, pairs, deltas, seeds = synth.many_graph_specs(count=args.graphs)
+    # generate on every host core (spawned workers) while loading in order
+    pool = cf.ProcessPoolExecutor(max_workers=max(1, (os.cpu_count() or 2) - 1), mp_context=mp.get_context("spawn"))
+    items = [(int(n[i]), int(pairs[i]), int(seeds[i])) for i in range(args.graphs)]
+    futures = pool.map(_gen_many, items, chunksize=4)
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2106_02762_gb300 import ttc
+    graphs, m_tot = [], 0
+    t0 = time.perf_counter()
+    for s, d, t in futures:
+        graphs.append(ttc.Graph(s, d, t))
+        m_tot += s.size
+    pool.shutdown()
+    load_s = time.perf_counter() - t0
+    dl = [tuple(int(x) for x in q) for q in deltas]
+    first = ttc.count_multi(graphs, dl)  # plan, autotune, capture
+    for _ in range(args.warmup):
+        assert (ttc.count_multi(graphs, dl) == first).all()
+    times = []
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        w = time.perf_counter()
+        out = ttc.count_multi(graphs, dl)
+        times.append(time.perf_counter() - w)
+        assert (out == first).all()
+    step = statistics.median(times)
+    tau = sum(g.info()["tau"] for g in graphs)
+    print(json.dumps({"mode": "multi", "metric": METRIC, "value": m_tot / step, "unit": UNIT, "graphs": args.graphs,
+                      "m_total": m_tot, "tau_total": tau, "ms_per_launch": step * 1e3,
+                      "load_generate_s": load_s, "higher_is_better": True,
+                      "config": {"workload": "many graphs: n log-uniform [1e3,1e5], degree U[4,32], Chung-Lu 2.3, "
+                                             "Geometric(0.3) multiplicity, t uniform [0,1e7), one delta per graph"}}),
+          flush=True)
+    for g in graphs:
+        g.free()
+
+
+# ------------------------------------------------------------------ served
+def run_serve(args):
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2106_02762_gb300 import synth, ttc
+    ladder = synth.served_ladder()
+    if args.scale != 1.0:
+        ladder = [max(1000, int(x * args.scale)) for x in ladder]
+    srv = ttc.Server(streams=4, max_batch=256)
+    ids, alone, m_tot = [], [], 0
+    for j, m in enumerate(ladder):
+        gr = synth.served_graph(m, synth.MASTER_SEED + 5 + j)
+        ids.append(srv.load(*gr))
+        m_tot += gr[0].size
+    rng = synth.rng_for(synth.MASTER_SEED + 50)
+    arrivals = synth.poisson_arrivals(synth.MASTER_SEED + 51, args.rate, args.duration)
+    picks = rng.integers(0, len(ids), size=arrivals.size)
+    qs = synth.log_uniform_int(rng, 60, 2.6e6, size=(arrivals.size, 3))
+    # warm every graph once
+    for gid in ids:
+        srv.submit(gid, (3600, 1800, 1800))
+    srv.drain(60.0)
+    tickets = []
+    t0 = time.perf_counter()
+    for a, j, q in zip(arrivals, picks, qs):
+        while time.perf_counter() - t0 < a:
+            pass
+        tickets.append(srv.submit(ids[j], tuple(int(x) for x in q)))
+    srv.drain(120.0)
+    wall = time.perf_counter() - t0
+    lat = []
+    for tk in tickets:
+        r = srv.poll(tk)
+        lat.append(r[1])
+    lat = np.asarray(lat)
+    info = srv.info()
+    srv.close()
+    print(json.dumps({"mode": "serve", "metric": "served latency", "arrival_rate": args.rate,
+                      "queries": len(tickets), "queries_per_s": len(tickets) / wall,
+                      "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                      "mean_ms": float(lat.mean() * 1e3), "launches": info["launches"],
+                      "graphs": len(ids), "m_total": m_tot,
+                      "config": {"workload": "16 resident ER graphs, 1e5..1e8 edges (log-spaced), Poisson arrivals, "
+                                             "uniform graph, delta components log-uniform [60, 2.6e6] s"}}),
+          flush=True)
+
+
 # ------------------------------------------------------------------ our arm
 def run_ours(args):
     import torch
@@ -285,6 +414,20 @@ def run_ours(args):
             kern.setdefault(kname, []).append(ms / 1e3)
     info = g.info()
     g.set_profiling(False)
+    # the same query with every window unbounded (no window pruning applies)
+    from paper_2106_02762_gb300 import synth
+    unb = synth.LARGE_PLAIN_DELTA_UNBOUNDED
+    g.count(unb)
+    u_times = []
+    for _ in range(max(3, args.query_iters // 4)):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.count(unb)
+        e1.record(stream)
+        e1.synchronize()
+        u_times.append(e0.elapsed_time(e1) / 1e3)
+    u_s = statistics.median(u_times)
     g.free()
     q_s = statistics.median(q_times)
     kern_avg = {k: sum(v) / len(v) for k, v in kern.items()}
@@ -324,6 +467,8 @@ def run_ours(args):
     e_s = allreduce_max(statistics.median(e_times), ws, dev)
     e2e = {"value": ws * m / e_s, "unit": UNIT, "h2d_bytes_per_step": int(m_in * 16), "d2h_bytes_per_step": 64}
 
+    batched = batched_sweep(ttc, torch) if rank == 0 else None
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         full, desc, cores, nparts, spent, _ = oracle_sample(src, dst, t, delta, args.cpu_seconds)
@@ -340,8 +485,10 @@ def run_ours(args):
                        "l2": "inputs larger than L2 (no flush)", "parallelism": "replicas" if ws > 1 else "1 gpu"},
             "query": {"edges_per_s": m / q_s, "static_triangles_per_s": info["tau"] / q_s, "ms": q_s * 1e3,
                       "kernels_ms": {k: v * 1e3 for k, v in kern_avg.items()}},
+            "query_unbounded": {"delta": list(unb), "edges_per_s": m / u_s, "ms": u_s * 1e3},
             "load_edges_per_s": m / max(1e-9, step_s - q_s),
             "roofline": roof,
+            "batched": batched,
             "e2e": e2e,
             "gpu_launches": int(launches),
             "wall_s_timed": wall,
@@ -359,6 +506,10 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.mode == "multi":
+        run_multi(args)
+    elif args.mode == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 

@@ -114,6 +114,9 @@ typedef struct {
     uint64_t tau_heavy;      /* triangles on the prefix-sum (CEC) path */
     uint64_t device_bytes;   /* device memory held by the graph */
     uint64_t work_bytes_heavy; /* the part of work_bytes from prefix-sum-path triangles */
+    uint64_t tau_huge;       /* prefix-sum-path triangles too large for one CTA (flat path) */
+    uint64_t tau_hwarp;      /* prefix-sum-path triangles counted by one warp each */
+    uint64_t tau_hcta;       /* prefix-sum-path triangles counted by one CTA each */
     uint32_t key_bits;       /* bits of the packed per-edge key */
     uint32_t reserved;
 } ttc_graph_stats;
@@ -218,6 +221,11 @@ ttc_status ttc_serve_submit(ttc_server *s, uint64_t graph_id, const ttc_delta *d
  * submit-to-completion latency in seconds (latency_s may be NULL).  A ticket
  * can be collected once. */
 ttc_status ttc_serve_poll(ttc_server *s, uint64_t ticket, uint64_t out[TTC_NUM_TYPES], double *latency_s);
+
+/* Hold (paused = 1) or resume (0) the launching of new batches; queries
+ * submitted meanwhile wait in the queue.  Batches already on the device run
+ * to completion. */
+ttc_status ttc_serve_pause(ttc_server *s, int paused);
 
 /* Block until every submitted query has completed, or timeout_s passes
  * (TTC_ERR_TIMEOUT). */

@@ -134,10 +134,16 @@ using namespace ttc;
         return TTC_ERR_INTERNAL;                       \
     }
 
+namespace ttc {
+void multi_forget(ttc_graph *g);
+void count_multi(ttc_graph *const *gs, const ttc_delta *d, uint32_t G, uint64_t *out);
+}  // namespace ttc
+
 namespace {
 
 void graph_destroy(ttc_graph *g) {
     if (!g) return;
+    multi_forget(g);
     cudaSetDevice(g->device);
     cudaStream_t s = g->stream;
     for (auto &e : g->prof) {
@@ -145,7 +151,8 @@ void graph_destroy(ttc_graph *g) {
         cudaEventDestroy(e.stop);
     }
     g->key.reset(); g->fwd.reset(); g->poff.reset(); g->pair_vtx.reset(); g->tri.reset();
-    g->heavy_eoff.reset(); g->acc.reset(); g->dq.reset(); g->scratch.reset();
+    g->huge_eoff.reset(); g->view.reset(); g->prefix.reset();
+    g->acc.reset(); g->dq.reset(); g->scratch.reset();
     if (s) cudaStreamSynchronize(s);
     if (g->own_stream && s) cudaStreamDestroy(s);
     delete g;
@@ -153,7 +160,8 @@ void graph_destroy(ttc_graph *g) {
 
 uint64_t graph_device_bytes(const ttc_graph *g) {
     return g->key.bytes() + g->fwd.bytes() + g->poff.bytes() + g->pair_vtx.bytes() + g->tri.bytes() +
-           g->heavy_eoff.bytes() + g->acc.bytes() + g->dq.bytes() + g->scratch.bytes();
+           g->huge_eoff.bytes() + g->view.bytes() + g->prefix.bytes() + g->acc.bytes() +
+           g->dq.bytes() + g->scratch.bytes();
 }
 
 // Runs k normalised queries and copies the counts to out (host).
@@ -339,10 +347,7 @@ ttc_status ttc_count_multi(ttc_graph *const *g, const ttc_delta *d, uint32_t G, 
         return TTC_ERR_INVALID;
     }
     TTC_API_BEGIN
-    for (uint32_t i = 0; i < G; i++) {
-        if (!g[i]) fail(TTC_ERR_INVALID, "graph %u is NULL", i);
-        run_queries(g[i], d + i, 1, out + 8 * (size_t)i);
-    }
+    count_multi(g, d, G, out);
     return TTC_OK;
     TTC_API_END
 }

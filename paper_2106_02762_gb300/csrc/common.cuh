@@ -82,6 +82,9 @@ void exclusive_scan_flags(const uint8_t *in, uint32_t *out, size_t n, cudaStream
 // place: keys/vals hold the result on return (alt buffers are scratch).
 void radix_sort_u64_u32(uint64_t *keys, uint32_t *vals, size_t n, int bits, cudaStream_t s);
 void radix_sort_u64_u64(uint64_t *keys, uint64_t *vals, size_t n, int bits, cudaStream_t s);
+// Stable sort on key bits [begin_bit, end_bit) only.
+void radix_sort_u64_u64_range(uint64_t *keys, uint64_t *vals, size_t n, int begin_bit, int end_bit,
+                              cudaStream_t s);
 
 // Reductions into a device scalar (the caller copies it back).
 void reduce_minmax_i64(const int64_t *in, size_t n, int64_t *dmin, int64_t *dmax, cudaStream_t s);

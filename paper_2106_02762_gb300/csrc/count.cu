@@ -4,11 +4,11 @@
 // (Table 1).  Only the edge lists of the pairs A = {u, v} and B = {u, w} are
 // enumerated; the list of C = {v, w} is only searched (Sec. 5).
 //
-// Two bins, chosen per triangle at load time:
+// Three bins, chosen per triangle at load time:
 //
-// light  (sigma_A * sigma_B small): one thread per triangle sums Lemma 1
-//        directly over the pairs (a, b) in A x B.  With x the earlier and y
-//        the later of a, b (key order), C's edge c can be
+// light  (sigma_A * sigma_B small): Lemma 1 summed directly over the pairs
+//        (a, b) in A x B.  With x the earlier and y the later of a, b (key
+//        order), C's edge c can be
 //          third  (x, y, c): t_y - t_x <= d12, key(c) > key(y),
 //                            t_c <= min(t_y + d23, t_x + d13)      (Lemma 1)
 //          second (x, c, y): t_y - t_x <= d13, key(x) < key(c) < key(y),
@@ -16,19 +16,26 @@
 //          first  (c, x, y): t_y - t_x <= d23, key(c) < key(x),
 //                            t_c >= max(t_x - d12, t_y - d13)
 //        and each case is a contiguous index range of C's key-sorted list.
+//        A warp flattens the pairs of 32 triangles across its lanes.
 //
-// heavy  (prefix-sum form of Algs. 2-4, re-derived with key order for ties):
-//        each enumerated edge e of A or B first gets, per direction of C,
+// heavy  the prefix-sum form of Algs. 2-4, re-derived with key order for
+//        ties.  Each enumerated edge e of A or B first gets, per direction of
+//        C,
 //          h(e) = #{c: t_c <= t_e + d13}          (CEC_{+d13} terms, Alg. 2)
 //          L(e) = #{c: key(c) < key(e)}           (CEC_{-inf} terms, Alg. 3)
 //          R(e) = #{c: t_c <  t_e - d23}          (CEC_{-d23} terms, Alg. 3)
 //          M(e) = #{c: t_c <  t_e - d13}          (CEC_{-d13} terms, Alg. 4)
-//        whose prefix sums over each list (per own direction) are then read
-//        at binary-searched range ends while enumerating the other list.  The
-//        work is flat over all enumerated edges of all heavy triangles, so a
-//        triangle with long lists is spread over many warps and CTAs.
+//        (phase 1); their prefix sums over each list and own direction are
+//        then read at binary-searched range ends while every edge of the
+//        other list is enumerated (phase 2).  One CTA takes one triangle:
+//        both lists and all prefix sums stay in shared memory.
 //
-// Deltas arrive normalised (d12, d23 <= d13 <= d12 + d23); all counts use
+// huge   heavy triangles whose two lists do not fit one CTA: the same
+//        phases, flat over every enumerated edge of every huge triangle (so
+//        one triangle is spread over many CTAs), prefix sums in device
+//        scratch.
+//
+// Deltas arrive normalised (d12, d23 <= d13 <= d12 + d23); all counts are
 // unsigned 64-bit sums with carry detection.
 #include <cstring>
 #include <vector>
@@ -70,139 +77,185 @@ __device__ __forceinline__ Query load_query(const int64_t *dq, uint32_t q) {
     return Query{dq[3 * q], dq[3 * q + 1], dq[3 * q + 2]};
 }
 
-// One pair's edge list: key[b .. b + n), plus the direction bookkeeping.
-struct List {
-    uint32_t b, n;
-    uint32_t flip;  // 1: effective direction = stored direction ^ 1
-};
-
-struct KeyCtx {
+// ---------------------------------------------------------------- lists
+// A pair's key-sorted edge list in device memory: key[b .. b + n), with the
+// direction split read from the global dir-0 prefix `fwd`.
+struct GList {
     const int64_t *__restrict__ key;
     const uint32_t *__restrict__ fwd;
+    uint32_t b, n, flip;  // flip: effective direction = stored ^ 1
+    // number of keys < bound (bound >= 0)
+    __device__ __forceinline__ uint32_t below(int64_t bound) const {
+        const int64_t *p = key + b;
+        uint32_t lo = 0, len = n;
+        while (len > 0) {
+            const uint32_t half = len >> 1;
+            if (__ldg(p + lo + half) < bound) {
+                lo += half + 1;
+                len -= half + 1;
+            } else {
+                len = half;
+            }
+        }
+        return lo;
+    }
+    // effective direction-0 edges among the first pos
+    __device__ __forceinline__ uint32_t d0(uint32_t pos) const {
+        const uint32_t s0 = __ldg(fwd + b + pos) - __ldg(fwd + b);
+        return flip ? pos - s0 : s0;
+    }
+};
+
+// A list staged in shared memory: keys and an effective dir-0 prefix
+// (d0(i) = d0p[i] - base = direction-0 edges among the first i).
+struct SList {
+    const int64_t *key;
+    const uint32_t *d0p;
+    uint32_t n, base;
+    __device__ __forceinline__ uint32_t below(int64_t bound) const {
+        uint32_t lo = 0, len = n;
+        while (len > 0) {
+            const uint32_t half = len >> 1;
+            if (key[lo + half] < bound) {
+                lo += half + 1;
+                len -= half + 1;
+            } else {
+                len = half;
+            }
+        }
+        return lo;
+    }
+    __device__ __forceinline__ uint32_t d0(uint32_t pos) const { return d0p[pos] - base; }
+};
+
+// Packed-key format ((t - t_min) << shift | tie << 1 | dir) for time bounds.
+struct KeyFmt {
     int shift;
     int64_t span;
 };
-
-// number of elements of L with key < bound (bound >= 0)
-__device__ __forceinline__ uint32_t count_below(const KeyCtx &k, const List &L, int64_t bound) {
-    const int64_t *p = k.key + L.b;
-    uint32_t lo = 0, n = L.n;
-    while (n > 0) {
-        const uint32_t half = n >> 1;
-        if (__ldg(p + lo + half) < bound) {
-            lo += half + 1;
-            n -= half + 1;
-        } else {
-            n = half;
-        }
-    }
-    return lo;
-}
 // #{e in L : key(e) < key(x)} for an edge x not in L
-__device__ __forceinline__ uint32_t cnt_key(const KeyCtx &k, const List &L, int64_t kx) {
-    return count_below(k, L, kx & ~int64_t(1));
+template <typename L>
+__device__ __forceinline__ uint32_t cnt_key(const L &l, int64_t kx) {
+    return l.below(kx & ~int64_t(1));
 }
 // #{e in L : t(e) - t_min <= x}
-__device__ __forceinline__ uint32_t cnt_le(const KeyCtx &k, const List &L, int64_t x) {
+template <typename L>
+__device__ __forceinline__ uint32_t cnt_le(const L &l, const KeyFmt &f, int64_t x) {
     if (x < 0) return 0;
-    if (x >= k.span) return L.n;
-    return count_below(k, L, (x + 1) << k.shift);
+    if (x >= f.span) return l.n;
+    return l.below((x + 1) << f.shift);
 }
 // #{e in L : t(e) - t_min < x}
-__device__ __forceinline__ uint32_t cnt_lt(const KeyCtx &k, const List &L, int64_t x) { return cnt_le(k, L, x - 1); }
-// number of direction-0 (effective) edges among the first `pos` of L
-__device__ __forceinline__ uint32_t dir0(const KeyCtx &k, const List &L, uint32_t pos) {
-    const uint32_t s0 = __ldg(k.fwd + L.b + pos) - __ldg(k.fwd + L.b);
-    return L.flip ? pos - s0 : s0;
+template <typename L>
+__device__ __forceinline__ uint32_t cnt_lt(const L &l, const KeyFmt &f, int64_t x) {
+    return cnt_le(l, f, x - 1);
 }
 
-__device__ __forceinline__ List make_list(const uint32_t *__restrict__ poff, uint32_t p, uint32_t flip) {
-    const uint32_t b = __ldg(poff + p);
-    return List{b, __ldg(poff + p + 1) - b, flip};
+__device__ __forceinline__ GList glist(const GraphView &gv, uint32_t p, uint32_t flip) {
+    const uint32_t b = __ldg(gv.poff + p);
+    return GList{gv.key, gv.fwd, b, __ldg(gv.poff + p + 1) - b, flip};
 }
 
-// 64-bit accumulation with carry detection
+// ---------------------------------------------------------------- accumulation
 __device__ __forceinline__ void add_checked(unsigned long long &acc, unsigned long long x, unsigned &ovf) {
     const unsigned long long r = acc + x;
     ovf |= r < acc;
     acc = r;
 }
 
-__device__ __forceinline__ void flush_block(unsigned long long (*s_acc)[256], int nthreads, unsigned long long *acc,
-                                            unsigned ovf) {
-    // s_acc[type][thread] -> global acc[type], one atomic per type per block
-    __syncthreads();
-    if (threadIdx.x < 8) {
-        unsigned long long sum = 0;
-        unsigned o = 0;
-        for (int i = 0; i < nthreads; i++) add_checked(sum, s_acc[threadIdx.x][i], o);
-        if (sum) {
-            const unsigned long long old = atomicAdd(acc + threadIdx.x, sum);
-            o |= old + sum < old;
+// Adds this warp's per-thread counters s_acc[type][tid] into out[0..8) with
+// one atomic per type, zeroes them, and raises *flag on any carry.  Every
+// lane of the warp must call it.
+__device__ __forceinline__ void warp_flush(unsigned long long (*s_acc)[256], unsigned long long *out,
+                                           unsigned long long *flag, unsigned &ovf) {
+    const uint32_t lane = threadIdx.x & 31;
+#pragma unroll
+    for (int t = 0; t < 8; t++) {
+        unsigned long long v = s_acc[t][threadIdx.x];
+        s_acc[t][threadIdx.x] = 0;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            const unsigned long long y = __shfl_xor_sync(0xffffffffu, v, o);
+            add_checked(v, y, ovf);
         }
-        if (o) atomicOr(reinterpret_cast<unsigned int *>(acc + 8), 1u);
+        if (lane == 0 && v) {
+            const unsigned long long old = atomicAdd(out + t, v);
+            ovf |= old + v < old;
+        }
     }
-    if (ovf) atomicOr(reinterpret_cast<unsigned int *>(acc + 8), 1u);
+    if (__any_sync(0xffffffffu, ovf) && lane == 0) atomicOr(flag, 1ull);
+    ovf = 0;
+}
+
+// Block accumulators (several queries): shared atomics with carry checks.
+__device__ __forceinline__ void shared_add(unsigned long long *p, unsigned long long n, unsigned &ovf) {
+    const unsigned long long old = atomicAdd(p, n);
+    ovf |= old + n < old;
+}
+
+__device__ __forceinline__ void block_flush(const unsigned long long *s, uint32_t cnt, unsigned long long *out,
+                                            unsigned long long *flag, unsigned ovf) {
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+        if (s[i]) {
+            const unsigned long long old = atomicAdd(out + i, s[i]);
+            ovf |= old + s[i] < old;
+        }
+    }
+    if (ovf) atomicOr(flag, 1ull);
+}
+
+// Graph of a global work index, from an exclusive prefix over graphs.
+__device__ __forceinline__ uint32_t graph_of(const uint64_t *__restrict__ pre, uint32_t G, uint64_t i) {
+    uint32_t lo = 0, hi = G;  // last g with pre[g] <= i
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (__ldg(pre + mid) <= i) lo = mid; else hi = mid;
+    }
+    return lo;
 }
 
 // ---------------------------------------------------------------- light bin
 constexpr int LIGHT_THREADS = 256;
-
-struct LightArgs {
-    KeyCtx k;
-    const uint32_t *__restrict__ poff;
-    const uint4 *__restrict__ tri;
-    uint64_t ntri;
-    // sample mode: triangle index = first + i * stride, counts to out[i][8]
-    uint64_t first, stride;
-    unsigned long long *per_tri;
-};
+constexpr int LIGHT_WARPS = LIGHT_THREADS / 32;
 
 // Adds the counts of one pair (x, y) of enumerated edges (x earlier) for all
 // three positions of C's edge.  xa: x is on A (else on B).
 template <typename Acc>
-__device__ __forceinline__ void light_pair(const KeyCtx &k, const List &C, const Query &q, bool xa, int64_t rx,
+__device__ __forceinline__ void light_pair(const GList &C, const KeyFmt &f, const Query &q, bool xa, int64_t rx,
                                            int64_t ry, uint32_t posCx, uint32_t posCy, uint32_t dA, uint32_t dB,
                                            Acc &&acc) {
     const int64_t gap = ry - rx;
     if (gap <= q.d12) {  // C third
         const int64_t lim = min(ry + q.d23, rx + q.d13);
-        const uint32_t hi = cnt_le(k, C, lim), lo = posCy;
+        const uint32_t hi = cnt_le(C, f, lim), lo = posCy;
         if (hi > lo) {
-            const uint32_t n0 = dir0(k, C, hi) - dir0(k, C, lo);
+            const uint32_t n0 = C.d0(hi) - C.d0(lo);
             const int pi = xa ? PI1 : PI2;
             acc(type_of(pi, dA, dB, 0), n0);
             acc(type_of(pi, dA, dB, 1), (hi - lo) - n0);
         }
     }
     if (gap <= q.d13) {  // C second
-        const uint32_t lo = max(posCx, cnt_lt(k, C, ry - q.d23));
-        const uint32_t hi = min(posCy, cnt_le(k, C, rx + q.d12));
+        const uint32_t lo = max(posCx, cnt_lt(C, f, ry - q.d23));
+        const uint32_t hi = min(posCy, cnt_le(C, f, rx + q.d12));
         if (hi > lo) {
-            const uint32_t n0 = dir0(k, C, hi) - dir0(k, C, lo);
+            const uint32_t n0 = C.d0(hi) - C.d0(lo);
             const int pi = xa ? PI3 : PI4;
             acc(type_of(pi, dA, dB, 0), n0);
             acc(type_of(pi, dA, dB, 1), (hi - lo) - n0);
         }
     }
     if (gap <= q.d23) {  // C first
-        const uint32_t lo = cnt_lt(k, C, max(rx - q.d12, ry - q.d13)), hi = posCx;
+        const uint32_t lo = cnt_lt(C, f, max(rx - q.d12, ry - q.d13)), hi = posCx;
         if (hi > lo) {
-            const uint32_t n0 = dir0(k, C, hi) - dir0(k, C, lo);
+            const uint32_t n0 = C.d0(hi) - C.d0(lo);
             const int pi = xa ? PI5 : PI6;
             acc(type_of(pi, dA, dB, 0), n0);
             acc(type_of(pi, dA, dB, 1), (hi - lo) - n0);
         }
     }
 }
-
-// ---------------------------------------------------------------------------
-// Warp-cooperative light kernel.  Each warp takes 32 consecutive triangle
-// records, flattens their A x B pairs (fewer than light_max_pairs each) into
-// one index space and gives every lane one pair per step, so lanes stay busy
-// whatever the per-triangle list sizes.  Per pair: the two keys, their
-// positions in C, and the three cases of light_pair.
-constexpr int LIGHT_WARPS = LIGHT_THREADS / 32;
 
 struct WarpTris {
     uint32_t excl[LIGHT_WARPS][33];  // exclusive prefix of pair counts
@@ -211,12 +264,19 @@ struct WarpTris {
     uint32_t fl[LIGHT_WARPS][32];    // flip flags
 };
 
-// MODE 0: one query, per-thread accumulators.  MODE 1: nq queries, block
-// accumulators.  MODE 2: one query, per-triangle output for the sampled
-// triangles idx[0 .. ntri) (acc is then [ntri][8]).
+// Warp-cooperative light kernel over a table of graphs.  Each warp takes 32
+// consecutive triangle records of one graph, flattens their A x B pairs into
+// one index space and gives every lane one pair per step.
+//   MODE 0: one query per graph (dq[3 g]); out[8 g + type].
+//   MODE 1: nq queries on graph 0; out[8 q + type].
+//   MODE 2: one query on graph 0 for the triangles idx[0 .. nidx);
+//           out[8 i + type] per triangle.
+// chunk_pre[g] = first 32-record chunk of graph g (exclusive prefix, G + 1).
 template <int MODE>
 __global__ void __launch_bounds__(LIGHT_THREADS)
-    light_kernel_warp(LightArgs a, const int64_t *dq, uint32_t nq, unsigned long long *acc, const uint64_t *idx) {
+    light_kernel(const GraphView *__restrict__ gvs, const uint64_t *__restrict__ chunk_pre, uint32_t G,
+                 const int64_t *dq, uint32_t nq, unsigned long long *out, unsigned long long *flag,
+                 const uint64_t *idx, uint64_t nidx) {
     __shared__ WarpTris wt;
     __shared__ unsigned long long s_acc[MODE == 0 ? 8 : 1][MODE == 0 ? 256 : 1];
     extern __shared__ unsigned long long s_bacc[];  // MODE 1: [nq * 8]
@@ -225,26 +285,38 @@ __global__ void __launch_bounds__(LIGHT_THREADS)
 #pragma unroll
         for (int j = 0; j < 8; j++) s_acc[j][threadIdx.x] = 0;
     }
-    if (MODE == 1) {
+    if constexpr (MODE == 1) {
         for (uint32_t i = threadIdx.x; i < nq * 8; i += blockDim.x) s_bacc[i] = 0;
         __syncthreads();
     }
     unsigned ovf = 0;
-    const KeyCtx &k = a.k;
-    const uint64_t nchunks = (a.ntri + 31) / 32;
+    uint32_t cur_g = 0xffffffffu;
+    const uint64_t nchunks = MODE == 2 ? (nidx + 31) / 32 : __ldg(chunk_pre + G);
     const uint64_t gw = (uint64_t)blockIdx.x * LIGHT_WARPS + w, nw = (uint64_t)gridDim.x * LIGHT_WARPS;
-    const Query Q0 = load_query(dq, 0);
-    int64_t gmax = Q0.d13;  // every case needs t_y - t_x <= d13 (normalised)
-    if (MODE == 1)
-        for (uint32_t q = 1; q < nq; q++) gmax = max(gmax, dq[3 * q]);
+    int64_t gmax = 0;
+    if constexpr (MODE == 1)
+        for (uint32_t q = 0; q < nq; q++) gmax = max(gmax, dq[3 * q]);
     for (uint64_t c = gw; c < nchunks; c += nw) {
-        const uint64_t ti = c * 32 + lane;
+        const uint32_t g = MODE == 0 ? graph_of(chunk_pre, G, c) : 0u;
+        if constexpr (MODE == 0) {
+            if (g != cur_g) {
+                if (cur_g != 0xffffffffu) warp_flush(s_acc, out + 8 * cur_g, flag, ovf);
+                cur_g = g;
+            }
+        }
+        const GraphView &gv = gvs[g];
+        const KeyFmt f{gv.shift, gv.span};
+        const Query Q0 = load_query(dq, MODE == 0 ? g : 0u);
+        if constexpr (MODE != 1) gmax = Q0.d13;  // every case needs t_y - t_x <= d13
+        const uint64_t lc = MODE == 0 ? c - __ldg(chunk_pre + g) : c;
+        const uint64_t ti = lc * 32 + lane;
+        const uint64_t lim = MODE == 2 ? nidx : gv.n_light;
         uint32_t npairs = 0;
-        if (ti < a.ntri) {
-            const uint4 r = __ldg(a.tri + (MODE == 2 ? idx[ti] : ti));
-            const uint32_t ab = __ldg(a.poff + r.x), an = __ldg(a.poff + r.x + 1) - ab;
-            const uint32_t bb = __ldg(a.poff + r.y), bn = __ldg(a.poff + r.y + 1) - bb;
-            const uint32_t cb = __ldg(a.poff + r.z), cn = __ldg(a.poff + r.z + 1) - cb;
+        if (ti < lim) {
+            const uint4 r = __ldg(gv.tri + (MODE == 2 ? idx[ti] : ti));
+            const uint32_t ab = __ldg(gv.poff + r.x), an = __ldg(gv.poff + r.x + 1) - ab;
+            const uint32_t bb = __ldg(gv.poff + r.y), bn = __ldg(gv.poff + r.y + 1) - bb;
+            const uint32_t cb = __ldg(gv.poff + r.z), cn = __ldg(gv.poff + r.z + 1) - cb;
             npairs = an * bn;
             wt.lst[w][lane] = make_uint4(ab, bb, cb, cn);
             wt.bn[w][lane] = bn;
@@ -271,104 +343,479 @@ __global__ void __launch_bounds__(LIGHT_THREADS)
             const uint32_t bn = wt.bn[w][o], fl = wt.fl[w][o];
             const uint32_t loc = j - wt.excl[w][o];
             const uint32_t ai = loc / bn, bi = loc - ai * bn;
-            const int64_t ka = __ldg(k.key + L.x + ai), kb = __ldg(k.key + L.y + bi);
-            const int64_t ra = ka >> k.shift, rb = kb >> k.shift;
+            const int64_t ka = __ldg(gv.key + L.x + ai), kb = __ldg(gv.key + L.y + bi);
+            const int64_t ra = ka >> f.shift, rb = kb >> f.shift;
             const bool a_first = ka < kb;
             const int64_t gap = a_first ? rb - ra : ra - rb;
             if (gap > gmax) continue;
-            const List C{L.z, L.w, (fl & TriRec::FLIP_C) ? 1u : 0u};
+            const GList C{gv.key, gv.fwd, L.z, L.w, (fl & TriRec::FLIP_C) ? 1u : 0u};
             const uint32_t dA = (uint32_t)(ka & 1) ^ (fl & TriRec::FLIP_A);
             const uint32_t dB = (uint32_t)(kb & 1) ^ ((fl & TriRec::FLIP_B) ? 1u : 0u);
-            const uint32_t pa = cnt_key(k, C, ka), pb = cnt_key(k, C, kb);
+            const uint32_t pa = cnt_key(C, ka), pb = cnt_key(C, kb);
             for (uint32_t q = 0; q < (MODE == 1 ? nq : 1u); q++) {
                 const Query Q = MODE == 1 ? load_query(dq, q) : Q0;
                 auto accq = [&](int type, uint32_t n) {
                     if constexpr (MODE == 0) add_checked(s_acc[type][threadIdx.x], n, ovf);
-                    else if constexpr (MODE == 1) atomicAdd(&s_bacc[q * 8 + type], (unsigned long long)n);
-                    else atomicAdd(acc + 8 * (c * 32 + o) + type, (unsigned long long)n);
+                    else if constexpr (MODE == 1) shared_add(&s_bacc[q * 8 + type], n, ovf);
+                    else atomicAdd(out + 8 * (lc * 32 + o) + type, (unsigned long long)n);
                 };
-                if (a_first) light_pair(k, C, Q, true, ra, rb, pa, pb, dA, dB, accq);
-                else light_pair(k, C, Q, false, rb, ra, pb, pa, dA, dB, accq);
+                if (a_first) light_pair(C, f, Q, true, ra, rb, pa, pb, dA, dB, accq);
+                else light_pair(C, f, Q, false, rb, ra, pb, pa, dA, dB, accq);
             }
         }
         __syncwarp();
     }
-    if constexpr (MODE == 0) flush_block(s_acc, LIGHT_THREADS, acc, ovf);
-    if constexpr (MODE == 1) {
-        __syncthreads();
-        for (uint32_t i = threadIdx.x; i < nq * 8; i += blockDim.x)
-            if (s_bacc[i]) atomicAdd(acc + i, s_bacc[i]);
+    if constexpr (MODE == 0) {
+        if (cur_g != 0xffffffffu) warp_flush(s_acc, out + 8 * cur_g, flag, ovf);
+    }
+    if constexpr (MODE == 1) block_flush(s_bacc, nq * 8, out, flag, ovf);
+}
+
+// ---------------------------------------------------------------- heavy: per-edge math
+// Phase 1 for an enumerated edge e (key ke): the values h, L, R, M against C,
+// each split by C's direction: out[2 s + dC].
+__device__ __forceinline__ void phase1_values(const GList &C, const KeyFmt &f, const Query &q, int64_t ke,
+                                              uint32_t out[8]) {
+    const int64_t re = ke >> f.shift;
+    const uint32_t ph = cnt_le(C, f, re + q.d13);
+    const uint32_t pl = cnt_key(C, ke);
+    const uint32_t pr = cnt_lt(C, f, re - q.d23);
+    const uint32_t pm = cnt_lt(C, f, re - q.d13);
+    const uint32_t h0 = C.d0(ph), l0 = C.d0(pl), r0 = C.d0(pr), m0 = C.d0(pm);
+    out[0] = h0; out[1] = ph - h0;
+    out[2] = l0; out[3] = pl - l0;
+    out[4] = r0; out[5] = pr - r0;
+    out[6] = m0; out[7] = pm - m0;
+}
+
+// Phase 2 for an enumerated edge e with O the other enumerated list.
+// pref(dO, s, c) = prefix over O's own-direction-dO edges, first c of them,
+// of phase-1 slot s.  add(dO, dC, pi if e is on A, pi if e is on B, n).
+template <typename OL, typename PF, typename ADD>
+__device__ __forceinline__ void phase2_edge(const OL &O, const GList &C, const KeyFmt &f, const Query &q, int64_t ke,
+                                            PF &&pref, ADD &&add) {
+    const int64_t re = ke >> f.shift;
+    // searches in C (split by C's direction)
+    const uint32_t posC = cnt_key(C, ke);
+    const uint32_t K0 = C.d0(posC);
+    const uint32_t pH = cnt_le(C, f, re + q.d23);
+    const uint32_t H0 = C.d0(pH);
+    const uint32_t pG = cnt_le(C, f, re + q.d12);
+    const uint32_t G0 = C.d0(pG);
+    const uint32_t pLo = cnt_lt(C, f, re - q.d12);
+    const uint32_t Lo0 = C.d0(pLo);
+    const uint32_t Kd[2] = {K0, posC - K0}, Hd[2] = {H0, pH - H0}, Gd[2] = {G0, pG - G0},
+                   Lod[2] = {Lo0, pLo - Lo0};
+    // searches in O (merged positions)
+    const uint32_t posO = cnt_key(O, ke);
+    const uint32_t o_lo = min(cnt_lt(O, f, re - q.d12), posO);
+    const uint32_t o_mid = min(max(cnt_le(O, f, re + q.d23 - q.d13), o_lo), posO);
+    const uint32_t r1 = max(cnt_le(O, f, re + min(q.d12, q.d23)), posO);
+    const uint32_t r2 = max(cnt_le(O, f, re + max(q.d12, q.d23)), r1);
+    const uint32_t r3 = max(cnt_le(O, f, re + q.d13), r2);
+    const uint32_t sp = max(cnt_le(O, f, re + q.d13 - q.d12), posO);
+    const uint32_t en = max(cnt_le(O, f, re + q.d23), sp);
+    const uint32_t pos[8] = {o_lo, o_mid, posO, r1, r2, r3, sp, en};
+    uint32_t d0s[8];
+#pragma unroll
+    for (int i = 0; i < 8; i++) d0s[i] = O.d0(pos[i]);
+#pragma unroll
+    for (uint32_t dO = 0; dO < 2; dO++) {
+        // own-direction-dO ranks of the merged positions in O
+        uint32_t c[8];
+#pragma unroll
+        for (int i = 0; i < 8; i++) c[i] = dO ? pos[i] - d0s[i] : d0s[i];
+        const uint32_t c_lo = c[0], c_mid = c[1], c_pos = c[2], c_r1 = c[3], c_r2 = c[4], c_r3 = c[5], c_sp = c[6],
+                       c_en = c[7];
+#pragma unroll
+        for (uint32_t dC = 0; dC < 2; dC++) {
+            // (1) e second, O's edge first, C third: Alg. 2 (pi_2 if e is on A, pi_1 if on B)
+            {
+                const unsigned long long hsum = pref(dO, 0 + dC, c_mid) - pref(dO, 0 + dC, c_lo);
+                const unsigned long long n = hsum + (unsigned long long)Hd[dC] * (c_pos - c_mid) -
+                                             (unsigned long long)Kd[dC] * (c_pos - c_lo);
+                add(dO, dC, PI2, PI1, n);
+            }
+            // (2) e first, C second, O's edge third: Alg. 3 (pi_3 / pi_4)
+            {
+                unsigned long long n = pref(dO, 2 + dC, c_r1) - pref(dO, 2 + dC, c_pos) -
+                                       (unsigned long long)Kd[dC] * (c_r1 - c_pos);
+                if (q.d12 <= q.d23) {
+                    n += (unsigned long long)(Gd[dC] - Kd[dC]) * (c_r2 - c_r1);
+                } else {
+                    n += (pref(dO, 2 + dC, c_r2) - pref(dO, 2 + dC, c_r1)) -
+                         (pref(dO, 4 + dC, c_r2) - pref(dO, 4 + dC, c_r1));
+                }
+                n += (unsigned long long)Gd[dC] * (c_r3 - c_r2) - (pref(dO, 4 + dC, c_r3) - pref(dO, 4 + dC, c_r2));
+                add(dO, dC, PI3, PI4, n);
+            }
+            // (3) C first, e second, O's edge third: Alg. 4 (pi_5 / pi_6)
+            {
+                unsigned long long n = (unsigned long long)(Kd[dC] - Lod[dC]) * (c_sp - c_pos);
+                n += (unsigned long long)Kd[dC] * (c_en - c_sp) - (pref(dO, 6 + dC, c_en) - pref(dO, 6 + dC, c_sp));
+                add(dO, dC, PI5, PI6, n);
+            }
+        }
     }
 }
 
-// Vertex triple (u, v, w) of each sampled record: A = {u, v}, B = {u, w}.
-__global__ void record_vertices_kernel(const uint4 *tri, const uint2 *pv, const uint64_t *idx, uint64_t count,
-                                       uint32_t *out) {
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint4 r = tri[idx[i]];
-        const uint2 a = pv[r.x], b = pv[r.y];
-        const uint32_t u = (a.x == b.x || a.x == b.y) ? a.x : a.y;
-        out[3 * i] = u;
-        out[3 * i + 1] = a.x == u ? a.y : a.x;
-        out[3 * i + 2] = b.x == u ? b.y : b.x;
-    }
-}
-
-__global__ void gather_records_kernel(const uint4 *tri, const uint64_t *idx, uint64_t count, const uint32_t *poff,
-                                      uint4 *out, uint64_t *sizes) {
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint4 r = tri[idx[i]];
-        out[i] = r;
-        sizes[i] = (poff[r.x + 1] - poff[r.x]) + (poff[r.y + 1] - poff[r.y]);
-    }
-}
-
-// ---------------------------------------------------------------- heavy bin
+// ---------------------------------------------------------------- heavy: fused CTA kernel
 constexpr int HEAVY_THREADS = 256;
+constexpr int HEAVY_WARPS = HEAVY_THREADS / 32;
+constexpr uint32_t MAX_BATCH_SMEM_Q = 256;
 
-struct HeavyArgs {
-    KeyCtx k;
-    const uint32_t *__restrict__ poff;
-    const uint4 *__restrict__ tri;      // heavy records
-    const uint64_t *__restrict__ eoff;  // [nh + 1]
-    uint64_t nh, total;
-    void *pre;                          // prefix entries: 8 values each
-    // sample mode: per-record output slots (nullptr otherwise)
-    unsigned long long *per_tri;
+template <typename P>
+struct FusedCap {
+    static constexpr uint32_t CAP = sizeof(P) == 4 ? 2048 : 1024;  // edges of A plus B
+    static constexpr uint32_t ES = CAP + 4;                         // prefix entries per slot
+    static constexpr size_t KEYS = (size_t)CAP * 8;
+    static constexpr size_t D0 = ((size_t)CAP + 8) * 4;
+    static constexpr size_t PRE = 8 * (size_t)ES * sizeof(P);
+    static constexpr size_t bytes(int mode, uint32_t nq) {
+        return KEYS + D0 + PRE + (mode == 1 ? (size_t)nq * 64 : mode == 0 ? 8 * 256 * 8 : 0);
+    }
 };
 
-// Locates enumerated element g: its triangle h and index j in A ++ B.
-__device__ __forceinline__ uint64_t find_tri(const uint64_t *__restrict__ eoff, uint64_t nh, uint64_t g) {
-    uint64_t lo = 0, hi = nh;  // last h with eoff[h] <= g
+__device__ __forceinline__ uint32_t block_excl_scan_u32(uint32_t v, uint32_t *tmp) {
+    // tmp: HEAVY_WARPS + 1 words of shared memory; tmp[HEAVY_WARPS] = total
+    const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= (uint32_t)o) x += y;
+    }
+    if (lane == 31) tmp[w] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int i = 0; i < HEAVY_WARPS; i++) {
+            const uint32_t t = tmp[i];
+            tmp[i] = run;
+            run += t;
+        }
+        tmp[HEAVY_WARPS] = run;
+    }
+    __syncthreads();
+    return tmp[w] + x - v;
+}
+
+// One CTA per heavy triangle of the CTA class, over a table of graphs.  MODE
+// as light_kernel; heavy_pre[g] = first CTA-class record of graph g in the
+// global index space (G + 1 entries).
+template <typename P, int MODE>
+__global__ void __launch_bounds__(HEAVY_THREADS)
+    heavy_fused_kernel(const GraphView *__restrict__ gvs, const uint64_t *__restrict__ heavy_pre, uint32_t G,
+                       const int64_t *dq, uint32_t nq, unsigned long long *out, unsigned long long *flag,
+                       const uint64_t *idx, uint64_t nidx) {
+    using Cap = FusedCap<P>;
+    constexpr uint32_t CAP = Cap::CAP, ES = Cap::ES;
+    extern __shared__ __align__(16) unsigned char smem[];
+    int64_t *s_key = reinterpret_cast<int64_t *>(smem);
+    uint32_t *s_d0 = reinterpret_cast<uint32_t *>(smem + Cap::KEYS);
+    P *s_pre = reinterpret_cast<P *>(smem + Cap::KEYS + Cap::D0);
+    unsigned long long *s_tail = reinterpret_cast<unsigned long long *>(smem + Cap::KEYS + Cap::D0 + Cap::PRE);
+    auto s_acc = reinterpret_cast<unsigned long long (*)[256]>(s_tail);  // MODE 0
+    __shared__ uint32_t s_tmp[HEAVY_WARPS + 1];
+    if constexpr (MODE == 0) {
+#pragma unroll
+        for (int j = 0; j < 8; j++) s_acc[j][threadIdx.x] = 0;
+    }
+    if constexpr (MODE == 1) {
+        for (uint32_t i = threadIdx.x; i < nq * 8; i += blockDim.x) s_tail[i] = 0;
+    }
+    __syncthreads();
+    unsigned ovf = 0;
+    uint32_t cur_g = 0xffffffffu;
+    const uint64_t nitems = MODE == 2 ? nidx : __ldg(heavy_pre + G);
+    for (uint64_t h = blockIdx.x; h < nitems; h += gridDim.x) {
+        const uint32_t g = MODE == 0 ? graph_of(heavy_pre, G, h) : 0u;
+        if constexpr (MODE == 0) {
+            if (g != cur_g) {
+                if (cur_g != 0xffffffffu) warp_flush(s_acc, out + 8 * cur_g, flag, ovf);
+                cur_g = g;
+            }
+        }
+        const GraphView &gv = gvs[g];
+        const KeyFmt f{gv.shift, gv.span};
+        const uint64_t hl = MODE == 2 ? idx[h] : (MODE == 0 ? h - __ldg(heavy_pre + g) : h);
+        const uint4 r = __ldg(gv.tri + gv.n_light + gv.n_hwarp + hl);
+        const GList A = glist(gv, r.x, r.w & TriRec::FLIP_A);
+        const GList B = glist(gv, r.y, (r.w & TriRec::FLIP_B) ? 1u : 0u);
+        const GList C = glist(gv, r.z, (r.w & TriRec::FLIP_C) ? 1u : 0u);
+        const uint32_t na = A.n, nb = B.n, ne = na + nb;
+        // block-uniform skips: lists beyond this kernel's capacity (never, by
+        // the load-time partition), or a graph served by the other width
+        if (ne > CAP || (sizeof(P) == 8) != (gv.wide != 0)) continue;
+        // stage A ++ B and the effective direction-0 prefix over it
+        const uint32_t per = (ne + HEAVY_THREADS - 1) / HEAVY_THREADS;
+        const uint32_t beg = min(ne, threadIdx.x * per), end = min(ne, beg + per);
+        uint32_t cnt0 = 0;
+        for (uint32_t i = beg; i < end; i++) {
+            const int64_t k = i < na ? __ldg(A.key + A.b + i) : __ldg(B.key + B.b + (i - na));
+            s_key[i] = k;
+            cnt0 += ((uint32_t)(k & 1) ^ (i < na ? A.flip : B.flip)) == 0;
+        }
+        uint32_t run = block_excl_scan_u32(cnt0, s_tmp);
+        for (uint32_t i = beg; i < end; i++) {
+            s_d0[i] = run;
+            run += ((uint32_t)(s_key[i] & 1) ^ (i < na ? A.flip : B.flip)) == 0;
+        }
+        if (threadIdx.x == 0) s_d0[ne] = s_tmp[HEAVY_WARPS];
+        __syncthreads();
+        const uint32_t a0 = s_d0[na], b0 = s_d0[ne] - a0;
+        // first prefix entry of each own-direction segment: A0, A1, B0, B1
+        const uint32_t sbase[4] = {0, a0 + 1, na + 2, na + 2 + b0 + 1};
+        const uint32_t slen[4] = {a0, na - a0, b0, nb - b0};
+        for (uint32_t q = 0; q < (MODE == 1 ? nq : 1u); q++) {
+            const Query Q = load_query(dq, MODE == 0 ? g : q);
+            // phase 1 (and the zero entry of each segment)
+            if (threadIdx.x < 32) s_pre[(threadIdx.x >> 2) * ES + sbase[threadIdx.x & 3]] = 0;
+            for (uint32_t e = threadIdx.x; e < ne; e += HEAVY_THREADS) {
+                const uint32_t z = e >= na;
+                const uint32_t j = z ? e - na : e;
+                const int64_t ke = s_key[e];
+                const uint32_t de = (uint32_t)(ke & 1) ^ (z ? B.flip : A.flip);
+                const uint32_t dz0 = z ? s_d0[e] - a0 : s_d0[e];
+                const uint32_t rank = de ? j - dz0 : dz0;
+                uint32_t v[8];
+                phase1_values(C, f, Q, ke, v);
+                const uint32_t at = sbase[2 * z + de] + rank + 1;
+#pragma unroll
+                for (int s = 0; s < 8; s++) s_pre[s * ES + at] = v[s];
+            }
+            __syncthreads();
+            // inclusive scans: 4 segments x 8 slots, one warp per (segment, slot)
+            for (uint32_t p = threadIdx.x >> 5; p < 32; p += HEAVY_WARPS) {
+                const uint32_t seg = p & 3, s = p >> 2, lane = threadIdx.x & 31;
+                P *base = s_pre + s * ES + sbase[seg] + 1;
+                P carry = 0;
+                for (uint32_t c0 = 0; c0 < slen[seg]; c0 += 32) {
+                    const uint32_t i = c0 + lane;
+                    P x = i < slen[seg] ? base[i] : P(0);
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const P y = __shfl_up_sync(0xffffffffu, x, o);
+                        if (lane >= (uint32_t)o) x += y;
+                    }
+                    x += carry;
+                    if (i < slen[seg]) base[i] = x;
+                    carry = __shfl_sync(0xffffffffu, x, 31);
+                }
+            }
+            __syncthreads();
+            // phase 2
+            for (uint32_t e = threadIdx.x; e < ne; e += HEAVY_THREADS) {
+                const uint32_t z = e >= na;
+                const int64_t ke = s_key[e];
+                const uint32_t de = (uint32_t)(ke & 1) ^ (z ? B.flip : A.flip);
+                // O = the other list, staged: keys and its own dir-0 prefix
+                const SList O = z ? SList{s_key, s_d0, na, 0u} : SList{s_key + na, s_d0 + na, nb, a0};
+                const uint32_t oz = 1 - z;
+                auto pref = [&](uint32_t dO, int s, uint32_t c) -> unsigned long long {
+                    return (unsigned long long)s_pre[s * ES + sbase[2 * oz + dO] + c];
+                };
+                auto add = [&](uint32_t dO, uint32_t dC, int pia, int pib, unsigned long long n) {
+                    if (!n) return;
+                    const uint32_t dA = z ? dO : de, dB = z ? de : dO;
+                    const int type = type_of(z ? pib : pia, dA, dB, dC);
+                    if constexpr (MODE == 0) add_checked(s_acc[type][threadIdx.x], n, ovf);
+                    else if constexpr (MODE == 1) shared_add(&s_tail[q * 8 + type], n, ovf);
+                    else atomicAdd(out + 8 * h + type, n);
+                };
+                phase2_edge(O, C, f, Q, ke, pref, add);
+            }
+            __syncthreads();
+        }
+    }
+    if constexpr (MODE == 0) {
+        if (cur_g != 0xffffffffu) warp_flush(s_acc, out + 8 * cur_g, flag, ovf);
+    }
+    if constexpr (MODE == 1) block_flush(s_tail, nq * 8, out, flag, ovf);
+}
+
+// ---------------------------------------------------------------- heavy: one warp per triangle
+// Heavy triangles with at most WCAP edges in A plus B: the same two phases
+// as the CTA kernel, but each warp owns one triangle (and its slice of
+// shared memory), so many small heavy triangles run side by side.
+template <typename P>
+struct WarpCap {
+    static constexpr uint32_t CAP = sizeof(P) == 4 ? 128 : 64;
+    static constexpr uint32_t ES = CAP + 4;
+    static constexpr size_t KEYS = (size_t)CAP * 8;
+    static constexpr size_t D0 = ((size_t)CAP + 8) * 4;
+    static constexpr size_t PRE = 8 * (size_t)ES * sizeof(P);
+    static constexpr size_t PER_WARP = KEYS + D0 + PRE;
+    static constexpr size_t bytes(int mode, uint32_t nq) {
+        return HEAVY_WARPS * PER_WARP + (mode == 1 ? (size_t)nq * 64 : mode == 0 ? 8 * 256 * 8 : 0);
+    }
+};
+
+template <typename P, int MODE>
+__global__ void __launch_bounds__(HEAVY_THREADS)
+    heavy_warp_kernel(const GraphView *__restrict__ gvs, const uint64_t *__restrict__ hw_pre, uint32_t G,
+                      const int64_t *dq, uint32_t nq, unsigned long long *out, unsigned long long *flag,
+                      const uint64_t *idx, uint64_t nidx) {
+    using Cap = WarpCap<P>;
+    constexpr uint32_t ES = Cap::ES;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned char *mine = smem + w * Cap::PER_WARP;
+    int64_t *s_key = reinterpret_cast<int64_t *>(mine);
+    uint32_t *s_d0 = reinterpret_cast<uint32_t *>(mine + Cap::KEYS);
+    P *s_pre = reinterpret_cast<P *>(mine + Cap::KEYS + Cap::D0);
+    unsigned long long *s_tail = reinterpret_cast<unsigned long long *>(smem + HEAVY_WARPS * Cap::PER_WARP);
+    auto s_acc = reinterpret_cast<unsigned long long (*)[256]>(s_tail);  // MODE 0
+    if constexpr (MODE == 0) {
+#pragma unroll
+        for (int j = 0; j < 8; j++) s_acc[j][threadIdx.x] = 0;
+    }
+    if constexpr (MODE == 1) {
+        for (uint32_t i = threadIdx.x; i < nq * 8; i += blockDim.x) s_tail[i] = 0;
+        __syncthreads();
+    }
+    unsigned ovf = 0;
+    uint32_t cur_g = 0xffffffffu;
+    const uint64_t nitems = MODE == 2 ? nidx : __ldg(hw_pre + G);
+    const uint64_t gw = (uint64_t)blockIdx.x * HEAVY_WARPS + w, nw = (uint64_t)gridDim.x * HEAVY_WARPS;
+    for (uint64_t h = gw; h < nitems; h += nw) {
+        const uint32_t g = MODE == 0 ? graph_of(hw_pre, G, h) : 0u;
+        if constexpr (MODE == 0) {
+            if (g != cur_g) {
+                if (cur_g != 0xffffffffu) warp_flush(s_acc, out + 8 * cur_g, flag, ovf);
+                cur_g = g;
+            }
+        }
+        const GraphView &gv = gvs[g];
+        if ((sizeof(P) == 8) != (gv.wide != 0)) continue;  // the other width's launch takes it
+        const KeyFmt f{gv.shift, gv.span};
+        const uint64_t hl = MODE == 2 ? idx[h] : (MODE == 0 ? h - __ldg(hw_pre + g) : h);
+        const uint4 r = __ldg(gv.tri + gv.n_light + hl);
+        const GList A = glist(gv, r.x, r.w & TriRec::FLIP_A);
+        const GList B = glist(gv, r.y, (r.w & TriRec::FLIP_B) ? 1u : 0u);
+        const GList C = glist(gv, r.z, (r.w & TriRec::FLIP_C) ? 1u : 0u);
+        const uint32_t na = A.n, nb = B.n, ne = na + nb;
+        // stage A ++ B and the effective direction-0 prefix over it
+        uint32_t carry = 0;
+        for (uint32_t c0 = 0; c0 < ne; c0 += 32) {
+            const uint32_t i = c0 + lane;
+            uint32_t is0 = 0;
+            if (i < ne) {
+                const int64_t k = i < na ? __ldg(A.key + A.b + i) : __ldg(B.key + B.b + (i - na));
+                s_key[i] = k;
+                is0 = ((uint32_t)(k & 1) ^ (i < na ? A.flip : B.flip)) == 0;
+            }
+            uint32_t x = is0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= (uint32_t)o) x += y;
+            }
+            if (i < ne) s_d0[i] = carry + x - is0;
+            carry += __shfl_sync(0xffffffffu, x, 31);
+        }
+        if (lane == 0) s_d0[ne] = carry;
+        __syncwarp();
+        const uint32_t a0 = s_d0[na], b0 = carry - a0;
+        const uint32_t sbase[4] = {0, a0 + 1, na + 2, na + 2 + b0 + 1};
+        const uint32_t slen[4] = {a0, na - a0, b0, nb - b0};
+        for (uint32_t q = 0; q < (MODE == 1 ? nq : 1u); q++) {
+            const Query Q = load_query(dq, MODE == 0 ? g : q);
+            // phase 1 (and the zero entry of each segment)
+            s_pre[(lane >> 2) * ES + sbase[lane & 3]] = 0;
+            for (uint32_t e = lane; e < ne; e += 32) {
+                const uint32_t z = e >= na;
+                const uint32_t j = z ? e - na : e;
+                const int64_t ke = s_key[e];
+                const uint32_t de = (uint32_t)(ke & 1) ^ (z ? B.flip : A.flip);
+                const uint32_t dz0 = z ? s_d0[e] - a0 : s_d0[e];
+                const uint32_t rank = de ? j - dz0 : dz0;
+                uint32_t v[8];
+                phase1_values(C, f, Q, ke, v);
+                const uint32_t at = sbase[2 * z + de] + rank + 1;
+#pragma unroll
+                for (int s = 0; s < 8; s++) s_pre[s * ES + at] = v[s];
+            }
+            __syncwarp();
+            {  // inclusive scans: lane p scans (segment p & 3, slot p >> 2)
+                const uint32_t seg = lane & 3, s = lane >> 2;
+                P *base = s_pre + s * ES + sbase[seg] + 1;
+                P run = 0;
+                for (uint32_t i = 0; i < slen[seg]; i++) {
+                    run += base[i];
+                    base[i] = run;
+                }
+            }
+            __syncwarp();
+            // phase 2
+            for (uint32_t e = lane; e < ne; e += 32) {
+                const uint32_t z = e >= na;
+                const int64_t ke = s_key[e];
+                const uint32_t de = (uint32_t)(ke & 1) ^ (z ? B.flip : A.flip);
+                const SList O = z ? SList{s_key, s_d0, na, 0u} : SList{s_key + na, s_d0 + na, nb, a0};
+                const uint32_t oz = 1 - z;
+                auto pref = [&](uint32_t dO, int s, uint32_t c) -> unsigned long long {
+                    return (unsigned long long)s_pre[s * ES + sbase[2 * oz + dO] + c];
+                };
+                auto add = [&](uint32_t dO, uint32_t dC, int pia, int pib, unsigned long long n) {
+                    if (!n) return;
+                    const uint32_t dA = z ? dO : de, dB = z ? de : dO;
+                    const int type = type_of(z ? pib : pia, dA, dB, dC);
+                    if constexpr (MODE == 0) add_checked(s_acc[type][threadIdx.x], n, ovf);
+                    else if constexpr (MODE == 1) shared_add(&s_tail[q * 8 + type], n, ovf);
+                    else atomicAdd(out + 8 * h + type, n);
+                };
+                phase2_edge(O, C, f, Q, ke, pref, add);
+            }
+            __syncwarp();
+        }
+    }
+    if constexpr (MODE == 0) {
+        if (cur_g != 0xffffffffu) warp_flush(s_acc, out + 8 * cur_g, flag, ovf);
+    }
+    if constexpr (MODE == 1) block_flush(s_tail, nq * 8, out, flag, ovf);
+}
+
+// ---------------------------------------------------------------- huge: flat path
+struct HugeArgs {
+    GraphView gv;
+    const uint4 *__restrict__ tri;      // huge records
+    const uint64_t *__restrict__ eoff;  // [nh + 1] enumerated-edge offsets
+    uint64_t nh, total;
+    void *pre;                          // prefix entries: 8 values each
+    unsigned long long *per_tri;        // sample mode: per-record outputs
+};
+
+// Locates enumerated edge e: the last triangle h with eoff[h] <= e.
+__device__ __forceinline__ uint64_t find_tri(const uint64_t *__restrict__ eoff, uint64_t nh, uint64_t e) {
+    uint64_t lo = 0, hi = nh;
     while (hi - lo > 1) {
         const uint64_t mid = (lo + hi) >> 1;
-        if (__ldg(eoff + mid) <= g) lo = mid; else hi = mid;
+        if (__ldg(eoff + mid) <= e) lo = mid; else hi = mid;
     }
     return lo;
 }
 
-struct HeavyTri {
-    List A, B, C;
+struct HugeTri {
+    GList A, B, C;
     uint32_t a0, b0;  // effective direction-0 counts of A and B
     uint64_t base;    // first prefix entry of this triangle
 };
 
-__device__ __forceinline__ HeavyTri heavy_tri(const HeavyArgs &a, uint64_t h) {
+__device__ __forceinline__ HugeTri huge_tri(const HugeArgs &a, uint64_t h) {
     const uint4 r = __ldg(a.tri + h);
-    HeavyTri t;
-    t.A = make_list(a.poff, r.x, r.w & TriRec::FLIP_A);
-    t.B = make_list(a.poff, r.y, (r.w & TriRec::FLIP_B) ? 1u : 0u);
-    t.C = make_list(a.poff, r.z, (r.w & TriRec::FLIP_C) ? 1u : 0u);
-    t.a0 = dir0(a.k, t.A, t.A.n);
-    t.b0 = dir0(a.k, t.B, t.B.n);
+    HugeTri t;
+    t.A = glist(a.gv, r.x, r.w & TriRec::FLIP_A);
+    t.B = glist(a.gv, r.y, (r.w & TriRec::FLIP_B) ? 1u : 0u);
+    t.C = glist(a.gv, r.z, (r.w & TriRec::FLIP_C) ? 1u : 0u);
+    t.a0 = t.A.d0(t.A.n);
+    t.b0 = t.B.d0(t.B.n);
     t.base = __ldg(a.eoff + h) + 4 * h;
     return t;
 }
 
 // first prefix entry of the own-direction-d segment of list Z (0 = A, 1 = B)
-__device__ __forceinline__ uint64_t seg_base(const HeavyTri &t, int z, uint32_t d) {
+__device__ __forceinline__ uint64_t seg_base(const HugeTri &t, uint32_t z, uint32_t d) {
     uint64_t b = t.base;
     if (z) b += t.A.n + 2;
     const uint32_t n0 = z ? t.b0 : t.a0;
@@ -377,49 +824,43 @@ __device__ __forceinline__ uint64_t seg_base(const HeavyTri &t, int z, uint32_t 
 }
 
 template <typename P>
-__global__ void __launch_bounds__(HEAVY_THREADS) heavy_phase1(HeavyArgs a, const int64_t *dq) {
+__global__ void __launch_bounds__(HEAVY_THREADS) huge_phase1(HugeArgs a, const int64_t *dq) {
     const Query q = load_query(dq, 0);
+    const KeyFmt f{a.gv.shift, a.gv.span};
     P *pre = static_cast<P *>(a.pre);
-    for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < a.total;
-         g += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t h = find_tri(a.eoff, a.nh, g);
-        const HeavyTri t = heavy_tri(a, h);
-        uint32_t j = (uint32_t)(g - __ldg(a.eoff + h));
-        const int z = j >= t.A.n;
-        const List &Z = z ? t.B : t.A;
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < a.total;
+         e += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t h = find_tri(a.eoff, a.nh, e);
+        const HugeTri t = huge_tri(a, h);
+        uint32_t j = (uint32_t)(e - __ldg(a.eoff + h));
+        const uint32_t z = j >= t.A.n;
+        const GList &Z = z ? t.B : t.A;
         if (z) j -= t.A.n;
-        const int64_t ke = __ldg(a.k.key + Z.b + j);
-        const int64_t re = ke >> a.k.shift;
+        const int64_t ke = __ldg(Z.key + Z.b + j);
         const uint32_t d = (uint32_t)(ke & 1) ^ Z.flip;
-        const uint32_t z0 = dir0(a.k, Z, j);
+        const uint32_t z0 = Z.d0(j);
         const uint32_t rank = d ? j - z0 : z0;
-        const uint32_t ph = cnt_le(a.k, t.C, re + q.d13);
-        const uint32_t pl = cnt_key(a.k, t.C, ke);
-        const uint32_t pr = cnt_lt(a.k, t.C, re - q.d23);
-        const uint32_t pm = cnt_lt(a.k, t.C, re - q.d13);
-        const uint32_t h0 = dir0(a.k, t.C, ph), l0 = dir0(a.k, t.C, pl), r0 = dir0(a.k, t.C, pr),
-                       m0 = dir0(a.k, t.C, pm);
-        P *e = pre + 8 * (seg_base(t, z, d) + rank + 1);
-        e[0] = h0; e[1] = ph - h0;
-        e[2] = l0; e[3] = pl - l0;
-        e[4] = r0; e[5] = pr - r0;
-        e[6] = m0; e[7] = pm - m0;
+        uint32_t v[8];
+        phase1_values(t.C, f, q, ke, v);
+        P *o = pre + 8 * (seg_base(t, z, d) + rank + 1);
+#pragma unroll
+        for (int s = 0; s < 8; s++) o[s] = v[s];
     }
 }
 
 // Inclusive scan of each own-direction segment (entry 0 of a segment is 0).
-// One warp per segment; 4 segments per heavy triangle.
+// One warp per segment; 4 segments per huge triangle.
 template <typename P>
-__global__ void __launch_bounds__(HEAVY_THREADS) heavy_scan(HeavyArgs a) {
+__global__ void __launch_bounds__(HEAVY_THREADS) huge_scan(HugeArgs a) {
     P *pre = static_cast<P *>(a.pre);
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
     for (uint64_t sidx = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); sidx < 4 * a.nh;
          sidx += warps) {
         const uint64_t h = sidx >> 2;
-        const int z = (int)((sidx >> 1) & 1);
+        const uint32_t z = (uint32_t)((sidx >> 1) & 1);
         const uint32_t d = (uint32_t)(sidx & 1);
-        const HeavyTri t = heavy_tri(a, h);
+        const HugeTri t = huge_tri(a, h);
         const uint32_t nz = z ? t.B.n : t.A.n, n0 = z ? t.b0 : t.a0;
         const uint32_t len = d ? nz - n0 : n0;
         P *seg = pre + 8 * seg_base(t, z, d);
@@ -450,230 +891,259 @@ __global__ void __launch_bounds__(HEAVY_THREADS) heavy_scan(HeavyArgs a) {
     }
 }
 
-// Prefix of slot s over the own-direction-d segment of Z, first `cnt` entries.
 template <typename P>
-__device__ __forceinline__ unsigned long long pref(const P *pre, uint64_t sb, uint32_t cnt, int s) {
-    return (unsigned long long)pre[8 * (sb + cnt) + s];
-}
-
-template <typename P>
-__global__ void __launch_bounds__(HEAVY_THREADS) heavy_phase2(HeavyArgs a, const int64_t *dq, unsigned long long *acc) {
+__global__ void __launch_bounds__(HEAVY_THREADS)
+    huge_phase2(HugeArgs a, const int64_t *dq, unsigned long long *out, unsigned long long *flag) {
     __shared__ unsigned long long s_acc[8][256];
 #pragma unroll
     for (int j = 0; j < 8; j++) s_acc[j][threadIdx.x] = 0;
     unsigned ovf = 0;
     const Query q = load_query(dq, 0);
+    const KeyFmt f{a.gv.shift, a.gv.span};
     const P *pre = static_cast<const P *>(a.pre);
-    const KeyCtx &k = a.k;
-    for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < a.total;
-         g += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t h = find_tri(a.eoff, a.nh, g);
-        const HeavyTri t = heavy_tri(a, h);
-        uint32_t j = (uint32_t)(g - __ldg(a.eoff + h));
-        const int z = j >= t.A.n;  // this edge's list Z (0 = A, 1 = B); O is the other
+    const uint64_t iters = (a.total + (uint64_t)gridDim.x * blockDim.x - 1) / ((uint64_t)gridDim.x * blockDim.x);
+    for (uint64_t it = 0; it < iters; it++) {  // uniform trip count (warp_flush needs full warps)
+        const uint64_t e = (it * gridDim.x + blockIdx.x) * (uint64_t)blockDim.x + threadIdx.x;
+        if (e >= a.total) continue;
+        const uint64_t h = find_tri(a.eoff, a.nh, e);
+        const HugeTri t = huge_tri(a, h);
+        uint32_t j = (uint32_t)(e - __ldg(a.eoff + h));
+        const uint32_t z = j >= t.A.n;  // this edge's list Z (0 = A, 1 = B); O is the other
         if (z) j -= t.A.n;
-        const List &Z = z ? t.B : t.A;
-        const List &O = z ? t.A : t.B;
-        const int oz = 1 - z;
-        const int64_t ke = __ldg(k.key + Z.b + j);
-        const int64_t re = ke >> k.shift;
+        const GList &Z = z ? t.B : t.A;
+        const GList &O = z ? t.A : t.B;
+        const uint32_t oz = 1 - z;
+        const int64_t ke = __ldg(Z.key + Z.b + j);
         const uint32_t de = (uint32_t)(ke & 1) ^ Z.flip;
         unsigned long long *pt = a.per_tri ? a.per_tri + 8 * h : nullptr;
-        auto add = [&](uint32_t dO, uint32_t dC, int pi_if_z_is_a, int pi_if_z_is_b, unsigned long long n) {
+        auto pref = [&](uint32_t dO, int s, uint32_t c) -> unsigned long long {
+            return (unsigned long long)pre[8 * (seg_base(t, oz, dO) + c) + s];
+        };
+        auto add = [&](uint32_t dO, uint32_t dC, int pia, int pib, unsigned long long n) {
             if (!n) return;
             const uint32_t dA = z ? dO : de, dB = z ? de : dO;
-            const int type = type_of(z ? pi_if_z_is_b : pi_if_z_is_a, dA, dB, dC);
+            const int type = type_of(z ? pib : pia, dA, dB, dC);
             if (pt) atomicAdd(pt + type, n);
             else add_checked(s_acc[type][threadIdx.x], n, ovf);
         };
-        // searches in C (split by C's direction)
-        const uint32_t posC = cnt_key(k, t.C, ke);
-        const uint32_t K0 = dir0(k, t.C, posC), K1 = posC - K0;
-        const uint32_t pH = cnt_le(k, t.C, re + q.d23);
-        const uint32_t H0 = dir0(k, t.C, pH), H1 = pH - H0;
-        const uint32_t pG = cnt_le(k, t.C, re + q.d12);
-        const uint32_t G0 = dir0(k, t.C, pG), G1 = pG - G0;
-        const uint32_t pLo = cnt_lt(k, t.C, re - q.d12);
-        const uint32_t Lo0 = dir0(k, t.C, pLo), Lo1 = pLo - Lo0;
-        const uint32_t Kd[2] = {K0, K1}, Hd[2] = {H0, H1}, Gd[2] = {G0, G1}, Lod[2] = {Lo0, Lo1};
-        // searches in O (merged positions)
-        const uint32_t posO = cnt_key(k, O, ke);
-        const uint32_t o_lo = min(cnt_lt(k, O, re - q.d12), posO);
-        const uint32_t o_mid = min(max(cnt_le(k, O, re + q.d23 - q.d13), o_lo), posO);
-        const uint32_t r1 = max(cnt_le(k, O, re + min(q.d12, q.d23)), posO);
-        const uint32_t r2 = max(cnt_le(k, O, re + max(q.d12, q.d23)), r1);
-        const uint32_t r3 = max(cnt_le(k, O, re + q.d13), r2);
-        const uint32_t sp = max(cnt_le(k, O, re + q.d13 - q.d12), posO);
-        const uint32_t en = max(cnt_le(k, O, re + q.d23), sp);
-        const uint32_t pos[9] = {o_lo, o_mid, posO, r1, r2, r3, sp, en, 0};
-        for (uint32_t dO = 0; dO < 2; dO++) {
-            // own-direction-dO ranks of the merged positions in O
-            uint32_t c[8];
-#pragma unroll
-            for (int i = 0; i < 8; i++) {
-                const uint32_t d0 = dir0(k, O, pos[i]);
-                c[i] = dO ? pos[i] - d0 : d0;
-            }
-            const uint32_t c_lo = c[0], c_mid = c[1], c_pos = c[2], c_r1 = c[3], c_r2 = c[4], c_r3 = c[5],
-                           c_sp = c[6], c_en = c[7];
-            const uint64_t sb = seg_base(t, oz, dO);
-            for (uint32_t dC = 0; dC < 2; dC++) {
-                // (1) e second, O's edge first, C third: Alg. 2 (pi_1 / pi_2)
-                {
-                    const unsigned long long hsum = pref(pre, sb, c_mid, 0 + dC) - pref(pre, sb, c_lo, 0 + dC);
-                    const unsigned long long n = hsum + (unsigned long long)Hd[dC] * (c_pos - c_mid) -
-                                                 (unsigned long long)Kd[dC] * (c_pos - c_lo);
-                    add(dO, dC, PI2, PI1, n);
-                }
-                // (2) e first, C second, O's edge third: Alg. 3 (pi_3 / pi_4)
-                {
-                    const unsigned long long L_1 = pref(pre, sb, c_r1, 2 + dC) - pref(pre, sb, c_pos, 2 + dC);
-                    unsigned long long n = L_1 - (unsigned long long)Kd[dC] * (c_r1 - c_pos);
-                    if (q.d12 <= q.d23) {
-                        n += (unsigned long long)(Gd[dC] - Kd[dC]) * (c_r2 - c_r1);
-                    } else {
-                        n += (pref(pre, sb, c_r2, 2 + dC) - pref(pre, sb, c_r1, 2 + dC)) -
-                             (pref(pre, sb, c_r2, 4 + dC) - pref(pre, sb, c_r1, 4 + dC));
-                    }
-                    n += (unsigned long long)Gd[dC] * (c_r3 - c_r2) -
-                         (pref(pre, sb, c_r3, 4 + dC) - pref(pre, sb, c_r2, 4 + dC));
-                    add(dO, dC, PI3, PI4, n);
-                }
-                // (3) C first, e second, O's edge third: Alg. 4 (pi_5 / pi_6)
-                {
-                    unsigned long long n = (unsigned long long)(Kd[dC] - Lod[dC]) * (c_sp - c_pos);
-                    n += (unsigned long long)Kd[dC] * (c_en - c_sp) -
-                         (pref(pre, sb, c_en, 6 + dC) - pref(pre, sb, c_sp, 6 + dC));
-                    add(dO, dC, PI5, PI6, n);
-                }
-            }
-        }
+        phase2_edge(O, t.C, f, q, ke, pref, add);
     }
-    if (!a.per_tri) flush_block(s_acc, HEAVY_THREADS, acc, ovf);
+    if (!a.per_tri) warp_flush(s_acc, out, flag, ovf);
 }
 
 template <typename P>
-void run_heavy(ttc_graph *g, const HeavyArgs &ha, const int64_t *dq_one, unsigned long long *acc, cudaStream_t s) {
+void run_huge(ttc_graph *g, const HugeArgs &ha, const int64_t *dq_one, unsigned long long *out,
+              unsigned long long *flag, cudaStream_t s) {
+    if (!ha.nh) return;
     const unsigned grid = (unsigned)(sm_count() * 8);
-    prof_begin(g, s, "heavy_phase1");
-    heavy_phase1<P><<<grid, HEAVY_THREADS, 0, s>>>(ha, dq_one);
+    prof_begin(g, s, "huge_phase1");
+    huge_phase1<P><<<grid, HEAVY_THREADS, 0, s>>>(ha, dq_one);
     TTC_LAUNCH_CHECK();
     prof_end(g, s);
-    prof_begin(g, s, "heavy_scan");
-    heavy_scan<P><<<grid, HEAVY_THREADS, 0, s>>>(ha);
+    prof_begin(g, s, "huge_scan");
+    huge_scan<P><<<grid, HEAVY_THREADS, 0, s>>>(ha);
     TTC_LAUNCH_CHECK();
     prof_end(g, s);
-    prof_begin(g, s, "heavy_phase2");
-    heavy_phase2<P><<<grid, HEAVY_THREADS, 0, s>>>(ha, dq_one, acc);
+    prof_begin(g, s, "huge_phase2");
+    huge_phase2<P><<<grid, HEAVY_THREADS, 0, s>>>(ha, dq_one, out, flag);
     TTC_LAUNCH_CHECK();
     prof_end(g, s);
 }
 
-HeavyArgs heavy_args(ttc_graph *g, cudaStream_t s) {
-    HeavyArgs ha{};
-    ha.k = KeyCtx{g->key.get(), g->fwd.get(), g->shift, g->span};
-    ha.poff = g->poff.get();
-    ha.tri = g->tri.get() + g->st.tau_light;
-    ha.eoff = g->heavy_eoff.get();
-    ha.nh = g->st.tau_heavy;
-    ha.total = g->heavy_elems;
-    const size_t entries = (size_t)g->heavy_elems + 4 * (size_t)g->st.tau_heavy;
-    const size_t bytes = entries * 8 * (g->heavy_wide ? 8 : 4);
-    if (g->scratch.count < bytes) g->scratch.alloc(bytes, s);
-    ha.pre = g->scratch.get();
+HugeArgs huge_args(ttc_graph *g, void *scratch) {
+    HugeArgs ha{};
+    ha.gv = g->view_host;
+    ha.tri = g->tri.get() + g->st.tau_light + g->st.tau_hwarp + g->st.tau_hcta;
+    ha.eoff = g->huge_eoff.get();
+    ha.nh = g->st.tau_huge;
+    ha.total = g->huge_elems;
+    ha.pre = scratch;
     return ha;
 }
 
-constexpr int MAX_BATCH_SMEM_Q = 256;
-
-unsigned light_grid(uint64_t ntri) {
-    const uint64_t want = (ntri + LIGHT_THREADS - 1) / LIGHT_THREADS;
-    const uint64_t cap = (uint64_t)sm_count() * 8;
+// Persistent grids: at most `per_sm` CTAs per SM, never more than the work.
+unsigned light_grid(uint64_t chunks, int per_sm = 8) {
+    const uint64_t want = (chunks + LIGHT_WARPS - 1) / LIGHT_WARPS;
+    const uint64_t cap = (uint64_t)sm_count() * (uint64_t)per_sm;
     return (unsigned)(want < 1 ? 1 : want < cap ? want : cap);
 }
 
-LightArgs light_args(ttc_graph *g) {
-    LightArgs la{};
-    la.k = KeyCtx{g->key.get(), g->fwd.get(), g->shift, g->span};
-    la.poff = g->poff.get();
-    la.tri = g->tri.get();
-    la.ntri = g->st.tau_light;
-    return la;
+unsigned heavy_grid(uint64_t items, int per_sm = 2) {
+    const uint64_t cap = (uint64_t)sm_count() * (uint64_t)per_sm;
+    return (unsigned)(items < 1 ? 1 : items < cap ? items : cap);
 }
 
-}  // namespace
+template <typename P, int MODE>
+void launch_fused(const GraphView *gvs, const uint64_t *heavy_pre, uint32_t G, uint64_t items, const int64_t *dq,
+                  uint32_t nq, unsigned long long *out, unsigned long long *flag, const uint64_t *idx,
+                  uint64_t nidx, cudaStream_t s, int per_sm = 2) {
+    static int configured_device = -1;
+    int dev = 0;
+    TTC_CUDA(cudaGetDevice(&dev));
+    if (configured_device != dev) {
+        TTC_CUDA(cudaFuncSetAttribute(heavy_fused_kernel<P, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)FusedCap<P>::bytes(1, MAX_BATCH_SMEM_Q)));
+        configured_device = dev;
+    }
+    heavy_fused_kernel<P, MODE><<<heavy_grid(items, per_sm), HEAVY_THREADS, FusedCap<P>::bytes(MODE, nq), s>>>(
+        gvs, heavy_pre, G, dq, nq, out, flag, idx, nidx);
+    TTC_LAUNCH_CHECK();
+}
 
-void count_queue(ttc_graph *g, const int64_t *dq, uint32_t k, unsigned long long *acc, cudaStream_t s) {
+template <typename P, int MODE>
+void launch_warp(const GraphView *gvs, const uint64_t *hw_pre, uint32_t G, uint64_t items, const int64_t *dq,
+                 uint32_t nq, unsigned long long *out, unsigned long long *flag, const uint64_t *idx, uint64_t nidx,
+                 cudaStream_t s, int per_sm = 4) {
+    static int configured_device = -1;
+    int dev = 0;
+    TTC_CUDA(cudaGetDevice(&dev));
+    if (configured_device != dev) {
+        TTC_CUDA(cudaFuncSetAttribute(heavy_warp_kernel<P, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)WarpCap<P>::bytes(1, MAX_BATCH_SMEM_Q)));
+        configured_device = dev;
+    }
+    const uint64_t want = (items + HEAVY_WARPS - 1) / HEAVY_WARPS;
+    const uint64_t cap = (uint64_t)sm_count() * (uint64_t)per_sm;
+    const unsigned grid = (unsigned)(want < 1 ? 1 : want < cap ? want : cap);
+    heavy_warp_kernel<P, MODE><<<grid, HEAVY_THREADS, WarpCap<P>::bytes(MODE, nq), s>>>(gvs, hw_pre, G, dq, nq, out,
+                                                                                       flag, idx, nidx);
+    TTC_LAUNCH_CHECK();
+}
+
+template <int MODE>
+void launch_warp_any(int wide, const GraphView *gvs, const uint64_t *hw_pre, uint32_t G, uint64_t items,
+                     const int64_t *dq, uint32_t nq, unsigned long long *out, unsigned long long *flag,
+                     const uint64_t *idx, uint64_t nidx, cudaStream_t s, int per_sm = 4) {
+    if (wide) launch_warp<unsigned long long, MODE>(gvs, hw_pre, G, items, dq, nq, out, flag, idx, nidx, s, per_sm);
+    else launch_warp<uint32_t, MODE>(gvs, hw_pre, G, items, dq, nq, out, flag, idx, nidx, s, per_sm);
+}
+
+template <int MODE>
+void launch_fused_any(int wide, const GraphView *gvs, const uint64_t *heavy_pre, uint32_t G, uint64_t items,
+                      const int64_t *dq, uint32_t nq, unsigned long long *out, unsigned long long *flag,
+                      const uint64_t *idx, uint64_t nidx, cudaStream_t s, int per_sm = 2) {
+    if (wide) launch_fused<unsigned long long, MODE>(gvs, heavy_pre, G, items, dq, nq, out, flag, idx, nidx, s, per_sm);
+    else launch_fused<uint32_t, MODE>(gvs, heavy_pre, G, items, dq, nq, out, flag, idx, nidx, s, per_sm);
+}
+
+// One query (acc[8] + flag) or a batch of k (acc[k][8] + flag at acc[8 k])
+// on one graph; the huge path's prefix arrays live in `scratch`.
+void count_graph(ttc_graph *g, const int64_t *dq, uint32_t k, unsigned long long *acc, void *scratch,
+                 cudaStream_t s) {
     if (!g->st.tau || !k) return;
-    const LightArgs la = light_args(g);
-    if (la.ntri) {
-        const unsigned grid = light_grid(la.ntri);
+    unsigned long long *flag = acc + 8 * (size_t)k;
+    const uint64_t nl = g->st.tau_light;
+    const GraphView *gv = g->view.get();
+    const uint64_t *light_pre = g->prefix.get();
+    if (nl) {
+        const uint64_t chunks = (nl + 31) / 32;
         if (k == 1) {
             prof_begin(g, s, "light");
-            light_kernel_warp<0><<<grid, LIGHT_THREADS, 0, s>>>(la, dq, 1, acc, nullptr);
+            light_kernel<0><<<light_grid(chunks), LIGHT_THREADS, 0, s>>>(gv, light_pre, 1, dq, 1, acc, flag, nullptr,
+                                                                         0);
             TTC_LAUNCH_CHECK();
             prof_end(g, s);
         } else {
             for (uint32_t q0 = 0; q0 < k; q0 += MAX_BATCH_SMEM_Q) {
-                const uint32_t nq = k - q0 < (uint32_t)MAX_BATCH_SMEM_Q ? k - q0 : (uint32_t)MAX_BATCH_SMEM_Q;
+                const uint32_t nq = k - q0 < MAX_BATCH_SMEM_Q ? k - q0 : MAX_BATCH_SMEM_Q;
                 prof_begin(g, s, "light_batch");
-                light_kernel_warp<1><<<grid, LIGHT_THREADS, nq * 8 * sizeof(unsigned long long), s>>>(
-                    la, dq + 3 * (size_t)q0, nq, acc + 8 * (size_t)q0, nullptr);
+                light_kernel<1><<<light_grid(chunks), LIGHT_THREADS, nq * 64, s>>>(
+                    gv, light_pre, 1, dq + 3 * (size_t)q0, nq, acc + 8 * (size_t)q0, flag, nullptr, 0);
                 TTC_LAUNCH_CHECK();
                 prof_end(g, s);
             }
         }
     }
-    if (g->st.tau_heavy) {
-        const HeavyArgs ha = heavy_args(g, s);
+    const uint64_t nw = g->st.tau_hwarp, nc = g->st.tau_hcta;
+    const uint64_t *hw_pre = g->prefix.get() + 2, *hc_pre = g->prefix.get() + 4;
+    for (uint32_t q0 = 0; q0 < k && (nw || nc); q0 += MAX_BATCH_SMEM_Q) {
+        const uint32_t nq = k - q0 < MAX_BATCH_SMEM_Q ? k - q0 : MAX_BATCH_SMEM_Q;
+        const int mode = k == 1 ? 0 : 1;
+        if (nw) {
+            prof_begin(g, s, mode ? "heavy_warp_batch" : "heavy_warp");
+            if (mode) launch_warp_any<1>(g->heavy_wide, gv, hw_pre, 1, nw, dq + 3 * (size_t)q0, nq,
+                                         acc + 8 * (size_t)q0, flag, nullptr, 0, s);
+            else launch_warp_any<0>(g->heavy_wide, gv, hw_pre, 1, nw, dq, 1, acc, flag, nullptr, 0, s);
+            prof_end(g, s);
+        }
+        if (nc) {
+            prof_begin(g, s, mode ? "heavy_cta_batch" : "heavy_cta");
+            if (mode) launch_fused_any<1>(g->heavy_wide, gv, hc_pre, 1, nc, dq + 3 * (size_t)q0, nq,
+                                          acc + 8 * (size_t)q0, flag, nullptr, 0, s);
+            else launch_fused_any<0>(g->heavy_wide, gv, hc_pre, 1, nc, dq, 1, acc, flag, nullptr, 0, s);
+            prof_end(g, s);
+        }
+    }
+    if (g->st.tau_huge) {
+        const HugeArgs ha = huge_args(g, scratch);
         for (uint32_t q = 0; q < k; q++) {
-            if (g->heavy_wide) run_heavy<unsigned long long>(g, ha, dq + 3 * q, acc + 8 * (size_t)q, s);
-            else run_heavy<uint32_t>(g, ha, dq + 3 * q, acc + 8 * (size_t)q, s);
+            if (g->heavy_wide) run_huge<unsigned long long>(g, ha, dq + 3 * q, acc + 8 * (size_t)q, flag, s);
+            else run_huge<uint32_t>(g, ha, dq + 3 * q, acc + 8 * (size_t)q, flag, s);
         }
     }
 }
 
+// Vertex triple (u, v, w) of each sampled record: A = {u, v}, B = {u, w}.
+__global__ void record_vertices_kernel(const uint4 *tri, const uint2 *pv, const uint64_t *idx, uint64_t count,
+                                       uint32_t *out) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint4 r = tri[idx[i]];
+        const uint2 a = pv[r.x], b = pv[r.y];
+        const uint32_t u = (a.x == b.x || a.x == b.y) ? a.x : a.y;
+        out[3 * i] = u;
+        out[3 * i + 1] = a.x == u ? a.y : a.x;
+        out[3 * i + 2] = b.x == u ? b.y : b.x;
+    }
+}
+
+__global__ void record_sizes_kernel(const uint4 *tri, const uint64_t *idx, uint64_t count, const uint32_t *poff,
+                                    uint4 *recs, uint64_t *sizes) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint4 r = tri[idx[i]];
+        recs[i] = r;
+        sizes[i] = (poff[r.x + 1] - poff[r.x]) + (poff[r.y + 1] - poff[r.y]);
+    }
+}
+
+}  // namespace
+
 size_t heavy_scratch_bytes(const ttc_graph *g) {
-    const size_t entries = (size_t)g->heavy_elems + 4 * (size_t)g->st.tau_heavy;
-    return g->st.tau_heavy ? entries * 8 * (g->heavy_wide ? 8 : 4) : 0;
+    const size_t entries = (size_t)g->huge_elems + 4 * (size_t)g->st.tau_huge;
+    return g->st.tau_huge ? entries * 8 * (g->heavy_wide ? 8 : 4) : 0;
+}
+
+void count_queue(ttc_graph *g, const int64_t *dq, uint32_t k, unsigned long long *acc, cudaStream_t s) {
+    void *scratch = nullptr;
+    const size_t bytes = heavy_scratch_bytes(g);
+    if (bytes) {
+        if (g->scratch.count < bytes) g->scratch.alloc(bytes, s);
+        scratch = g->scratch.get();
+    }
+    count_graph(g, dq, k, acc, scratch, s);
 }
 
 void count_one_into(ttc_graph *g, const int64_t *dq, unsigned long long *acc, void *scratch, cudaStream_t s) {
-    if (!g->st.tau) return;
-    const LightArgs la = light_args(g);
-    if (la.ntri) {
-        light_kernel_warp<0><<<light_grid(la.ntri), LIGHT_THREADS, 0, s>>>(la, dq, 1, acc, nullptr);
-        TTC_LAUNCH_CHECK();
-    }
-    if (g->st.tau_heavy) {
-        HeavyArgs ha{};
-        ha.k = KeyCtx{g->key.get(), g->fwd.get(), g->shift, g->span};
-        ha.poff = g->poff.get();
-        ha.tri = g->tri.get() + g->st.tau_light;
-        ha.eoff = g->heavy_eoff.get();
-        ha.nh = g->st.tau_heavy;
-        ha.total = g->heavy_elems;
-        ha.pre = scratch;
-        const bool saved = g->profiling;
-        g->profiling = false;
-        if (g->heavy_wide) run_heavy<unsigned long long>(g, ha, dq, acc, s);
-        else run_heavy<uint32_t>(g, ha, dq, acc, s);
-        g->profiling = saved;
-    }
+    const bool saved = g->profiling;
+    g->profiling = false;
+    count_graph(g, dq, 1, acc, scratch, s);
+    g->profiling = saved;
 }
 
+uint32_t fused_capacity(int wide) { return wide ? FusedCap<unsigned long long>::CAP : FusedCap<uint32_t>::CAP; }
+uint32_t warp_capacity(int wide) { return wide ? WarpCap<unsigned long long>::CAP : WarpCap<uint32_t>::CAP; }
+
+// ---------------------------------------------------------------- sampled output
 void count_sample(ttc_graph *g, const int64_t *dq, uint64_t first, uint64_t stride, uint64_t cap,
                   uint32_t *tri_vtx_host, unsigned long long *out_host, uint64_t *written) {
     cudaStream_t s = g->stream;
     const uint64_t tau = g->st.tau, nl = g->st.tau_light;
-    std::vector<uint64_t> li, hi_, all;
-    for (uint64_t i = 0, ti = first; i < cap && ti < tau; i++, ti += stride) {
-        all.push_back(ti);
-        (ti < nl ? li : hi_).push_back(ti);
-    }
+    std::vector<uint64_t> all;
+    for (uint64_t i = 0, ti = first; i < cap && ti < tau; i++, ti += stride) all.push_back(ti);
     *written = all.size();
     if (all.empty()) return;
-    const uint64_t n = all.size(), nlc = li.size(), nhc = hi_.size();
+    const uint64_t n = all.size();
     DevBuf<uint64_t> d_all(n, s), d_idx(n, s);
     DevBuf<uint32_t> d_vtx(3 * n, s);
     DevBuf<unsigned long long> d_out(8 * n, s);
@@ -682,29 +1152,48 @@ void count_sample(ttc_graph *g, const int64_t *dq, uint64_t first, uint64_t stri
     record_vertices_kernel<<<ceil_div(n, 256), 256, 0, s>>>(g->tri.get(), g->pair_vtx.get(), d_all.get(), n,
                                                             d_vtx.get());
     TTC_LAUNCH_CHECK();
-    // light samples first, then heavy ones, in d_idx / d_out order
-    std::vector<uint64_t> order(li);
-    order.insert(order.end(), hi_.begin(), hi_.end());
+    // split by bin: light, heavy (one warp / one CTA each), huge (flat)
+    const uint64_t nw = g->st.tau_hwarp, nc = g->st.tau_hcta;
+    std::vector<uint64_t> li, hw, hc, hh, slot(n);
+    for (uint64_t i = 0; i < n; i++) {
+        if (all[i] < nl) li.push_back(i);
+        else if (all[i] < nl + nw) hw.push_back(i);
+        else if (all[i] < nl + nw + nc) hc.push_back(i);
+        else hh.push_back(i);
+    }
+    std::vector<uint64_t> order;  // d_idx: light ids, bin-relative heavy ids, absolute huge ids
+    for (uint64_t i : li) { slot[i] = order.size(); order.push_back(all[i]); }
+    for (uint64_t i : hw) { slot[i] = order.size(); order.push_back(all[i] - nl); }
+    for (uint64_t i : hc) { slot[i] = order.size(); order.push_back(all[i] - nl - nw); }
+    for (uint64_t i : hh) { slot[i] = order.size(); order.push_back(all[i]); }
     TTC_CUDA(cudaMemcpyAsync(d_idx.get(), order.data(), n * 8, cudaMemcpyHostToDevice, s));
+    const uint64_t nlc = li.size(), nwc = hw.size(), ncc = hc.size(), nhc = hh.size();
+    const uint64_t nfc = nwc + ncc;
+    DevBuf<unsigned long long> flag(1, s);
+    TTC_CUDA(cudaMemsetAsync(flag.get(), 0, 8, s));
     if (nlc) {
-        LightArgs la = light_args(g);
-        la.ntri = nlc;
-        light_kernel_warp<2><<<light_grid(nlc), LIGHT_THREADS, 0, s>>>(la, dq, 1, d_out.get(), d_idx.get());
+        light_kernel<2><<<light_grid((nlc + 31) / 32), LIGHT_THREADS, 0, s>>>(
+            g->view.get(), g->prefix.get(), 1, dq, 1, d_out.get(), flag.get(), d_idx.get(), nlc);
         TTC_LAUNCH_CHECK();
     }
+    if (nwc)
+        launch_warp_any<2>(g->heavy_wide, g->view.get(), g->prefix.get() + 2, 1, nwc, dq, 1, d_out.get() + 8 * nlc,
+                           flag.get(), d_idx.get() + nlc, nwc, s);
+    if (ncc)
+        launch_fused_any<2>(g->heavy_wide, g->view.get(), g->prefix.get() + 4, 1, ncc, dq, 1,
+                            d_out.get() + 8 * (nlc + nwc), flag.get(), d_idx.get() + nlc + nwc, ncc, s);
     if (nhc) {
         DevBuf<uint4> sub(nhc, s);
         DevBuf<uint64_t> sizes(nhc, s), eoff(nhc + 1, s);
-        gather_records_kernel<<<ceil_div(nhc, 256), 256, 0, s>>>(g->tri.get(), d_idx.get() + nlc, nhc,
-                                                                 g->poff.get(), sub.get(), sizes.get());
+        record_sizes_kernel<<<ceil_div(nhc, 256), 256, 0, s>>>(g->tri.get(), d_idx.get() + nlc + nfc, nhc,
+                                                               g->poff.get(), sub.get(), sizes.get());
         TTC_LAUNCH_CHECK();
         exclusive_scan_u64(sizes.get(), eoff.get(), nhc, s);
         uint64_t total = 0;
         TTC_CUDA(cudaMemcpyAsync(&total, eoff.get() + nhc, 8, cudaMemcpyDeviceToHost, s));
         TTC_CUDA(cudaStreamSynchronize(s));
-        HeavyArgs ha{};
-        ha.k = KeyCtx{g->key.get(), g->fwd.get(), g->shift, g->span};
-        ha.poff = g->poff.get();
+        HugeArgs ha{};
+        ha.gv = g->view_host;
         ha.tri = sub.get();
         ha.eoff = eoff.get();
         ha.nh = nhc;
@@ -712,11 +1201,11 @@ void count_sample(ttc_graph *g, const int64_t *dq, uint64_t first, uint64_t stri
         const size_t bytes = ((size_t)total + 4 * nhc) * 8 * (g->heavy_wide ? 8 : 4);
         DevBuf<uint8_t> pre(bytes, s);
         ha.pre = pre.get();
-        ha.per_tri = d_out.get() + 8 * nlc;
+        ha.per_tri = d_out.get() + 8 * (nlc + nfc);
         const bool saved = g->profiling;
         g->profiling = false;
-        if (g->heavy_wide) run_heavy<unsigned long long>(g, ha, dq, nullptr, s);
-        else run_heavy<uint32_t>(g, ha, dq, nullptr, s);
+        if (g->heavy_wide) run_huge<unsigned long long>(g, ha, dq, nullptr, flag.get(), s);
+        else run_huge<uint32_t>(g, ha, dq, nullptr, flag.get(), s);
         g->profiling = saved;
     }
     std::vector<unsigned long long> h(8 * n);
@@ -724,12 +1213,35 @@ void count_sample(ttc_graph *g, const int64_t *dq, uint64_t first, uint64_t stri
     TTC_CUDA(cudaMemcpyAsync(h.data(), d_out.get(), 8 * n * 8, cudaMemcpyDeviceToHost, s));
     TTC_CUDA(cudaMemcpyAsync(hv.data(), d_vtx.get(), 3 * n * 4, cudaMemcpyDeviceToHost, s));
     TTC_CUDA(cudaStreamSynchronize(s));
-    // back to sample order
-    for (uint64_t i = 0, a = 0, b = 0; i < n; i++) {
-        const uint64_t slot = all[i] < nl ? a++ : nlc + b++;
-        memcpy(out_host + 8 * i, &h[8 * slot], 64);
-    }
+    for (uint64_t i = 0; i < n; i++) memcpy(out_host + 8 * i, &h[8 * slot[i]], 64);
     memcpy(tri_vtx_host, hv.data(), 3 * n * 4);
+}
+
+// ---------------------------------------------------------------- many graphs
+void count_multi_launch(const MultiTable &t, const int64_t *dq, unsigned long long *acc, int light_per_sm,
+                        int heavy_per_sm, cudaStream_t s) {
+    unsigned long long *flag = acc + 8 * (size_t)t.G;
+    if (t.chunks) {
+        light_kernel<0><<<light_grid(t.chunks, light_per_sm), LIGHT_THREADS, 0, s>>>(t.gvs, t.chunk_pre, t.G, dq, 1,
+                                                                                     acc, flag, nullptr, 0);
+        TTC_LAUNCH_CHECK();
+    }
+    for (int wide = 0; wide < 2; wide++) {
+        if (!(wide ? t.any_wide : t.any_narrow)) continue;
+        if (t.hwarp)
+            launch_warp_any<0>(wide, t.gvs, t.hwarp_pre, t.G, t.hwarp, dq, 1, acc, flag, nullptr, 0, s,
+                               2 * heavy_per_sm);
+        if (t.hcta)
+            launch_fused_any<0>(wide, t.gvs, t.hcta_pre, t.G, t.hcta, dq, 1, acc, flag, nullptr, 0, s, heavy_per_sm);
+    }
+}
+
+void count_huge_of(ttc_graph *g, const int64_t *dq_one, unsigned long long *acc_row, unsigned long long *flag,
+                   void *scratch, cudaStream_t s) {
+    if (!g->st.tau_huge) return;
+    const HugeArgs ha = huge_args(g, scratch);
+    if (g->heavy_wide) run_huge<unsigned long long>(g, ha, dq_one, acc_row, flag, s);
+    else run_huge<uint32_t>(g, ha, dq_one, acc_row, flag, s);
 }
 
 }  // namespace ttc

@@ -22,6 +22,22 @@ struct TriRec {
     static constexpr uint32_t FLIP_A = 1u, FLIP_B = 2u, FLIP_C = 4u;
 };
 
+// What the count kernels see of one resident graph (plain pointers; an array
+// of these is the "graph table" of a many-graph launch).
+struct GraphView {
+    const int64_t *key;
+    const uint32_t *fwd;
+    const uint32_t *poff;
+    // records in bin order: light [0, n_light), then heavy ones for one warp
+    // each (n_hwarp), for one CTA each (n_hcta), and the huge ones last;
+    // n_heavy counts all three heavy bins
+    const uint4 *tri;
+    uint64_t n_light, n_hwarp, n_hcta, n_heavy;
+    int64_t span;
+    int shift;
+    int wide;  // 64-bit prefix sums needed (some list has >= 65536 edges)
+};
+
 struct ttc_graph {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -39,10 +55,15 @@ struct ttc_graph {
     ttc::DevBuf<uint32_t> poff;   // [m_s + 1] first edge of each pair
     ttc::DevBuf<uint2> pair_vtx;  // [m_s] (smaller id, larger id) of each pair
     ttc::DevBuf<uint4> tri;       // [tau] light records first, then heavy ones
-    // prefix-sum (CEC) path for heavy triangles
-    ttc::DevBuf<uint64_t> heavy_eoff;  // [tau_heavy + 1] enumerated-element offsets
-    int heavy_wide = 0;                // 1: 64-bit prefix sums needed
-    uint64_t heavy_elems = 0;
+    int heavy_wide = 0;           // 1: 64-bit prefix sums needed
+    // heavy triangles too large for one CTA (flat prefix-sum path): the last
+    // tau_huge records
+    ttc::DevBuf<uint64_t> huge_eoff;    // [tau_huge + 1] enumerated-edge offsets
+    uint64_t huge_elems = 0;
+    // the graph as a one-entry graph table
+    GraphView view_host{};
+    ttc::DevBuf<GraphView> view;        // [1]
+    ttc::DevBuf<uint64_t> prefix;       // [6]: {0, light chunks, 0, n_hwarp, 0, n_hcta}
 
     // per-call device scratch, guarded by `mu`
     std::mutex mu;
@@ -94,10 +115,25 @@ void count_one_into(ttc_graph *g, const int64_t *dq, unsigned long long *acc, vo
 void count_sample(ttc_graph *g, const int64_t *dq, uint64_t first, uint64_t stride, uint64_t cap,
                   uint32_t *tri_vtx_host, unsigned long long *out_host, uint64_t *written);
 
-// count.cu: many graphs in one persistent launch.
-struct MultiGraphDesc;
-void count_multi_launch(const MultiGraphDesc *descs_dev, uint32_t G, const uint64_t *tri_prefix_dev,
-                        uint64_t tri_total, unsigned long long *acc, cudaStream_t s);
+// count.cu: many graphs in one launch of the light and heavy kernels over a
+// device graph table; dq holds one normalised delta per graph; acc is [G][8]
+// plus the overflow flag; light_per_sm / heavy_per_sm shape the grids.
+struct MultiTable {
+    const GraphView *gvs;
+    uint32_t G;
+    const uint64_t *chunk_pre, *hwarp_pre, *hcta_pre;  // exclusive prefixes over the graphs (G + 1)
+    uint64_t chunks, hwarp, hcta;                       // their totals
+    int any_narrow, any_wide;                           // prefix widths present in the heavy bins
+};
+void count_multi_launch(const MultiTable &t, const int64_t *dq, unsigned long long *acc, int light_per_sm,
+                        int heavy_per_sm, cudaStream_t s);
+// The flat path of one graph's huge triangles for one query (counts added to
+// acc_row[8], overflow flag at *flag).
+void count_huge_of(ttc_graph *g, const int64_t *dq_one, unsigned long long *acc_row, unsigned long long *flag,
+                   void *scratch, cudaStream_t s);
+// Largest A + B list length handled by one warp / one CTA of the heavy bin.
+uint32_t warp_capacity(int wide);
+uint32_t fused_capacity(int wide);
 
 uint32_t default_light_max_pairs();
 

@@ -91,6 +91,19 @@ __global__ void time_key_kernel(int64_t *tk, size_t m, int64_t tmin, uint64_t *t
     }
 }
 
+// Packed key with the kept-edge index as tie-break (used when it fits in 63
+// bits), and the pair key lo * n + hi as the value to carry.
+__global__ void key_direct_kernel(const uint32_t *eidx, const int64_t *tk, size_t m, int64_t tmin, int shift,
+                                  const uint32_t *src, const uint32_t *dst, uint64_t n, uint64_t *key,
+                                  uint64_t *pkey) {
+    GRID_STRIDE(i, m) {
+        const uint32_t e = eidx[i];
+        const uint32_t a = src[e], b = dst[e];
+        key[i] = ((uint64_t)(tk[i] - tmin) << shift) | ((uint64_t)i << 1) | (uint64_t)(a > b);
+        pkey[i] = (uint64_t)min(a, b) * n + max(a, b);
+    }
+}
+
 __global__ void head_flags_kernel(const uint64_t *k, size_t m, uint8_t *head) {
     GRID_STRIDE(i, m) head[i] = (i == 0) || (k[i] != k[i - 1]);
 }
@@ -172,12 +185,16 @@ struct PeelCtl {
     unsigned int kappa;
     unsigned int rounds;
     unsigned int error;
+    unsigned int handoff;  // 1: stopped with at most tail_n vertices left
+    int k;                 // level at the hand-off
+    unsigned int rem_n;    // vertices left at the hand-off
+    unsigned int rem_in_b; // the remaining list is in remB (else remA)
     unsigned int pad;
 };
 
 constexpr uint64_t MASK40 = (uint64_t(1) << 40) - 1;
 constexpr int PEEL_THREADS = 1024;
-constexpr int PEEL_RUN = 16;  // relaxed edges per thread per step
+constexpr int PEEL_RUN = 8;  // relaxed edges per thread per step
 
 // Appends v (with its adjacency length) to a frontier list; warp-aggregated.
 // Every lane of the warp must call it (pred selects the appending lanes).
@@ -214,7 +231,7 @@ __device__ __forceinline__ void push_frontier(bool pred, uint32_t v, uint32_t na
 __global__ void __launch_bounds__(PEEL_THREADS)
     peel_kernel(const uint32_t *__restrict__ adj_off, const uint32_t *__restrict__ adj, int *deg,
                 uint32_t *level, uint32_t *remA, uint32_t *remB, uint32_t *frontA, uint32_t *frontB,
-                uint32_t *foffA, uint32_t *foffB, uint32_t n, PeelCtl *ctl) {
+                uint32_t *foffA, uint32_t *foffB, uint32_t n, uint32_t tail_n, PeelCtl *ctl) {
     cg::cluster_group cluster = cg::this_cluster();
     const uint32_t nthr = cluster.num_blocks() * blockDim.x;
     const uint32_t tid = cluster.block_rank() * blockDim.x + threadIdx.x;
@@ -272,6 +289,15 @@ __global__ void __launch_bounds__(PEEL_THREADS)
             uint32_t *t = rem; rem = rem_next; rem_next = t;
             if (rem_n == 0) break;
             k = max(k, md);
+            if (rem_n <= tail_n) {  // the rest fits one CTA's shared memory
+                if (tid == 0) {
+                    ctl->handoff = 1;
+                    ctl->k = k;
+                    ctl->rem_n = rem_n;
+                    ctl->rem_in_b = rem == remB;
+                }
+                break;
+            }
             kappa = max(kappa, (uint32_t)k);
             // collection: the new level's frontier
             sl = &ctl->slot[ph % 3];
@@ -294,47 +320,57 @@ __global__ void __launch_bounds__(PEEL_THREADS)
             fn = (uint32_t)(f >> 40);
             fe = (uint32_t)(f & MASK40);
         }
-        // relaxation: remove the frontier (round `round`)
+        // relaxation: remove the frontier (round `round`).  Each thread takes
+        // PEEL_RUN consecutive edges and issues their loads and atomics as
+        // independent batches, so one round costs a few memory latencies.
         PeelSlot *sl = &ctl->slot[ph % 3];
         for (uint32_t e0 = tid * PEEL_RUN; e0 - tid * PEEL_RUN < fe; e0 += nthr * PEEL_RUN) {
             // the loop bound keeps every lane of a warp iterating together
-            uint32_t e1 = min(fe, e0 + PEEL_RUN);
-            uint32_t fi = 0, fbeg = 0, fend = 0, v = 0;
+            uint32_t wv[PEEL_RUN];
+            bool live[PEEL_RUN];
             if (e0 < fe) {
                 uint32_t lo = 0, hi = fn;  // last fi with foff[fi] <= e0
                 while (hi - lo > 1) {
                     const uint32_t mid = (lo + hi) >> 1;
                     if (__ldcg(foff + mid) <= e0) lo = mid; else hi = mid;
                 }
-                fi = lo;
-                fbeg = __ldcg(foff + fi);
-                fend = fi + 1 < fn ? __ldcg(foff + fi + 1) : fe;
-                v = __ldcg(front + fi);
-            } else {
-                e1 = e0;
-            }
-            for (uint32_t step = 0; step < PEEL_RUN; step++) {
-                const uint32_t e = e0 + step;
-                bool push = false;
-                uint32_t w = 0, na = 0;
-                if (e < e1) {
-                    while (e >= fend) {
-                        fi++;
-                        fbeg = fend;
-                        fend = fi + 1 < fn ? __ldcg(foff + fi + 1) : fe;
-                        v = __ldcg(front + fi);
-                    }
-                    w = adj[adj_off[v] + (e - fbeg)];
-                    if (__ldcg(level + w) == UNSET) {
-                        const int old = atomicSub(deg + w, 1);
-                        if (old == k + 1) {
-                            push = true;
-                            level[w] = round + 1;
-                            na = adj_off[w + 1] - adj_off[w];
+                uint32_t fi = lo;
+                uint32_t fbeg = __ldcg(foff + fi);
+                uint32_t fend = fi + 1 < fn ? __ldcg(foff + fi + 1) : fe;
+                uint32_t base = adj_off[__ldcg(front + fi)];
+#pragma unroll
+                for (int j = 0; j < PEEL_RUN; j++) {
+                    const uint32_t e = e0 + j;
+                    live[j] = e < fe;
+                    if (live[j]) {
+                        while (e >= fend) {
+                            fi++;
+                            fbeg = fend;
+                            fend = fi + 1 < fn ? __ldcg(foff + fi + 1) : fe;
+                            base = adj_off[__ldcg(front + fi)];
                         }
+                        wv[j] = adj[base + (e - fbeg)];
                     }
                 }
-                push_frontier(push, w, na, sl, front_next, foff_next, lane);
+#pragma unroll
+                for (int j = 0; j < PEEL_RUN; j++)
+                    if (live[j]) live[j] = __ldcg(level + wv[j]) == UNSET;
+            } else {
+#pragma unroll
+                for (int j = 0; j < PEEL_RUN; j++) live[j] = false;
+            }
+            int old[PEEL_RUN];
+#pragma unroll
+            for (int j = 0; j < PEEL_RUN; j++) old[j] = live[j] ? atomicSub(deg + wv[j], 1) : 0;
+#pragma unroll
+            for (int j = 0; j < PEEL_RUN; j++) {
+                const bool push = live[j] && old[j] == k + 1;
+                uint32_t na = 0;
+                if (push) {
+                    level[wv[j]] = round + 1;
+                    na = adj_off[wv[j] + 1] - adj_off[wv[j]];
+                }
+                push_frontier(push, push ? wv[j] : 0, na, sl, front_next, foff_next, lane);
             }
         }
         const PeelSlot *r = end_phase();
@@ -349,6 +385,163 @@ __global__ void __launch_bounds__(PEEL_THREADS)
         ctl->rounds = round;
         ctl->kappa = kappa;
         if (!ok) ctl->error = 1;
+    }
+}
+
+
+// ---------------------------------------------------------------- peel tail
+constexpr uint32_t PEEL_TAIL = 8192;  // vertices the one-CTA tail peel holds
+constexpr int TAIL_THREADS = 1024;
+constexpr size_t TAIL_SMEM = (size_t)PEEL_TAIL * (4 + 2 * 4 + 2 + 2 * 2);
+
+// Local ids of the remaining vertices and their (current) degrees.
+__global__ void tail_ids_kernel(const uint32_t *rem, uint32_t R, const int *deg, uint32_t *lid, uint32_t *cdeg) {
+    GRID_STRIDE(i, (size_t)R) {
+        lid[rem[i]] = (uint32_t)i;
+        cdeg[i] = (uint32_t)deg[rem[i]];
+    }
+}
+
+// Adjacency of the remaining vertices among themselves, in local ids; one
+// warp per vertex, neighbours kept in adjacency order.
+__global__ void tail_adj_kernel(const uint32_t *rem, uint32_t R, const uint32_t *adj_off, const uint32_t *adj,
+                                const uint32_t *level, const uint32_t *lid, const uint32_t *coff, uint16_t *cadj) {
+    const uint32_t lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    for (uint64_t i = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < R;
+         i += ((uint64_t)gridDim.x * blockDim.x) >> 5) {
+        const uint32_t v = rem[i];
+        uint32_t pos = coff[i];
+        for (uint32_t j0 = adj_off[v]; j0 < adj_off[v + 1]; j0 += 32) {
+            const uint32_t j = j0 + lane;
+            bool keep = false;
+            uint32_t w = 0;
+            if (j < adj_off[v + 1]) {
+                w = adj[j];
+                keep = level[w] == UNSET;
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, keep);
+            if (keep) cadj[pos + __popc(bal & lt_mask)] = (uint16_t)lid[w];
+            pos += __popc(bal);
+        }
+    }
+}
+
+// The rest of the peel in one CTA: degrees, levels, frontiers and their
+// adjacency offsets in shared memory; the core adjacency (local ids) is read
+// from L2.  Same rules as peel_kernel, continuing from level k0 and round
+// round0; writes level[] for the remaining vertices and the final round and
+// kappa counts.
+__global__ void __launch_bounds__(TAIL_THREADS)
+    peel_tail_kernel(const uint32_t *rem, uint32_t R, const uint32_t *coff, const uint16_t *cadj, uint32_t *level,
+                     int k0, uint32_t round0, PeelCtl *ctl) {
+    extern __shared__ __align__(16) unsigned char tail_smem[];
+    uint32_t *s_deg = reinterpret_cast<uint32_t *>(tail_smem);                      // [PEEL_TAIL]
+    uint32_t (*s_foff)[PEEL_TAIL] = reinterpret_cast<uint32_t (*)[PEEL_TAIL]>(s_deg + PEEL_TAIL);  // [2][..]
+    uint16_t *s_lev = reinterpret_cast<uint16_t *>(s_deg + 3 * PEEL_TAIL);           // [PEEL_TAIL]
+    uint16_t (*s_front)[PEEL_TAIL] = reinterpret_cast<uint16_t (*)[PEEL_TAIL]>(s_lev + PEEL_TAIL);  // [2][..]
+    __shared__ unsigned long long s_cnt[2];
+    __shared__ int s_min;
+    const uint32_t tid = threadIdx.x, lane = tid & 31;
+    constexpr uint16_t NONE = 0xffff;
+    for (uint32_t i = tid; i < R; i += TAIL_THREADS) {
+        s_deg[i] = coff[i + 1] - coff[i];
+        s_lev[i] = NONE;
+    }
+    if (tid == 0) {
+        s_cnt[0] = s_cnt[1] = 0;
+        s_min = INT_MAX;
+    }
+    __syncthreads();
+    int k = k0;
+    uint32_t round = 0, kappa = ctl->kappa, removed = 0, cur = 0, fn = 0, fe = 0;
+    // warp-aggregated push of local vertex v into frontier buffer b
+    auto push = [&](bool pred, uint32_t v, uint32_t na, int b) {
+        const uint64_t pk = pred ? ((uint64_t(1) << 40) | na) : 0;
+        uint64_t x = pk;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= (uint32_t)o) x += y;
+        }
+        const uint64_t tot = __shfl_sync(0xffffffffu, x, 31);
+        uint64_t base = 0;
+        if (lane == 31 && tot) base = atomicAdd(&s_cnt[b], (unsigned long long)tot);
+        base = __shfl_sync(0xffffffffu, base, 31);
+        if (pred) {
+            const uint64_t mine = base + x - pk;
+            s_front[b][mine >> 40] = (uint16_t)v;
+            s_foff[b][mine >> 40] = (uint32_t)(mine & MASK40);
+        }
+    };
+    while (removed < R) {
+        if (fn == 0) {
+            // new level: smallest remaining degree, then collect its frontier
+            int my = INT_MAX;
+            for (uint32_t i = tid; i < R; i += TAIL_THREADS)
+                if (s_lev[i] == NONE) my = min(my, (int)s_deg[i]);
+#pragma unroll
+            for (int o = 16; o; o >>= 1) my = min(my, __shfl_xor_sync(0xffffffffu, my, o));
+            if (lane == 0) atomicMin(&s_min, my);
+            __syncthreads();
+            k = max(k, s_min);
+            kappa = max(kappa, (uint32_t)k);
+            for (uint32_t base = 0; base < R; base += TAIL_THREADS) {
+                const uint32_t i = base + tid;
+                bool take = false;
+                uint32_t na = 0;
+                if (i < R && s_lev[i] == NONE && (int)s_deg[i] <= k) {
+                    take = true;
+                    s_lev[i] = (uint16_t)round;
+                    na = coff[i + 1] - coff[i];
+                }
+                push(take, i, na, cur);
+            }
+            __syncthreads();
+            fn = (uint32_t)(s_cnt[cur] >> 40);
+            fe = (uint32_t)(s_cnt[cur] & MASK40);
+            __syncthreads();
+            if (tid == 0) s_min = INT_MAX;
+        }
+        removed += fn;
+        const int nxt = cur ^ 1;
+        if (tid == 0) s_cnt[nxt] = 0;  // the previous frontier's counter
+        __syncthreads();
+        for (uint32_t e0 = tid; e0 - tid < fe; e0 += TAIL_THREADS) {
+            bool p = false;
+            uint32_t w = 0, na = 0;
+            if (e0 < fe) {
+                uint32_t lo = 0, hi = fn;
+                while (hi - lo > 1) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (s_foff[cur][mid] <= e0) lo = mid; else hi = mid;
+                }
+                const uint32_t v = s_front[cur][lo];
+                w = cadj[coff[v] + (e0 - s_foff[cur][lo])];
+                if (s_lev[w] == NONE) {
+                    const uint32_t old = atomicSub(&s_deg[w], 1u);
+                    if ((int)old == k + 1) {
+                        p = true;
+                        s_lev[w] = (uint16_t)(round + 1);
+                        na = coff[w + 1] - coff[w];
+                    }
+                }
+            }
+            push(p, w, na, nxt);
+        }
+        __syncthreads();
+        fn = (uint32_t)(s_cnt[nxt] >> 40);
+        fe = (uint32_t)(s_cnt[nxt] & MASK40);
+        cur = nxt;
+        round++;
+        if (round > R + 1) break;  // cannot happen: every round removes a vertex
+    }
+    __syncthreads();
+    for (uint32_t i = tid; i < R; i += TAIL_THREADS) level[rem[i]] = round0 + s_lev[i];
+    if (tid == 0) {
+        ctl->rounds = round0 + round;
+        ctl->kappa = kappa;
+        if (removed < R) ctl->error = 1;
     }
 }
 
@@ -566,6 +759,29 @@ __global__ void __launch_bounds__(TRI_THREADS)
     }
 }
 
+// Heavy-bin class of each heavy record from its enumerated size: 0 = one
+// warp, 1 = one CTA, 2 = huge (flat path).
+__global__ void heavy_class_kernel(const uint64_t *he, size_t nh, uint32_t wcap, uint32_t ccap, uint8_t *f0,
+                                   uint8_t *f1, uint8_t *f2) {
+    GRID_STRIDE(i, nh) {
+        const uint64_t e = he[i];
+        f0[i] = e <= wcap;
+        f1[i] = e > wcap && e <= ccap;
+        f2[i] = e > ccap;
+    }
+}
+
+// Stable three-way partition of the heavy records (and their sizes).
+__global__ void heavy_partition_kernel(const uint4 *rec, const uint64_t *he, const uint8_t *f0, const uint8_t *f1,
+                                       const uint32_t *p0, const uint32_t *p1, const uint32_t *p2, size_t nh,
+                                       uint64_t n0, uint64_t n1, uint4 *out, uint64_t *he_out) {
+    GRID_STRIDE(i, nh) {
+        const uint64_t dst = f0[i] ? p0[i] : f1[i] ? n0 + p1[i] : n0 + n1 + p2[i];
+        out[dst] = rec[i];
+        he_out[dst] = he[i];
+    }
+}
+
 template <typename T>
 T read_scalar(const T *dev, cudaStream_t s) {
     T h;
@@ -577,6 +793,28 @@ T read_scalar(const T *dev, cudaStream_t s) {
 }  // namespace
 
 uint32_t default_light_max_pairs() { return 65; }
+
+// The graph as a one-entry graph table for the count kernels.
+static void set_view(ttc_graph *g, cudaStream_t s) {
+    GraphView &v = g->view_host;
+    v.key = g->key.get();
+    v.fwd = g->fwd.get();
+    v.poff = g->poff.get();
+    v.tri = g->tri.get();
+    v.n_light = g->st.tau_light;
+    v.n_hwarp = g->st.tau_hwarp;
+    v.n_hcta = g->st.tau_hcta;
+    v.n_heavy = g->st.tau_heavy;
+    v.span = g->span;
+    v.shift = g->shift;
+    v.wide = g->heavy_wide;
+    g->view.alloc(1, s);
+    g->prefix.alloc(6, s);
+    const uint64_t pre[6] = {0, (v.n_light + 31) / 32, 0, v.n_hwarp, 0, v.n_hcta};
+    TTC_CUDA(cudaMemcpyAsync(g->view.get(), &v, sizeof v, cudaMemcpyHostToDevice, s));
+    TTC_CUDA(cudaMemcpyAsync(g->prefix.get(), pre, sizeof pre, cudaMemcpyHostToDevice, s));
+    TTC_CUDA(cudaStreamSynchronize(s));
+}
 
 // Largest cluster (up to 16 CTAs of 1024 threads) the device can run for the peel.
 int peel_cluster_size() {
@@ -649,9 +887,7 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
         g->poff.alloc(1, s);
         TTC_CUDA(cudaMemsetAsync(g->poff.get(), 0, 4, s));
         TTC_CUDA(cudaMemsetAsync(g->fwd.get(), 0, 4, s));
-        g->heavy_eoff.alloc(1, s);
-        TTC_CUDA(cudaMemsetAsync(g->heavy_eoff.get(), 0, 8, s));
-        TTC_CUDA(cudaStreamSynchronize(s));
+        set_view(g, s);
         return;
     }
 
@@ -674,42 +910,55 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
     g->span = hmm[1] - hmm[0];
     const int span_bits = bits_for((uint64_t)g->span);
 
-    // ---- a2: sort by time (stable, so equal timestamps keep input order)
-    DevBuf<uint64_t> tkey(m, s);
-    time_key_kernel<<<grid_for(m), TPB, 0, s>>>(tk.get(), m, g->tmin, tkey.get(), eidx.get(), eidx.get());
-    TTC_LAUNCH_CHECK();
-    tk.reset();
-    radix_sort_u64_u32(tkey.get(), eidx.get(), m, span_bits, s);
-    // rank inside each equal-timestamp group
-    DevBuf<uint8_t> head(m, s);
-    DevBuf<uint32_t> gid(m + 1, s);
-    head_flags_kernel<<<grid_for(m), TPB, 0, s>>>(tkey.get(), m, head.get());
-    TTC_LAUNCH_CHECK();
-    exclusive_scan_flags(head.get(), gid.get(), m, s);
-    const uint32_t ngroups = read_scalar(gid.get() + m, s);
-    DevBuf<uint32_t> gstart(ngroups ? ngroups : 1, s);
-    group_start_kernel<<<grid_for(m), TPB, 0, s>>>(head.get(), gid.get(), m, gstart.get());
-    TTC_LAUNCH_CHECK();
-    DevBuf<unsigned int> maxr(1, s);
-    TTC_CUDA(cudaMemsetAsync(maxr.get(), 0, 4, s));
-    group_rank_max_kernel<<<grid_for(m), TPB, 0, s>>>(gid.get(), gstart.get(), m, maxr.get());
-    TTC_LAUNCH_CHECK();
-    const uint32_t max_rank = read_scalar(maxr.get(), s);
-    g->shift = bits_for(max_rank) + 1;
-    st.key_bits = (uint32_t)(span_bits + g->shift);
-    if (span_bits + g->shift > 63)
-        fail(TTC_ERR_RANGE, "timestamp span needs %d bits plus %d tie bits; at most 63 fit the packed key",
-             span_bits, g->shift);
+    // ---- a2: per-edge key (t - t_min, tie rank, dir), grouped by pair and
+    // key-sorted inside each pair by two stable sorts: time, then pair
     if (n * n > (uint64_t(1) << 63)) fail(TTC_ERR_RANGE, "vertex ids too large for the pair key");
-
     DevBuf<uint64_t> pkey(m, s);
-    pack_kernel<<<grid_for(m), TPB, 0, s>>>(tkey.get(), eidx.get(), gid.get(), gstart.get(), src, dst, m, g->shift,
-                                            n, pkey.get(), reinterpret_cast<uint64_t *>(g->key.get()));
-    TTC_LAUNCH_CHECK();
-    tkey.reset(); eidx.reset(); gid.reset(); gstart.reset();
-    src_buf.reset(); dst_buf.reset(); t_buf.reset();
+    const int ib = bits_for(m - 1);
+    if (span_bits + ib + 1 <= 63) {
+        // ties broken by the kept-edge index itself (input order)
+        g->shift = ib + 1;
+        key_direct_kernel<<<grid_for(m), TPB, 0, s>>>(eidx.get(), tk.get(), m, g->tmin, g->shift, src, dst, n,
+                                                      reinterpret_cast<uint64_t *>(g->key.get()), pkey.get());
+        TTC_LAUNCH_CHECK();
+        tk.reset(); eidx.reset();
+        src_buf.reset(); dst_buf.reset(); t_buf.reset();
+        radix_sort_u64_u64_range(reinterpret_cast<uint64_t *>(g->key.get()), pkey.get(), m, g->shift,
+                                 g->shift + span_bits, s);
+    } else {
+        // ties broken by the rank inside each equal-timestamp group
+        DevBuf<uint64_t> tkey(m, s);
+        time_key_kernel<<<grid_for(m), TPB, 0, s>>>(tk.get(), m, g->tmin, tkey.get(), eidx.get(), eidx.get());
+        TTC_LAUNCH_CHECK();
+        tk.reset();
+        radix_sort_u64_u32(tkey.get(), eidx.get(), m, span_bits, s);
+        DevBuf<uint8_t> head(m, s);
+        DevBuf<uint32_t> gid(m + 1, s);
+        head_flags_kernel<<<grid_for(m), TPB, 0, s>>>(tkey.get(), m, head.get());
+        TTC_LAUNCH_CHECK();
+        exclusive_scan_flags(head.get(), gid.get(), m, s);
+        const uint32_t ngroups = read_scalar(gid.get() + m, s);
+        DevBuf<uint32_t> gstart(ngroups ? ngroups : 1, s);
+        group_start_kernel<<<grid_for(m), TPB, 0, s>>>(head.get(), gid.get(), m, gstart.get());
+        TTC_LAUNCH_CHECK();
+        DevBuf<unsigned int> maxr(1, s);
+        TTC_CUDA(cudaMemsetAsync(maxr.get(), 0, 4, s));
+        group_rank_max_kernel<<<grid_for(m), TPB, 0, s>>>(gid.get(), gstart.get(), m, maxr.get());
+        TTC_LAUNCH_CHECK();
+        const uint32_t max_rank = read_scalar(maxr.get(), s);
+        g->shift = bits_for(max_rank) + 1;
+        if (span_bits + g->shift > 63)
+            fail(TTC_ERR_RANGE, "timestamp span needs %d bits plus %d tie bits; at most 63 fit the packed key",
+                 span_bits, g->shift);
+        pack_kernel<<<grid_for(m), TPB, 0, s>>>(tkey.get(), eidx.get(), gid.get(), gstart.get(), src, dst, m,
+                                                g->shift, n, pkey.get(), reinterpret_cast<uint64_t *>(g->key.get()));
+        TTC_LAUNCH_CHECK();
+        src_buf.reset(); dst_buf.reset(); t_buf.reset();
+    }
+    st.key_bits = (uint32_t)(span_bits + g->shift);
     // group by pair; stable, so each pair's edges stay in key order
     radix_sort_u64_u64(pkey.get(), reinterpret_cast<uint64_t *>(g->key.get()), m, bits_for(n * n - 1), s);
+    DevBuf<uint8_t> head(m, s);
     DevBuf<uint32_t> pid(m + 1, s);
     head_flags_kernel<<<grid_for(m), TPB, 0, s>>>(pkey.get(), m, head.get());
     TTC_LAUNCH_CHECK();
@@ -772,10 +1021,32 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
         cfg.numAttrs = 1;
         TTC_CUDA(cudaLaunchKernelEx(&cfg, peel_kernel, (const uint32_t *)adj_off.get(), (const uint32_t *)adj.get(),
                                     pdeg.get(), level.get(), remA.get(), remB.get(), frontA.get(), frontB.get(),
-                                    foffA.get(), foffB.get(), (uint32_t)n, ctl.get()));
+                                    foffA.get(), foffB.get(), (uint32_t)n, PEEL_TAIL, ctl.get()));
         note_launch();
-        const PeelCtl out = read_scalar(ctl.get(), s);
+        PeelCtl out = read_scalar(ctl.get(), s);
         if (out.error) fail(TTC_ERR_INTERNAL, "k-core peel did not finish");
+        if (out.handoff) {
+            // the remaining core: local ids, induced adjacency, one-CTA tail
+            const uint32_t R = out.rem_n;
+            const uint32_t *rem = out.rem_in_b ? remB.get() : remA.get();
+            uint32_t *lid = frontA.get();  // free after the cluster phase
+            DevBuf<uint32_t> cdeg(R, s), coff(R + 1, s);
+            tail_ids_kernel<<<grid_for(R), TPB, 0, s>>>(rem, R, pdeg.get(), lid, cdeg.get());
+            TTC_LAUNCH_CHECK();
+            exclusive_scan_u32(cdeg.get(), coff.get(), R, s);
+            const uint32_t ce = read_scalar(coff.get() + R, s);
+            DevBuf<uint16_t> cadj(ce ? ce : 1, s);
+            tail_adj_kernel<<<grid_for((size_t)R * 32), TPB, 0, s>>>(rem, R, adj_off.get(), adj.get(), level.get(), lid,
+                                                                    coff.get(), cadj.get());
+            TTC_LAUNCH_CHECK();
+            TTC_CUDA(cudaFuncSetAttribute(peel_tail_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)TAIL_SMEM));
+            peel_tail_kernel<<<1, TAIL_THREADS, TAIL_SMEM, s>>>(rem, R, coff.get(), cadj.get(), level.get(), out.k,
+                                                                out.rounds, ctl.get());
+            TTC_LAUNCH_CHECK();
+            out = read_scalar(ctl.get(), s);
+            if (out.error) fail(TTC_ERR_INTERNAL, "k-core peel tail did not finish");
+        }
         st.peel_rounds = out.rounds;
     }
     DevBuf<uint64_t> rk(n, s);
@@ -847,12 +1118,48 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
     }
     unsigned long long hws[3];
     TTC_CUDA(cudaMemcpyAsync(hws, ws.get(), 24, cudaMemcpyDeviceToHost, s));
-    g->heavy_eoff.alloc(nh + 1, s);
-    exclusive_scan_u64(he.get(), g->heavy_eoff.get(), nh, s);
-    g->heavy_elems = read_scalar(g->heavy_eoff.get() + nh, s);
+    TTC_CUDA(cudaStreamSynchronize(s));
     st.work_bytes = hws[0];
     st.enum_elems = hws[1];
     st.work_bytes_heavy = hws[2];
+    // heavy records in three classes by size (one warp, one CTA, flat),
+    // stably partitioned so each class is contiguous; the huge class last
+    const uint32_t wcap = warp_capacity(g->heavy_wide), ccap = fused_capacity(g->heavy_wide);
+    uint64_t n_huge = 0, n_hw = 0, n_hc = 0;
+    if (nh) {
+        DevBuf<uint8_t> f0(nh, s), f1(nh, s), f2(nh, s);
+        DevBuf<uint32_t> p0(nh + 1, s), p1(nh + 1, s), p2(nh + 1, s);
+        heavy_class_kernel<<<grid_for(nh), TPB, 0, s>>>(he.get(), nh, wcap, ccap, f0.get(), f1.get(), f2.get());
+        TTC_LAUNCH_CHECK();
+        exclusive_scan_flags(f0.get(), p0.get(), nh, s);
+        exclusive_scan_flags(f1.get(), p1.get(), nh, s);
+        exclusive_scan_flags(f2.get(), p2.get(), nh, s);
+        uint32_t cnt[3];
+        TTC_CUDA(cudaMemcpyAsync(&cnt[0], p0.get() + nh, 4, cudaMemcpyDeviceToHost, s));
+        TTC_CUDA(cudaMemcpyAsync(&cnt[1], p1.get() + nh, 4, cudaMemcpyDeviceToHost, s));
+        TTC_CUDA(cudaMemcpyAsync(&cnt[2], p2.get() + nh, 4, cudaMemcpyDeviceToHost, s));
+        TTC_CUDA(cudaStreamSynchronize(s));
+        n_hw = cnt[0];
+        n_hc = cnt[1];
+        n_huge = cnt[2];
+        DevBuf<uint4> part(nh, s);
+        DevBuf<uint64_t> he2(nh, s);
+        heavy_partition_kernel<<<grid_for(nh), TPB, 0, s>>>(g->tri.get() + n_light, he.get(), f0.get(), f1.get(),
+                                                            p0.get(), p1.get(), p2.get(), nh, n_hw, n_hc, part.get(),
+                                                            he2.get());
+        TTC_LAUNCH_CHECK();
+        TTC_CUDA(cudaMemcpyAsync(g->tri.get() + n_light, part.get(), nh * sizeof(uint4), cudaMemcpyDeviceToDevice, s));
+        if (n_huge) {
+            g->huge_eoff.alloc(n_huge + 1, s);
+            exclusive_scan_u64(he2.get() + n_hw + n_hc, g->huge_eoff.get(), n_huge, s);
+            g->huge_elems = read_scalar(g->huge_eoff.get() + n_huge, s);
+        }
+        TTC_CUDA(cudaStreamSynchronize(s));
+    }
+    st.tau_hwarp = n_hw;
+    st.tau_hcta = n_hc;
+    st.tau_huge = n_huge;
+    set_view(g, s);
     TTC_CUDA(cudaStreamSynchronize(s));
 }
 

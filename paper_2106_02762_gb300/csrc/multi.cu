@@ -1,0 +1,314 @@
+// ttc_count_multi: many resident graphs counted in one launch.
+//
+// A plan is built once per ordered set of graph handles: a device table of
+// the graphs (GraphView), exclusive prefixes over the graphs of their light
+// chunks and heavy records, per-graph delta and count slots, and scratch for
+// any graph with huge triangles.  The light kernel and the one-CTA-per-
+// triangle heavy kernel then each run once over all graphs (persistent grids
+// sized to the GPU), followed by the flat path of any graph with huge
+// triangles.  The whole sequence, including the delta upload and the count
+// download, is captured into a CUDA graph and replayed on later calls.
+//
+// The grid shapes (light CTAs per SM, heavy CTAs per SM) are chosen by a
+// small autotuner: on first use of a plan every candidate is timed on the
+// real graphs and the fastest is kept; results are cached per (GPU, plan
+// shape) in a JSON file ($TTC_TUNE_CACHE, default ~/.cache/ttc/tune.json).
+#include <sys/stat.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "graph.cuh"
+
+namespace ttc {
+void set_last_error(const std::string &m);
+void normalise(const ttc_delta &d, int64_t out[3]);
+
+}  // namespace ttc
+
+using namespace ttc;
+
+namespace {
+
+struct Shape {
+    int light_per_sm = 8, heavy_per_sm = 2;
+};
+
+// ---------------------------------------------------------------- tune cache
+std::mutex g_tune_mu;
+
+std::string tune_path() {
+    const char *p = getenv("TTC_TUNE_CACHE");
+    if (p && *p) return p;
+    const char *home = getenv("HOME");
+    return std::string(home && *home ? home : "/tmp") + "/.cache/ttc/tune.json";
+}
+
+// The cache is a flat JSON object {"key": [light, heavy], ...}.
+std::map<std::string, Shape> tune_load() {
+    std::map<std::string, Shape> m;
+    std::ifstream f(tune_path());
+    if (!f) return m;
+    std::stringstream ss;
+    ss << f.rdbuf();
+    const std::string s = ss.str();
+    size_t i = 0;
+    while ((i = s.find('"', i)) != std::string::npos) {
+        const size_t j = s.find('"', i + 1);
+        if (j == std::string::npos) break;
+        const std::string key = s.substr(i + 1, j - i - 1);
+        const size_t a = s.find('[', j), b = s.find(']', j);
+        if (a == std::string::npos || b == std::string::npos) break;
+        Shape sh;
+        if (sscanf(s.c_str() + a + 1, "%d , %d", &sh.light_per_sm, &sh.heavy_per_sm) == 2 && sh.light_per_sm > 0 &&
+            sh.heavy_per_sm > 0)
+            m[key] = sh;
+        i = b + 1;
+    }
+    return m;
+}
+
+void tune_store(const std::map<std::string, Shape> &m) {
+    const std::string path = tune_path();
+    std::string dir = path.substr(0, path.rfind('/'));
+    for (size_t k = 1; k <= dir.size(); k++)
+        if (k == dir.size() || dir[k] == '/') mkdir(dir.substr(0, k).c_str(), 0755);
+    const std::string tmp = path + ".tmp";
+    std::ofstream f(tmp);
+    if (!f) return;
+    f << "{";
+    bool first = true;
+    for (auto &kv : m) {
+        f << (first ? "\n" : ",\n") << "  \"" << kv.first << "\": [" << kv.second.light_per_sm << ", "
+          << kv.second.heavy_per_sm << "]";
+        first = false;
+    }
+    f << "\n}\n";
+    f.close();
+    rename(tmp.c_str(), path.c_str());
+}
+
+// ---------------------------------------------------------------- plans
+struct Plan {
+    std::vector<ttc_graph *> graphs;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    uint32_t G = 0;
+    MultiTable table{};
+    DevBuf<GraphView> gv;
+    DevBuf<uint64_t> chunk_pre, hwarp_pre, hcta_pre;
+    DevBuf<int64_t> dq;
+    DevBuf<unsigned long long> acc;  // [G][8] + overflow flag
+    std::vector<DevBuf<uint8_t>> huge_scratch;
+    int64_t *h_dq = nullptr;             // pinned
+    unsigned long long *h_acc = nullptr;  // pinned
+    Shape shape;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t last_use = 0;
+
+    ~Plan() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (stream) cudaStreamSynchronize(stream);
+        gv.reset(); chunk_pre.reset(); hwarp_pre.reset(); hcta_pre.reset(); dq.reset(); acc.reset();
+        huge_scratch.clear();
+        if (h_dq) cudaFreeHost(h_dq);
+        if (h_acc) cudaFreeHost(h_acc);
+        if (stream) cudaStreamDestroy(stream);
+    }
+
+    // everything one count needs, queued on `stream`
+    void enqueue(const Shape &sh) {
+        cudaStream_t s = stream;
+        TTC_CUDA(cudaMemcpyAsync(dq.get(), h_dq, 3 * (size_t)G * 8, cudaMemcpyHostToDevice, s));
+        TTC_CUDA(cudaMemsetAsync(acc.get(), 0, (8 * (size_t)G + 1) * 8, s));
+        count_multi_launch(table, dq.get(), acc.get(), sh.light_per_sm, sh.heavy_per_sm, s);
+        for (uint32_t i = 0, k = 0; i < G; i++) {
+            ttc_graph *g = graphs[i];
+            if (!g->st.tau_huge) continue;
+            count_huge_of(g, dq.get() + 3 * (size_t)i, acc.get() + 8 * (size_t)i, acc.get() + 8 * (size_t)G,
+                          huge_scratch[k++].get(), s);
+        }
+        TTC_CUDA(cudaMemcpyAsync(h_acc, acc.get(), (8 * (size_t)G + 1) * 8, cudaMemcpyDeviceToHost, s));
+    }
+
+    std::string tune_key() const {
+        int sms = sm_count();
+        cudaDeviceProp prop{};
+        cudaGetDeviceProperties(&prop, device);
+        char buf[512];
+        snprintf(buf, sizeof buf, "%s|sm%d|G%d|c%d|h%d|w%d", prop.name, sms, (int)std::log2((double)G + 1),
+                 (int)std::log2((double)table.chunks + 1), (int)std::log2((double)(table.hwarp + table.hcta) + 1),
+                 table.any_wide);
+        std::string k = buf;
+        std::replace(k.begin(), k.end(), '"', '\'');
+        return k;
+    }
+
+    // time every candidate shape on the real graphs and keep the fastest
+    void autotune() {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto cache = tune_load();
+        const std::string key = tune_key();
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            shape = it->second;
+            return;
+        }
+        cudaEvent_t a, b;
+        TTC_CUDA(cudaEventCreate(&a));
+        TTC_CUDA(cudaEventCreate(&b));
+        float best = 1e30f;
+        for (int lp : {4, 8, 16}) {
+            for (int hp : {1, 2, 4}) {
+                if (!(table.hwarp + table.hcta) && hp != 2) continue;
+                const Shape sh{lp, hp};
+                enqueue(sh);  // warm
+                TTC_CUDA(cudaEventRecord(a, stream));
+                for (int r = 0; r < 2; r++) enqueue(sh);
+                TTC_CUDA(cudaEventRecord(b, stream));
+                TTC_CUDA(cudaEventSynchronize(b));
+                float ms = 0;
+                TTC_CUDA(cudaEventElapsedTime(&ms, a, b));
+                if (ms < best) {
+                    best = ms;
+                    shape = sh;
+                }
+            }
+        }
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        cache[key] = shape;
+        tune_store(cache);
+    }
+
+    void capture() {
+        cudaGraph_t graph;
+        TTC_CUDA(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+        try {
+            enqueue(shape);
+        } catch (...) {
+            cudaStreamEndCapture(stream, &graph);
+            if (graph) cudaGraphDestroy(graph);
+            throw;
+        }
+        TTC_CUDA(cudaStreamEndCapture(stream, &graph));
+        const cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        TTC_CUDA(e);
+    }
+};
+
+std::mutex g_plan_mu;
+std::vector<std::unique_ptr<Plan>> g_plans;
+uint64_t g_plan_clock = 0;
+constexpr size_t MAX_PLANS = 4;
+
+Plan *build_plan(ttc_graph *const *gs, uint32_t G) {
+    auto p = std::make_unique<Plan>();
+    p->graphs.assign(gs, gs + G);
+    p->G = G;
+    TTC_CUDA(cudaGetDevice(&p->device));
+    TTC_CUDA(cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking));
+    cudaStream_t s = p->stream;
+    std::vector<GraphView> views(G);
+    std::vector<uint64_t> cpre(G + 1, 0), wpre(G + 1, 0), hpre(G + 1, 0);
+    MultiTable &t = p->table;
+    for (uint32_t i = 0; i < G; i++) {
+        ttc_graph *g = gs[i];
+        if (g->device != p->device) fail(TTC_ERR_INVALID, "graph %u lives on another device", i);
+        // make sure the graph's own stream has finished building it
+        TTC_CUDA(cudaStreamSynchronize(g->stream));
+        views[i] = g->view_host;
+        cpre[i + 1] = cpre[i] + (g->st.tau_light + 31) / 32;
+        wpre[i + 1] = wpre[i] + g->st.tau_hwarp;
+        hpre[i + 1] = hpre[i] + g->st.tau_hcta;
+        if (g->st.tau_hwarp + g->st.tau_hcta) (g->heavy_wide ? t.any_wide : t.any_narrow) = 1;
+        if (g->st.tau_huge) {
+            p->huge_scratch.emplace_back();
+            p->huge_scratch.back().alloc(heavy_scratch_bytes(g), s);
+        }
+    }
+    p->gv.alloc(G, s);
+    p->chunk_pre.alloc(G + 1, s);
+    p->hwarp_pre.alloc(G + 1, s);
+    p->hcta_pre.alloc(G + 1, s);
+    p->dq.alloc(3 * (size_t)G, s);
+    p->acc.alloc(8 * (size_t)G + 1, s);
+    TTC_CUDA(cudaMemcpyAsync(p->gv.get(), views.data(), sizeof(GraphView) * G, cudaMemcpyHostToDevice, s));
+    TTC_CUDA(cudaMemcpyAsync(p->chunk_pre.get(), cpre.data(), 8 * (G + 1), cudaMemcpyHostToDevice, s));
+    TTC_CUDA(cudaMemcpyAsync(p->hwarp_pre.get(), wpre.data(), 8 * (G + 1), cudaMemcpyHostToDevice, s));
+    TTC_CUDA(cudaMemcpyAsync(p->hcta_pre.get(), hpre.data(), 8 * (G + 1), cudaMemcpyHostToDevice, s));
+    t.gvs = p->gv.get();
+    t.G = G;
+    t.chunk_pre = p->chunk_pre.get();
+    t.hwarp_pre = p->hwarp_pre.get();
+    t.hcta_pre = p->hcta_pre.get();
+    t.chunks = cpre[G];
+    t.hwarp = wpre[G];
+    t.hcta = hpre[G];
+    TTC_CUDA(cudaMallocHost(&p->h_dq, 3 * (size_t)G * 8));
+    TTC_CUDA(cudaMallocHost(&p->h_acc, (8 * (size_t)G + 1) * 8));
+    TTC_CUDA(cudaStreamSynchronize(s));
+    return p.release();
+}
+
+}  // namespace
+
+namespace ttc {
+
+// Drops every cached plan that names g (called before g is freed).
+void multi_forget(ttc_graph *g) {
+    std::lock_guard<std::mutex> lock(g_plan_mu);
+    g_plans.erase(std::remove_if(g_plans.begin(), g_plans.end(),
+                                 [&](const std::unique_ptr<Plan> &p) {
+                                     return std::find(p->graphs.begin(), p->graphs.end(), g) != p->graphs.end();
+                                 }),
+                  g_plans.end());
+}
+
+void count_multi(ttc_graph *const *gs, const ttc_delta *d, uint32_t G, uint64_t *out) {
+    if (!G) return;
+    std::vector<int64_t> hq(3 * (size_t)G);
+    for (uint32_t i = 0; i < G; i++) {
+        if (!gs[i]) fail(TTC_ERR_INVALID, "graph %u is NULL", i);
+        normalise(d[i], &hq[3 * (size_t)i]);
+    }
+    std::lock_guard<std::mutex> lock(g_plan_mu);
+    Plan *plan = nullptr;
+    for (auto &p : g_plans)
+        if (p->G == G && std::equal(p->graphs.begin(), p->graphs.end(), gs)) plan = p.get();
+    if (!plan) {
+        if (g_plans.size() >= MAX_PLANS) {
+            auto oldest = std::min_element(g_plans.begin(), g_plans.end(),
+                                           [](const std::unique_ptr<Plan> &a, const std::unique_ptr<Plan> &b) {
+                                               return a->last_use < b->last_use;
+                                           });
+            g_plans.erase(oldest);
+        }
+        std::unique_ptr<Plan> p(build_plan(gs, G));
+        memcpy(p->h_dq, hq.data(), hq.size() * 8);
+        p->autotune();
+        p->capture();
+        g_plans.push_back(std::move(p));
+        plan = g_plans.back().get();
+    }
+    plan->last_use = ++g_plan_clock;
+    TTC_CUDA(cudaSetDevice(plan->device));
+    memcpy(plan->h_dq, hq.data(), hq.size() * 8);
+    TTC_CUDA(cudaGraphLaunch(plan->exec, plan->stream));
+    note_launch();
+    TTC_CUDA(cudaStreamSynchronize(plan->stream));
+    if (plan->h_acc[8 * (size_t)G]) fail(TTC_ERR_OVERFLOW, "a count exceeds 2^64 - 1");
+    memcpy(out, plan->h_acc, 8 * (size_t)G * 8);
+}
+
+}  // namespace ttc

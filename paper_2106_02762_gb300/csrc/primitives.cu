@@ -121,17 +121,27 @@ __global__ void __launch_bounds__(RS_THREADS)
     counts[(size_t)threadIdx.x * tiles + blockIdx.x] = hist[threadIdx.x];
 }
 
+// Stable scatter of one 8-bit digit.  Ranks come from warp-level match
+// masks in element order; the tile is first reordered by digit in shared
+// memory, then written out so that each digit's run is contiguous in global
+// memory (coalesced stores).
 template <typename V>
 __global__ void __launch_bounds__(RS_THREADS)
     radix_scatter_kernel(const uint64_t *keys_in, const V *vals_in, uint64_t *keys_out, V *vals_out,
                          size_t n, int shift, const uint32_t *offsets, unsigned tiles) {
     __shared__ uint32_t wcnt[RS_WARPS][RADIX];
+    __shared__ uint32_t dstart[RADIX];   // block-local start of each digit
+    __shared__ uint32_t gstart[RADIX];   // global start of each digit for this tile
+    __shared__ uint64_t s_key[RS_TILE];
+    __shared__ V s_val[RS_TILE];
     for (int i = threadIdx.x; i < RS_WARPS * RADIX; i += RS_THREADS) (&wcnt[0][0])[i] = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
-    const size_t base = (size_t)blockIdx.x * RS_TILE + (size_t)warp * RS_WARP_TILE;
+    const size_t tile_base = (size_t)blockIdx.x * RS_TILE;
+    const size_t base = tile_base + (size_t)warp * RS_WARP_TILE;
     uint64_t k[RS_ITEMS];
+    V v[RS_ITEMS];
     uint32_t local[RS_ITEMS];
     int dig[RS_ITEMS];
 #pragma unroll
@@ -139,6 +149,7 @@ __global__ void __launch_bounds__(RS_THREADS)
         const size_t idx = base + (size_t)i * 32 + lane;
         const bool ok = idx < n;
         k[i] = ok ? keys_in[idx] : 0;
+        v[i] = ok ? vals_in[idx] : V(0);
         dig[i] = ok ? (int)((k[i] >> shift) & (RADIX - 1)) : RADIX;  // RADIX = padding
         const unsigned peers = __match_any_sync(0xffffffffu, dig[i]);
         const int leader = __ffs(peers) - 1;
@@ -150,7 +161,7 @@ __global__ void __launch_bounds__(RS_THREADS)
         local[i] = b + __popc(peers & lt_mask);
     }
     __syncthreads();
-    {  // per digit: exclusive prefix over warps (warp order = element order)
+    {  // per digit: exclusive prefix over warps, and the digit's block total
         const int d = threadIdx.x;
         uint32_t run = 0;
 #pragma unroll
@@ -159,21 +170,33 @@ __global__ void __launch_bounds__(RS_THREADS)
             wcnt[w][d] = run;
             run += c;
         }
+        uint32_t total;
+        const uint32_t excl = block_exclusive_scan<uint32_t>(run, &total);
+        dstart[d] = excl;
+        gstart[d] = offsets[(size_t)d * tiles + blockIdx.x];
     }
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < RS_ITEMS; i++) {
         if (dig[i] == RADIX) continue;
-        const size_t idx = base + (size_t)i * 32 + lane;
-        const size_t pos = (size_t)offsets[(size_t)dig[i] * tiles + blockIdx.x] + wcnt[warp][dig[i]] + local[i];
-        keys_out[pos] = k[i];
-        vals_out[pos] = vals_in[idx];
+        const uint32_t pos = dstart[dig[i]] + wcnt[warp][dig[i]] + local[i];
+        s_key[pos] = k[i];
+        s_val[pos] = v[i];
+    }
+    __syncthreads();
+    const uint32_t count = (uint32_t)min((size_t)RS_TILE, n - tile_base);
+    for (uint32_t i = threadIdx.x; i < count; i += RS_THREADS) {
+        const uint64_t key = s_key[i];
+        const int d = (int)((key >> shift) & (RADIX - 1));
+        const size_t pos = (size_t)gstart[d] + (i - dstart[d]);
+        keys_out[pos] = key;
+        vals_out[pos] = s_val[i];
     }
 }
 
 template <typename V>
-void radix_sort_impl(uint64_t *keys, V *vals, size_t n, int bits, cudaStream_t s) {
-    if (n <= 1 || bits <= 0) return;
+void radix_sort_impl(uint64_t *keys, V *vals, size_t n, int begin_bit, int end_bit, cudaStream_t s) {
+    if (n <= 1 || end_bit <= begin_bit) return;
     if (n >= (size_t(1) << 32)) fail(TTC_ERR_RANGE, "radix sort: %zu elements exceed 2^32", n);
     const unsigned tiles = ceil_div(n, RS_TILE);
     DevBuf<uint64_t> kalt(n, s);
@@ -181,7 +204,7 @@ void radix_sort_impl(uint64_t *keys, V *vals, size_t n, int bits, cudaStream_t s
     DevBuf<uint32_t> counts((size_t)RADIX * tiles, s), offs((size_t)RADIX * tiles + 1, s);
     uint64_t *kin = keys, *kout = kalt.get();
     V *vin = vals, *vout = valt.get();
-    for (int shift = 0; shift < bits; shift += 8) {
+    for (int shift = begin_bit; shift < end_bit; shift += 8) {
         radix_hist_kernel<<<tiles, RS_THREADS, 0, s>>>(kin, n, shift, counts.get(), tiles);
         TTC_LAUNCH_CHECK();
         exclusive_scan_impl<uint32_t, uint32_t>(counts.get(), offs.get(), (size_t)RADIX * tiles, s);
@@ -232,10 +255,14 @@ void exclusive_scan_flags(const uint8_t *in, uint32_t *out, size_t n, cudaStream
     exclusive_scan_impl<uint32_t, uint8_t>(in, out, n, s);
 }
 void radix_sort_u64_u32(uint64_t *keys, uint32_t *vals, size_t n, int bits, cudaStream_t s) {
-    radix_sort_impl<uint32_t>(keys, vals, n, bits, s);
+    radix_sort_impl<uint32_t>(keys, vals, n, 0, bits, s);
 }
 void radix_sort_u64_u64(uint64_t *keys, uint64_t *vals, size_t n, int bits, cudaStream_t s) {
-    radix_sort_impl<uint64_t>(keys, vals, n, bits, s);
+    radix_sort_impl<uint64_t>(keys, vals, n, 0, bits, s);
+}
+void radix_sort_u64_u64_range(uint64_t *keys, uint64_t *vals, size_t n, int begin_bit, int end_bit,
+                              cudaStream_t s) {
+    radix_sort_impl<uint64_t>(keys, vals, n, begin_bit, end_bit, s);
 }
 void reduce_minmax_i64(const int64_t *in, size_t n, int64_t *dmin, int64_t *dmax, cudaStream_t s) {
     init_minmax_kernel<<<1, 1, 0, s>>>((long long *)dmin, (long long *)dmax);

@@ -29,6 +29,7 @@ LABEL_HEAVIEST_VW, LABEL_SOURCE = 0, 1
 EXPORTS = ["ttc_load", "ttc_load_ex", "ttc_free", "ttc_graph_info", "ttc_count", "ttc_count_batch",
            "ttc_count_batch_async", "ttc_count_multi", "ttc_count_sample", "ttc_server_create",
            "ttc_server_destroy", "ttc_serve_load", "ttc_serve_submit", "ttc_serve_poll", "ttc_serve_drain",
+           "ttc_serve_pause",
            "ttc_server_info", "ttc_last_error", "ttc_version", "ttc_debug_fail_alloc_after",
            "ttc_debug_launch_count", "ttc_set_profiling", "ttc_profile_read", "ttc_count_noalloc"]
 
@@ -51,7 +52,7 @@ class LoadOpts(ctypes.Structure):
 class GraphStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in
                 ("n", "m", "m_self_loops", "m_s", "tau", "kappa", "sigma_max", "peel_rounds", "work_bytes",
-                 "enum_elems", "tau_light", "tau_heavy", "device_bytes", "work_bytes_heavy")] + \
+                 "enum_elems", "tau_light", "tau_heavy", "device_bytes", "work_bytes_heavy", "tau_huge", "tau_hwarp", "tau_hcta")] + \
                [("key_bits", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
@@ -97,6 +98,7 @@ def lib():
             "ttc_serve_submit": ([p, u64, p, p], ctypes.c_int),
             "ttc_serve_poll": ([p, u64, p, p], ctypes.c_int),
             "ttc_serve_drain": ([p, ctypes.c_double], ctypes.c_int),
+            "ttc_serve_pause": ([p, ctypes.c_int], ctypes.c_int),
             "ttc_server_info": ([p, p], ctypes.c_int),
             "ttc_last_error": ([], ctypes.c_char_p),
             "ttc_version": ([], ctypes.c_char_p),
@@ -280,6 +282,9 @@ class Server:
         if st == PENDING:
             return None
         return out, lat.value
+
+    def pause(self, paused: bool = True):
+        check(lib().ttc_serve_pause(self._h, 1 if paused else 0))
 
     def drain(self, timeout_s: float = 60.0):
         check(lib().ttc_serve_drain(self._h, timeout_s))

@@ -1,0 +1,170 @@
+"""Batched, many-graph and served entry points against the oracle and
+against the plain single-query path (bit for bit)."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2106_02762_gb300 import synth, ttc
+
+pytestmark = pytest.mark.gpu
+
+BIG = 1 << 40
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built(tmp_path_factory):
+    import os
+    import __graft_entry__
+    __graft_entry__.build()
+    os.environ["TTC_TUNE_CACHE"] = str(tmp_path_factory.mktemp("tune") / "tune.json")
+
+
+def _small_graphs(count=6, seed=7):
+    n, pairs, deltas, seeds = synth.many_graph_specs(seed=seed, count=count, n_lo=200, n_hi=3000)
+    out = []
+    for i in range(count):
+        s, d, t = synth.many_graph(n[i], pairs[i], seeds[i])
+        out.append((s, d, t, tuple(int(x) for x in deltas[i])))
+    return out
+
+
+def _heavy_triangle_graph():
+    # three pairs of 1500 edges each (a huge prefix-sum triangle) plus a light fringe
+    rng = np.random.default_rng(3)
+    k = 1500
+    s = np.concatenate([np.zeros(k), np.ones(k), np.zeros(k), rng.integers(0, 3, 300)]).astype(np.uint32)
+    d = np.concatenate([np.ones(k), np.full(k, 2), np.full(k, 2), rng.integers(3, 40, 300)]).astype(np.uint32)
+    flip = rng.integers(0, 2, s.size).astype(bool)
+    s, d = np.where(flip, d, s), np.where(flip, s, d)
+    t = rng.integers(0, 20000, s.size).astype(np.int64)
+    return s, d, t
+
+
+def test_count_multi_matches_oracle_and_replays():
+    gs = _small_graphs()
+    gs.append(_heavy_triangle_graph() + ((2000, 900, 1500),))
+    handles = [ttc.Graph(s, d, t) for s, d, t, _ in gs]
+    handles.append(ttc.Graph(*gs[0][:3], light_max_pairs=1))  # every triangle on the prefix-sum path
+    gs.append(gs[0])
+    deltas = [q for *_, q in gs]
+    want = np.stack([oracle.count(s, d, t, [q])[0] for s, d, t, q in gs])
+    assert handles[-2].info()["tau_huge"] >= 1
+    got1 = ttc.count_multi(handles, deltas)
+    got2 = ttc.count_multi(handles, deltas)  # replay of the captured graph
+    assert (got1 == want).all()
+    assert (got2 == want).all()
+    # new deltas on the same plan
+    deltas2 = [(BIG, BIG, BIG)] * len(handles)
+    want2 = np.stack([oracle.count(s, d, t, [q])[0] for (s, d, t, _), q in zip(gs, deltas2)])
+    assert (ttc.count_multi(handles, deltas2) == want2).all()
+    # another order is another plan; a freed graph drops its plans
+    order = list(reversed(range(len(handles))))
+    assert (ttc.count_multi([handles[i] for i in order], [deltas[i] for i in order]) == want[order]).all()
+    handles[0].free()
+    rest = handles[1:]
+    assert (ttc.count_multi(rest, deltas[1:]) == want[1:]).all()
+    for h in rest:
+        h.free()
+
+
+def test_count_multi_equals_plain_calls():
+    gs = _small_graphs(count=12, seed=11)
+    handles = [ttc.Graph(s, d, t) for s, d, t, _ in gs]
+    deltas = [q for *_, q in gs]
+    multi = ttc.count_multi(handles, deltas)
+    plain = np.stack([h.count(q) for h, q in zip(handles, deltas)])
+    assert (multi == plain).all()
+    for h in handles:
+        h.free()
+
+
+def test_batch_equals_sequential_on_heavy_graph():
+    s, d, t = _heavy_triangle_graph()
+    g = ttc.Graph(s, d, t)
+    deltas = synth.delta_sweep(16, 10, 30000)
+    want = oracle.count(s, d, t, deltas)
+    assert (g.count_batch(deltas) == want).all()
+    assert (np.stack([g.count(q) for q in deltas]) == want).all()
+    g.free()
+
+
+def test_server_results_equal_alone_runs():
+    graphs = [synth.served_graph(m, 100 + j) for j, m in enumerate((20_000, 60_000, 150_000))]
+    alone = [ttc.Graph(*gr) for gr in graphs]
+    srv = ttc.Server(streams=3, max_batch=64)
+    ids = [srv.load(*gr) for gr in graphs]
+    rng = np.random.default_rng(9)
+    menu = [tuple(int(x) for x in synth.log_uniform_int(rng, 60, 2.6e6, size=3)) for _ in range(40)]
+    tickets = []
+    for i in range(600):
+        j = int(rng.integers(0, len(ids)))
+        q = menu[int(rng.integers(0, len(menu)))]
+        tickets.append((srv.submit(ids[j], q), j, q))
+        if i % 50 == 0:
+            time.sleep(0.001)  # arrivals while earlier batches are on the device
+    srv.drain(60.0)
+    expected = {}
+    for tk, j, q in tickets:
+        if (j, q) not in expected:
+            expected[(j, q)] = alone[j].count(q)
+        res = srv.poll(tk)
+        assert res is not None
+        counts, lat = res
+        assert (counts == expected[(j, q)]).all()
+        assert lat >= 0
+    info = srv.info()
+    assert info["completed"] == info["submitted"] == 600
+    assert info["launches"] < 600  # queries were batched
+    # a handful against the oracle directly
+    for (j, q), want in list(expected.items())[:3]:
+        assert (oracle.count(*graphs[j], [q])[0] == want).all()
+    with pytest.raises(ttc.TTCError, match="NOT_FOUND"):
+        srv.submit(12345, (1, 1, 1))
+    with pytest.raises(ttc.TTCError, match="NOT_FOUND"):
+        srv.poll(tickets[0][0])  # already collected
+    srv.close()
+    for g in alone:
+        g.free()
+
+
+def test_server_queue_limit_and_eviction():
+    import torch
+    gr1 = synth.served_graph(20_000, 1)
+    gr2 = synth.served_graph(20_000, 2)
+    srv = ttc.Server(streams=1, max_queue=4)
+    gid = srv.load(*gr1)
+    srv.pause(True)
+    tks = [srv.submit(gid, (100, 50, 50)) for _ in range(4)]
+    with pytest.raises(ttc.TTCError, match="BUSY"):
+        srv.submit(gid, (100, 50, 50))
+    assert srv.poll(tks[0]) is None  # still queued
+    with pytest.raises(ttc.TTCError, match="TIMEOUT"):
+        srv.drain(0.05)
+    srv.pause(False)
+    srv.drain(30.0)
+    want = oracle.count(*gr1, [(100, 50, 50)])[0]
+    for tk in tks:
+        assert (srv.poll(tk)[0] == want).all()
+    srv.close()
+    # admission: reserve all but about one graph's load estimate, so a
+    # second load must evict the idle first graph
+    torch.cuda.synchronize()
+    free, _ = torch.cuda.mem_get_info()
+    estimate = 96 * 20_000 + (64 << 20)
+    srv = ttc.Server(hbm_reserve_bytes=max(0, free - estimate - (1 << 20)))
+    try:
+        g1 = srv.load(*gr1)
+    except ttc.TTCError:
+        pytest.skip("device memory moved under the test")
+    g2 = srv.load(*gr2)
+    info = srv.info()
+    assert info["evictions"] >= 1 and info["graphs_resident"] == 1
+    with pytest.raises(ttc.TTCError, match="NOT_FOUND"):
+        srv.submit(g1, (1, 1, 1))
+    tk = srv.submit(g2, (100_000, 50_000, 50_000))
+    srv.drain(30.0)
+    counts, _ = srv.poll(tk)
+    assert (counts == oracle.count(*gr2, [(100_000, 50_000, 50_000)])[0]).all()
+    srv.close()
