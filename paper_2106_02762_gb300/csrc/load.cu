@@ -196,8 +196,9 @@ constexpr uint64_t MASK40 = (uint64_t(1) << 40) - 1;
 constexpr int PEEL_THREADS = 1024;
 constexpr int PEEL_RUN = 8;  // relaxed edges per thread per step
 
-// Appends v (with its adjacency length) to a frontier list; warp-aggregated.
-// Every lane of the warp must call it (pred selects the appending lanes).
+// Appends a frontier entry (the vertex's adjacency start, with its adjacency
+// length) to a frontier list; warp-aggregated.  Every lane of the warp must
+// call it (pred selects the appending lanes).
 __device__ __forceinline__ void push_frontier(bool pred, uint32_t v, uint32_t nadj, PeelSlot *sl, uint32_t *front,
                                               uint32_t *foff, uint32_t lane) {
     const uint64_t pk = pred ? ((uint64_t(1) << 40) | nadj) : 0;
@@ -305,15 +306,17 @@ __global__ void __launch_bounds__(PEEL_THREADS)
                 const uint32_t i = base + tid;
                 bool take = false;
                 uint32_t v = 0, na = 0;
+                uint32_t ab = 0;
                 if (i < rem_n) {
                     v = __ldcg(rem + i);
                     take = __ldcg(deg + v) <= k;
                     if (take) {
                         level[v] = round;
-                        na = adj_off[v + 1] - adj_off[v];
+                        ab = adj_off[v];
+                        na = adj_off[v + 1] - ab;
                     }
                 }
-                push_frontier(take, v, na, sl, front, foff, lane);
+                push_frontier(take, ab, na, sl, front, foff, lane);
             }
             r = end_phase();
             const uint64_t f = __ldcg(&r->front);
@@ -337,7 +340,7 @@ __global__ void __launch_bounds__(PEEL_THREADS)
                 uint32_t fi = lo;
                 uint32_t fbeg = __ldcg(foff + fi);
                 uint32_t fend = fi + 1 < fn ? __ldcg(foff + fi + 1) : fe;
-                uint32_t base = adj_off[__ldcg(front + fi)];
+                uint32_t base = __ldcg(front + fi);
 #pragma unroll
                 for (int j = 0; j < PEEL_RUN; j++) {
                     const uint32_t e = e0 + j;
@@ -347,7 +350,7 @@ __global__ void __launch_bounds__(PEEL_THREADS)
                             fi++;
                             fbeg = fend;
                             fend = fi + 1 < fn ? __ldcg(foff + fi + 1) : fe;
-                            base = adj_off[__ldcg(front + fi)];
+                            base = __ldcg(front + fi);
                         }
                         wv[j] = adj[base + (e - fbeg)];
                     }
@@ -365,12 +368,13 @@ __global__ void __launch_bounds__(PEEL_THREADS)
 #pragma unroll
             for (int j = 0; j < PEEL_RUN; j++) {
                 const bool push = live[j] && old[j] == k + 1;
-                uint32_t na = 0;
+                uint32_t na = 0, ab = 0;
                 if (push) {
                     level[wv[j]] = round + 1;
-                    na = adj_off[wv[j] + 1] - adj_off[wv[j]];
+                    ab = adj_off[wv[j]];
+                    na = adj_off[wv[j] + 1] - ab;
                 }
-                push_frontier(push, push ? wv[j] : 0, na, sl, front_next, foff_next, lane);
+                push_frontier(push, ab, na, sl, front_next, foff_next, lane);
             }
         }
         const PeelSlot *r = end_phase();
@@ -402,27 +406,61 @@ __global__ void tail_ids_kernel(const uint32_t *rem, uint32_t R, const int *deg,
     }
 }
 
-// Adjacency of the remaining vertices among themselves, in local ids; one
-// warp per vertex, neighbours kept in adjacency order.
-__global__ void tail_adj_kernel(const uint32_t *rem, uint32_t R, const uint32_t *adj_off, const uint32_t *adj,
-                                const uint32_t *level, const uint32_t *lid, const uint32_t *coff, uint16_t *cadj) {
-    const uint32_t lane = threadIdx.x & 31;
-    const unsigned lt_mask = (1u << lane) - 1u;
-    for (uint64_t i = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < R;
-         i += ((uint64_t)gridDim.x * blockDim.x) >> 5) {
+// Adjacency of the remaining vertices among themselves, in local ids.  The
+// full adjacency lists of the remaining vertices are cut into chunks of
+// TAIL_CHUNK entries (chunk_pre: exclusive prefix of chunks per vertex); one
+// CTA takes one chunk and appends the remaining neighbours to the vertex's
+// slice through a per-vertex cursor (order inside a slice is immaterial).
+constexpr uint32_t TAIL_CHUNK = 4096;
+
+__global__ void tail_chunks_kernel(const uint32_t *rem, uint32_t R, const uint32_t *adj_off, uint32_t *nchunk) {
+    GRID_STRIDE(i, (size_t)R) {
         const uint32_t v = rem[i];
-        uint32_t pos = coff[i];
-        for (uint32_t j0 = adj_off[v]; j0 < adj_off[v + 1]; j0 += 32) {
-            const uint32_t j = j0 + lane;
+        nchunk[i] = (adj_off[v + 1] - adj_off[v] + TAIL_CHUNK - 1) / TAIL_CHUNK;
+    }
+}
+
+__global__ void __launch_bounds__(256)
+    tail_adj_kernel(const uint32_t *rem, uint32_t R, const uint32_t *chunk_pre, const uint32_t *adj_off,
+                    const uint32_t *adj, const uint32_t *level, const uint32_t *lid, const uint32_t *coff,
+                    uint32_t *cursor, uint16_t *cadj) {
+    __shared__ uint32_t s_w[8];
+    __shared__ uint32_t s_base;
+    const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const uint32_t nchunks = chunk_pre[R];
+    for (uint32_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        uint32_t lo = 0, hi = R;  // vertex of chunk c: last i with chunk_pre[i] <= c
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (chunk_pre[mid] <= c) lo = mid; else hi = mid;
+        }
+        const uint32_t i = lo, v = rem[i];
+        const uint32_t b = adj_off[v] + (c - chunk_pre[i]) * TAIL_CHUNK;
+        const uint32_t e = min(adj_off[v + 1], b + TAIL_CHUNK);
+        for (uint32_t j0 = b; j0 < e; j0 += 256) {
+            const uint32_t j = j0 + threadIdx.x;
             bool keep = false;
-            uint32_t w = 0;
-            if (j < adj_off[v + 1]) {
-                w = adj[j];
-                keep = level[w] == UNSET;
+            uint32_t x = 0;
+            if (j < e) {
+                x = adj[j];
+                keep = level[x] == UNSET;
             }
             const unsigned bal = __ballot_sync(0xffffffffu, keep);
-            if (keep) cadj[pos + __popc(bal & lt_mask)] = (uint16_t)lid[w];
-            pos += __popc(bal);
+            if (lane == 0) s_w[w] = __popc(bal);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                uint32_t run = 0;
+                for (int k = 0; k < 8; k++) {
+                    const uint32_t t = s_w[k];
+                    s_w[k] = run;
+                    run += t;
+                }
+                s_base = run ? atomicAdd(cursor + i, run) : 0;
+            }
+            __syncthreads();
+            if (keep) cadj[coff[i] + s_base + s_w[w] + __popc(bal & lt_mask)] = (uint16_t)lid[x];
+            __syncthreads();
         }
     }
 }
@@ -659,105 +697,114 @@ __global__ void record_stats_kernel(const uint4 *rec, size_t tau, uint64_t n_lig
     }
 }
 
-// Triangle enumeration, warp-cooperative.  A warp takes 32 consecutive
-// oriented edges (u, v) and flattens the elements of their N+(v) lists into
-// one index space; each lane takes one element w per step and looks it up in
-// N+(u) by binary search (both lists sorted by id), so a hit is the triangle
-// <u, v, w> of Sec. 5.  COUNT pass: per edge, the number of light and heavy
-// records.  WRITE pass: the records, each at its edge's offset in its bin
-// plus its rank among the edge's hits of that bin (hits are ranked in
-// (step, lane) order, so the layout is deterministic).
+// Triangle enumeration (Sec. 5: for each oriented edge (u, v), each
+// w in N+(u) and N+(v) closes <u, v, w>).  One warp per source vertex u:
+// N+(u) is staged in the warp's shared memory (when it fits), the edges of u
+// are taken 32 at a time, and the elements of their N+(v) lists are
+// flattened across the lanes; each lane looks its element w up in N+(u) by
+// binary search.  COUNT pass: per oriented edge, its light and heavy records.
+// WRITE pass: the records, each at its edge's offset in its bin plus its rank
+// among that edge's hits of that bin (ranked in (step, lane) order, so the
+// layout is deterministic).
 constexpr int TRI_THREADS = 256;
 constexpr int TRI_WARPS = TRI_THREADS / 32;
+constexpr uint32_t TRI_NU_CAP = 1024;  // staged N+(u) entries per warp
 
 template <bool WRITE>
 __global__ void __launch_bounds__(TRI_THREADS)
-    tri_enum_kernel(const uint32_t *__restrict__ osrc, const uint32_t *__restrict__ onbr,
-                    const uint32_t *__restrict__ opair, const uint32_t *__restrict__ out_off, size_t ms, RecCtx rc,
-                    uint32_t *cnt_light, uint32_t *cnt_heavy, const uint64_t *light_off, const uint64_t *heavy_off,
-                    uint64_t heavy_base, uint4 *rec) {
+    tri_enum_kernel(const uint32_t *__restrict__ onbr, const uint32_t *__restrict__ opair,
+                    const uint32_t *__restrict__ out_off, uint32_t n, RecCtx rc, uint32_t *cnt_light,
+                    uint32_t *cnt_heavy, const uint64_t *light_off, const uint64_t *heavy_off, uint64_t heavy_base,
+                    uint4 *rec) {
+    __shared__ uint32_t s_nu[TRI_WARPS][TRI_NU_CAP];
     __shared__ uint32_t s_excl[TRI_WARPS][33];
-    __shared__ uint32_t s_u[TRI_WARPS][32], s_v[TRI_WARPS][32], s_vb[TRI_WARPS][32];
+    __shared__ uint32_t s_v[TRI_WARPS][32], s_vb[TRI_WARPS][32];
     __shared__ uint32_t s_run[TRI_WARPS][64];  // per edge slot: light, heavy hits so far
     const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
-    const uint64_t nchunks = (ms + 31) / 32;
-    for (uint64_t c = (uint64_t)blockIdx.x * TRI_WARPS + w; c < nchunks; c += (uint64_t)gridDim.x * TRI_WARPS) {
-        const uint64_t e = c * 32 + lane;
-        uint32_t len = 0;
-        if (e < ms) {
-            const uint32_t u = osrc[e], v = onbr[e];
-            s_u[w][lane] = u;
-            s_v[w][lane] = v;
-            s_vb[w][lane] = out_off[v];
-            len = out_off[v + 1] - out_off[v];
-        }
-        s_run[w][2 * lane] = 0;
-        s_run[w][2 * lane + 1] = 0;
-        uint32_t x = len;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= (uint32_t)o) x += y;
-        }
-        s_excl[w][lane] = x - len;
-        const uint32_t total = __shfl_sync(0xffffffffu, x, 31);
-        if (lane == 0) s_excl[w][32] = total;
+    for (uint64_t u = (uint64_t)blockIdx.x * TRI_WARPS + w; u < n; u += (uint64_t)gridDim.x * TRI_WARPS) {
+        const uint32_t ub = out_off[u], du = out_off[u + 1] - ub;
+        if (du < 2) continue;  // a triangle needs two out-neighbours of u
+        const bool staged = du <= TRI_NU_CAP;
+        if (staged)
+            for (uint32_t i = lane; i < du; i += 32) s_nu[w][i] = onbr[ub + i];
         __syncwarp();
-        for (uint32_t base = 0; base < total; base += 32) {
-            const uint32_t j = base + lane;
-            bool hit = false, heavy = false;
-            uint32_t slot = 0;
-            uint4 r = make_uint4(0, 0, 0, 0);
-            if (j < total) {
-                uint32_t o = 0;
+        const uint32_t *nu = staged ? s_nu[w] : onbr + ub;
+        for (uint32_t c0 = 0; c0 < du; c0 += 32) {
+            const uint32_t i = c0 + lane;
+            uint32_t len = 0;
+            if (i < du) {
+                const uint32_t v = nu[i];
+                s_v[w][lane] = v;
+                s_vb[w][lane] = out_off[v];
+                len = out_off[v + 1] - out_off[v];
+            }
+            s_run[w][2 * lane] = 0;
+            s_run[w][2 * lane + 1] = 0;
+            uint32_t x = len;
 #pragma unroll
-                for (uint32_t step = 16; step; step >>= 1)
-                    if (s_excl[w][o + step] <= j) o += step;
-                slot = o;
-                const uint32_t u = s_u[w][o];
-                const uint32_t jv = s_vb[w][o] + (j - s_excl[w][o]);
-                const uint32_t x3 = onbr[jv];
-                // binary search x3 in N+(u)
-                const uint32_t ub = out_off[u];
-                uint32_t lo = 0, n = out_off[u + 1] - ub;
-                while (n > 0) {
-                    const uint32_t half = n >> 1;
-                    if (onbr[ub + lo + half] < x3) {
-                        lo += half + 1;
-                        n -= half + 1;
-                    } else {
-                        n = half;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= (uint32_t)o) x += y;
+            }
+            s_excl[w][lane] = x - len;
+            const uint32_t total = __shfl_sync(0xffffffffu, x, 31);
+            if (lane == 0) s_excl[w][32] = total;
+            __syncwarp();
+            for (uint32_t base = 0; base < total; base += 32) {
+                const uint32_t j = base + lane;
+                bool hit = false, heavy = false;
+                uint32_t slot = 0;
+                uint4 r = make_uint4(0, 0, 0, 0);
+                if (j < total) {
+                    uint32_t o = 0;
+#pragma unroll
+                    for (uint32_t step = 16; step; step >>= 1)
+                        if (s_excl[w][o + step] <= j) o += step;
+                    slot = o;
+                    const uint32_t jv = s_vb[w][o] + (j - s_excl[w][o]);
+                    const uint32_t x3 = onbr[jv];
+                    uint32_t lo = 0, len2 = du;  // x3 in N+(u)
+                    while (len2 > 0) {
+                        const uint32_t half = len2 >> 1;
+                        if (nu[lo + half] < x3) {
+                            lo += half + 1;
+                            len2 -= half + 1;
+                        } else {
+                            len2 = half;
+                        }
+                    }
+                    if (lo < du && nu[lo] == x3) {
+                        hit = true;
+                        r = make_record(rc, (uint32_t)u, s_v[w][o], x3, opair[ub + c0 + o], opair[ub + lo], opair[jv],
+                                        &heavy);
                     }
                 }
-                if (lo < out_off[u + 1] - ub && onbr[ub + lo] == x3) {
-                    hit = true;
-                    r = make_record(rc, u, s_v[w][o], x3, opair[c * 32 + o], opair[ub + lo], opair[jv], &heavy);
+                const unsigned act = __ballot_sync(0xffffffffu, hit);
+                if (!act) continue;
+                const uint32_t key = slot * 2 + (heavy ? 1u : 0u);
+                const unsigned peers = __match_any_sync(0xffffffffu, hit ? key : 0xffffffffu) & act;
+                uint32_t rank = 0;
+                if (hit) rank = s_run[w][key] + __popc(peers & lt_mask);
+                __syncwarp();
+                if (hit && (peers & lt_mask) == 0) s_run[w][key] += __popc(peers);
+                __syncwarp();
+                if (WRITE && hit) {
+                    const uint64_t ee = ub + c0 + slot;
+                    const uint64_t pos = heavy ? heavy_base + heavy_off[ee] + rank : light_off[ee] + rank;
+                    rec[pos] = r;
                 }
             }
-            const unsigned act = __ballot_sync(0xffffffffu, hit);
-            if (!act) continue;
-            const uint32_t key = slot * 2 + (heavy ? 1u : 0u);
-            const unsigned peers = __match_any_sync(0xffffffffu, hit ? key : 0xffffffffu) & act;
-            uint32_t rank = 0;
-            if (hit) rank = s_run[w][key] + __popc(peers & lt_mask);
             __syncwarp();
-            if (hit && (peers & lt_mask) == 0) s_run[w][key] += __popc(peers);
-            __syncwarp();
-            if (WRITE && hit) {
-                const uint64_t ee = c * 32 + slot;
-                const uint64_t pos = heavy ? heavy_base + heavy_off[ee] + rank : light_off[ee] + rank;
-                rec[pos] = r;
+            if (!WRITE && i < du) {
+                cnt_light[ub + i] = s_run[w][2 * lane];
+                cnt_heavy[ub + i] = s_run[w][2 * lane + 1];
             }
+            __syncwarp();
         }
-        __syncwarp();
-        if (!WRITE && e < ms) {
-            cnt_light[e] = s_run[w][2 * lane];
-            cnt_heavy[e] = s_run[w][2 * lane + 1];
-        }
-        __syncwarp();
     }
 }
+
 
 // Heavy-bin class of each heavy record from its enumerated size: 0 = one
 // warp, 1 = one CTA, 2 = huge (flat path).
@@ -1036,8 +1083,13 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
             exclusive_scan_u32(cdeg.get(), coff.get(), R, s);
             const uint32_t ce = read_scalar(coff.get() + R, s);
             DevBuf<uint16_t> cadj(ce ? ce : 1, s);
-            tail_adj_kernel<<<grid_for((size_t)R * 32), TPB, 0, s>>>(rem, R, adj_off.get(), adj.get(), level.get(), lid,
-                                                                    coff.get(), cadj.get());
+            DevBuf<uint32_t> nchunk(R, s), chunk_pre(R + 1, s), cursor(R, s);
+            tail_chunks_kernel<<<grid_for(R), TPB, 0, s>>>(rem, R, adj_off.get(), nchunk.get());
+            TTC_LAUNCH_CHECK();
+            exclusive_scan_u32(nchunk.get(), chunk_pre.get(), R, s);
+            TTC_CUDA(cudaMemsetAsync(cursor.get(), 0, (size_t)R * 4, s));
+            tail_adj_kernel<<<sm_count() * 8, 256, 0, s>>>(rem, R, chunk_pre.get(), adj_off.get(), adj.get(),
+                                                           level.get(), lid, coff.get(), cursor.get(), cadj.get());
             TTC_LAUNCH_CHECK();
             TTC_CUDA(cudaFuncSetAttribute(peel_tail_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)TAIL_SMEM));
@@ -1077,10 +1129,12 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
 
     // ---- a6: triangles, written straight into the light and heavy bins
     RecCtx rc{g->poff.get(), g->pair_vtx.get(), g->labeling, g->light_max_pairs};
-    const unsigned tgrid = (unsigned)std::min<uint64_t>((ms + 255) / 256 + 1, (uint64_t)sm_count() * 16);
+    const unsigned tgrid = (unsigned)std::min<uint64_t>(n / TRI_WARPS + 1, (uint64_t)sm_count() * 8);
     DevBuf<uint32_t> cl(ms + 1, s), ch(ms + 1, s);
     DevBuf<uint64_t> loff(ms + 1, s), hoff(ms + 1, s), cl64(ms + 1, s), ch64(ms + 1, s);
-    tri_enum_kernel<false><<<tgrid, TRI_THREADS, 0, s>>>(osrc.get(), onbr.get(), opair.get(), out_off.get(), ms, rc,
+    TTC_CUDA(cudaMemsetAsync(cl.get(), 0, (ms + 1) * 4, s));
+    TTC_CUDA(cudaMemsetAsync(ch.get(), 0, (ms + 1) * 4, s));
+    tri_enum_kernel<false><<<tgrid, TRI_THREADS, 0, s>>>(onbr.get(), opair.get(), out_off.get(), (uint32_t)n, rc,
                                                         cl.get(), ch.get(), nullptr, nullptr, 0, nullptr);
     TTC_LAUNCH_CHECK();
     widen_kernel<<<grid_for(ms), TPB, 0, s>>>(cl.get(), ch.get(), ms, cl64.get(), ch64.get());
@@ -1096,8 +1150,8 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
     st.tau = tau;
     g->tri.alloc(tau, s);
     if (tau) {
-        tri_enum_kernel<true><<<tgrid, TRI_THREADS, 0, s>>>(osrc.get(), onbr.get(), opair.get(), out_off.get(), ms,
-                                                           rc, nullptr, nullptr, loff.get(), hoff.get(), n_light,
+        tri_enum_kernel<true><<<tgrid, TRI_THREADS, 0, s>>>(onbr.get(), opair.get(), out_off.get(), (uint32_t)n, rc,
+                                                           nullptr, nullptr, loff.get(), hoff.get(), n_light,
                                                            g->tri.get());
         TTC_LAUNCH_CHECK();
     }
