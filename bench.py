@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--graphs", type=int, default=4096, help="multi: number of graphs")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: query arrivals per second")
     ap.add_argument("--duration", type=float, default=20.0, help="serve: seconds of arrivals")
+    ap.add_argument("--load-rate", type=float, default=1.0, help="serve: new-graph loads per second")
     return ap.parse_args()
 
 
@@ -268,9 +269,19 @@ def run_multi(args):
         times.append(time.perf_counter() - w)
         assert (out == first).all()
     step = statistics.median(times)
+    # the same work as one plain ttc_count call per graph
+    seq = []
+    for _ in range(2):
+        torch.cuda.synchronize()
+        w = time.perf_counter()
+        outs = [g.count(q) for g, q in zip(graphs, dl)]
+        seq.append(time.perf_counter() - w)
+        assert (np.stack(outs) == first).all()
+    seq_s = min(seq)
     tau = sum(g.info()["tau"] for g in graphs)
     print(json.dumps({"mode": "multi", "metric": METRIC, "value": m_tot / step, "unit": UNIT, "graphs": args.graphs,
                       "m_total": m_tot, "tau_total": tau, "ms_per_launch": step * 1e3,
+                      "sequential_ms": seq_s * 1e3, "speedup_vs_sequential": seq_s / step,
                       "load_generate_s": load_s, "higher_is_better": True,
                       "config": {"workload": "many graphs: n log-uniform [1e3,1e5], degree U[4,32], Chung-Lu 2.3, "
                                              "Geometric(0.3) multiplicity, t uniform [0,1e7), one delta per graph"}}),
@@ -281,6 +292,11 @@ def run_multi(args):
 
 # ------------------------------------------------------------------ served
 def run_serve(args):
+    """Served pool: 16 resident graphs, Poisson query arrivals, and new-graph
+    loads at --load-rate per second admitted under an HBM budget (the pool's
+    resident bytes plus one arriving graph's load estimate), so arrivals evict
+    least recently used idle graphs."""
+    import threading
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -289,41 +305,92 @@ def run_serve(args):
     if args.scale != 1.0:
         ladder = [max(1000, int(x * args.scale)) for x in ladder]
     srv = ttc.Server(streams=4, max_batch=256)
-    ids, alone, m_tot = [], [], 0
+    ids, m_tot = [], 0
     for j, m in enumerate(ladder):
         gr = synth.served_graph(m, synth.MASTER_SEED + 5 + j)
         ids.append(srv.load(*gr))
         m_tot += gr[0].size
+        del gr
+    # arriving graphs: four distinct mid-ladder graphs, loaded in turn
+    arrive = [synth.served_graph(ladder[4 + 2 * j], synth.MASTER_SEED + 200 + j) for j in range(4)]
+    torch.cuda.synchronize()
+    ttc.release_cached()
+    free, _ = torch.cuda.mem_get_info()
+    est = max(96 * a[0].size + (64 << 20) for a in arrive)
+    srv.set_reserve(max(0, free - est))
     rng = synth.rng_for(synth.MASTER_SEED + 50)
     arrivals = synth.poisson_arrivals(synth.MASTER_SEED + 51, args.rate, args.duration)
-    picks = rng.integers(0, len(ids), size=arrivals.size)
+    picks = rng.random(size=arrivals.size)
     qs = synth.log_uniform_int(rng, 60, 2.6e6, size=(arrivals.size, 3))
-    # warm every graph once
-    for gid in ids:
+    for gid in ids:  # warm every graph once
         srv.submit(gid, (3600, 1800, 1800))
     srv.drain(60.0)
-    tickets = []
+    live = list(ids)
+    live_mu = threading.Lock()
+    load_log = []
+    stop = threading.Event()
+
+    def loader(t0):
+        k = 0
+        while not stop.is_set():
+            due = (k + 1) / args.load_rate
+            while time.perf_counter() - t0 < due and not stop.is_set():
+                time.sleep(0.001)
+            if stop.is_set():
+                break
+            w = time.perf_counter()
+            try:
+                gid = srv.load(*arrive[k % len(arrive)])
+                ok = True
+            except ttc.TTCError:
+                gid, ok = None, False
+            load_log.append((time.perf_counter() - w, ok))
+            if ok:
+                with live_mu:
+                    live.append(gid)
+            k += 1
+
+    tickets, missed = [], 0
     t0 = time.perf_counter()
-    for a, j, q in zip(arrivals, picks, qs):
+    th = threading.Thread(target=loader, args=(t0,), daemon=True)
+    th.start()
+    for a, u, q in zip(arrivals, picks, qs):
         while time.perf_counter() - t0 < a:
             pass
-        tickets.append(srv.submit(ids[j], tuple(int(x) for x in q)))
+        while True:
+            with live_mu:
+                gid = live[int(u * len(live)) % len(live)]
+            try:
+                tickets.append(srv.submit(gid, tuple(int(x) for x in q)))
+                break
+            except ttc.TTCError as e:
+                if "NOT_FOUND" not in str(e):
+                    raise
+                missed += 1  # evicted since it was picked: pick again
+                with live_mu:
+                    if gid in live:
+                        live.remove(gid)
+    stop.set()
     srv.drain(120.0)
     wall = time.perf_counter() - t0
-    lat = []
-    for tk in tickets:
-        r = srv.poll(tk)
-        lat.append(r[1])
-    lat = np.asarray(lat)
+    th.join(60.0)
+    lat = np.asarray([srv.poll(tk)[1] for tk in tickets])
     info = srv.info()
     srv.close()
+    loads_ok = [d for d, ok in load_log if ok]
     print(json.dumps({"mode": "serve", "metric": "served latency", "arrival_rate": args.rate,
                       "queries": len(tickets), "queries_per_s": len(tickets) / wall,
                       "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
                       "mean_ms": float(lat.mean() * 1e3), "launches": info["launches"],
                       "graphs": len(ids), "m_total": m_tot,
-                      "config": {"workload": "16 resident ER graphs, 1e5..1e8 edges (log-spaced), Poisson arrivals, "
-                                             "uniform graph, delta components log-uniform [60, 2.6e6] s"}}),
+                      "graph_loads": len(load_log), "graph_loads_admitted": len(loads_ok),
+                      "graph_load_ms_median": float(np.median(loads_ok) * 1e3) if loads_ok else None,
+                      "evictions": info["evictions"], "resubmits_after_eviction": missed,
+                      "hbm_headroom_bytes": int(est), "queue_depth_max": info["queue_depth_max"],
+                      "config": {"workload": "16 resident ER graphs, 1e5..1e8 edges (log-spaced), Poisson query "
+                                             "arrivals, uniform live graph, delta components log-uniform [60, 2.6e6] s; "
+                                             "graph loads at %g/s (ER, 6e5..1e7 edges) admitted with %.2f GB of headroom "
+                                             "free beyond the pool, LRU eviction" % (args.load_rate, est / 1e9)}}),
           flush=True)
 
 
@@ -397,7 +464,11 @@ def run_ours(args):
     value = ws * m / step_s
 
     # query only, on a resident graph (per-kernel times via CUDA events in the library)
-    g = ttc.Graph(d_src, d_dst, d_t, stream=sptr)
+    torch.cuda.synchronize()
+    w = time.perf_counter()
+    g = ttc.Graph(d_src, d_dst, d_t, stream=sptr, profile_load=True)
+    load_wall = time.perf_counter() - w
+    load_phases = {k: v for k, v in g.profile()}
     g.set_profiling(True)
     for _ in range(3):
         g.count(delta)
@@ -488,6 +559,7 @@ def run_ours(args):
                       "kernels_ms": {k: v * 1e3 for k, v in kern_avg.items()}},
             "query_unbounded": {"delta": list(unb), "edges_per_s": m / u_s, "ms": u_s * 1e3},
             "load_edges_per_s": m / max(1e-9, step_s - q_s),
+            "load_phases_ms": {"wall": load_wall * 1e3, **load_phases},
             "roofline": roof,
             "batched": batched,
             "e2e": e2e,

@@ -27,6 +27,13 @@
  *     ttc_last_error() gives a message for the calling thread.
  *   - Vertex ids must be < 2^31.  Timestamps must lie in [-2^62, 2^62] and
  *     every delta component in [0, 2^62].  m = 0 is valid and counts zero.
+ *   - The load packs each edge's (t - min t), a tie-break rank and its
+ *     direction into one 63-bit key.  The rank is the edge's input index
+ *     when that fits, else its rank among the edges with the same timestamp.
+ *     A graph whose span needs s bits and whose largest group of equal
+ *     timestamps needs r bits is refused with TTC_ERR_RANGE when
+ *     s + r + 1 > 63: a span of 2^62 or more always, a span of 2^61 or
+ *     more when some timestamp repeats.
  *   - Self-loops (src == dst) can never lie on a triangle and are dropped
  *     (and counted in the statistics).
  */
@@ -70,6 +77,8 @@ typedef enum {
 
 /* Load flags. */
 #define TTC_LOAD_DEVICE_INPUT 1u  /* src/dst/t are device pointers (same device) */
+#define TTC_LOAD_PROFILE 2u       /* time the load's phases (ttc_profile_read after
+                                     the load; profiling stays on for counts) */
 
 /* Vertex orderings used to orient the static graph.  Any acyclic orientation
  * gives identical counts; the degeneracy ordering (Sec. 3, Matula-Beck) bounds
@@ -227,6 +236,11 @@ ttc_status ttc_serve_poll(ttc_server *s, uint64_t ticket, uint64_t out[TTC_NUM_T
  * to completion. */
 ttc_status ttc_serve_pause(ttc_server *s, int paused);
 
+/* Change the device memory that admission keeps free (the server option
+ * hbm_reserve_bytes) for later ttc_serve_load calls.  Resident graphs stay;
+ * the next load evicts idle ones if it no longer fits. */
+ttc_status ttc_serve_set_reserve(ttc_server *s, uint64_t hbm_reserve_bytes);
+
 /* Block until every submitted query has completed, or timeout_s passes
  * (TTC_ERR_TIMEOUT). */
 ttc_status ttc_serve_drain(ttc_server *s, double timeout_s);
@@ -245,6 +259,21 @@ const char *ttc_last_error(void);
 
 /* Library version string. */
 const char *ttc_version(void);
+
+/* Device memory.  Every device allocation of the library comes from one
+ * stream-ordered pool per device that keeps freed blocks (of ttc_free and of
+ * a load's temporaries) mapped for reuse, so repeated loads do not map and
+ * unmap memory.  ttc_release_cached synchronises the calling thread's device
+ * and returns those cached blocks to it; *released (may be NULL) receives
+ * the bytes released.  Server admission counts cached bytes as free. */
+ttc_status ttc_release_cached(uint64_t *released);
+
+/* Device memory as admission sees it, for the calling thread's device:
+ * *device_free = free device memory (cudaMemGetInfo), *pool_reserved and
+ * *pool_used = bytes the library's pool has mapped and has handed out.
+ * Admission counts device_free + (pool_reserved - pool_used) as free.  Any
+ * pointer may be NULL. */
+ttc_status ttc_memory_info(uint64_t *device_free, uint64_t *pool_reserved, uint64_t *pool_used);
 
 /* Testing hook: make the n-th device allocation from now fail with
  * TTC_ERR_NOMEM (n = 0 disables).  Process-wide. */

@@ -33,18 +33,31 @@ def _headers():
     return max((os.path.getmtime(h) for h in hs), default=0.0)
 
 
+def count_source_hash() -> str:
+    """Short hash of the count kernels' source (csrc/count.cu and the shared
+    headers); profiles taken with ncu record it, so a stale profile can be
+    told from a current one."""
+    import hashlib
+    h = hashlib.sha1()
+    for f in ["count.cu", "graph.cuh", "common.cuh"]:
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(OUT, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
     hdr_t = _headers()
     cc = nvcc()
+    defs = ["-DTTC_COUNT_HASH=\"%s\"" % count_source_hash()]
 
     def compile_one(src):
         obj = os.path.join(OUT, os.path.basename(src) + ".o")
         if (not force and os.path.exists(obj)
                 and os.path.getmtime(obj) >= max(os.path.getmtime(src), hdr_t)):
             return obj, False
-        cmd = [cc, *ARCH, *FLAGS, "-c", src, "-o", obj + ".tmp"]
+        cmd = [cc, *ARCH, *FLAGS, *defs, "-c", src, "-o", obj + ".tmp"]
         if src.endswith(".cpp"):
             cmd = [cc, *FLAGS, "-x", "c++", "-c", src, "-o", obj + ".tmp"]
         r = subprocess.run(cmd, capture_output=True, text=True)

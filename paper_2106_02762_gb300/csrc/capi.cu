@@ -65,6 +65,8 @@ void cuda_check(cudaError_t e, const char *what, const char *file, int line) {
     fail(st, "%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
 }
 
+cudaMemPool_t library_pool();
+
 void *device_alloc(size_t bytes, cudaStream_t s) {
     uint64_t n = g_fail_after.load();
     while (n) {
@@ -74,13 +76,57 @@ void *device_alloc(size_t bytes, cudaStream_t s) {
         }
     }
     void *p = nullptr;
-    const cudaError_t e = cudaMallocAsync(&p, bytes, s);
+    cudaMemPool_t pool = library_pool();
+    cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, pool, s);
+    if (e != cudaSuccess) {
+        // give cached blocks back to the device and try once more
+        cudaGetLastError();
+        cudaStreamSynchronize(s);
+        cudaMemPoolTrimTo(pool, 0);
+        e = cudaMallocFromPoolAsync(&p, bytes, pool, s);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         fail(TTC_ERR_NOMEM, "device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
     }
     g_bytes += bytes;
     return p;
+}
+
+// One stream-ordered memory pool per device for everything the library
+// allocates.  Its release threshold is unbounded, so blocks freed by
+// ttc_free or by a load's temporaries are kept mapped and reused by the next
+// load instead of being unmapped at every stream synchronisation (the
+// default pool's behaviour).  pool_cached_bytes() reports what it holds
+// unused, which admission control counts as free.
+cudaMemPool_t library_pool() {
+    constexpr int MAXDEV = 64;
+    static cudaMemPool_t pools[MAXDEV] = {};
+    static std::mutex mu;
+    int dev = 0;
+    TTC_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= MAXDEV) fail(TTC_ERR_INTERNAL, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lk(mu);
+    if (!pools[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t p = nullptr;
+        TTC_CUDA(cudaMemPoolCreate(&p, &props));
+        uint64_t thr = UINT64_MAX;
+        TTC_CUDA(cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &thr));
+        pools[dev] = p;
+    }
+    return pools[dev];
+}
+
+uint64_t pool_cached_bytes() {
+    cudaMemPool_t p = library_pool();
+    uint64_t reserved = 0, used = 0;
+    TTC_CUDA(cudaMemPoolGetAttribute(p, cudaMemPoolAttrReservedMemCurrent, &reserved));
+    TTC_CUDA(cudaMemPoolGetAttribute(p, cudaMemPoolAttrUsedMemCurrent, &used));
+    return reserved > used ? reserved - used : 0;
 }
 
 void device_free(void *p, cudaStream_t s) {
@@ -137,6 +183,13 @@ using namespace ttc;
 namespace ttc {
 void multi_forget(ttc_graph *g);
 void count_multi(ttc_graph *const *gs, const ttc_delta *d, uint32_t G, uint64_t *out);
+
+// Device bytes a resident graph holds.
+uint64_t graph_device_bytes(const ttc_graph *g) {
+    return g->key.bytes() + g->fwd.bytes() + g->poff.bytes() + g->pair_vtx.bytes() + g->tri.bytes() +
+           g->huge_eoff.bytes() + g->view.bytes() + g->prefix.bytes() + g->acc.bytes() +
+           g->dq.bytes() + g->scratch.bytes();
+}
 }  // namespace ttc
 
 namespace {
@@ -156,12 +209,6 @@ void graph_destroy(ttc_graph *g) {
     if (s) cudaStreamSynchronize(s);
     if (g->own_stream && s) cudaStreamDestroy(s);
     delete g;
-}
-
-uint64_t graph_device_bytes(const ttc_graph *g) {
-    return g->key.bytes() + g->fwd.bytes() + g->poff.bytes() + g->pair_vtx.bytes() + g->tri.bytes() +
-           g->huge_eoff.bytes() + g->view.bytes() + g->prefix.bytes() + g->acc.bytes() +
-           g->dq.bytes() + g->scratch.bytes();
 }
 
 // Runs k normalised queries and copies the counts to out (host).
@@ -194,7 +241,44 @@ extern "C" {
 
 const char *ttc_last_error(void) { return g_last_error.c_str(); }
 
-const char *ttc_version(void) { return "ttc 0.1 (sm_103a)"; }
+#ifndef TTC_COUNT_HASH
+#define TTC_COUNT_HASH "unknown"
+#endif
+const char *ttc_version(void) { return "ttc 0.1 (sm_103a) count:" TTC_COUNT_HASH; }
+
+ttc_status ttc_release_cached(uint64_t *released) {
+    try {
+        cudaMemPool_t pool = library_pool();
+        uint64_t before = 0, after = 0;
+        TTC_CUDA(cudaDeviceSynchronize());
+        TTC_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &before));
+        TTC_CUDA(cudaMemPoolTrimTo(pool, 0));
+        TTC_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &after));
+        if (released) *released = before > after ? before - after : 0;
+        return TTC_OK;
+    } catch (const Failure &f) {
+        set_last_error(f.message);
+        return f.status;
+    }
+}
+
+ttc_status ttc_memory_info(uint64_t *device_free, uint64_t *pool_reserved, uint64_t *pool_used) {
+    try {
+        cudaMemPool_t pool = library_pool();
+        size_t free_b = 0, total_b = 0;
+        uint64_t reserved = 0, used = 0;
+        TTC_CUDA(cudaMemGetInfo(&free_b, &total_b));
+        TTC_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved));
+        TTC_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used));
+        if (device_free) *device_free = free_b;
+        if (pool_reserved) *pool_reserved = reserved;
+        if (pool_used) *pool_used = used;
+        return TTC_OK;
+    } catch (const Failure &f) {
+        set_last_error(f.message);
+        return f.status;
+    }
+}
 
 void ttc_debug_fail_alloc_after(uint64_t n) { g_fail_after.store(n); }
 
@@ -249,7 +333,8 @@ ttc_status ttc_load_ex(const uint32_t *src, const uint32_t *dst, const int64_t *
         lo.labeling = opts->labeling;
         lo.light_max_pairs = opts->light_max_pairs;
         lo.seed = opts->seed;
-        if (lo.flags & ~TTC_LOAD_DEVICE_INPUT) fail(TTC_ERR_INVALID, "unknown load flags 0x%x", lo.flags);
+        if (lo.flags & ~(TTC_LOAD_DEVICE_INPUT | TTC_LOAD_PROFILE))
+            fail(TTC_ERR_INVALID, "unknown load flags 0x%x", lo.flags);
     }
     g = new ttc_graph();
     TTC_CUDA(cudaGetDevice(&g->device));
@@ -259,6 +344,7 @@ ttc_status ttc_load_ex(const uint32_t *src, const uint32_t *dst, const int64_t *
         TTC_CUDA(cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking));
         g->own_stream = true;
     }
+    g->profiling = (lo.flags & TTC_LOAD_PROFILE) != 0;
     build_graph(g, src, dst, t, m, lo);
     g->st.device_bytes = graph_device_bytes(g);
     *out = g;

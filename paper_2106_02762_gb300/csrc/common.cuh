@@ -30,6 +30,8 @@ void note_launch();
 // hook that fails the n-th allocation.
 void *device_alloc(size_t bytes, cudaStream_t s);
 void device_free(void *p, cudaStream_t s);
+cudaMemPool_t library_pool();
+uint64_t pool_cached_bytes();
 uint64_t device_bytes_in_use();
 
 template <typename T>

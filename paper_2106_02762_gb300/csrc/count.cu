@@ -37,6 +37,7 @@
 //
 // Deltas arrive normalised (d12, d23 <= d13 <= d12 + d23); all counts are
 // unsigned 64-bit sums with carry detection.
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
@@ -276,7 +277,7 @@ template <int MODE>
 __global__ void __launch_bounds__(LIGHT_THREADS)
     light_kernel(const GraphView *__restrict__ gvs, const uint64_t *__restrict__ chunk_pre, uint32_t G,
                  const int64_t *dq, uint32_t nq, unsigned long long *out, unsigned long long *flag,
-                 const uint64_t *idx, uint64_t nidx) {
+                 const uint64_t *idx, uint64_t nidx, uint32_t qpw = 1) {
     __shared__ WarpTris wt;
     __shared__ unsigned long long s_acc[MODE == 0 ? 8 : 1][MODE == 0 ? 256 : 1];
     extern __shared__ unsigned long long s_bacc[];  // MODE 1: [nq * 8]
@@ -293,10 +294,16 @@ __global__ void __launch_bounds__(LIGHT_THREADS)
     uint32_t cur_g = 0xffffffffu;
     const uint64_t nchunks = MODE == 2 ? (nidx + 31) / 32 : __ldg(chunk_pre + G);
     const uint64_t gw = (uint64_t)blockIdx.x * LIGHT_WARPS + w, nw = (uint64_t)gridDim.x * LIGHT_WARPS;
-    int64_t gmax = 0;
-    if constexpr (MODE == 1)
-        for (uint32_t q = 0; q < nq; q++) gmax = max(gmax, dq[3 * q]);
-    for (uint64_t c = gw; c < nchunks; c += nw) {
+    // MODE 1: work items are (chunk, group of qpw queries), so small graphs
+    // still spread a large batch over many warps
+    const uint32_t ngroups = MODE == 1 ? (nq + qpw - 1) / qpw : 1u;
+    for (uint64_t item = gw; item < nchunks * ngroups; item += nw) {
+        const uint64_t c = item / ngroups;
+        const uint32_t q_beg = MODE == 1 ? (uint32_t)(item % ngroups) * qpw : 0u;
+        const uint32_t q_end = MODE == 1 ? min(nq, q_beg + qpw) : 1u;
+        int64_t gmax = 0;
+        if constexpr (MODE == 1)
+            for (uint32_t q = q_beg; q < q_end; q++) gmax = max(gmax, dq[3 * q]);
         const uint32_t g = MODE == 0 ? graph_of(chunk_pre, G, c) : 0u;
         if constexpr (MODE == 0) {
             if (g != cur_g) {
@@ -352,7 +359,7 @@ __global__ void __launch_bounds__(LIGHT_THREADS)
             const uint32_t dA = (uint32_t)(ka & 1) ^ (fl & TriRec::FLIP_A);
             const uint32_t dB = (uint32_t)(kb & 1) ^ ((fl & TriRec::FLIP_B) ? 1u : 0u);
             const uint32_t pa = cnt_key(C, ka), pb = cnt_key(C, kb);
-            for (uint32_t q = 0; q < (MODE == 1 ? nq : 1u); q++) {
+            for (uint32_t q = q_beg; q < q_end; q++) {
                 const Query Q = MODE == 1 ? load_query(dq, q) : Q0;
                 auto accq = [&](int type, uint32_t n) {
                     if constexpr (MODE == 0) add_checked(s_acc[type][threadIdx.x], n, ovf);
@@ -1046,9 +1053,14 @@ void count_graph(ttc_graph *g, const int64_t *dq, uint32_t k, unsigned long long
         } else {
             for (uint32_t q0 = 0; q0 < k; q0 += MAX_BATCH_SMEM_Q) {
                 const uint32_t nq = k - q0 < MAX_BATCH_SMEM_Q ? k - q0 : MAX_BATCH_SMEM_Q;
+                // enough (chunk, query group) items to fill the GPU, and no
+                // smaller groups than that: each group re-reads its chunk
+                const uint64_t want_items = (uint64_t)sm_count() * 8 * LIGHT_WARPS;
+                const uint32_t groups = (uint32_t)std::min<uint64_t>(nq, (want_items + chunks - 1) / chunks);
+                const uint32_t qpw = (nq + groups - 1) / groups;
                 prof_begin(g, s, "light_batch");
-                light_kernel<1><<<light_grid(chunks), LIGHT_THREADS, nq * 64, s>>>(
-                    gv, light_pre, 1, dq + 3 * (size_t)q0, nq, acc + 8 * (size_t)q0, flag, nullptr, 0);
+                light_kernel<1><<<light_grid(chunks * ((nq + qpw - 1) / qpw)), LIGHT_THREADS, nq * 64, s>>>(
+                    gv, light_pre, 1, dq + 3 * (size_t)q0, nq, acc + 8 * (size_t)q0, flag, nullptr, 0, qpw);
                 TTC_LAUNCH_CHECK();
                 prof_end(g, s);
             }

@@ -6,9 +6,10 @@
 //   a3 peel        degeneracy ordering by a bucketed parallel k-core peel
 //                  (Sec. 3, Matula-Beck); one thread-block cluster runs every
 //                  round, separated by cluster barriers
-//   a4 orient      DAG G< and its out-CSR, neighbours sorted by id
-//   a6 triangles   for each oriented edge (u, v): N+(u) intersected with
-//                  N+(v) (Sec. 5: u < v < w in the ordering)
+//   a4 orient      vertices renamed by rank in the ordering; DAG G< as an
+//                  out-CSR (lists sorted by rank) and an in-CSR
+//   a6 triangles   for each oriented edge u -> v: the part of N+(u) after v
+//                  intersected with N+(v) (Sec. 5: u < v < w in the ordering)
 //   records        per triangle the three pair ids, labelled for counting
 //                  (which pair is only searched) and split into the light
 //                  and heavy (prefix-sum) bins
@@ -170,6 +171,122 @@ __global__ void adj_fill_kernel(const uint2 *pv, size_t ms, uint32_t *cursor, ui
     }
 }
 
+
+// ---------------------------------------------------------------- per-pair key sort
+// After the pair sort each pair's edges are contiguous but in input order;
+// these kernels sort every pair's keys in place (keys are unique, so the
+// result does not depend on which unit sorts which pair).  Pairs of at most
+// 32 edges: one warp, a bitonic network in registers.  33..SEG_MID_CAP: one
+// warp, a bitonic network in that warp's slice of shared memory.  Larger, up
+// to SEG_BIG_CAP: one CTA, a bitonic network in shared memory.
+constexpr uint32_t SEG_MID_CAP = 1024;    // largest pair sorted by one warp
+constexpr int SEG_MID_WARPS = 4;      // 32 KB of shared memory per CTA
+constexpr uint32_t SEG_BIG_CAP = 16384;  // largest pair sorted by one CTA
+constexpr int SEG_BIG_THREADS = 1024;
+
+__global__ void seg_sort_small_kernel(int64_t *key, const uint32_t *poff, uint32_t ms) {
+    const uint32_t lane = threadIdx.x & 31;
+    for (uint64_t p = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < ms;
+         p += ((uint64_t)gridDim.x * blockDim.x) >> 5) {
+        const uint32_t b = poff[p], len = poff[p + 1] - b;
+        if (len <= 1 || len > 32) continue;  // warp-uniform
+        int64_t x = lane < len ? key[b + lane] : INT64_MAX;
+#pragma unroll
+        for (uint32_t k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+            for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+                const int64_t y = __shfl_xor_sync(0xffffffffu, x, j);
+                const bool keep_min = ((lane & j) == 0) == ((lane & k) == 0);
+                x = keep_min ? min(x, y) : max(x, y);
+            }
+        }
+        if (lane < len) key[b + lane] = x;
+    }
+}
+
+// Appends the pairs of more than 32 edges to the mid (<= SEG_MID_CAP) and big
+// lists (warp-aggregated; list order is immaterial) and records the longest.
+__global__ void seg_classify_kernel(const uint32_t *poff, uint32_t ms, uint32_t *mid, uint32_t *big,
+                                    unsigned int *counts, unsigned int *longest) {
+    const uint32_t lane = threadIdx.x & 31;
+    unsigned int mx = 0;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t span = (ms + 31) & ~uint64_t(31);  // whole warps stay in the loop
+    for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < span; p += stride) {
+        const uint32_t len = p < ms ? poff[p + 1] - poff[p] : 0;
+        mx = max(mx, len);
+        for (int c = 0; c < 2; c++) {
+            const bool take = c == 0 ? (len > 32 && len <= SEG_MID_CAP) : (len > SEG_MID_CAP);
+            const unsigned int bal = __ballot_sync(0xffffffffu, take);
+            if (!bal) continue;
+            unsigned int base = 0;
+            if (lane == 0) base = atomicAdd(&counts[c], (unsigned int)__popc(bal));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (take) (c == 0 ? mid : big)[base + __popc(bal & ((1u << lane) - 1))] = (uint32_t)p;
+        }
+    }
+    for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0 && mx) atomicMax(longest, mx);
+}
+
+__global__ void __launch_bounds__(SEG_MID_WARPS * 32)
+    seg_sort_mid_kernel(int64_t *key, const uint32_t *poff, const uint32_t *mid, uint32_t nmid) {
+    __shared__ int64_t s_all[SEG_MID_WARPS][SEG_MID_CAP];
+    const uint32_t lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    int64_t *s_k = s_all[wib];
+    for (uint64_t w = (uint64_t)blockIdx.x * SEG_MID_WARPS + wib; w < nmid; w += (uint64_t)gridDim.x * SEG_MID_WARPS) {
+        const uint32_t p = mid[w], b = poff[p], len = poff[p + 1] - b;
+        uint32_t n2 = 64;
+        while (n2 < len) n2 <<= 1;
+        for (uint32_t i = lane; i < n2; i += 32) s_k[i] = i < len ? key[b + i] : INT64_MAX;
+        __syncwarp();
+        const uint32_t half = n2 >> 1;
+        for (uint32_t k = 2; k <= n2; k <<= 1) {
+            for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+                for (uint32_t x = lane; x < half; x += 32) {
+                    const uint32_t i = ((x & ~(j - 1)) << 1) | (x & (j - 1)), l = i + j;
+                    const int64_t a = s_k[i], c = s_k[l];
+                    if ((a > c) == ((i & k) == 0)) {
+                        s_k[i] = c;
+                        s_k[l] = a;
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        for (uint32_t i = lane; i < len; i += 32) key[b + i] = s_k[i];
+        __syncwarp();
+    }
+}
+
+__global__ void __launch_bounds__(SEG_BIG_THREADS)
+    seg_sort_big_kernel(int64_t *key, const uint32_t *poff, const uint32_t *big, uint32_t nbig) {
+    extern __shared__ int64_t s_k[];
+    for (uint32_t bi = blockIdx.x; bi < nbig; bi += gridDim.x) {
+        const uint32_t p = big[bi], b = poff[p], len = poff[p + 1] - b;
+        uint32_t n2 = 2 * SEG_BIG_THREADS;
+        while (n2 < len) n2 <<= 1;
+        for (uint32_t i = threadIdx.x; i < n2; i += SEG_BIG_THREADS) s_k[i] = i < len ? key[b + i] : INT64_MAX;
+        __syncthreads();
+        const uint32_t half = n2 >> 1;
+        for (uint32_t k = 2; k <= n2; k <<= 1) {
+            for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+                for (uint32_t x = threadIdx.x; x < half; x += SEG_BIG_THREADS) {
+                    const uint32_t i = ((x & ~(j - 1)) << 1) | (x & (j - 1)), l = i + j;
+                    const int64_t a = s_k[i], c = s_k[l];
+                    if ((a > c) == ((i & k) == 0)) {
+                        s_k[i] = c;
+                        s_k[l] = a;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        for (uint32_t i = threadIdx.x; i < len; i += SEG_BIG_THREADS) key[b + i] = s_k[i];
+        __syncthreads();
+    }
+}
+
 // ---------------------------------------------------------------- k-core peel
 // Counters of one phase of the peel.  Phases rotate through three slots: the
 // slot of phase p is read by every thread after the barrier that ends p and
@@ -190,17 +307,40 @@ struct PeelCtl {
     unsigned int rem_n;    // vertices left at the hand-off
     unsigned int rem_in_b; // the remaining list is in remB (else remA)
     unsigned int pad;
+    unsigned int bar_count, bar_gen;  // grid barrier of the grid-wide stage
 };
 
 constexpr uint64_t MASK40 = (uint64_t(1) << 40) - 1;
 constexpr int PEEL_THREADS = 1024;
 constexpr int PEEL_RUN = 8;  // relaxed edges per thread per step
+constexpr uint32_t PEEL_CACHE = 8192;  // frontier entries cached in shared memory
+constexpr uint32_t PEEL_GRID_STOP = 65536;  // the grid-wide stage hands off at this many vertices
 
-// Appends a frontier entry (the vertex's adjacency start, with its adjacency
-// length) to a frontier list; warp-aggregated.  Every lane of the warp must
-// call it (pred selects the appending lanes).
-__device__ __forceinline__ void push_frontier(bool pred, uint32_t v, uint32_t nadj, PeelSlot *sl, uint32_t *front,
-                                              uint32_t *foff, uint32_t lane) {
+// Frontier pushes of one CTA are staged in its shared memory and reach the
+// global frontier with one device-memory atomic per CTA and phase (flush), so
+// no counter in device memory is hit by every warp.  An entry is a vertex's
+// adjacency start with its adjacency length; reservations are packed
+// (entries << 40 | adjacency total).  A reservation that would overflow the
+// stage goes straight to the global frontier instead.
+constexpr uint32_t PEEL_STAGE = 4096;  // staged entries per CTA
+constexpr size_t PEEL_SMEM = (size_t)(2 * PEEL_CACHE + 2 * PEEL_STAGE) * 4;  // dynamic shared memory
+
+struct PeelStage {
+    unsigned long long cnt;  // reserved in the stage (packed)
+    unsigned long long cut;  // first reservation that did not fit (packed), or ~0
+    unsigned long long gbase;
+    unsigned long long total;
+    unsigned int rem;        // compaction: kept vertices staged
+    unsigned int rem_cut;    // compaction: first reservation that did not fit, or ~0
+    unsigned int rem_gbase;
+    unsigned int rem_total;
+    int min_deg;
+};
+
+// Every lane of the warp must call it (pred selects the appending lanes).
+__device__ __forceinline__ void push_frontier(bool pred, uint32_t ab, uint32_t nadj, PeelSlot *sl, uint32_t *front,
+                                              uint32_t *foff, uint32_t lane, PeelStage *st, uint32_t *s_ab,
+                                              uint32_t *s_off) {
     const uint64_t pk = pred ? ((uint64_t(1) << 40) | nadj) : 0;
     uint64_t x = pk;
 #pragma unroll
@@ -209,16 +349,103 @@ __device__ __forceinline__ void push_frontier(bool pred, uint32_t v, uint32_t na
         if (lane >= (uint32_t)o) x += y;
     }
     const uint64_t tot = __shfl_sync(0xffffffffu, x, 31);
+    if (!tot) return;
     uint64_t base = 0;
-    if (lane == 31 && tot) base = atomicAdd(&sl->front, (unsigned long long)tot);
+    int staged = 0;
+    if (lane == 31) {
+        base = atomicAdd(&st->cnt, (unsigned long long)tot);
+        if ((base >> 40) + (tot >> 40) <= PEEL_STAGE) {
+            staged = 1;
+        } else {
+            atomicMin(&st->cut, (unsigned long long)base);
+            base = atomicAdd(&sl->front, (unsigned long long)tot);
+        }
+    }
     base = __shfl_sync(0xffffffffu, base, 31);
+    staged = __shfl_sync(0xffffffffu, staged, 31);
     if (pred) {
         const uint64_t mine = base + x - pk;
         const uint32_t fi = (uint32_t)(mine >> 40);
-        front[fi] = v;
-        foff[fi] = (uint32_t)(mine & MASK40);
+        if (staged) {
+            s_ab[fi] = ab;
+            s_off[fi] = (uint32_t)(mine & MASK40);
+        } else {
+            front[fi] = ab;
+            foff[fi] = (uint32_t)(mine & MASK40);
+        }
     }
 }
+
+// Copies the CTA's staged frontier entries to the global frontier (one
+// reservation) and resets the stage.  Every thread of the CTA calls it.
+__device__ __forceinline__ void flush_frontier(PeelSlot *sl, uint32_t *front, uint32_t *foff, PeelStage *st,
+                                               const uint32_t *s_ab, const uint32_t *s_off) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned long long t = st->cnt < st->cut ? st->cnt : st->cut;
+        st->total = t;
+        st->gbase = t ? atomicAdd(&sl->front, t) : 0;
+        st->cnt = 0;
+        st->cut = ~0ull;
+    }
+    __syncthreads();
+    const uint32_t n = (uint32_t)(st->total >> 40), fb = (uint32_t)(st->gbase >> 40);
+    const uint32_t eb = (uint32_t)(st->gbase & MASK40);
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+        front[fb + i] = s_ab[i];
+        foff[fb + i] = eb + s_off[i];
+    }
+}
+
+// Phase barriers of the peel.  ClusterSync: one thread-block cluster
+// (hardware barrier).  GridSync: every CTA of a cooperative launch, through
+// an arrival counter and a generation word in device memory; the wait is
+// bounded, and a CTA that gives up reports failure so the kernel can stop.
+constexpr uint32_t GRID_BAR_SPIN = 1u << 24;
+
+struct ClusterSync {
+    cg::cluster_group cl = cg::this_cluster();
+    __device__ uint32_t nthreads() const { return cl.num_blocks() * blockDim.x; }
+    __device__ uint32_t rank() const { return cl.block_rank() * blockDim.x + threadIdx.x; }
+    __device__ bool sync(PeelCtl *) {
+        cl.sync();
+        return true;
+    }
+};
+
+struct GridSync {
+    uint32_t gen = 0;
+    __device__ uint32_t nthreads() const { return gridDim.x * blockDim.x; }
+    __device__ uint32_t rank() const { return blockIdx.x * blockDim.x + threadIdx.x; }
+    __device__ bool sync(PeelCtl *ctl) {
+        __shared__ int s_ok;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int ok = 1;
+            __threadfence();
+            const unsigned arrived = atomicAdd(&ctl->bar_count, 1u) + 1u;
+            if (arrived == gridDim.x) {
+                atomicExch(&ctl->bar_count, 0u);
+                __threadfence();
+                atomicExch(&ctl->bar_gen, gen + 1);
+            } else {
+                uint32_t spins = 0;
+                while (atomicAdd(&ctl->bar_gen, 0u) == gen) {
+                    if (++spins > GRID_BAR_SPIN) {
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+            __threadfence();
+            s_ok = ok;
+        }
+        gen++;
+        __syncthreads();
+        return s_ok != 0;
+    }
+};
 
 // Level-synchronous bucketed peel (Sec. 3, degeneracy ordering).  At level k
 // the frontier is every remaining vertex of degree <= k; removing it lowers
@@ -227,28 +454,62 @@ __device__ __forceinline__ void push_frontier(bool pred, uint32_t v, uint32_t na
 // round empties the frontier, the remaining set is compacted and k rises to
 // its smallest degree.  level[v] = round of removal; orienting every pair
 // from the lower (round, id) to the higher gives each vertex at most k <=
-// kappa out-neighbours.  All rounds run in one thread-block cluster,
-// separated by cluster barriers; every control decision is uniform.
+// kappa out-neighbours.  The rounds run in stages of falling width: every
+// SM (GridSync) while many vertices remain, then one thread-block cluster
+// (ClusterSync), then one CTA (peel_tail_kernel).  A stage stops at the first
+// level boundary with at most tail_n vertices left and records where it
+// stopped in ctl; the next stage resumes from there.  Every control decision
+// is uniform.
+template <typename Sync>
 __global__ void __launch_bounds__(PEEL_THREADS)
     peel_kernel(const uint32_t *__restrict__ adj_off, const uint32_t *__restrict__ adj, int *deg,
                 uint32_t *level, uint32_t *remA, uint32_t *remB, uint32_t *frontA, uint32_t *frontB,
-                uint32_t *foffA, uint32_t *foffB, uint32_t n, uint32_t tail_n, PeelCtl *ctl) {
-    cg::cluster_group cluster = cg::this_cluster();
-    const uint32_t nthr = cluster.num_blocks() * blockDim.x;
-    const uint32_t tid = cluster.block_rank() * blockDim.x + threadIdx.x;
+                uint32_t *foffA, uint32_t *foffB, uint32_t n, uint32_t tail_n, int resume, PeelCtl *ctl) {
+    Sync bar;
+    const uint32_t nthr = bar.nthreads();
+    const uint32_t tid = bar.rank();
     const uint32_t lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
+    extern __shared__ uint32_t peel_smem[];
+    uint32_t *s_foff = peel_smem, *s_front = peel_smem + PEEL_CACHE;
+    uint32_t *s_ab = peel_smem + 2 * PEEL_CACHE, *s_off = s_ab + PEEL_STAGE;
+    __shared__ PeelStage stg;
+    if (threadIdx.x == 0) {
+        stg.cnt = 0;
+        stg.cut = ~0ull;
+        stg.rem = 0;
+        stg.rem_cut = ~0u;
+        stg.min_deg = INT_MAX;
+    }
+    __syncthreads();
     uint32_t *rem = remA, *rem_next = remB;
     uint32_t *front = frontA, *front_next = frontB, *foff = foffA, *foff_next = foffB;
     uint32_t rem_n = n, fn = 0, fe = 0;
     bool identity = true;  // the remaining set is 0..n-1 until the first compaction
     int k = 0;
     uint32_t round = 0, kappa = 0, ph = 0;
+    bool stopped = false;  // handed the rest to the next stage
+    if (resume) {  // continue where the previous stage stopped
+        if (!__ldcg(&ctl->handoff) || __ldcg(&ctl->error)) return;  // nothing left, or it failed
+        k = __ldcg(&ctl->k);
+        round = __ldcg(&ctl->rounds);
+        kappa = __ldcg(&ctl->kappa);
+        rem_n = __ldcg(&ctl->rem_n);
+        identity = false;
+        if (__ldcg(&ctl->rem_in_b)) {
+            rem = remB;
+            rem_next = remA;
+        }
+    }
     const uint64_t ph_cap = 3ull * n + 8;
     bool ok = true;
     // ends phase ph: barrier, then zero the slot of phase ph + 2
+    // (nullptr: a barrier gave up; the kernel stops at once)
     auto end_phase = [&]() -> PeelSlot * {
-        cluster.sync();
+        if (!bar.sync(ctl)) {
+            ok = false;
+            return nullptr;
+        }
         PeelSlot *cur = &ctl->slot[ph % 3];
         if (tid == 0) {
             PeelSlot *z = &ctl->slot[(ph + 2) % 3];
@@ -276,27 +537,56 @@ __global__ void __launch_bounds__(PEEL_THREADS)
                 }
                 const unsigned bal = __ballot_sync(0xffffffffu, keep);
                 uint32_t b = 0;
-                if (lane == 0 && bal) b = atomicAdd(&sl->rem_n, (unsigned)__popc(bal));
+                int staged = 0;
+                if (lane == 0 && bal) {
+                    const unsigned c = (unsigned)__popc(bal);
+                    b = atomicAdd(&stg.rem, c);
+                    if (b + c <= PEEL_STAGE) {
+                        staged = 1;
+                    } else {
+                        atomicMin(&stg.rem_cut, b);
+                        b = atomicAdd(&sl->rem_n, c);
+                    }
+                }
                 b = __shfl_sync(0xffffffffu, b, 0);
-                if (keep) rem_next[b + __popc(bal & lt_mask)] = v;
+                staged = __shfl_sync(0xffffffffu, staged, 0);
+                if (keep) {
+                    const uint32_t at = b + __popc(bal & lt_mask);
+                    if (staged) s_ab[at] = v; else rem_next[at] = v;
+                }
             }
 #pragma unroll
             for (int o = 16; o; o >>= 1) my_min = min(my_min, __shfl_xor_sync(0xffffffffu, my_min, o));
-            if (lane == 0 && my_min != INT_MAX) atomicMin(&sl->min_deg, my_min);
+            if (lane == 0 && my_min != INT_MAX) atomicMin(&stg.min_deg, my_min);
+            // one reservation and one minimum per CTA
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                const unsigned t = min(stg.rem, stg.rem_cut);
+                stg.rem_total = t;
+                stg.rem_gbase = t ? atomicAdd(&sl->rem_n, t) : 0;
+                if (stg.min_deg != INT_MAX) atomicMin(&sl->min_deg, stg.min_deg);
+                stg.rem = 0;
+                stg.rem_cut = ~0u;
+                stg.min_deg = INT_MAX;
+            }
+            __syncthreads();
+            for (uint32_t i = threadIdx.x; i < stg.rem_total; i += blockDim.x) rem_next[stg.rem_gbase + i] = s_ab[i];
             const PeelSlot *r = end_phase();
+            if (!r) break;
             rem_n = __ldcg(&r->rem_n);
             const int md = __ldcg(&r->min_deg);
             identity = false;
             uint32_t *t = rem; rem = rem_next; rem_next = t;
             if (rem_n == 0) break;
             k = max(k, md);
-            if (rem_n <= tail_n) {  // the rest fits one CTA's shared memory
+            if (rem_n <= tail_n) {  // hand the rest to the next, narrower stage
                 if (tid == 0) {
                     ctl->handoff = 1;
                     ctl->k = k;
                     ctl->rem_n = rem_n;
                     ctl->rem_in_b = rem == remB;
                 }
+                stopped = true;
                 break;
             }
             kappa = max(kappa, (uint32_t)k);
@@ -316,9 +606,11 @@ __global__ void __launch_bounds__(PEEL_THREADS)
                         na = adj_off[v + 1] - ab;
                     }
                 }
-                push_frontier(take, ab, na, sl, front, foff, lane);
+                push_frontier(take, ab, na, sl, front, foff, lane, &stg, s_ab, s_off);
             }
+            flush_frontier(sl, front, foff, &stg, s_ab, s_off);
             r = end_phase();
+            if (!r) break;
             const uint64_t f = __ldcg(&r->front);
             fn = (uint32_t)(f >> 40);
             fe = (uint32_t)(f & MASK40);
@@ -327,6 +619,18 @@ __global__ void __launch_bounds__(PEEL_THREADS)
         // PEEL_RUN consecutive edges and issues their loads and atomics as
         // independent batches, so one round costs a few memory latencies.
         PeelSlot *sl = &ctl->slot[ph % 3];
+        // small frontiers are copied into every CTA's shared memory first, so
+        // the per-edge searches below cost no device-memory latency
+        const bool cached = fn <= PEEL_CACHE;
+        if (cached) {
+            for (uint32_t i = threadIdx.x; i < fn; i += blockDim.x) {
+                s_foff[i] = __ldcg(foff + i);
+                s_front[i] = __ldcg(front + i);
+            }
+            __syncthreads();
+        }
+        auto ld_foff = [&](uint32_t i) { return cached ? s_foff[i] : __ldcg(foff + i); };
+        auto ld_front = [&](uint32_t i) { return cached ? s_front[i] : __ldcg(front + i); };
         for (uint32_t e0 = tid * PEEL_RUN; e0 - tid * PEEL_RUN < fe; e0 += nthr * PEEL_RUN) {
             // the loop bound keeps every lane of a warp iterating together
             uint32_t wv[PEEL_RUN];
@@ -335,12 +639,12 @@ __global__ void __launch_bounds__(PEEL_THREADS)
                 uint32_t lo = 0, hi = fn;  // last fi with foff[fi] <= e0
                 while (hi - lo > 1) {
                     const uint32_t mid = (lo + hi) >> 1;
-                    if (__ldcg(foff + mid) <= e0) lo = mid; else hi = mid;
+                    if (ld_foff(mid) <= e0) lo = mid; else hi = mid;
                 }
                 uint32_t fi = lo;
-                uint32_t fbeg = __ldcg(foff + fi);
-                uint32_t fend = fi + 1 < fn ? __ldcg(foff + fi + 1) : fe;
-                uint32_t base = __ldcg(front + fi);
+                uint32_t fbeg = ld_foff(fi);
+                uint32_t fend = fi + 1 < fn ? ld_foff(fi + 1) : fe;
+                uint32_t base = ld_front(fi);
 #pragma unroll
                 for (int j = 0; j < PEEL_RUN; j++) {
                     const uint32_t e = e0 + j;
@@ -349,8 +653,8 @@ __global__ void __launch_bounds__(PEEL_THREADS)
                         while (e >= fend) {
                             fi++;
                             fbeg = fend;
-                            fend = fi + 1 < fn ? __ldcg(foff + fi + 1) : fe;
-                            base = __ldcg(front + fi);
+                            fend = fi + 1 < fn ? ld_foff(fi + 1) : fe;
+                            base = ld_front(fi);
                         }
                         wv[j] = adj[base + (e - fbeg)];
                     }
@@ -374,10 +678,12 @@ __global__ void __launch_bounds__(PEEL_THREADS)
                     ab = adj_off[wv[j]];
                     na = adj_off[wv[j] + 1] - ab;
                 }
-                push_frontier(push, ab, na, sl, front_next, foff_next, lane);
+                push_frontier(push, ab, na, sl, front_next, foff_next, lane, &stg, s_ab, s_off);
             }
         }
+        flush_frontier(sl, front_next, foff_next, &stg, s_ab, s_off);
         const PeelSlot *r = end_phase();
+        if (!r) break;
         const uint64_t f = __ldcg(&r->front);
         fn = (uint32_t)(f >> 40);
         fe = (uint32_t)(f & MASK40);
@@ -388,8 +694,21 @@ __global__ void __launch_bounds__(PEEL_THREADS)
     if (tid == 0) {
         ctl->rounds = round;
         ctl->kappa = kappa;
+        if (!stopped) ctl->handoff = 0;
         if (!ok) ctl->error = 1;
     }
+}
+
+// Prepares the control block for the next peel stage: phase slots and the
+// grid barrier start over; the hand-off state is kept.
+__global__ void peel_stage_reset_kernel(PeelCtl *ctl) {
+    for (int i = 0; i < 3; i++) {
+        ctl->slot[i].front = 0;
+        ctl->slot[i].rem_n = 0;
+        ctl->slot[i].min_deg = INT_MAX;
+    }
+    ctl->bar_count = 0;
+    ctl->bar_gen = 0;
 }
 
 
@@ -591,44 +910,82 @@ __device__ __forceinline__ uint32_t mix32(uint64_t x) {
     return (uint32_t)(x ^ (x >> 31));
 }
 
+// Ordering key of each vertex (ties by id come from the stable sort of the
+// identity permutation): its peel level, degree, a hash, or nothing (id).
 __global__ void order_key_kernel(uint32_t n, uint32_t orientation, const uint32_t *level, const unsigned int *deg,
-                                 uint64_t seed, uint64_t *rk) {
+                                 uint64_t seed, uint64_t *hi_out, uint32_t *ident, unsigned int *hi_max) {
+    unsigned int mx = 0;
     GRID_STRIDE(v, (size_t)n) {
-        uint64_t hi;
+        uint32_t hi;
         switch (orientation) {
             case TTC_ORIENT_ID: hi = 0; break;
             case TTC_ORIENT_DEGREE: hi = deg[v]; break;
             case TTC_ORIENT_RANDOM: hi = mix32(seed ^ (v * 0x100000001b3ull)); break;
             default: hi = level[v]; break;
         }
-        rk[v] = (hi << 32) | (uint64_t)v;
+        hi_out[v] = hi;
+        ident[v] = (uint32_t)v;
+        mx = max(mx, hi);
     }
+    for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0 && mx) atomicMax(hi_max, mx);
 }
 
-__global__ void orient_kernel(const uint2 *pv, size_t ms, const uint64_t *rk, uint64_t n, uint64_t *okey,
-                              uint32_t *oval, unsigned int *outdeg) {
+__global__ void rank_scatter_kernel(const uint32_t *id_of, uint32_t n, uint32_t *rank_of) {
+    GRID_STRIDE(r, (size_t)n) rank_of[id_of[r]] = (uint32_t)r;
+}
+
+// Orients each static edge from the lower to the higher rank; the key
+// (source rank, target rank) sorts the out-lists by target rank.
+__global__ void orient_kernel(const uint2 *pv, size_t ms, const uint32_t *rank_of, uint64_t n, uint64_t *okey,
+                              uint32_t *oval) {
     GRID_STRIDE(p, ms) {
-        const uint32_t a = pv[p].x, b = pv[p].y;
-        const bool ab = rk[a] < rk[b];
-        const uint32_t s = ab ? a : b, d = ab ? b : a;
+        const uint32_t ra = rank_of[pv[p].x], rb = rank_of[pv[p].y];
+        const uint32_t s = ra < rb ? ra : rb, d = ra < rb ? rb : ra;
         okey[p] = (uint64_t)s * n + d;
         oval[p] = (uint32_t)p;
-        atomicAdd(&outdeg[s], 1u);
     }
 }
 
-__global__ void split_okey_kernel(const uint64_t *okey, size_t ms, uint64_t n, uint32_t *osrc, uint32_t *onbr) {
-    GRID_STRIDE(i, ms) {
-        osrc[i] = (uint32_t)(okey[i] / n);
-        onbr[i] = (uint32_t)(okey[i] % n);
+// CSR offsets from sorted keys: off[r] = #{i : keys[i] < r * mult} for
+// r = 0..nv (binary search per r).
+__global__ void offsets_from_sorted_kernel(const uint64_t *keys, size_t len, uint64_t mult, uint32_t nv,
+                                           uint32_t *off) {
+    GRID_STRIDE(r, (size_t)nv + 1) {
+        const uint64_t x = (uint64_t)r * mult;
+        size_t lo = 0, cnt = len;
+        while (cnt > 0) {
+            const size_t half = cnt >> 1;
+            if (keys[lo + half] < x) {
+                lo += half + 1;
+                cnt -= half + 1;
+            } else {
+                cnt = half;
+            }
+        }
+        off[r] = (uint32_t)lo;
     }
 }
 
-__global__ void max_u32_kernel(const unsigned int *x, size_t n, unsigned int *mx_out) {
+// Largest gap between consecutive offsets (the largest list).
+__global__ void max_gap_kernel(const uint32_t *off, size_t nv, unsigned int *mx_out) {
     unsigned int mx = 0;
-    GRID_STRIDE(i, n) mx = max(mx, x[i]);
+    GRID_STRIDE(i, nv) mx = max(mx, off[i + 1] - off[i]);
     for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if ((threadIdx.x & 31) == 0 && mx) atomicMax(mx_out, mx);
+}
+
+// Splits the sorted keys into source and target ranks and sets up the sort
+// of the oriented edges by target (key = target rank, value = position).
+__global__ void split_okey_kernel(const uint64_t *okey, size_t ms, uint64_t n, uint32_t *osrc, uint32_t *onbr,
+                                  uint64_t *tkey, uint32_t *tpos) {
+    GRID_STRIDE(i, ms) {
+        const uint32_t d = (uint32_t)(okey[i] % n);
+        osrc[i] = (uint32_t)(okey[i] / n);
+        onbr[i] = d;
+        tkey[i] = d;
+        tpos[i] = (uint32_t)i;
+    }
 }
 
 __global__ void widen_kernel(const uint32_t *a, const uint32_t *b, size_t n, uint64_t *a64, uint64_t *b64) {
@@ -697,111 +1054,149 @@ __global__ void record_stats_kernel(const uint4 *rec, size_t tau, uint64_t n_lig
     }
 }
 
-// Triangle enumeration (Sec. 5: for each oriented edge (u, v), each
-// w in N+(u) and N+(v) closes <u, v, w>).  One warp per source vertex u:
-// N+(u) is staged in the warp's shared memory (when it fits), the edges of u
-// are taken 32 at a time, and the elements of their N+(v) lists are
-// flattened across the lanes; each lane looks its element w up in N+(u) by
-// binary search.  COUNT pass: per oriented edge, its light and heavy records.
-// WRITE pass: the records, each at its edge's offset in its bin plus its rank
-// among that edge's hits of that bin (ranked in (step, lane) order, so the
+// Triangle enumeration (Sec. 5: each triangle is found once, from its
+// oriented edges u -> v, u -> w, v -> w with u < v < w in the ordering).
+// Vertices are named by rank and every out-list is sorted by rank, so for an
+// in-edge u -> v at position e of N+(u), the candidates w are the suffix of
+// N+(u) after e.  Work items are (v, 32 in-edges of v): the warp stages N+(v)
+// in its shared memory (when it fits), flattens the 32 suffixes across its
+// lanes, and each lane looks its element w up in N+(v) by binary search.
+// COUNT pass: per oriented edge u -> v, its light and heavy records.  WRITE
+// pass: the records, each at its edge's offset in its bin plus its rank among
+// that edge's hits of that bin (hits of one edge come in ascending w, so the
 // layout is deterministic).
 constexpr int TRI_THREADS = 256;
 constexpr int TRI_WARPS = TRI_THREADS / 32;
-constexpr uint32_t TRI_NU_CAP = 1024;  // staged N+(u) entries per warp
+constexpr uint32_t TRI_NV_CAP = 1024;  // staged N+(v) entries per warp
+
+// Items: chunk c of target v covers its in-edges [32 c, 32 c + 32); a vertex
+// with no out-edge closes no triangle as the middle vertex.
+__global__ void tri_items_count_kernel(const uint32_t *out_off, const uint32_t *in_off, uint32_t n,
+                                       uint32_t *nitems) {
+    GRID_STRIDE(v, (size_t)n) {
+        const uint32_t dout = out_off[v + 1] - out_off[v], din = in_off[v + 1] - in_off[v];
+        nitems[v] = dout ? (din + 31) / 32 : 0;
+    }
+}
+
+// One thread per item: its vertex is the last v with item_pre[v] <= c.
+__global__ void tri_items_fill_kernel(const uint32_t *item_pre, uint32_t n, uint32_t nitems, uint2 *items) {
+    GRID_STRIDE(c, (size_t)nitems) {
+        uint32_t lo = 0, hi = n;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (item_pre[mid] <= c) lo = mid; else hi = mid;
+        }
+        items[c] = make_uint2(lo, ((uint32_t)c - item_pre[lo]) * 32);
+    }
+}
+
+struct TriCsr {
+    const uint32_t *onbr;     // out-lists: target ranks, sorted
+    const uint32_t *opair;    // pair id of each oriented edge
+    const uint32_t *out_off;  // out-list offsets by rank
+    const uint32_t *osrc;     // source rank of each oriented edge
+    const uint32_t *in_off;   // in-list offsets by rank
+    const uint32_t *in_e;     // in-lists: positions of the oriented edges
+    const uint32_t *id_of;    // vertex id of each rank
+};
 
 template <bool WRITE>
 __global__ void __launch_bounds__(TRI_THREADS)
-    tri_enum_kernel(const uint32_t *__restrict__ onbr, const uint32_t *__restrict__ opair,
-                    const uint32_t *__restrict__ out_off, uint32_t n, RecCtx rc, uint32_t *cnt_light,
+    tri_enum_kernel(const uint2 *__restrict__ items, uint32_t nitems, TriCsr g, RecCtx rc, uint32_t *cnt_light,
                     uint32_t *cnt_heavy, const uint64_t *light_off, const uint64_t *heavy_off, uint64_t heavy_base,
                     uint4 *rec) {
-    __shared__ uint32_t s_nu[TRI_WARPS][TRI_NU_CAP];
+    __shared__ uint32_t s_nv[TRI_WARPS][TRI_NV_CAP];
     __shared__ uint32_t s_excl[TRI_WARPS][33];
-    __shared__ uint32_t s_v[TRI_WARPS][32], s_vb[TRI_WARPS][32];
-    __shared__ uint32_t s_run[TRI_WARPS][64];  // per edge slot: light, heavy hits so far
+    __shared__ uint32_t s_e[TRI_WARPS][32], s_u[TRI_WARPS][32];
+    __shared__ uint32_t s_run[TRI_WARPS][64];  // per in-edge slot: light, heavy hits so far
     const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
-    for (uint64_t u = (uint64_t)blockIdx.x * TRI_WARPS + w; u < n; u += (uint64_t)gridDim.x * TRI_WARPS) {
-        const uint32_t ub = out_off[u], du = out_off[u + 1] - ub;
-        if (du < 2) continue;  // a triangle needs two out-neighbours of u
-        const bool staged = du <= TRI_NU_CAP;
-        if (staged)
-            for (uint32_t i = lane; i < du; i += 32) s_nu[w][i] = onbr[ub + i];
-        __syncwarp();
-        const uint32_t *nu = staged ? s_nu[w] : onbr + ub;
-        for (uint32_t c0 = 0; c0 < du; c0 += 32) {
-            const uint32_t i = c0 + lane;
-            uint32_t len = 0;
-            if (i < du) {
-                const uint32_t v = nu[i];
-                s_v[w][lane] = v;
-                s_vb[w][lane] = out_off[v];
-                len = out_off[v + 1] - out_off[v];
-            }
-            s_run[w][2 * lane] = 0;
-            s_run[w][2 * lane + 1] = 0;
-            uint32_t x = len;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-                if (lane >= (uint32_t)o) x += y;
-            }
-            s_excl[w][lane] = x - len;
-            const uint32_t total = __shfl_sync(0xffffffffu, x, 31);
-            if (lane == 0) s_excl[w][32] = total;
+    uint32_t staged_v = 0xffffffffu;
+    for (uint64_t it = (uint64_t)blockIdx.x * TRI_WARPS + w; it < nitems; it += (uint64_t)gridDim.x * TRI_WARPS) {
+        const uint2 item = items[it];
+        const uint32_t v = item.x, c0 = item.y;
+        const uint32_t vb = __ldg(g.out_off + v), dv = __ldg(g.out_off + v + 1) - vb;
+        const bool staged = dv <= TRI_NV_CAP;
+        if (staged && staged_v != v) {
             __syncwarp();
-            for (uint32_t base = 0; base < total; base += 32) {
-                const uint32_t j = base + lane;
-                bool hit = false, heavy = false;
-                uint32_t slot = 0;
-                uint4 r = make_uint4(0, 0, 0, 0);
-                if (j < total) {
-                    uint32_t o = 0;
-#pragma unroll
-                    for (uint32_t step = 16; step; step >>= 1)
-                        if (s_excl[w][o + step] <= j) o += step;
-                    slot = o;
-                    const uint32_t jv = s_vb[w][o] + (j - s_excl[w][o]);
-                    const uint32_t x3 = onbr[jv];
-                    uint32_t lo = 0, len2 = du;  // x3 in N+(u)
-                    while (len2 > 0) {
-                        const uint32_t half = len2 >> 1;
-                        if (nu[lo + half] < x3) {
-                            lo += half + 1;
-                            len2 -= half + 1;
-                        } else {
-                            len2 = half;
-                        }
-                    }
-                    if (lo < du && nu[lo] == x3) {
-                        hit = true;
-                        r = make_record(rc, (uint32_t)u, s_v[w][o], x3, opair[ub + c0 + o], opair[ub + lo], opair[jv],
-                                        &heavy);
-                    }
-                }
-                const unsigned act = __ballot_sync(0xffffffffu, hit);
-                if (!act) continue;
-                const uint32_t key = slot * 2 + (heavy ? 1u : 0u);
-                const unsigned peers = __match_any_sync(0xffffffffu, hit ? key : 0xffffffffu) & act;
-                uint32_t rank = 0;
-                if (hit) rank = s_run[w][key] + __popc(peers & lt_mask);
-                __syncwarp();
-                if (hit && (peers & lt_mask) == 0) s_run[w][key] += __popc(peers);
-                __syncwarp();
-                if (WRITE && hit) {
-                    const uint64_t ee = ub + c0 + slot;
-                    const uint64_t pos = heavy ? heavy_base + heavy_off[ee] + rank : light_off[ee] + rank;
-                    rec[pos] = r;
-                }
-            }
-            __syncwarp();
-            if (!WRITE && i < du) {
-                cnt_light[ub + i] = s_run[w][2 * lane];
-                cnt_heavy[ub + i] = s_run[w][2 * lane + 1];
-            }
-            __syncwarp();
+            for (uint32_t i = lane; i < dv; i += 32) s_nv[w][i] = __ldg(g.onbr + vb + i);
+            staged_v = v;
         }
+        __syncwarp();
+        const uint32_t *nv = staged ? s_nv[w] : g.onbr + vb;
+        const uint32_t ib = __ldg(g.in_off + v), din = __ldg(g.in_off + v + 1) - ib;
+        const uint32_t i = c0 + lane;
+        uint32_t len = 0;
+        if (i < din) {
+            const uint32_t e = __ldg(g.in_e + ib + i), u = __ldg(g.osrc + e);
+            s_e[w][lane] = e;
+            s_u[w][lane] = u;
+            len = __ldg(g.out_off + u + 1) - e - 1;  // the suffix of N+(u) after v
+        }
+        s_run[w][2 * lane] = 0;
+        s_run[w][2 * lane + 1] = 0;
+        uint32_t x = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= (uint32_t)o) x += y;
+        }
+        s_excl[w][lane] = x - len;
+        const uint32_t total = __shfl_sync(0xffffffffu, x, 31);
+        if (lane == 0) s_excl[w][32] = total;
+        __syncwarp();
+        for (uint32_t base = 0; base < total; base += 32) {
+            const uint32_t j = base + lane;
+            bool hit = false, heavy = false;
+            uint32_t slot = 0;
+            uint4 r = make_uint4(0, 0, 0, 0);
+            if (j < total) {
+                uint32_t o = 0;
+#pragma unroll
+                for (uint32_t step = 16; step; step >>= 1)
+                    if (s_excl[w][o + step] <= j) o += step;
+                slot = o;
+                const uint32_t eo = s_e[w][o];
+                const uint32_t ew = eo + 1 + (j - s_excl[w][o]);  // u -> w
+                const uint32_t x3 = __ldg(g.onbr + ew);
+                uint32_t lo = 0, len2 = dv;  // x3 in N+(v)
+                while (len2 > 0) {
+                    const uint32_t half = len2 >> 1;
+                    if (nv[lo + half] < x3) {
+                        lo += half + 1;
+                        len2 -= half + 1;
+                    } else {
+                        len2 = half;
+                    }
+                }
+                if (lo < dv && nv[lo] == x3) {
+                    hit = true;
+                    r = make_record(rc, __ldg(g.id_of + s_u[w][o]), __ldg(g.id_of + v), __ldg(g.id_of + x3),
+                                    __ldg(g.opair + eo), __ldg(g.opair + ew), __ldg(g.opair + vb + lo), &heavy);
+                }
+            }
+            const unsigned act = __ballot_sync(0xffffffffu, hit);
+            if (!act) continue;
+            const uint32_t key = slot * 2 + (heavy ? 1u : 0u);
+            const unsigned peers = __match_any_sync(0xffffffffu, hit ? key : 0xffffffffu) & act;
+            uint32_t rank = 0;
+            if (hit) rank = s_run[w][key] + __popc(peers & lt_mask);
+            __syncwarp();
+            if (hit && (peers & lt_mask) == 0) s_run[w][key] += __popc(peers);
+            __syncwarp();
+            if (WRITE && hit) {
+                const uint64_t ee = s_e[w][slot];
+                const uint64_t pos = heavy ? heavy_base + heavy_off[ee] + rank : light_off[ee] + rank;
+                rec[pos] = r;
+            }
+        }
+        __syncwarp();
+        if (!WRITE && i < din) {
+            cnt_light[s_e[w][lane]] = s_run[w][2 * lane];
+            cnt_heavy[s_e[w][lane]] = s_run[w][2 * lane + 1];
+        }
+        __syncwarp();
     }
 }
 
@@ -864,15 +1259,34 @@ static void set_view(ttc_graph *g, cudaStream_t s) {
 }
 
 // Largest cluster (up to 16 CTAs of 1024 threads) the device can run for the peel.
+// CTAs of the grid-wide peel stage: all co-resident (cooperative launch),
+// 0 when cooperative launches are unavailable.
+int peel_grid_ctas() {
+    static int ctas = -1;
+    if (ctas >= 0) return ctas;
+    int dev = 0, coop = 0, per_sm = 0;
+    ctas = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return ctas;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaFuncSetAttribute(peel_kernel<GridSync>, cudaFuncAttributeMaxDynamicSharedMemorySize, PEEL_SMEM);
+    if (coop && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, peel_kernel<GridSync>, PEEL_THREADS,
+                                                              PEEL_SMEM) == cudaSuccess)
+        ctas = std::max(0, per_sm) * sm_count();
+    cudaGetLastError();
+    return ctas;
+}
+
 int peel_cluster_size() {
     static int best = 0;
     if (best) return best;
-    cudaFuncSetAttribute(peel_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(peel_kernel<ClusterSync>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(peel_kernel<ClusterSync>, cudaFuncAttributeMaxDynamicSharedMemorySize, PEEL_SMEM);
     best = 8;
     for (int c = 16; c > 8; c /= 2) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(c);
         cfg.blockDim = dim3(PEEL_THREADS);
+        cfg.dynamicSmemBytes = PEEL_SMEM;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeClusterDimension;
         attr[0].val.clusterDim.x = c;
@@ -881,7 +1295,7 @@ int peel_cluster_size() {
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         int clusters = 0;
-        if (cudaOccupancyMaxActiveClusters(&clusters, peel_kernel, &cfg) == cudaSuccess && clusters >= 1) {
+        if (cudaOccupancyMaxActiveClusters(&clusters, peel_kernel<ClusterSync>, &cfg) == cudaSuccess && clusters >= 1) {
             best = c;
             break;
         }
@@ -901,6 +1315,7 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
     if (m_in >= (uint64_t(1) << 32) - 1) fail(TTC_ERR_RANGE, "m = %llu exceeds 2^32 - 2 edges", (unsigned long long)m_in);
     const size_t m0 = (size_t)m_in;
 
+    prof_begin(g, s, "load:ingest");
     // ---- a1: inputs on the device, validated
     DevBuf<uint32_t> src_buf, dst_buf;
     DevBuf<int64_t> t_buf;
@@ -957,11 +1372,14 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
     g->span = hmm[1] - hmm[0];
     const int span_bits = bits_for((uint64_t)g->span);
 
+    prof_end(g, s);
+    prof_begin(g, s, "load:keys_pair_sort");
     // ---- a2: per-edge key (t - t_min, tie rank, dir), grouped by pair and
     // key-sorted inside each pair by two stable sorts: time, then pair
     if (n * n > (uint64_t(1) << 63)) fail(TTC_ERR_RANGE, "vertex ids too large for the pair key");
     DevBuf<uint64_t> pkey(m, s);
     const int ib = bits_for(m - 1);
+    bool seg_sort_after = false;
     if (span_bits + ib + 1 <= 63) {
         // ties broken by the kept-edge index itself (input order)
         g->shift = ib + 1;
@@ -970,8 +1388,8 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
         TTC_LAUNCH_CHECK();
         tk.reset(); eidx.reset();
         src_buf.reset(); dst_buf.reset(); t_buf.reset();
-        radix_sort_u64_u64_range(reinterpret_cast<uint64_t *>(g->key.get()), pkey.get(), m, g->shift,
-                                 g->shift + span_bits, s);
+        // pairs are grouped first; each pair's keys are sorted below
+        seg_sort_after = true;
     } else {
         // ties broken by the rank inside each equal-timestamp group
         DevBuf<uint64_t> tkey(m, s);
@@ -1022,12 +1440,51 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
         TTC_CUDA(cudaMemcpyAsync(g->poff.get() + ms, &mm32, 4, cudaMemcpyHostToDevice, s));
         TTC_CUDA(cudaStreamSynchronize(s));
     }
+    prof_end(g, s);
+    prof_begin(g, s, "load:pair_lists");
+    if (seg_sort_after) {
+        // sort each pair's keys: warps for pairs of <= SEG_MID_CAP edges, CTAs
+        // up to SEG_BIG_CAP; a longer pair sends the whole array through a
+        // stable time sort and a second pair sort instead
+        DevBuf<uint32_t> mid(ms, s), big(ms, s);
+        DevBuf<unsigned int> cnt(3, s);  // mid count, big count, longest pair
+        TTC_CUDA(cudaMemsetAsync(cnt.get(), 0, 12, s));
+        seg_classify_kernel<<<grid_for(ms), TPB, 0, s>>>(g->poff.get(), ms, mid.get(), big.get(), cnt.get(),
+                                                         cnt.get() + 2);
+        TTC_LAUNCH_CHECK();
+        unsigned int hc[3];
+        TTC_CUDA(cudaMemcpyAsync(hc, cnt.get(), 12, cudaMemcpyDeviceToHost, s));
+        TTC_CUDA(cudaStreamSynchronize(s));
+        const uint32_t nmid = hc[0], nbig = hc[1], longest = hc[2];
+        if (longest <= SEG_BIG_CAP) {
+            seg_sort_small_kernel<<<grid_for((size_t)ms * 32), TPB, 0, s>>>(g->key.get(), g->poff.get(), ms);
+            TTC_LAUNCH_CHECK();
+            if (nmid) {
+                seg_sort_mid_kernel<<<std::min<uint32_t>(ceil_div(nmid, SEG_MID_WARPS), sm_count() * 7),
+                                      SEG_MID_WARPS * 32, 0, s>>>(g->key.get(), g->poff.get(), mid.get(), nmid);
+                TTC_LAUNCH_CHECK();
+            }
+            if (nbig) {
+                TTC_CUDA(cudaFuncSetAttribute(seg_sort_big_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)(SEG_BIG_CAP * 8)));
+                seg_sort_big_kernel<<<std::min<uint32_t>(nbig, sm_count()), SEG_BIG_THREADS, SEG_BIG_CAP * 8, s>>>(
+                    g->key.get(), g->poff.get(), big.get(), nbig);
+                TTC_LAUNCH_CHECK();
+            }
+        } else {
+            radix_sort_u64_u64_range(reinterpret_cast<uint64_t *>(g->key.get()), pkey.get(), m, g->shift,
+                                     g->shift + span_bits, s);
+            radix_sort_u64_u64(pkey.get(), reinterpret_cast<uint64_t *>(g->key.get()), m, bits_for(n * n - 1), s);
+        }
+    }
     pkey.reset(); pid.reset();
     dir0_flags_kernel<<<grid_for(m), TPB, 0, s>>>(g->key.get(), m, head.get());
     TTC_LAUNCH_CHECK();
     exclusive_scan_flags(head.get(), g->fwd.get(), m, s);
     head.reset();
 
+    prof_end(g, s);
+    prof_begin(g, s, "load:degrees");
     // ---- static graph: undirected CSR, degrees
     DevBuf<unsigned int> deg(n, s), smax(1, s);
     TTC_CUDA(cudaMemsetAsync(deg.get(), 0, n * 4, s));
@@ -1037,6 +1494,8 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
     st.sigma_max = read_scalar(smax.get(), s);
     g->heavy_wide = st.sigma_max >= 65536;
 
+    prof_end(g, s);
+    prof_begin(g, s, "load:peel");
     // ---- a3: ordering
     DevBuf<uint32_t> level(n, s);
     TTC_CUDA(cudaMemsetAsync(level.get(), 0xff, n * 4, s));
@@ -1054,10 +1513,33 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
         PeelCtl init{};
         for (auto &sl : init.slot) sl.min_deg = INT_MAX;
         TTC_CUDA(cudaMemcpyAsync(ctl.get(), &init, sizeof(init), cudaMemcpyHostToDevice, s));
+        const uint32_t *a_off = adj_off.get(), *a_adj = adj.get();
+        int *pd = pdeg.get();
+        uint32_t *lv = level.get(), *rA = remA.get(), *rB = remB.get(), *fA = frontA.get(), *fB = frontB.get(),
+                 *oA = foffA.get(), *oB = foffB.get();
+        uint32_t n32 = (uint32_t)n;
+        PeelCtl *pc = ctl.get();
+        int resume = 0;
+        // stage 1: every SM, while many vertices remain
+        const int grid_ctas = peel_grid_ctas();
+        if (n > PEEL_GRID_STOP && grid_ctas > 0) {
+            uint32_t stop = PEEL_GRID_STOP;
+            void *args[] = {(void *)&a_off, (void *)&a_adj, (void *)&pd, (void *)&lv, (void *)&rA, (void *)&rB,
+                            (void *)&fA, (void *)&fB, (void *)&oA, (void *)&oB, (void *)&n32, (void *)&stop,
+                            (void *)&resume, (void *)&pc};
+            TTC_CUDA(cudaLaunchCooperativeKernel((const void *)peel_kernel<GridSync>, dim3(grid_ctas),
+                                                 dim3(PEEL_THREADS), args, PEEL_SMEM, s));
+            note_launch();
+            peel_stage_reset_kernel<<<1, 1, 0, s>>>(pc);
+            TTC_LAUNCH_CHECK();
+            resume = 1;
+        }
+        // stage 2: one thread-block cluster, down to PEEL_TAIL vertices
         int cluster = peel_cluster_size();
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(cluster);
         cfg.blockDim = dim3(PEEL_THREADS);
+        cfg.dynamicSmemBytes = PEEL_SMEM;
         cfg.stream = s;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -1066,9 +1548,8 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        TTC_CUDA(cudaLaunchKernelEx(&cfg, peel_kernel, (const uint32_t *)adj_off.get(), (const uint32_t *)adj.get(),
-                                    pdeg.get(), level.get(), remA.get(), remB.get(), frontA.get(), frontB.get(),
-                                    foffA.get(), foffB.get(), (uint32_t)n, PEEL_TAIL, ctl.get()));
+        TTC_CUDA(cudaLaunchKernelEx(&cfg, peel_kernel<ClusterSync>, a_off, a_adj, pd, lv, rA, rB, fA, fB, oA, oB,
+                                    n32, PEEL_TAIL, resume, pc));
         note_launch();
         PeelCtl out = read_scalar(ctl.get(), s);
         if (out.error) fail(TTC_ERR_INTERNAL, "k-core peel did not finish");
@@ -1101,41 +1582,72 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
         }
         st.peel_rounds = out.rounds;
     }
-    DevBuf<uint64_t> rk(n, s);
+    prof_end(g, s);
+    prof_begin(g, s, "load:order_orient");
+    // ranks: vertices sorted by ordering key, ties by id
+    DevBuf<uint64_t> okey_v(n, s);
+    DevBuf<uint32_t> id_of(n, s), rank_of(n, s);
+    TTC_CUDA(cudaMemsetAsync(smax.get(), 0, 4, s));
     order_key_kernel<<<grid_for(n), TPB, 0, s>>>((uint32_t)n, opt.orientation, level.get(), deg.get(), opt.seed,
-                                                 rk.get());
+                                                 okey_v.get(), id_of.get(), smax.get());
     TTC_LAUNCH_CHECK();
     level.reset();
+    radix_sort_u64_u32(okey_v.get(), id_of.get(), n, bits_for(read_scalar(smax.get(), s)), s);
+    okey_v.reset();
+    rank_scatter_kernel<<<grid_for(n), TPB, 0, s>>>(id_of.get(), (uint32_t)n, rank_of.get());
+    TTC_LAUNCH_CHECK();
 
-    // ---- a4: orientation and out-CSR (neighbours sorted by id)
+    // ---- a4: orientation, out-CSR (lists sorted by rank) and in-CSR
     DevBuf<uint64_t> okey(ms, s);
     DevBuf<uint32_t> opair(ms, s);
-    DevBuf<unsigned int> outdeg(n, s);
-    TTC_CUDA(cudaMemsetAsync(outdeg.get(), 0, n * 4, s));
-    orient_kernel<<<grid_for(ms), TPB, 0, s>>>(g->pair_vtx.get(), ms, rk.get(), n, okey.get(), opair.get(),
-                                               outdeg.get());
+    orient_kernel<<<grid_for(ms), TPB, 0, s>>>(g->pair_vtx.get(), ms, rank_of.get(), n, okey.get(), opair.get());
     TTC_LAUNCH_CHECK();
-    rk.reset();
+    rank_of.reset();
     radix_sort_u64_u32(okey.get(), opair.get(), ms, bits_for(n * n - 1), s);
-    DevBuf<uint32_t> out_off(n + 1, s), osrc(ms, s), onbr(ms, s);
-    exclusive_scan_u32(outdeg.get(), out_off.get(), n, s);
+    DevBuf<uint32_t> out_off(n + 1, s), in_off(n + 1, s), osrc(ms, s), onbr(ms, s), in_e(ms, s);
+    offsets_from_sorted_kernel<<<grid_for(n + 1), TPB, 0, s>>>(okey.get(), ms, n, (uint32_t)n, out_off.get());
+    TTC_LAUNCH_CHECK();
     TTC_CUDA(cudaMemsetAsync(smax.get(), 0, 4, s));
-    max_u32_kernel<<<grid_for(n), TPB, 0, s>>>(outdeg.get(), n, smax.get());
+    max_gap_kernel<<<grid_for(n), TPB, 0, s>>>(out_off.get(), n, smax.get());
     TTC_LAUNCH_CHECK();
+    {
+        DevBuf<uint64_t> tkey(ms, s);
+        split_okey_kernel<<<grid_for(ms), TPB, 0, s>>>(okey.get(), ms, n, osrc.get(), onbr.get(), tkey.get(),
+                                                       in_e.get());
+        TTC_LAUNCH_CHECK();
+        okey.reset();
+        radix_sort_u64_u32(tkey.get(), in_e.get(), ms, bits_for(n - 1), s);
+        offsets_from_sorted_kernel<<<grid_for(n + 1), TPB, 0, s>>>(tkey.get(), ms, 1, (uint32_t)n, in_off.get());
+        TTC_LAUNCH_CHECK();
+    }
     st.kappa = read_scalar(smax.get(), s);
-    split_okey_kernel<<<grid_for(ms), TPB, 0, s>>>(okey.get(), ms, n, osrc.get(), onbr.get());
-    TTC_LAUNCH_CHECK();
-    okey.reset(); outdeg.reset(); deg.reset();
+    deg.reset();
 
+    prof_end(g, s);
+    prof_begin(g, s, "load:enumerate");
     // ---- a6: triangles, written straight into the light and heavy bins
     RecCtx rc{g->poff.get(), g->pair_vtx.get(), g->labeling, g->light_max_pairs};
-    const unsigned tgrid = (unsigned)std::min<uint64_t>(n / TRI_WARPS + 1, (uint64_t)sm_count() * 8);
+    const TriCsr tc{onbr.get(), opair.get(), out_off.get(), osrc.get(), in_off.get(), in_e.get(), id_of.get()};
+    // work items: (target v, 32 of its in-edges)
+    DevBuf<uint32_t> nit(n, s), it_pre(n + 1, s);
+    tri_items_count_kernel<<<grid_for(n), TPB, 0, s>>>(out_off.get(), in_off.get(), (uint32_t)n, nit.get());
+    TTC_LAUNCH_CHECK();
+    exclusive_scan_u32(nit.get(), it_pre.get(), n, s);
+    const uint32_t nitems = read_scalar(it_pre.get() + n, s);
+    DevBuf<uint2> items(nitems ? nitems : 1, s);
+    tri_items_fill_kernel<<<grid_for(nitems), TPB, 0, s>>>(it_pre.get(), (uint32_t)n, nitems, items.get());
+    TTC_LAUNCH_CHECK();
+    nit.reset(); it_pre.reset();
+    int tri_occ = 0;
+    TTC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&tri_occ, tri_enum_kernel<true>, TRI_THREADS, 0));
+    const unsigned tgrid =
+        (unsigned)std::min<uint64_t>(nitems / TRI_WARPS + 1, (uint64_t)sm_count() * std::max(1, tri_occ));
     DevBuf<uint32_t> cl(ms + 1, s), ch(ms + 1, s);
     DevBuf<uint64_t> loff(ms + 1, s), hoff(ms + 1, s), cl64(ms + 1, s), ch64(ms + 1, s);
     TTC_CUDA(cudaMemsetAsync(cl.get(), 0, (ms + 1) * 4, s));
     TTC_CUDA(cudaMemsetAsync(ch.get(), 0, (ms + 1) * 4, s));
-    tri_enum_kernel<false><<<tgrid, TRI_THREADS, 0, s>>>(onbr.get(), opair.get(), out_off.get(), (uint32_t)n, rc,
-                                                        cl.get(), ch.get(), nullptr, nullptr, 0, nullptr);
+    tri_enum_kernel<false><<<tgrid, TRI_THREADS, 0, s>>>(items.get(), nitems, tc, rc, cl.get(), ch.get(), nullptr,
+                                                        nullptr, 0, nullptr);
     TTC_LAUNCH_CHECK();
     widen_kernel<<<grid_for(ms), TPB, 0, s>>>(cl.get(), ch.get(), ms, cl64.get(), ch64.get());
     TTC_LAUNCH_CHECK();
@@ -1150,16 +1662,17 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
     st.tau = tau;
     g->tri.alloc(tau, s);
     if (tau) {
-        tri_enum_kernel<true><<<tgrid, TRI_THREADS, 0, s>>>(onbr.get(), opair.get(), out_off.get(), (uint32_t)n, rc,
-                                                           nullptr, nullptr, loff.get(), hoff.get(), n_light,
-                                                           g->tri.get());
+        tri_enum_kernel<true><<<tgrid, TRI_THREADS, 0, s>>>(items.get(), nitems, tc, rc, nullptr, nullptr, loff.get(),
+                                                           hoff.get(), n_light, g->tri.get());
         TTC_LAUNCH_CHECK();
     }
     cl.reset(); ch.reset(); loff.reset(); hoff.reset(); cl64.reset(); ch64.reset();
-    osrc.reset(); onbr.reset(); opair.reset(); out_off.reset();
+    osrc.reset(); onbr.reset(); opair.reset(); out_off.reset(); in_off.reset(); in_e.reset(); id_of.reset();
     st.tau_light = n_light;
     st.tau_heavy = tau - n_light;
 
+    prof_end(g, s);
+    prof_begin(g, s, "load:classify");
     // ---- statistics and heavy-path offsets
     const uint64_t nh = st.tau_heavy;
     DevBuf<uint64_t> he(nh ? nh : 1, s);
@@ -1214,6 +1727,7 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
     st.tau_hcta = n_hc;
     st.tau_huge = n_huge;
     set_view(g, s);
+    prof_end(g, s);
     TTC_CUDA(cudaStreamSynchronize(s));
 }
 

@@ -18,6 +18,7 @@
 // Every wait is bounded: the worker sleeps at most 200 us between polls and
 // ttc_serve_drain gives up after its timeout.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -32,6 +33,7 @@
 namespace ttc {
 void set_last_error(const std::string &m);
 void normalise(const ttc_delta &d, int64_t out[3]);
+uint64_t graph_device_bytes(const ttc_graph *g);
 }  // namespace ttc
 
 using namespace ttc;
@@ -90,6 +92,7 @@ struct ttc_server {
     uint64_t next_ticket = 1, next_graph = 1, clock = 0;
     uint64_t queued = 0;
     ttc_server_stats st{};
+    std::atomic<uint64_t> reserve{0};  // device bytes kept free by admission
 
     void run();
     bool complete_finished();
@@ -217,6 +220,7 @@ ttc_server *ttc_server_create(const ttc_server_opts *o) {
     try {
         s = new ttc_server();
         if (o) s->opts = *o;
+        s->reserve.store(s->opts.hbm_reserve_bytes);
         if (!s->opts.max_batch) s->opts.max_batch = 256;
         if (!s->opts.max_queue) s->opts.max_queue = 65536;
         if (!s->opts.streams) s->opts.streams = 4;
@@ -270,20 +274,26 @@ ttc_status ttc_serve_load(ttc_server *s, const uint32_t *src, const uint32_t *ds
     try {
         TTC_CUDA(cudaSetDevice(s->device));
         const uint64_t need = footprint_estimate(m);
-        // evict least recently used idle graphs until the estimate fits
-        for (;;) {
+        // evict least recently used idle graphs until the estimate fits;
+        // evict nothing when even evicting every idle graph would not do
+        for (bool first = true;; first = false) {
             size_t free_b = 0, total_b = 0;
             TTC_CUDA(cudaMemGetInfo(&free_b, &total_b));
-            const uint64_t avail = free_b > s->opts.hbm_reserve_bytes ? free_b - s->opts.hbm_reserve_bytes : 0;
+            free_b += pool_cached_bytes();  // freed blocks the library keeps for reuse
+            const uint64_t reserve = s->reserve.load();
+            const uint64_t avail = free_b > reserve ? free_b - reserve : 0;
             if (avail >= need) break;
             Served *victim = nullptr;
             {
                 std::lock_guard<std::mutex> lk(s->mu);
+                uint64_t idle_bytes = 0;
                 for (auto &kv : s->graphs) {
                     Served *c = kv.second;
                     if (c->busy || !c->pending.empty()) continue;
+                    idle_bytes += graph_device_bytes(c->g);
                     if (!victim || c->last_use < victim->last_use) victim = c;
                 }
+                if (first && avail + idle_bytes < need) victim = nullptr;
                 if (victim) {
                     s->graphs.erase(victim->id);
                     s->st.evictions++;
@@ -385,6 +395,15 @@ ttc_status ttc_serve_pause(ttc_server *s, int paused) {
         s->paused = paused != 0;
     }
     s->cv.notify_all();
+    return TTC_OK;
+}
+
+ttc_status ttc_serve_set_reserve(ttc_server *s, uint64_t hbm_reserve_bytes) {
+    if (!s) {
+        set_last_error("NULL argument");
+        return TTC_ERR_INVALID;
+    }
+    s->reserve.store(hbm_reserve_bytes);
     return TTC_OK;
 }
 

@@ -23,15 +23,17 @@ STATUS = {-1: "INVALID", -2: "RANGE", -3: "NOMEM", -4: "CUDA", -5: "TIMEOUT", -6
           -7: "BUSY", -8: "INTERNAL", -9: "NOT_FOUND"}
 
 LOAD_DEVICE_INPUT = 1
+LOAD_PROFILE = 2
 ORIENT_DEGENERACY, ORIENT_ID, ORIENT_DEGREE, ORIENT_RANDOM = 0, 1, 2, 3
 LABEL_HEAVIEST_VW, LABEL_SOURCE = 0, 1
 
 EXPORTS = ["ttc_load", "ttc_load_ex", "ttc_free", "ttc_graph_info", "ttc_count", "ttc_count_batch",
            "ttc_count_batch_async", "ttc_count_multi", "ttc_count_sample", "ttc_server_create",
            "ttc_server_destroy", "ttc_serve_load", "ttc_serve_submit", "ttc_serve_poll", "ttc_serve_drain",
-           "ttc_serve_pause",
+           "ttc_serve_pause", "ttc_serve_set_reserve",
            "ttc_server_info", "ttc_last_error", "ttc_version", "ttc_debug_fail_alloc_after",
-           "ttc_debug_launch_count", "ttc_set_profiling", "ttc_profile_read", "ttc_count_noalloc"]
+           "ttc_debug_launch_count", "ttc_set_profiling", "ttc_profile_read", "ttc_count_noalloc",
+           "ttc_release_cached", "ttc_memory_info"]
 
 
 class TTCError(RuntimeError):
@@ -99,10 +101,13 @@ def lib():
             "ttc_serve_poll": ([p, u64, p, p], ctypes.c_int),
             "ttc_serve_drain": ([p, ctypes.c_double], ctypes.c_int),
             "ttc_serve_pause": ([p, ctypes.c_int], ctypes.c_int),
+            "ttc_serve_set_reserve": ([p, u64], ctypes.c_int),
             "ttc_server_info": ([p, p], ctypes.c_int),
             "ttc_last_error": ([], ctypes.c_char_p),
             "ttc_version": ([], ctypes.c_char_p),
             "ttc_debug_fail_alloc_after": ([u64], None),
+            "ttc_release_cached": ([p], ctypes.c_int),
+            "ttc_memory_info": ([p, p, p], ctypes.c_int),
             "ttc_debug_launch_count": ([], u64),
             "ttc_set_profiling": ([p, ctypes.c_int], ctypes.c_int),
             "ttc_profile_read": ([p, p, u32], u32),
@@ -163,8 +168,10 @@ class Graph:
     """A device-resident temporal graph (``ttc_load_ex``)."""
 
     def __init__(self, src, dst, t, orientation=ORIENT_DEGENERACY, labeling=LABEL_HEAVIEST_VW,
-                 light_max_pairs=0, seed=0, stream=None):
+                 light_max_pairs=0, seed=0, stream=None, profile_load=False):
         ptrs, m, flags, keep = _edge_ptrs(src, dst, t)
+        if profile_load:
+            flags |= LOAD_PROFILE
         opts = LoadOpts(flags, orientation, labeling, light_max_pairs, seed, stream)
         h = ctypes.c_void_p()
         check(lib().ttc_load_ex(ptrs[0], ptrs[1], ptrs[2], m, ctypes.byref(opts), ctypes.byref(h)))
@@ -286,6 +293,9 @@ class Server:
     def pause(self, paused: bool = True):
         check(lib().ttc_serve_pause(self._h, 1 if paused else 0))
 
+    def set_reserve(self, hbm_reserve_bytes: int):
+        check(lib().ttc_serve_set_reserve(self._h, int(hbm_reserve_bytes)))
+
     def drain(self, timeout_s: float = 60.0):
         check(lib().ttc_serve_drain(self._h, timeout_s))
 
@@ -293,6 +303,21 @@ class Server:
         s = ServerStats()
         check(lib().ttc_server_info(self._h, ctypes.byref(s)))
         return {f: getattr(s, f) for f, _ in ServerStats._fields_}
+
+
+def release_cached() -> int:
+    """Return the library's cached device blocks to the device; bytes released."""
+    out = ctypes.c_uint64(0)
+    check(lib().ttc_release_cached(ctypes.byref(out)))
+    return int(out.value)
+
+
+def memory_info() -> dict:
+    """Free device memory and the library pool's mapped / handed-out bytes."""
+    f, r, u = ctypes.c_uint64(0), ctypes.c_uint64(0), ctypes.c_uint64(0)
+    check(lib().ttc_memory_info(ctypes.byref(f), ctypes.byref(r), ctypes.byref(u)))
+    return {"device_free": int(f.value), "pool_reserved": int(r.value), "pool_used": int(u.value),
+            "admission_free": int(f.value) + max(0, int(r.value) - int(u.value))}
 
 
 def debug_fail_alloc_after(n: int):

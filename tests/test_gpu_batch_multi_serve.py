@@ -148,23 +148,29 @@ def test_server_queue_limit_and_eviction():
     for tk in tks:
         assert (srv.poll(tk)[0] == want).all()
     srv.close()
-    # admission: reserve all but about one graph's load estimate, so a
-    # second load must evict the idle first graph
+    # admission: once g1 is resident, keep all but slightly less than g2's
+    # load estimate free, so loading g2 must evict the idle g1 first
+    srv = ttc.Server()
+    g1 = srv.load(*gr1)
     torch.cuda.synchronize()
-    free, _ = torch.cuda.mem_get_info()
-    estimate = 96 * 20_000 + (64 << 20)
-    srv = ttc.Server(hbm_reserve_bytes=max(0, free - estimate - (1 << 20)))
-    try:
-        g1 = srv.load(*gr1)
-    except ttc.TTCError:
-        pytest.skip("device memory moved under the test")
+    ttc.release_cached()
+    free = ttc.memory_info()["admission_free"]  # device free + the pool's cached blocks
+    estimate = 96 * gr2[0].size + (64 << 20)
+    srv.set_reserve(max(0, free - estimate + 4096))
     g2 = srv.load(*gr2)
     info = srv.info()
-    assert info["evictions"] >= 1 and info["graphs_resident"] == 1
+    assert info["evictions"] == 1 and info["graphs_resident"] == 1 and info["admissions"] == 2
     with pytest.raises(ttc.TTCError, match="NOT_FOUND"):
         srv.submit(g1, (1, 1, 1))
     tk = srv.submit(g2, (100_000, 50_000, 50_000))
     srv.drain(30.0)
     counts, _ = srv.poll(tk)
     assert (counts == oracle.count(*gr2, [(100_000, 50_000, 50_000)])[0]).all()
+    # a load that evicting every idle graph could not make room for is
+    # refused, and nothing is evicted for it
+    srv.set_reserve(1 << 62)
+    with pytest.raises(ttc.TTCError, match="NOMEM"):
+        srv.load(*gr1)
+    info = srv.info()
+    assert info["evictions"] == 1 and info["graphs_resident"] == 1
     srv.close()

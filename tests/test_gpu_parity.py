@@ -131,6 +131,32 @@ def test_adversarial_shapes():
             _check(s, d, t, deltas, light_max_pairs=lm)
 
 
+def _pair_size_graph(sizes, seed):
+    """One triangle per (a, b, c) on fresh vertices with a, b, c edges on its
+    pairs, random directions, edges shuffled, timestamps full of ties."""
+    rng = np.random.default_rng(seed)
+    src, dst = [], []
+    for j, triple in enumerate(sizes):
+        v = 3 * j
+        for (x, y), k in zip(((v, v + 1), (v + 1, v + 2), (v, v + 2)), triple):
+            flip = rng.integers(0, 2, k).astype(bool)
+            src.append(np.where(flip, y, x))
+            dst.append(np.where(flip, x, y))
+    s = np.concatenate(src).astype(np.uint32)
+    d = np.concatenate(dst).astype(np.uint32)
+    perm = rng.permutation(s.size)
+    return s[perm], d[perm], rng.integers(0, 300, s.size).astype(np.int64)
+
+
+def test_pair_sort_size_classes():
+    # pair lengths on both sides of each per-pair sort class boundary (32,
+    # 1024, 16384); the last graph holds a pair beyond the largest class
+    deltas = [(BIG, BIG, BIG), (50, 20, 30), (100, 100, 0), (0, 0, 0)]
+    for sizes in ([(1, 1, 1), (2, 32, 33), (64, 65, 100), (1000, 1024, 1025), (2048, 3000, 40), (5, 16384, 7)],
+                  [(16385, 3, 4), (33, 2000, 1)]):
+        _check(*_pair_size_graph(sizes, len(sizes)), deltas)
+
+
 def test_empty_graph():
     e = np.zeros(0, dtype=np.uint32)
     g = ttc.Graph(e, e, np.zeros(0, dtype=np.int64))
@@ -157,6 +183,62 @@ def test_orientation_invariance_and_degeneracy_bound():
         assert (g.count_batch(deltas) == want).all(), o
         if o == ttc.ORIENT_DEGENERACY:
             assert g.info()["kappa"] <= degeneracy
+        g.free()
+
+
+def _level_peel(s, d):
+    """Level-synchronous bucketed peel written with numpy: at level k (the
+    smallest remaining degree) every remaining vertex of degree <= k is
+    removed in one round, and each round's removals make the next round's
+    frontier.  Returns (largest out-degree when pairs are oriented from the
+    lower (round, id) to the higher, number of rounds)."""
+    keep = s != d
+    a = np.minimum(s[keep], d[keep]).astype(np.int64)
+    b = np.maximum(s[keep], d[keep]).astype(np.int64)
+    key = np.unique(a * (1 << 32) + b)
+    a, b = key >> 32, key & 0xFFFFFFFF
+    n = int(max(s.max(), d.max())) + 1
+    deg = np.bincount(a, minlength=n) + np.bincount(b, minlength=n)
+    nbr = np.concatenate([b, a])[np.argsort(np.concatenate([a, b]), kind="stable")]
+    off = np.zeros(n + 1, np.int64)
+    off[1:] = np.cumsum(deg)
+    alive = np.ones(n, bool)
+    level = np.full(n, -1, np.int64)
+    k = rounds = 0
+    while alive.any():
+        k = max(k, int(deg[alive].min()))
+        front = np.nonzero(alive & (deg <= k))[0]
+        while front.size:
+            level[front] = rounds
+            alive[front] = False
+            cnt = off[front + 1] - off[front]
+            start = off[front] - (np.cumsum(cnt) - cnt)
+            nb = nbr[np.repeat(start, cnt) + np.arange(cnt.sum())]
+            nb = nb[alive[nb]]
+            deg = deg - np.bincount(nb, minlength=n)
+            cand = np.unique(nb)
+            front = cand[deg[cand] <= k]
+            rounds += 1
+    a_first = (level[a] < level[b]) | ((level[a] == level[b]) & (a < b))
+    return int(np.bincount(np.where(a_first, a, b), minlength=n).max()), rounds
+
+
+def test_peel_stages_match_level_synchronous_reference():
+    # n = 100k vertices: the peel runs all three stages (every SM, one
+    # cluster, one CTA); the out-degree bound and the round count are fixed
+    # by the level-synchronous rule wherever the stage boundaries fall
+    s, d, t = synth.large_plain(scale=0.1)
+    kappa, rounds = _level_peel(s, d)
+    g = ttc.Graph(s, d, t)
+    info = g.info()
+    assert (info["kappa"], info["peel_rounds"]) == (kappa, rounds)
+    q = [synth.LARGE_PLAIN_DELTA]
+    assert (g.count_batch(q) == oracle.count(s, d, t, q)).all()
+    g.free()
+    # small graphs (one cluster and the tail only, or the tail only)
+    for s, d, t in (synth.large_plain(scale=0.004), synth.random_tiny(5, 40, 300, 3)):
+        g = ttc.Graph(s, d, t)
+        assert (g.info()["kappa"], g.info()["peel_rounds"]) == _level_peel(s, d)
         g.free()
 
 
@@ -197,6 +279,17 @@ def test_invalid_inputs_rejected():
         ttc.Graph(np.array([1 << 31, 1, 0], np.uint32), d, t)
     with pytest.raises(ttc.TTCError, match="RANGE"):
         ttc.Graph(s, d, np.array([0, 1, (1 << 62) + 1], np.int64))
+    # the packed key holds span bits + tie bits + 1 <= 63
+    with pytest.raises(ttc.TTCError, match="RANGE"):
+        ttc.Graph(s, d, np.array([0, 1, 1 << 62], np.int64))
+    with pytest.raises(ttc.TTCError, match="RANGE"):
+        ttc.Graph(s, d, np.array([0, 0, 1 << 61], np.int64))
+    for tt in ([0, 1, (1 << 62) - 1], [-(1 << 61), 0, (1 << 61) - 1], [0, 0, (1 << 60)]):
+        tt = np.array(tt, np.int64)
+        q = [(BIG, BIG, BIG), (1 << 62, 1 << 61, 1 << 61), (1 << 60, 1 << 60, 1 << 60)]
+        gw = ttc.Graph(s, d, tt)
+        assert (gw.count_batch(q) == oracle.count(s, d, tt, q)).all()
+        gw.free()
     g = ttc.Graph(s, d, t)
     with pytest.raises(ttc.TTCError, match="RANGE"):
         g.count((-1, 0, 0))
