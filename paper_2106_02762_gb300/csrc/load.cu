@@ -175,21 +175,52 @@ __global__ void adj_fill_kernel(const uint2 *pv, size_t ms, uint32_t *cursor, ui
 // ---------------------------------------------------------------- per-pair key sort
 // After the pair sort each pair's edges are contiguous but in input order;
 // these kernels sort every pair's keys in place (keys are unique, so the
-// result does not depend on which unit sorts which pair).  Pairs of at most
-// 32 edges: one warp, a bitonic network in registers.  33..SEG_MID_CAP: one
-// warp, a bitonic network in that warp's slice of shared memory.  Larger, up
-// to SEG_BIG_CAP: one CTA, a bitonic network in shared memory.
+// result does not depend on which unit sorts which pair).  Up to 8 edges:
+// one thread, a sorting network in registers; up to 32: one warp, a bitonic
+// network in registers; 33..SEG_MID_CAP: one warp, a bitonic network in that
+// warp's slice of shared memory; larger, up to SEG_BIG_CAP: one CTA, a
+// bitonic network in shared memory.
 constexpr uint32_t SEG_MID_CAP = 1024;    // largest pair sorted by one warp
 constexpr int SEG_MID_WARPS = 4;      // 32 KB of shared memory per CTA
 constexpr uint32_t SEG_BIG_CAP = 16384;  // largest pair sorted by one CTA
 constexpr int SEG_BIG_THREADS = 1024;
 
-__global__ void seg_sort_small_kernel(int64_t *key, const uint32_t *poff, uint32_t ms) {
-    const uint32_t lane = threadIdx.x & 31;
-    for (uint64_t p = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < ms;
-         p += ((uint64_t)gridDim.x * blockDim.x) >> 5) {
+// Pairs of 2..SEG_TINY_CAP edges: one thread, a sorting network in registers.
+constexpr uint32_t SEG_TINY_CAP = 8;
+
+__device__ __forceinline__ void cmp_swap(int64_t &a, int64_t &b) {
+    const int64_t lo = min(a, b), hi = max(a, b);
+    a = lo;
+    b = hi;
+}
+
+__global__ void seg_sort_tiny_kernel(int64_t *key, const uint32_t *poff, uint32_t ms) {
+    GRID_STRIDE(p, (size_t)ms) {
         const uint32_t b = poff[p], len = poff[p + 1] - b;
-        if (len <= 1 || len > 32) continue;  // warp-uniform
+        if (len <= 1 || len > SEG_TINY_CAP) continue;
+        int64_t x[8];
+#pragma unroll
+        for (int j = 0; j < 8; j++) x[j] = (uint32_t)j < len ? key[b + j] : INT64_MAX;
+        // Batcher's odd-even merge sort network for 8 inputs (19 comparators)
+        cmp_swap(x[0], x[1]); cmp_swap(x[2], x[3]); cmp_swap(x[4], x[5]); cmp_swap(x[6], x[7]);
+        cmp_swap(x[0], x[2]); cmp_swap(x[1], x[3]); cmp_swap(x[4], x[6]); cmp_swap(x[5], x[7]);
+        cmp_swap(x[1], x[2]); cmp_swap(x[5], x[6]);
+        cmp_swap(x[0], x[4]); cmp_swap(x[1], x[5]); cmp_swap(x[2], x[6]); cmp_swap(x[3], x[7]);
+        cmp_swap(x[2], x[4]); cmp_swap(x[3], x[5]);
+        cmp_swap(x[1], x[2]); cmp_swap(x[3], x[4]); cmp_swap(x[5], x[6]);
+#pragma unroll
+        for (int j = 0; j < 8; j++)
+            if ((uint32_t)j < len) key[b + j] = x[j];
+    }
+}
+
+// Pairs of SEG_TINY_CAP+1..32 edges (listed in `small`): one warp, a bitonic
+// network in registers.
+__global__ void seg_sort_small_kernel(int64_t *key, const uint32_t *poff, const uint32_t *small, uint32_t nsmall) {
+    const uint32_t lane = threadIdx.x & 31;
+    for (uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nsmall;
+         w += ((uint64_t)gridDim.x * blockDim.x) >> 5) {
+        const uint32_t p = small[w], b = poff[p], len = poff[p + 1] - b;
         int64_t x = lane < len ? key[b + lane] : INT64_MAX;
 #pragma unroll
         for (uint32_t k = 2; k <= 32; k <<= 1) {
@@ -204,9 +235,10 @@ __global__ void seg_sort_small_kernel(int64_t *key, const uint32_t *poff, uint32
     }
 }
 
-// Appends the pairs of more than 32 edges to the mid (<= SEG_MID_CAP) and big
-// lists (warp-aggregated; list order is immaterial) and records the longest.
-__global__ void seg_classify_kernel(const uint32_t *poff, uint32_t ms, uint32_t *mid, uint32_t *big,
+// Appends the pairs of more than SEG_TINY_CAP edges to the small (<= 32), mid
+// (<= SEG_MID_CAP) and big lists (warp-aggregated; list order is immaterial)
+// and records the longest pair.
+__global__ void seg_classify_kernel(const uint32_t *poff, uint32_t ms, uint32_t *small, uint32_t *mid, uint32_t *big,
                                     unsigned int *counts, unsigned int *longest) {
     const uint32_t lane = threadIdx.x & 31;
     unsigned int mx = 0;
@@ -215,14 +247,17 @@ __global__ void seg_classify_kernel(const uint32_t *poff, uint32_t ms, uint32_t 
     for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < span; p += stride) {
         const uint32_t len = p < ms ? poff[p + 1] - poff[p] : 0;
         mx = max(mx, len);
-        for (int c = 0; c < 2; c++) {
-            const bool take = c == 0 ? (len > 32 && len <= SEG_MID_CAP) : (len > SEG_MID_CAP);
-            const unsigned int bal = __ballot_sync(0xffffffffu, take);
+        for (int c = 0; c < 3; c++) {
+            const bool take = c == 0   ? (len > SEG_TINY_CAP && len <= 32)
+                              : c == 1 ? (len > 32 && len <= SEG_MID_CAP)
+                                       : (len > SEG_MID_CAP);
+            const unsigned bal = __ballot_sync(0xffffffffu, take);
             if (!bal) continue;
             unsigned int base = 0;
             if (lane == 0) base = atomicAdd(&counts[c], (unsigned int)__popc(bal));
             base = __shfl_sync(0xffffffffu, base, 0);
-            if (take) (c == 0 ? mid : big)[base + __popc(bal & ((1u << lane) - 1))] = (uint32_t)p;
+            uint32_t *list = c == 0 ? small : c == 1 ? mid : big;
+            if (take) list[base + __popc(bal & ((1u << lane) - 1))] = (uint32_t)p;
         }
     }
     for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -715,7 +750,11 @@ __global__ void peel_stage_reset_kernel(PeelCtl *ctl) {
 // ---------------------------------------------------------------- peel tail
 constexpr uint32_t PEEL_TAIL = 8192;  // vertices the one-CTA tail peel holds
 constexpr int TAIL_THREADS = 1024;
-constexpr size_t TAIL_SMEM = (size_t)PEEL_TAIL * (4 + 2 * 4 + 2 + 2 * 2);
+constexpr int TAIL_RUN = 4;  // relaxed edges per thread per step
+// degrees, two edge-offset buffers, levels (u16), two adjacency-start buffers
+constexpr size_t TAIL_SMEM = (size_t)PEEL_TAIL * (4 + 2 * 4 + 2 + 2 * 4);
+static_assert(TAIL_SMEM <= 227 * 1024, "tail peel state must fit one CTA's shared memory");
+static_assert((PEEL_TAIL * 14) % 4 == 0, "adjacency-start buffers must be 4-byte aligned");
 
 // Local ids of the remaining vertices and their (current) degrees.
 __global__ void tail_ids_kernel(const uint32_t *rem, uint32_t R, const int *deg, uint32_t *lid, uint32_t *cdeg) {
@@ -796,7 +835,9 @@ __global__ void __launch_bounds__(TAIL_THREADS)
     uint32_t *s_deg = reinterpret_cast<uint32_t *>(tail_smem);                      // [PEEL_TAIL]
     uint32_t (*s_foff)[PEEL_TAIL] = reinterpret_cast<uint32_t (*)[PEEL_TAIL]>(s_deg + PEEL_TAIL);  // [2][..]
     uint16_t *s_lev = reinterpret_cast<uint16_t *>(s_deg + 3 * PEEL_TAIL);           // [PEEL_TAIL]
-    uint16_t (*s_front)[PEEL_TAIL] = reinterpret_cast<uint16_t (*)[PEEL_TAIL]>(s_lev + PEEL_TAIL);  // [2][..]
+    // frontier entries: the vertex's core-adjacency start and its offset in
+    // the round's edge sequence
+    uint32_t (*s_front)[PEEL_TAIL] = reinterpret_cast<uint32_t (*)[PEEL_TAIL]>(s_lev + PEEL_TAIL);  // [2][..]
     __shared__ unsigned long long s_cnt[2];
     __shared__ int s_min;
     const uint32_t tid = threadIdx.x, lane = tid & 31;
@@ -812,8 +853,9 @@ __global__ void __launch_bounds__(TAIL_THREADS)
     __syncthreads();
     int k = k0;
     uint32_t round = 0, kappa = ctl->kappa, removed = 0, cur = 0, fn = 0, fe = 0;
-    // warp-aggregated push of local vertex v into frontier buffer b
-    auto push = [&](bool pred, uint32_t v, uint32_t na, int b) {
+    // warp-aggregated push of a vertex (adjacency start ab, length na) into
+    // frontier buffer b
+    auto push = [&](bool pred, uint32_t ab, uint32_t na, int b) {
         const uint64_t pk = pred ? ((uint64_t(1) << 40) | na) : 0;
         uint64_t x = pk;
 #pragma unroll
@@ -827,7 +869,7 @@ __global__ void __launch_bounds__(TAIL_THREADS)
         base = __shfl_sync(0xffffffffu, base, 31);
         if (pred) {
             const uint64_t mine = base + x - pk;
-            s_front[b][mine >> 40] = (uint16_t)v;
+            s_front[b][mine >> 40] = ab;
             s_foff[b][mine >> 40] = (uint32_t)(mine & MASK40);
         }
     };
@@ -846,13 +888,14 @@ __global__ void __launch_bounds__(TAIL_THREADS)
             for (uint32_t base = 0; base < R; base += TAIL_THREADS) {
                 const uint32_t i = base + tid;
                 bool take = false;
-                uint32_t na = 0;
+                uint32_t na = 0, ab = 0;
                 if (i < R && s_lev[i] == NONE && (int)s_deg[i] <= k) {
                     take = true;
                     s_lev[i] = (uint16_t)round;
-                    na = coff[i + 1] - coff[i];
+                    ab = coff[i];
+                    na = coff[i + 1] - ab;
                 }
-                push(take, i, na, cur);
+                push(take, ab, na, cur);
             }
             __syncthreads();
             fn = (uint32_t)(s_cnt[cur] >> 40);
@@ -864,27 +907,54 @@ __global__ void __launch_bounds__(TAIL_THREADS)
         const int nxt = cur ^ 1;
         if (tid == 0) s_cnt[nxt] = 0;  // the previous frontier's counter
         __syncthreads();
-        for (uint32_t e0 = tid; e0 - tid < fe; e0 += TAIL_THREADS) {
-            bool p = false;
-            uint32_t w = 0, na = 0;
+        // each thread takes TAIL_RUN consecutive edges and issues their
+        // adjacency loads together, so a round costs about one L2 latency
+        for (uint32_t e0 = tid * TAIL_RUN; e0 - tid * TAIL_RUN < fe; e0 += TAIL_THREADS * TAIL_RUN) {
+            uint32_t wv[TAIL_RUN];
+            bool live[TAIL_RUN];
             if (e0 < fe) {
                 uint32_t lo = 0, hi = fn;
                 while (hi - lo > 1) {
                     const uint32_t mid = (lo + hi) >> 1;
                     if (s_foff[cur][mid] <= e0) lo = mid; else hi = mid;
                 }
-                const uint32_t v = s_front[cur][lo];
-                w = cadj[coff[v] + (e0 - s_foff[cur][lo])];
-                if (s_lev[w] == NONE) {
+                uint32_t fi = lo, fbeg = s_foff[cur][fi];
+                uint32_t fend = fi + 1 < fn ? s_foff[cur][fi + 1] : fe;
+                uint32_t base = s_front[cur][fi];
+#pragma unroll
+                for (int j = 0; j < TAIL_RUN; j++) {
+                    const uint32_t e = e0 + j;
+                    live[j] = e < fe;
+                    if (live[j]) {
+                        while (e >= fend) {
+                            fi++;
+                            fbeg = fend;
+                            fend = fi + 1 < fn ? s_foff[cur][fi + 1] : fe;
+                            base = s_front[cur][fi];
+                        }
+                        wv[j] = cadj[base + (e - fbeg)];
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < TAIL_RUN; j++) live[j] = false;
+            }
+#pragma unroll
+            for (int j = 0; j < TAIL_RUN; j++) {
+                bool p = false;
+                const uint32_t w = live[j] ? wv[j] : 0;
+                uint32_t na = 0, ab = 0;
+                if (live[j] && s_lev[w] == NONE) {
                     const uint32_t old = atomicSub(&s_deg[w], 1u);
                     if ((int)old == k + 1) {
                         p = true;
                         s_lev[w] = (uint16_t)(round + 1);
-                        na = coff[w + 1] - coff[w];
+                        ab = coff[w];
+                        na = coff[w + 1] - ab;
                     }
                 }
+                push(p, ab, na, nxt);
             }
-            push(p, w, na, nxt);
         }
         __syncthreads();
         fn = (uint32_t)(s_cnt[nxt] >> 40);
@@ -1446,19 +1516,24 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
         // sort each pair's keys: warps for pairs of <= SEG_MID_CAP edges, CTAs
         // up to SEG_BIG_CAP; a longer pair sends the whole array through a
         // stable time sort and a second pair sort instead
-        DevBuf<uint32_t> mid(ms, s), big(ms, s);
-        DevBuf<unsigned int> cnt(3, s);  // mid count, big count, longest pair
-        TTC_CUDA(cudaMemsetAsync(cnt.get(), 0, 12, s));
-        seg_classify_kernel<<<grid_for(ms), TPB, 0, s>>>(g->poff.get(), ms, mid.get(), big.get(), cnt.get(),
-                                                         cnt.get() + 2);
+        DevBuf<uint32_t> small(ms, s), mid(ms, s), big(ms, s);
+        DevBuf<unsigned int> cnt(4, s);  // small, mid, big counts; longest pair
+        TTC_CUDA(cudaMemsetAsync(cnt.get(), 0, 16, s));
+        seg_classify_kernel<<<grid_for(ms), TPB, 0, s>>>(g->poff.get(), ms, small.get(), mid.get(), big.get(),
+                                                         cnt.get(), cnt.get() + 3);
         TTC_LAUNCH_CHECK();
-        unsigned int hc[3];
-        TTC_CUDA(cudaMemcpyAsync(hc, cnt.get(), 12, cudaMemcpyDeviceToHost, s));
+        unsigned int hc[4];
+        TTC_CUDA(cudaMemcpyAsync(hc, cnt.get(), 16, cudaMemcpyDeviceToHost, s));
         TTC_CUDA(cudaStreamSynchronize(s));
-        const uint32_t nmid = hc[0], nbig = hc[1], longest = hc[2];
+        const uint32_t nsmall = hc[0], nmid = hc[1], nbig = hc[2], longest = hc[3];
         if (longest <= SEG_BIG_CAP) {
-            seg_sort_small_kernel<<<grid_for((size_t)ms * 32), TPB, 0, s>>>(g->key.get(), g->poff.get(), ms);
+            seg_sort_tiny_kernel<<<grid_for(ms), TPB, 0, s>>>(g->key.get(), g->poff.get(), ms);
             TTC_LAUNCH_CHECK();
+            if (nsmall) {
+                seg_sort_small_kernel<<<grid_for((size_t)nsmall * 32), TPB, 0, s>>>(g->key.get(), g->poff.get(),
+                                                                                  small.get(), nsmall);
+                TTC_LAUNCH_CHECK();
+            }
             if (nmid) {
                 seg_sort_mid_kernel<<<std::min<uint32_t>(ceil_div(nmid, SEG_MID_WARPS), sm_count() * 7),
                                       SEG_MID_WARPS * 32, 0, s>>>(g->key.get(), g->poff.get(), mid.get(), nmid);

@@ -149,10 +149,11 @@ def _pair_size_graph(sizes, seed):
 
 
 def test_pair_sort_size_classes():
-    # pair lengths on both sides of each per-pair sort class boundary (32,
+    # pair lengths on both sides of each per-pair sort class boundary (8, 32,
     # 1024, 16384); the last graph holds a pair beyond the largest class
     deltas = [(BIG, BIG, BIG), (50, 20, 30), (100, 100, 0), (0, 0, 0)]
-    for sizes in ([(1, 1, 1), (2, 32, 33), (64, 65, 100), (1000, 1024, 1025), (2048, 3000, 40), (5, 16384, 7)],
+    for sizes in ([(1, 1, 1), (8, 9, 3), (2, 32, 33), (64, 65, 100), (1000, 1024, 1025), (2048, 3000, 40),
+                   (5, 16384, 7)],
                   [(16385, 3, 4), (33, 2000, 1)]):
         _check(*_pair_size_graph(sizes, len(sizes)), deltas)
 
