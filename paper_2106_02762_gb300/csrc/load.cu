@@ -177,13 +177,10 @@ __global__ void adj_fill_kernel(const uint2 *pv, size_t ms, uint32_t *cursor, ui
 // these kernels sort every pair's keys in place (keys are unique, so the
 // result does not depend on which unit sorts which pair).  Up to 8 edges:
 // one thread, a sorting network in registers; up to 32: one warp, a bitonic
-// network in registers; 33..SEG_MID_CAP: one warp, a bitonic network in that
-// warp's slice of shared memory; larger, up to SEG_BIG_CAP: one CTA, a
-// bitonic network in shared memory.
-constexpr uint32_t SEG_MID_CAP = 1024;    // largest pair sorted by one warp
-constexpr int SEG_MID_WARPS = 4;      // 32 KB of shared memory per CTA
-constexpr uint32_t SEG_BIG_CAP = 16384;  // largest pair sorted by one CTA
-constexpr int SEG_BIG_THREADS = 1024;
+// network in registers; up to SEG_BIG_CAP: a warp or a CTA with up to 16
+// keys per thread in registers (cross-warp stages through shared memory),
+// one instance per power-of-two size class.
+constexpr uint32_t SEG_BIG_CAP = 16384;  // largest pair sorted in place
 
 // Pairs of 2..SEG_TINY_CAP edges: one thread, a sorting network in registers.
 constexpr uint32_t SEG_TINY_CAP = 8;
@@ -235,90 +232,121 @@ __global__ void seg_sort_small_kernel(int64_t *key, const uint32_t *poff, const 
     }
 }
 
-// Appends the pairs of more than SEG_TINY_CAP edges to the small (<= 32), mid
-// (<= SEG_MID_CAP) and big lists (warp-aggregated; list order is immaterial)
-// and records the longest pair.
-__global__ void seg_classify_kernel(const uint32_t *poff, uint32_t ms, uint32_t *small, uint32_t *mid, uint32_t *big,
-                                    unsigned int *counts, unsigned int *longest) {
+// Size classes of the pairs above SEG_TINY_CAP edges: class 0 = 9..32 edges,
+// class c = 1..9 = (2^(c+4), 2^(c+5)] edges, class 10 = longer than
+// SEG_BIG_CAP (sorted by the whole-array fallback instead).
+constexpr int SEG_CLASSES = 11;
+
+__device__ __forceinline__ int seg_class(uint32_t len) {
+    if (len <= SEG_TINY_CAP) return -1;
+    if (len <= 32) return 0;
+    if (len > SEG_BIG_CAP) return SEG_CLASSES - 1;
+    return (32 - __clz(len - 1)) - 5;
+}
+
+// Per-class counts of the pairs (FILL = false), or each pair appended to its
+// class's slice of `list` (FILL = true; `cursor` starts at the class
+// offsets).  Warp-aggregated per class; the order inside a class is
+// immaterial.
+template <bool FILL>
+__global__ void seg_classify_kernel(const uint32_t *poff, uint32_t ms, unsigned int *cursor, uint32_t *list) {
     const uint32_t lane = threadIdx.x & 31;
-    unsigned int mx = 0;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t span = (ms + 31) & ~uint64_t(31);  // whole warps stay in the loop
     for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < span; p += stride) {
-        const uint32_t len = p < ms ? poff[p + 1] - poff[p] : 0;
-        mx = max(mx, len);
-        for (int c = 0; c < 3; c++) {
-            const bool take = c == 0   ? (len > SEG_TINY_CAP && len <= 32)
-                              : c == 1 ? (len > 32 && len <= SEG_MID_CAP)
-                                       : (len > SEG_MID_CAP);
-            const unsigned bal = __ballot_sync(0xffffffffu, take);
-            if (!bal) continue;
-            unsigned int base = 0;
-            if (lane == 0) base = atomicAdd(&counts[c], (unsigned int)__popc(bal));
-            base = __shfl_sync(0xffffffffu, base, 0);
-            uint32_t *list = c == 0 ? small : c == 1 ? mid : big;
-            if (take) list[base + __popc(bal & ((1u << lane) - 1))] = (uint32_t)p;
-        }
+        const int c = p < ms ? seg_class(poff[p + 1] - poff[p]) : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, c);
+        const int leader = __ffs(peers) - 1;
+        unsigned int base = 0;
+        if (c >= 0 && (int)lane == leader) base = atomicAdd(&cursor[c], (unsigned int)__popc(peers));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (FILL && c >= 0) list[base + __popc(peers & ((1u << lane) - 1))] = (uint32_t)p;
     }
-    for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (lane == 0 && mx) atomicMax(longest, mx);
 }
 
-__global__ void __launch_bounds__(SEG_MID_WARPS * 32)
-    seg_sort_mid_kernel(int64_t *key, const uint32_t *poff, const uint32_t *mid, uint32_t nmid) {
-    __shared__ int64_t s_all[SEG_MID_WARPS][SEG_MID_CAP];
-    const uint32_t lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    int64_t *s_k = s_all[wib];
-    for (uint64_t w = (uint64_t)blockIdx.x * SEG_MID_WARPS + wib; w < nmid; w += (uint64_t)gridDim.x * SEG_MID_WARPS) {
-        const uint32_t p = mid[w], b = poff[p], len = poff[p + 1] - b;
-        uint32_t n2 = 64;
-        while (n2 < len) n2 <<= 1;
-        for (uint32_t i = lane; i < n2; i += 32) s_k[i] = i < len ? key[b + i] : INT64_MAX;
-        __syncwarp();
-        const uint32_t half = n2 >> 1;
-        for (uint32_t k = 2; k <= n2; k <<= 1) {
-            for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-                for (uint32_t x = lane; x < half; x += 32) {
-                    const uint32_t i = ((x & ~(j - 1)) << 1) | (x & (j - 1)), l = i + j;
-                    const int64_t a = s_k[i], c = s_k[l];
-                    if ((a > c) == ((i & k) == 0)) {
-                        s_k[i] = c;
-                        s_k[l] = a;
-                    }
+// Bitonic sort of T * E keys held by T consecutive threads, E per thread in
+// registers (element i = t * E + r for thread t of the group).  A stage whose
+// partner element sits in the same thread compares registers; a partner in
+// another lane of the warp comes by shuffle; a partner in another warp (CTA
+// groups only) is exchanged through shared memory s_x (r-major, so a warp's
+// accesses are consecutive).
+template <int E, int T>
+__device__ __forceinline__ void bitonic_regs(int64_t (&x)[E], uint32_t t, int64_t *s_x) {
+    constexpr uint32_t N = (uint32_t)E * T;
+    for (uint32_t k = 2; k <= N; k <<= 1) {
+        // stages whose partner is another thread (j >= E): same register r
+        for (uint32_t j = k >> 1; j >= (uint32_t)E; j >>= 1) {
+            const uint32_t tj = j / E;  // partner thread t ^ tj
+            const bool lower = (t & tj) == 0;
+            if (T <= 32 || tj < 32) {
+#pragma unroll
+                for (int r = 0; r < E; r++) {
+                    const int64_t y = __shfl_xor_sync(0xffffffffu, x[r], tj);
+                    const bool asc = ((t * E + r) & k) == 0;
+                    x[r] = (lower == asc) ? min(x[r], y) : max(x[r], y);
                 }
-                __syncwarp();
-            }
-        }
-        for (uint32_t i = lane; i < len; i += 32) key[b + i] = s_k[i];
-        __syncwarp();
-    }
-}
-
-__global__ void __launch_bounds__(SEG_BIG_THREADS)
-    seg_sort_big_kernel(int64_t *key, const uint32_t *poff, const uint32_t *big, uint32_t nbig) {
-    extern __shared__ int64_t s_k[];
-    for (uint32_t bi = blockIdx.x; bi < nbig; bi += gridDim.x) {
-        const uint32_t p = big[bi], b = poff[p], len = poff[p + 1] - b;
-        uint32_t n2 = 2 * SEG_BIG_THREADS;
-        while (n2 < len) n2 <<= 1;
-        for (uint32_t i = threadIdx.x; i < n2; i += SEG_BIG_THREADS) s_k[i] = i < len ? key[b + i] : INT64_MAX;
-        __syncthreads();
-        const uint32_t half = n2 >> 1;
-        for (uint32_t k = 2; k <= n2; k <<= 1) {
-            for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-                for (uint32_t x = threadIdx.x; x < half; x += SEG_BIG_THREADS) {
-                    const uint32_t i = ((x & ~(j - 1)) << 1) | (x & (j - 1)), l = i + j;
-                    const int64_t a = s_k[i], c = s_k[l];
-                    if ((a > c) == ((i & k) == 0)) {
-                        s_k[i] = c;
-                        s_k[l] = a;
-                    }
+            } else {
+#pragma unroll
+                for (int r = 0; r < E; r++) s_x[r * T + t] = x[r];
+                __syncthreads();
+#pragma unroll
+                for (int r = 0; r < E; r++) {
+                    const int64_t y = s_x[r * T + (t ^ tj)];
+                    const bool asc = ((t * E + r) & k) == 0;
+                    x[r] = (lower == asc) ? min(x[r], y) : max(x[r], y);
                 }
                 __syncthreads();
             }
         }
-        for (uint32_t i = threadIdx.x; i < len; i += SEG_BIG_THREADS) key[b + i] = s_k[i];
-        __syncthreads();
+        // stages inside one thread's registers (j < E, j < k)
+#pragma unroll
+        for (int j = E / 2; j > 0; j >>= 1) {
+            if ((uint32_t)j < k) {
+#pragma unroll
+                for (int r = 0; r < E; r++) {
+                    if ((r & j) == 0) {
+                        const int q = r | j;
+                        const bool asc = ((t * E + r) & k) == 0;
+                        const int64_t a = x[r], c = x[q];
+                        const bool sw = (a > c) == asc;
+                        x[r] = sw ? c : a;
+                        x[q] = sw ? a : c;
+                    }
+                }
+            }
+        }
+    }
+}
+
+// Sorts one pair's keys [b, b + len) with T threads holding E keys each
+// (T * E >= len; the rest is padded with the largest key).
+template <int E, int T>
+__device__ __forceinline__ void sort_pair_regs(int64_t *key, uint32_t b, uint32_t len, uint32_t t, int64_t *s_x) {
+    int64_t x[E];
+#pragma unroll
+    for (int r = 0; r < E; r++) {
+        const uint32_t i = t * E + r;
+        x[r] = i < len ? key[b + i] : INT64_MAX;
+    }
+    bitonic_regs<E, T>(x, t, s_x);
+#pragma unroll
+    for (int r = 0; r < E; r++) {
+        const uint32_t i = t * E + r;
+        if (i < len) key[b + i] = x[r];
+    }
+}
+
+// One pair per group of T threads (a warp when T = 32, four groups per CTA;
+// the whole CTA otherwise), E keys per thread: pairs of up to E * T edges.
+template <int E, int T>
+__global__ void __launch_bounds__(T >= 128 ? T : 128)
+    seg_sort_group_kernel(int64_t *key, const uint32_t *poff, const uint32_t *list, uint32_t nlist) {
+    extern __shared__ int64_t s_x[];
+    constexpr uint32_t CTA = T >= 128 ? T : 128, G = CTA / T;
+    const uint32_t grp = threadIdx.x / T, t = threadIdx.x % T;
+    for (uint64_t w = (uint64_t)blockIdx.x * G + grp; w < nlist; w += (uint64_t)gridDim.x * G) {
+        const uint32_t p = list[w], b = poff[p], len = poff[p + 1] - b;
+        sort_pair_regs<E, T>(key, b, len, t, s_x);
     }
 }
 
@@ -347,7 +375,7 @@ struct PeelCtl {
 
 constexpr uint64_t MASK40 = (uint64_t(1) << 40) - 1;
 constexpr int PEEL_THREADS = 1024;
-constexpr int PEEL_RUN = 8;  // relaxed edges per thread per step
+constexpr int PEEL_RUN = 4;  // relaxed edges per thread per step
 constexpr uint32_t PEEL_CACHE = 8192;  // frontier entries cached in shared memory
 constexpr uint32_t PEEL_GRID_STOP = 65536;  // the grid-wide stage hands off at this many vertices
 
@@ -432,21 +460,10 @@ __device__ __forceinline__ void flush_frontier(PeelSlot *sl, uint32_t *front, ui
     }
 }
 
-// Phase barriers of the peel.  ClusterSync: one thread-block cluster
-// (hardware barrier).  GridSync: every CTA of a cooperative launch, through
-// an arrival counter and a generation word in device memory; the wait is
-// bounded, and a CTA that gives up reports failure so the kernel can stop.
+// Phase barrier of the grid-wide peel: every CTA of a cooperative launch,
+// through an arrival counter and a generation word in device memory.  The
+// wait is bounded; a CTA that gives up reports failure so the kernel stops.
 constexpr uint32_t GRID_BAR_SPIN = 1u << 24;
-
-struct ClusterSync {
-    cg::cluster_group cl = cg::this_cluster();
-    __device__ uint32_t nthreads() const { return cl.num_blocks() * blockDim.x; }
-    __device__ uint32_t rank() const { return cl.block_rank() * blockDim.x + threadIdx.x; }
-    __device__ bool sync(PeelCtl *) {
-        cl.sync();
-        return true;
-    }
-};
 
 struct GridSync {
     uint32_t gen = 0;
@@ -489,18 +506,16 @@ struct GridSync {
 // round empties the frontier, the remaining set is compacted and k rises to
 // its smallest degree.  level[v] = round of removal; orienting every pair
 // from the lower (round, id) to the higher gives each vertex at most k <=
-// kappa out-neighbours.  The rounds run in stages of falling width: every
-// SM (GridSync) while many vertices remain, then one thread-block cluster
-// (ClusterSync), then one CTA (peel_tail_kernel).  A stage stops at the first
-// level boundary with at most tail_n vertices left and records where it
-// stopped in ctl; the next stage resumes from there.  Every control decision
-// is uniform.
-template <typename Sync>
+// kappa out-neighbours.  This kernel runs the rounds on every SM while many
+// vertices remain; it stops at the first level boundary with at most tail_n
+// vertices left and records where it stopped in ctl, and peel_core_kernel
+// peels the rest in one thread-block cluster.  Every control decision is
+// uniform.
 __global__ void __launch_bounds__(PEEL_THREADS)
     peel_kernel(const uint32_t *__restrict__ adj_off, const uint32_t *__restrict__ adj, int *deg,
                 uint32_t *level, uint32_t *remA, uint32_t *remB, uint32_t *frontA, uint32_t *frontB,
-                uint32_t *foffA, uint32_t *foffB, uint32_t n, uint32_t tail_n, int resume, PeelCtl *ctl) {
-    Sync bar;
+                uint32_t *foffA, uint32_t *foffB, uint32_t n, uint32_t tail_n, PeelCtl *ctl) {
+    GridSync bar;
     const uint32_t nthr = bar.nthreads();
     const uint32_t tid = bar.rank();
     const uint32_t lane = threadIdx.x & 31;
@@ -523,19 +538,7 @@ __global__ void __launch_bounds__(PEEL_THREADS)
     bool identity = true;  // the remaining set is 0..n-1 until the first compaction
     int k = 0;
     uint32_t round = 0, kappa = 0, ph = 0;
-    bool stopped = false;  // handed the rest to the next stage
-    if (resume) {  // continue where the previous stage stopped
-        if (!__ldcg(&ctl->handoff) || __ldcg(&ctl->error)) return;  // nothing left, or it failed
-        k = __ldcg(&ctl->k);
-        round = __ldcg(&ctl->rounds);
-        kappa = __ldcg(&ctl->kappa);
-        rem_n = __ldcg(&ctl->rem_n);
-        identity = false;
-        if (__ldcg(&ctl->rem_in_b)) {
-            rem = remB;
-            rem_next = remA;
-        }
-    }
+    bool stopped = false;  // handed the rest to the core stage
     const uint64_t ph_cap = 3ull * n + 8;
     bool ok = true;
     // ends phase ph: barrier, then zero the slot of phase ph + 2
@@ -614,7 +617,7 @@ __global__ void __launch_bounds__(PEEL_THREADS)
             uint32_t *t = rem; rem = rem_next; rem_next = t;
             if (rem_n == 0) break;
             k = max(k, md);
-            if (rem_n <= tail_n) {  // hand the rest to the next, narrower stage
+            if (rem_n <= tail_n) {  // hand the rest to the core stage
                 if (tid == 0) {
                     ctl->handoff = 1;
                     ctl->k = k;
@@ -734,27 +737,14 @@ __global__ void __launch_bounds__(PEEL_THREADS)
     }
 }
 
-// Prepares the control block for the next peel stage: phase slots and the
-// grid barrier start over; the hand-off state is kept.
-__global__ void peel_stage_reset_kernel(PeelCtl *ctl) {
-    for (int i = 0; i < 3; i++) {
-        ctl->slot[i].front = 0;
-        ctl->slot[i].rem_n = 0;
-        ctl->slot[i].min_deg = INT_MAX;
-    }
-    ctl->bar_count = 0;
-    ctl->bar_gen = 0;
-}
 
 
-// ---------------------------------------------------------------- peel tail
-constexpr uint32_t PEEL_TAIL = 8192;  // vertices the one-CTA tail peel holds
-constexpr int TAIL_THREADS = 1024;
-constexpr int TAIL_RUN = 4;  // relaxed edges per thread per step
-// degrees, two edge-offset buffers, levels (u16), two adjacency-start buffers
-constexpr size_t TAIL_SMEM = (size_t)PEEL_TAIL * (4 + 2 * 4 + 2 + 2 * 4);
-static_assert(TAIL_SMEM <= 227 * 1024, "tail peel state must fit one CTA's shared memory");
-static_assert((PEEL_TAIL * 14) % 4 == 0, "adjacency-start buffers must be 4-byte aligned");
+// ---------------------------------------------------------------- peel core
+// The last PEEL_GRID_STOP (or fewer) vertices are peeled by one thread-block
+// cluster that keeps every remaining vertex's state in distributed shared
+// memory.  Their adjacency among themselves is first rebuilt with local ids
+// (16 bits, since at most 65 536 remain).
+static_assert(PEEL_GRID_STOP <= 65536, "core vertices need 16-bit local ids");
 
 // Local ids of the remaining vertices and their (current) degrees.
 __global__ void tail_ids_kernel(const uint32_t *rem, uint32_t R, const int *deg, uint32_t *lid, uint32_t *cdeg) {
@@ -823,154 +813,213 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-// The rest of the peel in one CTA: degrees, levels, frontiers and their
-// adjacency offsets in shared memory; the core adjacency (local ids) is read
-// from L2.  Same rules as peel_kernel, continuing from level k0 and round
-// round0; writes level[] for the remaining vertices and the final round and
-// kappa counts.
-__global__ void __launch_bounds__(TAIL_THREADS)
-    peel_tail_kernel(const uint32_t *rem, uint32_t R, const uint32_t *coff, const uint16_t *cadj, uint32_t *level,
-                     int k0, uint32_t round0, PeelCtl *ctl) {
-    extern __shared__ __align__(16) unsigned char tail_smem[];
-    uint32_t *s_deg = reinterpret_cast<uint32_t *>(tail_smem);                      // [PEEL_TAIL]
-    uint32_t (*s_foff)[PEEL_TAIL] = reinterpret_cast<uint32_t (*)[PEEL_TAIL]>(s_deg + PEEL_TAIL);  // [2][..]
-    uint16_t *s_lev = reinterpret_cast<uint16_t *>(s_deg + 3 * PEEL_TAIL);           // [PEEL_TAIL]
-    // frontier entries: the vertex's core-adjacency start and its offset in
-    // the round's edge sequence
-    uint32_t (*s_front)[PEEL_TAIL] = reinterpret_cast<uint32_t (*)[PEEL_TAIL]>(s_lev + PEEL_TAIL);  // [2][..]
-    __shared__ unsigned long long s_cnt[2];
-    __shared__ int s_min;
-    const uint32_t tid = threadIdx.x, lane = tid & 31;
-    constexpr uint16_t NONE = 0xffff;
-    for (uint32_t i = tid; i < R; i += TAIL_THREADS) {
-        s_deg[i] = coff[i + 1] - coff[i];
-        s_lev[i] = NONE;
+// The peel of the core (Sec. 3, same level-synchronous rule as peel_kernel)
+// in one thread-block cluster.  Local vertex l is owned by CTA l / per, which
+// holds its remaining degree, level, adjacency span and, when it is in a
+// frontier, its frontier entry, all in shared memory.  A round: each CTA
+// relaxes the edges of its own frontier vertices (adjacency read from L2);
+// level checks and degree decrements go to the owner's shared memory
+// (distributed shared memory); a vertex whose degree falls to k joins its
+// owner's next frontier.  Only counts cross the cluster barrier: pushes are
+// tallied per CTA in a slot that rotates over three rounds, so a slot is
+// read by every CTA between the barriers that end round r and r + 1 and is
+// zeroed in round r + 2.  Continues from level ctl->k and round ctl->rounds;
+// writes level[] of the core vertices and the final rounds and kappa.
+constexpr int CORE_THREADS = 1024;
+constexpr int CORE_RUN = 4;          // relaxed edges per thread per step
+constexpr uint32_t CORE_MAX_CLUSTER = 16;
+
+// degree, adjacency start, adjacency length, frontier edge offset, two
+// frontier buffers and the level of `per` owned vertices (u32 each)
+inline size_t core_smem_bytes(uint32_t per) { return (size_t)per * 7 * 4; }
+
+__device__ __forceinline__ uint32_t core_block_excl_scan(uint32_t x, uint32_t *s_warp, uint32_t *total) {
+    const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= (uint32_t)o) inc += y;
     }
-    if (tid == 0) {
-        s_cnt[0] = s_cnt[1] = 0;
-        s_min = INT_MAX;
-    }
+    if (lane == 31) s_warp[w] = inc;
     __syncthreads();
-    int k = k0;
-    uint32_t round = 0, kappa = ctl->kappa, removed = 0, cur = 0, fn = 0, fe = 0;
-    // warp-aggregated push of a vertex (adjacency start ab, length na) into
-    // frontier buffer b
-    auto push = [&](bool pred, uint32_t ab, uint32_t na, int b) {
-        const uint64_t pk = pred ? ((uint64_t(1) << 40) | na) : 0;
-        uint64_t x = pk;
+    if (w == 0) {
+        const uint32_t nw = blockDim.x >> 5;
+        uint32_t v = lane < nw ? s_warp[lane] : 0, vi = v;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= (uint32_t)o) x += y;
+            const uint32_t y = __shfl_up_sync(0xffffffffu, vi, o);
+            if (lane >= (uint32_t)o) vi += y;
         }
-        const uint64_t tot = __shfl_sync(0xffffffffu, x, 31);
-        uint64_t base = 0;
-        if (lane == 31 && tot) base = atomicAdd(&s_cnt[b], (unsigned long long)tot);
-        base = __shfl_sync(0xffffffffu, base, 31);
-        if (pred) {
-            const uint64_t mine = base + x - pk;
-            s_front[b][mine >> 40] = ab;
-            s_foff[b][mine >> 40] = (uint32_t)(mine & MASK40);
-        }
-    };
-    while (removed < R) {
-        if (fn == 0) {
-            // new level: smallest remaining degree, then collect its frontier
+        if (lane < nw) s_warp[lane] = vi - v;
+        if (lane == 31) *total = vi;
+    }
+    __syncthreads();
+    return s_warp[w] + inc - x;
+}
+
+__global__ void __launch_bounds__(CORE_THREADS)
+    peel_core_kernel(const uint32_t *rem, uint32_t R, uint32_t per, const uint32_t *coff, const uint16_t *cadj,
+                     uint32_t *level, PeelCtl *ctl) {
+    cg::cluster_group cl = cg::this_cluster();
+    const uint32_t crank = cl.block_rank(), csize = cl.num_blocks();
+    const uint32_t tid = threadIdx.x, lane = tid & 31;
+    extern __shared__ __align__(16) uint32_t core_smem[];
+    uint32_t *s_deg = core_smem, *s_ab = s_deg + per, *s_na = s_ab + per, *s_foff = s_na + per;
+    uint32_t *s_front = s_foff + per;  // [2][per]
+    uint32_t *s_lev = s_front + 2 * per;
+    __shared__ unsigned int s_fcnt[2];                 // entries in my frontier buffers
+    __shared__ unsigned int s_tot[3];                  // pushes made by this CTA, per round mod 3
+    __shared__ unsigned int s_peer[CORE_MAX_CLUSTER];  // the cluster's push tallies of one round
+    __shared__ int s_mins[CORE_MAX_CLUSTER];           // each CTA's smallest remaining degree
+    __shared__ int s_min;
+    __shared__ uint32_t s_warp[32];
+    __shared__ uint32_t s_fe;
+    const uint32_t base_lid = crank * per;
+    const uint32_t my_n = R > base_lid ? min(per, R - base_lid) : 0;
+    for (uint32_t i = tid; i < my_n; i += CORE_THREADS) {
+        const uint32_t ab = coff[base_lid + i], na = coff[base_lid + i + 1] - ab;
+        s_ab[i] = ab;
+        s_na[i] = na;
+        s_deg[i] = na;
+        s_lev[i] = UNSET;
+    }
+    if (tid == 0) {
+        s_fcnt[0] = s_fcnt[1] = 0;
+        s_tot[0] = s_tot[1] = s_tot[2] = 0;
+        s_min = INT_MAX;
+    }
+    int k = __ldcg(&ctl->k);
+    const uint32_t round0 = __ldcg(&ctl->rounds);
+    uint32_t kappa = __ldcg(&ctl->kappa);
+    uint32_t round = 0, cur = 0;
+    bool need_level = true, ok = true;
+    cl.sync();  // every CTA's state is initialised before any remote access
+    for (;;) {
+        if (need_level) {
+            // new level: the cluster's smallest remaining degree, then every
+            // owned vertex of degree <= k joins this CTA's frontier
             int my = INT_MAX;
-            for (uint32_t i = tid; i < R; i += TAIL_THREADS)
-                if (s_lev[i] == NONE) my = min(my, (int)s_deg[i]);
+            for (uint32_t i = tid; i < my_n; i += CORE_THREADS)
+                if (s_lev[i] == UNSET) my = min(my, (int)s_deg[i]);
 #pragma unroll
             for (int o = 16; o; o >>= 1) my = min(my, __shfl_xor_sync(0xffffffffu, my, o));
-            if (lane == 0) atomicMin(&s_min, my);
+            if (lane == 0 && my != INT_MAX) atomicMin(&s_min, my);
             __syncthreads();
-            k = max(k, s_min);
+            if (tid < csize) cl.map_shared_rank(s_mins, tid)[crank] = s_min;
+            cl.sync();
+            int g = INT_MAX;
+            for (uint32_t j = 0; j < csize; j++) g = min(g, s_mins[j]);
+            if (g == INT_MAX) break;  // nothing left anywhere (uniform)
+            k = max(k, g);
             kappa = max(kappa, (uint32_t)k);
-            for (uint32_t base = 0; base < R; base += TAIL_THREADS) {
-                const uint32_t i = base + tid;
-                bool take = false;
-                uint32_t na = 0, ab = 0;
-                if (i < R && s_lev[i] == NONE && (int)s_deg[i] <= k) {
-                    take = true;
-                    s_lev[i] = (uint16_t)round;
-                    ab = coff[i];
-                    na = coff[i + 1] - ab;
+            for (uint32_t i = tid; i < my_n; i += CORE_THREADS) {
+                if (s_lev[i] == UNSET && (int)s_deg[i] <= k) {
+                    s_lev[i] = round;
+                    s_front[cur * per + atomicAdd(&s_fcnt[cur], 1u)] = i;
                 }
-                push(take, ab, na, cur);
             }
             __syncthreads();
-            fn = (uint32_t)(s_cnt[cur] >> 40);
-            fe = (uint32_t)(s_cnt[cur] & MASK40);
-            __syncthreads();
             if (tid == 0) s_min = INT_MAX;
+            need_level = false;
         }
-        removed += fn;
-        const int nxt = cur ^ 1;
-        if (tid == 0) s_cnt[nxt] = 0;  // the previous frontier's counter
-        __syncthreads();
-        // each thread takes TAIL_RUN consecutive edges and issues their
-        // adjacency loads together, so a round costs about one L2 latency
-        for (uint32_t e0 = tid * TAIL_RUN; e0 - tid * TAIL_RUN < fe; e0 += TAIL_THREADS * TAIL_RUN) {
-            uint32_t wv[TAIL_RUN];
-            bool live[TAIL_RUN];
+        // relaxation of this CTA's frontier (round `round`)
+        const uint32_t nxt = cur ^ 1, slot = round % 3;
+        const uint32_t fn = s_fcnt[cur];
+        const uint32_t *F = s_front + cur * per;
+        {
+            // edge offsets of the frontier entries (exclusive scan of their
+            // adjacency lengths), each thread a run of consecutive entries
+            const uint32_t per_t = (fn + CORE_THREADS - 1) / CORE_THREADS;
+            const uint32_t b0 = min(fn, tid * per_t), b1 = min(fn, b0 + per_t);
+            uint32_t sum = 0;
+            for (uint32_t i = b0; i < b1; i++) sum += s_na[F[i]];
+            uint32_t run = core_block_excl_scan(sum, s_warp, &s_fe);
+            for (uint32_t i = b0; i < b1; i++) {
+                s_foff[i] = run;
+                run += s_na[F[i]];
+            }
+            // the tally slot of round - 2: every CTA read it before the
+            // barrier that ended round - 1
+            if (tid == 0) s_tot[(round + 1) % 3] = 0;
+            __syncthreads();
+        }
+        const uint32_t fe = s_fe;
+        for (uint32_t e0 = tid * CORE_RUN; e0 - tid * CORE_RUN < fe; e0 += CORE_THREADS * CORE_RUN) {
+            uint32_t wv[CORE_RUN];
+            bool live[CORE_RUN];
             if (e0 < fe) {
-                uint32_t lo = 0, hi = fn;
+                uint32_t lo = 0, hi = fn;  // last entry with s_foff <= e0
                 while (hi - lo > 1) {
                     const uint32_t mid = (lo + hi) >> 1;
-                    if (s_foff[cur][mid] <= e0) lo = mid; else hi = mid;
+                    if (s_foff[mid] <= e0) lo = mid; else hi = mid;
                 }
-                uint32_t fi = lo, fbeg = s_foff[cur][fi];
-                uint32_t fend = fi + 1 < fn ? s_foff[cur][fi + 1] : fe;
-                uint32_t base = s_front[cur][fi];
+                uint32_t fi = lo, fbeg = s_foff[fi];
+                uint32_t fend = fi + 1 < fn ? s_foff[fi + 1] : fe;
+                uint32_t ab = s_ab[F[fi]];
 #pragma unroll
-                for (int j = 0; j < TAIL_RUN; j++) {
+                for (int j = 0; j < CORE_RUN; j++) {
                     const uint32_t e = e0 + j;
                     live[j] = e < fe;
                     if (live[j]) {
                         while (e >= fend) {
                             fi++;
                             fbeg = fend;
-                            fend = fi + 1 < fn ? s_foff[cur][fi + 1] : fe;
-                            base = s_front[cur][fi];
+                            fend = fi + 1 < fn ? s_foff[fi + 1] : fe;
+                            ab = s_ab[F[fi]];
                         }
-                        wv[j] = cadj[base + (e - fbeg)];
+                        wv[j] = cadj[ab + (e - fbeg)];
                     }
                 }
             } else {
 #pragma unroll
-                for (int j = 0; j < TAIL_RUN; j++) live[j] = false;
+                for (int j = 0; j < CORE_RUN; j++) live[j] = false;
             }
+            uint32_t own[CORE_RUN], idx[CORE_RUN];
 #pragma unroll
-            for (int j = 0; j < TAIL_RUN; j++) {
-                bool p = false;
-                const uint32_t w = live[j] ? wv[j] : 0;
-                uint32_t na = 0, ab = 0;
-                if (live[j] && s_lev[w] == NONE) {
-                    const uint32_t old = atomicSub(&s_deg[w], 1u);
-                    if ((int)old == k + 1) {
-                        p = true;
-                        s_lev[w] = (uint16_t)(round + 1);
-                        ab = coff[w];
-                        na = coff[w + 1] - ab;
-                    }
+            for (int j = 0; j < CORE_RUN; j++) {
+                own[j] = live[j] ? wv[j] / per : 0;
+                idx[j] = live[j] ? wv[j] - own[j] * per : 0;
+                if (live[j]) live[j] = cl.map_shared_rank(s_lev, own[j])[idx[j]] == UNSET;
+            }
+            uint32_t old[CORE_RUN];
+#pragma unroll
+            for (int j = 0; j < CORE_RUN; j++) old[j] = live[j] ? atomicSub(cl.map_shared_rank(s_deg, own[j]) + idx[j], 1u) : 0;
+#pragma unroll
+            for (int j = 0; j < CORE_RUN; j++) {
+                if (live[j] && (int)old[j] == k + 1) {
+                    cl.map_shared_rank(s_lev, own[j])[idx[j]] = round + 1;
+                    const uint32_t at = atomicAdd(cl.map_shared_rank(s_fcnt, own[j]) + nxt, 1u);
+                    cl.map_shared_rank(s_front, own[j])[nxt * per + at] = idx[j];
+                    atomicAdd(&s_tot[slot], 1u);
                 }
-                push(p, ab, na, nxt);
             }
         }
         __syncthreads();
-        fn = (uint32_t)(s_cnt[nxt] >> 40);
-        fe = (uint32_t)(s_cnt[nxt] & MASK40);
-        cur = nxt;
+        if (tid == 0) s_fcnt[cur] = 0;  // consumed; others push into it only after the barrier
+        cl.sync();
+        if (tid < csize) s_peer[tid] = cl.map_shared_rank(s_tot, tid)[slot];
+        __syncthreads();
+        uint32_t pushed = 0;
+        for (uint32_t j = 0; j < csize; j++) pushed += s_peer[j];
         round++;
-        if (round > R + 1) break;  // cannot happen: every round removes a vertex
+        cur = nxt;
+        need_level = pushed == 0;
+        if (round > R + 1) {  // cannot happen: every round removes a vertex
+            ok = false;
+            break;
+        }
     }
-    __syncthreads();
-    for (uint32_t i = tid; i < R; i += TAIL_THREADS) level[rem[i]] = round0 + s_lev[i];
-    if (tid == 0) {
+    for (uint32_t i = tid; i < my_n; i += CORE_THREADS) level[rem[base_lid + i]] = round0 + s_lev[i];
+    if (crank == 0 && tid == 0) {
         ctl->rounds = round0 + round;
         ctl->kappa = kappa;
-        if (removed < R) ctl->error = 1;
+        ctl->handoff = 0;
+        if (!ok) ctl->error = 1;
     }
+    cl.sync();  // no CTA leaves while another may still read its shared memory
 }
+
 
 __device__ __forceinline__ uint32_t mix32(uint64_t x) {
     // splitmix64 finaliser, used only to draw a random vertex order
@@ -1338,25 +1387,32 @@ int peel_grid_ctas() {
     ctas = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return ctas;
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-    cudaFuncSetAttribute(peel_kernel<GridSync>, cudaFuncAttributeMaxDynamicSharedMemorySize, PEEL_SMEM);
-    if (coop && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, peel_kernel<GridSync>, PEEL_THREADS,
+    cudaFuncSetAttribute(peel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, PEEL_SMEM);
+    if (coop && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, peel_kernel, PEEL_THREADS,
                                                               PEEL_SMEM) == cudaSuccess)
         ctas = std::max(0, per_sm) * sm_count();
     cudaGetLastError();
     return ctas;
 }
 
-int peel_cluster_size() {
+// Cluster size for the core peel: 16 CTAs when such a cluster fits, else 8;
+// -1 when neither does.
+int core_cluster_size() {
     static int best = 0;
     if (best) return best;
-    cudaFuncSetAttribute(peel_kernel<ClusterSync>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    cudaFuncSetAttribute(peel_kernel<ClusterSync>, cudaFuncAttributeMaxDynamicSharedMemorySize, PEEL_SMEM);
-    best = 8;
-    for (int c = 16; c > 8; c /= 2) {
+    best = -1;
+    cudaFuncSetAttribute(peel_core_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    for (int c = (int)CORE_MAX_CLUSTER; c >= 8; c /= 2) {
+        const size_t smem = core_smem_bytes(PEEL_GRID_STOP / c);
+        if (cudaFuncSetAttribute(peel_core_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(c);
-        cfg.blockDim = dim3(PEEL_THREADS);
-        cfg.dynamicSmemBytes = PEEL_SMEM;
+        cfg.blockDim = dim3(CORE_THREADS);
+        cfg.dynamicSmemBytes = smem;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeClusterDimension;
         attr[0].val.clusterDim.x = c;
@@ -1365,13 +1421,47 @@ int peel_cluster_size() {
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         int clusters = 0;
-        if (cudaOccupancyMaxActiveClusters(&clusters, peel_kernel<ClusterSync>, &cfg) == cudaSuccess && clusters >= 1) {
+        if (cudaOccupancyMaxActiveClusters(&clusters, peel_core_kernel, &cfg) == cudaSuccess && clusters >= 1) {
             best = c;
             break;
         }
         cudaGetLastError();
     }
     return best;
+}
+
+// Launches the in-place sort of the pairs of size class c (list of n pairs).
+template <int E, int T>
+void launch_seg_group(int64_t *key, const uint32_t *poff, const uint32_t *list, uint32_t n, cudaStream_t s) {
+    constexpr int CTA = T >= 128 ? T : 128, G = CTA / T;
+    const size_t smem = T >= 64 ? (size_t)E * T * 8 : 0;
+    if (smem > 48 * 1024)
+        TTC_CUDA(cudaFuncSetAttribute(seg_sort_group_kernel<E, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+    int occ = 0;
+    TTC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, seg_sort_group_kernel<E, T>, CTA, smem));
+    const unsigned grid = std::min<uint32_t>(ceil_div(n, G), (uint32_t)sm_count() * std::max(1, occ));
+    seg_sort_group_kernel<E, T><<<grid, CTA, smem, s>>>(key, poff, list, n);
+    TTC_LAUNCH_CHECK();
+}
+
+void seg_sort_class(int c, int64_t *key, const uint32_t *poff, const uint32_t *list, uint32_t n, cudaStream_t s) {
+    switch (c) {
+        case 0:
+            seg_sort_small_kernel<<<grid_for((size_t)n * 32), TPB, 0, s>>>(key, poff, list, n);
+            TTC_LAUNCH_CHECK();
+            break;
+        case 1: launch_seg_group<2, 32>(key, poff, list, n, s); break;      // 33..64
+        case 2: launch_seg_group<4, 32>(key, poff, list, n, s); break;      // ..128
+        case 3: launch_seg_group<8, 32>(key, poff, list, n, s); break;      // ..256
+        case 4: launch_seg_group<16, 32>(key, poff, list, n, s); break;     // ..512
+        case 5: launch_seg_group<8, 128>(key, poff, list, n, s); break;     // ..1024
+        case 6: launch_seg_group<4, 512>(key, poff, list, n, s); break;     // ..2048
+        case 7: launch_seg_group<8, 512>(key, poff, list, n, s); break;     // ..4096
+        case 8: launch_seg_group<16, 512>(key, poff, list, n, s); break;    // ..8192
+        case 9: launch_seg_group<32, 512>(key, poff, list, n, s); break;    // ..16384
+        default: fail(TTC_ERR_INTERNAL, "per-pair sort: no size class %d", c);
+    }
 }
 
 void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, const int64_t *t_in, uint64_t m_in,
@@ -1513,39 +1603,32 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
     prof_end(g, s);
     prof_begin(g, s, "load:pair_lists");
     if (seg_sort_after) {
-        // sort each pair's keys: warps for pairs of <= SEG_MID_CAP edges, CTAs
-        // up to SEG_BIG_CAP; a longer pair sends the whole array through a
-        // stable time sort and a second pair sort instead
-        DevBuf<uint32_t> small(ms, s), mid(ms, s), big(ms, s);
-        DevBuf<unsigned int> cnt(4, s);  // small, mid, big counts; longest pair
-        TTC_CUDA(cudaMemsetAsync(cnt.get(), 0, 16, s));
-        seg_classify_kernel<<<grid_for(ms), TPB, 0, s>>>(g->poff.get(), ms, small.get(), mid.get(), big.get(),
-                                                         cnt.get(), cnt.get() + 3);
+        // sort each pair's keys in place by size class; a pair longer than
+        // SEG_BIG_CAP sends the whole array through a stable time sort and a
+        // second pair sort instead
+        DevBuf<unsigned int> cnt(SEG_CLASSES, s);
+        TTC_CUDA(cudaMemsetAsync(cnt.get(), 0, SEG_CLASSES * 4, s));
+        seg_classify_kernel<false><<<grid_for(ms), TPB, 0, s>>>(g->poff.get(), ms, cnt.get(), nullptr);
         TTC_LAUNCH_CHECK();
-        unsigned int hc[4];
-        TTC_CUDA(cudaMemcpyAsync(hc, cnt.get(), 16, cudaMemcpyDeviceToHost, s));
+        unsigned int hc[SEG_CLASSES], base[SEG_CLASSES];
+        TTC_CUDA(cudaMemcpyAsync(hc, cnt.get(), sizeof hc, cudaMemcpyDeviceToHost, s));
         TTC_CUDA(cudaStreamSynchronize(s));
-        const uint32_t nsmall = hc[0], nmid = hc[1], nbig = hc[2], longest = hc[3];
-        if (longest <= SEG_BIG_CAP) {
+        if (hc[SEG_CLASSES - 1] == 0) {
+            unsigned int run = 0;
+            for (int c = 0; c < SEG_CLASSES; c++) {
+                base[c] = run;
+                run += hc[c];
+            }
+            DevBuf<uint32_t> list(run ? run : 1, s);
+            if (run) {
+                TTC_CUDA(cudaMemcpyAsync(cnt.get(), base, sizeof base, cudaMemcpyHostToDevice, s));
+                seg_classify_kernel<true><<<grid_for(ms), TPB, 0, s>>>(g->poff.get(), ms, cnt.get(), list.get());
+                TTC_LAUNCH_CHECK();
+            }
             seg_sort_tiny_kernel<<<grid_for(ms), TPB, 0, s>>>(g->key.get(), g->poff.get(), ms);
             TTC_LAUNCH_CHECK();
-            if (nsmall) {
-                seg_sort_small_kernel<<<grid_for((size_t)nsmall * 32), TPB, 0, s>>>(g->key.get(), g->poff.get(),
-                                                                                  small.get(), nsmall);
-                TTC_LAUNCH_CHECK();
-            }
-            if (nmid) {
-                seg_sort_mid_kernel<<<std::min<uint32_t>(ceil_div(nmid, SEG_MID_WARPS), sm_count() * 7),
-                                      SEG_MID_WARPS * 32, 0, s>>>(g->key.get(), g->poff.get(), mid.get(), nmid);
-                TTC_LAUNCH_CHECK();
-            }
-            if (nbig) {
-                TTC_CUDA(cudaFuncSetAttribute(seg_sort_big_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)(SEG_BIG_CAP * 8)));
-                seg_sort_big_kernel<<<std::min<uint32_t>(nbig, sm_count()), SEG_BIG_THREADS, SEG_BIG_CAP * 8, s>>>(
-                    g->key.get(), g->poff.get(), big.get(), nbig);
-                TTC_LAUNCH_CHECK();
-            }
+            for (int c = 0; c < SEG_CLASSES - 1; c++)
+                if (hc[c]) seg_sort_class(c, g->key.get(), g->poff.get(), list.get() + base[c], hc[c], s);
         } else {
             radix_sort_u64_u64_range(reinterpret_cast<uint64_t *>(g->key.get()), pkey.get(), m, g->shift,
                                      g->shift + span_bits, s);
@@ -1594,45 +1677,28 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
                  *oA = foffA.get(), *oB = foffB.get();
         uint32_t n32 = (uint32_t)n;
         PeelCtl *pc = ctl.get();
-        int resume = 0;
-        // stage 1: every SM, while many vertices remain
-        const int grid_ctas = peel_grid_ctas();
-        if (n > PEEL_GRID_STOP && grid_ctas > 0) {
+        // stage 1: every SM, down to PEEL_GRID_STOP vertices (one CTA when
+        // cooperative launches are unavailable)
+        {
             uint32_t stop = PEEL_GRID_STOP;
             void *args[] = {(void *)&a_off, (void *)&a_adj, (void *)&pd, (void *)&lv, (void *)&rA, (void *)&rB,
                             (void *)&fA, (void *)&fB, (void *)&oA, (void *)&oB, (void *)&n32, (void *)&stop,
-                            (void *)&resume, (void *)&pc};
-            TTC_CUDA(cudaLaunchCooperativeKernel((const void *)peel_kernel<GridSync>, dim3(grid_ctas),
-                                                 dim3(PEEL_THREADS), args, PEEL_SMEM, s));
+                            (void *)&pc};
+            const int grid_ctas = peel_grid_ctas();
+            if (grid_ctas > 0)
+                TTC_CUDA(cudaLaunchCooperativeKernel((const void *)peel_kernel, dim3(grid_ctas), dim3(PEEL_THREADS),
+                                                     args, PEEL_SMEM, s));
+            else
+                TTC_CUDA(cudaLaunchKernel((const void *)peel_kernel, dim3(1), dim3(PEEL_THREADS), args, PEEL_SMEM, s));
             note_launch();
-            peel_stage_reset_kernel<<<1, 1, 0, s>>>(pc);
-            TTC_LAUNCH_CHECK();
-            resume = 1;
         }
-        // stage 2: one thread-block cluster, down to PEEL_TAIL vertices
-        int cluster = peel_cluster_size();
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(cluster);
-        cfg.blockDim = dim3(PEEL_THREADS);
-        cfg.dynamicSmemBytes = PEEL_SMEM;
-        cfg.stream = s;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = cluster;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        TTC_CUDA(cudaLaunchKernelEx(&cfg, peel_kernel<ClusterSync>, a_off, a_adj, pd, lv, rA, rB, fA, fB, oA, oB,
-                                    n32, PEEL_TAIL, resume, pc));
-        note_launch();
         PeelCtl out = read_scalar(ctl.get(), s);
         if (out.error) fail(TTC_ERR_INTERNAL, "k-core peel did not finish");
         if (out.handoff) {
-            // the remaining core: local ids, induced adjacency, one-CTA tail
+            // stage 2, the core: local ids, induced adjacency, one cluster
             const uint32_t R = out.rem_n;
             const uint32_t *rem = out.rem_in_b ? remB.get() : remA.get();
-            uint32_t *lid = frontA.get();  // free after the cluster phase
+            uint32_t *lid = frontA.get();  // free after the first stage
             DevBuf<uint32_t> cdeg(R, s), coff(R + 1, s);
             tail_ids_kernel<<<grid_for(R), TPB, 0, s>>>(rem, R, pdeg.get(), lid, cdeg.get());
             TTC_LAUNCH_CHECK();
@@ -1647,13 +1713,26 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
             tail_adj_kernel<<<sm_count() * 8, 256, 0, s>>>(rem, R, chunk_pre.get(), adj_off.get(), adj.get(),
                                                            level.get(), lid, coff.get(), cursor.get(), cadj.get());
             TTC_LAUNCH_CHECK();
-            TTC_CUDA(cudaFuncSetAttribute(peel_tail_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)TAIL_SMEM));
-            peel_tail_kernel<<<1, TAIL_THREADS, TAIL_SMEM, s>>>(rem, R, coff.get(), cadj.get(), level.get(), out.k,
-                                                                out.rounds, ctl.get());
-            TTC_LAUNCH_CHECK();
+            const int cluster = core_cluster_size();
+            if (cluster <= 0) fail(TTC_ERR_CUDA, "no thread-block cluster of 8 or 16 CTAs fits this device");
+            const uint32_t per = (R + cluster - 1) / cluster;
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(cluster);
+            cfg.blockDim = dim3(CORE_THREADS);
+            cfg.dynamicSmemBytes = core_smem_bytes(per);
+            cfg.stream = s;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = cluster;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            TTC_CUDA(cudaLaunchKernelEx(&cfg, peel_core_kernel, rem, R, per, (const uint32_t *)coff.get(),
+                                        (const uint16_t *)cadj.get(), level.get(), ctl.get()));
+            note_launch();
             out = read_scalar(ctl.get(), s);
-            if (out.error) fail(TTC_ERR_INTERNAL, "k-core peel tail did not finish");
+            if (out.error) fail(TTC_ERR_INTERNAL, "k-core peel of the core did not finish");
         }
         st.peel_rounds = out.rounds;
     }
