@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--scale", type=float, default=1.0, help="workload scale (1.0 = the full workload)")
     ap.add_argument("--query-iters", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", choices=["plain", "multi", "serve"], default="plain",
+    ap.add_argument("--mode", choices=["plain", "multi", "serve", "grid"], default="plain",
                     help="plain: the power-law workload (default line); multi: many graphs in one launch; "
                          "serve: Poisson queries against a resident pool")
     ap.add_argument("--graphs", type=int, default=4096, help="multi: number of graphs")
@@ -145,14 +145,14 @@ def allreduce_max(x, ws, device=None):
 
 
 # ------------------------------------------------------------------ CPU oracle timing
-SAMPLE_SCALE = 0.05
+SAMPLE_SCALE = 0.15
 
 
 def oracle_sample(delta, reps=3):
     """Times the oracle (O1, every host core) on a bounded sample of the
-    workload: the same recipe at 5% scale (50K vertices, 500K pairs, about
-    3M edges), whole graph, `reps` runs.  Returns (edges/s, description,
-    cores, seconds per run)."""
+    workload: the same recipe at 15% scale (150K vertices, 1.5M pairs, about
+    9M edges), whole graph, `reps` runs (about 10 s of host work).  Returns
+    (edges/s, description, cores, seconds per run)."""
     import oracle
     from paper_2106_02762_gb300 import synth
     oracle.build()
@@ -394,6 +394,39 @@ def run_serve(args):
           flush=True)
 
 
+# ------------------------------------------------------------------ δ-grid
+def run_grid(args):
+    """δ-grid analytics on the power-law workload: a 16 x 16 (δ12, δ23) grid,
+    log-spaced from 60 s to δ13 = 1 day, in one batched call; reports the
+    time per grid and the range of the cyclic (T4 + T8) share."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2106_02762_gb300 import ttc
+    src, dst, t, delta, name = workload(args.scale)
+    g = ttc.Graph(src, dst, t)
+    d13 = 86400
+    axis = np.unique(np.round(np.logspace(np.log10(60), np.log10(d13), 16)).astype(np.int64))
+    for _ in range(max(1, args.warmup)):
+        counts, cyc = g.count_grid(d13, axis, axis)
+    times = []
+    for _ in range(max(1, args.steps)):
+        torch.cuda.synchronize()
+        w = time.perf_counter()
+        counts, cyc = g.count_grid(d13, axis, axis)
+        times.append(time.perf_counter() - w)
+    sec = statistics.median(times)
+    k = axis.size * axis.size
+    info = g.info()
+    g.free()
+    print(json.dumps({"mode": "grid", "metric": "delta-grid queries/s", "grid": [int(axis.size), int(axis.size)],
+                      "d13": d13, "axis": axis.tolist(), "ms_per_grid": sec * 1e3, "queries_per_s": k / sec,
+                      "edges_per_s_per_query": info["m"] * k / sec,
+                      "cyclic_share_min": float(cyc.min()), "cyclic_share_max": float(cyc.max()),
+                      "cyclic_share_at_d12_eq_d23": [float(cyc[i, i]) for i in range(axis.size)],
+                      "config": {"workload": name}}), flush=True)
+
+
 # ------------------------------------------------------------------ our arm
 def run_ours(args):
     import torch
@@ -583,6 +616,8 @@ def main():
         run_multi(args)
     elif args.mode == "serve":
         run_serve(args)
+    elif args.mode == "grid":
+        run_grid(args)
     else:
         run_ours(args)
 

@@ -155,6 +155,16 @@ ttc_status ttc_count(ttc_graph *g, const ttc_delta *d, uint64_t out[TTC_NUM_TYPE
  * array of k * 8 counts, row q for d[q]. */
 ttc_status ttc_count_batch(ttc_graph *g, const ttc_delta *d, uint32_t k, uint64_t *out);
 
+/* δ-grid analytics: the counts at every (δ1,2, δ2,3) of the grid
+ * d12[0..n12) x d23[0..n23) for one δ1,3, in one batched pass (the
+ * dependence of the type mix on the windows, Sec. 6 and Figs. 1 and 5).
+ * out: n12 * n23 * TTC_NUM_TYPES uint64, row-major [i12][i23][type].
+ * cyclic (may be NULL): n12 * n23 doubles, the share of the two cyclic types
+ * (T4 + T8) in the total of that grid point (0 when the total is 0).
+ * Each δ as in ttc_count; TTC_ERR_RANGE if n12 * n23 exceeds 2^20. */
+ttc_status ttc_count_grid(ttc_graph *g, int64_t d13, const int64_t *d12, uint32_t n12, const int64_t *d23,
+                          uint32_t n23, uint64_t *out, double *cyclic);
+
 /* As ttc_count_batch, but asynchronous: d_dev (k deltas, each component in
  * [0, 2^62]; normalised on the device) and out_dev (k * 8 uint64) are device
  * pointers, and the work is queued on `stream` (cudaStream_t; NULL = the

@@ -405,6 +405,35 @@ ttc_status ttc_count_batch(ttc_graph *g, const ttc_delta *d, uint32_t k, uint64_
     TTC_API_END
 }
 
+ttc_status ttc_count_grid(ttc_graph *g, int64_t d13, const int64_t *d12, uint32_t n12, const int64_t *d23,
+                          uint32_t n23, uint64_t *out, double *cyclic) {
+    if (!g || (n12 && n23 && (!d12 || !d23 || !out))) {
+        set_last_error("NULL argument");
+        return TTC_ERR_INVALID;
+    }
+    const uint64_t k = (uint64_t)n12 * n23;
+    if (!k) return TTC_OK;
+    if (k > (uint64_t(1) << 20)) {
+        set_last_error("grid of " + std::to_string(k) + " points exceeds 2^20");
+        return TTC_ERR_RANGE;
+    }
+    TTC_API_BEGIN
+    std::vector<ttc_delta> d(k);
+    for (uint32_t i = 0; i < n12; i++)
+        for (uint32_t j = 0; j < n23; j++) d[(size_t)i * n23 + j] = ttc_delta{d13, d12[i], d23[j]};
+    const ttc_status rc = run_queries(g, d.data(), (uint32_t)k, out);
+    if (rc == TTC_OK && cyclic) {
+        for (uint64_t q = 0; q < k; q++) {
+            const uint64_t *c = out + 8 * q;
+            long double tot = 0;
+            for (int t = 0; t < 8; t++) tot += (long double)c[t];
+            cyclic[q] = tot > 0 ? (double)(((long double)c[3] + (long double)c[7]) / tot) : 0.0;
+        }
+    }
+    return rc;
+    TTC_API_END
+}
+
 ttc_status ttc_count_batch_async(ttc_graph *g, const ttc_delta *d_dev, uint32_t k, uint64_t *out_dev,
                                  void *stream) {
     if (!g || (k && (!d_dev || !out_dev))) {

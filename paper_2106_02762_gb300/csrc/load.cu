@@ -371,6 +371,7 @@ struct PeelCtl {
     unsigned int rem_in_b; // the remaining list is in remB (else remA)
     unsigned int pad;
     unsigned int bar_count, bar_gen;  // grid barrier of the grid-wide stage
+    unsigned int core_alive;          // vertices the cluster stage hands to one CTA
 };
 
 constexpr uint64_t MASK40 = (uint64_t(1) << 40) - 1;
@@ -697,9 +698,8 @@ __global__ void __launch_bounds__(PEEL_THREADS)
                         wv[j] = adj[base + (e - fbeg)];
                     }
                 }
-#pragma unroll
-                for (int j = 0; j < PEEL_RUN; j++)
-                    if (live[j]) live[j] = __ldcg(level + wv[j]) == UNSET;
+                // no level check: a removed vertex already has degree <= k,
+                // so a decrement returns k + 1 only for a remaining vertex
             } else {
 #pragma unroll
                 for (int j = 0; j < PEEL_RUN; j++) live[j] = false;
@@ -825,7 +825,9 @@ __global__ void __launch_bounds__(256)
 // read by every CTA between the barriers that end round r and r + 1 and is
 // zeroed in round r + 2.  Continues from level ctl->k and round ctl->rounds;
 // writes level[] of the core vertices and the final rounds and kappa.
-constexpr int CORE_THREADS = 1024;
+constexpr int CORE_THREADS = 256;       // per CTA of the cluster: rounds are small, few idle warps
+constexpr int CORE_TAIL_THREADS = 1024;  // the one-CTA run of the last PEEL_TAIL vertices
+constexpr uint32_t PEEL_TAIL = 8192;     // the cluster hands the last this many to one CTA
 constexpr int CORE_RUN = 4;          // relaxed edges per thread per step
 constexpr uint32_t CORE_MAX_CLUSTER = 16;
 
@@ -858,26 +860,41 @@ __device__ __forceinline__ uint32_t core_block_excl_scan(uint32_t x, uint32_t *s
     return s_warp[w] + inc - x;
 }
 
-__global__ void __launch_bounds__(CORE_THREADS)
+// CLUSTER = false: one CTA owns every vertex (plain shared memory, block
+// barriers); CLUSTER = true: `per` (a power of two) vertices per CTA.
+template <bool CLUSTER>
+__global__ void __launch_bounds__(CORE_TAIL_THREADS, 1)
     peel_core_kernel(const uint32_t *rem, uint32_t R, uint32_t per, const uint32_t *coff, const uint16_t *cadj,
-                     uint32_t *level, PeelCtl *ctl) {
+                     uint32_t *level, int *deg, uint32_t stop_n, uint32_t *alive_out, PeelCtl *ctl) {
     cg::cluster_group cl = cg::this_cluster();
-    const uint32_t crank = cl.block_rank(), csize = cl.num_blocks();
-    const uint32_t tid = threadIdx.x, lane = tid & 31;
+    const uint32_t crank = CLUSTER ? cl.block_rank() : 0u, csize = CLUSTER ? cl.num_blocks() : 1u;
+    const uint32_t per_lg = CLUSTER ? (uint32_t)(__ffs(per) - 1) : 0u;
+    // shared memory of the CTA that owns a vertex
+    auto at = [&](auto *p, uint32_t own) {
+        if constexpr (CLUSTER) return cl.map_shared_rank(p, own);
+        else return p;
+    };
+    auto csync = [&]() {
+        if constexpr (CLUSTER) cl.sync();
+        else __syncthreads();
+    };
+    const uint32_t tid = threadIdx.x, lane = tid & 31, nthr = blockDim.x;
     extern __shared__ __align__(16) uint32_t core_smem[];
     uint32_t *s_deg = core_smem, *s_ab = s_deg + per, *s_na = s_ab + per, *s_foff = s_na + per;
     uint32_t *s_front = s_foff + per;  // [2][per]
     uint32_t *s_lev = s_front + 2 * per;
     __shared__ unsigned int s_fcnt[2];                 // entries in my frontier buffers
-    __shared__ unsigned int s_tot[3];                  // pushes made by this CTA, per round mod 3
-    __shared__ unsigned int s_peer[CORE_MAX_CLUSTER];  // the cluster's push tallies of one round
+    __shared__ unsigned int s_tot[3];                  // the cluster's pushes, per round mod 3
+    __shared__ unsigned int s_peer[1];                 // this CTA's pushes in the current round
     __shared__ int s_mins[CORE_MAX_CLUSTER];           // each CTA's smallest remaining degree
+    __shared__ unsigned int s_alive[CORE_MAX_CLUSTER]; // and its number of remaining vertices
+    __shared__ unsigned int s_nalive;
     __shared__ int s_min;
     __shared__ uint32_t s_warp[32];
     __shared__ uint32_t s_fe;
     const uint32_t base_lid = crank * per;
     const uint32_t my_n = R > base_lid ? min(per, R - base_lid) : 0;
-    for (uint32_t i = tid; i < my_n; i += CORE_THREADS) {
+    for (uint32_t i = tid; i < my_n; i += nthr) {
         const uint32_t ab = coff[base_lid + i], na = coff[base_lid + i + 1] - ab;
         s_ab[i] = ab;
         s_na[i] = na;
@@ -887,33 +904,69 @@ __global__ void __launch_bounds__(CORE_THREADS)
     if (tid == 0) {
         s_fcnt[0] = s_fcnt[1] = 0;
         s_tot[0] = s_tot[1] = s_tot[2] = 0;
+        s_peer[0] = 0;
         s_min = INT_MAX;
+        s_nalive = 0;
     }
     int k = __ldcg(&ctl->k);
     const uint32_t round0 = __ldcg(&ctl->rounds);
     uint32_t kappa = __ldcg(&ctl->kappa);
     uint32_t round = 0, cur = 0;
-    bool need_level = true, ok = true;
-    cl.sync();  // every CTA's state is initialised before any remote access
+    bool need_level = true, ok = true, stopped = false;
+    csync();  // every CTA's state is initialised before any remote access
     for (;;) {
         if (need_level) {
             // new level: the cluster's smallest remaining degree, then every
             // owned vertex of degree <= k joins this CTA's frontier
             int my = INT_MAX;
-            for (uint32_t i = tid; i < my_n; i += CORE_THREADS)
-                if (s_lev[i] == UNSET) my = min(my, (int)s_deg[i]);
+            unsigned int na = 0;
+            for (uint32_t i = tid; i < my_n; i += nthr)
+                if (s_lev[i] == UNSET) {
+                    my = min(my, (int)s_deg[i]);
+                    na++;
+                }
 #pragma unroll
-            for (int o = 16; o; o >>= 1) my = min(my, __shfl_xor_sync(0xffffffffu, my, o));
+            for (int o = 16; o; o >>= 1) {
+                my = min(my, __shfl_xor_sync(0xffffffffu, my, o));
+                na += __shfl_xor_sync(0xffffffffu, na, o);
+            }
             if (lane == 0 && my != INT_MAX) atomicMin(&s_min, my);
+            if (lane == 0 && na) atomicAdd(&s_nalive, na);
             __syncthreads();
-            if (tid < csize) cl.map_shared_rank(s_mins, tid)[crank] = s_min;
-            cl.sync();
-            int g = INT_MAX;
-            for (uint32_t j = 0; j < csize; j++) g = min(g, s_mins[j]);
+            if (tid < csize) {
+                at(s_mins, tid)[crank] = s_min;
+                at(s_alive, tid)[crank] = s_nalive;
+            }
+            csync();
+            int g = lane < csize ? s_mins[lane] : INT_MAX;
+            unsigned int alive = lane < csize ? s_alive[lane] : 0u;
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                g = min(g, __shfl_xor_sync(0xffffffffu, g, o));
+                alive += __shfl_xor_sync(0xffffffffu, alive, o);
+            }
+            if (tid == 0) s_nalive = 0;  // read above; next written after a later barrier
             if (g == INT_MAX) break;  // nothing left anywhere (uniform)
+            if (alive <= stop_n) {
+                // hand the rest to one CTA: its vertices (ids) and their
+                // current degrees; levels of the removed ones below
+                for (uint32_t i = tid; i < my_n; i += nthr) {
+                    if (s_lev[i] == UNSET) {
+                        const uint32_t v = rem[base_lid + i];
+                        alive_out[atomicAdd(&ctl->core_alive, 1u)] = v;
+                        deg[v] = (int)s_deg[i];
+                    }
+                }
+                if (crank == 0 && tid == 0) {
+                    ctl->k = max(k, g);
+                    ctl->rem_n = alive;
+                }
+                stopped = true;
+                break;
+            }
             k = max(k, g);
             kappa = max(kappa, (uint32_t)k);
-            for (uint32_t i = tid; i < my_n; i += CORE_THREADS) {
+            for (uint32_t i = tid; i < my_n; i += nthr) {
                 if (s_lev[i] == UNSET && (int)s_deg[i] <= k) {
                     s_lev[i] = round;
                     s_front[cur * per + atomicAdd(&s_fcnt[cur], 1u)] = i;
@@ -930,7 +983,7 @@ __global__ void __launch_bounds__(CORE_THREADS)
         {
             // edge offsets of the frontier entries (exclusive scan of their
             // adjacency lengths), each thread a run of consecutive entries
-            const uint32_t per_t = (fn + CORE_THREADS - 1) / CORE_THREADS;
+            const uint32_t per_t = (fn + nthr - 1) / nthr;
             const uint32_t b0 = min(fn, tid * per_t), b1 = min(fn, b0 + per_t);
             uint32_t sum = 0;
             for (uint32_t i = b0; i < b1; i++) sum += s_na[F[i]];
@@ -945,7 +998,7 @@ __global__ void __launch_bounds__(CORE_THREADS)
             __syncthreads();
         }
         const uint32_t fe = s_fe;
-        for (uint32_t e0 = tid * CORE_RUN; e0 - tid * CORE_RUN < fe; e0 += CORE_THREADS * CORE_RUN) {
+        for (uint32_t e0 = tid * CORE_RUN; e0 - tid * CORE_RUN < fe; e0 += nthr * CORE_RUN) {
             uint32_t wv[CORE_RUN];
             bool live[CORE_RUN];
             if (e0 < fe) {
@@ -975,33 +1028,35 @@ __global__ void __launch_bounds__(CORE_THREADS)
 #pragma unroll
                 for (int j = 0; j < CORE_RUN; j++) live[j] = false;
             }
+            // no level check: a removed vertex already has degree <= k, so
+            // a decrement can return k + 1 only for a remaining vertex, once
             uint32_t own[CORE_RUN], idx[CORE_RUN];
 #pragma unroll
             for (int j = 0; j < CORE_RUN; j++) {
-                own[j] = live[j] ? wv[j] / per : 0;
-                idx[j] = live[j] ? wv[j] - own[j] * per : 0;
-                if (live[j]) live[j] = cl.map_shared_rank(s_lev, own[j])[idx[j]] == UNSET;
+                own[j] = CLUSTER && live[j] ? wv[j] >> per_lg : 0u;
+                idx[j] = live[j] ? (CLUSTER ? wv[j] & (per - 1) : wv[j]) : 0u;
             }
             uint32_t old[CORE_RUN];
 #pragma unroll
-            for (int j = 0; j < CORE_RUN; j++) old[j] = live[j] ? atomicSub(cl.map_shared_rank(s_deg, own[j]) + idx[j], 1u) : 0;
+            for (int j = 0; j < CORE_RUN; j++) old[j] = live[j] ? atomicSub(at(s_deg, own[j]) + idx[j], 1u) : 0;
 #pragma unroll
             for (int j = 0; j < CORE_RUN; j++) {
                 if (live[j] && (int)old[j] == k + 1) {
-                    cl.map_shared_rank(s_lev, own[j])[idx[j]] = round + 1;
-                    const uint32_t at = atomicAdd(cl.map_shared_rank(s_fcnt, own[j]) + nxt, 1u);
-                    cl.map_shared_rank(s_front, own[j])[nxt * per + at] = idx[j];
-                    atomicAdd(&s_tot[slot], 1u);
+                    at(s_lev, own[j])[idx[j]] = round + 1;
+                    const uint32_t slot_at = atomicAdd(at(s_fcnt, own[j]) + nxt, 1u);
+                    at(s_front, own[j])[nxt * per + slot_at] = idx[j];
+                    atomicAdd(&s_peer[0], 1u);
                 }
             }
         }
         __syncthreads();
         if (tid == 0) s_fcnt[cur] = 0;  // consumed; others push into it only after the barrier
-        cl.sync();
-        if (tid < csize) s_peer[tid] = cl.map_shared_rank(s_tot, tid)[slot];
-        __syncthreads();
-        uint32_t pushed = 0;
-        for (uint32_t j = 0; j < csize; j++) pushed += s_peer[j];
+        // add this CTA's pushes to every CTA's tally of this round before the
+        // barrier, so that after it each CTA reads the total locally
+        if (tid < csize && s_peer[0]) atomicAdd(at(s_tot, tid) + slot, s_peer[0]);
+        csync();
+        const uint32_t pushed = s_tot[slot];
+        if (tid == 0) s_peer[0] = 0;  // read above, before this CTA's barrier; next written after it
         round++;
         cur = nxt;
         need_level = pushed == 0;
@@ -1010,14 +1065,15 @@ __global__ void __launch_bounds__(CORE_THREADS)
             break;
         }
     }
-    for (uint32_t i = tid; i < my_n; i += CORE_THREADS) level[rem[base_lid + i]] = round0 + s_lev[i];
+    for (uint32_t i = tid; i < my_n; i += nthr)
+        if (s_lev[i] != UNSET) level[rem[base_lid + i]] = round0 + s_lev[i];
     if (crank == 0 && tid == 0) {
         ctl->rounds = round0 + round;
         ctl->kappa = kappa;
-        ctl->handoff = 0;
+        ctl->handoff = stopped ? 1u : 0u;
         if (!ok) ctl->error = 1;
     }
-    cl.sync();  // no CTA leaves while another may still read its shared memory
+    csync();  // no CTA leaves while another may still read its shared memory
 }
 
 
@@ -1116,36 +1172,48 @@ __global__ void widen_kernel(const uint32_t *a, const uint32_t *b, size_t n, uin
 
 // ---------------------------------------------------------------- triangles
 struct RecCtx {
-    const uint32_t *poff;
-    const uint2 *pv;
     uint32_t labeling;
     uint64_t light_max;
 };
 
-__device__ __forceinline__ uint32_t psize(const RecCtx &c, uint32_t p) { return c.poff[p + 1] - c.poff[p]; }
+// Per oriented edge a -> b (rank order): its pair's multiplicity σ (capped at
+// 2^31 - 1; a cap only moves a triangle between two exact counting bins) and,
+// in bit 31, whether id(a) > id(b).
+constexpr uint32_t SIG_MASK = 0x7fffffffu;
 
-// Names the triangle's vertices u, v, w for counting and returns the record.
-// (u0, v0, w0) come from the enumeration (u0 < v0 < w0 in the ordering), with
-// pairs p_uv, p_uw, p_vw.
-__device__ uint4 make_record(const RecCtx &c, uint32_t u0, uint32_t v0, uint32_t w0, uint32_t p_uv,
-                             uint32_t p_uw, uint32_t p_vw, bool *heavy) {
-    uint32_t U = u0, V = v0, W = w0, A = p_uv, B = p_uw, C = p_vw;
-    const uint32_t s_uv = psize(c, p_uv), s_uw = psize(c, p_uw), s_vw = psize(c, p_vw);
-    if (c.labeling == TTC_LABEL_HEAVIEST_VW) {
-        if (s_uw > s_vw && s_uw >= s_uv) {  // {u0, w0} is only searched
-            U = v0; V = u0; W = w0; A = p_uv; B = p_vw; C = p_uw;
-        } else if (s_uv > s_vw && s_uv > s_uw) {  // {u0, v0}
-            U = w0; V = u0; W = v0; A = p_uw; B = p_vw; C = p_uv;
-        }
+__global__ void osig_kernel(const uint32_t *opair, const uint32_t *osrc, const uint32_t *onbr, const uint32_t *id_of,
+                            const uint32_t *poff, size_t ms, uint32_t *osig) {
+    GRID_STRIDE(i, ms) {
+        const uint32_t p = opair[i], sig = poff[p + 1] - poff[p];
+        const uint32_t down = id_of[osrc[i]] > id_of[onbr[i]] ? 0x80000000u : 0u;
+        osig[i] = (sig < SIG_MASK ? sig : SIG_MASK) | down;
     }
-    const uint32_t flags = (U > V ? TriRec::FLIP_A : 0u) | (U > W ? TriRec::FLIP_B : 0u) | (V > W ? TriRec::FLIP_C : 0u);
-    *heavy = (uint64_t)psize(c, A) * psize(c, B) >= c.light_max;
-    return make_uint4(A, B, C, flags);
 }
 
-
-
-
+// Names the triangle's vertices u, v, w for counting and returns the record.
+// The triangle was found as u0 < v0 < w0 in the ordering with oriented edges
+// u0 -> v0, u0 -> w0, v0 -> w0: pairs p_*, packed (σ, id order) words s_*.
+// The flip bits say, per record pair, whether the labelled direction runs
+// from the larger id to the smaller.
+__device__ __forceinline__ uint4 make_record(const RecCtx &c, uint32_t s_uv, uint32_t s_uw, uint32_t s_vw,
+                                             uint32_t p_uv, uint32_t p_uw, uint32_t p_vw, bool *heavy) {
+    const uint32_t n_uv = s_uv & SIG_MASK, n_uw = s_uw & SIG_MASK, n_vw = s_vw & SIG_MASK;
+    const bool g_uv = s_uv >> 31, g_uw = s_uw >> 31, g_vw = s_vw >> 31;  // id(u0) > id(v0), ...
+    uint32_t A = p_uv, B = p_uw, C = p_vw, nA = n_uv, nB = n_uw;
+    bool fa = g_uv, fb = g_uw, fc = g_vw;  // (U, V, W) = (u0, v0, w0)
+    if (c.labeling == TTC_LABEL_HEAVIEST_VW) {
+        if (n_uw > n_vw && n_uw >= n_uv) {  // {u0, w0} is only searched: (U, V, W) = (v0, u0, w0)
+            A = p_uv; B = p_vw; C = p_uw; nA = n_uv; nB = n_vw;
+            fa = !g_uv; fb = g_vw; fc = g_uw;
+        } else if (n_uv > n_vw && n_uv > n_uw) {  // {u0, v0}: (U, V, W) = (w0, u0, v0)
+            A = p_uw; B = p_vw; C = p_uv; nA = n_uw; nB = n_vw;
+            fa = !g_uw; fb = !g_vw; fc = g_uv;
+        }
+    }
+    *heavy = (uint64_t)nA * nB >= c.light_max;
+    const uint32_t flags = (fa ? TriRec::FLIP_A : 0u) | (fb ? TriRec::FLIP_B : 0u) | (fc ? TriRec::FLIP_C : 0u);
+    return make_uint4(A, B, C, flags);
+}
 
 // sizes of heavy records and the work statistics of all records
 __global__ void record_stats_kernel(const uint4 *rec, size_t tau, uint64_t n_light, const uint32_t *poff,
@@ -1186,7 +1254,7 @@ __global__ void record_stats_kernel(const uint4 *rec, size_t tau, uint64_t n_lig
 // layout is deterministic).
 constexpr int TRI_THREADS = 256;
 constexpr int TRI_WARPS = TRI_THREADS / 32;
-constexpr uint32_t TRI_NV_CAP = 1024;  // staged N+(v) entries per warp
+constexpr uint32_t TRI_NV_CAP = 448;  // staged N+(v) entries per warp (4 CTAs per SM)
 
 // Items: chunk c of target v covers its in-edges [32 c, 32 c + 32); a vertex
 // with no out-edge closes no triangle as the middle vertex.
@@ -1213,24 +1281,32 @@ __global__ void tri_items_fill_kernel(const uint32_t *item_pre, uint32_t n, uint
 struct TriCsr {
     const uint32_t *onbr;     // out-lists: target ranks, sorted
     const uint32_t *opair;    // pair id of each oriented edge
+    const uint32_t *osig;     // packed (σ, id order) word of each oriented edge
     const uint32_t *out_off;  // out-list offsets by rank
     const uint32_t *osrc;     // source rank of each oriented edge
     const uint32_t *in_off;   // in-list offsets by rank
     const uint32_t *in_e;     // in-lists: positions of the oriented edges
-    const uint32_t *id_of;    // vertex id of each rank
 };
+
+// Shared memory of one warp: N+(v) (target ranks, σ words and, when writing,
+// pair ids) for dv <= TRI_NV_CAP.
+template <bool WRITE>
+constexpr size_t tri_warp_smem() { return (size_t)TRI_NV_CAP * 4 * (WRITE ? 3 : 2); }
 
 template <bool WRITE>
 __global__ void __launch_bounds__(TRI_THREADS)
     tri_enum_kernel(const uint2 *__restrict__ items, uint32_t nitems, TriCsr g, RecCtx rc, uint32_t *cnt_light,
                     uint32_t *cnt_heavy, const uint64_t *light_off, const uint64_t *heavy_off, uint64_t heavy_base,
                     uint4 *rec) {
-    __shared__ uint32_t s_nv[TRI_WARPS][TRI_NV_CAP];
+    extern __shared__ uint32_t tri_smem[];
     __shared__ uint32_t s_excl[TRI_WARPS][33];
-    __shared__ uint32_t s_e[TRI_WARPS][32], s_u[TRI_WARPS][32];
+    __shared__ uint32_t s_e[TRI_WARPS][32], s_se[TRI_WARPS][32], s_pe[TRI_WARPS][32];
+    __shared__ uint64_t s_lo[TRI_WARPS][32], s_ho[TRI_WARPS][32];  // WRITE: each slot's bin offsets
     __shared__ uint32_t s_run[TRI_WARPS][64];  // per in-edge slot: light, heavy hits so far
     const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
+    uint32_t *s_nv = tri_smem + (size_t)w * (tri_warp_smem<WRITE>() / 4);
+    uint32_t *s_nvs = s_nv + TRI_NV_CAP, *s_nvp = s_nvs + TRI_NV_CAP;
     uint32_t staged_v = 0xffffffffu;
     for (uint64_t it = (uint64_t)blockIdx.x * TRI_WARPS + w; it < nitems; it += (uint64_t)gridDim.x * TRI_WARPS) {
         const uint2 item = items[it];
@@ -1239,18 +1315,29 @@ __global__ void __launch_bounds__(TRI_THREADS)
         const bool staged = dv <= TRI_NV_CAP;
         if (staged && staged_v != v) {
             __syncwarp();
-            for (uint32_t i = lane; i < dv; i += 32) s_nv[w][i] = __ldg(g.onbr + vb + i);
+            for (uint32_t i = lane; i < dv; i += 32) {
+                s_nv[i] = __ldg(g.onbr + vb + i);
+                s_nvs[i] = __ldg(g.osig + vb + i);
+                if (WRITE) s_nvp[i] = __ldg(g.opair + vb + i);
+            }
             staged_v = v;
         }
         __syncwarp();
-        const uint32_t *nv = staged ? s_nv[w] : g.onbr + vb;
+        const uint32_t *nv = staged ? s_nv : g.onbr + vb;
+        const uint32_t *nvs = staged ? s_nvs : g.osig + vb;
+        const uint32_t *nvp = staged ? s_nvp : g.opair + vb;
         const uint32_t ib = __ldg(g.in_off + v), din = __ldg(g.in_off + v + 1) - ib;
         const uint32_t i = c0 + lane;
         uint32_t len = 0;
         if (i < din) {
             const uint32_t e = __ldg(g.in_e + ib + i), u = __ldg(g.osrc + e);
             s_e[w][lane] = e;
-            s_u[w][lane] = u;
+            s_se[w][lane] = __ldg(g.osig + e);
+            if (WRITE) {
+                s_pe[w][lane] = __ldg(g.opair + e);
+                s_lo[w][lane] = light_off[e];
+                s_ho[w][lane] = heavy_base + heavy_off[e];
+            }
             len = __ldg(g.out_off + u + 1) - e - 1;  // the suffix of N+(u) after v
         }
         s_run[w][2 * lane] = 0;
@@ -1276,8 +1363,7 @@ __global__ void __launch_bounds__(TRI_THREADS)
                 for (uint32_t step = 16; step; step >>= 1)
                     if (s_excl[w][o + step] <= j) o += step;
                 slot = o;
-                const uint32_t eo = s_e[w][o];
-                const uint32_t ew = eo + 1 + (j - s_excl[w][o]);  // u -> w
+                const uint32_t ew = s_e[w][o] + 1 + (j - s_excl[w][o]);  // u -> w
                 const uint32_t x3 = __ldg(g.onbr + ew);
                 uint32_t lo = 0, len2 = dv;  // x3 in N+(v)
                 while (len2 > 0) {
@@ -1291,8 +1377,8 @@ __global__ void __launch_bounds__(TRI_THREADS)
                 }
                 if (lo < dv && nv[lo] == x3) {
                     hit = true;
-                    r = make_record(rc, __ldg(g.id_of + s_u[w][o]), __ldg(g.id_of + v), __ldg(g.id_of + x3),
-                                    __ldg(g.opair + eo), __ldg(g.opair + ew), __ldg(g.opair + vb + lo), &heavy);
+                    r = make_record(rc, s_se[w][o], __ldg(g.osig + ew), nvs[lo], WRITE ? s_pe[w][o] : 0u,
+                                    WRITE ? __ldg(g.opair + ew) : 0u, WRITE ? nvp[lo] : 0u, &heavy);
                 }
             }
             const unsigned act = __ballot_sync(0xffffffffu, hit);
@@ -1304,11 +1390,7 @@ __global__ void __launch_bounds__(TRI_THREADS)
             __syncwarp();
             if (hit && (peers & lt_mask) == 0) s_run[w][key] += __popc(peers);
             __syncwarp();
-            if (WRITE && hit) {
-                const uint64_t ee = s_e[w][slot];
-                const uint64_t pos = heavy ? heavy_base + heavy_off[ee] + rank : light_off[ee] + rank;
-                rec[pos] = r;
-            }
+            if (WRITE && hit) rec[(heavy ? s_ho[w][slot] : s_lo[w][slot]) + rank] = r;
         }
         __syncwarp();
         if (!WRITE && i < din) {
@@ -1401,14 +1483,16 @@ int core_cluster_size() {
     static int best = 0;
     if (best) return best;
     best = -1;
-    cudaFuncSetAttribute(peel_core_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(peel_core_kernel<true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (cudaFuncSetAttribute(peel_core_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)core_smem_bytes(PEEL_TAIL)) != cudaSuccess ||
+        cudaFuncSetAttribute(peel_core_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)core_smem_bytes(PEEL_GRID_STOP / 8)) != cudaSuccess) {
+        cudaGetLastError();
+        return best;
+    }
     for (int c = (int)CORE_MAX_CLUSTER; c >= 8; c /= 2) {
         const size_t smem = core_smem_bytes(PEEL_GRID_STOP / c);
-        if (cudaFuncSetAttribute(peel_core_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess) {
-            cudaGetLastError();
-            continue;
-        }
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(c);
         cfg.blockDim = dim3(CORE_THREADS);
@@ -1421,7 +1505,7 @@ int core_cluster_size() {
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         int clusters = 0;
-        if (cudaOccupancyMaxActiveClusters(&clusters, peel_core_kernel, &cfg) == cudaSuccess && clusters >= 1) {
+        if (cudaOccupancyMaxActiveClusters(&clusters, peel_core_kernel<true>, &cfg) == cudaSuccess && clusters >= 1) {
             best = c;
             break;
         }
@@ -1695,44 +1779,62 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
         PeelCtl out = read_scalar(ctl.get(), s);
         if (out.error) fail(TTC_ERR_INTERNAL, "k-core peel did not finish");
         if (out.handoff) {
-            // stage 2, the core: local ids, induced adjacency, one cluster
-            const uint32_t R = out.rem_n;
+            // stage 2, the core: the remaining vertices get local ids and their
+            // induced adjacency; one cluster peels them down to PEEL_TAIL
+            // vertices, one CTA the rest (same kernel, one CTA, more threads)
+            uint32_t R = out.rem_n;
             const uint32_t *rem = out.rem_in_b ? remB.get() : remA.get();
-            uint32_t *lid = frontA.get();  // free after the first stage
-            DevBuf<uint32_t> cdeg(R, s), coff(R + 1, s);
-            tail_ids_kernel<<<grid_for(R), TPB, 0, s>>>(rem, R, pdeg.get(), lid, cdeg.get());
-            TTC_LAUNCH_CHECK();
-            exclusive_scan_u32(cdeg.get(), coff.get(), R, s);
-            const uint32_t ce = read_scalar(coff.get() + R, s);
-            DevBuf<uint16_t> cadj(ce ? ce : 1, s);
-            DevBuf<uint32_t> nchunk(R, s), chunk_pre(R + 1, s), cursor(R, s);
-            tail_chunks_kernel<<<grid_for(R), TPB, 0, s>>>(rem, R, adj_off.get(), nchunk.get());
-            TTC_LAUNCH_CHECK();
-            exclusive_scan_u32(nchunk.get(), chunk_pre.get(), R, s);
-            TTC_CUDA(cudaMemsetAsync(cursor.get(), 0, (size_t)R * 4, s));
-            tail_adj_kernel<<<sm_count() * 8, 256, 0, s>>>(rem, R, chunk_pre.get(), adj_off.get(), adj.get(),
-                                                           level.get(), lid, coff.get(), cursor.get(), cadj.get());
-            TTC_LAUNCH_CHECK();
-            const int cluster = core_cluster_size();
-            if (cluster <= 0) fail(TTC_ERR_CUDA, "no thread-block cluster of 8 or 16 CTAs fits this device");
-            const uint32_t per = (R + cluster - 1) / cluster;
-            cudaLaunchConfig_t cfg = {};
-            cfg.gridDim = dim3(cluster);
-            cfg.blockDim = dim3(CORE_THREADS);
-            cfg.dynamicSmemBytes = core_smem_bytes(per);
-            cfg.stream = s;
-            cudaLaunchAttribute attr[1];
-            attr[0].id = cudaLaunchAttributeClusterDimension;
-            attr[0].val.clusterDim.x = cluster;
-            attr[0].val.clusterDim.y = 1;
-            attr[0].val.clusterDim.z = 1;
-            cfg.attrs = attr;
-            cfg.numAttrs = 1;
-            TTC_CUDA(cudaLaunchKernelEx(&cfg, peel_core_kernel, rem, R, per, (const uint32_t *)coff.get(),
-                                        (const uint16_t *)cadj.get(), level.get(), ctl.get()));
-            note_launch();
-            out = read_scalar(ctl.get(), s);
-            if (out.error) fail(TTC_ERR_INTERNAL, "k-core peel of the core did not finish");
+            uint32_t *lid = frontA.get(), *tail_list = frontB.get();  // free after the first stage
+            for (int pass = 0; pass < 2 && R; pass++) {
+                const bool one_cta = R <= PEEL_TAIL;
+                DevBuf<uint32_t> cdeg(R, s), coff(R + 1, s);
+                tail_ids_kernel<<<grid_for(R), TPB, 0, s>>>(rem, R, pdeg.get(), lid, cdeg.get());
+                TTC_LAUNCH_CHECK();
+                exclusive_scan_u32(cdeg.get(), coff.get(), R, s);
+                const uint32_t ce = read_scalar(coff.get() + R, s);
+                DevBuf<uint16_t> cadj(ce ? ce : 1, s);
+                DevBuf<uint32_t> nchunk(R, s), chunk_pre(R + 1, s), cursor(R, s);
+                tail_chunks_kernel<<<grid_for(R), TPB, 0, s>>>(rem, R, adj_off.get(), nchunk.get());
+                TTC_LAUNCH_CHECK();
+                exclusive_scan_u32(nchunk.get(), chunk_pre.get(), R, s);
+                TTC_CUDA(cudaMemsetAsync(cursor.get(), 0, (size_t)R * 4, s));
+                tail_adj_kernel<<<sm_count() * 8, 256, 0, s>>>(rem, R, chunk_pre.get(), adj_off.get(), adj.get(),
+                                                               level.get(), lid, coff.get(), cursor.get(),
+                                                               cadj.get());
+                TTC_LAUNCH_CHECK();
+                const int cluster = core_cluster_size();
+                if (cluster <= 0) fail(TTC_ERR_CUDA, "no thread-block cluster of 8 or 16 CTAs fits this device");
+                const uint32_t ncta = one_cta ? 1u : (uint32_t)cluster;
+                uint32_t per = R;  // one CTA owns all; a cluster CTA a power of two
+                if (!one_cta) {
+                    per = 1;
+                    while (per * ncta < R) per <<= 1;
+                }
+                cudaLaunchConfig_t cfg = {};
+                cfg.gridDim = dim3(ncta);
+                cfg.blockDim = dim3(one_cta ? CORE_TAIL_THREADS : CORE_THREADS);
+                cfg.dynamicSmemBytes = core_smem_bytes(per);
+                cfg.stream = s;
+                cudaLaunchAttribute attr[1];
+                attr[0].id = cudaLaunchAttributeClusterDimension;
+                attr[0].val.clusterDim.x = ncta;
+                attr[0].val.clusterDim.y = 1;
+                attr[0].val.clusterDim.z = 1;
+                cfg.attrs = attr;
+                cfg.numAttrs = one_cta ? 0 : 1;
+                TTC_CUDA(cudaLaunchKernelEx(&cfg, one_cta ? peel_core_kernel<false> : peel_core_kernel<true>, rem, R,
+                                            per, (const uint32_t *)coff.get(), (const uint16_t *)cadj.get(),
+                                            level.get(), pdeg.get(), one_cta ? 0u : PEEL_TAIL, tail_list,
+                                            ctl.get()));
+                note_launch();
+                out = read_scalar(ctl.get(), s);
+                if (out.error) fail(TTC_ERR_INTERNAL, "k-core peel of the core did not finish");
+                if (!out.handoff) break;
+                if (one_cta || out.rem_n > PEEL_TAIL || out.core_alive != out.rem_n)
+                    fail(TTC_ERR_INTERNAL, "k-core peel: inconsistent hand-off");
+                R = out.rem_n;
+                rem = tail_list;
+            }
         }
         st.peel_rounds = out.rounds;
     }
@@ -1780,8 +1882,13 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
     prof_end(g, s);
     prof_begin(g, s, "load:enumerate");
     // ---- a6: triangles, written straight into the light and heavy bins
-    RecCtx rc{g->poff.get(), g->pair_vtx.get(), g->labeling, g->light_max_pairs};
-    const TriCsr tc{onbr.get(), opair.get(), out_off.get(), osrc.get(), in_off.get(), in_e.get(), id_of.get()};
+    const RecCtx rc{g->labeling, g->light_max_pairs};
+    DevBuf<uint32_t> osig(ms, s);
+    osig_kernel<<<grid_for(ms), TPB, 0, s>>>(opair.get(), osrc.get(), onbr.get(), id_of.get(), g->poff.get(), ms,
+                                             osig.get());
+    TTC_LAUNCH_CHECK();
+    id_of.reset();
+    const TriCsr tc{onbr.get(), opair.get(), osig.get(), out_off.get(), osrc.get(), in_off.get(), in_e.get()};
     // work items: (target v, 32 of its in-edges)
     DevBuf<uint32_t> nit(n, s), it_pre(n + 1, s);
     tri_items_count_kernel<<<grid_for(n), TPB, 0, s>>>(out_off.get(), in_off.get(), (uint32_t)n, nit.get());
@@ -1792,16 +1899,22 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
     tri_items_fill_kernel<<<grid_for(nitems), TPB, 0, s>>>(it_pre.get(), (uint32_t)n, nitems, items.get());
     TTC_LAUNCH_CHECK();
     nit.reset(); it_pre.reset();
-    int tri_occ = 0;
-    TTC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&tri_occ, tri_enum_kernel<true>, TRI_THREADS, 0));
-    const unsigned tgrid =
-        (unsigned)std::min<uint64_t>(nitems / TRI_WARPS + 1, (uint64_t)sm_count() * std::max(1, tri_occ));
+    const size_t smem_c = TRI_WARPS * tri_warp_smem<false>(), smem_w = TRI_WARPS * tri_warp_smem<true>();
+    TTC_CUDA(cudaFuncSetAttribute(tri_enum_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
+    TTC_CUDA(cudaFuncSetAttribute(tri_enum_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_w));
+    int occ_c = 0, occ_w = 0;
+    TTC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_c, tri_enum_kernel<false>, TRI_THREADS, smem_c));
+    TTC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_w, tri_enum_kernel<true>, TRI_THREADS, smem_w));
+    const unsigned grid_c =
+        (unsigned)std::min<uint64_t>(nitems / TRI_WARPS + 1, (uint64_t)sm_count() * std::max(1, occ_c));
+    const unsigned grid_w =
+        (unsigned)std::min<uint64_t>(nitems / TRI_WARPS + 1, (uint64_t)sm_count() * std::max(1, occ_w));
     DevBuf<uint32_t> cl(ms + 1, s), ch(ms + 1, s);
     DevBuf<uint64_t> loff(ms + 1, s), hoff(ms + 1, s), cl64(ms + 1, s), ch64(ms + 1, s);
     TTC_CUDA(cudaMemsetAsync(cl.get(), 0, (ms + 1) * 4, s));
     TTC_CUDA(cudaMemsetAsync(ch.get(), 0, (ms + 1) * 4, s));
-    tri_enum_kernel<false><<<tgrid, TRI_THREADS, 0, s>>>(items.get(), nitems, tc, rc, cl.get(), ch.get(), nullptr,
-                                                        nullptr, 0, nullptr);
+    tri_enum_kernel<false><<<grid_c, TRI_THREADS, smem_c, s>>>(items.get(), nitems, tc, rc, cl.get(), ch.get(),
+                                                              nullptr, nullptr, 0, nullptr);
     TTC_LAUNCH_CHECK();
     widen_kernel<<<grid_for(ms), TPB, 0, s>>>(cl.get(), ch.get(), ms, cl64.get(), ch64.get());
     TTC_LAUNCH_CHECK();
@@ -1816,12 +1929,12 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
     st.tau = tau;
     g->tri.alloc(tau, s);
     if (tau) {
-        tri_enum_kernel<true><<<tgrid, TRI_THREADS, 0, s>>>(items.get(), nitems, tc, rc, nullptr, nullptr, loff.get(),
-                                                           hoff.get(), n_light, g->tri.get());
+        tri_enum_kernel<true><<<grid_w, TRI_THREADS, smem_w, s>>>(items.get(), nitems, tc, rc, nullptr, nullptr,
+                                                                 loff.get(), hoff.get(), n_light, g->tri.get());
         TTC_LAUNCH_CHECK();
     }
     cl.reset(); ch.reset(); loff.reset(); hoff.reset(); cl64.reset(); ch64.reset();
-    osrc.reset(); onbr.reset(); opair.reset(); out_off.reset(); in_off.reset(); in_e.reset(); id_of.reset();
+    osrc.reset(); onbr.reset(); opair.reset(); osig.reset(); out_off.reset(); in_off.reset(); in_e.reset();
     st.tau_light = n_light;
     st.tau_heavy = tau - n_light;
 

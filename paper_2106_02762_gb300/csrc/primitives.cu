@@ -3,6 +3,8 @@
 // for this library (no CUB/Thrust).
 #include <cooperative_groups.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace ttc {
@@ -102,38 +104,41 @@ constexpr int RS_WARPS = RS_THREADS / 32;
 constexpr int RS_ITEMS = 8;                         // per lane
 constexpr int RS_WARP_TILE = 32 * RS_ITEMS;         // consecutive elements per warp
 constexpr int RS_TILE = RS_WARPS * RS_WARP_TILE;    // elements per block
-constexpr int RADIX = 256;
+constexpr int RADIX_BITS = 10;                      // digit width (the last pass may use fewer)
+constexpr int RADIX = 1 << RADIX_BITS;
+constexpr int RS_DPT = RADIX / RS_THREADS;          // digits per thread in the per-digit steps
 
 __global__ void __launch_bounds__(RS_THREADS)
-    radix_hist_kernel(const uint64_t *keys, size_t n, int shift, uint32_t *counts, unsigned tiles) {
+    radix_hist_kernel(const uint64_t *keys, size_t n, int shift, uint32_t mask, uint32_t *counts, unsigned tiles) {
     __shared__ uint32_t hist[RADIX];
-    hist[threadIdx.x] = 0;
+    for (int d = threadIdx.x; d < RADIX; d += RS_THREADS) hist[d] = 0;
     __syncthreads();
     const size_t base = (size_t)blockIdx.x * RS_TILE;
 #pragma unroll
     for (int i = 0; i < RS_TILE / RS_THREADS; i++) {
         const size_t idx = base + (size_t)i * RS_THREADS + threadIdx.x;
-        if (idx < n) atomicAdd(&hist[(keys[idx] >> shift) & (RADIX - 1)], 1u);
+        if (idx < n) atomicAdd(&hist[(keys[idx] >> shift) & mask], 1u);
     }
     __syncthreads();
     // digit-major layout: a flat exclusive scan gives each (digit, tile) its
     // output offset in stable order
-    counts[(size_t)threadIdx.x * tiles + blockIdx.x] = hist[threadIdx.x];
+    for (int d = threadIdx.x; d < RADIX; d += RS_THREADS) counts[(size_t)d * tiles + blockIdx.x] = hist[d];
 }
 
-// Stable scatter of one 8-bit digit.  Ranks come from warp-level match
-// masks in element order; the tile is first reordered by digit in shared
-// memory, then written out so that each digit's run is contiguous in global
-// memory (coalesced stores).
+// Stable scatter of one digit.  Ranks come from warp-level match masks in
+// element order; the tile is first reordered by digit in shared memory, then
+// written out so that each digit's run is contiguous in global memory
+// (coalesced stores).
 template <typename V>
 __global__ void __launch_bounds__(RS_THREADS)
     radix_scatter_kernel(const uint64_t *keys_in, const V *vals_in, uint64_t *keys_out, V *vals_out,
-                         size_t n, int shift, const uint32_t *offsets, unsigned tiles) {
-    __shared__ uint32_t wcnt[RS_WARPS][RADIX];
+                         size_t n, int shift, uint32_t mask, const uint32_t *offsets, unsigned tiles) {
+    __shared__ uint16_t wcnt[RS_WARPS][RADIX];  // per warp and digit (at most RS_WARP_TILE)
     __shared__ uint32_t dstart[RADIX];   // block-local start of each digit
     __shared__ uint32_t gstart[RADIX];   // global start of each digit for this tile
-    __shared__ uint64_t s_key[RS_TILE];
-    __shared__ V s_val[RS_TILE];
+    extern __shared__ __align__(16) unsigned char rs_dyn[];
+    uint64_t *s_key = reinterpret_cast<uint64_t *>(rs_dyn);
+    V *s_val = reinterpret_cast<V *>(s_key + RS_TILE);
     for (int i = threadIdx.x; i < RS_WARPS * RADIX; i += RS_THREADS) (&wcnt[0][0])[i] = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -150,30 +155,42 @@ __global__ void __launch_bounds__(RS_THREADS)
         const bool ok = idx < n;
         k[i] = ok ? keys_in[idx] : 0;
         v[i] = ok ? vals_in[idx] : V(0);
-        dig[i] = ok ? (int)((k[i] >> shift) & (RADIX - 1)) : RADIX;  // RADIX = padding
+        dig[i] = ok ? (int)((k[i] >> shift) & mask) : RADIX;  // RADIX = padding
         const unsigned peers = __match_any_sync(0xffffffffu, dig[i]);
         const int leader = __ffs(peers) - 1;
         uint32_t b = 0;
         if (ok) b = wcnt[warp][dig[i]];
         __syncwarp();
-        if (ok && lane == leader) wcnt[warp][dig[i]] = b + __popc(peers);
+        if (ok && lane == leader) wcnt[warp][dig[i]] = (uint16_t)(b + __popc(peers));
         __syncwarp();
         local[i] = b + __popc(peers & lt_mask);
     }
     __syncthreads();
-    {  // per digit: exclusive prefix over warps, and the digit's block total
-        const int d = threadIdx.x;
-        uint32_t run = 0;
+    {  // per digit: exclusive prefix over warps, the digit's block total, and
+       // an exclusive scan of the totals (RS_DPT consecutive digits a thread)
+        uint32_t tot[RS_DPT], sum = 0;
 #pragma unroll
-        for (int w = 0; w < RS_WARPS; w++) {
-            const uint32_t c = wcnt[w][d];
-            wcnt[w][d] = run;
-            run += c;
+        for (int j = 0; j < RS_DPT; j++) {
+            const int d = threadIdx.x * RS_DPT + j;
+            uint32_t run = 0;
+#pragma unroll
+            for (int w = 0; w < RS_WARPS; w++) {
+                const uint32_t c = wcnt[w][d];
+                wcnt[w][d] = (uint16_t)run;
+                run += c;
+            }
+            tot[j] = run;
+            sum += run;
         }
         uint32_t total;
-        const uint32_t excl = block_exclusive_scan<uint32_t>(run, &total);
-        dstart[d] = excl;
-        gstart[d] = offsets[(size_t)d * tiles + blockIdx.x];
+        uint32_t excl = block_exclusive_scan<uint32_t>(sum, &total);
+#pragma unroll
+        for (int j = 0; j < RS_DPT; j++) {
+            const int d = threadIdx.x * RS_DPT + j;
+            dstart[d] = excl;
+            excl += tot[j];
+            gstart[d] = offsets[(size_t)d * tiles + blockIdx.x];
+        }
     }
     __syncthreads();
 #pragma unroll
@@ -187,7 +204,7 @@ __global__ void __launch_bounds__(RS_THREADS)
     const uint32_t count = (uint32_t)min((size_t)RS_TILE, n - tile_base);
     for (uint32_t i = threadIdx.x; i < count; i += RS_THREADS) {
         const uint64_t key = s_key[i];
-        const int d = (int)((key >> shift) & (RADIX - 1));
+        const int d = (int)((key >> shift) & mask);
         const size_t pos = (size_t)gstart[d] + (i - dstart[d]);
         keys_out[pos] = key;
         vals_out[pos] = s_val[i];
@@ -204,11 +221,22 @@ void radix_sort_impl(uint64_t *keys, V *vals, size_t n, int begin_bit, int end_b
     DevBuf<uint32_t> counts((size_t)RADIX * tiles, s), offs((size_t)RADIX * tiles + 1, s);
     uint64_t *kin = keys, *kout = kalt.get();
     V *vin = vals, *vout = valt.get();
-    for (int shift = begin_bit; shift < end_bit; shift += 8) {
-        radix_hist_kernel<<<tiles, RS_THREADS, 0, s>>>(kin, n, shift, counts.get(), tiles);
+    const size_t dyn = (size_t)RS_TILE * (sizeof(uint64_t) + sizeof(V));
+    static int configured_device = -1;
+    int dev = 0;
+    TTC_CUDA(cudaGetDevice(&dev));
+    if (configured_device != dev) {
+        TTC_CUDA(cudaFuncSetAttribute(radix_scatter_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+        configured_device = dev;
+    }
+    for (int shift = begin_bit; shift < end_bit; shift += RADIX_BITS) {
+        const int width = std::min(RADIX_BITS, end_bit - shift);
+        const uint32_t mask = (1u << width) - 1u;
+        radix_hist_kernel<<<tiles, RS_THREADS, 0, s>>>(kin, n, shift, mask, counts.get(), tiles);
         TTC_LAUNCH_CHECK();
         exclusive_scan_impl<uint32_t, uint32_t>(counts.get(), offs.get(), (size_t)RADIX * tiles, s);
-        radix_scatter_kernel<V><<<tiles, RS_THREADS, 0, s>>>(kin, vin, kout, vout, n, shift, offs.get(), tiles);
+        radix_scatter_kernel<V><<<tiles, RS_THREADS, dyn, s>>>(kin, vin, kout, vout, n, shift, mask, offs.get(),
+                                                               tiles);
         TTC_LAUNCH_CHECK();
         uint64_t *tk = kin; kin = kout; kout = tk;
         V *tv = vin; vin = vout; vout = tv;

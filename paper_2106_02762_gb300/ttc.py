@@ -33,7 +33,7 @@ EXPORTS = ["ttc_load", "ttc_load_ex", "ttc_free", "ttc_graph_info", "ttc_count",
            "ttc_serve_pause", "ttc_serve_set_reserve",
            "ttc_server_info", "ttc_last_error", "ttc_version", "ttc_debug_fail_alloc_after",
            "ttc_debug_launch_count", "ttc_set_profiling", "ttc_profile_read", "ttc_count_noalloc",
-           "ttc_release_cached", "ttc_memory_info"]
+           "ttc_release_cached", "ttc_memory_info", "ttc_count_grid"]
 
 
 class TTCError(RuntimeError):
@@ -108,6 +108,7 @@ def lib():
             "ttc_debug_fail_alloc_after": ([u64], None),
             "ttc_release_cached": ([p], ctypes.c_int),
             "ttc_memory_info": ([p, p, p], ctypes.c_int),
+            "ttc_count_grid": ([p, ctypes.c_int64, p, u32, p, u32, p, p], ctypes.c_int),
             "ttc_debug_launch_count": ([], u64),
             "ttc_set_profiling": ([p, ctypes.c_int], ctypes.c_int),
             "ttc_profile_read": ([p, p, u32], u32),
@@ -224,6 +225,17 @@ class Graph:
         buf = (KernelTime * 64)()
         n = lib().ttc_profile_read(self.handle, buf, 64)
         return [(buf[i].name.decode(), buf[i].ms) for i in range(n)]
+
+    def count_grid(self, d13: int, d12, d23):
+        """Counts at every (δ12, δ23) of the grid for one δ13:
+        ([len(d12)][len(d23)][8] uint64, [len(d12)][len(d23)] cyclic share)."""
+        a = np.ascontiguousarray(np.asarray(d12, dtype=np.int64).ravel())
+        b = np.ascontiguousarray(np.asarray(d23, dtype=np.int64).ravel())
+        out = np.zeros((a.size, b.size, 8), dtype=np.uint64)
+        cyc = np.zeros((a.size, b.size), dtype=np.float64)
+        check(lib().ttc_count_grid(self.handle, int(d13), a.ctypes.data, a.size, b.ctypes.data, b.size,
+                                   out.ctypes.data, cyc.ctypes.data))
+        return out, cyc
 
     def sample(self, delta, first: int, stride: int, cap: int):
         d, dp = _deltas(delta)

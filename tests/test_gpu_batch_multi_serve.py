@@ -174,3 +174,19 @@ def test_server_queue_limit_and_eviction():
     info = srv.info()
     assert info["evictions"] == 1 and info["graphs_resident"] == 1
     srv.close()
+
+
+def test_delta_grid_matches_oracle():
+    s, d, t = synth.tiny_plain()
+    g = ttc.Graph(s, d, t)
+    d13 = 7200
+    d12 = [0, 600, 1800, 3600, 7200]
+    d23 = [300, 1800, 5400, 9000]
+    counts, cyc = g.count_grid(d13, d12, d23)
+    want = oracle.count(s, d, t, [(d13, a, b) for a in d12 for b in d23]).reshape(len(d12), len(d23), 8)
+    assert (counts == want).all()
+    tot = want.sum(axis=2).astype(np.float64)
+    share = np.where(tot > 0, (want[:, :, 3] + want[:, :, 7]) / np.maximum(tot, 1), 0.0)
+    assert np.allclose(cyc, share, rtol=0, atol=1e-12)
+    assert (counts == np.stack([g.count_batch([(d13, a, b) for b in d23]) for a in d12])).all()
+    g.free()

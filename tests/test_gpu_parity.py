@@ -158,6 +158,26 @@ def test_pair_sort_size_classes():
         _check(*_pair_size_graph(sizes, len(sizes)), deltas)
 
 
+def test_out_lists_longer_than_shared_memory():
+    # under the id order vertex 1 has 700 out-neighbours, each closing a
+    # triangle with the in-edge 0 -> 1: the enumeration searches N+(1) in
+    # device memory instead of shared memory
+    rng = np.random.default_rng(12)
+    edges = [(0, 1, 5), (1, 0, 9)]
+    for j in range(2, 702):
+        for a, b in ((0, j), (1, j)):
+            for _ in range(int(rng.integers(1, 3))):
+                x, y = (a, b) if rng.integers(0, 2) else (b, a)
+                edges.append((x, y, int(rng.integers(0, 50))))
+    s, d, t = _edges(edges)
+    deltas = [(BIG, BIG, BIG), (20, 10, 10), (0, 0, 0)]
+    for o in (ttc.ORIENT_ID, ttc.ORIENT_DEGENERACY):
+        g = ttc.Graph(s, d, t, orientation=o)
+        assert g.info()["tau"] == 700
+        assert (g.count_batch(deltas) == oracle.count(s, d, t, deltas)).all(), o
+        g.free()
+
+
 def test_empty_graph():
     e = np.zeros(0, dtype=np.uint32)
     g = ttc.Graph(e, e, np.zeros(0, dtype=np.int64))
