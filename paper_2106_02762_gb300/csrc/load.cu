@@ -972,7 +972,10 @@ __global__ void __launch_bounds__(CORE_TAIL_THREADS, 1)
                     s_front[cur * per + atomicAdd(&s_fcnt[cur], 1u)] = i;
                 }
             }
-            __syncthreads();
+            // every CTA has collected before any CTA decrements its
+            // neighbours' degrees (else a vertex a slow CTA is still
+            // collecting could also be pushed)
+            csync();
             if (tid == 0) s_min = INT_MAX;
             need_level = false;
         }
@@ -1248,10 +1251,13 @@ __global__ void record_stats_kernel(const uint4 *rec, size_t tau, uint64_t n_lig
 // N+(u) after e.  Work items are (v, 32 in-edges of v): the warp stages N+(v)
 // in its shared memory (when it fits), flattens the 32 suffixes across its
 // lanes, and each lane looks its element w up in N+(v) by binary search.
-// COUNT pass: per oriented edge u -> v, its light and heavy records.  WRITE
-// pass: the records, each at its edge's offset in its bin plus its rank among
-// that edge's hits of that bin (hits of one edge come in ascending w, so the
-// layout is deterministic).
+// One pass: the suffix length bounds an edge's triangles, so every oriented
+// edge has that much room reserved in a scratch array (`resv`, an exclusive
+// prefix of the suffix lengths); its light records fill the room from the
+// front and its heavy records from the back, each at its rank among that
+// edge's hits of that bin (hits of one edge come in ascending w), and the
+// per-edge counts go to cnt_light / cnt_heavy.  tri_compact_kernel then
+// copies every edge's records to their bins: the layout is deterministic.
 constexpr int TRI_THREADS = 256;
 constexpr int TRI_WARPS = TRI_THREADS / 32;
 constexpr uint32_t TRI_NV_CAP = 448;  // staged N+(v) entries per warp (4 CTAs per SM)
@@ -1290,22 +1296,19 @@ struct TriCsr {
 
 // Shared memory of one warp: N+(v) (target ranks, σ words and, when writing,
 // pair ids) for dv <= TRI_NV_CAP.
-template <bool WRITE>
-constexpr size_t tri_warp_smem() { return (size_t)TRI_NV_CAP * 4 * (WRITE ? 3 : 2); }
+constexpr size_t tri_warp_smem() { return (size_t)TRI_NV_CAP * 4 * 3; }
 
-template <bool WRITE>
 __global__ void __launch_bounds__(TRI_THREADS)
     tri_enum_kernel(const uint2 *__restrict__ items, uint32_t nitems, TriCsr g, RecCtx rc, uint32_t *cnt_light,
-                    uint32_t *cnt_heavy, const uint64_t *light_off, const uint64_t *heavy_off, uint64_t heavy_base,
-                    uint4 *rec) {
+                    uint32_t *cnt_heavy, const uint64_t *resv, uint4 *sparse) {
     extern __shared__ uint32_t tri_smem[];
     __shared__ uint32_t s_excl[TRI_WARPS][33];
     __shared__ uint32_t s_e[TRI_WARPS][32], s_se[TRI_WARPS][32], s_pe[TRI_WARPS][32];
-    __shared__ uint64_t s_lo[TRI_WARPS][32], s_ho[TRI_WARPS][32];  // WRITE: each slot's bin offsets
+    __shared__ uint64_t s_lo[TRI_WARPS][32], s_ho[TRI_WARPS][32];  // each slot's room: front, back
     __shared__ uint32_t s_run[TRI_WARPS][64];  // per in-edge slot: light, heavy hits so far
     const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
-    uint32_t *s_nv = tri_smem + (size_t)w * (tri_warp_smem<WRITE>() / 4);
+    uint32_t *s_nv = tri_smem + (size_t)w * (tri_warp_smem() / 4);
     uint32_t *s_nvs = s_nv + TRI_NV_CAP, *s_nvp = s_nvs + TRI_NV_CAP;
     uint32_t staged_v = 0xffffffffu;
     for (uint64_t it = (uint64_t)blockIdx.x * TRI_WARPS + w; it < nitems; it += (uint64_t)gridDim.x * TRI_WARPS) {
@@ -1318,7 +1321,7 @@ __global__ void __launch_bounds__(TRI_THREADS)
             for (uint32_t i = lane; i < dv; i += 32) {
                 s_nv[i] = __ldg(g.onbr + vb + i);
                 s_nvs[i] = __ldg(g.osig + vb + i);
-                if (WRITE) s_nvp[i] = __ldg(g.opair + vb + i);
+                s_nvp[i] = __ldg(g.opair + vb + i);
             }
             staged_v = v;
         }
@@ -1333,12 +1336,10 @@ __global__ void __launch_bounds__(TRI_THREADS)
             const uint32_t e = __ldg(g.in_e + ib + i), u = __ldg(g.osrc + e);
             s_e[w][lane] = e;
             s_se[w][lane] = __ldg(g.osig + e);
-            if (WRITE) {
-                s_pe[w][lane] = __ldg(g.opair + e);
-                s_lo[w][lane] = light_off[e];
-                s_ho[w][lane] = heavy_base + heavy_off[e];
-            }
+            s_pe[w][lane] = __ldg(g.opair + e);
             len = __ldg(g.out_off + u + 1) - e - 1;  // the suffix of N+(u) after v
+            s_lo[w][lane] = resv[e];
+            s_ho[w][lane] = resv[e] + len - 1;
         }
         s_run[w][2 * lane] = 0;
         s_run[w][2 * lane + 1] = 0;
@@ -1352,48 +1353,54 @@ __global__ void __launch_bounds__(TRI_THREADS)
         const uint32_t total = __shfl_sync(0xffffffffu, x, 31);
         if (lane == 0) s_excl[w][32] = total;
         __syncwarp();
-        for (uint32_t base = 0; base < total; base += 32) {
-            const uint32_t j = base + lane;
-            bool hit = false, heavy = false;
-            uint32_t slot = 0;
-            uint4 r = make_uint4(0, 0, 0, 0);
-            if (j < total) {
-                uint32_t o = 0;
+        // two elements per lane per step (j and j + 32), their loads and
+        // searches interleaved; ranks are then taken in element order
+        const uint32_t top = dv ? 1u << (31 - __clz(dv)) : 0u;  // largest power of two <= dv
+        for (uint32_t base = 0; base < total; base += 64) {
+            uint32_t jj[2] = {base + lane, base + 32 + lane};
+            uint32_t o[2] = {0, 0}, ew[2] = {0, 0}, x3[2] = {0, 0}, lo[2] = {0, 0};
+            bool in[2];
 #pragma unroll
-                for (uint32_t step = 16; step; step >>= 1)
-                    if (s_excl[w][o + step] <= j) o += step;
-                slot = o;
-                const uint32_t ew = s_e[w][o] + 1 + (j - s_excl[w][o]);  // u -> w
-                const uint32_t x3 = __ldg(g.onbr + ew);
-                uint32_t lo = 0, len2 = dv;  // x3 in N+(v)
-                while (len2 > 0) {
-                    const uint32_t half = len2 >> 1;
-                    if (nv[lo + half] < x3) {
-                        lo += half + 1;
-                        len2 -= half + 1;
-                    } else {
-                        len2 = half;
-                    }
-                }
-                if (lo < dv && nv[lo] == x3) {
-                    hit = true;
-                    r = make_record(rc, s_se[w][o], __ldg(g.osig + ew), nvs[lo], WRITE ? s_pe[w][o] : 0u,
-                                    WRITE ? __ldg(g.opair + ew) : 0u, WRITE ? nvp[lo] : 0u, &heavy);
+            for (int h = 0; h < 2; h++) {
+                in[h] = jj[h] < total;
+                if (in[h]) {
+#pragma unroll
+                    for (uint32_t step = 16; step; step >>= 1)
+                        if (s_excl[w][o[h] + step] <= jj[h]) o[h] += step;
+                    ew[h] = s_e[w][o[h]] + 1 + (jj[h] - s_excl[w][o[h]]);  // u -> w
+                    x3[h] = __ldg(g.onbr + ew[h]);
                 }
             }
-            const unsigned act = __ballot_sync(0xffffffffu, hit);
-            if (!act) continue;
-            const uint32_t key = slot * 2 + (heavy ? 1u : 0u);
-            const unsigned peers = __match_any_sync(0xffffffffu, hit ? key : 0xffffffffu) & act;
-            uint32_t rank = 0;
-            if (hit) rank = s_run[w][key] + __popc(peers & lt_mask);
-            __syncwarp();
-            if (hit && (peers & lt_mask) == 0) s_run[w][key] += __popc(peers);
-            __syncwarp();
-            if (WRITE && hit) rec[(heavy ? s_ho[w][slot] : s_lo[w][slot]) + rank] = r;
+            // lower bound of x3 in N+(v), branch-free, both searches in step
+            for (uint32_t step = top; step; step >>= 1) {
+#pragma unroll
+                for (int h = 0; h < 2; h++)
+                    if (lo[h] + step <= dv && nv[lo[h] + step - 1] < x3[h]) lo[h] += step;
+            }
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                bool hit = false, heavy = false;
+                uint4 r = make_uint4(0, 0, 0, 0);
+                if (in[h] && lo[h] < dv && nv[lo[h]] == x3[h]) {
+                    hit = true;
+                    r = make_record(rc, s_se[w][o[h]], __ldg(g.osig + ew[h]), nvs[lo[h]], s_pe[w][o[h]],
+                                    __ldg(g.opair + ew[h]), nvp[lo[h]], &heavy);
+                }
+                const unsigned act = __ballot_sync(0xffffffffu, hit);
+                if (!act) continue;
+                const uint32_t slot = o[h];
+                const uint32_t key = slot * 2 + (heavy ? 1u : 0u);
+                const unsigned peers = __match_any_sync(0xffffffffu, hit ? key : 0xffffffffu) & act;
+                uint32_t rank = 0;
+                if (hit) rank = s_run[w][key] + __popc(peers & lt_mask);
+                __syncwarp();
+                if (hit && (peers & lt_mask) == 0) s_run[w][key] += __popc(peers);
+                __syncwarp();
+                if (hit) sparse[heavy ? s_ho[w][slot] - rank : s_lo[w][slot] + rank] = r;
+            }
         }
         __syncwarp();
-        if (!WRITE && i < din) {
+        if (i < din) {
             cnt_light[s_e[w][lane]] = s_run[w][2 * lane];
             cnt_heavy[s_e[w][lane]] = s_run[w][2 * lane + 1];
         }
@@ -1401,6 +1408,56 @@ __global__ void __launch_bounds__(TRI_THREADS)
     }
 }
 
+
+// Room reserved per oriented edge e = u -> v: the length of N+(u) after v.
+__global__ void tri_room_kernel(const uint32_t *osrc, const uint32_t *out_off, size_t ms, uint64_t *room) {
+    GRID_STRIDE(e, ms) room[e] = out_off[osrc[e] + 1] - (uint32_t)e - 1;
+}
+
+// Copies each oriented edge's records from its reserved room to the bins:
+// light record r of edge e to light_off[e] + r, heavy record r (stored from
+// the back of the room) to heavy_base + heavy_off[e] + r.  A warp takes 32
+// consecutive edges and flattens their records over its lanes, so reads and
+// writes run along contiguous ranges.
+__global__ void __launch_bounds__(TRI_THREADS)
+    tri_compact_kernel(const uint64_t *resv, const uint32_t *cnt_light, const uint32_t *cnt_heavy,
+                       const uint64_t *light_off, const uint64_t *heavy_off, uint64_t heavy_base, size_t ms,
+                       const uint4 *__restrict__ sparse, uint4 *__restrict__ tri) {
+    __shared__ uint32_t s_excl[TRI_WARPS][33];
+    const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint64_t nwarps = (uint64_t)gridDim.x * TRI_WARPS;
+    for (uint64_t e0 = ((uint64_t)blockIdx.x * TRI_WARPS + w) * 32; e0 < ms; e0 += nwarps * 32) {
+        const uint64_t e = e0 + lane;
+        for (int heavy = 0; heavy < 2; heavy++) {
+            const uint32_t c = e < ms ? (heavy ? cnt_heavy[e] : cnt_light[e]) : 0;
+            uint32_t x = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= (uint32_t)o) x += y;
+            }
+            const uint32_t total = __shfl_sync(0xffffffffu, x, 31);
+            if (!total) continue;  // warp-uniform
+            s_excl[w][lane] = x - c;
+            if (lane == 0) s_excl[w][32] = total;
+            __syncwarp();
+            for (uint32_t base = 0; base < total; base += 32) {
+                const uint32_t j = base + lane;
+                if (j < total) {
+                    uint32_t o = 0;
+#pragma unroll
+                    for (uint32_t step = 16; step; step >>= 1)
+                        if (s_excl[w][o + step] <= j) o += step;
+                    const uint64_t eo = e0 + o;
+                    const uint32_t r = j - s_excl[w][o];
+                    if (heavy) tri[heavy_base + heavy_off[eo] + r] = sparse[resv[eo + 1] - 1 - r];
+                    else tri[light_off[eo] + r] = sparse[resv[eo] + r];
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
 
 // Heavy-bin class of each heavy record from its enumerated size: 0 = one
 // warp, 1 = one CTA, 2 = huge (flat path).
@@ -1899,22 +1956,26 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
     tri_items_fill_kernel<<<grid_for(nitems), TPB, 0, s>>>(it_pre.get(), (uint32_t)n, nitems, items.get());
     TTC_LAUNCH_CHECK();
     nit.reset(); it_pre.reset();
-    const size_t smem_c = TRI_WARPS * tri_warp_smem<false>(), smem_w = TRI_WARPS * tri_warp_smem<true>();
-    TTC_CUDA(cudaFuncSetAttribute(tri_enum_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c));
-    TTC_CUDA(cudaFuncSetAttribute(tri_enum_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_w));
-    int occ_c = 0, occ_w = 0;
-    TTC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_c, tri_enum_kernel<false>, TRI_THREADS, smem_c));
-    TTC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_w, tri_enum_kernel<true>, TRI_THREADS, smem_w));
-    const unsigned grid_c =
-        (unsigned)std::min<uint64_t>(nitems / TRI_WARPS + 1, (uint64_t)sm_count() * std::max(1, occ_c));
-    const unsigned grid_w =
-        (unsigned)std::min<uint64_t>(nitems / TRI_WARPS + 1, (uint64_t)sm_count() * std::max(1, occ_w));
+    const size_t smem_t = TRI_WARPS * tri_warp_smem();
+    TTC_CUDA(cudaFuncSetAttribute(tri_enum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_t));
+    int occ_t = 0;
+    TTC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_t, tri_enum_kernel, TRI_THREADS, smem_t));
+    const unsigned grid_t =
+        (unsigned)std::min<uint64_t>(nitems / TRI_WARPS + 1, (uint64_t)sm_count() * std::max(1, occ_t));
+    // room per oriented edge, then one enumeration pass into it
+    DevBuf<uint64_t> room(ms, s), resv(ms + 1, s);
+    tri_room_kernel<<<grid_for(ms), TPB, 0, s>>>(osrc.get(), out_off.get(), ms, room.get());
+    TTC_LAUNCH_CHECK();
+    exclusive_scan_u64(room.get(), resv.get(), ms, s);
+    room.reset();
+    const uint64_t total_room = read_scalar(resv.get() + ms, s);
+    DevBuf<uint4> sparse(total_room ? total_room : 1, s);
     DevBuf<uint32_t> cl(ms + 1, s), ch(ms + 1, s);
     DevBuf<uint64_t> loff(ms + 1, s), hoff(ms + 1, s), cl64(ms + 1, s), ch64(ms + 1, s);
     TTC_CUDA(cudaMemsetAsync(cl.get(), 0, (ms + 1) * 4, s));
     TTC_CUDA(cudaMemsetAsync(ch.get(), 0, (ms + 1) * 4, s));
-    tri_enum_kernel<false><<<grid_c, TRI_THREADS, smem_c, s>>>(items.get(), nitems, tc, rc, cl.get(), ch.get(),
-                                                              nullptr, nullptr, 0, nullptr);
+    tri_enum_kernel<<<grid_t, TRI_THREADS, smem_t, s>>>(items.get(), nitems, tc, rc, cl.get(), ch.get(), resv.get(),
+                                                       sparse.get());
     TTC_LAUNCH_CHECK();
     widen_kernel<<<grid_for(ms), TPB, 0, s>>>(cl.get(), ch.get(), ms, cl64.get(), ch64.get());
     TTC_LAUNCH_CHECK();
@@ -1929,10 +1990,12 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
     st.tau = tau;
     g->tri.alloc(tau, s);
     if (tau) {
-        tri_enum_kernel<true><<<grid_w, TRI_THREADS, smem_w, s>>>(items.get(), nitems, tc, rc, nullptr, nullptr,
-                                                                 loff.get(), hoff.get(), n_light, g->tri.get());
+        const unsigned grid_c = (unsigned)std::min<uint64_t>(ceil_div(ms, 32 * TRI_WARPS), (uint64_t)sm_count() * 8);
+        tri_compact_kernel<<<grid_c, TRI_THREADS, 0, s>>>(resv.get(), cl.get(), ch.get(), loff.get(), hoff.get(),
+                                                          n_light, ms, sparse.get(), g->tri.get());
         TTC_LAUNCH_CHECK();
     }
+    sparse.reset(); resv.reset();
     cl.reset(); ch.reset(); loff.reset(); hoff.reset(); cl64.reset(); ch64.reset();
     osrc.reset(); onbr.reset(); opair.reset(); osig.reset(); out_off.reset(); in_off.reset(); in_e.reset();
     st.tau_light = n_light;

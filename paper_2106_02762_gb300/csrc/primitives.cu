@@ -104,7 +104,7 @@ constexpr int RS_WARPS = RS_THREADS / 32;
 constexpr int RS_ITEMS = 8;                         // per lane
 constexpr int RS_WARP_TILE = 32 * RS_ITEMS;         // consecutive elements per warp
 constexpr int RS_TILE = RS_WARPS * RS_WARP_TILE;    // elements per block
-constexpr int RADIX_BITS = 10;                      // digit width (the last pass may use fewer)
+constexpr int RADIX_BITS = 8;                       // digit width (the last pass may use fewer)
 constexpr int RADIX = 1 << RADIX_BITS;
 constexpr int RS_DPT = RADIX / RS_THREADS;          // digits per thread in the per-digit steps
 

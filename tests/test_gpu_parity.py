@@ -256,11 +256,20 @@ def test_peel_stages_match_level_synchronous_reference():
     q = [synth.LARGE_PLAIN_DELTA]
     assert (g.count_batch(q) == oracle.count(s, d, t, q)).all()
     g.free()
-    # small graphs (one cluster and the tail only, or the tail only)
-    for s, d, t in (synth.large_plain(scale=0.004), synth.random_tiny(5, 40, 300, 3)):
-        g = ttc.Graph(s, d, t)
-        assert (g.info()["kappa"], g.info()["peel_rounds"]) == _level_peel(s, d)
-        g.free()
+    # smaller graphs: the cluster from the first level on (its widest rounds,
+    # loaded several times: the rule admits one answer whatever the timing),
+    # and the one-CTA stage alone
+    for scale, loads in ((0.05, 4), (0.004, 1)):
+        s, d, t = synth.large_plain(scale=scale)
+        want = _level_peel(s, d)
+        for _ in range(loads):
+            g = ttc.Graph(s, d, t)
+            assert (g.info()["kappa"], g.info()["peel_rounds"]) == want, scale
+            g.free()
+    s, d, t = synth.random_tiny(5, 40, 300, 3)
+    g = ttc.Graph(s, d, t)
+    assert (g.info()["kappa"], g.info()["peel_rounds"]) == _level_peel(s, d)
+    g.free()
 
 
 def test_graph_stats_match_oracle():
