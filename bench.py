@@ -145,13 +145,21 @@ def allreduce_max(x, ws, device=None):
 
 
 # ------------------------------------------------------------------ CPU oracle timing
-SAMPLE_SCALE = 0.15
+SAMPLE_SCALE = 0.1
+
+
+def step_queries(delta):
+    """The queries one timed step answers: the configured one and the same
+    with every window unbounded."""
+    from paper_2106_02762_gb300 import synth
+    return [tuple(delta), synth.LARGE_PLAIN_DELTA_UNBOUNDED]
 
 
 def oracle_sample(delta, reps=3):
     """Times the oracle (O1, every host core) on a bounded sample of the
-    workload: the same recipe at 15% scale (150K vertices, 1.5M pairs, about
-    9M edges), whole graph, `reps` runs (about 10 s of host work).  Returns
+    workload: the same recipe at 10% scale (100K vertices, 1M pairs, about
+    6M edges), whole graph, `reps` runs of the step's two queries (about
+    10 to 30 s of host work).  Returns
     (edges/s, description, cores, seconds per run)."""
     import oracle
     from paper_2106_02762_gb300 import synth
@@ -161,11 +169,12 @@ def oracle_sample(delta, reps=3):
     times = []
     for _ in range(reps):
         t0 = time.perf_counter()
-        oracle.count(src, dst, t, [delta])
+        oracle.count(src, dst, t, step_queries(delta))
         times.append(time.perf_counter() - t0)
     sec = statistics.median(times)
-    desc = ("O1 on the whole power-law recipe at %g scale (%d vertices, %d pairs, %d edges), median of %d runs; "
-            "the per-edge cost grows with scale (hub degrees), so the full-size oracle is slower per edge"
+    desc = ("O1 answering the step's two queries on the whole power-law recipe at %g scale (%d vertices, "
+            "%d pairs, %d edges), median of %d runs; the per-edge cost grows with scale (hub degrees), so the "
+            "full-size oracle is slower per edge"
             % (SAMPLE_SCALE, int(1e6 * SAMPLE_SCALE), int(1e7 * SAMPLE_SCALE), m, reps))
     return m / sec, desc, os.cpu_count() or 1, sec
 
@@ -185,18 +194,19 @@ def run_reference(args):
     times = []
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        oracle.count(src, dst, t, [delta])
+        oracle.count(src, dst, t, step_queries(delta))
         if i >= args.warmup:
             times.append(time.perf_counter() - t0)
     step_s = statistics.median(times)
     value = m / step_s
-    desc = ("O1 (plain adjacency + Lemma 1, every host core) on the whole power-law recipe at %g scale "
-            "(%d edges) per step" % (SAMPLE_SCALE, m))
+    desc = ("O1 (plain adjacency + Lemma 1, every host core) answering the step's two queries on the whole "
+            "power-law recipe at %g scale (%d edges) per step" % (SAMPLE_SCALE, m))
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": name, "delta": list(delta), "sample_m": m},
+        "config": {"workload": name, "delta": list(delta), "step_deltas": [list(q) for q in step_queries(delta)],
+                   "sample_m": m},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count() or 1, "kind": "oracle",
                          "sample": desc},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -397,16 +407,18 @@ def run_serve(args):
 # ------------------------------------------------------------------ δ-grid
 def run_grid(args):
     """δ-grid analytics on the power-law workload: a 16 x 16 (δ12, δ23) grid,
-    log-spaced from 60 s to δ13 = 1 day, in one batched call; reports the
-    time per grid and the range of the cyclic (T4 + T8) share."""
+    log-spaced from 1 hour to δ13 = 2^31 s (the whole span: each pair's
+    edges form one burst at a random time, so shorter windows close few
+    temporal triangles on this recipe), in one batched call; reports the time
+    per grid and the cyclic (T4 + T8) share."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
     from paper_2106_02762_gb300 import ttc
     src, dst, t, delta, name = workload(args.scale)
     g = ttc.Graph(src, dst, t)
-    d13 = 86400
-    axis = np.unique(np.round(np.logspace(np.log10(60), np.log10(d13), 16)).astype(np.int64))
+    d13 = 1 << 31
+    axis = np.unique(np.round(np.logspace(np.log10(3600), np.log10(d13), 16)).astype(np.int64))
     for _ in range(max(1, args.warmup)):
         counts, cyc = g.count_grid(d13, axis, axis)
     times = []
@@ -425,6 +437,28 @@ def run_grid(args):
                       "cyclic_share_min": float(cyc.min()), "cyclic_share_max": float(cyc.max()),
                       "cyclic_share_at_d12_eq_d23": [float(cyc[i, i]) for i in range(axis.size)],
                       "config": {"workload": name}}), flush=True)
+
+
+# ------------------------------------------------------------------ DRAM traffic
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "light_kernel_dram_power_law_1m.txt")
+
+
+def light_traffic(ttc):
+    """DRAM bytes (read + write) of one light-kernel launch on the full
+    power-law workload, from the one-pass ncu capture summarised in
+    profiles/; None when that capture was taken on other count-kernel source
+    than the library built here (the version string carries its hash)."""
+    try:
+        fields = dict(line.split(":", 1) for line in open(TRAFFIC_FILE) if ":" in line)
+    except OSError:
+        return None
+    built = ttc.lib().ttc_version().decode().rsplit("count:", 1)[-1].strip()
+    if fields.get("count_source", "").strip() != built:
+        return None
+    try:
+        return int(fields["dram_bytes_per_launch"].strip())
+    except (KeyError, ValueError):
+        return None
 
 
 # ------------------------------------------------------------------ our arm
@@ -452,14 +486,20 @@ def run_ours(args):
     h_t = torch.from_numpy(t).pin_memory()
     torch.cuda.synchronize()
 
+    # a step answers the configured query and the same query with every
+    # window unbounded, in one batched pass: with the second one present no
+    # window lets the kernels skip work, so the step time does not rest on
+    # the windows pruning it (the paper's cost does not depend on the windows)
+    step_deltas = step_queries(delta)
+
     def step_device():
         g = ttc.Graph(d_src, d_dst, d_t, stream=sptr)
-        out = g.count(delta)
+        out = g.count_batch(step_deltas)
         return g, out
 
     def step_host():
         g = ttc.Graph(h_src.numpy().view(np.uint32), h_dst.numpy().view(np.uint32), h_t.numpy(), stream=sptr)
-        out = g.count(delta)
+        out = g.count_batch(step_deltas)
         return g, out
 
     # warm-up
@@ -556,7 +596,8 @@ def run_ours(args):
         alg = wb_light if top.startswith("light") else wb_heavy
         ach = alg / kern_avg[top] / 1e9
         roof = {"kernel": top, "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
-                "frac": ach / hbm_peak, "traffic": None, "peak_source": peak_src,
+                "frac": ach / hbm_peak, "traffic": light_traffic(ttc) if top.startswith("light") else None,
+                "peak_source": peak_src,
                 "algorithmic_bytes": alg, "kernel_ms": kern_avg[top] * 1e3}
 
     # e2e: host (pinned) buffers through the C ABI, copies inside the timed region
@@ -570,7 +611,8 @@ def run_ours(args):
         assert (out == ref).all()
         g.free()
     e_s = allreduce_max(statistics.median(e_times), ws, dev)
-    e2e = {"value": ws * m / e_s, "unit": UNIT, "h2d_bytes_per_step": int(m_in * 16), "d2h_bytes_per_step": 64}
+    e2e = {"value": ws * m / e_s, "unit": UNIT, "h2d_bytes_per_step": int(m_in * 16),
+           "d2h_bytes_per_step": 64 * len(step_deltas)}
 
     batched = batched_sweep(ttc, torch) if rank == 0 else None
 
@@ -586,7 +628,9 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": name, "m": m, "tau": info["tau"], "delta": list(delta),
-                       "step": "ttc_load (device-resident edges) + ttc_count",
+                       "step": "ttc_load (device-resident edges) + one ttc_count_batch of the configured delta "
+                               "and the unbounded delta (2^31, 2^31, 2^31), so no window pruning applies",
+                       "step_deltas": [list(q) for q in step_deltas],
                        "l2": "inputs larger than L2 (no flush)", "parallelism": "replicas" if ws > 1 else "1 gpu"},
             "query": {"edges_per_s": m / q_s, "static_triangles_per_s": info["tau"] / q_s, "ms": q_s * 1e3,
                       "kernels_ms": {k: v * 1e3 for k, v in kern_avg.items()}},

@@ -218,6 +218,7 @@ __device__ __forceinline__ uint32_t graph_of(const uint64_t *__restrict__ pre, u
 
 // ---------------------------------------------------------------- light bin
 constexpr int LIGHT_THREADS = 256;
+constexpr uint32_t LIGHT_QT = 2;  // queries per group kept in per-thread accumulators
 constexpr int LIGHT_WARPS = LIGHT_THREADS / 32;
 
 // Adds the counts of one pair (x, y) of enumerated edges (x earlier) for all
@@ -280,7 +281,13 @@ __global__ void __launch_bounds__(LIGHT_THREADS)
                  const uint64_t *idx, uint64_t nidx, uint32_t qpw = 1) {
     __shared__ WarpTris wt;
     __shared__ unsigned long long s_acc[MODE == 0 ? 8 : 1][MODE == 0 ? 256 : 1];
-    extern __shared__ unsigned long long s_bacc[];  // MODE 1: [nq * 8]
+    // MODE 1: [nq * 8] block accumulators, then, when every item's query
+    // group has at most LIGHT_QT queries, per-thread accumulators
+    // [LIGHT_QT * 8][LIGHT_THREADS] (no shared atomics per pair)
+    extern __shared__ unsigned long long s_bacc[];
+    const bool tslots = MODE == 1 && qpw <= LIGHT_QT;
+    unsigned long long *s_t = s_bacc + 8 * (size_t)nq;
+    uint32_t slot_q0 = 0;  // first query of the group the thread's slots hold
     const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if constexpr (MODE == 0) {
 #pragma unroll
@@ -288,10 +295,31 @@ __global__ void __launch_bounds__(LIGHT_THREADS)
     }
     if constexpr (MODE == 1) {
         for (uint32_t i = threadIdx.x; i < nq * 8; i += blockDim.x) s_bacc[i] = 0;
+        if (tslots)
+            for (uint32_t i = 0; i < LIGHT_QT * 8; i++) s_t[i * LIGHT_THREADS + threadIdx.x] = 0;
         __syncthreads();
     }
+
     unsigned ovf = 0;
     uint32_t cur_g = 0xffffffffu;
+    // adds the thread's slots into the block accumulators of queries
+    // slot_q0 .. slot_q0 + qpw - 1 (warp sums first) and clears them
+    auto flush_slots = [&]() {
+        for (uint32_t ql = 0; ql < qpw && slot_q0 + ql < nq; ql++) {
+#pragma unroll
+            for (int t = 0; t < 8; t++) {
+                unsigned long long &cell = s_t[(ql * 8 + t) * LIGHT_THREADS + threadIdx.x];
+                unsigned long long v = cell;
+                cell = 0;
+#pragma unroll
+                for (int o = 16; o; o >>= 1) {
+                    const unsigned long long y = __shfl_xor_sync(0xffffffffu, v, o);
+                    add_checked(v, y, ovf);
+                }
+                if (lane == 0 && v) shared_add(&s_bacc[(slot_q0 + ql) * 8 + t], v, ovf);
+            }
+        }
+    };
     const uint64_t nchunks = MODE == 2 ? (nidx + 31) / 32 : __ldg(chunk_pre + G);
     const uint64_t gw = (uint64_t)blockIdx.x * LIGHT_WARPS + w, nw = (uint64_t)gridDim.x * LIGHT_WARPS;
     // MODE 1: work items are (chunk, group of qpw queries), so small graphs
@@ -301,6 +329,10 @@ __global__ void __launch_bounds__(LIGHT_THREADS)
         const uint64_t c = item / ngroups;
         const uint32_t q_beg = MODE == 1 ? (uint32_t)(item % ngroups) * qpw : 0u;
         const uint32_t q_end = MODE == 1 ? min(nq, q_beg + qpw) : 1u;
+        if (MODE == 1 && tslots && q_beg != slot_q0) {  // warp-uniform
+            flush_slots();
+            slot_q0 = q_beg;
+        }
         int64_t gmax = 0;
         if constexpr (MODE == 1)
             for (uint32_t q = q_beg; q < q_end; q++) gmax = max(gmax, dq[3 * q]);
@@ -363,7 +395,10 @@ __global__ void __launch_bounds__(LIGHT_THREADS)
                 const Query Q = MODE == 1 ? load_query(dq, q) : Q0;
                 auto accq = [&](int type, uint32_t n) {
                     if constexpr (MODE == 0) add_checked(s_acc[type][threadIdx.x], n, ovf);
-                    else if constexpr (MODE == 1) shared_add(&s_bacc[q * 8 + type], n, ovf);
+                    else if constexpr (MODE == 1) {
+                        if (tslots) add_checked(s_t[((q - q_beg) * 8 + type) * LIGHT_THREADS + threadIdx.x], n, ovf);
+                        else shared_add(&s_bacc[q * 8 + type], n, ovf);
+                    }
                     else atomicAdd(out + 8 * (lc * 32 + o) + type, (unsigned long long)n);
                 };
                 if (a_first) light_pair(C, f, Q, true, ra, rb, pa, pb, dA, dB, accq);
@@ -375,7 +410,10 @@ __global__ void __launch_bounds__(LIGHT_THREADS)
     if constexpr (MODE == 0) {
         if (cur_g != 0xffffffffu) warp_flush(s_acc, out + 8 * cur_g, flag, ovf);
     }
-    if constexpr (MODE == 1) block_flush(s_bacc, nq * 8, out, flag, ovf);
+    if constexpr (MODE == 1) {
+        if (tslots) flush_slots();
+        block_flush(s_bacc, nq * 8, out, flag, ovf);
+    }
 }
 
 // ---------------------------------------------------------------- heavy: per-edge math
@@ -1059,7 +1097,16 @@ void count_graph(ttc_graph *g, const int64_t *dq, uint32_t k, unsigned long long
                 const uint32_t groups = (uint32_t)std::min<uint64_t>(nq, (want_items + chunks - 1) / chunks);
                 const uint32_t qpw = (nq + groups - 1) / groups;
                 prof_begin(g, s, "light_batch");
-                light_kernel<1><<<light_grid(chunks * ((nq + qpw - 1) / qpw)), LIGHT_THREADS, nq * 64, s>>>(
+                const size_t smem = nq * 64 + (qpw <= LIGHT_QT ? (size_t)LIGHT_QT * 8 * LIGHT_THREADS * 8 : 0);
+                static int light1_device = -1;
+                int dev = 0;
+                TTC_CUDA(cudaGetDevice(&dev));
+                if (light1_device != dev) {
+                    TTC_CUDA(cudaFuncSetAttribute(light_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)(MAX_BATCH_SMEM_Q * 64 + LIGHT_QT * 8 * LIGHT_THREADS * 8)));
+                    light1_device = dev;
+                }
+                light_kernel<1><<<light_grid(chunks * ((nq + qpw - 1) / qpw)), LIGHT_THREADS, smem, s>>>(
                     gv, light_pre, 1, dq + 3 * (size_t)q0, nq, acc + 8 * (size_t)q0, flag, nullptr, 0, qpw);
                 TTC_LAUNCH_CHECK();
                 prof_end(g, s);

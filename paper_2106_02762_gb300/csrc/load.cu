@@ -213,7 +213,12 @@ __global__ void seg_sort_tiny_kernel(int64_t *key, const uint32_t *poff, uint32_
 
 // Pairs of SEG_TINY_CAP+1..32 edges (listed in `small`): one warp, a bitonic
 // network in registers.
-__global__ void seg_sort_small_kernel(int64_t *key, const uint32_t *poff, const uint32_t *small, uint32_t nsmall) {
+// The list of a class is the slice [base[c], base[c] + count[c]) of `lists`
+// (device memory, so no host round trip is needed).
+__global__ void seg_sort_small_kernel(int64_t *key, const uint32_t *poff, const uint32_t *lists,
+                                      const unsigned int *base, const unsigned int *count) {
+    const uint32_t *small = lists + base[0];
+    const uint32_t nsmall = count[0];
     const uint32_t lane = threadIdx.x & 31;
     for (uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nsmall;
          w += ((uint64_t)gridDim.x * blockDim.x) >> 5) {
@@ -261,6 +266,17 @@ __global__ void seg_classify_kernel(const uint32_t *poff, uint32_t ms, unsigned 
         if (c >= 0 && (int)lane == leader) base = atomicAdd(&cursor[c], (unsigned int)__popc(peers));
         base = __shfl_sync(0xffffffffu, base, leader);
         if (FILL && c >= 0) list[base + __popc(peers & ((1u << lane) - 1))] = (uint32_t)p;
+    }
+}
+
+// Class offsets in the list array (exclusive prefix of the counts) and the
+// fill cursors; one thread.
+__global__ void seg_bases_kernel(const unsigned int *count, unsigned int *base, unsigned int *cursor) {
+    unsigned int run = 0;
+    for (int c = 0; c < SEG_CLASSES; c++) {
+        base[c] = run;
+        cursor[c] = run;
+        run += count[c];
     }
 }
 
@@ -340,7 +356,10 @@ __device__ __forceinline__ void sort_pair_regs(int64_t *key, uint32_t b, uint32_
 // the whole CTA otherwise), E keys per thread: pairs of up to E * T edges.
 template <int E, int T>
 __global__ void __launch_bounds__(T >= 128 ? T : 128)
-    seg_sort_group_kernel(int64_t *key, const uint32_t *poff, const uint32_t *list, uint32_t nlist) {
+    seg_sort_group_kernel(int64_t *key, const uint32_t *poff, const uint32_t *lists, const unsigned int *base,
+                          const unsigned int *count, int cls) {
+    const uint32_t *list = lists + base[cls];
+    const uint32_t nlist = count[cls];
     extern __shared__ int64_t s_x[];
     constexpr uint32_t CTA = T >= 128 ? T : 128, G = CTA / T;
     const uint32_t grp = threadIdx.x / T, t = threadIdx.x % T;
@@ -378,7 +397,7 @@ constexpr uint64_t MASK40 = (uint64_t(1) << 40) - 1;
 constexpr int PEEL_THREADS = 1024;
 constexpr int PEEL_RUN = 4;  // relaxed edges per thread per step
 constexpr uint32_t PEEL_CACHE = 8192;  // frontier entries cached in shared memory
-constexpr uint32_t PEEL_GRID_STOP = 65536;  // the grid-wide stage hands off at this many vertices
+constexpr uint32_t CORE_PER_MAX = 8192;  // core vertices one CTA of the core cluster holds
 
 // Frontier pushes of one CTA are staged in its shared memory and reach the
 // global frontier with one device-memory atomic per CTA and phase (flush), so
@@ -740,11 +759,10 @@ __global__ void __launch_bounds__(PEEL_THREADS)
 
 
 // ---------------------------------------------------------------- peel core
-// The last PEEL_GRID_STOP (or fewer) vertices are peeled by one thread-block
-// cluster that keeps every remaining vertex's state in distributed shared
-// memory.  Their adjacency among themselves is first rebuilt with local ids
-// (16 bits, since at most 65 536 remain).
-static_assert(PEEL_GRID_STOP <= 65536, "core vertices need 16-bit local ids");
+// The last (cluster size x CORE_PER_MAX) or fewer vertices are peeled by one
+// thread-block cluster that keeps every remaining vertex's state in
+// distributed shared memory.  Their adjacency among themselves is first
+// rebuilt with local ids.
 
 // Local ids of the remaining vertices and their (current) degrees.
 __global__ void tail_ids_kernel(const uint32_t *rem, uint32_t R, const int *deg, uint32_t *lid, uint32_t *cdeg) {
@@ -771,7 +789,7 @@ __global__ void tail_chunks_kernel(const uint32_t *rem, uint32_t R, const uint32
 __global__ void __launch_bounds__(256)
     tail_adj_kernel(const uint32_t *rem, uint32_t R, const uint32_t *chunk_pre, const uint32_t *adj_off,
                     const uint32_t *adj, const uint32_t *level, const uint32_t *lid, const uint32_t *coff,
-                    uint32_t *cursor, uint16_t *cadj) {
+                    uint32_t *cursor, uint32_t *cadj) {
     __shared__ uint32_t s_w[8];
     __shared__ uint32_t s_base;
     const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -807,7 +825,7 @@ __global__ void __launch_bounds__(256)
                 s_base = run ? atomicAdd(cursor + i, run) : 0;
             }
             __syncthreads();
-            if (keep) cadj[coff[i] + s_base + s_w[w] + __popc(bal & lt_mask)] = (uint16_t)lid[x];
+            if (keep) cadj[coff[i] + s_base + s_w[w] + __popc(bal & lt_mask)] = lid[x];
             __syncthreads();
         }
     }
@@ -864,7 +882,7 @@ __device__ __forceinline__ uint32_t core_block_excl_scan(uint32_t x, uint32_t *s
 // barriers); CLUSTER = true: `per` (a power of two) vertices per CTA.
 template <bool CLUSTER>
 __global__ void __launch_bounds__(CORE_TAIL_THREADS, 1)
-    peel_core_kernel(const uint32_t *rem, uint32_t R, uint32_t per, const uint32_t *coff, const uint16_t *cadj,
+    peel_core_kernel(const uint32_t *rem, uint32_t R, uint32_t per, const uint32_t *coff, const uint32_t *cadj,
                      uint32_t *level, int *deg, uint32_t stop_n, uint32_t *alive_out, PeelCtl *ctl) {
     cg::cluster_group cl = cg::this_cluster();
     const uint32_t crank = CLUSTER ? cl.block_rank() : 0u, csize = CLUSTER ? cl.num_blocks() : 1u;
@@ -1482,6 +1500,32 @@ __global__ void heavy_partition_kernel(const uint4 *rec, const uint64_t *he, con
     }
 }
 
+// A second stream forked from `main` (it waits for everything enqueued on
+// main so far); fork_done() marks the end of its work, join() makes main wait
+// for it.  Buffers allocated on it are released before it is destroyed
+// (declare them after the SideStream).
+struct SideStream {
+    cudaStream_t s = nullptr, main;
+    cudaEvent_t fork = nullptr, done = nullptr;
+    explicit SideStream(cudaStream_t m) : main(m) {
+        TTC_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        TTC_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+        TTC_CUDA(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
+        TTC_CUDA(cudaEventRecord(fork, main));
+        TTC_CUDA(cudaStreamWaitEvent(s, fork, 0));
+    }
+    SideStream(const SideStream &) = delete;
+    SideStream &operator=(const SideStream &) = delete;
+    void fork_done() { TTC_CUDA(cudaEventRecord(done, s)); }
+    void join() { TTC_CUDA(cudaStreamWaitEvent(main, done, 0)); }
+    ~SideStream() {
+        cudaStreamSynchronize(s);
+        cudaEventDestroy(fork);
+        cudaEventDestroy(done);
+        cudaStreamDestroy(s);
+    }
+};
+
 template <typename T>
 T read_scalar(const T *dev, cudaStream_t s) {
     T h;
@@ -1544,12 +1588,12 @@ int core_cluster_size() {
     if (cudaFuncSetAttribute(peel_core_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)core_smem_bytes(PEEL_TAIL)) != cudaSuccess ||
         cudaFuncSetAttribute(peel_core_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)core_smem_bytes(PEEL_GRID_STOP / 8)) != cudaSuccess) {
+                             (int)core_smem_bytes(CORE_PER_MAX)) != cudaSuccess) {
         cudaGetLastError();
         return best;
     }
     for (int c = (int)CORE_MAX_CLUSTER; c >= 8; c /= 2) {
-        const size_t smem = core_smem_bytes(PEEL_GRID_STOP / c);
+        const size_t smem = core_smem_bytes(CORE_PER_MAX);
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(c);
         cfg.blockDim = dim3(CORE_THREADS);
@@ -1571,38 +1615,37 @@ int core_cluster_size() {
     return best;
 }
 
-// Launches the in-place sort of the pairs of size class c (list of n pairs).
+// Launches the in-place sort of size class c with a grid that fills the GPU;
+// the class's pair count is read on the device, so an empty class costs one
+// short launch.
 template <int E, int T>
-void launch_seg_group(int64_t *key, const uint32_t *poff, const uint32_t *list, uint32_t n, cudaStream_t s) {
-    constexpr int CTA = T >= 128 ? T : 128, G = CTA / T;
+void launch_seg_group(int64_t *key, const uint32_t *poff, const uint32_t *lists, const unsigned int *base,
+                      const unsigned int *count, int c, cudaStream_t s) {
+    constexpr int CTA = T >= 128 ? T : 128;
     const size_t smem = T >= 64 ? (size_t)E * T * 8 : 0;
     if (smem > 48 * 1024)
         TTC_CUDA(cudaFuncSetAttribute(seg_sort_group_kernel<E, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
     int occ = 0;
     TTC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, seg_sort_group_kernel<E, T>, CTA, smem));
-    const unsigned grid = std::min<uint32_t>(ceil_div(n, G), (uint32_t)sm_count() * std::max(1, occ));
-    seg_sort_group_kernel<E, T><<<grid, CTA, smem, s>>>(key, poff, list, n);
+    const unsigned grid = (uint32_t)sm_count() * std::max(1, occ);
+    seg_sort_group_kernel<E, T><<<grid, CTA, smem, s>>>(key, poff, lists, base, count, c);
     TTC_LAUNCH_CHECK();
 }
 
-void seg_sort_class(int c, int64_t *key, const uint32_t *poff, const uint32_t *list, uint32_t n, cudaStream_t s) {
-    switch (c) {
-        case 0:
-            seg_sort_small_kernel<<<grid_for((size_t)n * 32), TPB, 0, s>>>(key, poff, list, n);
-            TTC_LAUNCH_CHECK();
-            break;
-        case 1: launch_seg_group<2, 32>(key, poff, list, n, s); break;      // 33..64
-        case 2: launch_seg_group<4, 32>(key, poff, list, n, s); break;      // ..128
-        case 3: launch_seg_group<8, 32>(key, poff, list, n, s); break;      // ..256
-        case 4: launch_seg_group<16, 32>(key, poff, list, n, s); break;     // ..512
-        case 5: launch_seg_group<8, 128>(key, poff, list, n, s); break;     // ..1024
-        case 6: launch_seg_group<4, 512>(key, poff, list, n, s); break;     // ..2048
-        case 7: launch_seg_group<8, 512>(key, poff, list, n, s); break;     // ..4096
-        case 8: launch_seg_group<16, 512>(key, poff, list, n, s); break;    // ..8192
-        case 9: launch_seg_group<32, 512>(key, poff, list, n, s); break;    // ..16384
-        default: fail(TTC_ERR_INTERNAL, "per-pair sort: no size class %d", c);
-    }
+void seg_sort_classes(int64_t *key, const uint32_t *poff, const uint32_t *lists, const unsigned int *base,
+                      const unsigned int *count, cudaStream_t s) {
+    seg_sort_small_kernel<<<(unsigned)sm_count() * 8, TPB, 0, s>>>(key, poff, lists, base, count);  // ..32
+    TTC_LAUNCH_CHECK();
+    launch_seg_group<2, 32>(key, poff, lists, base, count, 1, s);     // 33..64
+    launch_seg_group<4, 32>(key, poff, lists, base, count, 2, s);     // ..128
+    launch_seg_group<8, 32>(key, poff, lists, base, count, 3, s);     // ..256
+    launch_seg_group<16, 32>(key, poff, lists, base, count, 4, s);    // ..512
+    launch_seg_group<8, 128>(key, poff, lists, base, count, 5, s);    // ..1024
+    launch_seg_group<4, 512>(key, poff, lists, base, count, 6, s);    // ..2048
+    launch_seg_group<8, 512>(key, poff, lists, base, count, 7, s);    // ..4096
+    launch_seg_group<16, 512>(key, poff, lists, base, count, 8, s);   // ..8192
+    launch_seg_group<32, 512>(key, poff, lists, base, count, 9, s);   // ..16384
 }
 
 void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, const int64_t *t_in, uint64_t m_in,
@@ -1741,46 +1784,31 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
         TTC_CUDA(cudaMemcpyAsync(g->poff.get() + ms, &mm32, 4, cudaMemcpyHostToDevice, s));
         TTC_CUDA(cudaStreamSynchronize(s));
     }
-    prof_end(g, s);
-    prof_begin(g, s, "load:pair_lists");
+    pid.reset(); head.reset();
+    // ---- a5: each pair's list in key order and its dir-0 prefix.  Nothing
+    // before the count reads them, so they run on a side stream that
+    // overlaps the peel, orientation and enumeration, and join at the end.
+    SideStream side(s);
+    DevBuf<unsigned int> cls(3 * SEG_CLASSES, side.s);  // counts, bases, cursors
+    DevBuf<uint32_t> lists(ms ? ms : 1, side.s);
+    DevBuf<uint8_t> dflag(m, side.s);
     if (seg_sort_after) {
-        // sort each pair's keys in place by size class; a pair longer than
-        // SEG_BIG_CAP sends the whole array through a stable time sort and a
-        // second pair sort instead
-        DevBuf<unsigned int> cnt(SEG_CLASSES, s);
-        TTC_CUDA(cudaMemsetAsync(cnt.get(), 0, SEG_CLASSES * 4, s));
-        seg_classify_kernel<false><<<grid_for(ms), TPB, 0, s>>>(g->poff.get(), ms, cnt.get(), nullptr);
+        unsigned int *cnt = cls.get(), *cbase = cnt + SEG_CLASSES, *cur = cbase + SEG_CLASSES;
+        TTC_CUDA(cudaMemsetAsync(cnt, 0, SEG_CLASSES * 4, side.s));
+        seg_classify_kernel<false><<<grid_for(ms), TPB, 0, side.s>>>(g->poff.get(), ms, cnt, nullptr);
         TTC_LAUNCH_CHECK();
-        unsigned int hc[SEG_CLASSES], base[SEG_CLASSES];
-        TTC_CUDA(cudaMemcpyAsync(hc, cnt.get(), sizeof hc, cudaMemcpyDeviceToHost, s));
-        TTC_CUDA(cudaStreamSynchronize(s));
-        if (hc[SEG_CLASSES - 1] == 0) {
-            unsigned int run = 0;
-            for (int c = 0; c < SEG_CLASSES; c++) {
-                base[c] = run;
-                run += hc[c];
-            }
-            DevBuf<uint32_t> list(run ? run : 1, s);
-            if (run) {
-                TTC_CUDA(cudaMemcpyAsync(cnt.get(), base, sizeof base, cudaMemcpyHostToDevice, s));
-                seg_classify_kernel<true><<<grid_for(ms), TPB, 0, s>>>(g->poff.get(), ms, cnt.get(), list.get());
-                TTC_LAUNCH_CHECK();
-            }
-            seg_sort_tiny_kernel<<<grid_for(ms), TPB, 0, s>>>(g->key.get(), g->poff.get(), ms);
-            TTC_LAUNCH_CHECK();
-            for (int c = 0; c < SEG_CLASSES - 1; c++)
-                if (hc[c]) seg_sort_class(c, g->key.get(), g->poff.get(), list.get() + base[c], hc[c], s);
-        } else {
-            radix_sort_u64_u64_range(reinterpret_cast<uint64_t *>(g->key.get()), pkey.get(), m, g->shift,
-                                     g->shift + span_bits, s);
-            radix_sort_u64_u64(pkey.get(), reinterpret_cast<uint64_t *>(g->key.get()), m, bits_for(n * n - 1), s);
-        }
+        seg_bases_kernel<<<1, 1, 0, side.s>>>(cnt, cbase, cur);
+        TTC_LAUNCH_CHECK();
+        seg_classify_kernel<true><<<grid_for(ms), TPB, 0, side.s>>>(g->poff.get(), ms, cur, lists.get());
+        TTC_LAUNCH_CHECK();
+        seg_sort_tiny_kernel<<<grid_for(ms), TPB, 0, side.s>>>(g->key.get(), g->poff.get(), ms);
+        TTC_LAUNCH_CHECK();
+        seg_sort_classes(g->key.get(), g->poff.get(), lists.get(), cbase, cnt, side.s);
     }
-    pkey.reset(); pid.reset();
-    dir0_flags_kernel<<<grid_for(m), TPB, 0, s>>>(g->key.get(), m, head.get());
+    dir0_flags_kernel<<<grid_for(m), TPB, 0, side.s>>>(g->key.get(), m, dflag.get());
     TTC_LAUNCH_CHECK();
-    exclusive_scan_flags(head.get(), g->fwd.get(), m, s);
-    head.reset();
+    exclusive_scan_flags(dflag.get(), g->fwd.get(), m, side.s);
+    side.fork_done();
 
     prof_end(g, s);
     prof_begin(g, s, "load:degrees");
@@ -1818,10 +1846,12 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
                  *oA = foffA.get(), *oB = foffB.get();
         uint32_t n32 = (uint32_t)n;
         PeelCtl *pc = ctl.get();
-        // stage 1: every SM, down to PEEL_GRID_STOP vertices (one CTA when
+        // stage 1: every SM, down to what the core cluster holds (one CTA when
         // cooperative launches are unavailable)
         {
-            uint32_t stop = PEEL_GRID_STOP;
+            const int csize = core_cluster_size();
+            if (csize <= 0) fail(TTC_ERR_CUDA, "no thread-block cluster of 8 or 16 CTAs fits this device");
+            uint32_t stop = (uint32_t)csize * CORE_PER_MAX;
             void *args[] = {(void *)&a_off, (void *)&a_adj, (void *)&pd, (void *)&lv, (void *)&rA, (void *)&rB,
                             (void *)&fA, (void *)&fB, (void *)&oA, (void *)&oB, (void *)&n32, (void *)&stop,
                             (void *)&pc};
@@ -1849,7 +1879,7 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
                 TTC_LAUNCH_CHECK();
                 exclusive_scan_u32(cdeg.get(), coff.get(), R, s);
                 const uint32_t ce = read_scalar(coff.get() + R, s);
-                DevBuf<uint16_t> cadj(ce ? ce : 1, s);
+                DevBuf<uint32_t> cadj(ce ? ce : 1, s);
                 DevBuf<uint32_t> nchunk(R, s), chunk_pre(R + 1, s), cursor(R, s);
                 tail_chunks_kernel<<<grid_for(R), TPB, 0, s>>>(rem, R, adj_off.get(), nchunk.get());
                 TTC_LAUNCH_CHECK();
@@ -1880,7 +1910,7 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
                 cfg.attrs = attr;
                 cfg.numAttrs = one_cta ? 0 : 1;
                 TTC_CUDA(cudaLaunchKernelEx(&cfg, one_cta ? peel_core_kernel<false> : peel_core_kernel<true>, rem, R,
-                                            per, (const uint32_t *)coff.get(), (const uint16_t *)cadj.get(),
+                                            per, (const uint32_t *)coff.get(), (const uint32_t *)cadj.get(),
                                             level.get(), pdeg.get(), one_cta ? 0u : PEEL_TAIL, tail_list,
                                             ctl.get()));
                 note_launch();
@@ -2056,6 +2086,22 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
     st.tau_hwarp = n_hw;
     st.tau_hcta = n_hc;
     st.tau_huge = n_huge;
+    // join the side stream; a pair longer than the in-place sort's largest
+    // class sends the whole array through a stable time sort and a second
+    // pair sort instead, and the dir-0 prefix is taken again
+    side.join();
+    if (seg_sort_after) {
+        const unsigned int too_long = read_scalar(cls.get() + SEG_CLASSES - 1, s);
+        if (too_long) {
+            radix_sort_u64_u64_range(reinterpret_cast<uint64_t *>(g->key.get()), pkey.get(), m, g->shift,
+                                     g->shift + span_bits, s);
+            radix_sort_u64_u64(pkey.get(), reinterpret_cast<uint64_t *>(g->key.get()), m, bits_for(n * n - 1), s);
+            dir0_flags_kernel<<<grid_for(m), TPB, 0, s>>>(g->key.get(), m, dflag.get());
+            TTC_LAUNCH_CHECK();
+            exclusive_scan_flags(dflag.get(), g->fwd.get(), m, s);
+        }
+    }
+    cls.reset(); lists.reset(); dflag.reset(); pkey.reset();
     set_view(g, s);
     prof_end(g, s);
     TTC_CUDA(cudaStreamSynchronize(s));

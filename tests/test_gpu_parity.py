@@ -87,6 +87,20 @@ def test_power_law_scaled():
         _check(s, d, t, deltas, **opts)
 
 
+def test_two_query_batch_on_a_large_graph():
+    # enough light triangles that a batch of two runs as one query group
+    # (both queries per pair, per-thread accumulators)
+    s, d, t = synth.large_plain(scale=0.05)
+    q = [synth.LARGE_PLAIN_DELTA, synth.LARGE_PLAIN_DELTA_UNBOUNDED, (7 * 86400, 86400, 6 * 86400)]
+    g = ttc.Graph(s, d, t)
+    want = oracle.count(s, d, t, q)
+    assert (g.count_batch(q[:2]) == want[:2]).all()
+    assert (g.count_batch(q) == want).all()
+    for i in range(3):
+        assert (g.count(q[i]) == want[i]).all()
+    g.free()
+
+
 def test_many_graph_shape():
     n, pairs, deltas, seeds = synth.many_graph_specs(count=3, n_lo=300, n_hi=3000)
     for i in range(3):
@@ -245,20 +259,23 @@ def _level_peel(s, d):
 
 
 def test_peel_stages_match_level_synchronous_reference():
-    # n = 100k vertices: the peel runs all three stages (every SM, one
-    # cluster, one CTA); the out-degree bound and the round count are fixed
-    # by the level-synchronous rule wherever the stage boundaries fall
-    s, d, t = synth.large_plain(scale=0.1)
-    kappa, rounds = _level_peel(s, d)
+    # n = 200k vertices: the peel runs all three stages (every SM down to
+    # what one cluster holds, the cluster, one CTA); the out-degree bound and
+    # the round count are fixed by the level-synchronous rule wherever the
+    # stage boundaries fall
+    s, d, t = synth.large_plain(scale=0.2)
     g = ttc.Graph(s, d, t)
-    info = g.info()
-    assert (info["kappa"], info["peel_rounds"]) == (kappa, rounds)
-    q = [synth.LARGE_PLAIN_DELTA]
-    assert (g.count_batch(q) == oracle.count(s, d, t, q)).all()
+    assert (g.info()["kappa"], g.info()["peel_rounds"]) == _level_peel(s, d)
     g.free()
     # smaller graphs: the cluster from the first level on (its widest rounds,
     # loaded several times: the rule admits one answer whatever the timing),
-    # and the one-CTA stage alone
+    # and the one-CTA stage alone; counts against the oracle on one of them
+    s, d, t = synth.large_plain(scale=0.1)
+    g = ttc.Graph(s, d, t)
+    assert (g.info()["kappa"], g.info()["peel_rounds"]) == _level_peel(s, d)
+    q = [synth.LARGE_PLAIN_DELTA]
+    assert (g.count_batch(q) == oracle.count(s, d, t, q)).all()
+    g.free()
     for scale, loads in ((0.05, 4), (0.004, 1)):
         s, d, t = synth.large_plain(scale=scale)
         want = _level_peel(s, d)
