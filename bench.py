@@ -646,7 +646,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "graph": {k: info[k] for k in ("n", "m", "m_s", "tau", "kappa", "sigma_max", "peel_rounds",
                                             "work_bytes", "work_bytes_heavy", "tau_light", "tau_heavy",
-                                            "enum_elems", "device_bytes")},
+                                            "enum_elems", "light_pairs", "device_bytes")},
         }
         print(json.dumps(line), flush=True)
     barrier(ws)

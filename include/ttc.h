@@ -126,6 +126,8 @@ typedef struct {
     uint64_t tau_huge;       /* prefix-sum-path triangles too large for one CTA (flat path) */
     uint64_t tau_hwarp;      /* prefix-sum-path triangles counted by one warp each */
     uint64_t tau_hcta;       /* prefix-sum-path triangles counted by one CTA each */
+    uint64_t light_pairs;    /* sum over one-thread-per-triangle-path triangles of
+                                sigma_A * sigma_B (the (a, b) pairs that path visits) */
     uint32_t key_bits;       /* bits of the packed per-edge key */
     uint32_t reserved;
 } ttc_graph_stats;

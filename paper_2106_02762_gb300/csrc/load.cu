@@ -1239,7 +1239,7 @@ __device__ __forceinline__ uint4 make_record(const RecCtx &c, uint32_t s_uv, uin
 // sizes of heavy records and the work statistics of all records
 __global__ void record_stats_kernel(const uint4 *rec, size_t tau, uint64_t n_light, const uint32_t *poff,
                                     uint64_t *heavy_e, unsigned long long *sums) {
-    unsigned long long w = 0, en = 0, wh = 0;
+    unsigned long long w = 0, en = 0, wh = 0, lp = 0;
     GRID_STRIDE(i, tau) {
         const uint4 r = rec[i];
         const uint64_t a = poff[r.x + 1] - poff[r.x], b = poff[r.y + 1] - poff[r.y], c = poff[r.z + 1] - poff[r.z];
@@ -1248,17 +1248,21 @@ __global__ void record_stats_kernel(const uint4 *rec, size_t tau, uint64_t n_lig
         if (i >= n_light) {
             heavy_e[i - n_light] = a + b;
             wh += 8 * (a + b + c) + 12;
+        } else {
+            lp += a * b;
         }
     }
     for (int o = 16; o; o >>= 1) {
         w += __shfl_xor_sync(0xffffffffu, w, o);
         en += __shfl_xor_sync(0xffffffffu, en, o);
         wh += __shfl_xor_sync(0xffffffffu, wh, o);
+        lp += __shfl_xor_sync(0xffffffffu, lp, o);
     }
     if ((threadIdx.x & 31) == 0) {
         atomicAdd(sums, w);
         atomicAdd(sums + 1, en);
         atomicAdd(sums + 2, wh);
+        atomicAdd(sums + 3, lp);
     }
 }
 
@@ -2036,19 +2040,20 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
     // ---- statistics and heavy-path offsets
     const uint64_t nh = st.tau_heavy;
     DevBuf<uint64_t> he(nh ? nh : 1, s);
-    DevBuf<unsigned long long> ws(3, s);
-    TTC_CUDA(cudaMemsetAsync(ws.get(), 0, 24, s));
+    DevBuf<unsigned long long> ws(4, s);
+    TTC_CUDA(cudaMemsetAsync(ws.get(), 0, 32, s));
     if (tau) {
         record_stats_kernel<<<grid_for(tau), TPB, 0, s>>>(g->tri.get(), tau, n_light, g->poff.get(), he.get(),
                                                           ws.get());
         TTC_LAUNCH_CHECK();
     }
-    unsigned long long hws[3];
-    TTC_CUDA(cudaMemcpyAsync(hws, ws.get(), 24, cudaMemcpyDeviceToHost, s));
+    unsigned long long hws[4];
+    TTC_CUDA(cudaMemcpyAsync(hws, ws.get(), 32, cudaMemcpyDeviceToHost, s));
     TTC_CUDA(cudaStreamSynchronize(s));
     st.work_bytes = hws[0];
     st.enum_elems = hws[1];
     st.work_bytes_heavy = hws[2];
+    st.light_pairs = hws[3];
     // heavy records in three classes by size (one warp, one CTA, flat),
     // stably partitioned so each class is contiguous; the huge class last
     const uint32_t wcap = warp_capacity(g->heavy_wide), ccap = fused_capacity(g->heavy_wide);

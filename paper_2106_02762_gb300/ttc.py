@@ -54,7 +54,7 @@ class LoadOpts(ctypes.Structure):
 class GraphStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in
                 ("n", "m", "m_self_loops", "m_s", "tau", "kappa", "sigma_max", "peel_rounds", "work_bytes",
-                 "enum_elems", "tau_light", "tau_heavy", "device_bytes", "work_bytes_heavy", "tau_huge", "tau_hwarp", "tau_hcta")] + \
+                 "enum_elems", "tau_light", "tau_heavy", "device_bytes", "work_bytes_heavy", "tau_huge", "tau_hwarp", "tau_hcta", "light_pairs")] + \
                [("key_bits", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
