@@ -102,7 +102,8 @@ typedef struct {
     uint32_t labeling;         /* TTC_LABEL_* */
     uint32_t light_max_pairs;  /* triangles with sigma_A * sigma_B below this use the
                                   one-thread-per-triangle path, the others the
-                                  prefix-sum path (1 = all prefix-sum); 0 = default */
+                                  prefix-sum path (1 = all prefix-sum); 0 = default;
+                                  values above 2^20 count as 2^20 */
     uint64_t seed;             /* TTC_ORIENT_RANDOM permutation seed */
     void *stream;              /* cudaStream_t to adopt; NULL = create one */
 } ttc_load_opts;

@@ -47,27 +47,50 @@ namespace ttc {
 
 namespace {
 
-// Table 1: psi(pi_k, rho_r) = T_(value + 1); rows pi_1..pi_6, columns rho_1..rho_8.
-__constant__ uint8_t PSI[6][8] = {
-    {6, 5, 4, 7, 2, 1, 3, 0},
-    {4, 2, 6, 3, 5, 0, 7, 1},
-    {2, 1, 0, 3, 6, 5, 7, 4},
-    {0, 6, 2, 7, 1, 4, 3, 5},
-    {5, 0, 1, 7, 4, 2, 3, 6},
-    {1, 4, 5, 3, 0, 6, 7, 2},
-};
-// Fig. 4: index of rho from the directions (dA, dB, dC) of the three pairs,
-// code = 4 dA + 2 dB + dC, direction 0 being u->v, u->w, v->w.
-//   rho_1 = (0,0,0), rho_2 = (0,1,1), rho_3 = (0,0,1), rho_4 = (0,1,0),
-//   rho_5 = (1,0,0), rho_6 = (1,1,1), rho_7 = (1,0,1), rho_8 = (1,1,0)
-__constant__ uint8_t RHO_OF_CODE[8] = {0, 2, 3, 1, 4, 6, 7, 5};
+// Table 1 composed with Fig. 4, packed into one word per temporal ordering:
+// bits 3 code .. 3 code + 2 of type_pack(pi) hold the type index (T_(value + 1))
+// of psi(pi, rho(code)), where code = 4 dA + 2 dB + dC from the directions of
+// the three pairs, direction 0 being u->v, u->w, v->w.  The lookup is then
+// a shift of a compile-time word instead of a table load.
+constexpr uint32_t type_pack(int pi) {
+    // Table 1: psi(pi_k, rho_r); rows pi_1..pi_6, columns rho_1..rho_8
+    const uint8_t psi[6][8] = {
+        {6, 5, 4, 7, 2, 1, 3, 0},
+        {4, 2, 6, 3, 5, 0, 7, 1},
+        {2, 1, 0, 3, 6, 5, 7, 4},
+        {0, 6, 2, 7, 1, 4, 3, 5},
+        {5, 0, 1, 7, 4, 2, 3, 6},
+        {1, 4, 5, 3, 0, 6, 7, 2},
+    };
+    // Fig. 4: rho_1 = (0,0,0), rho_2 = (0,1,1), rho_3 = (0,0,1), rho_4 = (0,1,0),
+    // rho_5 = (1,0,0), rho_6 = (1,1,1), rho_7 = (1,0,1), rho_8 = (1,1,0) as (dA, dB, dC)
+    const uint8_t rho_of_code[8] = {0, 2, 3, 1, 4, 6, 7, 5};
+    uint32_t v = 0;
+    for (int code = 0; code < 8; code++) v |= uint32_t(psi[pi][rho_of_code[code]]) << (3 * code);
+    return v;
+}
 
 // Temporal orderings (Fig. 3), 0-based: pi_1 = A,B,C  pi_2 = B,A,C  pi_3 = A,C,B
 // pi_4 = B,C,A  pi_5 = C,A,B  pi_6 = C,B,A  (first, second, third pair).
 enum { PI1 = 0, PI2 = 1, PI3 = 2, PI4 = 3, PI5 = 4, PI6 = 5 };
+constexpr uint32_t TP1 = type_pack(PI1), TP2 = type_pack(PI2), TP3 = type_pack(PI3), TP4 = type_pack(PI4),
+                   TP5 = type_pack(PI5), TP6 = type_pack(PI6);
+// every row of Table 1 is a permutation of the eight types
+constexpr bool packs_types_once(uint32_t pack) {
+    uint32_t seen = 0;
+    for (int code = 0; code < 8; code++) seen |= 1u << ((pack >> (3 * code)) & 7u);
+    return seen == 0xffu;
+}
+static_assert(packs_types_once(TP1) && packs_types_once(TP2) && packs_types_once(TP3) && packs_types_once(TP4) &&
+                  packs_types_once(TP5) && packs_types_once(TP6),
+              "Table 1 rows are permutations");
 
+__device__ __forceinline__ uint32_t pack_of(int pi) {
+    return pi == PI1 ? TP1 : pi == PI2 ? TP2 : pi == PI3 ? TP3 : pi == PI4 ? TP4 : pi == PI5 ? TP5 : TP6;
+}
+__device__ __forceinline__ int type_in(uint32_t pack, uint32_t code) { return (int)((pack >> (3 * code)) & 7u); }
 __device__ __forceinline__ int type_of(int pi, uint32_t dA, uint32_t dB, uint32_t dC) {
-    return PSI[pi][RHO_OF_CODE[(dA << 2) | (dB << 1) | dC]];
+    return type_in(pack_of(pi), (dA << 2) | (dB << 1) | dC);
 }
 
 struct Query {
@@ -81,25 +104,27 @@ __device__ __forceinline__ Query load_query(const int64_t *dq, uint32_t q) {
 // ---------------------------------------------------------------- lists
 // A pair's key-sorted edge list in device memory: key[b .. b + n), with the
 // direction split read from the global dir-0 prefix `fwd`.
+// number of keys < bound in the sorted p[0 .. n)
+__device__ __forceinline__ uint32_t search_below(const int64_t *__restrict__ p, uint32_t n, int64_t bound) {
+    uint32_t lo = 0, len = n;
+    while (len > 0) {
+        const uint32_t half = len >> 1;
+        if (__ldg(p + lo + half) < bound) {
+            lo += half + 1;
+            len -= half + 1;
+        } else {
+            len = half;
+        }
+    }
+    return lo;
+}
+
 struct GList {
     const int64_t *__restrict__ key;
     const uint32_t *__restrict__ fwd;
     uint32_t b, n, flip;  // flip: effective direction = stored ^ 1
     // number of keys < bound (bound >= 0)
-    __device__ __forceinline__ uint32_t below(int64_t bound) const {
-        const int64_t *p = key + b;
-        uint32_t lo = 0, len = n;
-        while (len > 0) {
-            const uint32_t half = len >> 1;
-            if (__ldg(p + lo + half) < bound) {
-                lo += half + 1;
-                len -= half + 1;
-            } else {
-                len = half;
-            }
-        }
-        return lo;
-    }
+    __device__ __forceinline__ uint32_t below(int64_t bound) const { return search_below(key + b, n, bound); }
     // effective direction-0 edges among the first pos
     __device__ __forceinline__ uint32_t d0(uint32_t pos) const {
         const uint32_t s0 = __ldg(fwd + b + pos) - __ldg(fwd + b);
@@ -150,6 +175,50 @@ __device__ __forceinline__ uint32_t cnt_le(const L &l, const KeyFmt &f, int64_t 
 template <typename L>
 __device__ __forceinline__ uint32_t cnt_lt(const L &l, const KeyFmt &f, int64_t x) {
     return cnt_le(l, f, x - 1);
+}
+
+// Search bounds, as keys: #{e : key(e) < bound} gives cnt_key, cnt_le and
+// cnt_lt.  Every key is >= 0 and below INT64_MAX, so bound 0 counts nothing
+// and INT64_MAX counts the whole list.
+__device__ __forceinline__ int64_t key_bound(int64_t kx) { return kx & ~int64_t(1); }
+__device__ __forceinline__ int64_t le_bound(const KeyFmt &f, int64_t x) {
+    return x < 0 ? 0 : x >= f.span ? INT64_MAX : (x + 1) << f.shift;
+}
+__device__ __forceinline__ int64_t lt_bound(const KeyFmt &f, int64_t x) { return le_bound(f, x - 1); }
+
+// res[i] = #{keys < bound[i]} in a sorted list of n keys (at(i) reads key
+// i), for N bounds at once.  The halving steps depend only on n, so the N
+// searches advance in lockstep and their loads are in flight together.
+template <int N, typename AT>
+__device__ __forceinline__ void search_n(AT &&at, uint32_t n, const int64_t (&bound)[N], uint32_t (&res)[N]) {
+#pragma unroll
+    for (int i = 0; i < N; i++) res[i] = 0;
+    uint32_t len = n;  // each answer lies in [res[i], res[i] + len]
+    while (len > 1) {
+        const uint32_t half = len >> 1;
+        int64_t v[N];
+#pragma unroll
+        for (int i = 0; i < N; i++) v[i] = at(res[i] + half - 1);
+#pragma unroll
+        for (int i = 0; i < N; i++) res[i] += v[i] < bound[i] ? half : 0u;
+        len -= half;
+    }
+    if (len == 1) {
+        int64_t v[N];
+#pragma unroll
+        for (int i = 0; i < N; i++) v[i] = at(res[i]);
+#pragma unroll
+        for (int i = 0; i < N; i++) res[i] += v[i] < bound[i] ? 1u : 0u;
+    }
+}
+template <int N>
+__device__ __forceinline__ void search_n(const GList &l, const int64_t (&bound)[N], uint32_t (&res)[N]) {
+    const int64_t *p = l.key + l.b;
+    search_n<N>([&](uint32_t i) { return __ldg(p + i); }, l.n, bound, res);
+}
+template <int N>
+__device__ __forceinline__ void search_n(const SList &l, const int64_t (&bound)[N], uint32_t (&res)[N]) {
+    search_n<N>([&](uint32_t i) { return l.key[i]; }, l.n, bound, res);
 }
 
 __device__ __forceinline__ GList glist(const GraphView &gv, uint32_t p, uint32_t flip) {
@@ -220,73 +289,96 @@ __device__ __forceinline__ uint32_t graph_of(const uint64_t *__restrict__ pre, u
 constexpr int LIGHT_THREADS = 256;
 constexpr uint32_t LIGHT_QT = 2;  // queries per group kept in per-thread accumulators
 constexpr int LIGHT_WARPS = LIGHT_THREADS / 32;
+// Records per lane in one work item of a batched (MODE 1) launch: a warp
+// takes 32 * LIGHT_BATCH_R triangles, so the last, partly filled round of
+// their flattened pairs is a smaller share of the rounds.  (Measured on the
+// power-law workload: one record per lane is faster for single queries, two
+// for batches.)
+constexpr int LIGHT_BATCH_R = 2;
 
-// Adds the counts of one pair (x, y) of enumerated edges (x earlier) for all
-// three positions of C's edge.  xa: x is on A (else on B).
+// C's key-sorted list seen from one pair (x, y) of enumerated edges, x the
+// earlier: px, py = #{c : key(c) < key(x)}, #{c : key(c) < key(y)}, and the
+// raw dir-0 prefix fwd[b + pos] at pos = 0, px, py, n, the four positions
+// that bound every case of Lemma 1 once its window is unbounded.
+struct CView {
+    const int64_t *__restrict__ key;
+    const uint32_t *__restrict__ fwd;
+    uint32_t b, n, flip;
+    uint32_t px, py, f0, fx, fy, fn;
+    __device__ __forceinline__ uint32_t below(int64_t bound) const { return search_below(key + b, n, bound); }
+    __device__ __forceinline__ uint32_t raw(uint32_t pos) const {
+        return pos == px ? fx : pos == py ? fy : pos == n ? fn : pos == 0 ? f0 : __ldg(fwd + b + pos);
+    }
+    // effective direction-0 edges among C's positions [lo, hi)
+    __device__ __forceinline__ uint32_t d0_range(uint32_t lo, uint32_t hi) const {
+        const uint32_t s = raw(hi) - raw(lo);
+        return flip ? (hi - lo) - s : s;
+    }
+};
+
+// Adds the counts of one pair (x, y) of enumerated edges (x earlier, times
+// rx <= ry) for all three positions of C's edge.  xa: x is on A (else on B).
+// code = 4 dA + 2 dB (Fig. 4 with dC = 0).
 template <typename Acc>
-__device__ __forceinline__ void light_pair(const GList &C, const KeyFmt &f, const Query &q, bool xa, int64_t rx,
-                                           int64_t ry, uint32_t posCx, uint32_t posCy, uint32_t dA, uint32_t dB,
-                                           Acc &&acc) {
+__device__ __forceinline__ void light_pair(const CView &C, const KeyFmt &f, const Query &q, bool xa, int64_t rx,
+                                           int64_t ry, uint32_t code, Acc &&acc) {
     const int64_t gap = ry - rx;
+    auto add = [&](uint32_t pack, uint32_t lo, uint32_t hi) {
+        const uint32_t n0 = C.d0_range(lo, hi);
+        acc(type_in(pack, code), n0);
+        acc(type_in(pack, code | 1u), (hi - lo) - n0);
+    };
     if (gap <= q.d12) {  // C third
-        const int64_t lim = min(ry + q.d23, rx + q.d13);
-        const uint32_t hi = cnt_le(C, f, lim), lo = posCy;
-        if (hi > lo) {
-            const uint32_t n0 = C.d0(hi) - C.d0(lo);
-            const int pi = xa ? PI1 : PI2;
-            acc(type_of(pi, dA, dB, 0), n0);
-            acc(type_of(pi, dA, dB, 1), (hi - lo) - n0);
-        }
+        const uint32_t hi = cnt_le(C, f, min(ry + q.d23, rx + q.d13));
+        if (hi > C.py) add(xa ? TP1 : TP2, C.py, hi);
     }
     if (gap <= q.d13) {  // C second
-        const uint32_t lo = max(posCx, cnt_lt(C, f, ry - q.d23));
-        const uint32_t hi = min(posCy, cnt_le(C, f, rx + q.d12));
-        if (hi > lo) {
-            const uint32_t n0 = C.d0(hi) - C.d0(lo);
-            const int pi = xa ? PI3 : PI4;
-            acc(type_of(pi, dA, dB, 0), n0);
-            acc(type_of(pi, dA, dB, 1), (hi - lo) - n0);
-        }
+        const uint32_t lo = max(C.px, cnt_lt(C, f, ry - q.d23));
+        const uint32_t hi = min(C.py, cnt_le(C, f, rx + q.d12));
+        if (hi > lo) add(xa ? TP3 : TP4, lo, hi);
     }
     if (gap <= q.d23) {  // C first
-        const uint32_t lo = cnt_lt(C, f, max(rx - q.d12, ry - q.d13)), hi = posCx;
-        if (hi > lo) {
-            const uint32_t n0 = C.d0(hi) - C.d0(lo);
-            const int pi = xa ? PI5 : PI6;
-            acc(type_of(pi, dA, dB, 0), n0);
-            acc(type_of(pi, dA, dB, 1), (hi - lo) - n0);
-        }
+        const uint32_t lo = cnt_lt(C, f, max(rx - q.d12, ry - q.d13));
+        if (C.px > lo) add(xa ? TP5 : TP6, lo, C.px);
     }
 }
 
+template <int R>
 struct WarpTris {
-    uint32_t excl[LIGHT_WARPS][33];  // exclusive prefix of pair counts
-    uint4 lst[LIGHT_WARPS][32];      // A.b, B.b, C.b, C.n
-    uint32_t bn[LIGHT_WARPS][32];    // B.n
-    uint32_t fl[LIGHT_WARPS][32];    // flip flags
+    uint32_t excl[LIGHT_WARPS][32 * R + 1];  // exclusive prefix of pair counts
+    uint4 lst[LIGHT_WARPS][32 * R];          // A.b, B.b, C.b, C.n
+    uint4 aux[LIGHT_WARPS][32 * R];          // B.n, flip flags, fwd[C.b], fwd[C.b + C.n]
+    float inv[LIGHT_WARPS][32 * R];          // 1 / B.n
+    Query q[LIGHT_WARPS][LIGHT_QT];          // MODE 1: the item's query group
 };
 
-// Warp-cooperative light kernel over a table of graphs.  Each warp takes 32
-// consecutive triangle records of one graph, flattens their A x B pairs into
-// one index space and gives every lane one pair per step.
+// Warp-cooperative light kernel over a table of graphs.  Each warp takes
+// 32 R consecutive triangle records (record base + r * 32 + lane in slot
+// r * 32 + lane), flattens their A x B pairs into one index space and gives
+// every lane one pair per round.
 //   MODE 0: one query per graph (dq[3 g]); out[8 g + type].
 //   MODE 1: nq queries on graph 0; out[8 q + type].
 //   MODE 2: one query on graph 0 for the triangles idx[0 .. nidx);
 //           out[8 i + type] per triangle.
-// chunk_pre[g] = first 32-record chunk of graph g (exclusive prefix, G + 1).
-template <int MODE>
-__global__ void __launch_bounds__(LIGHT_THREADS)
+// chunk_pre[g] = first 32-record chunk of graph g (exclusive prefix, G + 1);
+// R > 1 needs G == 1.  Every light triangle has sigma_A * sigma_B below the
+// light threshold (at most 2^20), so a work item has fewer than 2^32 pairs
+// and a pair's index within its triangle is below 2^20.
+template <int MODE, int R>
+__global__ void __launch_bounds__(LIGHT_THREADS, MODE == 1 ? 4 : 5)
     light_kernel(const GraphView *__restrict__ gvs, const uint64_t *__restrict__ chunk_pre, uint32_t G,
                  const int64_t *dq, uint32_t nq, unsigned long long *out, unsigned long long *flag,
                  const uint64_t *idx, uint64_t nidx, uint32_t qpw = 1) {
-    __shared__ WarpTris wt;
+    __shared__ WarpTris<R> wt;
     __shared__ unsigned long long s_acc[MODE == 0 ? 8 : 1][MODE == 0 ? 256 : 1];
     // MODE 1: [nq * 8] block accumulators, then, when every item's query
-    // group has at most LIGHT_QT queries, per-thread accumulators
-    // [LIGHT_QT * 8][LIGHT_THREADS] (no shared atomics per pair)
+    // group has at most LIGHT_QT queries, per-thread 32-bit accumulators
+    // [LIGHT_QT * 8][LIGHT_THREADS] (no shared atomics per pair; a carry out
+    // of one adds 2^32 to the block accumulator, and 32-bit cells keep the
+    // block's shared memory small enough for four blocks per SM)
     extern __shared__ unsigned long long s_bacc[];
     const bool tslots = MODE == 1 && qpw <= LIGHT_QT;
-    unsigned long long *s_t = s_bacc + 8 * (size_t)nq;
+    uint32_t *s_t = reinterpret_cast<uint32_t *>(s_bacc + 8 * (size_t)nq);
     uint32_t slot_q0 = 0;  // first query of the group the thread's slots hold
     const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if constexpr (MODE == 0) {
@@ -308,7 +400,7 @@ __global__ void __launch_bounds__(LIGHT_THREADS)
         for (uint32_t ql = 0; ql < qpw && slot_q0 + ql < nq; ql++) {
 #pragma unroll
             for (int t = 0; t < 8; t++) {
-                unsigned long long &cell = s_t[(ql * 8 + t) * LIGHT_THREADS + threadIdx.x];
+                uint32_t &cell = s_t[(ql * 8 + t) * LIGHT_THREADS + threadIdx.x];
                 unsigned long long v = cell;
                 cell = 0;
 #pragma unroll
@@ -320,7 +412,10 @@ __global__ void __launch_bounds__(LIGHT_THREADS)
             }
         }
     };
-    const uint64_t nchunks = MODE == 2 ? (nidx + 31) / 32 : __ldg(chunk_pre + G);
+    constexpr uint32_t PER = 32 * R;  // records per work item
+    const uint64_t nchunks = MODE == 2 ? (nidx + PER - 1) / PER
+                             : R == 1 ? __ldg(chunk_pre + G)
+                                      : (__ldg(chunk_pre + 1) + R - 1) / R;
     const uint64_t gw = (uint64_t)blockIdx.x * LIGHT_WARPS + w, nw = (uint64_t)gridDim.x * LIGHT_WARPS;
     // MODE 1: work items are (chunk, group of qpw queries), so small graphs
     // still spread a large batch over many warps
@@ -333,10 +428,7 @@ __global__ void __launch_bounds__(LIGHT_THREADS)
             flush_slots();
             slot_q0 = q_beg;
         }
-        int64_t gmax = 0;
-        if constexpr (MODE == 1)
-            for (uint32_t q = q_beg; q < q_end; q++) gmax = max(gmax, dq[3 * q]);
-        const uint32_t g = MODE == 0 ? graph_of(chunk_pre, G, c) : 0u;
+        const uint32_t g = MODE == 0 && R == 1 ? graph_of(chunk_pre, G, c) : 0u;
         if constexpr (MODE == 0) {
             if (g != cur_g) {
                 if (cur_g != 0xffffffffu) warp_flush(s_acc, out + 8 * cur_g, flag, ovf);
@@ -345,64 +437,119 @@ __global__ void __launch_bounds__(LIGHT_THREADS)
         }
         const GraphView &gv = gvs[g];
         const KeyFmt f{gv.shift, gv.span};
-        const Query Q0 = load_query(dq, MODE == 0 ? g : 0u);
-        if constexpr (MODE != 1) gmax = Q0.d13;  // every case needs t_y - t_x <= d13
-        const uint64_t lc = MODE == 0 ? c - __ldg(chunk_pre + g) : c;
-        const uint64_t ti = lc * 32 + lane;
+        // the group's queries (MODE 1: in the warp's shared slots when the
+        // thread's accumulators hold them)
+        Query Q0{0, 0, 0};
+        int64_t gmax = 0;  // every case needs t_y - t_x <= d13
+        if constexpr (MODE == 1) {
+            if (tslots && lane < q_end - q_beg) wt.q[w][lane] = load_query(dq, q_beg + lane);
+            for (uint32_t q = q_beg; q < q_end; q++) gmax = max(gmax, dq[3 * q]);
+        } else {
+            Q0 = load_query(dq, MODE == 0 ? g : 0u);
+            gmax = Q0.d13;
+        }
+        // with every pair inside the widest window, C's prefix ends are
+        // staged per triangle; otherwise a passing pair loads them
+        const bool wide = gmax >= f.span;
+        const uint64_t base = (MODE == 0 && R == 1 ? c - __ldg(chunk_pre + g) : c) * PER;
         const uint64_t lim = MODE == 2 ? nidx : gv.n_light;
-        uint32_t npairs = 0;
-        if (ti < lim) {
-            const uint4 r = __ldg(gv.tri + (MODE == 2 ? idx[ti] : ti));
-            const uint32_t ab = __ldg(gv.poff + r.x), an = __ldg(gv.poff + r.x + 1) - ab;
-            const uint32_t bb = __ldg(gv.poff + r.y), bn = __ldg(gv.poff + r.y + 1) - bb;
-            const uint32_t cb = __ldg(gv.poff + r.z), cn = __ldg(gv.poff + r.z + 1) - cb;
-            npairs = an * bn;
-            wt.lst[w][lane] = make_uint4(ab, bb, cb, cn);
-            wt.bn[w][lane] = bn;
-            wt.fl[w][lane] = r.w;
-        }
-        uint32_t x = npairs;
+        uint32_t np[R];
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= (uint32_t)o) x += y;
+        for (int r = 0; r < R; r++) {
+            const uint32_t slot = r * 32 + lane;
+            const uint64_t ti = base + slot;
+            np[r] = 0;
+            if (ti < lim) {
+                const uint4 rec = __ldg(gv.tri + (MODE == 2 ? idx[ti] : ti));
+                const uint32_t ab = __ldg(gv.poff + rec.x), an = __ldg(gv.poff + rec.x + 1) - ab;
+                const uint32_t bb = __ldg(gv.poff + rec.y), bn = __ldg(gv.poff + rec.y + 1) - bb;
+                const uint32_t cb = __ldg(gv.poff + rec.z), cn = __ldg(gv.poff + rec.z + 1) - cb;
+                np[r] = an * bn;
+                wt.lst[w][slot] = make_uint4(ab, bb, cb, cn);
+                uint32_t f0 = 0, fn = 0;
+                if (wide && np[r]) {
+                    f0 = __ldg(gv.fwd + cb);
+                    fn = __ldg(gv.fwd + cb + cn);
+                }
+                wt.aux[w][slot] = make_uint4(bn, rec.w, f0, fn);
+                wt.inv[w][slot] = bn ? __frcp_rn((float)bn) : 0.f;
+            }
         }
-        wt.excl[w][lane] = x - npairs;
-        const uint32_t total = __shfl_sync(0xffffffffu, x, 31);
-        if (lane == 0) wt.excl[w][32] = total;
+        uint32_t total = 0;
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            uint32_t x = np[r];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= (uint32_t)o) x += y;
+            }
+            wt.excl[w][r * 32 + lane] = total + x - np[r];
+            total += __shfl_sync(0xffffffffu, x, 31);
+        }
+        if (lane == 0) wt.excl[w][PER] = total;
         __syncwarp();
-        for (uint32_t base = 0; base < total; base += 32) {
-            const uint32_t j = base + lane;
+        for (uint32_t rbase = 0; rbase < total; rbase += 32) {
+            const uint32_t j = rbase + lane;
             if (j >= total) continue;
             uint32_t o = 0;  // last slot with excl <= j (skips empty slots before it)
 #pragma unroll
-            for (uint32_t step = 16; step; step >>= 1)
+            for (uint32_t step = PER / 2; step; step >>= 1)
                 if (wt.excl[w][o + step] <= j) o += step;
-            const uint4 L = wt.lst[w][o];
-            const uint32_t bn = wt.bn[w][o], fl = wt.fl[w][o];
+            const uint4 L = wt.lst[w][o], X = wt.aux[w][o];
+            const uint32_t bn = X.x, fl = X.y;
             const uint32_t loc = j - wt.excl[w][o];
-            const uint32_t ai = loc / bn, bi = loc - ai * bn;
+            // loc < 2^20: (loc + 1/2) / bn is at least 1 / (2 bn) from an
+            // integer, and the float product is within 2^-3 / bn of it
+            const uint32_t ai = __float2uint_rz(((float)loc + 0.5f) * wt.inv[w][o]), bi = loc - ai * bn;
             const int64_t ka = __ldg(gv.key + L.x + ai), kb = __ldg(gv.key + L.y + bi);
             const int64_t ra = ka >> f.shift, rb = kb >> f.shift;
             const bool a_first = ka < kb;
             const int64_t gap = a_first ? rb - ra : ra - rb;
             if (gap > gmax) continue;
-            const GList C{gv.key, gv.fwd, L.z, L.w, (fl & TriRec::FLIP_C) ? 1u : 0u};
             const uint32_t dA = (uint32_t)(ka & 1) ^ (fl & TriRec::FLIP_A);
             const uint32_t dB = (uint32_t)(kb & 1) ^ ((fl & TriRec::FLIP_B) ? 1u : 0u);
-            const uint32_t pa = cnt_key(C, ka), pb = cnt_key(C, kb);
-            for (uint32_t q = q_beg; q < q_end; q++) {
-                const Query Q = MODE == 1 ? load_query(dq, q) : Q0;
-                auto accq = [&](int type, uint32_t n) {
-                    if constexpr (MODE == 0) add_checked(s_acc[type][threadIdx.x], n, ovf);
-                    else if constexpr (MODE == 1) {
-                        if (tslots) add_checked(s_t[((q - q_beg) * 8 + type) * LIGHT_THREADS + threadIdx.x], n, ovf);
-                        else shared_add(&s_bacc[q * 8 + type], n, ovf);
-                    }
-                    else atomicAdd(out + 8 * (lc * 32 + o) + type, (unsigned long long)n);
-                };
-                if (a_first) light_pair(C, f, Q, true, ra, rb, pa, pb, dA, dB, accq);
-                else light_pair(C, f, Q, false, rb, ra, pb, pa, dA, dB, accq);
+            const uint32_t code = (dA << 2) | (dB << 1);
+            const int64_t *ck = gv.key + L.z;
+            const int64_t bab[2] = {key_bound(ka), key_bound(kb)};
+            uint32_t pab[2];
+            search_n<2>([&](uint32_t i) { return __ldg(ck + i); }, L.w, bab, pab);
+            const uint32_t pa = pab[0], pb = pab[1];
+            CView C;
+            C.key = gv.key;
+            C.fwd = gv.fwd;
+            C.b = L.z;
+            C.n = L.w;
+            C.flip = (fl & TriRec::FLIP_C) ? 1u : 0u;
+            C.px = a_first ? pa : pb;
+            C.py = a_first ? pb : pa;
+            C.f0 = wide ? X.z : __ldg(gv.fwd + L.z);
+            C.fn = wide ? X.w : __ldg(gv.fwd + L.z + L.w);
+            C.fx = __ldg(gv.fwd + L.z + C.px);
+            C.fy = __ldg(gv.fwd + L.z + C.py);
+            const int64_t rx = a_first ? ra : rb, ry = a_first ? rb : ra;
+            if (MODE != 1 || tslots) {
+#pragma unroll
+                for (uint32_t ql = 0; ql < (MODE == 1 ? LIGHT_QT : 1u); ql++) {
+                    if (MODE == 1 && q_beg + ql >= q_end) break;
+                    auto accq = [&](int type, uint32_t n) {
+                        if constexpr (MODE == 0) add_checked(s_acc[type][threadIdx.x], n, ovf);
+                        else if constexpr (MODE == 1) {
+                            uint32_t &cell = s_t[(ql * 8 + type) * LIGHT_THREADS + threadIdx.x];
+                            const uint32_t old = cell;
+                            cell = old + n;
+                            if (cell < old) shared_add(&s_bacc[(q_beg + ql) * 8 + type], 1ull << 32, ovf);
+                        }
+                        else atomicAdd(out + 8 * (base + o) + type, (unsigned long long)n);
+                    };
+                    light_pair(C, f, MODE == 1 ? wt.q[w][ql] : Q0, a_first, rx, ry, code, accq);
+                }
+            } else {
+                for (uint32_t q = q_beg; q < q_end; q++) {
+                    const Query Q = load_query(dq, q);
+                    auto accq = [&](int type, uint32_t n) { shared_add(&s_bacc[q * 8 + type], n, ovf); };
+                    light_pair(C, f, Q, a_first, rx, ry, code, accq);
+                }
             }
         }
         __syncwarp();
@@ -422,10 +569,10 @@ __global__ void __launch_bounds__(LIGHT_THREADS)
 __device__ __forceinline__ void phase1_values(const GList &C, const KeyFmt &f, const Query &q, int64_t ke,
                                               uint32_t out[8]) {
     const int64_t re = ke >> f.shift;
-    const uint32_t ph = cnt_le(C, f, re + q.d13);
-    const uint32_t pl = cnt_key(C, ke);
-    const uint32_t pr = cnt_lt(C, f, re - q.d23);
-    const uint32_t pm = cnt_lt(C, f, re - q.d13);
+    const int64_t bd[4] = {le_bound(f, re + q.d13), key_bound(ke), lt_bound(f, re - q.d23), lt_bound(f, re - q.d13)};
+    uint32_t ps[4];
+    search_n<4>(C, bd, ps);
+    const uint32_t ph = ps[0], pl = ps[1], pr = ps[2], pm = ps[3];
     const uint32_t h0 = C.d0(ph), l0 = C.d0(pl), r0 = C.d0(pr), m0 = C.d0(pm);
     out[0] = h0; out[1] = ph - h0;
     out[2] = l0; out[3] = pl - l0;
@@ -441,25 +588,32 @@ __device__ __forceinline__ void phase2_edge(const OL &O, const GList &C, const K
                                             PF &&pref, ADD &&add) {
     const int64_t re = ke >> f.shift;
     // searches in C (split by C's direction)
-    const uint32_t posC = cnt_key(C, ke);
-    const uint32_t K0 = C.d0(posC);
-    const uint32_t pH = cnt_le(C, f, re + q.d23);
-    const uint32_t H0 = C.d0(pH);
-    const uint32_t pG = cnt_le(C, f, re + q.d12);
-    const uint32_t G0 = C.d0(pG);
-    const uint32_t pLo = cnt_lt(C, f, re - q.d12);
-    const uint32_t Lo0 = C.d0(pLo);
+    const int64_t bc[4] = {key_bound(ke), le_bound(f, re + q.d23), le_bound(f, re + q.d12), lt_bound(f, re - q.d12)};
+    uint32_t pc[4];
+    search_n<4>(C, bc, pc);
+    const uint32_t posC = pc[0], pH = pc[1], pG = pc[2], pLo = pc[3];
+    const uint32_t K0 = C.d0(posC), H0 = C.d0(pH), G0 = C.d0(pG), Lo0 = C.d0(pLo);
     const uint32_t Kd[2] = {K0, posC - K0}, Hd[2] = {H0, pH - H0}, Gd[2] = {G0, pG - G0},
                    Lod[2] = {Lo0, pLo - Lo0};
     // searches in O (merged positions)
-    const uint32_t posO = cnt_key(O, ke);
-    const uint32_t o_lo = min(cnt_lt(O, f, re - q.d12), posO);
-    const uint32_t o_mid = min(max(cnt_le(O, f, re + q.d23 - q.d13), o_lo), posO);
-    const uint32_t r1 = max(cnt_le(O, f, re + min(q.d12, q.d23)), posO);
-    const uint32_t r2 = max(cnt_le(O, f, re + max(q.d12, q.d23)), r1);
-    const uint32_t r3 = max(cnt_le(O, f, re + q.d13), r2);
-    const uint32_t sp = max(cnt_le(O, f, re + q.d13 - q.d12), posO);
-    const uint32_t en = max(cnt_le(O, f, re + q.d23), sp);
+    const int64_t bo[8] = {key_bound(ke),
+                           lt_bound(f, re - q.d12),
+                           le_bound(f, re + q.d23 - q.d13),
+                           le_bound(f, re + min(q.d12, q.d23)),
+                           le_bound(f, re + max(q.d12, q.d23)),
+                           le_bound(f, re + q.d13),
+                           le_bound(f, re + q.d13 - q.d12),
+                           le_bound(f, re + q.d23)};
+    uint32_t po[8];
+    search_n<8>(O, bo, po);
+    const uint32_t posO = po[0];
+    const uint32_t o_lo = min(po[1], posO);
+    const uint32_t o_mid = min(max(po[2], o_lo), posO);
+    const uint32_t r1 = max(po[3], posO);
+    const uint32_t r2 = max(po[4], r1);
+    const uint32_t r3 = max(po[5], r2);
+    const uint32_t sp = max(po[6], posO);
+    const uint32_t en = max(po[7], sp);
     const uint32_t pos[8] = {o_lo, o_mid, posO, r1, r2, r3, sp, en};
     uint32_t d0s[8];
 #pragma unroll
@@ -1081,14 +1235,15 @@ void count_graph(ttc_graph *g, const int64_t *dq, uint32_t k, unsigned long long
     const GraphView *gv = g->view.get();
     const uint64_t *light_pre = g->prefix.get();
     if (nl) {
-        const uint64_t chunks = (nl + 31) / 32;
         if (k == 1) {
             prof_begin(g, s, "light");
-            light_kernel<0><<<light_grid(chunks), LIGHT_THREADS, 0, s>>>(gv, light_pre, 1, dq, 1, acc, flag, nullptr,
-                                                                         0);
+            light_kernel<0, 1><<<light_grid((nl + 31) / 32), LIGHT_THREADS, 0, s>>>(gv, light_pre, 1, dq, 1, acc, flag,
+                                                                                  nullptr, 0);
             TTC_LAUNCH_CHECK();
             prof_end(g, s);
         } else {
+            // work items of 32 * LIGHT_BATCH_R records
+            const uint64_t chunks = (nl + 32 * LIGHT_BATCH_R - 1) / (32 * LIGHT_BATCH_R);
             for (uint32_t q0 = 0; q0 < k; q0 += MAX_BATCH_SMEM_Q) {
                 const uint32_t nq = k - q0 < MAX_BATCH_SMEM_Q ? k - q0 : MAX_BATCH_SMEM_Q;
                 // enough (chunk, query group) items to fill the GPU, and no
@@ -1097,16 +1252,17 @@ void count_graph(ttc_graph *g, const int64_t *dq, uint32_t k, unsigned long long
                 const uint32_t groups = (uint32_t)std::min<uint64_t>(nq, (want_items + chunks - 1) / chunks);
                 const uint32_t qpw = (nq + groups - 1) / groups;
                 prof_begin(g, s, "light_batch");
-                const size_t smem = nq * 64 + (qpw <= LIGHT_QT ? (size_t)LIGHT_QT * 8 * LIGHT_THREADS * 8 : 0);
+                const size_t smem = nq * 64 + (qpw <= LIGHT_QT ? (size_t)LIGHT_QT * 8 * LIGHT_THREADS * 4 : 0);
                 static int light1_device = -1;
                 int dev = 0;
                 TTC_CUDA(cudaGetDevice(&dev));
                 if (light1_device != dev) {
-                    TTC_CUDA(cudaFuncSetAttribute(light_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  (int)(MAX_BATCH_SMEM_Q * 64 + LIGHT_QT * 8 * LIGHT_THREADS * 8)));
+                    TTC_CUDA(cudaFuncSetAttribute(light_kernel<1, LIGHT_BATCH_R>,
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)(MAX_BATCH_SMEM_Q * 64 + LIGHT_QT * 8 * LIGHT_THREADS * 4)));
                     light1_device = dev;
                 }
-                light_kernel<1><<<light_grid(chunks * ((nq + qpw - 1) / qpw)), LIGHT_THREADS, smem, s>>>(
+                light_kernel<1, LIGHT_BATCH_R><<<light_grid(chunks * ((nq + qpw - 1) / qpw)), LIGHT_THREADS, smem, s>>>(
                     gv, light_pre, 1, dq + 3 * (size_t)q0, nq, acc + 8 * (size_t)q0, flag, nullptr, 0, qpw);
                 TTC_LAUNCH_CHECK();
                 prof_end(g, s);
@@ -1231,7 +1387,7 @@ void count_sample(ttc_graph *g, const int64_t *dq, uint64_t first, uint64_t stri
     DevBuf<unsigned long long> flag(1, s);
     TTC_CUDA(cudaMemsetAsync(flag.get(), 0, 8, s));
     if (nlc) {
-        light_kernel<2><<<light_grid((nlc + 31) / 32), LIGHT_THREADS, 0, s>>>(
+        light_kernel<2, 1><<<light_grid((nlc + 31) / 32), LIGHT_THREADS, 0, s>>>(
             g->view.get(), g->prefix.get(), 1, dq, 1, d_out.get(), flag.get(), d_idx.get(), nlc);
         TTC_LAUNCH_CHECK();
     }
@@ -1281,7 +1437,7 @@ void count_multi_launch(const MultiTable &t, const int64_t *dq, unsigned long lo
                         int heavy_per_sm, cudaStream_t s) {
     unsigned long long *flag = acc + 8 * (size_t)t.G;
     if (t.chunks) {
-        light_kernel<0><<<light_grid(t.chunks, light_per_sm), LIGHT_THREADS, 0, s>>>(t.gvs, t.chunk_pre, t.G, dq, 1,
+        light_kernel<0, 1><<<light_grid(t.chunks, light_per_sm), LIGHT_THREADS, 0, s>>>(t.gvs, t.chunk_pre, t.G, dq, 1,
                                                                                      acc, flag, nullptr, 0);
         TTC_LAUNCH_CHECK();
     }

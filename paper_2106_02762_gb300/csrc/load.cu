@@ -1657,7 +1657,10 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
     cudaStream_t s = g->stream;
     ttc_graph_stats &st = g->st;
     g->labeling = opt.labeling;
-    g->light_max_pairs = opt.light_max_pairs ? opt.light_max_pairs : default_light_max_pairs();
+    // the light path decodes a pair's index within its triangle in float
+    // arithmetic, exact below 2^20 pairs per triangle
+    g->light_max_pairs = opt.light_max_pairs ? std::min<uint32_t>(opt.light_max_pairs, 1u << 20)
+                                             : default_light_max_pairs();
     if (opt.orientation > TTC_ORIENT_RANDOM) fail(TTC_ERR_INVALID, "unknown orientation %u", opt.orientation);
     if (opt.labeling > TTC_LABEL_SOURCE) fail(TTC_ERR_INVALID, "unknown labeling %u", opt.labeling);
     if (m_in >= (uint64_t(1) << 32) - 1) fail(TTC_ERR_RANGE, "m = %llu exceeds 2^32 - 2 edges", (unsigned long long)m_in);

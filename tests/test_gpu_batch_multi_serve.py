@@ -190,3 +190,46 @@ def test_delta_grid_matches_oracle():
     assert np.allclose(cyc, share, rtol=0, atol=1e-12)
     assert (counts == np.stack([g.count_batch([(d13, a, b) for b in d23]) for a in d12])).all()
     g.free()
+
+
+def _one_triangle(n_a, n_b, n_c, a_before_b=None, seed=11):
+    # u = 0, v = 1, w = 2: A = {0, 1}, B = {0, 2} and the heaviest pair
+    # C = {1, 2}, every edge directed the same way; A's and B's edges take
+    # the times 0 .. n_a + n_b - 1 (A's all first, B's all first, or mixed),
+    # C's edges come after all of them
+    rng = np.random.default_rng(seed)
+    if a_before_b is None:
+        ab = rng.permutation(n_a + n_b)
+    else:
+        ab = np.arange(n_a + n_b) if a_before_b else np.concatenate([np.arange(n_b, n_a + n_b), np.arange(n_b)])
+    s = np.concatenate([np.zeros(n_a), np.zeros(n_b), np.ones(n_c)]).astype(np.uint32)
+    d = np.concatenate([np.ones(n_a), np.full(n_b, 2), np.full(n_c, 2)]).astype(np.uint32)
+    t = np.concatenate([ab, 10**6 + np.arange(n_c)]).astype(np.int64)
+    return s, d, t
+
+
+def test_batched_light_counts_past_32_bits():
+    # one light triangle with 1023 x 1024 enumerated pairs and 150000 edges
+    # on C: each lane of the batched light path takes 32736 pairs, and with
+    # every window unbounded each pair puts all of C's edges in one type, so
+    # a lane's 32-bit accumulator carries past 2^32 several times
+    unb = synth.LARGE_PLAIN_DELTA_UNBOUNDED
+    # the type of "A's edge, then B's edge, then C's" and of "B, A, C" on
+    # this layout, from the oracle on small copies of it
+    t_ab = int(np.flatnonzero(oracle.count(*_one_triangle(2, 2, 3, True), [unb])[0])[0])
+    t_ba = int(np.flatnonzero(oracle.count(*_one_triangle(2, 2, 3, False), [unb])[0])[0])
+    assert t_ab != t_ba
+    n_a, n_b, n_c = 1023, 1024, 150000
+    s, d, t = _one_triangle(n_a, n_b, n_c)
+    g = ttc.Graph(s, d, t, light_max_pairs=1 << 20)
+    assert g.info()["tau_light"] == 1
+    # pairs (a, b) with a earlier: for each b, the A edges before it
+    ta, tb = np.sort(t[:n_a]), t[n_a:n_a + n_b]
+    n_ab = int(np.searchsorted(ta, tb).sum())
+    want = np.zeros(8, np.uint64)
+    want[t_ab] = n_ab * n_c
+    want[t_ba] = (n_a * n_b - n_ab) * n_c
+    assert int(want.sum()) == n_a * n_b * n_c
+    assert (g.count(unb) == want).all()
+    assert (g.count_batch([unb, unb]) == np.stack([want, want])).all()
+    g.free()
