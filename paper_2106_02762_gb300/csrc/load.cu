@@ -18,6 +18,7 @@
 #include <algorithm>
 
 #include "graph.cuh"
+#include "sort.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -1773,7 +1774,7 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
     }
     st.key_bits = (uint32_t)(span_bits + g->shift);
     // group by pair; stable, so each pair's edges stay in key order
-    radix_sort_u64_u64(pkey.get(), reinterpret_cast<uint64_t *>(g->key.get()), m, bits_for(n * n - 1), s);
+    radix_sort_bufs(pkey, g->key, m, 0, bits_for(n * n - 1), s);
     DevBuf<uint8_t> head(m, s);
     DevBuf<uint32_t> pid(m + 1, s);
     head_flags_kernel<<<grid_for(m), TPB, 0, s>>>(pkey.get(), m, head.get());
@@ -1942,7 +1943,7 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
                                                  okey_v.get(), id_of.get(), smax.get());
     TTC_LAUNCH_CHECK();
     level.reset();
-    radix_sort_u64_u32(okey_v.get(), id_of.get(), n, bits_for(read_scalar(smax.get(), s)), s);
+    radix_sort_bufs(okey_v, id_of, n, 0, bits_for(read_scalar(smax.get(), s)), s);
     okey_v.reset();
     rank_scatter_kernel<<<grid_for(n), TPB, 0, s>>>(id_of.get(), (uint32_t)n, rank_of.get());
     TTC_LAUNCH_CHECK();
@@ -1953,7 +1954,7 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
     orient_kernel<<<grid_for(ms), TPB, 0, s>>>(g->pair_vtx.get(), ms, rank_of.get(), n, okey.get(), opair.get());
     TTC_LAUNCH_CHECK();
     rank_of.reset();
-    radix_sort_u64_u32(okey.get(), opair.get(), ms, bits_for(n * n - 1), s);
+    radix_sort_bufs(okey, opair, ms, 0, bits_for(n * n - 1), s);
     DevBuf<uint32_t> out_off(n + 1, s), in_off(n + 1, s), osrc(ms, s), onbr(ms, s), in_e(ms, s);
     offsets_from_sorted_kernel<<<grid_for(n + 1), TPB, 0, s>>>(okey.get(), ms, n, (uint32_t)n, out_off.get());
     TTC_LAUNCH_CHECK();
@@ -1966,7 +1967,7 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
                                                        in_e.get());
         TTC_LAUNCH_CHECK();
         okey.reset();
-        radix_sort_u64_u32(tkey.get(), in_e.get(), ms, bits_for(n - 1), s);
+        radix_sort_bufs(tkey, in_e, ms, 0, bits_for(n - 1), s);
         offsets_from_sorted_kernel<<<grid_for(n + 1), TPB, 0, s>>>(tkey.get(), ms, 1, (uint32_t)n, in_off.get());
         TTC_LAUNCH_CHECK();
     }

@@ -6,6 +6,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "sort.cuh"
 
 namespace ttc {
 
@@ -211,16 +212,17 @@ __global__ void __launch_bounds__(RS_THREADS)
     }
 }
 
+// The passes of the sort, ping-ponging between (keys, vals) and (kalt,
+// valt); returns true when the result is left in (kalt, valt).
 template <typename V>
-void radix_sort_impl(uint64_t *keys, V *vals, size_t n, int begin_bit, int end_bit, cudaStream_t s) {
-    if (n <= 1 || end_bit <= begin_bit) return;
+bool radix_sort_passes(uint64_t *keys, V *vals, uint64_t *kalt, V *valt, size_t n, int begin_bit, int end_bit,
+                       cudaStream_t s) {
+    if (n <= 1 || end_bit <= begin_bit) return false;
     if (n >= (size_t(1) << 32)) fail(TTC_ERR_RANGE, "radix sort: %zu elements exceed 2^32", n);
     const unsigned tiles = ceil_div(n, RS_TILE);
-    DevBuf<uint64_t> kalt(n, s);
-    DevBuf<V> valt(n, s);
     DevBuf<uint32_t> counts((size_t)RADIX * tiles, s), offs((size_t)RADIX * tiles + 1, s);
-    uint64_t *kin = keys, *kout = kalt.get();
-    V *vin = vals, *vout = valt.get();
+    uint64_t *kin = keys, *kout = kalt;
+    V *vin = vals, *vout = valt;
     const size_t dyn = (size_t)RS_TILE * (sizeof(uint64_t) + sizeof(V));
     static int configured_device = -1;
     int dev = 0;
@@ -241,9 +243,17 @@ void radix_sort_impl(uint64_t *keys, V *vals, size_t n, int begin_bit, int end_b
         uint64_t *tk = kin; kin = kout; kout = tk;
         V *tv = vin; vin = vout; vout = tv;
     }
-    if (kin != keys) {
-        TTC_CUDA(cudaMemcpyAsync(keys, kin, n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
-        TTC_CUDA(cudaMemcpyAsync(vals, vin, n * sizeof(V), cudaMemcpyDeviceToDevice, s));
+    return kin != keys;
+}
+
+template <typename V>
+void radix_sort_impl(uint64_t *keys, V *vals, size_t n, int begin_bit, int end_bit, cudaStream_t s) {
+    if (n <= 1 || end_bit <= begin_bit) return;
+    DevBuf<uint64_t> kalt(n, s);
+    DevBuf<V> valt(n, s);
+    if (radix_sort_passes<V>(keys, vals, kalt.get(), valt.get(), n, begin_bit, end_bit, s)) {
+        TTC_CUDA(cudaMemcpyAsync(keys, kalt.get(), n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+        TTC_CUDA(cudaMemcpyAsync(vals, valt.get(), n * sizeof(V), cudaMemcpyDeviceToDevice, s));
     }
 }
 
@@ -291,6 +301,14 @@ void radix_sort_u64_u64(uint64_t *keys, uint64_t *vals, size_t n, int bits, cuda
 void radix_sort_u64_u64_range(uint64_t *keys, uint64_t *vals, size_t n, int begin_bit, int end_bit,
                               cudaStream_t s) {
     radix_sort_impl<uint64_t>(keys, vals, n, begin_bit, end_bit, s);
+}
+bool radix_sort_passes_u32(uint64_t *keys, uint32_t *vals, uint64_t *kalt, uint32_t *valt, size_t n, int begin_bit,
+                           int end_bit, cudaStream_t s) {
+    return radix_sort_passes<uint32_t>(keys, vals, kalt, valt, n, begin_bit, end_bit, s);
+}
+bool radix_sort_passes_u64(uint64_t *keys, uint64_t *vals, uint64_t *kalt, uint64_t *valt, size_t n, int begin_bit,
+                           int end_bit, cudaStream_t s) {
+    return radix_sort_passes<uint64_t>(keys, vals, kalt, valt, n, begin_bit, end_bit, s);
 }
 void reduce_minmax_i64(const int64_t *in, size_t n, int64_t *dmin, int64_t *dmax, cudaStream_t s) {
     init_minmax_kernel<<<1, 1, 0, s>>>((long long *)dmin, (long long *)dmax);
