@@ -1203,12 +1203,14 @@ struct RecCtx {
 // in bit 31, whether id(a) > id(b).
 constexpr uint32_t SIG_MASK = 0x7fffffffu;
 
+// ocsr[i] = (target rank, sigma word, pair id, 0) of oriented edge i, so one
+// 16-byte load gives the enumeration everything it needs about an edge.
 __global__ void osig_kernel(const uint32_t *opair, const uint32_t *osrc, const uint32_t *onbr, const uint32_t *id_of,
-                            const uint32_t *poff, size_t ms, uint32_t *osig) {
+                            const uint32_t *poff, size_t ms, uint4 *ocsr) {
     GRID_STRIDE(i, ms) {
-        const uint32_t p = opair[i], sig = poff[p + 1] - poff[p];
-        const uint32_t down = id_of[osrc[i]] > id_of[onbr[i]] ? 0x80000000u : 0u;
-        osig[i] = (sig < SIG_MASK ? sig : SIG_MASK) | down;
+        const uint32_t p = opair[i], sig = poff[p + 1] - poff[p], b = onbr[i];
+        const uint32_t down = id_of[osrc[i]] > id_of[b] ? 0x80000000u : 0u;
+        ocsr[i] = make_uint4(b, (sig < SIG_MASK ? sig : SIG_MASK) | down, p, 0u);
     }
 }
 
@@ -1218,7 +1220,8 @@ __global__ void osig_kernel(const uint32_t *opair, const uint32_t *osrc, const u
 // The flip bits say, per record pair, whether the labelled direction runs
 // from the larger id to the smaller.
 __device__ __forceinline__ uint4 make_record(const RecCtx &c, uint32_t s_uv, uint32_t s_uw, uint32_t s_vw,
-                                             uint32_t p_uv, uint32_t p_uw, uint32_t p_vw, bool *heavy) {
+                                             uint32_t p_uv, uint32_t p_uw, uint32_t p_vw, bool *heavy,
+                                             uint32_t *n_a = nullptr, uint32_t *n_b = nullptr) {
     const uint32_t n_uv = s_uv & SIG_MASK, n_uw = s_uw & SIG_MASK, n_vw = s_vw & SIG_MASK;
     const bool g_uv = s_uv >> 31, g_uw = s_uw >> 31, g_vw = s_vw >> 31;  // id(u0) > id(v0), ...
     uint32_t A = p_uv, B = p_uw, C = p_vw, nA = n_uv, nB = n_uw;
@@ -1233,11 +1236,22 @@ __device__ __forceinline__ uint4 make_record(const RecCtx &c, uint32_t s_uv, uin
         }
     }
     *heavy = (uint64_t)nA * nB >= c.light_max;
+    if (n_a) *n_a = nA;
+    if (n_b) *n_b = nB;
     const uint32_t flags = (fa ? TriRec::FLIP_A : 0u) | (fb ? TriRec::FLIP_B : 0u) | (fc ? TriRec::FLIP_C : 0u);
     return make_uint4(A, B, C, flags);
 }
 
-// sizes of heavy records and the work statistics of all records
+// enumerated edges (sigma_A + sigma_B) of each heavy record
+__global__ void heavy_sizes_kernel(const uint4 *rec, size_t nh, const uint32_t *poff, uint64_t *heavy_e) {
+    GRID_STRIDE(i, nh) {
+        const uint4 r = rec[i];
+        heavy_e[i] = (uint64_t)(poff[r.x + 1] - poff[r.x]) + (poff[r.y + 1] - poff[r.y]);
+    }
+}
+
+// sizes of heavy records and the work statistics of all records, from the
+// records themselves (used when the enumeration's sigma words were capped)
 __global__ void record_stats_kernel(const uint4 *rec, size_t tau, uint64_t n_light, const uint32_t *poff,
                                     uint64_t *heavy_e, unsigned long long *sums) {
     unsigned long long w = 0, en = 0, wh = 0, lp = 0;
@@ -1309,8 +1323,7 @@ __global__ void tri_items_fill_kernel(const uint32_t *item_pre, uint32_t n, uint
 
 struct TriCsr {
     const uint32_t *onbr;     // out-lists: target ranks, sorted
-    const uint32_t *opair;    // pair id of each oriented edge
-    const uint32_t *osig;     // packed (σ, id order) word of each oriented edge
+    const uint4 *ocsr;        // per oriented edge: target rank, (σ, id order) word, pair id
     const uint32_t *out_off;  // out-list offsets by rank
     const uint32_t *osrc;     // source rank of each oriented edge
     const uint32_t *in_off;   // in-list offsets by rank
@@ -1323,7 +1336,11 @@ constexpr size_t tri_warp_smem() { return (size_t)TRI_NV_CAP * 4 * 3; }
 
 __global__ void __launch_bounds__(TRI_THREADS)
     tri_enum_kernel(const uint2 *__restrict__ items, uint32_t nitems, TriCsr g, RecCtx rc, uint32_t *cnt_light,
-                    uint32_t *cnt_heavy, const uint64_t *resv, uint4 *sparse) {
+                    uint32_t *cnt_heavy, const uint64_t *resv, uint4 *sparse, unsigned long long *sums) {
+    // work statistics of the records written: sum of 8 (s_A + s_B + s_C) + 12,
+    // of s_A + s_B, the first over heavy records, of s_A s_B over light
+    // ones, and whether a sigma word was capped
+    unsigned long long st_w = 0, st_en = 0, st_wh = 0, st_lp = 0, st_cap = 0;
     extern __shared__ uint32_t tri_smem[];
     __shared__ uint32_t s_excl[TRI_WARPS][33];
     __shared__ uint32_t s_e[TRI_WARPS][32], s_se[TRI_WARPS][32], s_pe[TRI_WARPS][32];
@@ -1342,24 +1359,24 @@ __global__ void __launch_bounds__(TRI_THREADS)
         if (staged && staged_v != v) {
             __syncwarp();
             for (uint32_t i = lane; i < dv; i += 32) {
-                s_nv[i] = __ldg(g.onbr + vb + i);
-                s_nvs[i] = __ldg(g.osig + vb + i);
-                s_nvp[i] = __ldg(g.opair + vb + i);
+                const uint4 q = __ldg(g.ocsr + vb + i);
+                s_nv[i] = q.x;
+                s_nvs[i] = q.y;
+                s_nvp[i] = q.z;
             }
             staged_v = v;
         }
         __syncwarp();
         const uint32_t *nv = staged ? s_nv : g.onbr + vb;
-        const uint32_t *nvs = staged ? s_nvs : g.osig + vb;
-        const uint32_t *nvp = staged ? s_nvp : g.opair + vb;
         const uint32_t ib = __ldg(g.in_off + v), din = __ldg(g.in_off + v + 1) - ib;
         const uint32_t i = c0 + lane;
         uint32_t len = 0;
         if (i < din) {
             const uint32_t e = __ldg(g.in_e + ib + i), u = __ldg(g.osrc + e);
+            const uint4 q = __ldg(g.ocsr + e);
             s_e[w][lane] = e;
-            s_se[w][lane] = __ldg(g.osig + e);
-            s_pe[w][lane] = __ldg(g.opair + e);
+            s_se[w][lane] = q.y;
+            s_pe[w][lane] = q.z;
             len = __ldg(g.out_off + u + 1) - e - 1;  // the suffix of N+(u) after v
             s_lo[w][lane] = resv[e];
             s_ho[w][lane] = resv[e] + len - 1;
@@ -1381,7 +1398,8 @@ __global__ void __launch_bounds__(TRI_THREADS)
         const uint32_t top = dv ? 1u << (31 - __clz(dv)) : 0u;  // largest power of two <= dv
         for (uint32_t base = 0; base < total; base += 64) {
             uint32_t jj[2] = {base + lane, base + 32 + lane};
-            uint32_t o[2] = {0, 0}, ew[2] = {0, 0}, x3[2] = {0, 0}, lo[2] = {0, 0};
+            uint32_t o[2] = {0, 0}, lo[2] = {0, 0};
+            uint4 qw[2] = {make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};  // the edge u -> w
             bool in[2];
 #pragma unroll
             for (int h = 0; h < 2; h++) {
@@ -1390,10 +1408,10 @@ __global__ void __launch_bounds__(TRI_THREADS)
 #pragma unroll
                     for (uint32_t step = 16; step; step >>= 1)
                         if (s_excl[w][o[h] + step] <= jj[h]) o[h] += step;
-                    ew[h] = s_e[w][o[h]] + 1 + (jj[h] - s_excl[w][o[h]]);  // u -> w
-                    x3[h] = __ldg(g.onbr + ew[h]);
+                    qw[h] = __ldg(g.ocsr + s_e[w][o[h]] + 1 + (jj[h] - s_excl[w][o[h]]));
                 }
             }
+            const uint32_t x3[2] = {qw[0].x, qw[1].x};
             // lower bound of x3 in N+(v), branch-free, both searches in step
             for (uint32_t step = top; step; step >>= 1) {
 #pragma unroll
@@ -1406,8 +1424,24 @@ __global__ void __launch_bounds__(TRI_THREADS)
                 uint4 r = make_uint4(0, 0, 0, 0);
                 if (in[h] && lo[h] < dv && nv[lo[h]] == x3[h]) {
                     hit = true;
-                    r = make_record(rc, s_se[w][o[h]], __ldg(g.osig + ew[h]), nvs[lo[h]], s_pe[w][o[h]],
-                                    __ldg(g.opair + ew[h]), nvp[lo[h]], &heavy);
+                    uint32_t s_vw, p_vw;  // the edge v -> w
+                    if (staged) {
+                        s_vw = s_nvs[lo[h]];
+                        p_vw = s_nvp[lo[h]];
+                    } else {
+                        const uint4 q = __ldg(g.ocsr + vb + lo[h]);
+                        s_vw = q.y;
+                        p_vw = q.z;
+                    }
+                    uint32_t na, nb;
+                    r = make_record(rc, s_se[w][o[h]], qw[h].y, s_vw, s_pe[w][o[h]], qw[h].z, p_vw, &heavy, &na,
+                                    &nb);
+                    const uint32_t s1 = s_se[w][o[h]] & SIG_MASK, s2 = qw[h].y & SIG_MASK, s3 = s_vw & SIG_MASK;
+                    const unsigned long long wb = 8ull * ((unsigned long long)s1 + s2 + s3) + 12;
+                    st_w += wb;
+                    st_en += (unsigned long long)na + nb;
+                    if (heavy) st_wh += wb; else st_lp += (unsigned long long)na * nb;
+                    st_cap |= (s1 == SIG_MASK || s2 == SIG_MASK || s3 == SIG_MASK) ? 1ull : 0ull;
                 }
                 const unsigned act = __ballot_sync(0xffffffffu, hit);
                 if (!act) continue;
@@ -1428,6 +1462,21 @@ __global__ void __launch_bounds__(TRI_THREADS)
             cnt_heavy[s_e[w][lane]] = s_run[w][2 * lane + 1];
         }
         __syncwarp();
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        st_w += __shfl_xor_sync(0xffffffffu, st_w, o);
+        st_en += __shfl_xor_sync(0xffffffffu, st_en, o);
+        st_wh += __shfl_xor_sync(0xffffffffu, st_wh, o);
+        st_lp += __shfl_xor_sync(0xffffffffu, st_lp, o);
+        st_cap |= __shfl_xor_sync(0xffffffffu, st_cap, o);
+    }
+    if (lane == 0 && st_w) {
+        atomicAdd(sums, st_w);
+        atomicAdd(sums + 1, st_en);
+        atomicAdd(sums + 2, st_wh);
+        atomicAdd(sums + 3, st_lp);
+        if (st_cap) atomicOr(sums + 4, 1ull);
     }
 }
 
@@ -1978,12 +2027,13 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
     prof_begin(g, s, "load:enumerate");
     // ---- a6: triangles, written straight into the light and heavy bins
     const RecCtx rc{g->labeling, g->light_max_pairs};
-    DevBuf<uint32_t> osig(ms, s);
+    DevBuf<uint4> ocsr(ms, s);
     osig_kernel<<<grid_for(ms), TPB, 0, s>>>(opair.get(), osrc.get(), onbr.get(), id_of.get(), g->poff.get(), ms,
-                                             osig.get());
+                                             ocsr.get());
     TTC_LAUNCH_CHECK();
     id_of.reset();
-    const TriCsr tc{onbr.get(), opair.get(), osig.get(), out_off.get(), osrc.get(), in_off.get(), in_e.get()};
+    opair.reset();
+    const TriCsr tc{onbr.get(), ocsr.get(), out_off.get(), osrc.get(), in_off.get(), in_e.get()};
     // work items: (target v, 32 of its in-edges)
     DevBuf<uint32_t> nit(n, s), it_pre(n + 1, s);
     tri_items_count_kernel<<<grid_for(n), TPB, 0, s>>>(out_off.get(), in_off.get(), (uint32_t)n, nit.get());
@@ -2012,8 +2062,10 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
     DevBuf<uint64_t> loff(ms + 1, s), hoff(ms + 1, s), cl64(ms + 1, s), ch64(ms + 1, s);
     TTC_CUDA(cudaMemsetAsync(cl.get(), 0, (ms + 1) * 4, s));
     TTC_CUDA(cudaMemsetAsync(ch.get(), 0, (ms + 1) * 4, s));
+    DevBuf<unsigned long long> ws(5, s);
+    TTC_CUDA(cudaMemsetAsync(ws.get(), 0, 40, s));
     tri_enum_kernel<<<grid_t, TRI_THREADS, smem_t, s>>>(items.get(), nitems, tc, rc, cl.get(), ch.get(), resv.get(),
-                                                       sparse.get());
+                                                       sparse.get(), ws.get());
     TTC_LAUNCH_CHECK();
     widen_kernel<<<grid_for(ms), TPB, 0, s>>>(cl.get(), ch.get(), ms, cl64.get(), ch64.get());
     TTC_LAUNCH_CHECK();
@@ -2035,7 +2087,7 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
     }
     sparse.reset(); resv.reset();
     cl.reset(); ch.reset(); loff.reset(); hoff.reset(); cl64.reset(); ch64.reset();
-    osrc.reset(); onbr.reset(); opair.reset(); osig.reset(); out_off.reset(); in_off.reset(); in_e.reset();
+    osrc.reset(); onbr.reset(); ocsr.reset(); out_off.reset(); in_off.reset(); in_e.reset();
     st.tau_light = n_light;
     st.tau_heavy = tau - n_light;
 
@@ -2044,16 +2096,22 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
     // ---- statistics and heavy-path offsets
     const uint64_t nh = st.tau_heavy;
     DevBuf<uint64_t> he(nh ? nh : 1, s);
-    DevBuf<unsigned long long> ws(4, s);
-    TTC_CUDA(cudaMemsetAsync(ws.get(), 0, 32, s));
-    if (tau) {
+    // the statistics were summed by the enumeration from the sigma words;
+    // if one was capped they are taken again from the records
+    unsigned long long hws[5];
+    TTC_CUDA(cudaMemcpyAsync(hws, ws.get(), 40, cudaMemcpyDeviceToHost, s));
+    TTC_CUDA(cudaStreamSynchronize(s));
+    if (hws[4]) {
+        TTC_CUDA(cudaMemsetAsync(ws.get(), 0, 32, s));
         record_stats_kernel<<<grid_for(tau), TPB, 0, s>>>(g->tri.get(), tau, n_light, g->poff.get(), he.get(),
                                                           ws.get());
         TTC_LAUNCH_CHECK();
+        TTC_CUDA(cudaMemcpyAsync(hws, ws.get(), 32, cudaMemcpyDeviceToHost, s));
+        TTC_CUDA(cudaStreamSynchronize(s));
+    } else if (nh) {
+        heavy_sizes_kernel<<<grid_for(nh), TPB, 0, s>>>(g->tri.get() + n_light, nh, g->poff.get(), he.get());
+        TTC_LAUNCH_CHECK();
     }
-    unsigned long long hws[4];
-    TTC_CUDA(cudaMemcpyAsync(hws, ws.get(), 32, cudaMemcpyDeviceToHost, s));
-    TTC_CUDA(cudaStreamSynchronize(s));
     st.work_bytes = hws[0];
     st.enum_elems = hws[1];
     st.work_bytes_heavy = hws[2];

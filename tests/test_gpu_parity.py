@@ -289,6 +289,33 @@ def test_peel_stages_match_level_synchronous_reference():
     g.free()
 
 
+def _enumerated_stats(s, d, light_max=65):
+    """Over the static triangles (plain adjacency sets): the number of
+    triangles, the sum of the two smaller multiplicities (the enumerated
+    lists when the heaviest pair is only searched) and, over triangles whose
+    two smaller multiplicities multiply to less than light_max, the sum of
+    that product (the pairs the light path visits)."""
+    keep = s != d
+    a = np.minimum(s[keep], d[keep]).astype(np.int64)
+    b = np.maximum(s[keep], d[keep]).astype(np.int64)
+    key, cnt = np.unique(a * (1 << 32) + b, return_counts=True)
+    sig = {(int(k >> 32), int(k & 0xFFFFFFFF)): int(c) for k, c in zip(key, cnt)}
+    adj = {}
+    for x, y in sig:
+        adj.setdefault(x, set()).add(y)
+        adj.setdefault(y, set()).add(x)
+    tau = en = lp = 0
+    for (x, y), sxy in sig.items():
+        for z in adj[x] & adj[y]:
+            if z > y:
+                lo = sorted([sxy, sig[(x, z)], sig[(y, z)]])
+                tau += 1
+                en += lo[0] + lo[1]
+                if lo[0] * lo[1] < light_max:
+                    lp += lo[0] * lo[1]
+    return tau, en, lp
+
+
 def test_graph_stats_match_oracle():
     s, d, t = synth.large_plain(scale=0.003)
     st = oracle.stats(s, d, t)
@@ -298,6 +325,7 @@ def test_graph_stats_match_oracle():
     for key in ("m", "m_s", "tau", "sigma_max", "work_bytes"):
         assert info[key] == st[key], key
     assert info["tau_light"] + info["tau_heavy"] == info["tau"]
+    assert (info["tau"], info["enum_elems"], info["light_pairs"]) == _enumerated_stats(s, d)
 
 
 def test_device_input_tensors():
