@@ -52,9 +52,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
     cc = nvcc()
     defs = ["-DTTC_COUNT_HASH=\"%s\"" % count_source_hash()]
 
+    # the object that embeds the count hash is rebuilt whenever the hash changes
+    stamp = os.path.join(OUT, "count_hash.txt")
+    old_hash = open(stamp).read().strip() if os.path.exists(stamp) else ""
+
     def compile_one(src):
         obj = os.path.join(OUT, os.path.basename(src) + ".o")
-        if (not force and os.path.exists(obj)
+        stale_hash = os.path.basename(src) == "capi.cu" and old_hash != count_source_hash()
+        if (not force and not stale_hash and os.path.exists(obj)
                 and os.path.getmtime(obj) >= max(os.path.getmtime(src), hdr_t)):
             return obj, False
         cmd = [cc, *ARCH, *FLAGS, *defs, "-c", src, "-o", obj + ".tmp"]
@@ -70,6 +75,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 4))) as ex:
         results = list(ex.map(compile_one, srcs))
+    with open(stamp, "w") as fh:
+        fh.write(count_source_hash())
     objs = [o for o, _ in results]
     changed = any(c for _, c in results)
     if force or changed or not os.path.exists(LIB):

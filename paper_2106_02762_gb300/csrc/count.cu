@@ -322,6 +322,20 @@ struct CView {
 template <typename Acc>
 __device__ __forceinline__ void light_pair(const CView &C, const KeyFmt &f, const Query &q, bool xa, int64_t rx,
                                            int64_t ry, uint32_t code, Acc &&acc) {
+    if (q.d12 >= f.span && q.d23 >= f.span) {
+        // every window covers the graph's whole time span (then so does d13
+        // >= d12): C's edges after y, between x and y, and before x make the
+        // three cases whole
+        auto add_raw = [&](uint32_t pack, uint32_t len, uint32_t s) {  // s: raw dir-0 count of the range
+            const uint32_t n0 = C.flip ? len - s : s;
+            acc(type_in(pack, code), n0);
+            acc(type_in(pack, code | 1u), len - n0);
+        };
+        if (C.n > C.py) add_raw(xa ? TP1 : TP2, C.n - C.py, C.fn - C.fy);
+        if (C.py > C.px) add_raw(xa ? TP3 : TP4, C.py - C.px, C.fy - C.fx);
+        if (C.px > 0) add_raw(xa ? TP5 : TP6, C.px, C.fx - C.f0);
+        return;
+    }
     const int64_t gap = ry - rx;
     auto add = [&](uint32_t pack, uint32_t lo, uint32_t hi) {
         const uint32_t n0 = C.d0_range(lo, hi);

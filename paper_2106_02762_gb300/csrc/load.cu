@@ -844,7 +844,7 @@ __global__ void __launch_bounds__(256)
 // read by every CTA between the barriers that end round r and r + 1 and is
 // zeroed in round r + 2.  Continues from level ctl->k and round ctl->rounds;
 // writes level[] of the core vertices and the final rounds and kappa.
-constexpr int CORE_THREADS = 256;       // per CTA of the cluster: rounds are small, few idle warps
+constexpr int CORE_THREADS = 1024;      // per CTA of the cluster (measured: more threads per round beat fewer idle warps)
 constexpr int CORE_TAIL_THREADS = 1024;  // the one-CTA run of the last PEEL_TAIL vertices
 constexpr uint32_t PEEL_TAIL = 8192;     // the cluster hands the last this many to one CTA
 constexpr int CORE_RUN = 4;          // relaxed edges per thread per step
