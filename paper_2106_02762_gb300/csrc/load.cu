@@ -44,6 +44,8 @@ struct IngestStats {
     unsigned int max_id;
     unsigned int bad_id;
     unsigned int bad_t;
+    unsigned int pad;
+    long long tmin, tmax;  // over the kept edges
 };
 
 __global__ void ingest_check_kernel(const uint32_t *src, const uint32_t *dst, const int64_t *t, size_t m,
@@ -51,11 +53,16 @@ __global__ void ingest_check_kernel(const uint32_t *src, const uint32_t *dst, co
     const int64_t TLIM = (int64_t)1 << 62;
     unsigned int my_max = 0, bad_id = 0, bad_t = 0;
     unsigned long long loops = 0;
+    long long lo = LLONG_MAX, hi = LLONG_MIN;
     GRID_STRIDE(i, m) {
         const uint32_t a = src[i], b = dst[i];
         const int64_t tt = t[i];
         keep[i] = a != b;
         loops += a == b;
+        if (a != b) {
+            lo = min(lo, (long long)tt);
+            hi = max(hi, (long long)tt);
+        }
         my_max = max(my_max, max(a, b));
         bad_id |= (a >> 31) | (b >> 31);
         bad_t |= (tt < -TLIM) | (tt > TLIM);
@@ -65,12 +72,16 @@ __global__ void ingest_check_kernel(const uint32_t *src, const uint32_t *dst, co
         bad_id |= __shfl_xor_sync(0xffffffffu, bad_id, o);
         bad_t |= __shfl_xor_sync(0xffffffffu, bad_t, o);
         loops += __shfl_xor_sync(0xffffffffu, loops, o);
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
     }
     if ((threadIdx.x & 31) == 0) {
         atomicMax(&st->max_id, my_max);
         if (bad_id) atomicOr(&st->bad_id, 1u);
         if (bad_t) atomicOr(&st->bad_t, 1u);
         if (loops) atomicAdd(&st->loops, loops);
+        if (lo != LLONG_MAX) atomicMin(&st->tmin, lo);
+        if (hi != LLONG_MIN) atomicMax(&st->tmax, hi);
     }
 }
 
@@ -94,12 +105,13 @@ __global__ void time_key_kernel(int64_t *tk, size_t m, int64_t tmin, uint64_t *t
 }
 
 // Packed key with the kept-edge index as tie-break (used when it fits in 63
-// bits), and the pair key lo * n + hi as the value to carry.
+// bits), and the pair key lo * n + hi as the value to carry.  eidx == nullptr:
+// every input edge was kept (no self-loops), kept index = input index.
 __global__ void key_direct_kernel(const uint32_t *eidx, const int64_t *tk, size_t m, int64_t tmin, int shift,
                                   const uint32_t *src, const uint32_t *dst, uint64_t n, uint64_t *key,
                                   uint64_t *pkey) {
     GRID_STRIDE(i, m) {
-        const uint32_t e = eidx[i];
+        const uint32_t e = eidx ? eidx[i] : (uint32_t)i;
         const uint32_t a = src[e], b = dst[e];
         key[i] = ((uint64_t)(tk[i] - tmin) << shift) | ((uint64_t)i << 1) | (uint64_t)(a > b);
         pkey[i] = (uint64_t)min(a, b) * n + max(a, b);
@@ -1730,7 +1742,12 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
         src = src_buf.get(); dst = dst_buf.get(); t = t_buf.get();
     }
     DevBuf<IngestStats> ist(1, s);
-    TTC_CUDA(cudaMemsetAsync(ist.get(), 0, sizeof(IngestStats), s));
+    {
+        IngestStats init{};
+        init.tmin = LLONG_MAX;
+        init.tmax = LLONG_MIN;
+        TTC_CUDA(cudaMemcpyAsync(ist.get(), &init, sizeof(init), cudaMemcpyHostToDevice, s));
+    }
     DevBuf<uint8_t> keep(m0 + 1, s);
     if (m0) {
         ingest_check_kernel<<<grid_for(m0), TPB, 0, s>>>(src, dst, t, m0, keep.get(), ist.get());
@@ -1754,24 +1771,28 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
         return;
     }
 
-    // kept edges, input order
-    DevBuf<uint32_t> eidx(m, s);
-    DevBuf<int64_t> tk(m, s);
-    {
+    g->tmin = is.tmin;
+    g->span = is.tmax - is.tmin;
+    const int span_bits = bits_for((uint64_t)g->span);
+    const int ib = bits_for(m - 1);
+    const bool direct = span_bits + ib + 1 <= 63;
+    // kept edges in input order (index, time): with no self-loops and the
+    // direct key they are the inputs themselves
+    DevBuf<uint32_t> eidx;
+    DevBuf<int64_t> tk;
+    const uint32_t *eidx_p = nullptr;
+    const int64_t *tk_p = t;
+    if (is.loops || !direct) {
+        eidx.alloc(m, s);
+        tk.alloc(m, s);
         DevBuf<uint32_t> pos(m0 + 1, s);
         exclusive_scan_flags(keep.get(), pos.get(), m0, s);
         compact_kernel<<<grid_for(m0), TPB, 0, s>>>(keep.get(), pos.get(), m0, t, eidx.get(), tk.get());
         TTC_LAUNCH_CHECK();
+        eidx_p = eidx.get();
+        tk_p = tk.get();
     }
     keep.reset();
-    DevBuf<int64_t> mm(2, s);
-    reduce_minmax_i64(tk.get(), m, mm.get(), mm.get() + 1, s);
-    int64_t hmm[2];
-    TTC_CUDA(cudaMemcpyAsync(hmm, mm.get(), 16, cudaMemcpyDeviceToHost, s));
-    TTC_CUDA(cudaStreamSynchronize(s));
-    g->tmin = hmm[0];
-    g->span = hmm[1] - hmm[0];
-    const int span_bits = bits_for((uint64_t)g->span);
 
     prof_end(g, s);
     prof_begin(g, s, "load:keys_pair_sort");
@@ -1779,12 +1800,11 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
     // key-sorted inside each pair by two stable sorts: time, then pair
     if (n * n > (uint64_t(1) << 63)) fail(TTC_ERR_RANGE, "vertex ids too large for the pair key");
     DevBuf<uint64_t> pkey(m, s);
-    const int ib = bits_for(m - 1);
     bool seg_sort_after = false;
-    if (span_bits + ib + 1 <= 63) {
+    if (direct) {
         // ties broken by the kept-edge index itself (input order)
         g->shift = ib + 1;
-        key_direct_kernel<<<grid_for(m), TPB, 0, s>>>(eidx.get(), tk.get(), m, g->tmin, g->shift, src, dst, n,
+        key_direct_kernel<<<grid_for(m), TPB, 0, s>>>(eidx_p, tk_p, m, g->tmin, g->shift, src, dst, n,
                                                       reinterpret_cast<uint64_t *>(g->key.get()), pkey.get());
         TTC_LAUNCH_CHECK();
         tk.reset(); eidx.reset();

@@ -4,6 +4,7 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <cstring>
 
 #include "common.cuh"
 #include "sort.cuh"
@@ -60,25 +61,76 @@ __global__ void __launch_bounds__(SCAN_THREADS) tile_sums_kernel(const In *in, s
     if (threadIdx.x == 0) sums[blockIdx.x] = total;
 }
 
-template <typename T, typename In>
+// SCAN_ITEMS consecutive items of one thread as whole 16-byte (or 8-byte)
+// words, for tiles that lie wholly inside the array.
+template <typename X>
+__device__ __forceinline__ void load_items(const X *p, X (&v)[SCAN_ITEMS]) {
+    constexpr int B = (int)sizeof(X) * SCAN_ITEMS;
+    static_assert(B % 8 == 0, "item group of whole 8-byte words");
+    if constexpr (B % 16 == 0) {
+        uint4 w[B / 16];
+#pragma unroll
+        for (int i = 0; i < B / 16; i++) w[i] = reinterpret_cast<const uint4 *>(p)[i];
+        memcpy(v, w, B);
+    } else {
+        uint2 w[B / 8];
+#pragma unroll
+        for (int i = 0; i < B / 8; i++) w[i] = reinterpret_cast<const uint2 *>(p)[i];
+        memcpy(v, w, B);
+    }
+}
+template <typename X>
+__device__ __forceinline__ void store_items(X *p, const X (&v)[SCAN_ITEMS]) {
+    constexpr int B = (int)sizeof(X) * SCAN_ITEMS;
+    static_assert(B % 16 == 0, "item group of whole 16-byte words");
+    uint4 w[B / 16];
+    memcpy(w, v, B);
+#pragma unroll
+    for (int i = 0; i < B / 16; i++) reinterpret_cast<uint4 *>(p)[i] = w[i];
+}
+
+// VEC: in and out are aligned to a thread's item group (SCAN_ITEMS items),
+// so full tiles move as whole words.
+template <typename T, typename In, bool VEC>
 __global__ void __launch_bounds__(SCAN_THREADS)
     tile_scan_kernel(const In *in, T *out, size_t n, const T *tile_off) {
     const size_t base = (size_t)blockIdx.x * SCAN_TILE + (size_t)threadIdx.x * SCAN_ITEMS;
+    const bool full = VEC && (size_t)(blockIdx.x + 1) * SCAN_TILE <= n;  // block-uniform
     T v[SCAN_ITEMS];
     T s = 0;
+    if (full) {
+        In x[SCAN_ITEMS];
+        load_items<In>(in + base, x);
 #pragma unroll
-    for (int i = 0; i < SCAN_ITEMS; i++) {
-        const size_t idx = base + i;
-        v[i] = idx < n ? (T)in[idx] : T(0);
-        s += v[i];
+        for (int i = 0; i < SCAN_ITEMS; i++) {
+            v[i] = (T)x[i];
+            s += v[i];
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < SCAN_ITEMS; i++) {
+            const size_t idx = base + i;
+            v[i] = idx < n ? (T)in[idx] : T(0);
+            s += v[i];
+        }
     }
     T total;
     T run = block_exclusive_scan<T>(s, &total) + (tile_off ? tile_off[blockIdx.x] : T(0));
+    if (full) {
+        T o[SCAN_ITEMS];
 #pragma unroll
-    for (int i = 0; i < SCAN_ITEMS; i++) {
-        const size_t idx = base + i;
-        if (idx < n) out[idx] = run;
-        run += v[i];
+        for (int i = 0; i < SCAN_ITEMS; i++) {
+            o[i] = run;
+            run += v[i];
+        }
+        store_items<T>(out + base, o);
+    } else {
+#pragma unroll
+        for (int i = 0; i < SCAN_ITEMS; i++) {
+            const size_t idx = base + i;
+            if (idx < n) out[idx] = run;
+            run += v[i];
+        }
     }
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == SCAN_THREADS - 1) out[n] = run;
 }
@@ -87,7 +139,7 @@ template <typename T, typename In>
 void exclusive_scan_impl(const In *in, T *out, size_t n, cudaStream_t s) {
     const unsigned tiles = n ? ceil_div(n, SCAN_TILE) : 1;
     if (tiles == 1) {
-        tile_scan_kernel<T, In><<<1, SCAN_THREADS, 0, s>>>(in, out, n, nullptr);
+        tile_scan_kernel<T, In, false><<<1, SCAN_THREADS, 0, s>>>(in, out, n, nullptr);
         TTC_LAUNCH_CHECK();
         return;
     }
@@ -95,7 +147,10 @@ void exclusive_scan_impl(const In *in, T *out, size_t n, cudaStream_t s) {
     tile_sums_kernel<T, In><<<tiles, SCAN_THREADS, 0, s>>>(in, n, sums.get());
     TTC_LAUNCH_CHECK();
     exclusive_scan_impl<T, T>(sums.get(), offs.get(), tiles, s);
-    tile_scan_kernel<T, In><<<tiles, SCAN_THREADS, 0, s>>>(in, out, n, offs.get());
+    const bool vec = reinterpret_cast<uintptr_t>(in) % (sizeof(In) * SCAN_ITEMS) == 0 &&
+                     reinterpret_cast<uintptr_t>(out) % 16 == 0 && (sizeof(T) * SCAN_ITEMS) % 16 == 0;
+    if (vec) tile_scan_kernel<T, In, true><<<tiles, SCAN_THREADS, 0, s>>>(in, out, n, offs.get());
+    else tile_scan_kernel<T, In, false><<<tiles, SCAN_THREADS, 0, s>>>(in, out, n, offs.get());
     TTC_LAUNCH_CHECK();
 }
 
