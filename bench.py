@@ -596,7 +596,30 @@ def run_ours(args):
     batched_large = {"workload": name + ", 64 delta-triples log-spaced 60 s..30 d (d13), resident graph",
                      "batch_queries_per_s": len(sweep) / sw_b_s, "sequential_queries_per_s": len(sweep) / sw_q_s,
                      "speedup": sw_q_s / sw_b_s, "batch_ms": sw_b_s * 1e3, "sequential_ms": sw_q_s * 1e3}
+    listed_bytes = g.info()["device_bytes"]
     g.free()
+    # the same step with a streamed handle (no light-triangle list: each
+    # count enumerates again), device-timed
+    st_step, st_load = [], []
+    for i in range(4):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e2 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        gs = ttc.Graph(d_src, d_dst, d_t, stream=sptr, streamed=True)
+        e1.record(stream)
+        out_s = gs.count_batch(step_deltas)
+        e2.record(stream)
+        e2.synchronize()
+        assert (out_s == ref).all()
+        if i:
+            st_step.append(e0.elapsed_time(e2))
+            st_load.append(e0.elapsed_time(e1))
+        st_bytes = gs.info()["device_bytes"]
+        gs.free()
+    streamed = {"step_ms": statistics.median(st_step), "load_ms": statistics.median(st_load),
+                "device_bytes": st_bytes, "listed_device_bytes": listed_bytes,
+                "note": "TTC_LOAD_STREAM: the handle keeps the oriented graph instead of the light-triangle list"}
     q_s = statistics.median(q_times)
     kern_avg = {k: sum(v) / len(v) for k, v in kern.items()}
     # dominant count kernel and its algorithmic bytes (sum over its triangles
@@ -663,6 +686,7 @@ def run_ours(args):
             "roofline": roof,
             "batched": batched,
             "batched_large": batched_large,
+            "streamed": streamed,
             "e2e": e2e,
             "gpu_launches": int(launches),
             "wall_s_timed": wall,

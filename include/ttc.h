@@ -79,6 +79,19 @@ typedef enum {
 #define TTC_LOAD_DEVICE_INPUT 1u  /* src/dst/t are device pointers (same device) */
 #define TTC_LOAD_PROFILE 2u       /* time the load's phases (ttc_profile_read after
                                      the load; profiling stays on for counts) */
+#define TTC_LOAD_STREAM 4u        /* keep no list of light triangles: the handle keeps
+                                     the oriented graph instead (about 28 B per vertex
+                                     pair) and every count enumerates the triangles
+                                     again, counting light ones as they are found
+                                     (Alg. 1 with enumeration and counting fused);
+                                     heavy triangles are still listed.  For graphs
+                                     whose triangle list (16 B per triangle) does not
+                                     fit.  ttc_count and ttc_count_batch only: the
+                                     many-graph, sample and no-allocation entry points
+                                     refuse such a handle with TTC_ERR_INVALID.  A count
+                                     collects the light triangles chunk by chunk into a
+                                     buffer of TTC_STREAM_CHUNK records (environment,
+                                     read at load; default 2^24 = 256 MiB) */
 
 /* Vertex orderings used to orient the static graph.  Any acyclic orientation
  * gives identical counts; the degeneracy ordering (Sec. 3, Matula-Beck) bounds

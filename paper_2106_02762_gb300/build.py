@@ -34,12 +34,12 @@ def _headers():
 
 
 def count_source_hash() -> str:
-    """Short hash of the count kernels' source (csrc/count.cu and the shared
-    headers); profiles taken with ncu record it, so a stale profile can be
-    told from a current one."""
+    """Short hash of the count kernels' source (csrc/count.cu, csrc/count_dev.cuh
+    and the shared headers); profiles taken with ncu record it, so a stale
+    profile can be told from a current one."""
     import hashlib
     h = hashlib.sha1()
-    for f in ["count.cu", "graph.cuh", "common.cuh"]:
+    for f in ["count.cu", "count_dev.cuh", "graph.cuh", "common.cuh"]:
         with open(os.path.join(CSRC, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]

@@ -188,7 +188,8 @@ void count_multi(ttc_graph *const *gs, const ttc_delta *d, uint32_t G, uint64_t 
 uint64_t graph_device_bytes(const ttc_graph *g) {
     return g->key.bytes() + g->fwd.bytes() + g->poff.bytes() + g->pair_vtx.bytes() + g->tri.bytes() +
            g->huge_eoff.bytes() + g->view.bytes() + g->prefix.bytes() + g->acc.bytes() +
-           g->dq.bytes() + g->scratch.bytes();
+           g->dq.bytes() + g->scratch.bytes() + g->s_items.bytes() + g->s_ocsr.bytes() + g->s_onbr.bytes() +
+           g->s_osrc.bytes() + g->s_in_e.bytes() + g->s_out_off.bytes() + g->s_in_off.bytes();
 }
 }  // namespace ttc
 
@@ -206,6 +207,9 @@ void graph_destroy(ttc_graph *g) {
     g->key.reset(); g->fwd.reset(); g->poff.reset(); g->pair_vtx.reset(); g->tri.reset();
     g->huge_eoff.reset(); g->view.reset(); g->prefix.reset();
     g->acc.reset(); g->dq.reset(); g->scratch.reset();
+    g->s_items.reset(); g->s_ocsr.reset(); g->s_onbr.reset(); g->s_osrc.reset(); g->s_in_e.reset();
+    g->s_out_off.reset(); g->s_in_off.reset();
+    // every buffer is freed on the graph's stream, so before that stream goes
     if (s) cudaStreamSynchronize(s);
     if (g->own_stream && s) cudaStreamDestroy(s);
     delete g;
@@ -333,7 +337,7 @@ ttc_status ttc_load_ex(const uint32_t *src, const uint32_t *dst, const int64_t *
         lo.labeling = opts->labeling;
         lo.light_max_pairs = opts->light_max_pairs;
         lo.seed = opts->seed;
-        if (lo.flags & ~(TTC_LOAD_DEVICE_INPUT | TTC_LOAD_PROFILE))
+        if (lo.flags & ~(TTC_LOAD_DEVICE_INPUT | TTC_LOAD_PROFILE | TTC_LOAD_STREAM))
             fail(TTC_ERR_INVALID, "unknown load flags 0x%x", lo.flags);
     }
     g = new ttc_graph();
@@ -461,6 +465,11 @@ ttc_status ttc_count_multi(ttc_graph *const *g, const ttc_delta *d, uint32_t G, 
         set_last_error("NULL argument");
         return TTC_ERR_INVALID;
     }
+    for (uint32_t i = 0; i < G; i++)
+        if (g[i] && g[i]->streamed) {
+            set_last_error("a graph was loaded with TTC_LOAD_STREAM (no triangle list to share)");
+            return TTC_ERR_INVALID;
+        }
     TTC_API_BEGIN
     count_multi(g, d, G, out);
     return TTC_OK;
@@ -471,6 +480,10 @@ ttc_status ttc_count_sample(ttc_graph *g, const ttc_delta *d, uint64_t first, ui
                             uint32_t *tri, uint64_t *out, uint64_t *written) {
     if (!g || !d || !written || (cap && (!tri || !out)) || !stride) {
         set_last_error("NULL argument or zero stride");
+        return TTC_ERR_INVALID;
+    }
+    if (g->streamed) {
+        set_last_error("the graph was loaded with TTC_LOAD_STREAM: it keeps no triangle list to sample");
         return TTC_ERR_INVALID;
     }
     TTC_API_BEGIN

@@ -42,248 +42,11 @@
 #include <vector>
 
 #include "graph.cuh"
+#include "count_dev.cuh"
 
 namespace ttc {
 
 namespace {
-
-// Table 1 composed with Fig. 4, packed into one word per temporal ordering:
-// bits 3 code .. 3 code + 2 of type_pack(pi) hold the type index (T_(value + 1))
-// of psi(pi, rho(code)), where code = 4 dA + 2 dB + dC from the directions of
-// the three pairs, direction 0 being u->v, u->w, v->w.  The lookup is then
-// a shift of a compile-time word instead of a table load.
-constexpr uint32_t type_pack(int pi) {
-    // Table 1: psi(pi_k, rho_r); rows pi_1..pi_6, columns rho_1..rho_8
-    const uint8_t psi[6][8] = {
-        {6, 5, 4, 7, 2, 1, 3, 0},
-        {4, 2, 6, 3, 5, 0, 7, 1},
-        {2, 1, 0, 3, 6, 5, 7, 4},
-        {0, 6, 2, 7, 1, 4, 3, 5},
-        {5, 0, 1, 7, 4, 2, 3, 6},
-        {1, 4, 5, 3, 0, 6, 7, 2},
-    };
-    // Fig. 4: rho_1 = (0,0,0), rho_2 = (0,1,1), rho_3 = (0,0,1), rho_4 = (0,1,0),
-    // rho_5 = (1,0,0), rho_6 = (1,1,1), rho_7 = (1,0,1), rho_8 = (1,1,0) as (dA, dB, dC)
-    const uint8_t rho_of_code[8] = {0, 2, 3, 1, 4, 6, 7, 5};
-    uint32_t v = 0;
-    for (int code = 0; code < 8; code++) v |= uint32_t(psi[pi][rho_of_code[code]]) << (3 * code);
-    return v;
-}
-
-// Temporal orderings (Fig. 3), 0-based: pi_1 = A,B,C  pi_2 = B,A,C  pi_3 = A,C,B
-// pi_4 = B,C,A  pi_5 = C,A,B  pi_6 = C,B,A  (first, second, third pair).
-enum { PI1 = 0, PI2 = 1, PI3 = 2, PI4 = 3, PI5 = 4, PI6 = 5 };
-constexpr uint32_t TP1 = type_pack(PI1), TP2 = type_pack(PI2), TP3 = type_pack(PI3), TP4 = type_pack(PI4),
-                   TP5 = type_pack(PI5), TP6 = type_pack(PI6);
-// every row of Table 1 is a permutation of the eight types
-constexpr bool packs_types_once(uint32_t pack) {
-    uint32_t seen = 0;
-    for (int code = 0; code < 8; code++) seen |= 1u << ((pack >> (3 * code)) & 7u);
-    return seen == 0xffu;
-}
-static_assert(packs_types_once(TP1) && packs_types_once(TP2) && packs_types_once(TP3) && packs_types_once(TP4) &&
-                  packs_types_once(TP5) && packs_types_once(TP6),
-              "Table 1 rows are permutations");
-
-__device__ __forceinline__ uint32_t pack_of(int pi) {
-    return pi == PI1 ? TP1 : pi == PI2 ? TP2 : pi == PI3 ? TP3 : pi == PI4 ? TP4 : pi == PI5 ? TP5 : TP6;
-}
-__device__ __forceinline__ int type_in(uint32_t pack, uint32_t code) { return (int)((pack >> (3 * code)) & 7u); }
-__device__ __forceinline__ int type_of(int pi, uint32_t dA, uint32_t dB, uint32_t dC) {
-    return type_in(pack_of(pi), (dA << 2) | (dB << 1) | dC);
-}
-
-struct Query {
-    int64_t d13, d12, d23;
-};
-
-__device__ __forceinline__ Query load_query(const int64_t *dq, uint32_t q) {
-    return Query{dq[3 * q], dq[3 * q + 1], dq[3 * q + 2]};
-}
-
-// ---------------------------------------------------------------- lists
-// A pair's key-sorted edge list in device memory: key[b .. b + n), with the
-// direction split read from the global dir-0 prefix `fwd`.
-// number of keys < bound in the sorted p[0 .. n)
-__device__ __forceinline__ uint32_t search_below(const int64_t *__restrict__ p, uint32_t n, int64_t bound) {
-    uint32_t lo = 0, len = n;
-    while (len > 0) {
-        const uint32_t half = len >> 1;
-        if (__ldg(p + lo + half) < bound) {
-            lo += half + 1;
-            len -= half + 1;
-        } else {
-            len = half;
-        }
-    }
-    return lo;
-}
-
-struct GList {
-    const int64_t *__restrict__ key;
-    const uint32_t *__restrict__ fwd;
-    uint32_t b, n, flip;  // flip: effective direction = stored ^ 1
-    // number of keys < bound (bound >= 0)
-    __device__ __forceinline__ uint32_t below(int64_t bound) const { return search_below(key + b, n, bound); }
-    // effective direction-0 edges among the first pos
-    __device__ __forceinline__ uint32_t d0(uint32_t pos) const {
-        const uint32_t s0 = __ldg(fwd + b + pos) - __ldg(fwd + b);
-        return flip ? pos - s0 : s0;
-    }
-};
-
-// A list staged in shared memory: keys and an effective dir-0 prefix
-// (d0(i) = d0p[i] - base = direction-0 edges among the first i).
-struct SList {
-    const int64_t *key;
-    const uint32_t *d0p;
-    uint32_t n, base;
-    __device__ __forceinline__ uint32_t below(int64_t bound) const {
-        uint32_t lo = 0, len = n;
-        while (len > 0) {
-            const uint32_t half = len >> 1;
-            if (key[lo + half] < bound) {
-                lo += half + 1;
-                len -= half + 1;
-            } else {
-                len = half;
-            }
-        }
-        return lo;
-    }
-    __device__ __forceinline__ uint32_t d0(uint32_t pos) const { return d0p[pos] - base; }
-};
-
-// Packed-key format ((t - t_min) << shift | tie << 1 | dir) for time bounds.
-struct KeyFmt {
-    int shift;
-    int64_t span;
-};
-// #{e in L : key(e) < key(x)} for an edge x not in L
-template <typename L>
-__device__ __forceinline__ uint32_t cnt_key(const L &l, int64_t kx) {
-    return l.below(kx & ~int64_t(1));
-}
-// #{e in L : t(e) - t_min <= x}
-template <typename L>
-__device__ __forceinline__ uint32_t cnt_le(const L &l, const KeyFmt &f, int64_t x) {
-    if (x < 0) return 0;
-    if (x >= f.span) return l.n;
-    return l.below((x + 1) << f.shift);
-}
-// #{e in L : t(e) - t_min < x}
-template <typename L>
-__device__ __forceinline__ uint32_t cnt_lt(const L &l, const KeyFmt &f, int64_t x) {
-    return cnt_le(l, f, x - 1);
-}
-
-// Search bounds, as keys: #{e : key(e) < bound} gives cnt_key, cnt_le and
-// cnt_lt.  Every key is >= 0 and below INT64_MAX, so bound 0 counts nothing
-// and INT64_MAX counts the whole list.
-__device__ __forceinline__ int64_t key_bound(int64_t kx) { return kx & ~int64_t(1); }
-__device__ __forceinline__ int64_t le_bound(const KeyFmt &f, int64_t x) {
-    return x < 0 ? 0 : x >= f.span ? INT64_MAX : (x + 1) << f.shift;
-}
-__device__ __forceinline__ int64_t lt_bound(const KeyFmt &f, int64_t x) { return le_bound(f, x - 1); }
-
-// res[i] = #{keys < bound[i]} in a sorted list of n keys (at(i) reads key
-// i), for N bounds at once.  The halving steps depend only on n, so the N
-// searches advance in lockstep and their loads are in flight together.
-template <int N, typename AT>
-__device__ __forceinline__ void search_n(AT &&at, uint32_t n, const int64_t (&bound)[N], uint32_t (&res)[N]) {
-#pragma unroll
-    for (int i = 0; i < N; i++) res[i] = 0;
-    uint32_t len = n;  // each answer lies in [res[i], res[i] + len]
-    while (len > 1) {
-        const uint32_t half = len >> 1;
-        int64_t v[N];
-#pragma unroll
-        for (int i = 0; i < N; i++) v[i] = at(res[i] + half - 1);
-#pragma unroll
-        for (int i = 0; i < N; i++) res[i] += v[i] < bound[i] ? half : 0u;
-        len -= half;
-    }
-    if (len == 1) {
-        int64_t v[N];
-#pragma unroll
-        for (int i = 0; i < N; i++) v[i] = at(res[i]);
-#pragma unroll
-        for (int i = 0; i < N; i++) res[i] += v[i] < bound[i] ? 1u : 0u;
-    }
-}
-template <int N>
-__device__ __forceinline__ void search_n(const GList &l, const int64_t (&bound)[N], uint32_t (&res)[N]) {
-    const int64_t *p = l.key + l.b;
-    search_n<N>([&](uint32_t i) { return __ldg(p + i); }, l.n, bound, res);
-}
-template <int N>
-__device__ __forceinline__ void search_n(const SList &l, const int64_t (&bound)[N], uint32_t (&res)[N]) {
-    search_n<N>([&](uint32_t i) { return l.key[i]; }, l.n, bound, res);
-}
-
-__device__ __forceinline__ GList glist(const GraphView &gv, uint32_t p, uint32_t flip) {
-    const uint32_t b = __ldg(gv.poff + p);
-    return GList{gv.key, gv.fwd, b, __ldg(gv.poff + p + 1) - b, flip};
-}
-
-// ---------------------------------------------------------------- accumulation
-__device__ __forceinline__ void add_checked(unsigned long long &acc, unsigned long long x, unsigned &ovf) {
-    const unsigned long long r = acc + x;
-    ovf |= r < acc;
-    acc = r;
-}
-
-// Adds this warp's per-thread counters s_acc[type][tid] into out[0..8) with
-// one atomic per type, zeroes them, and raises *flag on any carry.  Every
-// lane of the warp must call it.
-__device__ __forceinline__ void warp_flush(unsigned long long (*s_acc)[256], unsigned long long *out,
-                                           unsigned long long *flag, unsigned &ovf) {
-    const uint32_t lane = threadIdx.x & 31;
-#pragma unroll
-    for (int t = 0; t < 8; t++) {
-        unsigned long long v = s_acc[t][threadIdx.x];
-        s_acc[t][threadIdx.x] = 0;
-#pragma unroll
-        for (int o = 16; o; o >>= 1) {
-            const unsigned long long y = __shfl_xor_sync(0xffffffffu, v, o);
-            add_checked(v, y, ovf);
-        }
-        if (lane == 0 && v) {
-            const unsigned long long old = atomicAdd(out + t, v);
-            ovf |= old + v < old;
-        }
-    }
-    if (__any_sync(0xffffffffu, ovf) && lane == 0) atomicOr(flag, 1ull);
-    ovf = 0;
-}
-
-// Block accumulators (several queries): shared atomics with carry checks.
-__device__ __forceinline__ void shared_add(unsigned long long *p, unsigned long long n, unsigned &ovf) {
-    const unsigned long long old = atomicAdd(p, n);
-    ovf |= old + n < old;
-}
-
-__device__ __forceinline__ void block_flush(const unsigned long long *s, uint32_t cnt, unsigned long long *out,
-                                            unsigned long long *flag, unsigned ovf) {
-    __syncthreads();
-    for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
-        if (s[i]) {
-            const unsigned long long old = atomicAdd(out + i, s[i]);
-            ovf |= old + s[i] < old;
-        }
-    }
-    if (ovf) atomicOr(flag, 1ull);
-}
-
-// Graph of a global work index, from an exclusive prefix over graphs.
-__device__ __forceinline__ uint32_t graph_of(const uint64_t *__restrict__ pre, uint32_t G, uint64_t i) {
-    uint32_t lo = 0, hi = G;  // last g with pre[g] <= i
-    while (hi - lo > 1) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (__ldg(pre + mid) <= i) lo = mid; else hi = mid;
-    }
-    return lo;
-}
 
 // ---------------------------------------------------------------- light bin
 constexpr int LIGHT_THREADS = 256;
@@ -295,67 +58,6 @@ constexpr int LIGHT_WARPS = LIGHT_THREADS / 32;
 // power-law workload: one record per lane is faster for single queries, two
 // for batches.)
 constexpr int LIGHT_BATCH_R = 2;
-
-// C's key-sorted list seen from one pair (x, y) of enumerated edges, x the
-// earlier: px, py = #{c : key(c) < key(x)}, #{c : key(c) < key(y)}, and the
-// raw dir-0 prefix fwd[b + pos] at pos = 0, px, py, n, the four positions
-// that bound every case of Lemma 1 once its window is unbounded.
-struct CView {
-    const int64_t *__restrict__ key;
-    const uint32_t *__restrict__ fwd;
-    uint32_t b, n, flip;
-    uint32_t px, py, f0, fx, fy, fn;
-    __device__ __forceinline__ uint32_t below(int64_t bound) const { return search_below(key + b, n, bound); }
-    __device__ __forceinline__ uint32_t raw(uint32_t pos) const {
-        return pos == px ? fx : pos == py ? fy : pos == n ? fn : pos == 0 ? f0 : __ldg(fwd + b + pos);
-    }
-    // effective direction-0 edges among C's positions [lo, hi)
-    __device__ __forceinline__ uint32_t d0_range(uint32_t lo, uint32_t hi) const {
-        const uint32_t s = raw(hi) - raw(lo);
-        return flip ? (hi - lo) - s : s;
-    }
-};
-
-// Adds the counts of one pair (x, y) of enumerated edges (x earlier, times
-// rx <= ry) for all three positions of C's edge.  xa: x is on A (else on B).
-// code = 4 dA + 2 dB (Fig. 4 with dC = 0).
-template <typename Acc>
-__device__ __forceinline__ void light_pair(const CView &C, const KeyFmt &f, const Query &q, bool xa, int64_t rx,
-                                           int64_t ry, uint32_t code, Acc &&acc) {
-    if (q.d12 >= f.span && q.d23 >= f.span) {
-        // every window covers the graph's whole time span (then so does d13
-        // >= d12): C's edges after y, between x and y, and before x make the
-        // three cases whole
-        auto add_raw = [&](uint32_t pack, uint32_t len, uint32_t s) {  // s: raw dir-0 count of the range
-            const uint32_t n0 = C.flip ? len - s : s;
-            acc(type_in(pack, code), n0);
-            acc(type_in(pack, code | 1u), len - n0);
-        };
-        if (C.n > C.py) add_raw(xa ? TP1 : TP2, C.n - C.py, C.fn - C.fy);
-        if (C.py > C.px) add_raw(xa ? TP3 : TP4, C.py - C.px, C.fy - C.fx);
-        if (C.px > 0) add_raw(xa ? TP5 : TP6, C.px, C.fx - C.f0);
-        return;
-    }
-    const int64_t gap = ry - rx;
-    auto add = [&](uint32_t pack, uint32_t lo, uint32_t hi) {
-        const uint32_t n0 = C.d0_range(lo, hi);
-        acc(type_in(pack, code), n0);
-        acc(type_in(pack, code | 1u), (hi - lo) - n0);
-    };
-    if (gap <= q.d12) {  // C third
-        const uint32_t hi = cnt_le(C, f, min(ry + q.d23, rx + q.d13));
-        if (hi > C.py) add(xa ? TP1 : TP2, C.py, hi);
-    }
-    if (gap <= q.d13) {  // C second
-        const uint32_t lo = max(C.px, cnt_lt(C, f, ry - q.d23));
-        const uint32_t hi = min(C.py, cnt_le(C, f, rx + q.d12));
-        if (hi > lo) add(xa ? TP3 : TP4, lo, hi);
-    }
-    if (gap <= q.d23) {  // C first
-        const uint32_t lo = cnt_lt(C, f, max(rx - q.d12, ry - q.d13));
-        if (C.px > lo) add(xa ? TP5 : TP6, lo, C.px);
-    }
-}
 
 template <int R>
 struct WarpTris {
@@ -516,55 +218,29 @@ __global__ void __launch_bounds__(LIGHT_THREADS, MODE == 1 ? 4 : 5)
             // loc < 2^20: (loc + 1/2) / bn is at least 1 / (2 bn) from an
             // integer, and the float product is within 2^-3 / bn of it
             const uint32_t ai = __float2uint_rz(((float)loc + 0.5f) * wt.inv[w][o]), bi = loc - ai * bn;
-            const int64_t ka = __ldg(gv.key + L.x + ai), kb = __ldg(gv.key + L.y + bi);
-            const int64_t ra = ka >> f.shift, rb = kb >> f.shift;
-            const bool a_first = ka < kb;
-            const int64_t gap = a_first ? rb - ra : ra - rb;
-            if (gap > gmax) continue;
-            const uint32_t dA = (uint32_t)(ka & 1) ^ (fl & TriRec::FLIP_A);
-            const uint32_t dB = (uint32_t)(kb & 1) ^ ((fl & TriRec::FLIP_B) ? 1u : 0u);
-            const uint32_t code = (dA << 2) | (dB << 1);
-            const int64_t *ck = gv.key + L.z;
-            const int64_t bab[2] = {key_bound(ka), key_bound(kb)};
-            uint32_t pab[2];
-            search_n<2>([&](uint32_t i) { return __ldg(ck + i); }, L.w, bab, pab);
-            const uint32_t pa = pab[0], pb = pab[1];
-            CView C;
-            C.key = gv.key;
-            C.fwd = gv.fwd;
-            C.b = L.z;
-            C.n = L.w;
-            C.flip = (fl & TriRec::FLIP_C) ? 1u : 0u;
-            C.px = a_first ? pa : pb;
-            C.py = a_first ? pb : pa;
-            C.f0 = wide ? X.z : __ldg(gv.fwd + L.z);
-            C.fn = wide ? X.w : __ldg(gv.fwd + L.z + L.w);
-            C.fx = __ldg(gv.fwd + L.z + C.px);
-            C.fy = __ldg(gv.fwd + L.z + C.py);
-            const int64_t rx = a_first ? ra : rb, ry = a_first ? rb : ra;
-            if (MODE != 1 || tslots) {
+            light_count_pair(gv, f, L.x, L.y, L.z, L.w, fl, wide, X.z, X.w, ai, bi, gmax,
+                             [&](const CView &C, bool a_first, int64_t rx, int64_t ry, uint32_t code) {
+                if (MODE != 1 || tslots) {
 #pragma unroll
-                for (uint32_t ql = 0; ql < (MODE == 1 ? LIGHT_QT : 1u); ql++) {
-                    if (MODE == 1 && q_beg + ql >= q_end) break;
-                    auto accq = [&](int type, uint32_t n) {
-                        if constexpr (MODE == 0) add_checked(s_acc[type][threadIdx.x], n, ovf);
-                        else if constexpr (MODE == 1) {
-                            uint32_t &cell = s_t[(ql * 8 + type) * LIGHT_THREADS + threadIdx.x];
-                            const uint32_t old = cell;
-                            cell = old + n;
-                            if (cell < old) shared_add(&s_bacc[(q_beg + ql) * 8 + type], 1ull << 32, ovf);
-                        }
-                        else atomicAdd(out + 8 * (base + o) + type, (unsigned long long)n);
-                    };
-                    light_pair(C, f, MODE == 1 ? wt.q[w][ql] : Q0, a_first, rx, ry, code, accq);
+                    for (uint32_t ql = 0; ql < (MODE == 1 ? LIGHT_QT : 1u); ql++) {
+                        if (MODE == 1 && q_beg + ql >= q_end) break;
+                        auto accq = [&](int type, uint32_t n) {
+                            if constexpr (MODE == 0) add_checked(s_acc[type][threadIdx.x], n, ovf);
+                            else if constexpr (MODE == 1)
+                                add_u32_carry(s_t[(ql * 8 + type) * LIGHT_THREADS + threadIdx.x], n,
+                                              &s_bacc[(q_beg + ql) * 8 + type], ovf);
+                            else atomicAdd(out + 8 * (base + o) + type, (unsigned long long)n);
+                        };
+                        light_pair(C, f, MODE == 1 ? wt.q[w][ql] : Q0, a_first, rx, ry, code, accq);
+                    }
+                } else {
+                    for (uint32_t q = q_beg; q < q_end; q++) {
+                        const Query Q = load_query(dq, q);
+                        auto accq = [&](int type, uint32_t n) { shared_add(&s_bacc[q * 8 + type], n, ovf); };
+                        light_pair(C, f, Q, a_first, rx, ry, code, accq);
+                    }
                 }
-            } else {
-                for (uint32_t q = q_beg; q < q_end; q++) {
-                    const Query Q = load_query(dq, q);
-                    auto accq = [&](int type, uint32_t n) { shared_add(&s_bacc[q * 8 + type], n, ovf); };
-                    light_pair(C, f, Q, a_first, rx, ry, code, accq);
-                }
-            }
+            });
         }
         __syncwarp();
     }
@@ -1166,7 +842,8 @@ void run_huge(ttc_graph *g, const HugeArgs &ha, const int64_t *dq_one, unsigned 
 HugeArgs huge_args(ttc_graph *g, void *scratch) {
     HugeArgs ha{};
     ha.gv = g->view_host;
-    ha.tri = g->tri.get() + g->st.tau_light + g->st.tau_hwarp + g->st.tau_hcta;
+    // (a streamed handle lists no light records: the view's light count is 0)
+    ha.tri = g->tri.get() + g->view_host.n_light + g->st.tau_hwarp + g->st.tau_hcta;
     ha.eoff = g->huge_eoff.get();
     ha.nh = g->st.tau_huge;
     ha.total = g->huge_elems;
@@ -1245,44 +922,9 @@ void count_graph(ttc_graph *g, const int64_t *dq, uint32_t k, unsigned long long
                  cudaStream_t s) {
     if (!g->st.tau || !k) return;
     unsigned long long *flag = acc + 8 * (size_t)k;
-    const uint64_t nl = g->st.tau_light;
     const GraphView *gv = g->view.get();
-    const uint64_t *light_pre = g->prefix.get();
-    if (nl) {
-        if (k == 1) {
-            prof_begin(g, s, "light");
-            light_kernel<0, 1><<<light_grid((nl + 31) / 32), LIGHT_THREADS, 0, s>>>(gv, light_pre, 1, dq, 1, acc, flag,
-                                                                                  nullptr, 0);
-            TTC_LAUNCH_CHECK();
-            prof_end(g, s);
-        } else {
-            // work items of 32 * LIGHT_BATCH_R records
-            const uint64_t chunks = (nl + 32 * LIGHT_BATCH_R - 1) / (32 * LIGHT_BATCH_R);
-            for (uint32_t q0 = 0; q0 < k; q0 += MAX_BATCH_SMEM_Q) {
-                const uint32_t nq = k - q0 < MAX_BATCH_SMEM_Q ? k - q0 : MAX_BATCH_SMEM_Q;
-                // enough (chunk, query group) items to fill the GPU, and no
-                // smaller groups than that: each group re-reads its chunk
-                const uint64_t want_items = (uint64_t)sm_count() * 8 * LIGHT_WARPS;
-                const uint32_t groups = (uint32_t)std::min<uint64_t>(nq, (want_items + chunks - 1) / chunks);
-                const uint32_t qpw = (nq + groups - 1) / groups;
-                prof_begin(g, s, "light_batch");
-                const size_t smem = nq * 64 + (qpw <= LIGHT_QT ? (size_t)LIGHT_QT * 8 * LIGHT_THREADS * 4 : 0);
-                static int light1_device = -1;
-                int dev = 0;
-                TTC_CUDA(cudaGetDevice(&dev));
-                if (light1_device != dev) {
-                    TTC_CUDA(cudaFuncSetAttribute(light_kernel<1, LIGHT_BATCH_R>,
-                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  (int)(MAX_BATCH_SMEM_Q * 64 + LIGHT_QT * 8 * LIGHT_THREADS * 4)));
-                    light1_device = dev;
-                }
-                light_kernel<1, LIGHT_BATCH_R><<<light_grid(chunks * ((nq + qpw - 1) / qpw)), LIGHT_THREADS, smem, s>>>(
-                    gv, light_pre, 1, dq + 3 * (size_t)q0, nq, acc + 8 * (size_t)q0, flag, nullptr, 0, qpw);
-                TTC_LAUNCH_CHECK();
-                prof_end(g, s);
-            }
-        }
-    }
+    if (g->streamed) stream_count_light(g, dq, k, acc, s);  // the light triangles are found again and counted
+    else if (g->st.tau_light) count_light_records(g, gv, g->prefix.get(), g->st.tau_light, dq, k, acc, s);
     const uint64_t nw = g->st.tau_hwarp, nc = g->st.tau_hcta;
     const uint64_t *hw_pre = g->prefix.get() + 2, *hc_pre = g->prefix.get() + 4;
     for (uint32_t q0 = 0; q0 < k && (nw || nc); q0 += MAX_BATCH_SMEM_Q) {
@@ -1337,6 +979,44 @@ __global__ void record_sizes_kernel(const uint4 *tri, const uint64_t *idx, uint6
 }
 
 }  // namespace
+
+void count_light_records(ttc_graph *g, const GraphView *gv, const uint64_t *light_pre, uint64_t nl,
+                         const int64_t *dq, uint32_t k, unsigned long long *acc, cudaStream_t s) {
+    if (!nl || !k) return;
+    unsigned long long *flag = acc + 8 * (size_t)k;
+    if (k == 1) {
+        prof_begin(g, s, "light");
+        light_kernel<0, 1><<<light_grid((nl + 31) / 32), LIGHT_THREADS, 0, s>>>(gv, light_pre, 1, dq, 1, acc, flag,
+                                                                              nullptr, 0);
+        TTC_LAUNCH_CHECK();
+        prof_end(g, s);
+        return;
+    }
+    // work items of 32 * LIGHT_BATCH_R records
+    const uint64_t chunks = (nl + 32 * LIGHT_BATCH_R - 1) / (32 * LIGHT_BATCH_R);
+    for (uint32_t q0 = 0; q0 < k; q0 += MAX_BATCH_SMEM_Q) {
+        const uint32_t nq = k - q0 < MAX_BATCH_SMEM_Q ? k - q0 : MAX_BATCH_SMEM_Q;
+        // enough (chunk, query group) items to fill the GPU, and no
+        // smaller groups than that: each group re-reads its chunk
+        const uint64_t want_items = (uint64_t)sm_count() * 8 * LIGHT_WARPS;
+        const uint32_t groups = (uint32_t)std::min<uint64_t>(nq, (want_items + chunks - 1) / chunks);
+        const uint32_t qpw = (nq + groups - 1) / groups;
+        prof_begin(g, s, "light_batch");
+        const size_t smem = nq * 64 + (qpw <= LIGHT_QT ? (size_t)LIGHT_QT * 8 * LIGHT_THREADS * 4 : 0);
+        static int light1_device = -1;
+        int dev = 0;
+        TTC_CUDA(cudaGetDevice(&dev));
+        if (light1_device != dev) {
+            TTC_CUDA(cudaFuncSetAttribute(light_kernel<1, LIGHT_BATCH_R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)(MAX_BATCH_SMEM_Q * 64 + LIGHT_QT * 8 * LIGHT_THREADS * 4)));
+            light1_device = dev;
+        }
+        light_kernel<1, LIGHT_BATCH_R><<<light_grid(chunks * ((nq + qpw - 1) / qpw)), LIGHT_THREADS, smem, s>>>(
+            gv, light_pre, 1, dq + 3 * (size_t)q0, nq, acc + 8 * (size_t)q0, flag, nullptr, 0, qpw);
+        TTC_LAUNCH_CHECK();
+        prof_end(g, s);
+    }
+}
 
 size_t heavy_scratch_bytes(const ttc_graph *g) {
     const size_t entries = (size_t)g->huge_elems + 4 * (size_t)g->st.tau_huge;

@@ -60,6 +60,16 @@ struct ttc_graph {
     // tau_huge records
     ttc::DevBuf<uint64_t> huge_eoff;    // [tau_huge + 1] enumerated-edge offsets
     uint64_t huge_elems = 0;
+    // TTC_LOAD_STREAM: no light records; the oriented CSR and the
+    // enumeration's work items are kept and each count enumerates again
+    bool streamed = false;
+    ttc::DevBuf<uint2> s_items;     // [s_nitems] (target v, first in-edge)
+    uint32_t s_nitems = 0;
+    ttc::DevBuf<uint4> s_ocsr;      // [m_s] per oriented edge: target rank, sigma word, pair
+    ttc::DevBuf<uint32_t> s_onbr, s_osrc, s_in_e;  // [m_s]
+    ttc::DevBuf<uint32_t> s_out_off, s_in_off;     // [n + 1]
+    std::vector<uint32_t> s_chunks;  // work-item boundaries of the collecting passes
+    uint64_t s_chunk_cap = 0;        // light records one collecting pass can hold
     // the graph as a one-entry graph table
     GraphView view_host{};
     ttc::DevBuf<GraphView> view;        // [1]
@@ -102,6 +112,23 @@ void prof_end(ttc_graph *g, cudaStream_t s);
 // (dq: k * 3 int64 as d13, d12, d23), accumulated into acc ([k][8] u64 plus a
 // trailing overflow flag), which the caller zeroes.
 void count_queue(ttc_graph *g, const int64_t *dq, uint32_t k, unsigned long long *acc, cudaStream_t s);
+
+// load.cu: for a TTC_LOAD_STREAM handle, the light triangles' counts for k
+// normalised queries (dq on the device), added into acc ([k][8] plus the
+// overflow flag): the enumeration runs again chunk by chunk of its work
+// items, collects each chunk's light records into a buffer of
+// s_chunk_cap records, and the light kernels count them for all k queries.
+void stream_count_light(ttc_graph *g, const int64_t *dq, uint32_t k, unsigned long long *acc, cudaStream_t s);
+// Records per collecting buffer: TTC_STREAM_CHUNK from the environment, else
+// 2^24 (at least the largest work item's room).
+uint64_t stream_chunk_records();
+
+// count.cu: the light kernels over the light records of the one-graph table
+// view (pre: its 32-record chunk prefix {0, chunks}, both on the device);
+// n_bound bounds the record count (sizes the grid).  k normalised queries,
+// acc [k][8] plus the overflow flag.
+void count_light_records(ttc_graph *g, const GraphView *view, const uint64_t *pre, uint64_t n_bound,
+                         const int64_t *dq, uint32_t k, unsigned long long *acc, cudaStream_t s);
 
 // count.cu: the same kernels as count_queue for one normalised query, but
 // with every device buffer supplied by the caller: acc (9 u64, zeroed by the

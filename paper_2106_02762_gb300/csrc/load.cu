@@ -16,8 +16,10 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <cstdlib>
 
 #include "graph.cuh"
+#include "count_dev.cuh"
 #include "sort.cuh"
 
 namespace cg = cooperative_groups;
@@ -1346,13 +1348,38 @@ struct TriCsr {
 // pair ids) for dv <= TRI_NV_CAP.
 constexpr size_t tri_warp_smem() { return (size_t)TRI_NV_CAP * 4 * 3; }
 
+// What an enumeration pass does with the triangles it finds.
+enum EnumMode {
+    ENUM_WRITE = 0,    // write every record into its edge's room (cnt_light/heavy, resv, sparse)
+    ENUM_SCAN = 1,     // statistics and light/heavy totals; heavy records appended to `heavy`
+    ENUM_COLLECT = 2,  // light records appended to `light` (streamed handle, one chunk of items)
+};
+
+struct EnumArgs {
+    // ENUM_WRITE
+    uint32_t *cnt_light, *cnt_heavy;
+    const uint64_t *resv;
+    uint4 *sparse;
+    // ENUM_WRITE, ENUM_SCAN: sums[0..4] as below, ENUM_SCAN also sums[5..6] =
+    // light, heavy triangles
+    unsigned long long *sums;
+    // ENUM_SCAN: heavy records, appended while heavy_n < heavy_cap
+    uint4 *heavy;
+    unsigned long long *heavy_n;
+    uint64_t heavy_cap;
+    // ENUM_COLLECT: light records, appended while light_n < light_cap
+    uint4 *light;
+    unsigned long long *light_n;
+    uint64_t light_cap;
+};
+
+template <int EM>
 __global__ void __launch_bounds__(TRI_THREADS)
-    tri_enum_kernel(const uint2 *__restrict__ items, uint32_t nitems, TriCsr g, RecCtx rc, uint32_t *cnt_light,
-                    uint32_t *cnt_heavy, const uint64_t *resv, uint4 *sparse, unsigned long long *sums) {
+    tri_enum_kernel(const uint2 *__restrict__ items, uint32_t nitems, TriCsr g, RecCtx rc, EnumArgs ea) {
     // work statistics of the records written: sum of 8 (s_A + s_B + s_C) + 12,
     // of s_A + s_B, the first over heavy records, of s_A s_B over light
     // ones, and whether a sigma word was capped
-    unsigned long long st_w = 0, st_en = 0, st_wh = 0, st_lp = 0, st_cap = 0;
+    unsigned long long st_w = 0, st_en = 0, st_wh = 0, st_lp = 0, st_cap = 0, st_nl = 0, st_nh = 0;
     extern __shared__ uint32_t tri_smem[];
     __shared__ uint32_t s_excl[TRI_WARPS][33];
     __shared__ uint32_t s_e[TRI_WARPS][32], s_se[TRI_WARPS][32], s_pe[TRI_WARPS][32];
@@ -1390,8 +1417,10 @@ __global__ void __launch_bounds__(TRI_THREADS)
             s_se[w][lane] = q.y;
             s_pe[w][lane] = q.z;
             len = __ldg(g.out_off + u + 1) - e - 1;  // the suffix of N+(u) after v
-            s_lo[w][lane] = resv[e];
-            s_ho[w][lane] = resv[e] + len - 1;
+            if constexpr (EM == ENUM_WRITE) {
+                s_lo[w][lane] = ea.resv[e];
+                s_ho[w][lane] = ea.resv[e] + len - 1;
+            }
         }
         s_run[w][2 * lane] = 0;
         s_run[w][2 * lane + 1] = 0;
@@ -1448,13 +1477,36 @@ __global__ void __launch_bounds__(TRI_THREADS)
                     uint32_t na, nb;
                     r = make_record(rc, s_se[w][o[h]], qw[h].y, s_vw, s_pe[w][o[h]], qw[h].z, p_vw, &heavy, &na,
                                     &nb);
-                    const uint32_t s1 = s_se[w][o[h]] & SIG_MASK, s2 = qw[h].y & SIG_MASK, s3 = s_vw & SIG_MASK;
-                    const unsigned long long wb = 8ull * ((unsigned long long)s1 + s2 + s3) + 12;
-                    st_w += wb;
-                    st_en += (unsigned long long)na + nb;
-                    if (heavy) st_wh += wb; else st_lp += (unsigned long long)na * nb;
-                    st_cap |= (s1 == SIG_MASK || s2 == SIG_MASK || s3 == SIG_MASK) ? 1ull : 0ull;
+                    if constexpr (EM != ENUM_COLLECT) {
+                        const uint32_t s1 = s_se[w][o[h]] & SIG_MASK, s2 = qw[h].y & SIG_MASK,
+                                       s3 = s_vw & SIG_MASK;
+                        const unsigned long long wb = 8ull * ((unsigned long long)s1 + s2 + s3) + 12;
+                        st_w += wb;
+                        st_en += (unsigned long long)na + nb;
+                        if (heavy) st_wh += wb; else st_lp += (unsigned long long)na * nb;
+                        st_cap |= (s1 == SIG_MASK || s2 == SIG_MASK || s3 == SIG_MASK) ? 1ull : 0ull;
+                    }
+                    if constexpr (EM == ENUM_SCAN) {
+                        if (heavy) {
+                            st_nh++;
+                            const unsigned long long at = atomicAdd(ea.heavy_n, 1ull);
+                            if (at < ea.heavy_cap) ea.heavy[at] = r;
+                        } else {
+                            st_nl++;
+                        }
+                    }
                 }
+                if constexpr (EM == ENUM_COLLECT) {
+                    // one reservation per warp for its light hits
+                    const bool take = hit && !heavy;
+                    const unsigned lm = __ballot_sync(0xffffffffu, take);
+                    if (!lm) continue;
+                    unsigned long long at = 0;
+                    if (lane == (uint32_t)(__ffs(lm) - 1)) at = atomicAdd(ea.light_n, (unsigned long long)__popc(lm));
+                    at = __shfl_sync(0xffffffffu, at, __ffs(lm) - 1) + __popc(lm & lt_mask);
+                    if (take && at < ea.light_cap) ea.light[at] = r;
+                }
+                if constexpr (EM != ENUM_WRITE) continue;
                 const unsigned act = __ballot_sync(0xffffffffu, hit);
                 if (!act) continue;
                 const uint32_t slot = o[h];
@@ -1465,30 +1517,42 @@ __global__ void __launch_bounds__(TRI_THREADS)
                 __syncwarp();
                 if (hit && (peers & lt_mask) == 0) s_run[w][key] += __popc(peers);
                 __syncwarp();
-                if (hit) sparse[heavy ? s_ho[w][slot] - rank : s_lo[w][slot] + rank] = r;
+                if (hit) ea.sparse[heavy ? s_ho[w][slot] - rank : s_lo[w][slot] + rank] = r;
             }
         }
         __syncwarp();
-        if (i < din) {
-            cnt_light[s_e[w][lane]] = s_run[w][2 * lane];
-            cnt_heavy[s_e[w][lane]] = s_run[w][2 * lane + 1];
+        if constexpr (EM == ENUM_WRITE) {
+            if (i < din) {
+                ea.cnt_light[s_e[w][lane]] = s_run[w][2 * lane];
+                ea.cnt_heavy[s_e[w][lane]] = s_run[w][2 * lane + 1];
+            }
         }
         __syncwarp();
     }
+    if constexpr (EM == ENUM_COLLECT) {
+        return;
+    } else {
 #pragma unroll
-    for (int o = 16; o; o >>= 1) {
-        st_w += __shfl_xor_sync(0xffffffffu, st_w, o);
-        st_en += __shfl_xor_sync(0xffffffffu, st_en, o);
-        st_wh += __shfl_xor_sync(0xffffffffu, st_wh, o);
-        st_lp += __shfl_xor_sync(0xffffffffu, st_lp, o);
-        st_cap |= __shfl_xor_sync(0xffffffffu, st_cap, o);
-    }
-    if (lane == 0 && st_w) {
-        atomicAdd(sums, st_w);
-        atomicAdd(sums + 1, st_en);
-        atomicAdd(sums + 2, st_wh);
-        atomicAdd(sums + 3, st_lp);
-        if (st_cap) atomicOr(sums + 4, 1ull);
+        for (int o = 16; o; o >>= 1) {
+            st_w += __shfl_xor_sync(0xffffffffu, st_w, o);
+            st_en += __shfl_xor_sync(0xffffffffu, st_en, o);
+            st_wh += __shfl_xor_sync(0xffffffffu, st_wh, o);
+            st_lp += __shfl_xor_sync(0xffffffffu, st_lp, o);
+            st_cap |= __shfl_xor_sync(0xffffffffu, st_cap, o);
+            st_nl += __shfl_xor_sync(0xffffffffu, st_nl, o);
+            st_nh += __shfl_xor_sync(0xffffffffu, st_nh, o);
+        }
+        if (lane == 0 && st_w) {
+            atomicAdd(ea.sums, st_w);
+            atomicAdd(ea.sums + 1, st_en);
+            atomicAdd(ea.sums + 2, st_wh);
+            atomicAdd(ea.sums + 3, st_lp);
+            if (st_cap) atomicOr(ea.sums + 4, 1ull);
+            if constexpr (EM == ENUM_SCAN) {
+                atomicAdd(ea.sums + 5, st_nl);
+                atomicAdd(ea.sums + 6, st_nh);
+            }
+        }
     }
 }
 
@@ -1605,13 +1669,58 @@ T read_scalar(const T *dev, cudaStream_t s) {
 uint32_t default_light_max_pairs() { return 65; }
 
 // The graph as a one-entry graph table for the count kernels.
+// Records an enumeration work item (target v, in-edges c0 .. c0 + 31) can
+// produce at most: the suffixes of N+(u) after v over its in-edges u -> v.
+__global__ void item_room_kernel(const uint2 *items, uint32_t nitems, TriCsr g, uint64_t *room) {
+    GRID_STRIDE(it, (size_t)nitems) {
+        const uint2 item = items[it];
+        const uint32_t ib = g.in_off[item.x], din = g.in_off[item.x + 1] - ib;
+        uint64_t r = 0;
+        for (uint32_t i = item.y; i < din && i < item.y + 32; i++) {
+            const uint32_t e = g.in_e[ib + i];
+            r += g.out_off[g.osrc[e] + 1] - e - 1;
+        }
+        room[it] = r;
+    }
+}
+
+// After a collecting pass: the chunk's view lists its n light records, and
+// its 32-record chunk prefix is {0, ceil(n / 32)}.
+__global__ void chunk_view_kernel(const unsigned long long *light_n, uint64_t cap, GraphView *view,
+                                  uint64_t *pre) {
+    const uint64_t n = min((uint64_t)*light_n, cap);
+    view->n_light = n;
+    pre[0] = 0;
+    pre[1] = (n + 31) / 32;
+}
+
+// One enumeration pass over the work items (grid: as many CTAs as fit).
+template <int EM>
+void launch_enum(const uint2 *items, uint32_t nitems, const TriCsr &tc, const RecCtx &rc, const EnumArgs &ea,
+                 cudaStream_t s) {
+    if (!nitems) return;
+    const size_t smem = TRI_WARPS * tri_warp_smem();
+    static int configured_device = -1;
+    static int occ = 1;
+    int dev = 0;
+    TTC_CUDA(cudaGetDevice(&dev));
+    if (configured_device != dev) {
+        TTC_CUDA(cudaFuncSetAttribute(tri_enum_kernel<EM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        TTC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, tri_enum_kernel<EM>, TRI_THREADS, smem));
+        configured_device = dev;
+    }
+    const unsigned grid = (unsigned)std::min<uint64_t>(nitems / TRI_WARPS + 1, (uint64_t)sm_count() * std::max(1, occ));
+    tri_enum_kernel<EM><<<grid, TRI_THREADS, smem, s>>>(items, nitems, tc, rc, ea);
+    TTC_LAUNCH_CHECK();
+}
+
 static void set_view(ttc_graph *g, cudaStream_t s) {
     GraphView &v = g->view_host;
     v.key = g->key.get();
     v.fwd = g->fwd.get();
     v.poff = g->poff.get();
     v.tri = g->tri.get();
-    v.n_light = g->st.tau_light;
+    v.n_light = g->streamed ? 0 : g->st.tau_light;  // a streamed handle lists heavy triangles only
     v.n_hwarp = g->st.tau_hwarp;
     v.n_hcta = g->st.tau_hcta;
     v.n_heavy = g->st.tau_heavy;
@@ -2064,12 +2173,67 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
     tri_items_fill_kernel<<<grid_for(nitems), TPB, 0, s>>>(it_pre.get(), (uint32_t)n, nitems, items.get());
     TTC_LAUNCH_CHECK();
     nit.reset(); it_pre.reset();
-    const size_t smem_t = TRI_WARPS * tri_warp_smem();
-    TTC_CUDA(cudaFuncSetAttribute(tri_enum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_t));
-    int occ_t = 0;
-    TTC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_t, tri_enum_kernel, TRI_THREADS, smem_t));
-    const unsigned grid_t =
-        (unsigned)std::min<uint64_t>(nitems / TRI_WARPS + 1, (uint64_t)sm_count() * std::max(1, occ_t));
+    DevBuf<unsigned long long> ws(7, s);
+    TTC_CUDA(cudaMemsetAsync(ws.get(), 0, 56, s));
+    uint64_t n_light = 0, tau = 0, n_rec_light = 0;  // n_rec_light: light records stored
+    if (opt.flags & TTC_LOAD_STREAM) {
+        // no light records: one scan pass for the statistics and the heavy
+        // records; the oriented graph stays for the counts
+        DevBuf<unsigned long long> hn(1, s);
+        uint64_t cap = 1u << 20;  // heavy records are few; a second pass takes any excess
+        for (int pass = 0; pass < 2; pass++) {
+            TTC_CUDA(cudaMemsetAsync(hn.get(), 0, 8, s));
+            TTC_CUDA(cudaMemsetAsync(ws.get(), 0, 56, s));
+            g->tri.alloc(cap, s);
+            EnumArgs ea{};
+            ea.sums = ws.get();
+            ea.heavy = g->tri.get();
+            ea.heavy_n = hn.get();
+            ea.heavy_cap = cap;
+            launch_enum<ENUM_SCAN>(items.get(), nitems, tc, rc, ea, s);
+            const uint64_t nh = read_scalar(hn.get(), s);
+            if (nh <= cap) break;
+            cap = nh;  // too many heavy triangles for the first guess: again, with room for all
+        }
+        uint64_t c[2];
+        TTC_CUDA(cudaMemcpyAsync(c, ws.get() + 5, 16, cudaMemcpyDeviceToHost, s));
+        TTC_CUDA(cudaStreamSynchronize(s));
+        n_light = c[0];
+        tau = c[0] + c[1];
+        if (tau >= (uint64_t(1) << 32)) fail(TTC_ERR_RANGE, "more than 2^32 static triangles");
+        g->streamed = true;
+        g->s_items = static_cast<DevBuf<uint2> &&>(items);
+        g->s_nitems = nitems;
+        g->s_ocsr = static_cast<DevBuf<uint4> &&>(ocsr);
+        g->s_onbr = static_cast<DevBuf<uint32_t> &&>(onbr);
+        g->s_osrc = static_cast<DevBuf<uint32_t> &&>(osrc);
+        g->s_in_e = static_cast<DevBuf<uint32_t> &&>(in_e);
+        g->s_out_off = static_cast<DevBuf<uint32_t> &&>(out_off);
+        g->s_in_off = static_cast<DevBuf<uint32_t> &&>(in_off);
+        // chunks of work items whose light records fit the collecting buffer
+        DevBuf<uint64_t> room(nitems ? nitems : 1, s), rpre(nitems + 1, s);
+        const TriCsr kept{g->s_onbr.get(), g->s_ocsr.get(), g->s_out_off.get(), g->s_osrc.get(), g->s_in_off.get(),
+                          g->s_in_e.get()};
+        if (nitems) {
+            item_room_kernel<<<grid_for(nitems), TPB, 0, s>>>(g->s_items.get(), nitems, kept, room.get());
+            TTC_LAUNCH_CHECK();
+        }
+        exclusive_scan_u64(room.get(), rpre.get(), nitems, s);
+        std::vector<uint64_t> hp(nitems + 1);
+        TTC_CUDA(cudaMemcpyAsync(hp.data(), rpre.get(), (nitems + 1) * 8, cudaMemcpyDeviceToHost, s));
+        TTC_CUDA(cudaStreamSynchronize(s));
+        uint64_t chunk = stream_chunk_records();
+        for (uint32_t it = 0; it < nitems; it++) chunk = std::max<uint64_t>(chunk, hp[it + 1] - hp[it]);
+        g->s_chunk_cap = std::min<uint64_t>(chunk, std::max<uint64_t>(hp[nitems], 1));
+        g->s_chunks.assign(1, 0u);
+        for (uint32_t it = 0; it < nitems;) {
+            // the longest run of items from `it` whose rooms fit the buffer
+            const uint64_t lim = hp[it] + g->s_chunk_cap;
+            const uint32_t end = (uint32_t)(std::upper_bound(hp.begin() + it + 1, hp.end(), lim) - hp.begin()) - 1;
+            it = std::max(end, it + 1);
+            g->s_chunks.push_back(it);
+        }
+    } else {
     // room per oriented edge, then one enumeration pass into it
     DevBuf<uint64_t> room(ms, s), resv(ms + 1, s);
     tri_room_kernel<<<grid_for(ms), TPB, 0, s>>>(osrc.get(), out_off.get(), ms, room.get());
@@ -2082,11 +2246,15 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
     DevBuf<uint64_t> loff(ms + 1, s), hoff(ms + 1, s), cl64(ms + 1, s), ch64(ms + 1, s);
     TTC_CUDA(cudaMemsetAsync(cl.get(), 0, (ms + 1) * 4, s));
     TTC_CUDA(cudaMemsetAsync(ch.get(), 0, (ms + 1) * 4, s));
-    DevBuf<unsigned long long> ws(5, s);
-    TTC_CUDA(cudaMemsetAsync(ws.get(), 0, 40, s));
-    tri_enum_kernel<<<grid_t, TRI_THREADS, smem_t, s>>>(items.get(), nitems, tc, rc, cl.get(), ch.get(), resv.get(),
-                                                       sparse.get(), ws.get());
-    TTC_LAUNCH_CHECK();
+    {
+        EnumArgs ea{};
+        ea.cnt_light = cl.get();
+        ea.cnt_heavy = ch.get();
+        ea.resv = resv.get();
+        ea.sparse = sparse.get();
+        ea.sums = ws.get();
+        launch_enum<ENUM_WRITE>(items.get(), nitems, tc, rc, ea, s);
+    }
     widen_kernel<<<grid_for(ms), TPB, 0, s>>>(cl.get(), ch.get(), ms, cl64.get(), ch64.get());
     TTC_LAUNCH_CHECK();
     exclusive_scan_u64(cl64.get(), loff.get(), ms, s);
@@ -2095,9 +2263,10 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
     TTC_CUDA(cudaMemcpyAsync(&nlh[0], loff.get() + ms, 8, cudaMemcpyDeviceToHost, s));
     TTC_CUDA(cudaMemcpyAsync(&nlh[1], hoff.get() + ms, 8, cudaMemcpyDeviceToHost, s));
     TTC_CUDA(cudaStreamSynchronize(s));
-    const uint64_t n_light = nlh[0], tau = nlh[0] + nlh[1];
+    n_light = nlh[0];
+    n_rec_light = n_light;
+    tau = nlh[0] + nlh[1];
     if (tau >= (uint64_t(1) << 32)) fail(TTC_ERR_RANGE, "more than 2^32 static triangles");
-    st.tau = tau;
     g->tri.alloc(tau, s);
     if (tau) {
         const unsigned grid_c = (unsigned)std::min<uint64_t>(ceil_div(ms, 32 * TRI_WARPS), (uint64_t)sm_count() * 8);
@@ -2105,9 +2274,9 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
                                                           n_light, ms, sparse.get(), g->tri.get());
         TTC_LAUNCH_CHECK();
     }
-    sparse.reset(); resv.reset();
-    cl.reset(); ch.reset(); loff.reset(); hoff.reset(); cl64.reset(); ch64.reset();
+    }
     osrc.reset(); onbr.reset(); ocsr.reset(); out_off.reset(); in_off.reset(); in_e.reset();
+    st.tau = tau;
     st.tau_light = n_light;
     st.tau_heavy = tau - n_light;
 
@@ -2121,7 +2290,7 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
     unsigned long long hws[5];
     TTC_CUDA(cudaMemcpyAsync(hws, ws.get(), 40, cudaMemcpyDeviceToHost, s));
     TTC_CUDA(cudaStreamSynchronize(s));
-    if (hws[4]) {
+    if (hws[4] && !g->streamed) {
         TTC_CUDA(cudaMemsetAsync(ws.get(), 0, 32, s));
         record_stats_kernel<<<grid_for(tau), TPB, 0, s>>>(g->tri.get(), tau, n_light, g->poff.get(), he.get(),
                                                           ws.get());
@@ -2129,7 +2298,7 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
         TTC_CUDA(cudaMemcpyAsync(hws, ws.get(), 32, cudaMemcpyDeviceToHost, s));
         TTC_CUDA(cudaStreamSynchronize(s));
     } else if (nh) {
-        heavy_sizes_kernel<<<grid_for(nh), TPB, 0, s>>>(g->tri.get() + n_light, nh, g->poff.get(), he.get());
+        heavy_sizes_kernel<<<grid_for(nh), TPB, 0, s>>>(g->tri.get() + n_rec_light, nh, g->poff.get(), he.get());
         TTC_LAUNCH_CHECK();
     }
     st.work_bytes = hws[0];
@@ -2158,11 +2327,12 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
         n_huge = cnt[2];
         DevBuf<uint4> part(nh, s);
         DevBuf<uint64_t> he2(nh, s);
-        heavy_partition_kernel<<<grid_for(nh), TPB, 0, s>>>(g->tri.get() + n_light, he.get(), f0.get(), f1.get(),
-                                                            p0.get(), p1.get(), p2.get(), nh, n_hw, n_hc, part.get(),
-                                                            he2.get());
+        heavy_partition_kernel<<<grid_for(nh), TPB, 0, s>>>(g->tri.get() + n_rec_light, he.get(), f0.get(),
+                                                            f1.get(), p0.get(), p1.get(), p2.get(), nh, n_hw, n_hc,
+                                                            part.get(), he2.get());
         TTC_LAUNCH_CHECK();
-        TTC_CUDA(cudaMemcpyAsync(g->tri.get() + n_light, part.get(), nh * sizeof(uint4), cudaMemcpyDeviceToDevice, s));
+        TTC_CUDA(cudaMemcpyAsync(g->tri.get() + n_rec_light, part.get(), nh * sizeof(uint4),
+                                 cudaMemcpyDeviceToDevice, s));
         if (n_huge) {
             g->huge_eoff.alloc(n_huge + 1, s);
             exclusive_scan_u64(he2.get() + n_hw + n_hc, g->huge_eoff.get(), n_huge, s);
@@ -2192,6 +2362,41 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
     set_view(g, s);
     prof_end(g, s);
     TTC_CUDA(cudaStreamSynchronize(s));
+}
+
+uint64_t stream_chunk_records() {
+    const char *e = getenv("TTC_STREAM_CHUNK");
+    const long long v = e ? atoll(e) : 0;
+    return v > 0 ? (uint64_t)v : (uint64_t(1) << 24);
+}
+
+void stream_count_light(ttc_graph *g, const int64_t *dq, uint32_t k, unsigned long long *acc, cudaStream_t s) {
+    if (!g->streamed || !g->st.tau_light || !k) return;
+    const TriCsr tc{g->s_onbr.get(), g->s_ocsr.get(), g->s_out_off.get(), g->s_osrc.get(), g->s_in_off.get(),
+                    g->s_in_e.get()};
+    const RecCtx rc{g->labeling, g->light_max_pairs};
+    const uint64_t cap = g->s_chunk_cap;
+    DevBuf<uint4> light(cap, s);
+    DevBuf<unsigned long long> light_n(1, s);
+    DevBuf<GraphView> view(1, s);
+    DevBuf<uint64_t> pre(2, s);
+    GraphView v = g->view_host;
+    v.tri = light.get();
+    TTC_CUDA(cudaMemcpyAsync(view.get(), &v, sizeof v, cudaMemcpyHostToDevice, s));
+    for (size_t c = 0; c + 1 < g->s_chunks.size(); c++) {
+        const uint32_t i0 = g->s_chunks[c], i1 = g->s_chunks[c + 1];
+        TTC_CUDA(cudaMemsetAsync(light_n.get(), 0, 8, s));
+        EnumArgs ea{};
+        ea.light = light.get();
+        ea.light_n = light_n.get();
+        ea.light_cap = cap;
+        prof_begin(g, s, "stream_collect");
+        launch_enum<ENUM_COLLECT>(g->s_items.get() + i0, i1 - i0, tc, rc, ea, s);
+        prof_end(g, s);
+        chunk_view_kernel<<<1, 1, 0, s>>>(light_n.get(), cap, view.get(), pre.get());
+        TTC_LAUNCH_CHECK();
+        count_light_records(g, view.get(), pre.get(), cap, dq, k, acc, s);
+    }
 }
 
 }  // namespace ttc

@@ -54,6 +54,10 @@ extern "C" ttc_status ttc_count_noalloc(ttc_graph *g, const ttc_delta *d, uint64
         set_last_error("NULL argument");
         return TTC_ERR_INVALID;
     }
+    if (g->streamed) {
+        set_last_error("the graph was loaded with TTC_LOAD_STREAM, whose counts need scratch of their own");
+        return TTC_ERR_INVALID;
+    }
     try {
         int64_t hq[3];
         normalise(*d, hq);
