@@ -44,9 +44,10 @@ def parse():
     ap.add_argument("--scale", type=float, default=1.0, help="workload scale (1.0 = the full workload)")
     ap.add_argument("--query-iters", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", choices=["plain", "multi", "serve", "grid"], default="plain",
+    ap.add_argument("--mode", choices=["plain", "multi", "serve", "grid", "zipf15"], default="plain",
                     help="plain: the power-law workload (default line); multi: many graphs in one launch; "
-                         "serve: Poisson queries against a resident pool")
+                         "serve: Poisson queries against a resident pool; grid: a delta grid; zipf15: the "
+                         "power-law workload with multiplicity exponent 1.5 (about 766M edges)")
     ap.add_argument("--graphs", type=int, default=4096, help="multi: number of graphs")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: query arrivals per second")
     ap.add_argument("--duration", type=float, default=20.0, help="serve: seconds of arrivals")
@@ -700,6 +701,59 @@ def run_ours(args):
     barrier(ws)
 
 
+def run_zipf15(args):
+    """The power-law recipe with the multiplicity exponent 1.5 taken
+    literally (about 766M edges, mean multiplicity 77): the same timed step
+    (load from device edges + one batched count of the configured and the
+    unbounded delta) with a listed and with a streamed handle, device-timed."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2106_02762_gb300 import ttc, synth
+    w = time.perf_counter()
+    src, dst, t = synth.large_plain_zipf15(scale=args.scale)
+    gen_s = time.perf_counter() - w
+    dev = torch.device("cuda", 0)
+    d_src = torch.from_numpy(src.view(np.int32)).to(dev)
+    d_dst = torch.from_numpy(dst.view(np.int32)).to(dev)
+    d_t = torch.from_numpy(t).to(dev)
+    del src, dst, t
+    stream = torch.cuda.Stream(device=dev)
+    qs = step_queries(synth.LARGE_PLAIN_DELTA)
+    res, ref = {}, None
+    for streamed in (False, True):
+        st, ld = [], []
+        for i in range(max(1, args.warmup) + max(1, args.steps)):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e2 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g = ttc.Graph(d_src, d_dst, d_t, stream=stream.cuda_stream, streamed=streamed)
+            e1.record(stream)
+            out = g.count_batch(qs)
+            e2.record(stream)
+            e2.synchronize()
+            if ref is None:
+                ref = out
+            assert (out == ref).all()
+            if i >= max(1, args.warmup):
+                st.append(e0.elapsed_time(e2))
+                ld.append(e0.elapsed_time(e1))
+            info = g.info()
+            g.free()
+        res["streamed" if streamed else "listed"] = {"step_ms": statistics.median(st), "load_ms": statistics.median(ld),
+                                                     "device_bytes": info["device_bytes"]}
+    m = info["m"]
+    print(json.dumps({"mode": "zipf15", "metric": "temporal edges/s per delta-query",
+                      "value": m / (res["listed"]["step_ms"] / 1e3), "unit": UNIT, **res,
+                      "graph": {k: info[k] for k in ("n", "m", "m_s", "tau", "tau_light", "tau_heavy", "tau_huge",
+                                                     "kappa", "sigma_max", "work_bytes", "light_pairs")},
+                      "unbounded_total": int(ref[1].sum()), "generate_s": gen_s,
+                      "config": {"workload": "power-law n=%d pairs=%d gamma=2.1 zipf1.5-cap1e4 lognormal(6,2) span 2^31"
+                                 % (int(round(1_000_000 * args.scale)), int(round(10_000_000 * args.scale))),
+                                 "step_deltas": [list(q) for q in qs]}}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -710,6 +764,8 @@ def main():
         run_serve(args)
     elif args.mode == "grid":
         run_grid(args)
+    elif args.mode == "zipf15":
+        run_zipf15(args)
     else:
         run_ours(args)
 

@@ -93,6 +93,13 @@ typedef enum {
                                      buffer of TTC_STREAM_CHUNK records (environment,
                                      read at load; default 2^24 = 256 MiB) */
 
+#define TTC_LOAD_STRICT_TIME 8u   /* read Def. 1's t1 < t2 < t3 literally: a triple
+                                     counts only if its three timestamps strictly
+                                     increase.  Default: edges are ordered by the key
+                                     (t, input index), so equal timestamps are ordered
+                                     by input position (Sec. 3 assumes distinct
+                                     timestamps; both readings agree on such inputs) */
+
 /* Vertex orderings used to orient the static graph.  Any acyclic orientation
  * gives identical counts; the degeneracy ordering (Sec. 3, Matula-Beck) bounds
  * every out-degree by the degeneracy kappa (Theorem 1). */

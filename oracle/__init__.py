@@ -45,11 +45,14 @@ def _load():
         p = ctypes.c_void_p
         u64, u32, i32 = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
         lib.ttc_oracle_bruteforce.argtypes = [p, p, p, u64, p, u32, p]
+        lib.ttc_oracle_bruteforce_ex.argtypes = [p, p, p, u64, p, u32, i32, p]
         lib.ttc_oracle_count.argtypes = [p, p, p, u64, p, u32, i32, p]
+        lib.ttc_oracle_count_ex.argtypes = [p, p, p, u64, p, u32, i32, i32, p]
         lib.ttc_oracle_count_part.argtypes = [p, p, p, u64, p, u32, i32, u32, u32, p]
         lib.ttc_oracle_count_triangles.argtypes = [p, p, p, u64, p, u64, p, u32, i32, p]
         lib.ttc_oracle_stats.argtypes = [p, p, p, u64, i32, p]
-        for f in (lib.ttc_oracle_bruteforce, lib.ttc_oracle_count, lib.ttc_oracle_count_part,
+        for f in (lib.ttc_oracle_bruteforce, lib.ttc_oracle_bruteforce_ex, lib.ttc_oracle_count,
+                  lib.ttc_oracle_count_ex, lib.ttc_oracle_count_part,
                   lib.ttc_oracle_count_triangles, lib.ttc_oracle_stats):
             f.restype = ctypes.c_int
         _lib = lib
@@ -81,23 +84,26 @@ def _check(rc, allow_overflow=False):
                        ERR_OVERFLOW: "count exceeds 2^64-1"}.get(rc, "error %d" % rc))
 
 
-def bruteforce(src, dst, t, deltas):
-    """O0: every edge triple checked against Def. 1.  Returns [k][8]."""
+def bruteforce(src, dst, t, deltas, strict: bool = False):
+    """O0: every edge triple checked against Def. 1.  Returns [k][8].
+    strict: t1 < t2 < t3 literally (no two edges of a counted triple share a
+    timestamp) instead of key order."""
     src, dst, t = _edges(src, dst, t)
     d = _deltas(deltas)
     out = np.zeros((d.shape[0], 8), dtype=np.uint64)
-    _check(_load().ttc_oracle_bruteforce(_ptr(src), _ptr(dst), _ptr(t), src.size,
-                                         _ptr(d), d.shape[0], _ptr(out)))
+    _check(_load().ttc_oracle_bruteforce_ex(_ptr(src), _ptr(dst), _ptr(t), src.size,
+                                            _ptr(d), d.shape[0], int(bool(strict)), _ptr(out)))
     return out
 
 
-def count(src, dst, t, deltas, threads: int = 0):
-    """O1: plain adjacency + Lemma 1 summed directly.  Returns [k][8]."""
+def count(src, dst, t, deltas, threads: int = 0, strict: bool = False):
+    """O1: plain adjacency + Lemma 1 summed directly.  Returns [k][8].
+    strict: as for bruteforce."""
     src, dst, t = _edges(src, dst, t)
     d = _deltas(deltas)
     out = np.zeros((d.shape[0], 8), dtype=np.uint64)
-    _check(_load().ttc_oracle_count(_ptr(src), _ptr(dst), _ptr(t), src.size,
-                                    _ptr(d), d.shape[0], int(threads), _ptr(out)))
+    _check(_load().ttc_oracle_count_ex(_ptr(src), _ptr(dst), _ptr(t), src.size,
+                                       _ptr(d), d.shape[0], int(threads), int(bool(strict)), _ptr(out)))
     return out
 
 

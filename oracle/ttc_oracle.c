@@ -20,7 +20,10 @@
  * Readings taken where the paper is silent:
  *   - Ties: the paper assumes unique timestamps (Sec. 3).  Edges are ordered
  *     by the key (t, idx); "t1 < t2 < t3" is read as key order and the three
- *     windows are applied to timestamp differences, inclusive.
+ *     windows are applied to timestamp differences, inclusive.  The strict
+ *     variant (the *_ex entry points with strict = 1) reads Def. 1's
+ *     t1 < t2 < t3 literally instead: a triple whose edges share a timestamp
+ *     is not counted.
  *   - Self-loops never lie on three distinct vertices; they are dropped.
  *   - Duplicate (u, v, t) edges are distinct edges, ordered by idx.
  *   - delta components are taken as given (no normalisation); each is >= 0.
@@ -126,8 +129,16 @@ static int finish(const u128 *acc, uint32_t nd, uint64_t *out) {
 /* ------------------------------------------------------------------------ */
 /* O0: brute force over all edge triples                                     */
 /* ------------------------------------------------------------------------ */
+int ttc_oracle_bruteforce_ex(const uint32_t *src, const uint32_t *dst, const int64_t *t, uint64_t m,
+                             const int64_t *deltas, uint32_t nd, int strict, uint64_t *out);
+
 int ttc_oracle_bruteforce(const uint32_t *src, const uint32_t *dst, const int64_t *t, uint64_t m,
                           const int64_t *deltas, uint32_t nd, uint64_t *out) {
+    return ttc_oracle_bruteforce_ex(src, dst, t, m, deltas, nd, 0, out);
+}
+
+int ttc_oracle_bruteforce_ex(const uint32_t *src, const uint32_t *dst, const int64_t *t, uint64_t m,
+                             const int64_t *deltas, uint32_t nd, int strict, uint64_t *out) {
     if ((m && (!src || !dst || !t)) || !out || (nd && !deltas) || !check_deltas(deltas, nd))
         return ORACLE_ERR_INVALID;
     edge_t *e = (edge_t *)malloc(sizeof(edge_t) * (m ? m : 1));
@@ -157,6 +168,7 @@ int ttc_oracle_bruteforce(const uint32_t *src, const uint32_t *dst, const int64_
                     continue;
                 const int ty = classify(x[0], x[1], x[2]);
                 if (ty < 0) continue;
+                if (strict && !(x[0]->t < x[1]->t && x[1]->t < x[2]->t)) continue;
                 for (uint32_t q = 0; q < nd; q++)
                     if (in_windows(x[0], x[1], x[2], deltas[3 * q], deltas[3 * q + 1], deltas[3 * q + 2]))
                         acc[8 * q + ty] += 1;
@@ -291,14 +303,20 @@ static int64_t count_t_le(const sublist_t *s, i128 bound) {
     return l;
 }
 
+/* first index of `s` after x: by key, or (strict) by time, t > t(x) */
+static int64_t first_after(const sublist_t *s, const edge_t *x, int strict) {
+    return strict ? count_t_le(s, (i128)x->t) : first_key_after(s, x);
+}
+
 /*
  * Lemma 1 for one static triangle with the role assignment (P1, P2, P3) and
  * every direction: sum over e1 in P1, e2 in P2 (key after e1, t2 - t1 <= d12)
  * of #{e3 in P3 (each direction separately): key(e3) > key(e2),
  * t3 <= min(t2 + d23, t1 + d13)}.  Each hit set is classified by Fig. 2.
+ * strict: "after" is t2 > t1 and t3 > t2 instead of key order.
  */
 static void lemma1_roles(const int64_t pr[3], const sublist_t sub[3][2],
-                         const int64_t *deltas, uint32_t nd, u128 *acc) {
+                         const int64_t *deltas, uint32_t nd, int strict, u128 *acc) {
     int64_t maxd12 = 0;
     for (uint32_t q = 0; q < nd; q++) if (deltas[3 * q + 1] > maxd12) maxd12 = deltas[3 * q + 1];
     for (int d1 = 0; d1 < 2; d1++) {
@@ -310,11 +328,11 @@ static void lemma1_roles(const int64_t pr[3], const sublist_t sub[3][2],
                 if (!S1->len || !S2->len || !S3->len) continue;
                 for (int64_t i = 0; i < S1->len; i++) {
                     const edge_t *e1 = S1->e[i];
-                    for (int64_t j = first_key_after(S2, e1); j < S2->len; j++) {
+                    for (int64_t j = first_after(S2, e1, strict); j < S2->len; j++) {
                         const edge_t *e2 = S2->e[j];
                         const i128 gap12 = (i128)e2->t - e1->t;
                         if (gap12 > maxd12) break; /* later e2 are later still */
-                        const int64_t lo3 = first_key_after(S3, e2);
+                        const int64_t lo3 = first_after(S3, e2, strict);
                         if (lo3 >= S3->len) continue;
                         const int ty = classify(e1, e2, S3->e[lo3]);
                         for (uint32_t q = 0; q < nd; q++) {
@@ -334,7 +352,7 @@ static void lemma1_roles(const int64_t pr[3], const sublist_t sub[3][2],
 
 /* all six role assignments of one static triangle {a, b, c} */
 static int count_one_triangle(const graph_t *g, const int64_t p[3], const uint32_t lo_hi[3][2],
-                              const int64_t *deltas, uint32_t nd, u128 *acc) {
+                              const int64_t *deltas, uint32_t nd, int strict, u128 *acc) {
     /* split each pair into its two directions */
     size_t tot = 0;
     for (int i = 0; i < 3; i++) tot += g->pairs[p[i]].len;
@@ -349,7 +367,7 @@ static int count_one_triangle(const graph_t *g, const int64_t p[3], const uint32
         }
     }
     static const int64_t roles[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
-    for (int r = 0; r < 6; r++) lemma1_roles(roles[r], (const sublist_t(*)[2])sub, deltas, nd, acc);
+    for (int r = 0; r < 6; r++) lemma1_roles(roles[r], (const sublist_t(*)[2])sub, deltas, nd, strict, acc);
     free(buf);
     return ORACLE_OK;
 }
@@ -368,18 +386,29 @@ static int threads_or_default(int threads) {
  * a % nparts == part (a sampling aid for timing: the parts partition the
  * triangles, so their counts sum to the full count).
  */
-int ttc_oracle_count_part(const uint32_t *src, const uint32_t *dst, const int64_t *t, uint64_t m,
-                          const int64_t *deltas, uint32_t nd, int threads, uint32_t part, uint32_t nparts,
-                          uint64_t *out);
+static int count_part(const uint32_t *src, const uint32_t *dst, const int64_t *t, uint64_t m,
+                      const int64_t *deltas, uint32_t nd, int threads, uint32_t part, uint32_t nparts, int strict,
+                      uint64_t *out);
 
 int ttc_oracle_count(const uint32_t *src, const uint32_t *dst, const int64_t *t, uint64_t m,
                      const int64_t *deltas, uint32_t nd, int threads, uint64_t *out) {
-    return ttc_oracle_count_part(src, dst, t, m, deltas, nd, threads, 0, 1, out);
+    return count_part(src, dst, t, m, deltas, nd, threads, 0, 1, 0, out);
+}
+
+int ttc_oracle_count_ex(const uint32_t *src, const uint32_t *dst, const int64_t *t, uint64_t m,
+                        const int64_t *deltas, uint32_t nd, int threads, int strict, uint64_t *out) {
+    return count_part(src, dst, t, m, deltas, nd, threads, 0, 1, strict, out);
 }
 
 int ttc_oracle_count_part(const uint32_t *src, const uint32_t *dst, const int64_t *t, uint64_t m,
                           const int64_t *deltas, uint32_t nd, int threads, uint32_t part, uint32_t nparts,
                           uint64_t *out) {
+    return count_part(src, dst, t, m, deltas, nd, threads, part, nparts, 0, out);
+}
+
+static int count_part(const uint32_t *src, const uint32_t *dst, const int64_t *t, uint64_t m,
+                      const int64_t *deltas, uint32_t nd, int threads, uint32_t part, uint32_t nparts, int strict,
+                      uint64_t *out) {
     if (nparts == 0 || part >= nparts) return ORACLE_ERR_INVALID;
     if ((m && (!src || !dst || !t)) || !out || (nd && !deltas) || !check_deltas(deltas, nd))
         return ORACLE_ERR_INVALID;
@@ -407,7 +436,7 @@ int ttc_oracle_count_part(const uint32_t *src, const uint32_t *dst, const int64_
                 if (pbc < 0) continue;
                 const int64_t pp[3] = {g.adj_pair[i], g.adj_pair[j], pbc};
                 const uint32_t lh[3][2] = {{(uint32_t)a, b}, {(uint32_t)a, c}, {b, c}};
-                if (count_one_triangle(&g, pp, lh, deltas, nd, my)) err = 1;
+                if (count_one_triangle(&g, pp, lh, deltas, nd, strict, my)) err = 1;
             }
         }
     }
@@ -448,7 +477,7 @@ int ttc_oracle_count_triangles(const uint32_t *src, const uint32_t *dst, const i
         const int64_t pp[3] = {find_pair(&g, x, y), find_pair(&g, x, z), find_pair(&g, y, z)};
         if (x != y && y != z && pp[0] >= 0 && pp[1] >= 0 && pp[2] >= 0) {
             const uint32_t lh[3][2] = {{x, y}, {x, z}, {y, z}};
-            if (count_one_triangle(&g, pp, lh, deltas, nd, a)) err = 1;
+            if (count_one_triangle(&g, pp, lh, deltas, nd, 0, a)) err = 1;
         }
         for (uint32_t q = 0; q < 8 * nd; q++) {
             if (a[q] > (u128)UINT64_MAX) { ovf = 1; out[8 * nd * i + q] = UINT64_MAX; }

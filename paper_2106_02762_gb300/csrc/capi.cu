@@ -337,7 +337,7 @@ ttc_status ttc_load_ex(const uint32_t *src, const uint32_t *dst, const int64_t *
         lo.labeling = opts->labeling;
         lo.light_max_pairs = opts->light_max_pairs;
         lo.seed = opts->seed;
-        if (lo.flags & ~(TTC_LOAD_DEVICE_INPUT | TTC_LOAD_PROFILE | TTC_LOAD_STREAM))
+        if (lo.flags & ~(TTC_LOAD_DEVICE_INPUT | TTC_LOAD_PROFILE | TTC_LOAD_STREAM | TTC_LOAD_STRICT_TIME))
             fail(TTC_ERR_INVALID, "unknown load flags 0x%x", lo.flags);
     }
     g = new ttc_graph();

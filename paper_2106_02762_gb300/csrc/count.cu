@@ -63,8 +63,7 @@ template <int R>
 struct WarpTris {
     uint32_t excl[LIGHT_WARPS][32 * R + 1];  // exclusive prefix of pair counts
     uint4 lst[LIGHT_WARPS][32 * R];          // A.b, B.b, C.b, C.n
-    uint4 aux[LIGHT_WARPS][32 * R];          // B.n, flip flags, fwd[C.b], fwd[C.b + C.n]
-    float inv[LIGHT_WARPS][32 * R];          // 1 / B.n
+    uint32_t aux[LIGHT_WARPS][32 * R];       // B.n | flip flags << 29 (B.n < 2^20 in the light bin)
     Query q[LIGHT_WARPS][LIGHT_QT];          // MODE 1: the item's query group
 };
 
@@ -80,7 +79,7 @@ struct WarpTris {
 // R > 1 needs G == 1.  Every light triangle has sigma_A * sigma_B below the
 // light threshold (at most 2^20), so a work item has fewer than 2^32 pairs
 // and a pair's index within its triangle is below 2^20.
-template <int MODE, int R>
+template <int MODE, int R, bool ST>
 __global__ void __launch_bounds__(LIGHT_THREADS, MODE == 1 ? 4 : 5)
     light_kernel(const GraphView *__restrict__ gvs, const uint64_t *__restrict__ chunk_pre, uint32_t G,
                  const int64_t *dq, uint32_t nq, unsigned long long *out, unsigned long long *flag,
@@ -152,7 +151,7 @@ __global__ void __launch_bounds__(LIGHT_THREADS, MODE == 1 ? 4 : 5)
             }
         }
         const GraphView &gv = gvs[g];
-        const KeyFmt f{gv.shift, gv.span};
+        const KeyFmt f{gv.shift, gv.span, ST};
         // the group's queries (MODE 1: in the warp's shared slots when the
         // thread's accumulators hold them)
         Query Q0{0, 0, 0};
@@ -164,9 +163,6 @@ __global__ void __launch_bounds__(LIGHT_THREADS, MODE == 1 ? 4 : 5)
             Q0 = load_query(dq, MODE == 0 ? g : 0u);
             gmax = Q0.d13;
         }
-        // with every pair inside the widest window, C's prefix ends are
-        // staged per triangle; otherwise a passing pair loads them
-        const bool wide = gmax >= f.span;
         const uint64_t base = (MODE == 0 && R == 1 ? c - __ldg(chunk_pre + g) : c) * PER;
         const uint64_t lim = MODE == 2 ? nidx : gv.n_light;
         uint32_t np[R];
@@ -182,13 +178,7 @@ __global__ void __launch_bounds__(LIGHT_THREADS, MODE == 1 ? 4 : 5)
                 const uint32_t cb = __ldg(gv.poff + rec.z), cn = __ldg(gv.poff + rec.z + 1) - cb;
                 np[r] = an * bn;
                 wt.lst[w][slot] = make_uint4(ab, bb, cb, cn);
-                uint32_t f0 = 0, fn = 0;
-                if (wide && np[r]) {
-                    f0 = __ldg(gv.fwd + cb);
-                    fn = __ldg(gv.fwd + cb + cn);
-                }
-                wt.aux[w][slot] = make_uint4(bn, rec.w, f0, fn);
-                wt.inv[w][slot] = bn ? __frcp_rn((float)bn) : 0.f;
+                wt.aux[w][slot] = bn | (rec.w << 29);
             }
         }
         uint32_t total = 0;
@@ -212,13 +202,13 @@ __global__ void __launch_bounds__(LIGHT_THREADS, MODE == 1 ? 4 : 5)
 #pragma unroll
             for (uint32_t step = PER / 2; step; step >>= 1)
                 if (wt.excl[w][o + step] <= j) o += step;
-            const uint4 L = wt.lst[w][o], X = wt.aux[w][o];
-            const uint32_t bn = X.x, fl = X.y;
+            const uint4 L = wt.lst[w][o];
+            const uint32_t X = wt.aux[w][o], bn = X & ((1u << 29) - 1), fl = X >> 29;
             const uint32_t loc = j - wt.excl[w][o];
             // loc < 2^20: (loc + 1/2) / bn is at least 1 / (2 bn) from an
             // integer, and the float product is within 2^-3 / bn of it
-            const uint32_t ai = __float2uint_rz(((float)loc + 0.5f) * wt.inv[w][o]), bi = loc - ai * bn;
-            light_count_pair(gv, f, L.x, L.y, L.z, L.w, fl, wide, X.z, X.w, ai, bi, gmax,
+            const uint32_t ai = __float2uint_rz(((float)loc + 0.5f) * __frcp_rn((float)bn)), bi = loc - ai * bn;
+            light_count_pair(gv, f, L.x, L.y, L.z, L.w, fl, false, 0u, 0u, ai, bi, gmax,
                              [&](const CView &C, bool a_first, int64_t rx, int64_t ry, uint32_t code) {
                 if (MODE != 1 || tslots) {
 #pragma unroll
@@ -259,7 +249,9 @@ __global__ void __launch_bounds__(LIGHT_THREADS, MODE == 1 ? 4 : 5)
 __device__ __forceinline__ void phase1_values(const GList &C, const KeyFmt &f, const Query &q, int64_t ke,
                                               uint32_t out[8]) {
     const int64_t re = ke >> f.shift;
-    const int64_t bd[4] = {le_bound(f, re + q.d13), key_bound(ke), lt_bound(f, re - q.d23), lt_bound(f, re - q.d13)};
+    // L(e): C's edges before e, by key or (strict) by time
+    const int64_t bd[4] = {le_bound(f, re + q.d13), f.strict ? lt_bound(f, re) : key_bound(ke),
+                           lt_bound(f, re - q.d23), lt_bound(f, re - q.d13)};
     uint32_t ps[4];
     search_n<4>(C, bd, ps);
     const uint32_t ph = ps[0], pl = ps[1], pr = ps[2], pm = ps[3];
@@ -277,16 +269,21 @@ template <typename OL, typename PF, typename ADD>
 __device__ __forceinline__ void phase2_edge(const OL &O, const GList &C, const KeyFmt &f, const Query &q, int64_t ke,
                                             PF &&pref, ADD &&add) {
     const int64_t re = ke >> f.shift;
-    // searches in C (split by C's direction)
-    const int64_t bc[4] = {key_bound(ke), le_bound(f, re + q.d23), le_bound(f, re + q.d12), lt_bound(f, re - q.d12)};
+    // searches in C (split by C's direction).  C's edges not after e (Ka)
+    // and before e (Kb): the same key position, or (strict) those with
+    // t <= t_e and t < t_e
+    const int64_t bc[4] = {f.strict ? le_bound(f, re) : key_bound(ke), le_bound(f, re + q.d23),
+                           le_bound(f, re + q.d12), lt_bound(f, re - q.d12)};
     uint32_t pc[4];
     search_n<4>(C, bc, pc);
-    const uint32_t posC = pc[0], pH = pc[1], pG = pc[2], pLo = pc[3];
-    const uint32_t K0 = C.d0(posC), H0 = C.d0(pH), G0 = C.d0(pG), Lo0 = C.d0(pLo);
-    const uint32_t Kd[2] = {K0, posC - K0}, Hd[2] = {H0, pH - H0}, Gd[2] = {G0, pG - G0},
-                   Lod[2] = {Lo0, pLo - Lo0};
+    const uint32_t posCa = pc[0], pH = pc[1], pG = pc[2], pLo = pc[3];
+    const uint32_t posCb = f.strict ? C.below(lt_bound(f, re)) : posCa;
+    const uint32_t Ka0 = C.d0(posCa), H0 = C.d0(pH), G0 = C.d0(pG), Lo0 = C.d0(pLo);
+    const uint32_t Kb0 = f.strict ? C.d0(posCb) : Ka0;
+    const uint32_t Ka[2] = {Ka0, posCa - Ka0}, Kb[2] = {Kb0, posCb - Kb0}, Hd[2] = {H0, pH - H0},
+                   Gd[2] = {G0, pG - G0}, Lod[2] = {Lo0, pLo - Lo0};
     // searches in O (merged positions)
-    const int64_t bo[8] = {key_bound(ke),
+    const int64_t bo[8] = {f.strict ? le_bound(f, re) : key_bound(ke),
                            lt_bound(f, re - q.d12),
                            le_bound(f, re + q.d23 - q.d13),
                            le_bound(f, re + min(q.d12, q.d23)),
@@ -296,41 +293,44 @@ __device__ __forceinline__ void phase2_edge(const OL &O, const GList &C, const K
                            le_bound(f, re + q.d23)};
     uint32_t po[8];
     search_n<8>(O, bo, po);
-    const uint32_t posO = po[0];
-    const uint32_t o_lo = min(po[1], posO);
-    const uint32_t o_mid = min(max(po[2], o_lo), posO);
-    const uint32_t r1 = max(po[3], posO);
+    // O's edges before e end at posOb, those after e start at posOa: one
+    // key position, or (strict) t < t_e and t <= t_e
+    const uint32_t posOa = po[0], posOb = f.strict ? O.below(lt_bound(f, re)) : posOa;
+    const uint32_t o_lo = min(po[1], posOb);
+    const uint32_t o_mid = min(max(po[2], o_lo), posOb);
+    const uint32_t r1 = max(po[3], posOa);
     const uint32_t r2 = max(po[4], r1);
     const uint32_t r3 = max(po[5], r2);
-    const uint32_t sp = max(po[6], posO);
+    const uint32_t sp = max(po[6], posOa);
     const uint32_t en = max(po[7], sp);
-    const uint32_t pos[8] = {o_lo, o_mid, posO, r1, r2, r3, sp, en};
-    uint32_t d0s[8];
+    const uint32_t pos[9] = {o_lo, o_mid, posOb, r1, r2, r3, sp, en, posOa};
+    uint32_t d0s[9];
 #pragma unroll
     for (int i = 0; i < 8; i++) d0s[i] = O.d0(pos[i]);
+    d0s[8] = f.strict ? O.d0(posOa) : d0s[2];
 #pragma unroll
     for (uint32_t dO = 0; dO < 2; dO++) {
         // own-direction-dO ranks of the merged positions in O
-        uint32_t c[8];
+        uint32_t c[9];
 #pragma unroll
-        for (int i = 0; i < 8; i++) c[i] = dO ? pos[i] - d0s[i] : d0s[i];
-        const uint32_t c_lo = c[0], c_mid = c[1], c_pos = c[2], c_r1 = c[3], c_r2 = c[4], c_r3 = c[5], c_sp = c[6],
-                       c_en = c[7];
+        for (int i = 0; i < 9; i++) c[i] = dO ? pos[i] - d0s[i] : d0s[i];
+        const uint32_t c_lo = c[0], c_mid = c[1], c_pb = c[2], c_r1 = c[3], c_r2 = c[4], c_r3 = c[5], c_sp = c[6],
+                       c_en = c[7], c_pa = c[8];
 #pragma unroll
         for (uint32_t dC = 0; dC < 2; dC++) {
             // (1) e second, O's edge first, C third: Alg. 2 (pi_2 if e is on A, pi_1 if on B)
             {
                 const unsigned long long hsum = pref(dO, 0 + dC, c_mid) - pref(dO, 0 + dC, c_lo);
-                const unsigned long long n = hsum + (unsigned long long)Hd[dC] * (c_pos - c_mid) -
-                                             (unsigned long long)Kd[dC] * (c_pos - c_lo);
+                const unsigned long long n = hsum + (unsigned long long)Hd[dC] * (c_pb - c_mid) -
+                                             (unsigned long long)Ka[dC] * (c_pb - c_lo);
                 add(dO, dC, PI2, PI1, n);
             }
             // (2) e first, C second, O's edge third: Alg. 3 (pi_3 / pi_4)
             {
-                unsigned long long n = pref(dO, 2 + dC, c_r1) - pref(dO, 2 + dC, c_pos) -
-                                       (unsigned long long)Kd[dC] * (c_r1 - c_pos);
+                unsigned long long n = pref(dO, 2 + dC, c_r1) - pref(dO, 2 + dC, c_pa) -
+                                       (unsigned long long)Ka[dC] * (c_r1 - c_pa);
                 if (q.d12 <= q.d23) {
-                    n += (unsigned long long)(Gd[dC] - Kd[dC]) * (c_r2 - c_r1);
+                    n += (unsigned long long)(Gd[dC] - Ka[dC]) * (c_r2 - c_r1);
                 } else {
                     n += (pref(dO, 2 + dC, c_r2) - pref(dO, 2 + dC, c_r1)) -
                          (pref(dO, 4 + dC, c_r2) - pref(dO, 4 + dC, c_r1));
@@ -340,8 +340,8 @@ __device__ __forceinline__ void phase2_edge(const OL &O, const GList &C, const K
             }
             // (3) C first, e second, O's edge third: Alg. 4 (pi_5 / pi_6)
             {
-                unsigned long long n = (unsigned long long)(Kd[dC] - Lod[dC]) * (c_sp - c_pos);
-                n += (unsigned long long)Kd[dC] * (c_en - c_sp) - (pref(dO, 6 + dC, c_en) - pref(dO, 6 + dC, c_sp));
+                unsigned long long n = (unsigned long long)(Kb[dC] - Lod[dC]) * (c_sp - c_pa);
+                n += (unsigned long long)Kb[dC] * (c_en - c_sp) - (pref(dO, 6 + dC, c_en) - pref(dO, 6 + dC, c_sp));
                 add(dO, dC, PI5, PI6, n);
             }
         }
@@ -392,7 +392,7 @@ __device__ __forceinline__ uint32_t block_excl_scan_u32(uint32_t v, uint32_t *tm
 // One CTA per heavy triangle of the CTA class, over a table of graphs.  MODE
 // as light_kernel; heavy_pre[g] = first CTA-class record of graph g in the
 // global index space (G + 1 entries).
-template <typename P, int MODE>
+template <typename P, int MODE, bool ST>
 __global__ void __launch_bounds__(HEAVY_THREADS)
     heavy_fused_kernel(const GraphView *__restrict__ gvs, const uint64_t *__restrict__ heavy_pre, uint32_t G,
                        const int64_t *dq, uint32_t nq, unsigned long long *out, unsigned long long *flag,
@@ -426,7 +426,7 @@ __global__ void __launch_bounds__(HEAVY_THREADS)
             }
         }
         const GraphView &gv = gvs[g];
-        const KeyFmt f{gv.shift, gv.span};
+        const KeyFmt f{gv.shift, gv.span, ST};
         const uint64_t hl = MODE == 2 ? idx[h] : (MODE == 0 ? h - __ldg(heavy_pre + g) : h);
         const uint4 r = __ldg(gv.tri + gv.n_light + gv.n_hwarp + hl);
         const GList A = glist(gv, r.x, r.w & TriRec::FLIP_A);
@@ -540,7 +540,7 @@ struct WarpCap {
     }
 };
 
-template <typename P, int MODE>
+template <typename P, int MODE, bool ST>
 __global__ void __launch_bounds__(HEAVY_THREADS)
     heavy_warp_kernel(const GraphView *__restrict__ gvs, const uint64_t *__restrict__ hw_pre, uint32_t G,
                       const int64_t *dq, uint32_t nq, unsigned long long *out, unsigned long long *flag,
@@ -577,7 +577,7 @@ __global__ void __launch_bounds__(HEAVY_THREADS)
         }
         const GraphView &gv = gvs[g];
         if ((sizeof(P) == 8) != (gv.wide != 0)) continue;  // the other width's launch takes it
-        const KeyFmt f{gv.shift, gv.span};
+        const KeyFmt f{gv.shift, gv.span, ST};
         const uint64_t hl = MODE == 2 ? idx[h] : (MODE == 0 ? h - __ldg(hw_pre + g) : h);
         const uint4 r = __ldg(gv.tri + gv.n_light + hl);
         const GList A = glist(gv, r.x, r.w & TriRec::FLIP_A);
@@ -712,10 +712,10 @@ __device__ __forceinline__ uint64_t seg_base(const HugeTri &t, uint32_t z, uint3
     return b;
 }
 
-template <typename P>
+template <typename P, bool ST>
 __global__ void __launch_bounds__(HEAVY_THREADS) huge_phase1(HugeArgs a, const int64_t *dq) {
     const Query q = load_query(dq, 0);
-    const KeyFmt f{a.gv.shift, a.gv.span};
+    const KeyFmt f{a.gv.shift, a.gv.span, ST};
     P *pre = static_cast<P *>(a.pre);
     for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < a.total;
          e += (uint64_t)gridDim.x * blockDim.x) {
@@ -780,7 +780,7 @@ __global__ void __launch_bounds__(HEAVY_THREADS) huge_scan(HugeArgs a) {
     }
 }
 
-template <typename P>
+template <typename P, bool ST>
 __global__ void __launch_bounds__(HEAVY_THREADS)
     huge_phase2(HugeArgs a, const int64_t *dq, unsigned long long *out, unsigned long long *flag) {
     __shared__ unsigned long long s_acc[8][256];
@@ -788,7 +788,7 @@ __global__ void __launch_bounds__(HEAVY_THREADS)
     for (int j = 0; j < 8; j++) s_acc[j][threadIdx.x] = 0;
     unsigned ovf = 0;
     const Query q = load_query(dq, 0);
-    const KeyFmt f{a.gv.shift, a.gv.span};
+    const KeyFmt f{a.gv.shift, a.gv.span, ST};
     const P *pre = static_cast<const P *>(a.pre);
     const uint64_t iters = (a.total + (uint64_t)gridDim.x * blockDim.x - 1) / ((uint64_t)gridDim.x * blockDim.x);
     for (uint64_t it = 0; it < iters; it++) {  // uniform trip count (warp_flush needs full warps)
@@ -826,7 +826,8 @@ void run_huge(ttc_graph *g, const HugeArgs &ha, const int64_t *dq_one, unsigned 
     if (!ha.nh) return;
     const unsigned grid = (unsigned)(sm_count() * 8);
     prof_begin(g, s, "huge_phase1");
-    huge_phase1<P><<<grid, HEAVY_THREADS, 0, s>>>(ha, dq_one);
+    if (ha.gv.strict) huge_phase1<P, true><<<grid, HEAVY_THREADS, 0, s>>>(ha, dq_one);
+    else huge_phase1<P, false><<<grid, HEAVY_THREADS, 0, s>>>(ha, dq_one);
     TTC_LAUNCH_CHECK();
     prof_end(g, s);
     prof_begin(g, s, "huge_scan");
@@ -834,7 +835,8 @@ void run_huge(ttc_graph *g, const HugeArgs &ha, const int64_t *dq_one, unsigned 
     TTC_LAUNCH_CHECK();
     prof_end(g, s);
     prof_begin(g, s, "huge_phase2");
-    huge_phase2<P><<<grid, HEAVY_THREADS, 0, s>>>(ha, dq_one, out, flag);
+    if (ha.gv.strict) huge_phase2<P, true><<<grid, HEAVY_THREADS, 0, s>>>(ha, dq_one, out, flag);
+    else huge_phase2<P, false><<<grid, HEAVY_THREADS, 0, s>>>(ha, dq_one, out, flag);
     TTC_LAUNCH_CHECK();
     prof_end(g, s);
 }
@@ -863,7 +865,7 @@ unsigned heavy_grid(uint64_t items, int per_sm = 2) {
     return (unsigned)(items < 1 ? 1 : items < cap ? items : cap);
 }
 
-template <typename P, int MODE>
+template <typename P, int MODE, bool ST>
 void launch_fused(const GraphView *gvs, const uint64_t *heavy_pre, uint32_t G, uint64_t items, const int64_t *dq,
                   uint32_t nq, unsigned long long *out, unsigned long long *flag, const uint64_t *idx,
                   uint64_t nidx, cudaStream_t s, int per_sm = 2) {
@@ -871,16 +873,16 @@ void launch_fused(const GraphView *gvs, const uint64_t *heavy_pre, uint32_t G, u
     int dev = 0;
     TTC_CUDA(cudaGetDevice(&dev));
     if (configured_device != dev) {
-        TTC_CUDA(cudaFuncSetAttribute(heavy_fused_kernel<P, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        TTC_CUDA(cudaFuncSetAttribute(heavy_fused_kernel<P, MODE, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)FusedCap<P>::bytes(1, MAX_BATCH_SMEM_Q)));
         configured_device = dev;
     }
-    heavy_fused_kernel<P, MODE><<<heavy_grid(items, per_sm), HEAVY_THREADS, FusedCap<P>::bytes(MODE, nq), s>>>(
+    heavy_fused_kernel<P, MODE, ST><<<heavy_grid(items, per_sm), HEAVY_THREADS, FusedCap<P>::bytes(MODE, nq), s>>>(
         gvs, heavy_pre, G, dq, nq, out, flag, idx, nidx);
     TTC_LAUNCH_CHECK();
 }
 
-template <typename P, int MODE>
+template <typename P, int MODE, bool ST>
 void launch_warp(const GraphView *gvs, const uint64_t *hw_pre, uint32_t G, uint64_t items, const int64_t *dq,
                  uint32_t nq, unsigned long long *out, unsigned long long *flag, const uint64_t *idx, uint64_t nidx,
                  cudaStream_t s, int per_sm = 4) {
@@ -888,32 +890,49 @@ void launch_warp(const GraphView *gvs, const uint64_t *hw_pre, uint32_t G, uint6
     int dev = 0;
     TTC_CUDA(cudaGetDevice(&dev));
     if (configured_device != dev) {
-        TTC_CUDA(cudaFuncSetAttribute(heavy_warp_kernel<P, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        TTC_CUDA(cudaFuncSetAttribute(heavy_warp_kernel<P, MODE, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)WarpCap<P>::bytes(1, MAX_BATCH_SMEM_Q)));
         configured_device = dev;
     }
     const uint64_t want = (items + HEAVY_WARPS - 1) / HEAVY_WARPS;
     const uint64_t cap = (uint64_t)sm_count() * (uint64_t)per_sm;
     const unsigned grid = (unsigned)(want < 1 ? 1 : want < cap ? want : cap);
-    heavy_warp_kernel<P, MODE><<<grid, HEAVY_THREADS, WarpCap<P>::bytes(MODE, nq), s>>>(gvs, hw_pre, G, dq, nq, out,
+    heavy_warp_kernel<P, MODE, ST><<<grid, HEAVY_THREADS, WarpCap<P>::bytes(MODE, nq), s>>>(gvs, hw_pre, G, dq, nq, out,
                                                                                        flag, idx, nidx);
     TTC_LAUNCH_CHECK();
 }
 
+// kind: bit 0 = 64-bit prefix sums (wide lists), bit 1 = strict time order
+inline int heavy_kind(int wide, bool strict) { return (wide ? 1 : 0) | (strict ? 2 : 0); }
+
 template <int MODE>
-void launch_warp_any(int wide, const GraphView *gvs, const uint64_t *hw_pre, uint32_t G, uint64_t items,
+void launch_warp_any(int kind, const GraphView *gvs, const uint64_t *hw_pre, uint32_t G, uint64_t items,
                      const int64_t *dq, uint32_t nq, unsigned long long *out, unsigned long long *flag,
                      const uint64_t *idx, uint64_t nidx, cudaStream_t s, int per_sm = 4) {
-    if (wide) launch_warp<unsigned long long, MODE>(gvs, hw_pre, G, items, dq, nq, out, flag, idx, nidx, s, per_sm);
-    else launch_warp<uint32_t, MODE>(gvs, hw_pre, G, items, dq, nq, out, flag, idx, nidx, s, per_sm);
+    switch (kind & 3) {
+        case 0: launch_warp<uint32_t, MODE, false>(gvs, hw_pre, G, items, dq, nq, out, flag, idx, nidx, s, per_sm); break;
+        case 1: launch_warp<unsigned long long, MODE, false>(gvs, hw_pre, G, items, dq, nq, out, flag, idx, nidx, s,
+                                                            per_sm); break;
+        case 2: launch_warp<uint32_t, MODE, true>(gvs, hw_pre, G, items, dq, nq, out, flag, idx, nidx, s, per_sm); break;
+        default: launch_warp<unsigned long long, MODE, true>(gvs, hw_pre, G, items, dq, nq, out, flag, idx, nidx, s,
+                                                             per_sm);
+    }
 }
 
 template <int MODE>
-void launch_fused_any(int wide, const GraphView *gvs, const uint64_t *heavy_pre, uint32_t G, uint64_t items,
+void launch_fused_any(int kind, const GraphView *gvs, const uint64_t *heavy_pre, uint32_t G, uint64_t items,
                       const int64_t *dq, uint32_t nq, unsigned long long *out, unsigned long long *flag,
                       const uint64_t *idx, uint64_t nidx, cudaStream_t s, int per_sm = 2) {
-    if (wide) launch_fused<unsigned long long, MODE>(gvs, heavy_pre, G, items, dq, nq, out, flag, idx, nidx, s, per_sm);
-    else launch_fused<uint32_t, MODE>(gvs, heavy_pre, G, items, dq, nq, out, flag, idx, nidx, s, per_sm);
+    switch (kind & 3) {
+        case 0: launch_fused<uint32_t, MODE, false>(gvs, heavy_pre, G, items, dq, nq, out, flag, idx, nidx, s, per_sm);
+            break;
+        case 1: launch_fused<unsigned long long, MODE, false>(gvs, heavy_pre, G, items, dq, nq, out, flag, idx, nidx, s,
+                                                              per_sm); break;
+        case 2: launch_fused<uint32_t, MODE, true>(gvs, heavy_pre, G, items, dq, nq, out, flag, idx, nidx, s, per_sm);
+            break;
+        default: launch_fused<unsigned long long, MODE, true>(gvs, heavy_pre, G, items, dq, nq, out, flag, idx, nidx, s,
+                                                              per_sm);
+    }
 }
 
 // One query (acc[8] + flag) or a batch of k (acc[k][8] + flag at acc[8 k])
@@ -932,16 +951,16 @@ void count_graph(ttc_graph *g, const int64_t *dq, uint32_t k, unsigned long long
         const int mode = k == 1 ? 0 : 1;
         if (nw) {
             prof_begin(g, s, mode ? "heavy_warp_batch" : "heavy_warp");
-            if (mode) launch_warp_any<1>(g->heavy_wide, gv, hw_pre, 1, nw, dq + 3 * (size_t)q0, nq,
+            if (mode) launch_warp_any<1>(heavy_kind(g->heavy_wide, g->strict), gv, hw_pre, 1, nw, dq + 3 * (size_t)q0, nq,
                                          acc + 8 * (size_t)q0, flag, nullptr, 0, s);
-            else launch_warp_any<0>(g->heavy_wide, gv, hw_pre, 1, nw, dq, 1, acc, flag, nullptr, 0, s);
+            else launch_warp_any<0>(heavy_kind(g->heavy_wide, g->strict), gv, hw_pre, 1, nw, dq, 1, acc, flag, nullptr, 0, s);
             prof_end(g, s);
         }
         if (nc) {
             prof_begin(g, s, mode ? "heavy_cta_batch" : "heavy_cta");
-            if (mode) launch_fused_any<1>(g->heavy_wide, gv, hc_pre, 1, nc, dq + 3 * (size_t)q0, nq,
+            if (mode) launch_fused_any<1>(heavy_kind(g->heavy_wide, g->strict), gv, hc_pre, 1, nc, dq + 3 * (size_t)q0, nq,
                                           acc + 8 * (size_t)q0, flag, nullptr, 0, s);
-            else launch_fused_any<0>(g->heavy_wide, gv, hc_pre, 1, nc, dq, 1, acc, flag, nullptr, 0, s);
+            else launch_fused_any<0>(heavy_kind(g->heavy_wide, g->strict), gv, hc_pre, 1, nc, dq, 1, acc, flag, nullptr, 0, s);
             prof_end(g, s);
         }
     }
@@ -986,8 +1005,12 @@ void count_light_records(ttc_graph *g, const GraphView *gv, const uint64_t *ligh
     unsigned long long *flag = acc + 8 * (size_t)k;
     if (k == 1) {
         prof_begin(g, s, "light");
-        light_kernel<0, 1><<<light_grid((nl + 31) / 32), LIGHT_THREADS, 0, s>>>(gv, light_pre, 1, dq, 1, acc, flag,
-                                                                              nullptr, 0);
+        if (g->strict)
+            light_kernel<0, 1, true><<<light_grid((nl + 31) / 32), LIGHT_THREADS, 0, s>>>(gv, light_pre, 1, dq, 1, acc,
+                                                                                        flag, nullptr, 0);
+        else
+            light_kernel<0, 1, false><<<light_grid((nl + 31) / 32), LIGHT_THREADS, 0, s>>>(gv, light_pre, 1, dq, 1, acc,
+                                                                                         flag, nullptr, 0);
         TTC_LAUNCH_CHECK();
         prof_end(g, s);
         return;
@@ -1007,12 +1030,20 @@ void count_light_records(ttc_graph *g, const GraphView *gv, const uint64_t *ligh
         int dev = 0;
         TTC_CUDA(cudaGetDevice(&dev));
         if (light1_device != dev) {
-            TTC_CUDA(cudaFuncSetAttribute(light_kernel<1, LIGHT_BATCH_R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)(MAX_BATCH_SMEM_Q * 64 + LIGHT_QT * 8 * LIGHT_THREADS * 4)));
+            const int most = (int)(MAX_BATCH_SMEM_Q * 64 + LIGHT_QT * 8 * LIGHT_THREADS * 4);
+            TTC_CUDA(cudaFuncSetAttribute(light_kernel<1, LIGHT_BATCH_R, false>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, most));
+            TTC_CUDA(cudaFuncSetAttribute(light_kernel<1, LIGHT_BATCH_R, true>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, most));
             light1_device = dev;
         }
-        light_kernel<1, LIGHT_BATCH_R><<<light_grid(chunks * ((nq + qpw - 1) / qpw)), LIGHT_THREADS, smem, s>>>(
-            gv, light_pre, 1, dq + 3 * (size_t)q0, nq, acc + 8 * (size_t)q0, flag, nullptr, 0, qpw);
+        const unsigned grid = light_grid(chunks * ((nq + qpw - 1) / qpw));
+        if (g->strict)
+            light_kernel<1, LIGHT_BATCH_R, true><<<grid, LIGHT_THREADS, smem, s>>>(
+                gv, light_pre, 1, dq + 3 * (size_t)q0, nq, acc + 8 * (size_t)q0, flag, nullptr, 0, qpw);
+        else
+            light_kernel<1, LIGHT_BATCH_R, false><<<grid, LIGHT_THREADS, smem, s>>>(
+                gv, light_pre, 1, dq + 3 * (size_t)q0, nq, acc + 8 * (size_t)q0, flag, nullptr, 0, qpw);
         TTC_LAUNCH_CHECK();
         prof_end(g, s);
     }
@@ -1081,15 +1112,19 @@ void count_sample(ttc_graph *g, const int64_t *dq, uint64_t first, uint64_t stri
     DevBuf<unsigned long long> flag(1, s);
     TTC_CUDA(cudaMemsetAsync(flag.get(), 0, 8, s));
     if (nlc) {
-        light_kernel<2, 1><<<light_grid((nlc + 31) / 32), LIGHT_THREADS, 0, s>>>(
-            g->view.get(), g->prefix.get(), 1, dq, 1, d_out.get(), flag.get(), d_idx.get(), nlc);
+        if (g->strict)
+            light_kernel<2, 1, true><<<light_grid((nlc + 31) / 32), LIGHT_THREADS, 0, s>>>(
+                g->view.get(), g->prefix.get(), 1, dq, 1, d_out.get(), flag.get(), d_idx.get(), nlc);
+        else
+            light_kernel<2, 1, false><<<light_grid((nlc + 31) / 32), LIGHT_THREADS, 0, s>>>(
+                g->view.get(), g->prefix.get(), 1, dq, 1, d_out.get(), flag.get(), d_idx.get(), nlc);
         TTC_LAUNCH_CHECK();
     }
     if (nwc)
-        launch_warp_any<2>(g->heavy_wide, g->view.get(), g->prefix.get() + 2, 1, nwc, dq, 1, d_out.get() + 8 * nlc,
+        launch_warp_any<2>(heavy_kind(g->heavy_wide, g->strict), g->view.get(), g->prefix.get() + 2, 1, nwc, dq, 1, d_out.get() + 8 * nlc,
                            flag.get(), d_idx.get() + nlc, nwc, s);
     if (ncc)
-        launch_fused_any<2>(g->heavy_wide, g->view.get(), g->prefix.get() + 4, 1, ncc, dq, 1,
+        launch_fused_any<2>(heavy_kind(g->heavy_wide, g->strict), g->view.get(), g->prefix.get() + 4, 1, ncc, dq, 1,
                             d_out.get() + 8 * (nlc + nwc), flag.get(), d_idx.get() + nlc + nwc, ncc, s);
     if (nhc) {
         DevBuf<uint4> sub(nhc, s);
@@ -1131,17 +1166,21 @@ void count_multi_launch(const MultiTable &t, const int64_t *dq, unsigned long lo
                         int heavy_per_sm, cudaStream_t s) {
     unsigned long long *flag = acc + 8 * (size_t)t.G;
     if (t.chunks) {
-        light_kernel<0, 1><<<light_grid(t.chunks, light_per_sm), LIGHT_THREADS, 0, s>>>(t.gvs, t.chunk_pre, t.G, dq, 1,
-                                                                                     acc, flag, nullptr, 0);
+        if (t.strict)
+            light_kernel<0, 1, true><<<light_grid(t.chunks, light_per_sm), LIGHT_THREADS, 0, s>>>(
+                t.gvs, t.chunk_pre, t.G, dq, 1, acc, flag, nullptr, 0);
+        else
+            light_kernel<0, 1, false><<<light_grid(t.chunks, light_per_sm), LIGHT_THREADS, 0, s>>>(
+                t.gvs, t.chunk_pre, t.G, dq, 1, acc, flag, nullptr, 0);
         TTC_LAUNCH_CHECK();
     }
     for (int wide = 0; wide < 2; wide++) {
         if (!(wide ? t.any_wide : t.any_narrow)) continue;
         if (t.hwarp)
-            launch_warp_any<0>(wide, t.gvs, t.hwarp_pre, t.G, t.hwarp, dq, 1, acc, flag, nullptr, 0, s,
+            launch_warp_any<0>(heavy_kind(wide, t.strict), t.gvs, t.hwarp_pre, t.G, t.hwarp, dq, 1, acc, flag, nullptr, 0, s,
                                2 * heavy_per_sm);
         if (t.hcta)
-            launch_fused_any<0>(wide, t.gvs, t.hcta_pre, t.G, t.hcta, dq, 1, acc, flag, nullptr, 0, s, heavy_per_sm);
+            launch_fused_any<0>(heavy_kind(wide, t.strict), t.gvs, t.hcta_pre, t.G, t.hcta, dq, 1, acc, flag, nullptr, 0, s, heavy_per_sm);
     }
 }
 

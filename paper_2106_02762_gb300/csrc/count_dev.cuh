@@ -122,6 +122,9 @@ struct SList {
 struct KeyFmt {
     int shift;
     int64_t span;
+    // Def. 1's t1 < t2 < t3 read literally: "after" is a later timestamp,
+    // not a later key (t, input index)
+    bool strict;
 };
 // #{e in L : key(e) < key(x)} for an edge x not in L
 template <typename L>
@@ -286,7 +289,7 @@ struct CView {
 template <typename Acc>
 __device__ __forceinline__ void light_pair(const CView &C, const KeyFmt &f, const Query &q, bool xa, int64_t rx,
                                            int64_t ry, uint32_t code, Acc &&acc) {
-    if (q.d12 >= f.span && q.d23 >= f.span) {
+    if (!f.strict && q.d12 >= f.span && q.d23 >= f.span) {
         // every window covers the graph's whole time span (then so does d13
         // >= d12): C's edges after y, between x and y, and before x make the
         // three cases whole
@@ -301,6 +304,11 @@ __device__ __forceinline__ void light_pair(const CView &C, const KeyFmt &f, cons
         return;
     }
     const int64_t gap = ry - rx;
+    if (f.strict && gap == 0) return;  // x and y at one time: no strict order
+    // C's edges after y (from ay on) and before y (below by), likewise for x:
+    // by key, or (strict) by time
+    const uint32_t ay = f.strict ? cnt_le(C, f, ry) : C.py, by = f.strict ? cnt_lt(C, f, ry) : C.py;
+    const uint32_t ax = f.strict ? cnt_le(C, f, rx) : C.px, bx = f.strict ? cnt_lt(C, f, rx) : C.px;
     auto add = [&](uint32_t pack, uint32_t lo, uint32_t hi) {
         const uint32_t n0 = C.d0_range(lo, hi);
         acc(type_in(pack, code), n0);
@@ -308,16 +316,16 @@ __device__ __forceinline__ void light_pair(const CView &C, const KeyFmt &f, cons
     };
     if (gap <= q.d12) {  // C third
         const uint32_t hi = cnt_le(C, f, min(ry + q.d23, rx + q.d13));
-        if (hi > C.py) add(xa ? TP1 : TP2, C.py, hi);
+        if (hi > ay) add(xa ? TP1 : TP2, ay, hi);
     }
     if (gap <= q.d13) {  // C second
-        const uint32_t lo = max(C.px, cnt_lt(C, f, ry - q.d23));
-        const uint32_t hi = min(C.py, cnt_le(C, f, rx + q.d12));
+        const uint32_t lo = max(ax, cnt_lt(C, f, ry - q.d23));
+        const uint32_t hi = min(by, cnt_le(C, f, rx + q.d12));
         if (hi > lo) add(xa ? TP3 : TP4, lo, hi);
     }
     if (gap <= q.d23) {  // C first
         const uint32_t lo = cnt_lt(C, f, max(rx - q.d12, ry - q.d13));
-        if (C.px > lo) add(xa ? TP5 : TP6, lo, C.px);
+        if (bx > lo) add(xa ? TP5 : TP6, lo, bx);
     }
 }
 

@@ -36,6 +36,7 @@ struct GraphView {
     int64_t span;
     int shift;
     int wide;  // 64-bit prefix sums needed (some list has >= 65536 edges)
+    int strict;  // TTC_LOAD_STRICT_TIME: a triple counts only if its times strictly increase
 };
 
 struct ttc_graph {
@@ -45,6 +46,7 @@ struct ttc_graph {
     ttc_graph_stats st{};
     uint32_t labeling = 0;
     uint32_t light_max_pairs = 0;
+    bool strict = false;  // TTC_LOAD_STRICT_TIME
 
     int64_t tmin = 0;   // smallest timestamp
     int64_t span = 0;   // largest minus smallest timestamp
@@ -151,6 +153,7 @@ struct MultiTable {
     const uint64_t *chunk_pre, *hwarp_pre, *hcta_pre;  // exclusive prefixes over the graphs (G + 1)
     uint64_t chunks, hwarp, hcta;                       // their totals
     int any_narrow, any_wide;                           // prefix widths present in the heavy bins
+    bool strict;                                        // TTC_LOAD_STRICT_TIME (all graphs alike)
 };
 void count_multi_launch(const MultiTable &t, const int64_t *dq, unsigned long long *acc, int light_per_sm,
                         int heavy_per_sm, cudaStream_t s);

@@ -1737,6 +1737,7 @@ static void set_view(ttc_graph *g, cudaStream_t s) {
     v.span = g->span;
     v.shift = g->shift;
     v.wide = g->heavy_wide;
+    v.strict = g->strict ? 1 : 0;
     g->view.alloc(1, s);
     g->prefix.alloc(6, s);
     const uint64_t pre[6] = {0, (v.n_light + 31) / 32, 0, v.n_hwarp, 0, v.n_hcta};
@@ -1840,6 +1841,7 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
     g->labeling = opt.labeling;
     // the light path decodes a pair's index within its triangle in float
     // arithmetic, exact below 2^20 pairs per triangle
+    g->strict = (opt.flags & TTC_LOAD_STRICT_TIME) != 0;
     g->light_max_pairs = opt.light_max_pairs ? std::min<uint32_t>(opt.light_max_pairs, 1u << 20)
                                              : default_light_max_pairs();
     if (opt.orientation > TTC_ORIENT_RANDOM) fail(TTC_ERR_INVALID, "unknown orientation %u", opt.orientation);

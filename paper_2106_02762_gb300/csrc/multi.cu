@@ -225,6 +225,9 @@ Plan *build_plan(ttc_graph *const *gs, uint32_t G) {
     for (uint32_t i = 0; i < G; i++) {
         ttc_graph *g = gs[i];
         if (g->device != p->device) fail(TTC_ERR_INVALID, "graph %u lives on another device", i);
+        if (g->strict != gs[0]->strict)
+            fail(TTC_ERR_INVALID, "graph %u reads ties differently (TTC_LOAD_STRICT_TIME) from graph 0", i);
+        t.strict = gs[0]->strict;
         // make sure the graph's own stream has finished building it
         TTC_CUDA(cudaStreamSynchronize(g->stream));
         views[i] = g->view_host;

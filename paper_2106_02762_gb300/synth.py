@@ -183,6 +183,15 @@ def large_plain(seed: int = MASTER_SEED + 2, scale: float = 1.0):
     return power_law_temporal(seed, n, pairs, 2.1, 2.0, 10_000, 6.0, 2.0, T_SPAN_2_31)
 
 
+def large_plain_zipf15(seed: int = MASTER_SEED + 2, scale: float = 1.0):
+    """The power-law workload with the multiplicity exponent taken literally:
+    pmf k^-1.5 on [1, 1e4] (mean about 77, so about 766M edges at scale 1);
+    the same skeleton and timestamps recipe as ``large_plain``."""
+    n = max(16, int(round(1_000_000 * scale)))
+    pairs = max(8, int(round(10_000_000 * scale)))
+    return power_law_temporal(seed, n, pairs, 2.1, 1.5, 10_000, 6.0, 2.0, T_SPAN_2_31)
+
+
 LARGE_PLAIN_DELTA = (86400, 43200, 43200)
 LARGE_PLAIN_DELTA_UNBOUNDED = (1 << 31, 1 << 31, 1 << 31)
 

@@ -25,6 +25,7 @@ STATUS = {-1: "INVALID", -2: "RANGE", -3: "NOMEM", -4: "CUDA", -5: "TIMEOUT", -6
 LOAD_DEVICE_INPUT = 1
 LOAD_PROFILE = 2
 LOAD_STREAM = 4
+LOAD_STRICT_TIME = 8
 ORIENT_DEGENERACY, ORIENT_ID, ORIENT_DEGREE, ORIENT_RANDOM = 0, 1, 2, 3
 LABEL_HEAVIEST_VW, LABEL_SOURCE = 0, 1
 
@@ -170,14 +171,18 @@ class Graph:
     """A device-resident temporal graph (``ttc_load_ex``)."""
 
     def __init__(self, src, dst, t, orientation=ORIENT_DEGENERACY, labeling=LABEL_HEAVIEST_VW,
-                 light_max_pairs=0, seed=0, stream=None, profile_load=False, streamed=False):
+                 light_max_pairs=0, seed=0, stream=None, profile_load=False, streamed=False, strict_time=False):
         """streamed: TTC_LOAD_STREAM (no light-triangle list; every count
-        enumerates the triangles again and counts light ones as it finds them)."""
+        enumerates the triangles again and counts light ones as it finds them).
+        strict_time: TTC_LOAD_STRICT_TIME (count a triple only if its three
+        timestamps strictly increase)."""
         ptrs, m, flags, keep = _edge_ptrs(src, dst, t)
         if profile_load:
             flags |= LOAD_PROFILE
         if streamed:
             flags |= LOAD_STREAM
+        if strict_time:
+            flags |= LOAD_STRICT_TIME
         opts = LoadOpts(flags, orientation, labeling, light_max_pairs, seed, stream)
         h = ctypes.c_void_p()
         check(lib().ttc_load_ex(ptrs[0], ptrs[1], ptrs[2], m, ctypes.byref(opts), ctypes.byref(h)))

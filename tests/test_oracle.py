@@ -268,3 +268,47 @@ def test_parts_partition_the_count():
     total = oracle.count(s, d, t, deltas)
     parts = sum(oracle.count_part(s, d, t, deltas, p, 5) for p in range(5))
     assert (parts == total).all()
+
+
+# --------------------------------------------------------------------------
+# strict variant: Def. 1's t1 < t2 < t3 read literally
+# --------------------------------------------------------------------------
+def test_strict_o1_matches_strict_bruteforce():
+    # O0 drops a key-ordered triple unless its timestamps strictly increase;
+    # O1 starts each later role after the earlier edge's time instead of its
+    # key.  Tiny graphs with timestamps in [0, 6) tie often.
+    ds = [(5, 3, 3), (0, 0, 0), (2, 1, 2), (BIG, BIG, BIG), (4, 0, 4)]
+    for seed in range(40):
+        s, d, t = synth.random_tiny(100 + seed, 6, 30, 6)
+        assert (oracle.count(s, d, t, ds, strict=True) == oracle.bruteforce(s, d, t, ds, strict=True)).all(), seed
+
+
+def test_strict_equals_key_order_without_ties():
+    ds = [(5, 3, 3), (BIG, BIG, BIG)]
+    for seed in range(10):
+        s, d, _ = synth.random_tiny(200 + seed, 7, 40, 6)
+        t = np.random.default_rng(seed).permutation(s.size).astype(np.int64)  # all distinct
+        assert (oracle.count(s, d, t, ds, strict=True) == oracle.count(s, d, t, ds)).all()
+
+
+def test_strict_counts_nothing_when_all_times_are_equal():
+    s, d, _ = synth.random_tiny(7, 6, 40, 6)
+    t = np.zeros(s.size, dtype=np.int64)
+    assert oracle.count(s, d, t, [(BIG, BIG, BIG)], strict=True).sum() == 0
+    # key order counts every triple on a triangle exactly once instead
+    assert oracle.count(s, d, t, [(BIG, BIG, BIG)]).sum() == oracle.stats(s, d, t)["prod"]
+
+
+def test_strict_hand_case():
+    # the first hand case of Def. 1 (T1 at delta = (20, 10, 10)) with its
+    # last edge moved onto the second edge's time: key order still counts it
+    # (the input index breaks the tie), the strict reading does not; one
+    # second later both count it
+    s, d, t = _arr([(0, 1, 0), (2, 1, 10), (0, 2, 10)])
+    q = [(20, 10, 10)]
+    assert oracle.count(s, d, t, q).sum() == 1
+    assert oracle.count(s, d, t, q, strict=True).sum() == 0
+    s, d, t = _arr([(0, 1, 0), (2, 1, 10), (0, 2, 11)])
+    q = [(20, 10, 10)]
+    assert (oracle.count(s, d, t, q, strict=True) == oracle.count(s, d, t, q)).all()
+    assert oracle.count(s, d, t, q, strict=True).sum() == 1
