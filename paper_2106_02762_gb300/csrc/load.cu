@@ -861,37 +861,12 @@ __global__ void __launch_bounds__(256)
 constexpr int CORE_THREADS = 1024;      // per CTA of the cluster (measured: more threads per round beat fewer idle warps)
 constexpr int CORE_TAIL_THREADS = 1024;  // the one-CTA run of the last PEEL_TAIL vertices
 constexpr uint32_t PEEL_TAIL = 8192;     // the cluster hands the last this many to one CTA
-constexpr int CORE_RUN = 4;          // relaxed edges per thread per step
+constexpr int CORE_RUN = 4;          // adjacency entries a lane relaxes per step
 constexpr uint32_t CORE_MAX_CLUSTER = 16;
 
-// degree, adjacency start, adjacency length, frontier edge offset, two
-// frontier buffers and the level of `per` owned vertices (u32 each)
-inline size_t core_smem_bytes(uint32_t per) { return (size_t)per * 7 * 4; }
-
-__device__ __forceinline__ uint32_t core_block_excl_scan(uint32_t x, uint32_t *s_warp, uint32_t *total) {
-    const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    uint32_t inc = x;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= (uint32_t)o) inc += y;
-    }
-    if (lane == 31) s_warp[w] = inc;
-    __syncthreads();
-    if (w == 0) {
-        const uint32_t nw = blockDim.x >> 5;
-        uint32_t v = lane < nw ? s_warp[lane] : 0, vi = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, vi, o);
-            if (lane >= (uint32_t)o) vi += y;
-        }
-        if (lane < nw) s_warp[lane] = vi - v;
-        if (lane == 31) *total = vi;
-    }
-    __syncthreads();
-    return s_warp[w] + inc - x;
-}
+// degree, adjacency start, adjacency length, two frontier buffers and the
+// level of `per` owned vertices (u32 each)
+inline size_t core_smem_bytes(uint32_t per) { return (size_t)per * 6 * 4; }
 
 // CLUSTER = false: one CTA owns every vertex (plain shared memory, block
 // barriers); CLUSTER = true: `per` (a power of two) vertices per CTA.
@@ -913,18 +888,16 @@ __global__ void __launch_bounds__(CORE_TAIL_THREADS, 1)
     };
     const uint32_t tid = threadIdx.x, lane = tid & 31, nthr = blockDim.x;
     extern __shared__ __align__(16) uint32_t core_smem[];
-    uint32_t *s_deg = core_smem, *s_ab = s_deg + per, *s_na = s_ab + per, *s_foff = s_na + per;
-    uint32_t *s_front = s_foff + per;  // [2][per]
+    uint32_t *s_deg = core_smem, *s_ab = s_deg + per, *s_na = s_ab + per;
+    uint32_t *s_front = s_na + per;  // [2][per]
     uint32_t *s_lev = s_front + 2 * per;
     __shared__ unsigned int s_fcnt[2];                 // entries in my frontier buffers
     __shared__ unsigned int s_tot[3];                  // the cluster's pushes, per round mod 3
-    __shared__ unsigned int s_peer[1];                 // this CTA's pushes in the current round
+    __shared__ unsigned int s_peer[2];                 // this CTA's pushes, by round parity
     __shared__ int s_mins[CORE_MAX_CLUSTER];           // each CTA's smallest remaining degree
     __shared__ unsigned int s_alive[CORE_MAX_CLUSTER]; // and its number of remaining vertices
     __shared__ unsigned int s_nalive;
     __shared__ int s_min;
-    __shared__ uint32_t s_warp[32];
-    __shared__ uint32_t s_fe;
     const uint32_t base_lid = crank * per;
     const uint32_t my_n = R > base_lid ? min(per, R - base_lid) : 0;
     for (uint32_t i = tid; i < my_n; i += nthr) {
@@ -937,7 +910,7 @@ __global__ void __launch_bounds__(CORE_TAIL_THREADS, 1)
     if (tid == 0) {
         s_fcnt[0] = s_fcnt[1] = 0;
         s_tot[0] = s_tot[1] = s_tot[2] = 0;
-        s_peer[0] = 0;
+        s_peer[0] = s_peer[1] = 0;
         s_min = INT_MAX;
         s_nalive = 0;
     }
@@ -1016,72 +989,44 @@ __global__ void __launch_bounds__(CORE_TAIL_THREADS, 1)
         const uint32_t nxt = cur ^ 1, slot = round % 3;
         const uint32_t fn = s_fcnt[cur];
         const uint32_t *F = s_front + cur * per;
-        {
-            // edge offsets of the frontier entries (exclusive scan of their
-            // adjacency lengths), each thread a run of consecutive entries
-            const uint32_t per_t = (fn + nthr - 1) / nthr;
-            const uint32_t b0 = min(fn, tid * per_t), b1 = min(fn, b0 + per_t);
-            uint32_t sum = 0;
-            for (uint32_t i = b0; i < b1; i++) sum += s_na[F[i]];
-            uint32_t run = core_block_excl_scan(sum, s_warp, &s_fe);
-            for (uint32_t i = b0; i < b1; i++) {
-                s_foff[i] = run;
-                run += s_na[F[i]];
-            }
-            // the tally slot of round - 2: every CTA read it before the
-            // barrier that ended round - 1
-            if (tid == 0) s_tot[(round + 1) % 3] = 0;
-            __syncthreads();
-        }
-        const uint32_t fe = s_fe;
-        for (uint32_t e0 = tid * CORE_RUN; e0 - tid * CORE_RUN < fe; e0 += nthr * CORE_RUN) {
-            uint32_t wv[CORE_RUN];
-            bool live[CORE_RUN];
-            if (e0 < fe) {
-                uint32_t lo = 0, hi = fn;  // last entry with s_foff <= e0
-                while (hi - lo > 1) {
-                    const uint32_t mid = (lo + hi) >> 1;
-                    if (s_foff[mid] <= e0) lo = mid; else hi = mid;
-                }
-                uint32_t fi = lo, fbeg = s_foff[fi];
-                uint32_t fend = fi + 1 < fn ? s_foff[fi + 1] : fe;
-                uint32_t ab = s_ab[F[fi]];
+        const uint32_t par = round & 1;
+        // the tally slot of round - 2: every CTA read it before the barrier
+        // that ended round - 1
+        if (tid == 0) s_tot[(round + 1) % 3] = 0;
+        // one warp per frontier vertex, its lanes over the adjacency,
+        // CORE_RUN entries a lane per step with their loads in flight together
+        const uint32_t wid = tid >> 5, nwarp = nthr >> 5;
+        for (uint32_t fi = wid; fi < fn; fi += nwarp) {
+            const uint32_t fv = F[fi], ab = s_ab[fv], na = s_na[fv];
+            for (uint32_t j0 = 0; j0 < na; j0 += 32 * CORE_RUN) {
+                uint32_t wv[CORE_RUN];
+                bool live[CORE_RUN];
 #pragma unroll
                 for (int j = 0; j < CORE_RUN; j++) {
-                    const uint32_t e = e0 + j;
-                    live[j] = e < fe;
-                    if (live[j]) {
-                        while (e >= fend) {
-                            fi++;
-                            fbeg = fend;
-                            fend = fi + 1 < fn ? s_foff[fi + 1] : fe;
-                            ab = s_ab[F[fi]];
-                        }
-                        wv[j] = cadj[ab + (e - fbeg)];
-                    }
+                    const uint32_t e = j0 + (uint32_t)j * 32 + lane;
+                    live[j] = e < na;
+                    wv[j] = live[j] ? cadj[ab + e] : 0u;
                 }
-            } else {
+                // no level check: a removed vertex already has degree <= k, so
+                // a decrement can return k + 1 only for a remaining vertex, once
+                uint32_t own[CORE_RUN], idx[CORE_RUN];
 #pragma unroll
-                for (int j = 0; j < CORE_RUN; j++) live[j] = false;
-            }
-            // no level check: a removed vertex already has degree <= k, so
-            // a decrement can return k + 1 only for a remaining vertex, once
-            uint32_t own[CORE_RUN], idx[CORE_RUN];
+                for (int j = 0; j < CORE_RUN; j++) {
+                    own[j] = CLUSTER && live[j] ? wv[j] >> per_lg : 0u;
+                    idx[j] = live[j] ? (CLUSTER ? wv[j] & (per - 1) : wv[j]) : 0u;
+                }
+                uint32_t old[CORE_RUN];
 #pragma unroll
-            for (int j = 0; j < CORE_RUN; j++) {
-                own[j] = CLUSTER && live[j] ? wv[j] >> per_lg : 0u;
-                idx[j] = live[j] ? (CLUSTER ? wv[j] & (per - 1) : wv[j]) : 0u;
-            }
-            uint32_t old[CORE_RUN];
+                for (int j = 0; j < CORE_RUN; j++)
+                    old[j] = live[j] ? atomicSub(at(s_deg, own[j]) + idx[j], 1u) : 0;
 #pragma unroll
-            for (int j = 0; j < CORE_RUN; j++) old[j] = live[j] ? atomicSub(at(s_deg, own[j]) + idx[j], 1u) : 0;
-#pragma unroll
-            for (int j = 0; j < CORE_RUN; j++) {
-                if (live[j] && (int)old[j] == k + 1) {
-                    at(s_lev, own[j])[idx[j]] = round + 1;
-                    const uint32_t slot_at = atomicAdd(at(s_fcnt, own[j]) + nxt, 1u);
-                    at(s_front, own[j])[nxt * per + slot_at] = idx[j];
-                    atomicAdd(&s_peer[0], 1u);
+                for (int j = 0; j < CORE_RUN; j++) {
+                    if (live[j] && (int)old[j] == k + 1) {
+                        at(s_lev, own[j])[idx[j]] = round + 1;
+                        const uint32_t slot_at = atomicAdd(at(s_fcnt, own[j]) + nxt, 1u);
+                        at(s_front, own[j])[nxt * per + slot_at] = idx[j];
+                        atomicAdd(&s_peer[par], 1u);
+                    }
                 }
             }
         }
@@ -1089,10 +1034,11 @@ __global__ void __launch_bounds__(CORE_TAIL_THREADS, 1)
         if (tid == 0) s_fcnt[cur] = 0;  // consumed; others push into it only after the barrier
         // add this CTA's pushes to every CTA's tally of this round before the
         // barrier, so that after it each CTA reads the total locally
-        if (tid < csize && s_peer[0]) atomicAdd(at(s_tot, tid) + slot, s_peer[0]);
+        if (tid < csize && s_peer[par]) atomicAdd(at(s_tot, tid) + slot, s_peer[par]);
         csync();
         const uint32_t pushed = s_tot[slot];
-        if (tid == 0) s_peer[0] = 0;  // read above, before this CTA's barrier; next written after it
+        // read above, before this barrier; counted into again two rounds on
+        if (tid == 0) s_peer[par] = 0;
         round++;
         cur = nxt;
         need_level = pushed == 0;
