@@ -856,8 +856,13 @@ __global__ void __launch_bounds__(256)
 // owner's next frontier.  Only counts cross the cluster barrier: pushes are
 // tallied per CTA in a slot that rotates over three rounds, so a slot is
 // read by every CTA between the barriers that end round r and r + 1 and is
-// zeroed in round r + 2.  Continues from level ctl->k and round ctl->rounds;
-// writes level[] of the core vertices and the final rounds and kappa.
+// zeroed in round r + 2.  One CTA alone needs no tally: its frontier counts
+// rotate over three slots (round r's frontier in slot r mod 3, its pushes in
+// slot r + 1 mod 3, slot r + 2 mod 3 zeroed during round r, once every
+// thread read it as round r - 1's count), so a round ends on one barrier
+// that also tells whether anything was pushed.  Continues from level ctl->k
+// and round ctl->rounds; writes level[] of the core vertices and the final
+// rounds and kappa.
 constexpr int CORE_THREADS = 1024;      // per CTA of the cluster (measured: more threads per round beat fewer idle warps)
 constexpr int CORE_TAIL_THREADS = 1024;  // the one-CTA run of the last PEEL_TAIL vertices
 constexpr uint32_t PEEL_TAIL = 8192;     // the cluster hands the last this many to one CTA
@@ -891,7 +896,8 @@ __global__ void __launch_bounds__(CORE_TAIL_THREADS, 1)
     uint32_t *s_deg = core_smem, *s_ab = s_deg + per, *s_na = s_ab + per;
     uint32_t *s_front = s_na + per;  // [2][per]
     uint32_t *s_lev = s_front + 2 * per;
-    __shared__ unsigned int s_fcnt[2];                 // entries in my frontier buffers
+    __shared__ unsigned int s_fcnt[3];                 // entries in my frontier buffers (by round parity;
+                                                       // one CTA alone: by round mod 3)
     __shared__ unsigned int s_tot[3];                  // the cluster's pushes, per round mod 3
     __shared__ unsigned int s_peer[2];                 // this CTA's pushes, by round parity
     __shared__ int s_mins[CORE_MAX_CLUSTER];           // each CTA's smallest remaining degree
@@ -908,7 +914,7 @@ __global__ void __launch_bounds__(CORE_TAIL_THREADS, 1)
         s_lev[i] = UNSET;
     }
     if (tid == 0) {
-        s_fcnt[0] = s_fcnt[1] = 0;
+        s_fcnt[0] = s_fcnt[1] = s_fcnt[2] = 0;
         s_tot[0] = s_tot[1] = s_tot[2] = 0;
         s_peer[0] = s_peer[1] = 0;
         s_min = INT_MAX;
@@ -975,7 +981,7 @@ __global__ void __launch_bounds__(CORE_TAIL_THREADS, 1)
             for (uint32_t i = tid; i < my_n; i += nthr) {
                 if (s_lev[i] == UNSET && (int)s_deg[i] <= k) {
                     s_lev[i] = round;
-                    s_front[cur * per + atomicAdd(&s_fcnt[cur], 1u)] = i;
+                    s_front[cur * per + atomicAdd(&s_fcnt[CLUSTER ? cur : round % 3], 1u)] = i;
                 }
             }
             // every CTA has collected before any CTA decrements its
@@ -987,12 +993,17 @@ __global__ void __launch_bounds__(CORE_TAIL_THREADS, 1)
         }
         // relaxation of this CTA's frontier (round `round`)
         const uint32_t nxt = cur ^ 1, slot = round % 3;
-        const uint32_t fn = s_fcnt[cur];
+        const uint32_t fn = s_fcnt[CLUSTER ? cur : slot];
+        const uint32_t push_slot = CLUSTER ? nxt : (round + 1) % 3;
         const uint32_t *F = s_front + cur * per;
         const uint32_t par = round & 1;
-        // the tally slot of round - 2: every CTA read it before the barrier
-        // that ended round - 1
-        if (tid == 0) s_tot[(round + 1) % 3] = 0;
+        // the tally slot (one CTA: the count slot) of round - 2: every CTA
+        // read it before the barrier that ended round - 1
+        if (tid == 0) {
+            if constexpr (CLUSTER) s_tot[(round + 1) % 3] = 0;
+            else s_fcnt[(round + 2) % 3] = 0;
+        }
+        bool pushed_any = false;
         // one warp per frontier vertex, its lanes over the adjacency,
         // CORE_RUN entries a lane per step with their loads in flight together
         const uint32_t wid = tid >> 5, nwarp = nthr >> 5;
@@ -1023,22 +1034,28 @@ __global__ void __launch_bounds__(CORE_TAIL_THREADS, 1)
                 for (int j = 0; j < CORE_RUN; j++) {
                     if (live[j] && (int)old[j] == k + 1) {
                         at(s_lev, own[j])[idx[j]] = round + 1;
-                        const uint32_t slot_at = atomicAdd(at(s_fcnt, own[j]) + nxt, 1u);
+                        const uint32_t slot_at = atomicAdd(at(s_fcnt, own[j]) + push_slot, 1u);
                         at(s_front, own[j])[nxt * per + slot_at] = idx[j];
-                        atomicAdd(&s_peer[par], 1u);
+                        if constexpr (CLUSTER) atomicAdd(&s_peer[par], 1u);
+                        pushed_any = true;
                     }
                 }
             }
         }
-        __syncthreads();
-        if (tid == 0) s_fcnt[cur] = 0;  // consumed; others push into it only after the barrier
-        // add this CTA's pushes to every CTA's tally of this round before the
-        // barrier, so that after it each CTA reads the total locally
-        if (tid < csize && s_peer[par]) atomicAdd(at(s_tot, tid) + slot, s_peer[par]);
-        csync();
-        const uint32_t pushed = s_tot[slot];
-        // read above, before this barrier; counted into again two rounds on
-        if (tid == 0) s_peer[par] = 0;
+        uint32_t pushed;
+        if constexpr (CLUSTER) {
+            __syncthreads();
+            if (tid == 0) s_fcnt[cur] = 0;  // consumed; others push into it only after the barrier
+            // add this CTA's pushes to every CTA's tally of this round before
+            // the barrier, so that after it each CTA reads the total locally
+            if (tid < csize && s_peer[par]) atomicAdd(at(s_tot, tid) + slot, s_peer[par]);
+            cl.sync();
+            pushed = s_tot[slot];
+            // read above, before this barrier; counted into again two rounds on
+            if (tid == 0) s_peer[par] = 0;
+        } else {
+            pushed = __syncthreads_or(pushed_any) ? 1u : 0u;
+        }
         round++;
         cur = nxt;
         need_level = pushed == 0;
