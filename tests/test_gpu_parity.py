@@ -415,3 +415,10 @@ def test_allocation_failure_leaves_no_leak():
     g = ttc.Graph(s, d, t)
     assert (g.count(synth.TINY_PLAIN_DELTA) == ref).all()
     g.free()
+
+
+def test_smoke_entry_point():
+    # the package's own smoke check (a small batch and one single query
+    # against the oracle on cuda:0) stays runnable
+    import __graft_entry__
+    __graft_entry__.smoke()
