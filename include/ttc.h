@@ -165,6 +165,12 @@ ttc_status ttc_load_ex(const uint32_t *src, const uint32_t *dst, const int64_t *
 /* Release a graph and all of its device memory.  NULL is a no-op. */
 void ttc_free(ttc_graph *g);
 
+/* Statistics of a loaded graph (the static quantities of Sec. 3 and Table 2:
+ * n, m, m_s, static triangles tau, degeneracy kappa, largest multiplicity;
+ * and this library's work figures: the work bytes of the count, W = sum over
+ * static triangles of 8 (s_uv + s_uw + s_vw) + 12, the enumerated list
+ * lengths of Sec. 5, the bin sizes and device memory).  *s is a
+ * caller-owned host struct, written on TTC_OK; TTC_ERR_INVALID for NULL. */
 ttc_status ttc_graph_info(const ttc_graph *g, ttc_graph_stats *s);
 
 /* ----------------------------------------------------------------- count */
@@ -177,6 +183,21 @@ ttc_status ttc_count(ttc_graph *g, const ttc_delta *d, uint64_t out[TTC_NUM_TYPE
 /* k queries in one pass over the triangles.  d[k] host array; out is a host
  * array of k * 8 counts, row q for d[q]. */
 ttc_status ttc_count_batch(ttc_graph *g, const ttc_delta *d, uint32_t k, uint64_t *out);
+
+/* One shard of ttc_count_batch, for counting one graph on several GPUs (or
+ * processes): every static triangle is counted on its own (Alg. 1 counts
+ * each triangle of the oriented graph independently; Sec. 5, proof of
+ * Theorem 1), so the triangle list can be divided.  Each of the handle's bins
+ * (light, warp, CTA and flat records) is cut into nshards consecutive slices
+ * of near-equal length, and this call counts slice `shard` of every bin.  The
+ * shards partition the triangles: summing out over shard = 0 .. nshards - 1
+ * gives ttc_count_batch's counts (the caller sums; TTC_ERR_OVERFLOW covers
+ * this shard's counts only).  Every process loads the same edges, and the
+ * load is deterministic, so all hold the same bins.  d[k], out[k * 8] host
+ * arrays as in ttc_count_batch.  TTC_ERR_INVALID for shard >= nshards,
+ * nshards = 0, or a TTC_LOAD_STREAM handle. */
+ttc_status ttc_count_shard(ttc_graph *g, const ttc_delta *d, uint32_t k, uint32_t shard, uint32_t nshards,
+                           uint64_t *out);
 
 /* δ-grid analytics: the counts at every (δ1,2, δ2,3) of the grid
  * d12[0..n12) x d23[0..n23) for one δ1,3, in one batched pass (the
@@ -212,21 +233,24 @@ ttc_status ttc_count_sample(ttc_graph *g, const ttc_delta *d, uint64_t first, ui
 
 /* No-allocation variant of ttc_count (the paper has no counterpart; this is
  * an interface convenience).  For callers that cannot allocate device memory
- * when they count: inside a CUDA stream capture, beside a framework allocator
- * that owns the device's memory, or in latency-critical loops.  It runs the
- * same kernels as ttc_count, but its device scratch (the counts, the delta
- * and the prefix-sum arrays of the heavy bin) is one static __device__ array
- * of TTC_NOALLOC_SCRATCH_BYTES that every device holds from library load to
- * process exit; it calls no cudaMalloc, cudaFree or other allocator.
+ * when they count: beside a framework allocator that owns the device's
+ * memory, or in latency-critical loops where an allocation may stall.  It
+ * runs the same kernels as ttc_count, but its device scratch (the counts, the
+ * delta and the prefix-sum arrays of the heavy bin) is one static __device__
+ * array of TTC_NOALLOC_SCRATCH_BYTES that every device holds from library
+ * load to process exit; it calls no cudaMalloc, cudaFree or other allocator.
  *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *     (cudaGetSymbolAddress) with that device current.
  *   - A graph whose heavy-bin prefix arrays need more than the array holds
  *     (TTC_NOALLOC_SCRATCH_BYTES - 512 bytes) is rejected with TTC_ERR_RANGE;
  *     use ttc_count for it.
  *   - Every call shares the one array and keeps the previous call's contents;
- *     each call zeroes the counts it needs.  Calls are serialised by a lock and
- *     return only when their kernels are done; work that overlapped a call on
- *     the GPU while using the same array would race.
+ *     each call zeroes the counts it needs.  Calls are serialised by a lock;
+ *     other work that overlapped a call on the GPU while using the same
+ *     array would race.
+ *   - The call is synchronous: it waits on `stream` for its kernels and
+ *     copies the counts to out before it returns.  The caller's current
+ *     device is current again on return.
  * d and out are host pointers; stream is a cudaStream_t (NULL = the graph's
  * stream). */
 #define TTC_NOALLOC_SCRATCH_BYTES (64u << 20)
@@ -239,7 +263,9 @@ typedef struct {
     uint32_t max_batch;          /* most queries per graph per launch (0 = 256) */
     uint32_t max_queue;          /* most pending queries (0 = 65536) */
     uint32_t streams;            /* concurrent launch streams (0 = 4) */
-    uint32_t reserved;
+    uint32_t wait_limit_us;      /* longest the worker sleeps between checks for finished
+                                    launches and new queries, in microseconds (0 = 200):
+                                    every wait of the server is bounded */
 } ttc_server_opts;
 
 /* A server keeps graphs resident and runs queries as they arrive: pending

@@ -51,9 +51,12 @@ def _load():
         lib.ttc_oracle_count_part.argtypes = [p, p, p, u64, p, u32, i32, u32, u32, p]
         lib.ttc_oracle_count_triangles.argtypes = [p, p, p, u64, p, u64, p, u32, i32, p]
         lib.ttc_oracle_stats.argtypes = [p, p, p, u64, i32, p]
+        lib.ttc_oracle_count_fwd.argtypes = [p, p, p, u64, p, u32, i32, i32, p]
+        lib.ttc_oracle_stats_fwd.argtypes = [p, p, p, u64, i32, p]
         for f in (lib.ttc_oracle_bruteforce, lib.ttc_oracle_bruteforce_ex, lib.ttc_oracle_count,
                   lib.ttc_oracle_count_ex, lib.ttc_oracle_count_part,
-                  lib.ttc_oracle_count_triangles, lib.ttc_oracle_stats):
+                  lib.ttc_oracle_count_triangles, lib.ttc_oracle_stats, lib.ttc_oracle_count_fwd,
+                  lib.ttc_oracle_stats_fwd):
             f.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -107,6 +110,18 @@ def count(src, dst, t, deltas, threads: int = 0, strict: bool = False):
     return out
 
 
+def count_fwd(src, dst, t, deltas, threads: int = 0, strict: bool = False):
+    """O1 with the static triangles found by the forward rule (pairs oriented
+    by (degree, id)) instead of plain adjacency: the same counts, in time that
+    suits graphs with hubs.  Returns [k][8]."""
+    src, dst, t = _edges(src, dst, t)
+    d = _deltas(deltas)
+    out = np.zeros((d.shape[0], 8), dtype=np.uint64)
+    _check(_load().ttc_oracle_count_fwd(_ptr(src), _ptr(dst), _ptr(t), src.size,
+                                        _ptr(d), d.shape[0], int(threads), int(bool(strict)), _ptr(out)))
+    return out
+
+
 def count_part(src, dst, t, deltas, part: int, nparts: int, threads: int = 0):
     """O1 over the triangles whose smallest vertex id is part mod nparts
     (the parts partition the triangles).  Returns [k][8]."""
@@ -136,6 +151,16 @@ def stats(src, dst, t, threads: int = 0):
     src, dst, t = _edges(src, dst, t)
     s = np.zeros(8, dtype=np.uint64)
     _check(_load().ttc_oracle_stats(_ptr(src), _ptr(dst), _ptr(t), src.size, int(threads), _ptr(s)))
+    return {"n": int(s[0]), "m": int(s[1]), "m_s": int(s[2]), "tau": int(s[3]),
+            "sigma_max": int(s[4]), "work_bytes": int(s[5]),
+            "prod": int(s[6]) + (int(s[7]) << 64)}
+
+
+def stats_fwd(src, dst, t, threads: int = 0):
+    """stats() with the triangles found by the forward rule."""
+    src, dst, t = _edges(src, dst, t)
+    s = np.zeros(8, dtype=np.uint64)
+    _check(_load().ttc_oracle_stats_fwd(_ptr(src), _ptr(dst), _ptr(t), src.size, int(threads), _ptr(s)))
     return {"n": int(s[0]), "m": int(s[1]), "m_s": int(s[2]), "tau": int(s[3]),
             "sigma_max": int(s[4]), "work_bytes": int(s[5]),
             "prod": int(s[6]) + (int(s[7]) << 64)}

@@ -41,6 +41,15 @@
  *      key(e2) > key(e1) and t2 - t1 <= d12, the number of e3 on the third
  *      pair with key(e3) > key(e2) and t3 <= min(t2 + d23, t1 + d13),
  *      counted separately for each direction of the third pair.
+ *   O1f (ttc_oracle_count_fwd, ttc_oracle_stats_fwd): the same per-triangle
+ *      sums, with the static triangles found by the textbook "forward" rule
+ *      instead of the plain one (every pair oriented from the endpoint of
+ *      smaller (degree, id) to the larger; each triangle found once, at its
+ *      first vertex, by merging two sorted out-lists).  On power-law graphs
+ *      the plain rule visits about deg^2 vertex pairs at every hub, which
+ *      takes hours at a million vertices; the forward rule visits the same
+ *      triangles in O(m_s^1.5).  The tests check that both rules give the
+ *      same triangles and counts.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -490,6 +499,138 @@ int ttc_oracle_count_triangles(const uint32_t *src, const uint32_t *dst, const i
 }
 
 /*
+ * The forward rule.  Pairs are oriented from the endpoint that comes first in
+ * (degree, id) order; out(v) keeps v's adjacency order (by neighbour id).  A
+ * triangle whose vertices come in the order a, b, c is visited once: at a,
+ * for the out-neighbour b, as the common element c of out(a) and out(b).
+ * The visitor gets the vertex ids sorted (x < y < z) and the pair indices
+ * of {x, y}, {x, z}, {y, z}.
+ */
+typedef struct {
+    uint64_t *off;   /* n + 1 */
+    uint32_t *nbr;   /* out-neighbours, by id */
+    int64_t *pair;   /* pair index of each out-entry */
+} fwd_adj_t;
+
+static void fwd_free(fwd_adj_t *f) {
+    free(f->off); free(f->nbr); free(f->pair);
+    memset(f, 0, sizeof(*f));
+}
+
+static int fwd_first(const graph_t *g, uint32_t v, uint32_t w) {
+    const uint64_t dv = g->adj_off[v + 1] - g->adj_off[v], dw = g->adj_off[w + 1] - g->adj_off[w];
+    return dv < dw || (dv == dw && v < w);
+}
+
+static int fwd_build(const graph_t *g, fwd_adj_t *f) {
+    memset(f, 0, sizeof(*f));
+    f->off = (uint64_t *)calloc((size_t)g->n + 1, sizeof(uint64_t));
+    f->nbr = (uint32_t *)malloc(sizeof(uint32_t) * ((size_t)g->ms + 1));
+    f->pair = (int64_t *)malloc(sizeof(int64_t) * ((size_t)g->ms + 1));
+    if (!f->off || !f->nbr || !f->pair) { fwd_free(f); return ORACLE_ERR_NOMEM; }
+    uint64_t k = 0;
+    for (uint32_t v = 0; v < g->n; v++) {
+        f->off[v] = k;
+        for (uint64_t i = g->adj_off[v]; i < g->adj_off[v + 1]; i++) {
+            if (!fwd_first(g, v, g->adj_nbr[i])) continue;
+            f->nbr[k] = g->adj_nbr[i];
+            f->pair[k] = g->adj_pair[i];
+            k++;
+        }
+    }
+    f->off[g->n] = k;
+    return ORACLE_OK;
+}
+
+typedef void (*tri_visit_t)(const graph_t *g, const uint32_t xyz[3], const int64_t p[3], void *ctx, int thread);
+
+static void fwd_enumerate(const graph_t *g, const fwd_adj_t *f, int nt, tri_visit_t visit, void *ctx) {
+#pragma omp parallel for schedule(dynamic, 64) num_threads(nt)
+    for (int64_t a = 0; a < (int64_t)g->n; a++) {
+#ifdef _OPENMP
+        const int th = omp_get_thread_num();
+#else
+        const int th = 0;
+#endif
+        for (uint64_t i = f->off[a]; i < f->off[a + 1]; i++) {
+            const uint32_t b = f->nbr[i];
+            uint64_t p = f->off[a], q = f->off[b];
+            while (p < f->off[a + 1] && q < f->off[b + 1]) {
+                if (f->nbr[p] < f->nbr[q]) { p++; continue; }
+                if (f->nbr[p] > f->nbr[q]) { q++; continue; }
+                /* c = f->nbr[p]: pairs {a, b} = f->pair[i], {a, c} = f->pair[p], {b, c} = f->pair[q] */
+                const uint32_t v[3] = {(uint32_t)a, b, f->nbr[p]};
+                const int64_t pv[3] = {f->pair[i], f->pair[p], f->pair[q]};  /* {v0,v1}, {v0,v2}, {v1,v2} */
+                /* sort the ids; the pair of two ids is the one not naming the third */
+                int o[3] = {0, 1, 2};
+                if (v[o[0]] > v[o[1]]) { int x = o[0]; o[0] = o[1]; o[1] = x; }
+                if (v[o[1]] > v[o[2]]) { int x = o[1]; o[1] = o[2]; o[2] = x; }
+                if (v[o[0]] > v[o[1]]) { int x = o[0]; o[0] = o[1]; o[1] = x; }
+                /* pair index of {v_i, v_j}: vertex k = 3 - i - j is the one left out */
+                static const int pair_without[3] = {2, 1, 0};
+                const uint32_t xyz[3] = {v[o[0]], v[o[1]], v[o[2]]};
+                const int64_t pp[3] = {pv[pair_without[o[2]]], pv[pair_without[o[1]]], pv[pair_without[o[0]]]};
+                visit(g, xyz, pp, ctx, th);
+                p++;
+                q++;
+            }
+        }
+    }
+}
+
+typedef struct {
+    const int64_t *deltas;
+    uint32_t nd;
+    int strict;
+    u128 *acc;   /* per thread: 8 * nd */
+    int err;
+} fwd_count_ctx;
+
+static void fwd_count_visit(const graph_t *g, const uint32_t xyz[3], const int64_t p[3], void *vctx, int th) {
+    fwd_count_ctx *c = (fwd_count_ctx *)vctx;
+    const uint32_t lh[3][2] = {{xyz[0], xyz[1]}, {xyz[0], xyz[2]}, {xyz[1], xyz[2]}};
+    if (count_one_triangle(g, p, lh, c->deltas, c->nd, c->strict, c->acc + (size_t)th * 8 * c->nd)) c->err = 1;
+}
+
+/* O1 with the forward rule: the same result as ttc_oracle_count_ex. */
+int ttc_oracle_count_fwd(const uint32_t *src, const uint32_t *dst, const int64_t *t, uint64_t m,
+                         const int64_t *deltas, uint32_t nd, int threads, int strict, uint64_t *out) {
+    if ((m && (!src || !dst || !t)) || !out || (nd && !deltas) || !check_deltas(deltas, nd))
+        return ORACLE_ERR_INVALID;
+    graph_t g;
+    int rc = graph_build(src, dst, t, m, 1, &g);
+    if (rc) return rc;
+    fwd_adj_t f;
+    rc = fwd_build(&g, &f);
+    if (rc) { graph_free(&g); return rc; }
+    const int nt = threads_or_default(threads);
+    fwd_count_ctx c = {deltas, nd, strict, (u128 *)calloc((size_t)nt * 8 * (nd ? nd : 1), sizeof(u128)), 0};
+    if (!c.acc) { fwd_free(&f); graph_free(&g); return ORACLE_ERR_NOMEM; }
+    fwd_enumerate(&g, &f, nt, fwd_count_visit, &c);
+    for (int th = 1; th < nt; th++)
+        for (uint32_t q = 0; q < 8 * nd; q++) c.acc[q] += c.acc[(size_t)th * 8 * nd + q];
+    rc = c.err ? ORACLE_ERR_NOMEM : finish(c.acc, nd, out);
+    free(c.acc);
+    fwd_free(&f);
+    graph_free(&g);
+    return rc;
+}
+
+typedef struct {
+    uint64_t *tau, *work;  /* per thread */
+    u128 *prod;
+} fwd_stats_ctx;
+
+static void fwd_stats_visit(const graph_t *g, const uint32_t xyz[3], const int64_t p[3], void *vctx, int th) {
+    (void)xyz;
+    fwd_stats_ctx *c = (fwd_stats_ctx *)vctx;
+    const uint64_t s1 = g->pairs[p[0]].len, s2 = g->pairs[p[1]].len, s3 = g->pairs[p[2]].len;
+    c->tau[th]++;
+    c->work[th] += 8 * (s1 + s2 + s3) + 12;
+    c->prod[th] += (u128)s1 * s2 * s3;
+}
+
+/*
  * Static statistics (Sec. 3, Table 2 columns): n, m (self-loops dropped),
  * m_s, tau (static triangles), sigma_max (largest undirected multiplicity),
  * and two sums over static triangles {a, b, c} with undirected
@@ -534,6 +675,36 @@ int ttc_oracle_stats(const uint32_t *src, const uint32_t *dst, const int64_t *t,
     }
     stats[0] = g.n; stats[1] = (uint64_t)g.k; stats[2] = (uint64_t)g.ms; stats[3] = tau;
     stats[4] = smax; stats[5] = work; stats[6] = (uint64_t)prod; stats[7] = (uint64_t)(prod >> 64);
+    graph_free(&g);
+    return ORACLE_OK;
+}
+
+/* ttc_oracle_stats with the forward rule: the same statistics. */
+int ttc_oracle_stats_fwd(const uint32_t *src, const uint32_t *dst, const int64_t *t, uint64_t m,
+                         int threads, uint64_t *stats) {
+    if ((m && (!src || !dst || !t)) || !stats) return ORACLE_ERR_INVALID;
+    graph_t g;
+    int rc = graph_build(src, dst, t, m, 1, &g);
+    if (rc) return rc;
+    fwd_adj_t f;
+    rc = fwd_build(&g, &f);
+    if (rc) { graph_free(&g); return rc; }
+    const int nt = threads_or_default(threads);
+    fwd_stats_ctx c = {(uint64_t *)calloc((size_t)nt, 8), (uint64_t *)calloc((size_t)nt, 8),
+                       (u128 *)calloc((size_t)nt, sizeof(u128))};
+    if (!c.tau || !c.work || !c.prod) {
+        free(c.tau); free(c.work); free(c.prod); fwd_free(&f); graph_free(&g);
+        return ORACLE_ERR_NOMEM;
+    }
+    fwd_enumerate(&g, &f, nt, fwd_stats_visit, &c);
+    uint64_t tau = 0, work = 0, smax = 0;
+    u128 prod = 0;
+    for (int th = 0; th < nt; th++) { tau += c.tau[th]; work += c.work[th]; prod += c.prod[th]; }
+    for (int64_t p = 0; p < g.ms; p++) if (g.pairs[p].len > smax) smax = g.pairs[p].len;
+    stats[0] = g.n; stats[1] = (uint64_t)g.k; stats[2] = (uint64_t)g.ms; stats[3] = tau;
+    stats[4] = smax; stats[5] = work; stats[6] = (uint64_t)prod; stats[7] = (uint64_t)(prod >> 64);
+    free(c.tau); free(c.work); free(c.prod);
+    fwd_free(&f);
     graph_free(&g);
     return ORACLE_OK;
 }

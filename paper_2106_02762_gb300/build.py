@@ -81,7 +81,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     changed = any(c for _, c in results)
     if force or changed or not os.path.exists(LIB):
         tmp = LIB + ".%d.tmp" % os.getpid()
-        cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"]
+        cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread", "-ldl"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))

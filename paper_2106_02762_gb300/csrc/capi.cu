@@ -6,6 +6,10 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <set>
+#include <tuple>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "graph.cuh"
 
@@ -13,6 +17,7 @@ namespace ttc {
 
 namespace {
 thread_local std::string g_last_error;
+thread_local int t_prof_off = 0;
 std::atomic<uint64_t> g_fail_after{0};
 std::atomic<uint64_t> g_bytes{0};
 std::atomic<uint64_t> g_launches{0};
@@ -20,10 +25,18 @@ std::atomic<uint64_t> g_launches{0};
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
-void prof_reset(ttc_graph *g) { g->prof_used = 0; }
+ProfOff::ProfOff() { t_prof_off++; }
+ProfOff::~ProfOff() { t_prof_off--; }
 
+void prof_reset(ttc_graph *g) {
+    if (!t_prof_off) g->prof_used = 0;
+}
+
+// Every load phase and count kernel is also an NVTX range (named as in the
+// profile), so a timeline tool shows the stages.
 void prof_begin(ttc_graph *g, cudaStream_t s, const char *name) {
-    if (!g->profiling) return;
+    nvtxRangePushA(name);
+    if (!g->profiling || t_prof_off) return;
     if (g->prof_used == g->prof.size()) {
         ttc_graph::ProfEntry e{name, nullptr, nullptr};
         TTC_CUDA(cudaEventCreate(&e.start));
@@ -35,7 +48,8 @@ void prof_begin(ttc_graph *g, cudaStream_t s, const char *name) {
 }
 
 void prof_end(ttc_graph *g, cudaStream_t s) {
-    if (!g->profiling) return;
+    nvtxRangePop();
+    if (!g->profiling || t_prof_off) return;
     TTC_CUDA(cudaEventRecord(g->prof[g->prof_used].stop, s));
     g->prof_used++;
 }
@@ -136,17 +150,37 @@ void device_free(void *p, cudaStream_t s) {
 uint64_t device_bytes_in_use() { return g_bytes.load(); }
 
 int sm_count() {
-    static int n = 0;
+    constexpr int MAXDEV = 64;
+    static std::atomic<int> counts[MAXDEV] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= MAXDEV) dev = 0;
+    int n = counts[dev].load(std::memory_order_relaxed);
     if (!n) {
-        int dev = 0;
-        cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
         if (n <= 0) n = 1;
+        counts[dev].store(n, std::memory_order_relaxed);
     }
     return n;
 }
 
+void ensure_smem(const void *fn, size_t bytes) {
+    static std::mutex mu;
+    static std::set<std::tuple<const void *, int, size_t>> done;
+    int dev = 0;
+    TTC_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    if (done.count({fn, dev, bytes})) return;
+    TTC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    done.insert({fn, dev, bytes});
+}
+
 void set_last_error(const std::string &m) { g_last_error = m; }
+
+void check_count_flag(unsigned long long flag) {
+    if (flag & 2ull) fail(TTC_ERR_TIMEOUT, "a bounded wait in a count kernel gave up (bulk copy not complete)");
+    if (flag) fail(TTC_ERR_OVERFLOW, "a count exceeds 2^64 - 1");
+}
 
 // Normalised copy of a delta-triple (leaves every count unchanged):
 //   d12 <- min(d12, d13), d23 <- min(d23, d13), d13 <- min(d13, d12 + d23).
@@ -187,6 +221,7 @@ void count_multi(ttc_graph *const *gs, const ttc_delta *d, uint32_t G, uint64_t 
 // Device bytes a resident graph holds.
 uint64_t graph_device_bytes(const ttc_graph *g) {
     return g->key.bytes() + g->fwd.bytes() + g->poff.bytes() + g->pair_vtx.bytes() + g->tri.bytes() +
+           g->shard_view.bytes() + g->shard_pre.bytes() + g->shard_eoff.bytes() +
            g->huge_eoff.bytes() + g->view.bytes() + g->prefix.bytes() + g->acc.bytes() +
            g->dq.bytes() + g->scratch.bytes() + g->s_items.bytes() + g->s_ocsr.bytes() + g->s_onbr.bytes() +
            g->s_osrc.bytes() + g->s_in_e.bytes() + g->s_out_off.bytes() + g->s_in_off.bytes();
@@ -207,6 +242,7 @@ void graph_destroy(ttc_graph *g) {
     g->key.reset(); g->fwd.reset(); g->poff.reset(); g->pair_vtx.reset(); g->tri.reset();
     g->huge_eoff.reset(); g->view.reset(); g->prefix.reset();
     g->acc.reset(); g->dq.reset(); g->scratch.reset();
+    g->shard_view.reset(); g->shard_pre.reset(); g->shard_eoff.reset();
     g->s_items.reset(); g->s_ocsr.reset(); g->s_onbr.reset(); g->s_osrc.reset(); g->s_in_e.reset();
     g->s_out_off.reset(); g->s_in_off.reset();
     // every buffer is freed on the graph's stream, so before that stream goes
@@ -215,8 +251,10 @@ void graph_destroy(ttc_graph *g) {
     delete g;
 }
 
-// Runs k normalised queries and copies the counts to out (host).
-ttc_status run_queries(ttc_graph *g, const ttc_delta *d, uint32_t k, uint64_t *out) {
+// Runs k normalised queries and copies the counts to out (host); nshards > 0:
+// only shard `shard` of that many.
+ttc_status run_queries(ttc_graph *g, const ttc_delta *d, uint32_t k, uint64_t *out, uint32_t shard = 0,
+                       uint32_t nshards = 0) {
     std::vector<int64_t> hq(3 * (size_t)k);
     for (uint32_t q = 0; q < k; q++) normalise(d[q], &hq[3 * (size_t)q]);
     std::lock_guard<std::mutex> lock(g->mu);
@@ -230,11 +268,12 @@ ttc_status run_queries(ttc_graph *g, const ttc_delta *d, uint32_t k, uint64_t *o
     TTC_CUDA(cudaMemcpyAsync(g->dq.get(), hq.data(), hq.size() * 8, cudaMemcpyHostToDevice, s));
     TTC_CUDA(cudaMemsetAsync(g->acc.get(), 0, (8 * (size_t)k + 1) * 8, s));
     prof_reset(g);
-    count_queue(g, g->dq.get(), k, g->acc.get(), s);
+    if (nshards) count_queue_shard(g, g->dq.get(), k, g->acc.get(), shard, nshards, s);
+    else count_queue(g, g->dq.get(), k, g->acc.get(), s);
     std::vector<unsigned long long> h(8 * (size_t)k + 1);
     TTC_CUDA(cudaMemcpyAsync(h.data(), g->acc.get(), h.size() * 8, cudaMemcpyDeviceToHost, s));
     TTC_CUDA(cudaStreamSynchronize(s));
-    if (h[8 * (size_t)k]) fail(TTC_ERR_OVERFLOW, "a count exceeds 2^64 - 1");
+    check_count_flag(h[8 * (size_t)k]);
     memcpy(out, h.data(), 8 * (size_t)k * 8);
     return TTC_OK;
 }
@@ -406,6 +445,26 @@ ttc_status ttc_count_batch(ttc_graph *g, const ttc_delta *d, uint32_t k, uint64_
     if (!k) return TTC_OK;
     TTC_API_BEGIN
     return run_queries(g, d, k, out);
+    TTC_API_END
+}
+
+ttc_status ttc_count_shard(ttc_graph *g, const ttc_delta *d, uint32_t k, uint32_t shard, uint32_t nshards,
+                           uint64_t *out) {
+    if (!g || (k && (!d || !out))) {
+        set_last_error("NULL argument");
+        return TTC_ERR_INVALID;
+    }
+    if (!nshards || shard >= nshards) {
+        set_last_error("shard " + std::to_string(shard) + " of " + std::to_string(nshards) + " does not exist");
+        return TTC_ERR_INVALID;
+    }
+    if (g->streamed) {
+        set_last_error("the graph was loaded with TTC_LOAD_STREAM: it keeps no triangle list to divide");
+        return TTC_ERR_INVALID;
+    }
+    if (!k) return TTC_OK;
+    TTC_API_BEGIN
+    return run_queries(g, d, k, out, shard, nshards);
     TTC_API_END
 }
 

@@ -68,8 +68,22 @@ struct DevBuf {
     T *get() const { return ptr; }
 };
 
-// Number of SMs of the current device (cached).
+// Number of SMs of the current device (cached per device).
 int sm_count();
+
+// Raises kernel `fn`'s dynamic shared-memory limit to `bytes` on the current
+// device, once per (kernel, device, size); thread-safe.
+void ensure_smem(const void *fn, size_t bytes);
+
+// While an object of this type lives, the calling thread's count calls
+// record no per-kernel timing (the handle's profiling setting is left as it
+// is, so other threads see no change).
+struct ProfOff {
+    ProfOff();
+    ~ProfOff();
+    ProfOff(const ProfOff &) = delete;
+    ProfOff &operator=(const ProfOff &) = delete;
+};
 
 // ---------------------------------------------------------------- primitives
 // (primitives.cu)  All run on stream `s` and use scratch from DevBuf.

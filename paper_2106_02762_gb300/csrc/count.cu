@@ -58,12 +58,19 @@ constexpr int LIGHT_WARPS = LIGHT_THREADS / 32;
 // power-law workload: one record per lane is faster for single queries, two
 // for batches.)
 constexpr int LIGHT_BATCH_R = 2;
+// Records per lane in one work item of a single-query (MODE 0) launch on
+// one graph (measured on the power-law workload: two beat one and four).
+constexpr int LIGHT_SINGLE_R = 2;
+// Length classes of C's list (at most 4, 16, 64 edges, longer) by which a
+// work item orders its triangles.
+constexpr uint32_t LIGHT_CLASSES = 4;
 
 template <int R>
 struct WarpTris {
     uint32_t excl[LIGHT_WARPS][32 * R + 1];  // exclusive prefix of pair counts
     uint4 lst[LIGHT_WARPS][32 * R];          // A.b, B.b, C.b, C.n
     uint32_t aux[LIGHT_WARPS][32 * R];       // B.n | flip flags << 29 (B.n < 2^20 in the light bin)
+    uint8_t orig[LIGHT_WARPS][32 * R];       // MODE 2: the record's place in the item
     Query q[LIGHT_WARPS][LIGHT_QT];          // MODE 1: the item's query group
 };
 
@@ -80,12 +87,15 @@ struct WarpTris {
 // light threshold (at most 2^20), so a work item has fewer than 2^32 pairs
 // and a pair's index within its triangle is below 2^20.
 template <int MODE, int R, bool ST>
-__global__ void __launch_bounds__(LIGHT_THREADS, MODE == 1 ? 4 : 5)
+__global__ void __launch_bounds__(LIGHT_THREADS, 4)
     light_kernel(const GraphView *__restrict__ gvs, const uint64_t *__restrict__ chunk_pre, uint32_t G,
                  const int64_t *dq, uint32_t nq, unsigned long long *out, unsigned long long *flag,
                  const uint64_t *idx, uint64_t nidx, uint32_t qpw = 1) {
     __shared__ WarpTris<R> wt;
-    __shared__ unsigned long long s_acc[MODE == 0 ? 8 : 1][MODE == 0 ? 256 : 1];
+    // MODE 0: per-thread 32-bit counters; a carry out of one adds 2^32 to
+    // its warp's 64-bit word (warps of one block may be on different graphs)
+    __shared__ uint32_t s_acc[MODE == 0 ? 8 : 1][MODE == 0 ? 256 : 1];
+    __shared__ unsigned long long s_wide[MODE == 0 ? LIGHT_WARPS : 1][8];
     // MODE 1: [nq * 8] block accumulators, then, when every item's query
     // group has at most LIGHT_QT queries, per-thread 32-bit accumulators
     // [LIGHT_QT * 8][LIGHT_THREADS] (no shared atomics per pair; a carry out
@@ -99,6 +109,7 @@ __global__ void __launch_bounds__(LIGHT_THREADS, MODE == 1 ? 4 : 5)
     if constexpr (MODE == 0) {
 #pragma unroll
         for (int j = 0; j < 8; j++) s_acc[j][threadIdx.x] = 0;
+        if ((threadIdx.x & 31) < 8) s_wide[threadIdx.x >> 5][threadIdx.x & 31] = 0;
     }
     if constexpr (MODE == 1) {
         for (uint32_t i = threadIdx.x; i < nq * 8; i += blockDim.x) s_bacc[i] = 0;
@@ -146,7 +157,7 @@ __global__ void __launch_bounds__(LIGHT_THREADS, MODE == 1 ? 4 : 5)
         const uint32_t g = MODE == 0 && R == 1 ? graph_of(chunk_pre, G, c) : 0u;
         if constexpr (MODE == 0) {
             if (g != cur_g) {
-                if (cur_g != 0xffffffffu) warp_flush(s_acc, out + 8 * cur_g, flag, ovf);
+                if (cur_g != 0xffffffffu) warp_flush32(s_acc, s_wide[w], out + 8 * cur_g, flag, ovf);
                 cur_g = g;
             }
         }
@@ -163,23 +174,64 @@ __global__ void __launch_bounds__(LIGHT_THREADS, MODE == 1 ? 4 : 5)
             Q0 = load_query(dq, MODE == 0 ? g : 0u);
             gmax = Q0.d13;
         }
+        // the largest d13 of the item's queries with a window shorter than the
+        // time span (-1 if none): pairs within it load C's end keys
+        // (the batched kernel searches window ends one by one and loads no end
+        // keys: it keeps state for several queries and has no registers to spare)
+        int64_t gfin = -1;
+        if constexpr (MODE != 1) {
+            if (ST || Q0.d12 < gv.span || Q0.d23 < gv.span) gfin = Q0.d13;
+        }
         const uint64_t base = (MODE == 0 && R == 1 ? c - __ldg(chunk_pre + g) : c) * PER;
         const uint64_t lim = MODE == 2 ? nidx : gv.n_light;
-        uint32_t np[R];
+        uint32_t np[R], cls[R];
+        uint4 lst[R];
+        uint32_t aux[R];
 #pragma unroll
         for (int r = 0; r < R; r++) {
             const uint32_t slot = r * 32 + lane;
             const uint64_t ti = base + slot;
             np[r] = 0;
+            cls[r] = 0;
+            lst[r] = make_uint4(0, 0, 0, 0);
+            aux[r] = 0;
             if (ti < lim) {
                 const uint4 rec = __ldg(gv.tri + (MODE == 2 ? idx[ti] : ti));
                 const uint32_t ab = __ldg(gv.poff + rec.x), an = __ldg(gv.poff + rec.x + 1) - ab;
                 const uint32_t bb = __ldg(gv.poff + rec.y), bn = __ldg(gv.poff + rec.y + 1) - bb;
                 const uint32_t cb = __ldg(gv.poff + rec.z), cn = __ldg(gv.poff + rec.z + 1) - cb;
                 np[r] = an * bn;
-                wt.lst[w][slot] = make_uint4(ab, bb, cb, cn);
-                wt.aux[w][slot] = bn | (rec.w << 29);
+                cls[r] = cn <= 4 ? 0u : cn <= 16 ? 1u : cn <= 64 ? 2u : 3u;
+                lst[r] = make_uint4(ab, bb, cb, cn);
+                aux[r] = bn | (rec.w << 29);
             }
+        }
+        // the item's triangles in order of the length class of C (counting
+        // sort by ballots): a round of pairs then covers C lists of similar
+        // length, so its lanes' searches take about the same number of steps
+        {
+            const uint32_t below = (1u << lane) - 1u;
+            uint32_t done = 0, pos[R];
+#pragma unroll
+            for (uint32_t k = 0; k < LIGHT_CLASSES; k++) {
+#pragma unroll
+                for (int r = 0; r < R; r++) {
+                    const uint32_t m = __ballot_sync(0xffffffffu, cls[r] == k);
+                    if (cls[r] == k) pos[r] = done + __popc(m & below);
+                    done += __popc(m);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < R; r++) {
+                wt.lst[w][pos[r]] = lst[r];
+                wt.aux[w][pos[r]] = aux[r];
+                wt.excl[w][pos[r]] = np[r];
+                if constexpr (MODE == 2) wt.orig[w][pos[r]] = (uint8_t)(r * 32 + lane);
+            }
+            __syncwarp();
+#pragma unroll
+            for (int r = 0; r < R; r++) np[r] = wt.excl[w][r * 32 + lane];
+            __syncwarp();
         }
         uint32_t total = 0;
 #pragma unroll
@@ -208,26 +260,26 @@ __global__ void __launch_bounds__(LIGHT_THREADS, MODE == 1 ? 4 : 5)
             // loc < 2^20: (loc + 1/2) / bn is at least 1 / (2 bn) from an
             // integer, and the float product is within 2^-3 / bn of it
             const uint32_t ai = __float2uint_rz(((float)loc + 0.5f) * __frcp_rn((float)bn)), bi = loc - ai * bn;
-            light_count_pair(gv, f, L.x, L.y, L.z, L.w, fl, false, 0u, 0u, ai, bi, gmax,
+            light_count_pair(gv, f, L.x, L.y, L.z, L.w, fl, false, 0u, 0u, ai, bi, gmax, gfin,
                              [&](const CView &C, bool a_first, int64_t rx, int64_t ry, uint32_t code) {
                 if (MODE != 1 || tslots) {
-#pragma unroll
+#pragma unroll 1
                     for (uint32_t ql = 0; ql < (MODE == 1 ? LIGHT_QT : 1u); ql++) {
                         if (MODE == 1 && q_beg + ql >= q_end) break;
                         auto accq = [&](int type, uint32_t n) {
-                            if constexpr (MODE == 0) add_checked(s_acc[type][threadIdx.x], n, ovf);
+                            if constexpr (MODE == 0) add_u32_carry(s_acc[type][threadIdx.x], n, &s_wide[w][type], ovf);
                             else if constexpr (MODE == 1)
                                 add_u32_carry(s_t[(ql * 8 + type) * LIGHT_THREADS + threadIdx.x], n,
                                               &s_bacc[(q_beg + ql) * 8 + type], ovf);
-                            else atomicAdd(out + 8 * (base + o) + type, (unsigned long long)n);
+                            else atomicAdd(out + 8 * (base + wt.orig[w][o]) + type, (unsigned long long)n);
                         };
-                        light_pair(C, f, MODE == 1 ? wt.q[w][ql] : Q0, a_first, rx, ry, code, accq);
+                        light_pair<MODE != 1>(C, f, MODE == 1 ? wt.q[w][ql] : Q0, a_first, rx, ry, code, accq);
                     }
                 } else {
                     for (uint32_t q = q_beg; q < q_end; q++) {
                         const Query Q = load_query(dq, q);
                         auto accq = [&](int type, uint32_t n) { shared_add(&s_bacc[q * 8 + type], n, ovf); };
-                        light_pair(C, f, Q, a_first, rx, ry, code, accq);
+                        light_pair<false>(C, f, Q, a_first, rx, ry, code, accq);
                     }
                 }
             });
@@ -235,7 +287,7 @@ __global__ void __launch_bounds__(LIGHT_THREADS, MODE == 1 ? 4 : 5)
         __syncwarp();
     }
     if constexpr (MODE == 0) {
-        if (cur_g != 0xffffffffu) warp_flush(s_acc, out + 8 * cur_g, flag, ovf);
+        if (cur_g != 0xffffffffu) warp_flush32(s_acc, s_wide[w], out + 8 * cur_g, flag, ovf);
     }
     if constexpr (MODE == 1) {
         if (tslots) flush_slots();
@@ -246,7 +298,8 @@ __global__ void __launch_bounds__(LIGHT_THREADS, MODE == 1 ? 4 : 5)
 // ---------------------------------------------------------------- heavy: per-edge math
 // Phase 1 for an enumerated edge e (key ke): the values h, L, R, M against C,
 // each split by C's direction: out[2 s + dC].
-__device__ __forceinline__ void phase1_values(const GList &C, const KeyFmt &f, const Query &q, int64_t ke,
+template <typename CL>
+__device__ __forceinline__ void phase1_values(const CL &C, const KeyFmt &f, const Query &q, int64_t ke,
                                               uint32_t out[8]) {
     const int64_t re = ke >> f.shift;
     // L(e): C's edges before e, by key or (strict) by time
@@ -265,8 +318,8 @@ __device__ __forceinline__ void phase1_values(const GList &C, const KeyFmt &f, c
 // Phase 2 for an enumerated edge e with O the other enumerated list.
 // pref(dO, s, c) = prefix over O's own-direction-dO edges, first c of them,
 // of phase-1 slot s.  add(dO, dC, pi if e is on A, pi if e is on B, n).
-template <typename OL, typename PF, typename ADD>
-__device__ __forceinline__ void phase2_edge(const OL &O, const GList &C, const KeyFmt &f, const Query &q, int64_t ke,
+template <typename OL, typename CL, typename PF, typename ADD>
+__device__ __forceinline__ void phase2_edge(const OL &O, const CL &C, const KeyFmt &f, const Query &q, int64_t ke,
                                             PF &&pref, ADD &&add) {
     const int64_t re = ke >> f.shift;
     // searches in C (split by C's direction).  C's edges not after e (Ka)
@@ -357,11 +410,17 @@ template <typename P>
 struct FusedCap {
     static constexpr uint32_t CAP = sizeof(P) == 4 ? 2048 : 1024;  // edges of A plus B
     static constexpr uint32_t ES = CAP + 4;                         // prefix entries per slot
-    static constexpr size_t KEYS = (size_t)CAP * 8;
+    static constexpr uint32_t CC = 1024;                            // C lists up to this long are staged too
+    static constexpr size_t KEYS = ((size_t)CAP + 4) * 8;            // A and B, each padded to 16-byte words
     static constexpr size_t D0 = ((size_t)CAP + 8) * 4;
     static constexpr size_t PRE = 8 * (size_t)ES * sizeof(P);
+    static constexpr size_t CKEYS = ((size_t)CC + 2) * 8;            // C, padded to 16-byte words
+    static constexpr size_t CD0 = ((size_t)CC + 8) * 4;
+    // MODE 0 tail: 32-bit per-thread counters and one 64-bit carry word per
+    // (warp, type); MODE 1: the queries' block accumulators
+    static constexpr size_t TAIL0 = 8 * 256 * 4 + HEAVY_WARPS * 8 * 8;
     static constexpr size_t bytes(int mode, uint32_t nq) {
-        return KEYS + D0 + PRE + (mode == 1 ? (size_t)nq * 64 : mode == 0 ? 8 * 256 * 8 : 0);
+        return KEYS + D0 + PRE + CKEYS + CD0 + (mode == 1 ? (size_t)nq * 64 : mode == 0 ? TAIL0 : 0);
     }
 };
 
@@ -403,12 +462,20 @@ __global__ void __launch_bounds__(HEAVY_THREADS)
     int64_t *s_key = reinterpret_cast<int64_t *>(smem);
     uint32_t *s_d0 = reinterpret_cast<uint32_t *>(smem + Cap::KEYS);
     P *s_pre = reinterpret_cast<P *>(smem + Cap::KEYS + Cap::D0);
-    unsigned long long *s_tail = reinterpret_cast<unsigned long long *>(smem + Cap::KEYS + Cap::D0 + Cap::PRE);
-    auto s_acc = reinterpret_cast<unsigned long long (*)[256]>(s_tail);  // MODE 0
+    int64_t *s_ck = reinterpret_cast<int64_t *>(smem + Cap::KEYS + Cap::D0 + Cap::PRE);
+    uint32_t *s_cd0 = reinterpret_cast<uint32_t *>(smem + Cap::KEYS + Cap::D0 + Cap::PRE + Cap::CKEYS);
+    unsigned long long *s_tail =
+        reinterpret_cast<unsigned long long *>(smem + Cap::KEYS + Cap::D0 + Cap::PRE + Cap::CKEYS + Cap::CD0);
+    auto s_acc = reinterpret_cast<uint32_t (*)[256]>(s_tail);                        // MODE 0
+    unsigned long long *s_wide = s_tail + 8 * 256 / 2 + (threadIdx.x >> 5) * 8;  // MODE 0: this warp's carries
     __shared__ uint32_t s_tmp[HEAVY_WARPS + 1];
+    __shared__ __align__(8) uint64_t s_bar;
+    uint32_t bar_phase = 0;
+    if (threadIdx.x == 0) mbar_init(&s_bar, 1);
     if constexpr (MODE == 0) {
 #pragma unroll
         for (int j = 0; j < 8; j++) s_acc[j][threadIdx.x] = 0;
+        if ((threadIdx.x & 31) < 8) s_wide[threadIdx.x & 31] = 0;
     }
     if constexpr (MODE == 1) {
         for (uint32_t i = threadIdx.x; i < nq * 8; i += blockDim.x) s_tail[i] = 0;
@@ -421,7 +488,7 @@ __global__ void __launch_bounds__(HEAVY_THREADS)
         const uint32_t g = MODE == 0 ? graph_of(heavy_pre, G, h) : 0u;
         if constexpr (MODE == 0) {
             if (g != cur_g) {
-                if (cur_g != 0xffffffffu) warp_flush(s_acc, out + 8 * cur_g, flag, ovf);
+                if (cur_g != 0xffffffffu) warp_flush32(s_acc, s_wide, out + 8 * cur_g, flag, ovf);
                 cur_g = g;
             }
         }
@@ -436,19 +503,58 @@ __global__ void __launch_bounds__(HEAVY_THREADS)
         // block-uniform skips: lists beyond this kernel's capacity (never, by
         // the load-time partition), or a graph served by the other width
         if (ne > CAP || (sizeof(P) == 8) != (gv.wide != 0)) continue;
-        // stage A ++ B and the effective direction-0 prefix over it
+        // a C list up to CC edges is staged too, so both phases search it in
+        // shared memory; a longer one is searched where it lies
+        const bool c_staged = C.n <= Cap::CC;  // block-uniform
+        // stage A, B (and C when staged) by bulk copies of whole 16-byte
+        // words: A's keys at s_key[ao ..), B's at s_key[aw + bo ..), C's at
+        // s_ck[co ..) (ao, bo, co: the lists' odd starts); the key array has
+        // padding for the last word
+        const uint32_t ao = A.b & 1u, bo = B.b & 1u, co = C.b & 1u;
+        const uint32_t aw = (ao + na + 1u) & ~1u, bw = (bo + nb + 1u) & ~1u;
+        const uint32_t cw = c_staged ? (co + C.n + 1u) & ~1u : 0u;
+        if (threadIdx.x == 0) {
+            fence_async_smem();  // earlier triangles' reads of s_key (all past the last barrier)
+            mbar_arrive_expect(&s_bar, (aw + bw + cw) * 8u);
+            bulk_to_smem(s_key, A.key + (A.b - ao), aw * 8u, &s_bar);
+            bulk_to_smem(s_key + aw, B.key + (B.b - bo), bw * 8u, &s_bar);
+            if (cw) bulk_to_smem(s_ck, C.key + (C.b - co), cw * 8u, &s_bar);
+        }
+        if (!mbar_wait(&s_bar, bar_phase, 1u << 24)) {
+            // the copy did not arrive: report it and stop using shared memory
+            if (threadIdx.x == 0) atomicOr(flag, FLAG_TIMEOUT);
+            mbar_wait(&s_bar, bar_phase, 1u << 24);
+            return;
+        }
+        bar_phase ^= 1u;
+        const int64_t *sA = s_key + ao, *sB = s_key + aw + bo, *sC = s_ck + co;
+        // C's effective direction-0 prefix, when staged (contiguous runs
+        // per thread, one block scan)
+        if (c_staged) {
+            const uint32_t cper = (C.n + HEAVY_THREADS - 1) / HEAVY_THREADS;
+            const uint32_t cbeg = min(C.n, threadIdx.x * cper), cend = min(C.n, cbeg + cper);
+            uint32_t c0 = 0;
+            for (uint32_t i = cbeg; i < cend; i++) c0 += ((uint32_t)(sC[i] & 1) ^ C.flip) == 0;
+            uint32_t crun = block_excl_scan_u32(c0, s_tmp);
+            for (uint32_t i = cbeg; i < cend; i++) {
+                s_cd0[i] = crun;
+                crun += ((uint32_t)(sC[i] & 1) ^ C.flip) == 0;
+            }
+            if (threadIdx.x == 0) s_cd0[C.n] = s_tmp[HEAVY_WARPS];
+            __syncthreads();  // s_tmp is reused below
+        }
+        const SList Cs{sC, s_cd0, C.n, 0u};
+        auto key_at = [&](uint32_t i) { return i < na ? sA[i] : sB[i - na]; };
+        // the effective direction-0 prefix over A ++ B: each thread scans a
+        // contiguous run of the staged keys
         const uint32_t per = (ne + HEAVY_THREADS - 1) / HEAVY_THREADS;
         const uint32_t beg = min(ne, threadIdx.x * per), end = min(ne, beg + per);
         uint32_t cnt0 = 0;
-        for (uint32_t i = beg; i < end; i++) {
-            const int64_t k = i < na ? __ldg(A.key + A.b + i) : __ldg(B.key + B.b + (i - na));
-            s_key[i] = k;
-            cnt0 += ((uint32_t)(k & 1) ^ (i < na ? A.flip : B.flip)) == 0;
-        }
+        for (uint32_t i = beg; i < end; i++) cnt0 += ((uint32_t)(key_at(i) & 1) ^ (i < na ? A.flip : B.flip)) == 0;
         uint32_t run = block_excl_scan_u32(cnt0, s_tmp);
         for (uint32_t i = beg; i < end; i++) {
             s_d0[i] = run;
-            run += ((uint32_t)(s_key[i] & 1) ^ (i < na ? A.flip : B.flip)) == 0;
+            run += ((uint32_t)(key_at(i) & 1) ^ (i < na ? A.flip : B.flip)) == 0;
         }
         if (threadIdx.x == 0) s_d0[ne] = s_tmp[HEAVY_WARPS];
         __syncthreads();
@@ -463,12 +569,13 @@ __global__ void __launch_bounds__(HEAVY_THREADS)
             for (uint32_t e = threadIdx.x; e < ne; e += HEAVY_THREADS) {
                 const uint32_t z = e >= na;
                 const uint32_t j = z ? e - na : e;
-                const int64_t ke = s_key[e];
+                const int64_t ke = key_at(e);
                 const uint32_t de = (uint32_t)(ke & 1) ^ (z ? B.flip : A.flip);
                 const uint32_t dz0 = z ? s_d0[e] - a0 : s_d0[e];
                 const uint32_t rank = de ? j - dz0 : dz0;
                 uint32_t v[8];
-                phase1_values(C, f, Q, ke, v);
+                if (c_staged) phase1_values(Cs, f, Q, ke, v);
+                else phase1_values(C, f, Q, ke, v);
                 const uint32_t at = sbase[2 * z + de] + rank + 1;
 #pragma unroll
                 for (int s = 0; s < 8; s++) s_pre[s * ES + at] = v[s];
@@ -496,10 +603,10 @@ __global__ void __launch_bounds__(HEAVY_THREADS)
             // phase 2
             for (uint32_t e = threadIdx.x; e < ne; e += HEAVY_THREADS) {
                 const uint32_t z = e >= na;
-                const int64_t ke = s_key[e];
+                const int64_t ke = key_at(e);
                 const uint32_t de = (uint32_t)(ke & 1) ^ (z ? B.flip : A.flip);
                 // O = the other list, staged: keys and its own dir-0 prefix
-                const SList O = z ? SList{s_key, s_d0, na, 0u} : SList{s_key + na, s_d0 + na, nb, a0};
+                const SList O = z ? SList{sA, s_d0, na, 0u} : SList{sB, s_d0 + na, nb, a0};
                 const uint32_t oz = 1 - z;
                 auto pref = [&](uint32_t dO, int s, uint32_t c) -> unsigned long long {
                     return (unsigned long long)s_pre[s * ES + sbase[2 * oz + dO] + c];
@@ -508,17 +615,18 @@ __global__ void __launch_bounds__(HEAVY_THREADS)
                     if (!n) return;
                     const uint32_t dA = z ? dO : de, dB = z ? de : dO;
                     const int type = type_of(z ? pib : pia, dA, dB, dC);
-                    if constexpr (MODE == 0) add_checked(s_acc[type][threadIdx.x], n, ovf);
+                    if constexpr (MODE == 0) add_wide32(s_acc[type][threadIdx.x], n, &s_wide[type], ovf);
                     else if constexpr (MODE == 1) shared_add(&s_tail[q * 8 + type], n, ovf);
                     else atomicAdd(out + 8 * h + type, n);
                 };
-                phase2_edge(O, C, f, Q, ke, pref, add);
+                if (c_staged) phase2_edge(O, Cs, f, Q, ke, pref, add);
+                else phase2_edge(O, C, f, Q, ke, pref, add);
             }
             __syncthreads();
         }
     }
     if constexpr (MODE == 0) {
-        if (cur_g != 0xffffffffu) warp_flush(s_acc, out + 8 * cur_g, flag, ovf);
+        if (cur_g != 0xffffffffu) warp_flush32(s_acc, s_wide, out + 8 * cur_g, flag, ovf);
     }
     if constexpr (MODE == 1) block_flush(s_tail, nq * 8, out, flag, ovf);
 }
@@ -531,10 +639,13 @@ template <typename P>
 struct WarpCap {
     static constexpr uint32_t CAP = sizeof(P) == 4 ? 128 : 64;
     static constexpr uint32_t ES = CAP + 4;
+    static constexpr uint32_t CC = 256;  // C lists up to this long are staged too
     static constexpr size_t KEYS = (size_t)CAP * 8;
     static constexpr size_t D0 = ((size_t)CAP + 8) * 4;
     static constexpr size_t PRE = 8 * (size_t)ES * sizeof(P);
-    static constexpr size_t PER_WARP = KEYS + D0 + PRE;
+    static constexpr size_t CKEYS = (size_t)CC * 8;
+    static constexpr size_t CD0 = ((size_t)CC + 8) * 4;
+    static constexpr size_t PER_WARP = KEYS + D0 + PRE + CKEYS + CD0;
     static constexpr size_t bytes(int mode, uint32_t nq) {
         return HEAVY_WARPS * PER_WARP + (mode == 1 ? (size_t)nq * 64 : mode == 0 ? 8 * 256 * 8 : 0);
     }
@@ -553,6 +664,8 @@ __global__ void __launch_bounds__(HEAVY_THREADS)
     int64_t *s_key = reinterpret_cast<int64_t *>(mine);
     uint32_t *s_d0 = reinterpret_cast<uint32_t *>(mine + Cap::KEYS);
     P *s_pre = reinterpret_cast<P *>(mine + Cap::KEYS + Cap::D0);
+    int64_t *s_ck = reinterpret_cast<int64_t *>(mine + Cap::KEYS + Cap::D0 + Cap::PRE);
+    uint32_t *s_cd0 = reinterpret_cast<uint32_t *>(mine + Cap::KEYS + Cap::D0 + Cap::PRE + Cap::CKEYS);
     unsigned long long *s_tail = reinterpret_cast<unsigned long long *>(smem + HEAVY_WARPS * Cap::PER_WARP);
     auto s_acc = reinterpret_cast<unsigned long long (*)[256]>(s_tail);  // MODE 0
     if constexpr (MODE == 0) {
@@ -604,10 +717,36 @@ __global__ void __launch_bounds__(HEAVY_THREADS)
             carry += __shfl_sync(0xffffffffu, x, 31);
         }
         if (lane == 0) s_d0[ne] = carry;
+        // a short C list is staged as well (keys and effective dir-0
+        // prefix), so both phases search it in shared memory; a longer one
+        // is searched where it lies
+        const bool c_staged = C.n <= Cap::CC;  // warp-uniform
+        if (c_staged) {
+            uint32_t cc = 0;
+            for (uint32_t c0 = 0; c0 < C.n; c0 += 32) {
+                const uint32_t i = c0 + lane;
+                uint32_t is0 = 0;
+                if (i < C.n) {
+                    const int64_t k = __ldg(C.key + C.b + i);
+                    s_ck[i] = k;
+                    is0 = ((uint32_t)(k & 1) ^ C.flip) == 0;
+                }
+                uint32_t x = is0;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                    if (lane >= (uint32_t)o) x += y;
+                }
+                if (i < C.n) s_cd0[i] = cc + x - is0;
+                cc += __shfl_sync(0xffffffffu, x, 31);
+            }
+            if (lane == 0) s_cd0[C.n] = cc;
+        }
         __syncwarp();
         const uint32_t a0 = s_d0[na], b0 = carry - a0;
         const uint32_t sbase[4] = {0, a0 + 1, na + 2, na + 2 + b0 + 1};
         const uint32_t slen[4] = {a0, na - a0, b0, nb - b0};
+        const SList Cs{s_ck, s_cd0, C.n, 0u};
         for (uint32_t q = 0; q < (MODE == 1 ? nq : 1u); q++) {
             const Query Q = load_query(dq, MODE == 0 ? g : q);
             // phase 1 (and the zero entry of each segment)
@@ -620,7 +759,8 @@ __global__ void __launch_bounds__(HEAVY_THREADS)
                 const uint32_t dz0 = z ? s_d0[e] - a0 : s_d0[e];
                 const uint32_t rank = de ? j - dz0 : dz0;
                 uint32_t v[8];
-                phase1_values(C, f, Q, ke, v);
+                if (c_staged) phase1_values(Cs, f, Q, ke, v);
+                else phase1_values(C, f, Q, ke, v);
                 const uint32_t at = sbase[2 * z + de] + rank + 1;
 #pragma unroll
                 for (int s = 0; s < 8; s++) s_pre[s * ES + at] = v[s];
@@ -654,7 +794,8 @@ __global__ void __launch_bounds__(HEAVY_THREADS)
                     else if constexpr (MODE == 1) shared_add(&s_tail[q * 8 + type], n, ovf);
                     else atomicAdd(out + 8 * h + type, n);
                 };
-                phase2_edge(O, C, f, Q, ke, pref, add);
+                if (c_staged) phase2_edge(O, Cs, f, Q, ke, pref, add);
+                else phase2_edge(O, C, f, Q, ke, pref, add);
             }
             __syncwarp();
         }
@@ -869,14 +1010,7 @@ template <typename P, int MODE, bool ST>
 void launch_fused(const GraphView *gvs, const uint64_t *heavy_pre, uint32_t G, uint64_t items, const int64_t *dq,
                   uint32_t nq, unsigned long long *out, unsigned long long *flag, const uint64_t *idx,
                   uint64_t nidx, cudaStream_t s, int per_sm = 2) {
-    static int configured_device = -1;
-    int dev = 0;
-    TTC_CUDA(cudaGetDevice(&dev));
-    if (configured_device != dev) {
-        TTC_CUDA(cudaFuncSetAttribute(heavy_fused_kernel<P, MODE, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)FusedCap<P>::bytes(1, MAX_BATCH_SMEM_Q)));
-        configured_device = dev;
-    }
+    ensure_smem((const void *)heavy_fused_kernel<P, MODE, ST>, FusedCap<P>::bytes(1, MAX_BATCH_SMEM_Q));
     heavy_fused_kernel<P, MODE, ST><<<heavy_grid(items, per_sm), HEAVY_THREADS, FusedCap<P>::bytes(MODE, nq), s>>>(
         gvs, heavy_pre, G, dq, nq, out, flag, idx, nidx);
     TTC_LAUNCH_CHECK();
@@ -886,14 +1020,7 @@ template <typename P, int MODE, bool ST>
 void launch_warp(const GraphView *gvs, const uint64_t *hw_pre, uint32_t G, uint64_t items, const int64_t *dq,
                  uint32_t nq, unsigned long long *out, unsigned long long *flag, const uint64_t *idx, uint64_t nidx,
                  cudaStream_t s, int per_sm = 4) {
-    static int configured_device = -1;
-    int dev = 0;
-    TTC_CUDA(cudaGetDevice(&dev));
-    if (configured_device != dev) {
-        TTC_CUDA(cudaFuncSetAttribute(heavy_warp_kernel<P, MODE, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)WarpCap<P>::bytes(1, MAX_BATCH_SMEM_Q)));
-        configured_device = dev;
-    }
+    ensure_smem((const void *)heavy_warp_kernel<P, MODE, ST>, WarpCap<P>::bytes(1, MAX_BATCH_SMEM_Q));
     const uint64_t want = (items + HEAVY_WARPS - 1) / HEAVY_WARPS;
     const uint64_t cap = (uint64_t)sm_count() * (uint64_t)per_sm;
     const unsigned grid = (unsigned)(want < 1 ? 1 : want < cap ? want : cap);
@@ -935,42 +1062,66 @@ void launch_fused_any(int kind, const GraphView *gvs, const uint64_t *heavy_pre,
     }
 }
 
+// The record ranges one count covers: per bin a device graph view and the
+// prefix its kernel reads, and the huge records as flat-path arguments.  The
+// whole graph uses the handle's own view; a shard uses views whose record
+// pointer starts at the shard's first record of each bin.
+struct BinViews {
+    const GraphView *light_view, *hw_view, *hc_view;
+    const uint64_t *light_pre, *hw_pre, *hc_pre;  // {0, 32-record chunks}, {0, n_hw}, {0, n_hc}
+    uint64_t n_light, n_hw, n_hc;
+    HugeArgs huge;                                 // huge.nh = 0: none
+};
+
 // One query (acc[8] + flag) or a batch of k (acc[k][8] + flag at acc[8 k])
-// on one graph; the huge path's prefix arrays live in `scratch`.
-void count_graph(ttc_graph *g, const int64_t *dq, uint32_t k, unsigned long long *acc, void *scratch,
-                 cudaStream_t s) {
-    if (!g->st.tau || !k) return;
+// over the records of `b`; the huge path's prefix arrays live in `scratch`.
+void count_bins(ttc_graph *g, const BinViews &b, const int64_t *dq, uint32_t k, unsigned long long *acc,
+                cudaStream_t s) {
     unsigned long long *flag = acc + 8 * (size_t)k;
-    const GraphView *gv = g->view.get();
     if (g->streamed) stream_count_light(g, dq, k, acc, s);  // the light triangles are found again and counted
-    else if (g->st.tau_light) count_light_records(g, gv, g->prefix.get(), g->st.tau_light, dq, k, acc, s);
-    const uint64_t nw = g->st.tau_hwarp, nc = g->st.tau_hcta;
-    const uint64_t *hw_pre = g->prefix.get() + 2, *hc_pre = g->prefix.get() + 4;
+    else if (b.n_light) count_light_records(g, b.light_view, b.light_pre, b.n_light, dq, k, acc, s);
+    const uint64_t nw = b.n_hw, nc = b.n_hc;
     for (uint32_t q0 = 0; q0 < k && (nw || nc); q0 += MAX_BATCH_SMEM_Q) {
         const uint32_t nq = k - q0 < MAX_BATCH_SMEM_Q ? k - q0 : MAX_BATCH_SMEM_Q;
         const int mode = k == 1 ? 0 : 1;
         if (nw) {
             prof_begin(g, s, mode ? "heavy_warp_batch" : "heavy_warp");
-            if (mode) launch_warp_any<1>(heavy_kind(g->heavy_wide, g->strict), gv, hw_pre, 1, nw, dq + 3 * (size_t)q0, nq,
-                                         acc + 8 * (size_t)q0, flag, nullptr, 0, s);
-            else launch_warp_any<0>(heavy_kind(g->heavy_wide, g->strict), gv, hw_pre, 1, nw, dq, 1, acc, flag, nullptr, 0, s);
+            if (mode) launch_warp_any<1>(heavy_kind(g->heavy_wide, g->strict), b.hw_view, b.hw_pre, 1, nw,
+                                         dq + 3 * (size_t)q0, nq, acc + 8 * (size_t)q0, flag, nullptr, 0, s);
+            else launch_warp_any<0>(heavy_kind(g->heavy_wide, g->strict), b.hw_view, b.hw_pre, 1, nw, dq, 1, acc,
+                                    flag, nullptr, 0, s);
             prof_end(g, s);
         }
         if (nc) {
             prof_begin(g, s, mode ? "heavy_cta_batch" : "heavy_cta");
-            if (mode) launch_fused_any<1>(heavy_kind(g->heavy_wide, g->strict), gv, hc_pre, 1, nc, dq + 3 * (size_t)q0, nq,
-                                          acc + 8 * (size_t)q0, flag, nullptr, 0, s);
-            else launch_fused_any<0>(heavy_kind(g->heavy_wide, g->strict), gv, hc_pre, 1, nc, dq, 1, acc, flag, nullptr, 0, s);
+            if (mode) launch_fused_any<1>(heavy_kind(g->heavy_wide, g->strict), b.hc_view, b.hc_pre, 1, nc,
+                                          dq + 3 * (size_t)q0, nq, acc + 8 * (size_t)q0, flag, nullptr, 0, s);
+            else launch_fused_any<0>(heavy_kind(g->heavy_wide, g->strict), b.hc_view, b.hc_pre, 1, nc, dq, 1, acc,
+                                     flag, nullptr, 0, s);
             prof_end(g, s);
         }
     }
-    if (g->st.tau_huge) {
-        const HugeArgs ha = huge_args(g, scratch);
+    if (b.huge.nh) {
         for (uint32_t q = 0; q < k; q++) {
-            if (g->heavy_wide) run_huge<unsigned long long>(g, ha, dq + 3 * q, acc + 8 * (size_t)q, flag, s);
-            else run_huge<uint32_t>(g, ha, dq + 3 * q, acc + 8 * (size_t)q, flag, s);
+            if (g->heavy_wide) run_huge<unsigned long long>(g, b.huge, dq + 3 * q, acc + 8 * (size_t)q, flag, s);
+            else run_huge<uint32_t>(g, b.huge, dq + 3 * q, acc + 8 * (size_t)q, flag, s);
         }
     }
+}
+
+void count_graph(ttc_graph *g, const int64_t *dq, uint32_t k, unsigned long long *acc, void *scratch,
+                 cudaStream_t s) {
+    if (!g->st.tau || !k) return;
+    BinViews b{};
+    b.light_view = b.hw_view = b.hc_view = g->view.get();
+    b.light_pre = g->prefix.get();
+    b.hw_pre = g->prefix.get() + 2;
+    b.hc_pre = g->prefix.get() + 4;
+    b.n_light = g->st.tau_light;
+    b.n_hw = g->st.tau_hwarp;
+    b.n_hc = g->st.tau_hcta;
+    if (g->st.tau_huge) b.huge = huge_args(g, scratch);
+    count_bins(g, b, dq, k, acc, s);
 }
 
 // Vertex triple (u, v, w) of each sampled record: A = {u, v}, B = {u, w}.
@@ -1005,12 +1156,12 @@ void count_light_records(ttc_graph *g, const GraphView *gv, const uint64_t *ligh
     unsigned long long *flag = acc + 8 * (size_t)k;
     if (k == 1) {
         prof_begin(g, s, "light");
+        constexpr int R0 = LIGHT_SINGLE_R;
+        const unsigned grid = light_grid((nl + 32 * R0 - 1) / (32 * R0));
         if (g->strict)
-            light_kernel<0, 1, true><<<light_grid((nl + 31) / 32), LIGHT_THREADS, 0, s>>>(gv, light_pre, 1, dq, 1, acc,
-                                                                                        flag, nullptr, 0);
+            light_kernel<0, R0, true><<<grid, LIGHT_THREADS, 0, s>>>(gv, light_pre, 1, dq, 1, acc, flag, nullptr, 0);
         else
-            light_kernel<0, 1, false><<<light_grid((nl + 31) / 32), LIGHT_THREADS, 0, s>>>(gv, light_pre, 1, dq, 1, acc,
-                                                                                         flag, nullptr, 0);
+            light_kernel<0, R0, false><<<grid, LIGHT_THREADS, 0, s>>>(gv, light_pre, 1, dq, 1, acc, flag, nullptr, 0);
         TTC_LAUNCH_CHECK();
         prof_end(g, s);
         return;
@@ -1026,16 +1177,10 @@ void count_light_records(ttc_graph *g, const GraphView *gv, const uint64_t *ligh
         const uint32_t qpw = (nq + groups - 1) / groups;
         prof_begin(g, s, "light_batch");
         const size_t smem = nq * 64 + (qpw <= LIGHT_QT ? (size_t)LIGHT_QT * 8 * LIGHT_THREADS * 4 : 0);
-        static int light1_device = -1;
-        int dev = 0;
-        TTC_CUDA(cudaGetDevice(&dev));
-        if (light1_device != dev) {
-            const int most = (int)(MAX_BATCH_SMEM_Q * 64 + LIGHT_QT * 8 * LIGHT_THREADS * 4);
-            TTC_CUDA(cudaFuncSetAttribute(light_kernel<1, LIGHT_BATCH_R, false>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, most));
-            TTC_CUDA(cudaFuncSetAttribute(light_kernel<1, LIGHT_BATCH_R, true>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, most));
-            light1_device = dev;
+        {
+            const size_t most = MAX_BATCH_SMEM_Q * 64 + LIGHT_QT * 8 * LIGHT_THREADS * 4;
+            ensure_smem((const void *)light_kernel<1, LIGHT_BATCH_R, false>, most);
+            ensure_smem((const void *)light_kernel<1, LIGHT_BATCH_R, true>, most);
         }
         const unsigned grid = light_grid(chunks * ((nq + qpw - 1) / qpw));
         if (g->strict)
@@ -1064,11 +1209,74 @@ void count_queue(ttc_graph *g, const int64_t *dq, uint32_t k, unsigned long long
     count_graph(g, dq, k, acc, scratch, s);
 }
 
+// Records [lo, hi) of a bin of n records for shard `shard` of `nshards`:
+// consecutive slices of near-equal length, so the shards partition the bin.
+static inline void shard_slice(uint64_t n, uint32_t shard, uint32_t nshards, uint64_t &lo, uint64_t &hi) {
+    lo = (uint64_t)(((unsigned __int128)n * shard) / nshards);
+    hi = (uint64_t)(((unsigned __int128)n * (shard + 1)) / nshards);
+}
+
+void count_queue_shard(ttc_graph *g, const int64_t *dq, uint32_t k, unsigned long long *acc, uint32_t shard,
+                       uint32_t nshards, cudaStream_t s) {
+    if (!g->st.tau || !k) return;
+    uint64_t lo[4], hi[4];
+    shard_slice(g->st.tau_light, shard, nshards, lo[0], hi[0]);
+    shard_slice(g->st.tau_hwarp, shard, nshards, lo[1], hi[1]);
+    shard_slice(g->st.tau_hcta, shard, nshards, lo[2], hi[2]);
+    shard_slice(g->st.tau_huge, shard, nshards, lo[3], hi[3]);
+    // views whose record pointer starts at the slice: the light kernel reads
+    // tri[i], the warp kernel tri[n_light + i], the CTA kernel
+    // tri[n_light + n_hwarp + i] for i below the slice length
+    GraphView v[3] = {g->view_host, g->view_host, g->view_host};
+    v[0].tri = g->tri.get() + lo[0];
+    v[0].n_light = hi[0] - lo[0];
+    v[1].tri = g->tri.get() + lo[1];
+    v[2].tri = g->tri.get() + lo[2];
+    const uint64_t pre[6] = {0, (hi[0] - lo[0] + 31) / 32, 0, hi[1] - lo[1], 0, hi[2] - lo[2]};
+    if (!g->shard_view.get()) {
+        g->shard_view.alloc(3, s);
+        g->shard_pre.alloc(6, s);
+    }
+    TTC_CUDA(cudaMemcpyAsync(g->shard_view.get(), v, sizeof v, cudaMemcpyHostToDevice, s));
+    TTC_CUDA(cudaMemcpyAsync(g->shard_pre.get(), pre, sizeof pre, cudaMemcpyHostToDevice, s));
+    BinViews b{};
+    b.light_view = g->shard_view.get();
+    b.hw_view = g->shard_view.get() + 1;
+    b.hc_view = g->shard_view.get() + 2;
+    b.light_pre = g->shard_pre.get();
+    b.hw_pre = g->shard_pre.get() + 2;
+    b.hc_pre = g->shard_pre.get() + 4;
+    b.n_light = hi[0] - lo[0];
+    b.n_hw = hi[1] - lo[1];
+    b.n_hc = hi[2] - lo[2];
+    if (hi[3] > lo[3]) {
+        // the slice's enumerated-edge offsets, rebased to start at zero
+        if (g->huge_eoff_host.size() != g->st.tau_huge + 1) {
+            g->huge_eoff_host.resize(g->st.tau_huge + 1);
+            TTC_CUDA(cudaMemcpyAsync(g->huge_eoff_host.data(), g->huge_eoff.get(), g->huge_eoff_host.size() * 8,
+                                     cudaMemcpyDeviceToHost, s));
+            TTC_CUDA(cudaStreamSynchronize(s));
+        }
+        const uint64_t nh = hi[3] - lo[3];
+        std::vector<uint64_t> eo(nh + 1);
+        for (uint64_t i = 0; i <= nh; i++) eo[i] = g->huge_eoff_host[lo[3] + i] - g->huge_eoff_host[lo[3]];
+        if (g->shard_eoff.count < nh + 1) g->shard_eoff.alloc(g->st.tau_huge + 1, s);
+        TTC_CUDA(cudaMemcpyAsync(g->shard_eoff.get(), eo.data(), (nh + 1) * 8, cudaMemcpyHostToDevice, s));
+        TTC_CUDA(cudaStreamSynchronize(s));  // eo is about to go out of scope
+        const size_t bytes = heavy_scratch_bytes(g);
+        if (g->scratch.count < bytes) g->scratch.alloc(bytes, s);
+        b.huge = huge_args(g, g->scratch.get());
+        b.huge.tri += lo[3];
+        b.huge.eoff = g->shard_eoff.get();
+        b.huge.nh = nh;
+        b.huge.total = eo[nh];
+    }
+    count_bins(g, b, dq, k, acc, s);
+}
+
 void count_one_into(ttc_graph *g, const int64_t *dq, unsigned long long *acc, void *scratch, cudaStream_t s) {
-    const bool saved = g->profiling;
-    g->profiling = false;
+    ProfOff off;  // no timing events: the caller's handle may be profiled by another thread
     count_graph(g, dq, 1, acc, scratch, s);
-    g->profiling = saved;
 }
 
 uint32_t fused_capacity(int wide) { return wide ? FusedCap<unsigned long long>::CAP : FusedCap<uint32_t>::CAP; }
@@ -1146,11 +1354,9 @@ void count_sample(ttc_graph *g, const int64_t *dq, uint64_t first, uint64_t stri
         DevBuf<uint8_t> pre(bytes, s);
         ha.pre = pre.get();
         ha.per_tri = d_out.get() + 8 * (nlc + nfc);
-        const bool saved = g->profiling;
-        g->profiling = false;
+        ProfOff off;
         if (g->heavy_wide) run_huge<unsigned long long>(g, ha, dq, nullptr, flag.get(), s);
         else run_huge<uint32_t>(g, ha, dq, nullptr, flag.get(), s);
-        g->profiling = saved;
     }
     std::vector<unsigned long long> h(8 * n);
     std::vector<uint32_t> hv(3 * n);

@@ -178,6 +178,31 @@ __device__ __forceinline__ void search_n(AT &&at, uint32_t n, const int64_t (&bo
         for (int i = 0; i < N; i++) res[i] += v[i] < bound[i] ? 1u : 0u;
     }
 }
+// search_n for the bounds whose bit is set in `mask` (the others are not
+// searched: their lanes issue no loads and res stays 0).
+template <int N, typename AT>
+__device__ __forceinline__ void search_n_masked(AT &&at, uint32_t n, const int64_t (&bound)[N], uint32_t mask,
+                                                uint32_t (&res)[N]) {
+#pragma unroll
+    for (int i = 0; i < N; i++) res[i] = 0;
+    uint32_t len = n;
+    while (len > 1) {
+        const uint32_t half = len >> 1;
+        int64_t v[N];
+#pragma unroll
+        for (int i = 0; i < N; i++) v[i] = (mask >> i & 1u) ? at(res[i] + half - 1) : INT64_MAX;
+#pragma unroll
+        for (int i = 0; i < N; i++) res[i] += v[i] < bound[i] ? half : 0u;
+        len -= half;
+    }
+    if (len == 1) {
+        int64_t v[N];
+#pragma unroll
+        for (int i = 0; i < N; i++) v[i] = (mask >> i & 1u) ? at(res[i]) : INT64_MAX;
+#pragma unroll
+        for (int i = 0; i < N; i++) res[i] += v[i] < bound[i] ? 1u : 0u;
+    }
+}
 template <int N>
 __device__ __forceinline__ void search_n(const GList &l, const int64_t (&bound)[N], uint32_t (&res)[N]) {
     const int64_t *p = l.key + l.b;
@@ -192,6 +217,55 @@ __device__ __forceinline__ GList glist(const GraphView &gv, uint32_t p, uint32_t
     const uint32_t b = __ldg(gv.poff + p);
     return GList{gv.key, gv.fwd, b, __ldg(gv.poff + p + 1) - b, flip};
 }
+
+// ---------------------------------------------------------------- bulk copies
+// Global -> shared copies by the bulk-copy engine (cp.async.bulk), tracked
+// by a transaction-count mbarrier in shared memory.  Both addresses must be
+// 16-byte aligned and the size a multiple of 16.
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t arrivals) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(arrivals) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Orders this thread's earlier generic-proxy accesses of shared memory
+// before later bulk copies into it (after a barrier, for the whole CTA's).
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// One arrival that also expects `bytes` of bulk-copy transactions.
+__device__ __forceinline__ void mbar_arrive_expect(uint64_t *bar, uint32_t bytes) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
+                     smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_to_smem(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+// Waits for the phase with parity `parity` to complete, for at most `limit`
+// polls; false if it gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t limit) {
+    for (uint32_t i = 0; i < limit; i++) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(smem_addr(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// Bit of the count calls' device flag word set when a bounded wait gave up
+// (bit 0 is the overflow bit).
+constexpr unsigned long long FLAG_TIMEOUT = 2ull;
 
 // ---------------------------------------------------------------- accumulation
 __device__ __forceinline__ void add_checked(unsigned long long &acc, unsigned long long x, unsigned &ovf) {
@@ -224,6 +298,31 @@ __device__ __forceinline__ void warp_flush(unsigned long long (*s_acc)[256], uns
     ovf = 0;
 }
 
+// The same for 32-bit per-thread counters s_c[type][tid] whose carries went
+// to this warp's 64-bit words s_w[type] (see add_u32_carry).
+__device__ __forceinline__ void warp_flush32(uint32_t (*s_c)[256], unsigned long long *s_w,
+                                             unsigned long long *out, unsigned long long *flag, unsigned &ovf) {
+    const uint32_t lane = threadIdx.x & 31;
+#pragma unroll
+    for (int t = 0; t < 8; t++) {
+        unsigned long long v = s_c[t][threadIdx.x];
+        s_c[t][threadIdx.x] = 0;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);  // 32 terms < 2^32: no carry
+        __syncwarp();
+        if (lane == 0) {
+            add_checked(v, s_w[t], ovf);
+            s_w[t] = 0;
+            if (v) {
+                const unsigned long long old = atomicAdd(out + t, v);
+                ovf |= old + v < old;
+            }
+        }
+    }
+    if (__any_sync(0xffffffffu, ovf) && lane == 0) atomicOr(flag, 1ull);
+    ovf = 0;
+}
+
 // A 32-bit per-thread counter: a carry out of it adds 2^32 to the 64-bit
 // accumulator `wide` (a shared atomic, rare).
 __device__ __forceinline__ void add_u32_carry(uint32_t &cell, uint32_t n, unsigned long long *wide, unsigned &ovf) {
@@ -232,6 +331,20 @@ __device__ __forceinline__ void add_u32_carry(uint32_t &cell, uint32_t n, unsign
     if (cell < old) {
         const unsigned long long o = atomicAdd(wide, 1ull << 32);
         ovf |= o + (1ull << 32) < o;
+    }
+}
+
+// A 32-bit per-thread counter whose carries go to a 64-bit word of the
+// warp (shared by its lanes, hence the atomic).
+__device__ __forceinline__ void add_wide32(uint32_t &cell, unsigned long long n, unsigned long long *wide,
+                                           unsigned &ovf) {
+    const unsigned long long hi = n >> 32;
+    const uint32_t lo = (uint32_t)n, old = cell;
+    cell = old + lo;
+    const unsigned long long carry = hi + (cell < old ? 1ull : 0ull);
+    if (carry) {
+        const unsigned long long o = atomicAdd(wide, carry << 32);
+        ovf |= (carry >> 32) != 0 || o + (carry << 32) < o;
     }
 }
 
@@ -272,6 +385,7 @@ struct CView {
     const uint32_t *__restrict__ fwd;
     uint32_t b, n, flip;
     uint32_t px, py, f0, fx, fy, fn;
+    int64_t kfirst, klast;  // C's first and last keys (when loaded; else 0 and INT64_MAX)
     __device__ __forceinline__ uint32_t below(int64_t bound) const { return search_below(key + b, n, bound); }
     __device__ __forceinline__ uint32_t raw(uint32_t pos) const {
         return pos == px ? fx : pos == py ? fy : pos == n ? fn : pos == 0 ? f0 : __ldg(fwd + b + pos);
@@ -286,7 +400,7 @@ struct CView {
 // Adds the counts of one pair (x, y) of enumerated edges (x earlier, times
 // rx <= ry) for all three positions of C's edge.  xa: x is on A (else on B).
 // code = 4 dA + 2 dB (Fig. 4 with dC = 0).
-template <typename Acc>
+template <bool LOCKSTEP, typename Acc>
 __device__ __forceinline__ void light_pair(const CView &C, const KeyFmt &f, const Query &q, bool xa, int64_t rx,
                                            int64_t ry, uint32_t code, Acc &&acc) {
     if (!f.strict && q.d12 >= f.span && q.d23 >= f.span) {
@@ -304,29 +418,85 @@ __device__ __forceinline__ void light_pair(const CView &C, const KeyFmt &f, cons
         return;
     }
     const int64_t gap = ry - rx;
-    if (f.strict && gap == 0) return;  // x and y at one time: no strict order
-    // C's edges after y (from ay on) and before y (below by), likewise for x:
-    // by key, or (strict) by time
-    const uint32_t ay = f.strict ? cnt_le(C, f, ry) : C.py, by = f.strict ? cnt_lt(C, f, ry) : C.py;
-    const uint32_t ax = f.strict ? cnt_le(C, f, rx) : C.px, bx = f.strict ? cnt_lt(C, f, rx) : C.px;
+    // every case needs t_y - t_x <= d13 (d12, d23 <= d13 once normalised);
+    // in the strict reading x and y at one time have no order
+    if (gap > q.d13 || (f.strict && gap == 0)) return;
+    if constexpr (!LOCKSTEP) {
+        // one search per window end, each when its case can count (fewer
+        // registers than the lockstep form, for kernels that keep state for
+        // several queries)
+        const uint32_t ay = f.strict ? cnt_le(C, f, ry) : C.py, by = f.strict ? cnt_lt(C, f, ry) : C.py;
+        const uint32_t ax = f.strict ? cnt_le(C, f, rx) : C.px, bx = f.strict ? cnt_lt(C, f, rx) : C.px;
+        auto add = [&](uint32_t pack, uint32_t lo, uint32_t hi) {
+            const uint32_t n0 = C.d0_range(lo, hi);
+            acc(type_in(pack, code), n0);
+            acc(type_in(pack, code | 1u), (hi - lo) - n0);
+        };
+        if (gap <= q.d12) {  // C third
+            const uint32_t hi = cnt_le(C, f, min(ry + q.d23, rx + q.d13));
+            if (hi > ay) add(xa ? TP1 : TP2, ay, hi);
+        }
+        {  // C second (gap <= d13 here)
+            const uint32_t lo = max(ax, cnt_lt(C, f, ry - q.d23));
+            const uint32_t hi = min(by, cnt_le(C, f, rx + q.d12));
+            if (hi > lo) add(xa ? TP3 : TP4, lo, hi);
+        }
+        if (gap <= q.d23) {  // C first
+            const uint32_t lo = cnt_lt(C, f, max(rx - q.d12, ry - q.d13));
+            if (bx > lo) add(xa ? TP5 : TP6, lo, bx);
+        }
+        return;
+    }
+    // the window ends of the three cases, found by one lockstep search (a
+    // case whose gap condition fails gets bound 0, which needs no load):
+    //   C third  [after y, le(min(ry + d23, rx + d13)))
+    //   C second [max(after x, lt(ry - d23)), min(before y, le(rx + d12)))
+    //   C first  [lt(max(rx - d12, ry - d13)), before x)
+    // In the strict reading "after" and "before" are time bounds too.
+    constexpr int NB = 8;
+    const int64_t b[NB] = {gap <= q.d12 ? le_bound(f, min(ry + q.d23, rx + q.d13)) : 0,
+                           gap <= q.d13 ? lt_bound(f, ry - q.d23) : 0,
+                           gap <= q.d13 ? le_bound(f, rx + q.d12) : 0,
+                           gap <= q.d23 ? lt_bound(f, max(rx - q.d12, ry - q.d13)) : 0,
+                           f.strict ? le_bound(f, ry) : 0, f.strict ? lt_bound(f, ry) : 0,
+                           f.strict ? le_bound(f, rx) : 0, f.strict ? lt_bound(f, rx) : 0};
+    // a bound at or below C's first key counts nothing and one above its
+    // last key counts all of C; only the others are searched
+    uint32_t p[NB], mask = 0;
+#pragma unroll
+    for (int i = 0; i < NB; i++) {
+        p[i] = b[i] <= C.kfirst ? 0u : b[i] > C.klast ? C.n : 0u;
+        if (b[i] > C.kfirst && b[i] <= C.klast && (f.strict || i < 4)) mask |= 1u << i;
+    }
+    if (mask) {
+        uint32_t sp[NB];
+        if (f.strict) {
+            search_n_masked<8>([&](uint32_t i) { return __ldg(C.key + C.b + i); }, C.n, b, mask, sp);
+        } else {
+            const int64_t b4[4] = {b[0], b[1], b[2], b[3]};
+            uint32_t s4[4];
+            search_n_masked<4>([&](uint32_t i) { return __ldg(C.key + C.b + i); }, C.n, b4, mask, s4);
+#pragma unroll
+            for (int i = 0; i < 4; i++) sp[i] = s4[i];
+        }
+#pragma unroll
+        for (int i = 0; i < NB; i++)
+            if (mask >> i & 1u) p[i] = sp[i];
+    }
+    // C's edges after y start at ay, those before y end at by; likewise x
+    const uint32_t ay = f.strict ? p[4] : C.py, by = f.strict ? p[5] : C.py;
+    const uint32_t ax = f.strict ? p[6] : C.px, bx = f.strict ? p[7] : C.px;
     auto add = [&](uint32_t pack, uint32_t lo, uint32_t hi) {
         const uint32_t n0 = C.d0_range(lo, hi);
         acc(type_in(pack, code), n0);
         acc(type_in(pack, code | 1u), (hi - lo) - n0);
     };
-    if (gap <= q.d12) {  // C third
-        const uint32_t hi = cnt_le(C, f, min(ry + q.d23, rx + q.d13));
-        if (hi > ay) add(xa ? TP1 : TP2, ay, hi);
-    }
-    if (gap <= q.d13) {  // C second
-        const uint32_t lo = max(ax, cnt_lt(C, f, ry - q.d23));
-        const uint32_t hi = min(by, cnt_le(C, f, rx + q.d12));
+    if (gap <= q.d12 && p[0] > ay) add(xa ? TP1 : TP2, ay, p[0]);  // C third
+    if (gap <= q.d13) {                                            // C second
+        const uint32_t lo = max(ax, p[1]), hi = min(by, p[2]);
         if (hi > lo) add(xa ? TP3 : TP4, lo, hi);
     }
-    if (gap <= q.d23) {  // C first
-        const uint32_t lo = cnt_lt(C, f, max(rx - q.d12, ry - q.d13));
-        if (bx > lo) add(xa ? TP5 : TP6, lo, bx);
-    }
+    if (gap <= q.d23 && bx > p[3]) add(xa ? TP5 : TP6, p[3], bx);  // C first
 }
 
 // One (a, b) pair of a light triangle (Lemma 1 over A x B): a = A's edge ai
@@ -335,15 +505,24 @@ __device__ __forceinline__ void light_pair(const CView &C, const KeyFmt &f, cons
 // fn = fwd[cb + cn] are given, else loaded here.  A pair whose time gap
 // exceeds gmax (the largest d13 of the queries at hand) is skipped;
 // otherwise each(C, a_first, rx, ry, code) runs light_pair for each query.
+// gfin: the largest d13 of the queries whose windows do not cover the whole
+// time span (-1 if none).
 template <typename EACH>
 __device__ __forceinline__ void light_count_pair(const GraphView &gv, const KeyFmt &f, uint32_t ab, uint32_t bb,
                                                  uint32_t cb, uint32_t cn, uint32_t fl, bool have_ends, uint32_t f0,
-                                                 uint32_t fn, uint32_t ai, uint32_t bi, int64_t gmax, EACH &&each) {
+                                                 uint32_t fn, uint32_t ai, uint32_t bi, int64_t gmax, int64_t gfin,
+                                                 EACH &&each) {
     const int64_t ka = __ldg(gv.key + ab + ai), kb = __ldg(gv.key + bb + bi);
     const int64_t ra = ka >> f.shift, rb = kb >> f.shift;
     const bool a_first = ka < kb;
     const int64_t gap = a_first ? rb - ra : ra - rb;
     if (gap > gmax) return;
+    // C's first and last keys settle most window ends without a search;
+    // only a query with finite windows and d13 >= gap can need them (gfin:
+    // the largest d13 of such queries, -1 if none).  Loaded before the key
+    // searches, they arrive while those run.
+    const bool ends = gap <= gfin;
+    const int64_t kfirst = ends ? __ldg(gv.key + cb) : 0, klast = ends ? __ldg(gv.key + cb + cn - 1) : INT64_MAX;
     const uint32_t dA = (uint32_t)(ka & 1) ^ (fl & TriRec::FLIP_A);
     const uint32_t dB = (uint32_t)(kb & 1) ^ ((fl & TriRec::FLIP_B) ? 1u : 0u);
     const uint32_t code = (dA << 2) | (dB << 1);
@@ -364,6 +543,8 @@ __device__ __forceinline__ void light_count_pair(const GraphView &gv, const KeyF
     C.fn = have_ends ? fn : __ldg(gv.fwd + cb + cn);
     C.fx = __ldg(gv.fwd + cb + C.px);
     C.fy = __ldg(gv.fwd + cb + C.py);
+    C.kfirst = kfirst;
+    C.klast = klast;
     each(C, a_first, a_first ? ra : rb, a_first ? rb : ra, code);
 }
 

@@ -77,6 +77,13 @@ struct ttc_graph {
     ttc::DevBuf<GraphView> view;        // [1]
     ttc::DevBuf<uint64_t> prefix;       // [6]: {0, light chunks, 0, n_hwarp, 0, n_hcta}
 
+    // sharded counts: per-bin views of one shard, and the huge offsets
+    // (device copy of the shard's slice; host copy of the whole array)
+    ttc::DevBuf<GraphView> shard_view;   // [3]
+    ttc::DevBuf<uint64_t> shard_pre;     // [6]
+    ttc::DevBuf<uint64_t> shard_eoff;    // [tau_huge + 1]
+    std::vector<uint64_t> huge_eoff_host;
+
     // per-call device scratch, guarded by `mu`
     std::mutex mu;
     ttc::DevBuf<unsigned long long> acc;  // [cap * 8 + 1]: counts and the overflow flag
@@ -114,6 +121,13 @@ void prof_end(ttc_graph *g, cudaStream_t s);
 // (dq: k * 3 int64 as d13, d12, d23), accumulated into acc ([k][8] u64 plus a
 // trailing overflow flag), which the caller zeroes.
 void count_queue(ttc_graph *g, const int64_t *dq, uint32_t k, unsigned long long *acc, cudaStream_t s);
+// The same for shard `shard` of `nshards`: the light, warp, CTA and huge
+// records of the handle's bins are each cut into nshards consecutive slices
+// of near-equal length, and only this shard's slices are counted.  Every
+// static triangle lies in exactly one slice, so the shards' counts sum to
+// count_queue's.  Not for TTC_LOAD_STREAM handles.
+void count_queue_shard(ttc_graph *g, const int64_t *dq, uint32_t k, unsigned long long *acc, uint32_t shard,
+                       uint32_t nshards, cudaStream_t s);
 
 // load.cu: for a TTC_LOAD_STREAM handle, the light triangles' counts for k
 // normalised queries (dq on the device), added into acc ([k][8] plus the
@@ -166,5 +180,10 @@ uint32_t warp_capacity(int wide);
 uint32_t fused_capacity(int wide);
 
 uint32_t default_light_max_pairs();
+
+// Turns the count kernels' device flag word into a failure: bit 1 (a
+// bounded wait in a kernel gave up) is TTC_ERR_TIMEOUT, any other bit (a
+// carry out of a 64-bit count) TTC_ERR_OVERFLOW; 0 returns.
+void check_count_flag(unsigned long long flag);
 
 }  // namespace ttc

@@ -1672,14 +1672,7 @@ void launch_enum(const uint2 *items, uint32_t nitems, const TriCsr &tc, const Re
                  uint32_t nv_cap, cudaStream_t s) {
     if (!nitems) return;
     const size_t smem = TRI_WARPS * tri_warp_smem(nv_cap);
-    static int configured_device = -1;
-    int dev = 0;
-    TTC_CUDA(cudaGetDevice(&dev));
-    if (configured_device != dev) {
-        TTC_CUDA(cudaFuncSetAttribute(tri_enum_kernel<EM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)(TRI_WARPS * tri_warp_smem(TRI_NV_CAP))));
-        configured_device = dev;
-    }
+    ensure_smem((const void *)tri_enum_kernel<EM>, TRI_WARPS * tri_warp_smem(TRI_NV_CAP));
     int occ = 1;
     TTC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, tri_enum_kernel<EM>, TRI_THREADS, smem));
     const unsigned grid = (unsigned)std::min<uint64_t>(nitems / TRI_WARPS + 1, (uint64_t)sm_count() * std::max(1, occ));
@@ -1772,9 +1765,7 @@ void launch_seg_group(int64_t *key, const uint32_t *poff, const uint32_t *lists,
                       const unsigned int *count, int c, cudaStream_t s) {
     constexpr int CTA = T >= 128 ? T : 128;
     const size_t smem = T >= 64 ? (size_t)E * T * 8 : 0;
-    if (smem > 48 * 1024)
-        TTC_CUDA(cudaFuncSetAttribute(seg_sort_group_kernel<E, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
+    if (smem > 48 * 1024) ensure_smem((const void *)seg_sort_group_kernel<E, T>, smem);
     int occ = 0;
     TTC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, seg_sort_group_kernel<E, T>, CTA, smem));
     const unsigned grid = (uint32_t)sm_count() * std::max(1, occ);
@@ -1845,7 +1836,9 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
     st.m = m;
     const uint64_t n = m ? (uint64_t)is.max_id + 1 : 0;
     st.n = m0 ? (uint64_t)is.max_id + 1 : 0;
-    g->key.alloc(m, s);
+    // two keys of padding: the count kernels' bulk copies move whole 16-byte
+    // words, so a list that ends on an odd key reads 8 bytes beyond it
+    g->key.alloc(m + 2, s);
     g->fwd.alloc(m + 1, s);
     if (m == 0) {
         g->poff.alloc(1, s);

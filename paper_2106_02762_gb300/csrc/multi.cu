@@ -310,7 +310,7 @@ void count_multi(ttc_graph *const *gs, const ttc_delta *d, uint32_t G, uint64_t 
     TTC_CUDA(cudaGraphLaunch(plan->exec, plan->stream));
     note_launch();
     TTC_CUDA(cudaStreamSynchronize(plan->stream));
-    if (plan->h_acc[8 * (size_t)G]) fail(TTC_ERR_OVERFLOW, "a count exceeds 2^64 - 1");
+    check_count_flag(plan->h_acc[8 * (size_t)G]);
     memcpy(out, plan->h_acc, 8 * (size_t)G * 8);
 }
 

@@ -1,13 +1,14 @@
 // ttc_count_noalloc: one query without any device allocation.
 //
-// Some callers cannot allocate device memory at the moment they count: code
-// running inside a CUDA stream capture (cudaMalloc is not capturable), hosts
+// Some callers cannot allocate device memory at the moment they count: hosts
 // whose framework's caching allocator owns nearly all of HBM and forbids
 // foreign allocations, and latency-critical loops where an allocation can
 // stall or synchronise the device.  This entry point serves them: it runs the
 // same light and prefix-sum kernels as ttc_count, but every device buffer it
 // needs beyond the graph and the caller's output lives in one file-scope
-// __device__ array of fixed size, reserved when the library is loaded.
+// __device__ array of fixed size, reserved when the library is loaded.  The
+// call is synchronous: it waits for its kernels and copies the counts back
+// before it returns.
 #include <cstring>
 #include <mutex>
 
@@ -67,6 +68,13 @@ extern "C" ttc_status ttc_count_noalloc(ttc_graph *g, const ttc_delta *d, uint64
                  "graph needs %zu bytes of prefix scratch; ttc_count_noalloc holds %zu (use ttc_count)", need,
                  (size_t)(TTC_NOALLOC_SCRATCH_BYTES - NOALLOC_HEAD));
         std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        int caller_dev = 0;
+        TTC_CUDA(cudaGetDevice(&caller_dev));
+        // the caller's current device is current again whenever this returns
+        struct Restore {
+            int dev;
+            ~Restore() { cudaSetDevice(dev); }
+        } restore{caller_dev};
         TTC_CUDA(cudaSetDevice(g->device));
         cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : g->stream;
         unsigned char *base = static_cast<unsigned char *>(noalloc_base(g->device));
@@ -80,7 +88,7 @@ extern "C" ttc_status ttc_count_noalloc(ttc_graph *g, const ttc_delta *d, uint64
         unsigned long long h[9];
         TTC_CUDA(cudaMemcpyAsync(h, acc, sizeof h, cudaMemcpyDeviceToHost, s));
         TTC_CUDA(cudaStreamSynchronize(s));
-        if (h[8]) fail(TTC_ERR_OVERFLOW, "a count exceeds 2^64 - 1");
+        check_count_flag(h[8]);
         memcpy(out, h, 8 * sizeof(uint64_t));
         return TTC_OK;
     } catch (const Failure &f) {

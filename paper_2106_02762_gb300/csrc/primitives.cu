@@ -279,13 +279,7 @@ bool radix_sort_passes(uint64_t *keys, V *vals, uint64_t *kalt, V *valt, size_t 
     uint64_t *kin = keys, *kout = kalt;
     V *vin = vals, *vout = valt;
     const size_t dyn = (size_t)RS_TILE * (sizeof(uint64_t) + sizeof(V));
-    static int configured_device = -1;
-    int dev = 0;
-    TTC_CUDA(cudaGetDevice(&dev));
-    if (configured_device != dev) {
-        TTC_CUDA(cudaFuncSetAttribute(radix_scatter_kernel<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
-        configured_device = dev;
-    }
+    ensure_smem((const void *)radix_scatter_kernel<V>, dyn);
     for (int shift = begin_bit; shift < end_bit; shift += RADIX_BITS) {
         const int width = std::min(RADIX_BITS, end_bit - shift);
         const uint32_t mask = (1u << width) - 1u;

@@ -15,8 +15,8 @@
 // reserve) covers an estimate of its load footprint; otherwise it evicts the
 // least recently used idle graphs (no queued or running queries) first.
 //
-// Every wait is bounded: the worker sleeps at most 200 us between polls and
-// ttc_serve_drain gives up after its timeout.
+// Every wait is bounded: the worker sleeps at most wait_limit_us (default
+// 200 us) between polls, and ttc_serve_drain gives up after its timeout.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -148,11 +148,11 @@ bool ttc_server::complete_finished() {
         if (e == cudaErrorNotReady) continue;
         const auto now = Clock::now();
         const uint32_t k = (uint32_t)slot.batch.size();
-        const bool ovf = e == cudaSuccess && slot.h_acc[8 * (size_t)k] != 0;
+        const unsigned long long fl = e == cudaSuccess ? slot.h_acc[8 * (size_t)k] : 0ull;
         for (uint32_t i = 0; i < k; i++) {
             Result &r = results[slot.batch[i].ticket];
             r.done = true;
-            r.status = e != cudaSuccess ? TTC_ERR_CUDA : ovf ? TTC_ERR_OVERFLOW : TTC_OK;
+            r.status = e != cudaSuccess ? TTC_ERR_CUDA : (fl & 2ull) ? TTC_ERR_TIMEOUT : fl ? TTC_ERR_OVERFLOW : TTC_OK;
             if (e == cudaSuccess) memcpy(r.out, slot.h_acc + 8 * (size_t)i, 64);
             r.latency = std::chrono::duration<double>(now - slot.batch[i].submit).count();
         }
@@ -209,7 +209,7 @@ void ttc_server::run() {
         const bool a = complete_finished();
         const bool b = paused ? false : launch_ready();
         if (a) cv_done.notify_all();
-        if (!a && !b) cv.wait_for(lk, std::chrono::microseconds(200));
+        if (!a && !b) cv.wait_for(lk, std::chrono::microseconds(opts.wait_limit_us));
     }
 }
 
@@ -224,6 +224,7 @@ ttc_server *ttc_server_create(const ttc_server_opts *o) {
         if (!s->opts.max_batch) s->opts.max_batch = 256;
         if (!s->opts.max_queue) s->opts.max_queue = 65536;
         if (!s->opts.streams) s->opts.streams = 4;
+        if (!s->opts.wait_limit_us) s->opts.wait_limit_us = 200;
         TTC_CUDA(cudaGetDevice(&s->device));
         s->slots.resize(s->opts.streams);
         for (auto &slot : s->slots) {

@@ -20,8 +20,10 @@ template <typename K, typename V>
 void radix_sort_bufs(DevBuf<K> &keys, DevBuf<V> &vals, size_t n, int begin_bit, int end_bit, cudaStream_t s) {
     static_assert(sizeof(K) == 8 && (sizeof(V) == 4 || sizeof(V) == 8), "64-bit keys, 32- or 64-bit values");
     if (n <= 1 || end_bit <= begin_bit) return;
-    DevBuf<K> kalt(n, s);
-    DevBuf<V> valt(n, s);
+    // the scratch pair is as long as the buffers it may replace (a buffer
+    // allocated with padding keeps it)
+    DevBuf<K> kalt(keys.count > n ? keys.count : n, s);
+    DevBuf<V> valt(vals.count > n ? vals.count : n, s);
     uint64_t *k0 = reinterpret_cast<uint64_t *>(keys.get()), *k1 = reinterpret_cast<uint64_t *>(kalt.get());
     bool alt;
     if constexpr (sizeof(V) == 4)

@@ -35,7 +35,7 @@ EXPORTS = ["ttc_load", "ttc_load_ex", "ttc_free", "ttc_graph_info", "ttc_count",
            "ttc_serve_pause", "ttc_serve_set_reserve",
            "ttc_server_info", "ttc_last_error", "ttc_version", "ttc_debug_fail_alloc_after",
            "ttc_debug_launch_count", "ttc_set_profiling", "ttc_profile_read", "ttc_count_noalloc",
-           "ttc_release_cached", "ttc_memory_info", "ttc_count_grid"]
+           "ttc_release_cached", "ttc_memory_info", "ttc_count_grid", "ttc_count_shard"]
 
 
 class TTCError(RuntimeError):
@@ -66,7 +66,7 @@ class KernelTime(ctypes.Structure):
 
 class ServerOpts(ctypes.Structure):
     _fields_ = [("hbm_reserve_bytes", ctypes.c_uint64), ("max_batch", ctypes.c_uint32),
-                ("max_queue", ctypes.c_uint32), ("streams", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("max_queue", ctypes.c_uint32), ("streams", ctypes.c_uint32), ("wait_limit_us", ctypes.c_uint32)]
 
 
 class ServerStats(ctypes.Structure):
@@ -94,6 +94,7 @@ def lib():
             "ttc_count": ([p, p, p], ctypes.c_int),
             "ttc_count_batch": ([p, p, u32, p], ctypes.c_int),
             "ttc_count_batch_async": ([p, p, u32, p, p], ctypes.c_int),
+            "ttc_count_shard": ([p, p, u32, u32, u32, p], ctypes.c_int),
             "ttc_count_multi": ([p, p, u32, p], ctypes.c_int),
             "ttc_count_sample": ([p, p, u64, u64, u64, p, p, p], ctypes.c_int),
             "ttc_server_create": ([p], p),
@@ -223,6 +224,13 @@ class Graph:
         check(lib().ttc_count_batch(self.handle, dp, d.shape[0], out.ctypes.data))
         return out
 
+    def count_shard(self, deltas, shard: int, nshards: int) -> np.ndarray:
+        """Shard `shard` of `nshards` of count_batch (the shards' counts sum to it)."""
+        d, dp = _deltas(deltas)
+        out = np.zeros((d.shape[0], NUM_TYPES), dtype=np.uint64)
+        check(lib().ttc_count_shard(self.handle, dp, d.shape[0], shard, nshards, out.ctypes.data))
+        return out
+
     def count_batch_async(self, d_dev_ptr: int, k: int, out_dev_ptr: int, stream_ptr: int = 0):
         """Device pointers: k deltas (int64 x 3) in, k x 8 uint64 out."""
         check(lib().ttc_count_batch_async(self.handle, d_dev_ptr, k, out_dev_ptr, stream_ptr or None))
@@ -271,8 +279,8 @@ def count_multi(graphs, deltas) -> np.ndarray:
 class Server:
     """Continuous-batching server (``ttc_server_*``)."""
 
-    def __init__(self, hbm_reserve_bytes=0, max_batch=0, max_queue=0, streams=0):
-        o = ServerOpts(hbm_reserve_bytes, max_batch, max_queue, streams, 0)
+    def __init__(self, hbm_reserve_bytes=0, max_batch=0, max_queue=0, streams=0, wait_limit_us=0):
+        o = ServerOpts(hbm_reserve_bytes, max_batch, max_queue, streams, wait_limit_us)
         h = lib().ttc_server_create(ctypes.byref(o))
         if not h:
             raise TTCError(-8, last_error())

@@ -41,3 +41,24 @@ def hand_cases():
                 exp = [int(x) for x in line[arrow + 1:]]
                 cases[-1][2].append((d, exp))
     return cases
+
+
+def power_law_counts():
+    """The oracle's counts on the full power-law workload, written by
+    make_power_law_counts.py.  Returns (fields, [(delta triple, counts[8])]):
+    fields holds 'sha256' (of the src, dst, t arrays) and the static
+    statistics n, m, m_s, tau, sigma_max, work_bytes, prod as ints."""
+    fields, rows = {}, []
+    with open(os.path.join(HERE, "power_law_1m_counts.txt")) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if not line:
+                continue
+            key, val = (x.strip() for x in line.split(":", 1))
+            if key.startswith("delta "):
+                rows.append((tuple(int(x) for x in key.split()[1:]), [int(x) for x in val.split()]))
+            elif key == "sha256":
+                fields[key] = val
+            else:
+                fields[key] = int(val)
+    return fields, rows

@@ -69,6 +69,25 @@ def test_count_multi_matches_oracle_and_replays():
         h.free()
 
 
+@pytest.mark.slow
+def test_many_graph_workload_sample_matches_oracle():
+    # a seeded sample of 64 of the 4096 graphs of the many-graphs workload
+    # (every 64th spec: n log-uniform in [1e3, 1e5], average degree U[4, 32],
+    # Chung-Lu 2.3, Geometric(0.3) multiplicities, own delta per graph), in
+    # one many-graph launch, against the oracle graph by graph
+    n, pairs, deltas, seeds = synth.many_graph_specs()
+    pick = np.arange(0, n.size, 64)
+    gs = [synth.many_graph(n[i], pairs[i], seeds[i]) for i in pick]
+    dl = [tuple(int(x) for x in deltas[i]) for i in pick]
+    handles = [ttc.Graph(*e) for e in gs]
+    got = ttc.count_multi(handles, dl)
+    want = np.stack([oracle.count_fwd(*e, [q])[0] for e, q in zip(gs, dl)])
+    assert (got == want).all()
+    assert (want.sum(axis=1) > 0).sum() >= 32
+    for h in handles:
+        h.free()
+
+
 def test_count_multi_equals_plain_calls():
     gs = _small_graphs(count=12, seed=11)
     handles = [ttc.Graph(s, d, t) for s, d, t, _ in gs]

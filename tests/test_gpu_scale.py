@@ -1,15 +1,23 @@
 """Full-size checks: the power-law workload at its benchmark size (n = 1M,
-10M pairs, ~60M edges) in the launch configuration bench.py times.  The
-oracle cannot enumerate every triangle of it in test time, so the CUDA path's
-per-triangle counts are compared with the oracle's one triangle at a time, on
-strided samples of both the light and the prefix-sum bins, and the totals are
-checked against properties that hold at any size.
+10M pairs, ~60M edges) in the launch configuration bench.py times.
+
+- Totals: the oracle's counts for the step's two queries and a wide finite
+  one, computed once by tests/golden/make_power_law_counts.py (O1 with the
+  forward enumeration) and stored with the input's SHA-256, are compared
+  bit-exactly; the unbounded total also equals Def. 1's closed form
+  (sum over static triangles of s_uv s_uw s_vw).
+- Per triangle: strided samples of the light and the prefix-sum bins are
+  compared with the oracle one triangle at a time.
+- Properties that hold at any size: monotonicity and normalisation.
 """
+import hashlib
+
 import numpy as np
 import pytest
 
 import oracle
 from paper_2106_02762_gb300 import synth, ttc
+from tests.golden import readers
 
 pytestmark = pytest.mark.gpu
 
@@ -45,6 +53,34 @@ def test_sample_matches_oracle_small():
     tri, per = g.sample(synth.LARGE_PLAIN_DELTA, 0, 1, info["tau"])
     assert len(tri) == info["tau"]
     assert (per.sum(axis=0) == g.count(synth.LARGE_PLAIN_DELTA)).all()
+    g.free()
+
+
+def _sha256(src, dst, t):
+    h = hashlib.sha256()
+    for a in (src, dst, t):
+        h.update(np.ascontiguousarray(a).tobytes())
+    return h.hexdigest()
+
+
+@pytest.mark.slow
+def test_full_size_power_law_totals_match_oracle():
+    fields, rows = readers.power_law_counts()
+    s, d, t = synth.large_plain()
+    assert _sha256(s, d, t) == fields["sha256"], "the generator made another graph than the stored counts'"
+    g = ttc.Graph(s, d, t)
+    info = g.info()
+    for k in ("n", "m", "m_s", "tau", "sigma_max", "work_bytes"):
+        assert info[k] == fields[k], k
+    deltas = [r[0] for r in rows]
+    want = np.array([r[1] for r in rows], dtype=np.uint64)
+    # the bench step's launch configuration: one batched call of its queries
+    got = g.count_batch(deltas[:2])
+    assert (got == want[:2]).all()
+    for q, dq in enumerate(deltas):
+        assert (g.count(dq) == want[q]).all(), dq
+    unb = deltas.index(synth.LARGE_PLAIN_DELTA_UNBOUNDED)
+    assert int(want[unb].sum()) == fields["prod"]
     g.free()
 
 

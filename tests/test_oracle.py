@@ -262,6 +262,43 @@ def test_stats_against_networkx():
     assert st["m"] == s.size
 
 
+def test_stats_hand_case():
+    # pairs {0,1} x2, {0,2} x3, {1,2} x1, {2,3} x1, {1,3} x4 (directions mixed):
+    # static triangles {0,1,2} (multiplicities 2, 3, 1) and {1,2,3} (1, 1, 4), so
+    # work_bytes = (8 (2+3+1) + 12) + (8 (1+1+4) + 12) = 120 and the unbounded
+    # total (Def. 1 with every window open) = 2*3*1 + 1*1*4 = 10
+    edges = [(0, 1, 5), (1, 0, 9), (0, 2, 1), (2, 0, 2), (0, 2, 3), (1, 2, 7),
+             (3, 2, 4), (1, 3, 6), (3, 1, 8), (1, 3, 10), (3, 1, 11)]
+    s, d, t = _arr(edges)
+    for st in (oracle.stats(s, d, t), oracle.stats_fwd(s, d, t)):
+        assert st == {"n": 4, "m": 11, "m_s": 5, "tau": 2, "sigma_max": 4, "work_bytes": 120, "prod": 10}
+    assert int(oracle.count(s, d, t, [(BIG, BIG, BIG)]).sum()) == 10
+
+
+def test_forward_rule_matches_plain_rule():
+    # the forward enumeration must visit the same triangles: identical
+    # statistics and identical counts, on uniform and on hub-heavy graphs
+    deltas = [(1500, 700, 900), (BIG, BIG, BIG), (0, 0, 0), (3000, 3000, 100)]
+    graphs = [synth.er_temporal(31, 60, 500, 3000, 3.0), synth.large_plain(scale=0.002)]
+    graphs += [synth.random_tiny(40 + i, n=7, m=30, t_range=6) for i in range(20)]
+    for s, d, t in graphs:
+        assert oracle.stats_fwd(s, d, t) == oracle.stats(s, d, t)
+        assert (oracle.count_fwd(s, d, t, deltas) == oracle.count(s, d, t, deltas)).all()
+        assert (oracle.count_fwd(s, d, t, deltas, strict=True) == oracle.count(s, d, t, deltas, strict=True)).all()
+
+
+def test_full_size_golden_counts_are_consistent():
+    # the stored full-size counts: unbounded total = sum of s_uv s_uw s_vw,
+    # and monotone in the windows (the wide finite triple lies between)
+    fields, rows = readers.power_law_counts()
+    by = {d: np.asarray(c, dtype=np.uint64) for d, c in rows}
+    unb = by[synth.LARGE_PLAIN_DELTA_UNBOUNDED]
+    assert int(unb.sum()) == fields["prod"]
+    for d, c in by.items():
+        assert (c <= unb).all()
+    assert (by[synth.LARGE_PLAIN_DELTA] <= by[(1 << 26, 1 << 25, 1 << 25)]).all()
+
+
 def test_parts_partition_the_count():
     s, d, t = synth.er_temporal(18, 60, 400, 3000, 3.0)
     deltas = [(1500, 700, 900), (BIG, BIG, BIG)]
