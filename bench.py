@@ -3,14 +3,22 @@
 
 One step = the whole hot path on one synthetic graph whose edge arrays are
 already resident in device memory: ttc_load (ingest, pair lists, k-core peel,
-orientation, triangle list) followed by one delta-query (ttc_count).  The
-metric is temporal edges per second per delta-query.
+orientation, triangle list) followed by one ttc_count_batch of the
+configured delta and the same delta with every window unbounded (so no
+window lets a kernel skip work).  The metric is temporal edges per second
+per step; on N GPUs every rank loads the graph and counts its shard of the
+triangles, and the counts are summed.
 
 Workload (default): Chung-Lu power-law skeleton, n = 1M vertices, 10M vertex
 pairs, degree exponent 2.1, multiplicity pmf k^-2 on [1, 1e4] (about 60M
 edges), lognormal(6, 2) inter-arrival times over a 2^31 s span; delta =
 (86400, 43200, 43200).  The edge arrays (~1 GB) and the resident graph exceed
 the 129 MB L2, so no flush is needed between steps.
+
+Beside the step the line carries per-kernel times of the configured, the
+unbounded and the batched queries, the roofline of the unbounded light
+kernel, the tuned light threshold, the 64-delta sweep, and (unless
+--no-extras) the many-graphs and served measurements.
 
 Prints one JSON line (rank 0).  --impl reference times the CPU oracle
 instead, on a bounded sample of the same workload.
@@ -557,6 +565,13 @@ def run_ours(args):
     # the windows pruning it (the paper's cost does not depend on the windows)
     step_deltas = step_queries(delta)
 
+    # the light threshold, tuned on this graph (rank 0; every rank then loads
+    # with the same explicit value, so all hold the same bins)
+    chosen, tune_ms = 0, None
+    if rank == 0:
+        chosen, tune_ms = ttc.tune_light(d_src, d_dst, d_t, step_deltas, stream=sptr)
+    chosen = int(allreduce_max(float(chosen), ws, dev))
+
     # on N GPUs every rank loads the same graph and counts its shard of the
     # triangle list; the ranks' counts are summed (the one exchange)
     def count(g):
@@ -566,11 +581,12 @@ def run_ours(args):
         return shard.count_sharded(g, step_deltas, rank, ws, device=dev)
 
     def step_device():
-        g = ttc.Graph(d_src, d_dst, d_t, stream=sptr)
+        g = ttc.Graph(d_src, d_dst, d_t, stream=sptr, light_max_pairs=chosen)
         return g, count(g)
 
     def step_host():
-        g = ttc.Graph(h_src.numpy().view(np.uint32), h_dst.numpy().view(np.uint32), h_t.numpy(), stream=sptr)
+        g = ttc.Graph(h_src.numpy().view(np.uint32), h_dst.numpy().view(np.uint32), h_t.numpy(), stream=sptr,
+                      light_max_pairs=chosen)
         return g, count(g)
 
     # warm-up
@@ -613,7 +629,7 @@ def run_ours(args):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        g = ttc.Graph(d_src, d_dst, d_t, stream=sptr)
+        g = ttc.Graph(d_src, d_dst, d_t, stream=sptr, light_max_pairs=chosen)
         e1.record(stream)
         e1.synchronize()
         load_ms.append(e0.elapsed_time(e1))
@@ -624,7 +640,7 @@ def run_ours(args):
     # recorded by the library on the graph's stream
     torch.cuda.synchronize()
     w = time.perf_counter()
-    g = ttc.Graph(d_src, d_dst, d_t, stream=sptr, profile_load=True)
+    g = ttc.Graph(d_src, d_dst, d_t, stream=sptr, profile_load=True, light_max_pairs=chosen)
     load_wall = time.perf_counter() - w
     load_phases = {k: v for k, v in g.profile()}
     info = g.info()
@@ -668,7 +684,7 @@ def run_ours(args):
         e1 = torch.cuda.Event(enable_timing=True)
         e2 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        gs = ttc.Graph(d_src, d_dst, d_t, stream=sptr, streamed=True)
+        gs = ttc.Graph(d_src, d_dst, d_t, stream=sptr, streamed=True, light_max_pairs=chosen)
         e1.record(stream)
         out_s = gs.count_batch(step_deltas)
         e2.record(stream)
@@ -729,7 +745,7 @@ def run_ours(args):
     multi = served = None
     if rank == 0 and not args.no_extras:
         multi = multi_measure(ttc, torch, args.multi_graphs)
-        served = serve_measure(ttc, torch, [2000.0, 20000.0], args.serve_seconds, ladder_scale=0.1)
+        served = serve_measure(ttc, torch, [2000.0, 50000.0], args.serve_seconds, ladder_scale=0.1)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -756,6 +772,8 @@ def run_ours(args):
                                 "kernels_ms": {k: v * 1e3 for k, v in kern_unb.items()}},
             "step_count": {"deltas": [list(q) for q in step_deltas], "ms": b_s * 1e3,
                            "kernels_ms": {k: v * 1e3 for k, v in kern_step.items()}},
+            "light_threshold": {"chosen": chosen, "candidates_ms": tune_ms,
+                                "note": "ttc_tune_light: load + the step's batch at each threshold"},
             "load_ms": load_s * 1e3,
             "load_edges_per_s": m / load_s,
             "load_phases_ms": {"wall": load_wall * 1e3, **load_phases},

@@ -150,7 +150,7 @@ typedef struct {
     uint64_t light_pairs;    /* sum over one-thread-per-triangle-path triangles of
                                 sigma_A * sigma_B (the (a, b) pairs that path visits) */
     uint32_t key_bits;       /* bits of the packed per-edge key */
-    uint32_t reserved;
+    uint32_t light_max_pairs; /* the light threshold the load used (given, tuned or default) */
 } ttc_graph_stats;
 
 /* Build the device-resident graph (Alg. 1 steps up to the triangle list:
@@ -161,6 +161,24 @@ ttc_graph *ttc_load(const uint32_t *src, const uint32_t *dst, const int64_t *t, 
 /* As ttc_load with options (opts may be NULL).  *out receives the handle. */
 ttc_status ttc_load_ex(const uint32_t *src, const uint32_t *dst, const int64_t *t, uint64_t m,
                        const ttc_load_opts *opts, ttc_graph **out);
+
+/* Tuning of the light threshold (this library's split of the static
+ * triangles between the direct Lemma 1 sum over A x B and the prefix-sum
+ * form of Algs. 2-4; the paper has no such split).  Loads the graph once per
+ * candidate threshold (ttc_tune_candidates), times load plus one
+ * ttc_count_batch of the k probe queries (host arrays) with CUDA events on
+ * opts->stream, and keeps the fastest: *chosen receives it, ms (may be NULL)
+ * the time of each candidate.  The choice is cached for graphs of the same
+ * shape (bit lengths of m, m_s, largest multiplicity and kappa) on a GPU
+ * with the same number of SMs, in the JSON file $TTC_TUNE_CACHE (default
+ * ~/.cache/ttc/tune.json); ttc_load_ex with light_max_pairs = 0 then uses
+ * it.  opts->light_max_pairs must be 0.  Processes that must bin a graph
+ * identically (ttc_count_shard) should pass one explicit threshold. */
+#define TTC_TUNE_CANDIDATES 6
+static const uint32_t ttc_tune_candidates[TTC_TUNE_CANDIDATES] = {17, 33, 65, 129, 257, 1025};
+ttc_status ttc_tune_light(const uint32_t *src, const uint32_t *dst, const int64_t *t, uint64_t m,
+                          const ttc_load_opts *opts, const ttc_delta *probe, uint32_t k, uint32_t *chosen,
+                          float *ms);
 
 /* Release a graph and all of its device memory.  NULL is a no-op. */
 void ttc_free(ttc_graph *g);

@@ -16,6 +16,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libttc.so")
+# the build with device index checks (TTC_DEBUG_BOUNDS) goes beside it
+DEBUG_OUT = os.path.join(HERE, "_build_debug")
+DEBUG_LIB = os.path.join(DEBUG_OUT, "libttc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-Wno-deprecated-gpu-targets"]
@@ -45,19 +48,23 @@ def count_source_hash() -> str:
     return h.hexdigest()[:12]
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    os.makedirs(OUT, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, debug_bounds: bool = False) -> str:
+    """Builds _build/libttc.so, or with debug_bounds the library whose count
+    kernels check their indices on the device (_build_debug/libttc.so)."""
+    out_dir = DEBUG_OUT if debug_bounds else OUT
+    lib_path = DEBUG_LIB if debug_bounds else LIB
+    os.makedirs(out_dir, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
     hdr_t = _headers()
     cc = nvcc()
-    defs = ["-DTTC_COUNT_HASH=\"%s\"" % count_source_hash()]
+    defs = ["-DTTC_COUNT_HASH=\"%s\"" % count_source_hash()] + (["-DTTC_DEBUG_BOUNDS=1"] if debug_bounds else [])
 
     # the object that embeds the count hash is rebuilt whenever the hash changes
-    stamp = os.path.join(OUT, "count_hash.txt")
+    stamp = os.path.join(out_dir, "count_hash.txt")
     old_hash = open(stamp).read().strip() if os.path.exists(stamp) else ""
 
     def compile_one(src):
-        obj = os.path.join(OUT, os.path.basename(src) + ".o")
+        obj = os.path.join(out_dir, os.path.basename(src) + ".o")
         stale_hash = os.path.basename(src) == "capi.cu" and old_hash != count_source_hash()
         if (not force and not stale_hash and os.path.exists(obj)
                 and os.path.getmtime(obj) >= max(os.path.getmtime(src), hdr_t)):
@@ -79,14 +86,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
         fh.write(count_source_hash())
     objs = [o for o, _ in results]
     changed = any(c for _, c in results)
-    if force or changed or not os.path.exists(LIB):
-        tmp = LIB + ".%d.tmp" % os.getpid()
+    if force or changed or not os.path.exists(lib_path):
+        tmp = lib_path + ".%d.tmp" % os.getpid()
         cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread", "-ldl"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

@@ -178,6 +178,7 @@ void ensure_smem(const void *fn, size_t bytes) {
 void set_last_error(const std::string &m) { g_last_error = m; }
 
 void check_count_flag(unsigned long long flag) {
+    if (take_bounds_word()) fail(TTC_ERR_INTERNAL, "a count kernel read an index outside its array (index checks)");
     if (flag & 2ull) fail(TTC_ERR_TIMEOUT, "a bounded wait in a count kernel gave up (bulk copy not complete)");
     if (flag) fail(TTC_ERR_OVERFLOW, "a count exceeds 2^64 - 1");
 }

@@ -197,10 +197,14 @@ __global__ void __launch_bounds__(LIGHT_THREADS, 4)
             aux[r] = 0;
             if (ti < lim) {
                 const uint4 rec = __ldg(gv.tri + (MODE == 2 ? idx[ti] : ti));
-                const uint32_t ab = __ldg(gv.poff + rec.x), an = __ldg(gv.poff + rec.x + 1) - ab;
-                const uint32_t bb = __ldg(gv.poff + rec.y), bn = __ldg(gv.poff + rec.y + 1) - bb;
-                const uint32_t cb = __ldg(gv.poff + rec.z), cn = __ldg(gv.poff + rec.z + 1) - cb;
-                np[r] = an * bn;
+                const uint32_t pm = max(rec.x, max(rec.y, rec.z));
+                const bool ok = in_range((uint64_t)pm + 1, gv.ms);
+                const uint32_t ab = ok ? __ldg(gv.poff + rec.x) : 0u, an = ok ? __ldg(gv.poff + rec.x + 1) - ab : 0u;
+                const uint32_t bb = ok ? __ldg(gv.poff + rec.y) : 0u, bn = ok ? __ldg(gv.poff + rec.y + 1) - bb : 0u;
+                const uint32_t cb = ok ? __ldg(gv.poff + rec.z) : 0u, cn = ok ? __ldg(gv.poff + rec.z + 1) - cb : 0u;
+                const bool lists_ok = ok && in_range((uint64_t)ab + an, gv.m) && in_range((uint64_t)bb + bn, gv.m) &&
+                                      in_range((uint64_t)cb + cn, gv.m) && cn > 0;
+                np[r] = lists_ok ? an * bn : 0u;
                 cls[r] = cn <= 4 ? 0u : cn <= 16 ? 1u : cn <= 64 ? 2u : 3u;
                 lst[r] = make_uint4(ab, bb, cb, cn);
                 aux[r] = bn | (rec.w << 29);
@@ -260,7 +264,7 @@ __global__ void __launch_bounds__(LIGHT_THREADS, 4)
             // loc < 2^20: (loc + 1/2) / bn is at least 1 / (2 bn) from an
             // integer, and the float product is within 2^-3 / bn of it
             const uint32_t ai = __float2uint_rz(((float)loc + 0.5f) * __frcp_rn((float)bn)), bi = loc - ai * bn;
-            light_count_pair(gv, f, L.x, L.y, L.z, L.w, fl, false, 0u, 0u, ai, bi, gmax, gfin,
+            light_count_pair<MODE == 1 ? 4u : 2u>(gv, f, L.x, L.y, L.z, L.w, fl, false, 0u, 0u, ai, bi, gmax, gfin,
                              [&](const CView &C, bool a_first, int64_t rx, int64_t ry, uint32_t code) {
                 if (MODE != 1 || tslots) {
 #pragma unroll 1
@@ -513,6 +517,10 @@ __global__ void __launch_bounds__(HEAVY_THREADS)
         const uint32_t ao = A.b & 1u, bo = B.b & 1u, co = C.b & 1u;
         const uint32_t aw = (ao + na + 1u) & ~1u, bw = (bo + nb + 1u) & ~1u;
         const uint32_t cw = c_staged ? (co + C.n + 1u) & ~1u : 0u;
+        // the copies end at most one key past a list, inside the padding
+        if (!(in_range((uint64_t)A.b - ao + aw, gv.m + 2) && in_range((uint64_t)B.b - bo + bw, gv.m + 2) &&
+              in_range((uint64_t)C.b - co + cw, gv.m + 2)))
+            continue;  // block-uniform
         if (threadIdx.x == 0) {
             fence_async_smem();  // earlier triangles' reads of s_key (all past the last barrier)
             mbar_arrive_expect(&s_bar, (aw + bw + cw) * 8u);
@@ -1281,6 +1289,18 @@ void count_one_into(ttc_graph *g, const int64_t *dq, unsigned long long *acc, vo
 
 uint32_t fused_capacity(int wide) { return wide ? FusedCap<unsigned long long>::CAP : FusedCap<uint32_t>::CAP; }
 uint32_t warp_capacity(int wide) { return wide ? WarpCap<unsigned long long>::CAP : WarpCap<uint32_t>::CAP; }
+
+unsigned int take_bounds_word() {
+#if TTC_DEBUG_BOUNDS
+    unsigned int w = 0;
+    const unsigned int zero = 0;
+    TTC_CUDA(cudaMemcpyFromSymbol(&w, g_bounds_bad, sizeof w));
+    TTC_CUDA(cudaMemcpyToSymbol(g_bounds_bad, &zero, sizeof zero));
+    return w;
+#else
+    return 0;
+#endif
+}
 
 // ---------------------------------------------------------------- sampled output
 void count_sample(ttc_graph *g, const int64_t *dq, uint64_t first, uint64_t stride, uint64_t cap,

@@ -61,6 +61,26 @@ struct Query {
     int64_t d13, d12, d23;
 };
 
+// ---------------------------------------------------------------- index checks
+// A build with -DTTC_DEBUG_BOUNDS=1 (the stand-in for a device memory
+// checker) checks, before a list is used, every pair id read from a
+// triangle record against the number of pairs and every list's range
+// against the key array, and every bulk copy's range against the array and
+// its padding.  A failed check sets g_bounds_bad, the triangle is not
+// counted (no access is made), and the count call returns
+// TTC_ERR_INTERNAL.  Searches stay inside a checked range by construction.
+#ifndef TTC_DEBUG_BOUNDS
+#define TTC_DEBUG_BOUNDS 0
+#endif
+static __device__ unsigned int g_bounds_bad;
+
+// true when [.., hi) lies below lim (always, unless checking)
+__device__ __forceinline__ bool in_range(uint64_t hi, uint64_t lim) {
+    if (!TTC_DEBUG_BOUNDS || hi <= lim) return true;
+    atomicOr(&g_bounds_bad, 1u);
+    return false;
+}
+
 __device__ __forceinline__ Query load_query(const int64_t *dq, uint32_t q) {
     return Query{dq[3 * q], dq[3 * q + 1], dq[3 * q + 2]};
 }
@@ -214,8 +234,11 @@ __device__ __forceinline__ void search_n(const SList &l, const int64_t (&bound)[
 }
 
 __device__ __forceinline__ GList glist(const GraphView &gv, uint32_t p, uint32_t flip) {
+    if (!in_range((uint64_t)p + 1, gv.ms)) return GList{gv.key, gv.fwd, 0u, 0u, flip};
     const uint32_t b = __ldg(gv.poff + p);
-    return GList{gv.key, gv.fwd, b, __ldg(gv.poff + p + 1) - b, flip};
+    const uint32_t n = __ldg(gv.poff + p + 1) - b;
+    if (!in_range((uint64_t)b + n, gv.m)) return GList{gv.key, gv.fwd, 0u, 0u, flip};
+    return GList{gv.key, gv.fwd, b, n, flip};
 }
 
 // ---------------------------------------------------------------- bulk copies
@@ -386,8 +409,14 @@ struct CView {
     uint32_t b, n, flip;
     uint32_t px, py, f0, fx, fy, fn;
     int64_t kfirst, klast;  // C's first and last keys (when loaded; else 0 and INT64_MAX)
+    // a short list read whole: bit j of mask0 is set when C's key j has
+    // stored direction 0, and the raw prefix is counted from it (from 0, so
+    // every raw value of the list is on the same footing)
+    bool small;
+    uint32_t mask0;
     __device__ __forceinline__ uint32_t below(int64_t bound) const { return search_below(key + b, n, bound); }
     __device__ __forceinline__ uint32_t raw(uint32_t pos) const {
+        if (small) return __popc(mask0 & ((1u << pos) - 1u));
         return pos == px ? fx : pos == py ? fy : pos == n ? fn : pos == 0 ? f0 : __ldg(fwd + b + pos);
     }
     // effective direction-0 edges among C's positions [lo, hi)
@@ -507,44 +536,83 @@ __device__ __forceinline__ void light_pair(const CView &C, const KeyFmt &f, cons
 // otherwise each(C, a_first, rx, ry, code) runs light_pair for each query.
 // gfin: the largest d13 of the queries whose windows do not cover the whole
 // time span (-1 if none).
-template <typename EACH>
+template <uint32_t SHORT_C, typename EACH>
 __device__ __forceinline__ void light_count_pair(const GraphView &gv, const KeyFmt &f, uint32_t ab, uint32_t bb,
                                                  uint32_t cb, uint32_t cn, uint32_t fl, bool have_ends, uint32_t f0,
                                                  uint32_t fn, uint32_t ai, uint32_t bi, int64_t gmax, int64_t gfin,
                                                  EACH &&each) {
     const int64_t ka = __ldg(gv.key + ab + ai), kb = __ldg(gv.key + bb + bi);
+    // a list of at most SHORT_C keys is read whole (one memory round trip)
+    // and its positions and direction counts are taken in registers
+    // When the largest d13 at hand covers the whole time span no pair is
+    // skipped, and the list is loaded with the pair's keys; otherwise after
+    // the gap test, so that skipped pairs load nothing.
+    const bool shortc = SHORT_C > 0 && cn <= SHORT_C;
+    const bool early = gmax >= f.span;
+    int64_t sk[SHORT_C > 0 ? SHORT_C : 1];
+    if (shortc && early) {
+#pragma unroll
+        for (uint32_t j = 0; j < SHORT_C; j++) sk[j] = j < cn ? __ldg(gv.key + cb + j) : INT64_MAX;
+    }
     const int64_t ra = ka >> f.shift, rb = kb >> f.shift;
     const bool a_first = ka < kb;
     const int64_t gap = a_first ? rb - ra : ra - rb;
     if (gap > gmax) return;
-    // C's first and last keys settle most window ends without a search;
-    // only a query with finite windows and d13 >= gap can need them (gfin:
-    // the largest d13 of such queries, -1 if none).  Loaded before the key
-    // searches, they arrive while those run.
-    const bool ends = gap <= gfin;
-    const int64_t kfirst = ends ? __ldg(gv.key + cb) : 0, klast = ends ? __ldg(gv.key + cb + cn - 1) : INT64_MAX;
+    if (shortc && !early) {
+#pragma unroll
+        for (uint32_t j = 0; j < SHORT_C; j++) sk[j] = j < cn ? __ldg(gv.key + cb + j) : INT64_MAX;
+    }
     const uint32_t dA = (uint32_t)(ka & 1) ^ (fl & TriRec::FLIP_A);
     const uint32_t dB = (uint32_t)(kb & 1) ^ ((fl & TriRec::FLIP_B) ? 1u : 0u);
     const uint32_t code = (dA << 2) | (dB << 1);
-    const int64_t *ck = gv.key + cb;
-    const int64_t bab[2] = {key_bound(ka), key_bound(kb)};
-    uint32_t pab[2];
-    search_n<2>([&](uint32_t i) { return __ldg(ck + i); }, cn, bab, pab);
-    const uint32_t pa = pab[0], pb = pab[1];
     CView C;
     C.key = gv.key;
     C.fwd = gv.fwd;
     C.b = cb;
     C.n = cn;
     C.flip = (fl & TriRec::FLIP_C) ? 1u : 0u;
-    C.px = a_first ? pa : pb;
-    C.py = a_first ? pb : pa;
-    C.f0 = have_ends ? f0 : __ldg(gv.fwd + cb);
-    C.fn = have_ends ? fn : __ldg(gv.fwd + cb + cn);
-    C.fx = __ldg(gv.fwd + cb + C.px);
-    C.fy = __ldg(gv.fwd + cb + C.py);
-    C.kfirst = kfirst;
-    C.klast = klast;
+    if (shortc) {
+        const int64_t ba = key_bound(ka), bbd = key_bound(kb);
+        uint32_t pa = 0, pb = 0, mask = 0;
+        int64_t last = sk[0];
+#pragma unroll
+        for (uint32_t j = 0; j < SHORT_C; j++) {
+            pa += sk[j] < ba;
+            pb += sk[j] < bbd;
+            mask |= ((uint32_t)~sk[j] & 1u) << j;  // padding (INT64_MAX) is odd: no bit
+            if (j < cn) last = sk[j];
+        }
+        C.small = true;
+        C.mask0 = mask;
+        C.px = a_first ? pa : pb;
+        C.py = a_first ? pb : pa;
+        C.f0 = 0;
+        C.fx = __popc(mask & ((1u << C.px) - 1u));
+        C.fy = __popc(mask & ((1u << C.py) - 1u));
+        C.fn = __popc(mask);
+        C.kfirst = sk[0];
+        C.klast = last;
+    } else {
+        // C's first and last keys settle most window ends without a search;
+        // only a query with finite windows and d13 >= gap can need them
+        // (gfin: the largest d13 of such queries, -1 if none).  Loaded
+        // before the key searches, they arrive while those run.
+        const bool ends = gap <= gfin;
+        C.kfirst = ends ? __ldg(gv.key + cb) : 0;
+        C.klast = ends ? __ldg(gv.key + cb + cn - 1) : INT64_MAX;
+        const int64_t *ck = gv.key + cb;
+        const int64_t bab[2] = {key_bound(ka), key_bound(kb)};
+        uint32_t pab[2];
+        search_n<2>([&](uint32_t i) { return __ldg(ck + i); }, cn, bab, pab);
+        C.small = false;
+        C.mask0 = 0;
+        C.px = a_first ? pab[0] : pab[1];
+        C.py = a_first ? pab[1] : pab[0];
+        C.f0 = have_ends ? f0 : __ldg(gv.fwd + cb);
+        C.fn = have_ends ? fn : __ldg(gv.fwd + cb + cn);
+        C.fx = __ldg(gv.fwd + cb + C.px);
+        C.fy = __ldg(gv.fwd + cb + C.py);
+    }
     each(C, a_first, a_first ? ra : rb, a_first ? rb : ra, code);
 }
 

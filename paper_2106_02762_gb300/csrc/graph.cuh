@@ -37,6 +37,7 @@ struct GraphView {
     int shift;
     int wide;  // 64-bit prefix sums needed (some list has >= 65536 edges)
     int strict;  // TTC_LOAD_STRICT_TIME: a triple counts only if its times strictly increase
+    uint64_t m, ms;  // lengths of key (edges) and of the pair arrays (for index checks)
 };
 
 struct ttc_graph {
@@ -180,6 +181,14 @@ uint32_t warp_capacity(int wide);
 uint32_t fused_capacity(int wide);
 
 uint32_t default_light_max_pairs();
+// multi.cu: the light threshold ttc_tune_light chose for graphs of this
+// shape on the current GPU (the tune cache), else default_light_max_pairs().
+uint32_t tuned_light_max(const ttc_graph_stats &st);
+
+// A build with -DTTC_DEBUG_BOUNDS=1 checks the count kernels' indices on
+// the device (count_dev.cuh); this returns and clears the device word those
+// checks set (always 0 in other builds).
+unsigned int take_bounds_word();
 
 // Turns the count kernels' device flag word into a failure: bit 1 (a
 // bounded wait in a kernel gave up) is TTC_ERR_TIMEOUT, any other bit (a

@@ -1694,6 +1694,8 @@ static void set_view(ttc_graph *g, cudaStream_t s) {
     v.shift = g->shift;
     v.wide = g->heavy_wide;
     v.strict = g->strict ? 1 : 0;
+    v.m = g->st.m;
+    v.ms = g->st.m_s;
     g->view.alloc(1, s);
     g->prefix.alloc(6, s);
     const uint64_t pre[6] = {0, (v.n_light + 31) / 32, 0, v.n_hwarp, 0, v.n_hcta};
@@ -2122,7 +2124,11 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
 
     prof_end(g, s);
     prof_begin(g, s, "load:enumerate");
-    // ---- a6: triangles, written straight into the light and heavy bins
+    // ---- a6: triangles, written straight into the light and heavy bins.
+    // With no threshold given, the tuned one for graphs of this shape (if
+    // ttc_tune_light measured one on this GPU), else the default.
+    if (!opt.light_max_pairs) g->light_max_pairs = tuned_light_max(st);
+    st.light_max_pairs = g->light_max_pairs;
     const RecCtx rc{g->labeling, g->light_max_pairs};
     DevBuf<uint4> ocsr(ms, s);
     osig_kernel<<<grid_for(ms), TPB, 0, s>>>(opair.get(), osrc.get(), onbr.get(), id_of.get(), g->poff.get(), ms,

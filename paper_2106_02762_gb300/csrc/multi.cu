@@ -70,7 +70,7 @@ std::map<std::string, Shape> tune_load() {
         if (a == std::string::npos || b == std::string::npos) break;
         Shape sh;
         if (sscanf(s.c_str() + a + 1, "%d , %d", &sh.light_per_sm, &sh.heavy_per_sm) == 2 && sh.light_per_sm > 0 &&
-            sh.heavy_per_sm > 0)
+            (sh.heavy_per_sm > 0 || key.rfind("light|", 0) == 0))
             m[key] = sh;
         i = b + 1;
     }
@@ -95,6 +95,20 @@ void tune_store(const std::map<std::string, Shape> &m) {
     f << "\n}\n";
     f.close();
     rename(tmp.c_str(), path.c_str());
+}
+
+// ---------------------------------------------------------------- light threshold
+// Graphs are tuned by shape: the GPU's SM count and the bit lengths of m,
+// m_s, the largest multiplicity and kappa.  The cache keeps
+// "light|..." keys as [threshold, 0].
+std::map<std::string, Shape> g_light_mem;  // guarded by g_tune_mu; loaded once
+bool g_light_loaded = false;
+
+std::string light_key(const ttc_graph_stats &st) {
+    char b[128];
+    snprintf(b, sizeof b, "light|sm%d|m%d|s%d|x%d|k%d", sm_count(), bits_for(st.m), bits_for(st.m_s),
+             bits_for(st.sigma_max), bits_for(st.kappa));
+    return b;
 }
 
 // ---------------------------------------------------------------- plans
@@ -315,3 +329,87 @@ void count_multi(ttc_graph *const *gs, const ttc_delta *d, uint32_t G, uint64_t 
 }
 
 }  // namespace ttc
+
+namespace ttc {
+
+uint32_t tuned_light_max(const ttc_graph_stats &st) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (!g_light_loaded) {
+        g_light_mem = tune_load();
+        g_light_loaded = true;
+    }
+    const auto it = g_light_mem.find(light_key(st));
+    return it != g_light_mem.end() ? (uint32_t)it->second.light_per_sm : default_light_max_pairs();
+}
+
+}  // namespace ttc
+
+extern "C" ttc_status ttc_tune_light(const uint32_t *src, const uint32_t *dst, const int64_t *t, uint64_t m,
+                                     const ttc_load_opts *opts, const ttc_delta *probe, uint32_t k,
+                                     uint32_t *chosen, float *ms) {
+    if (!chosen || (k && !probe)) {
+        set_last_error("NULL argument");
+        return TTC_ERR_INVALID;
+    }
+    if (opts && opts->light_max_pairs) {
+        set_last_error("ttc_tune_light chooses light_max_pairs itself: pass 0");
+        return TTC_ERR_INVALID;
+    }
+    try {
+        ttc_load_opts o = opts ? *opts : ttc_load_opts{};
+        std::vector<uint64_t> out(8 * (size_t)(k ? k : 1));
+        float best = 0.f;
+        uint32_t best_c = default_light_max_pairs();
+        ttc_graph_stats st{};
+        for (uint32_t i = 0; i < TTC_TUNE_CANDIDATES; i++) {
+            o.light_max_pairs = ttc_tune_candidates[i];
+            // one untimed load and count (first-use work), then a timed one
+            float el = 0.f;
+            for (int rep = 0; rep < 2; rep++) {
+                cudaEvent_t e0 = nullptr, e1 = nullptr;
+                TTC_CUDA(cudaEventCreate(&e0));
+                TTC_CUDA(cudaEventCreate(&e1));
+                cudaStream_t s = static_cast<cudaStream_t>(o.stream);
+                TTC_CUDA(cudaEventRecord(e0, s));
+                ttc_graph *g = nullptr;
+                ttc_status rc = ttc_load_ex(src, dst, t, m, &o, &g);
+                if (rc == TTC_OK && k) rc = ttc_count_batch(g, probe, k, out.data());
+                if (rc == TTC_OK) {
+                    st = g->st;
+                    TTC_CUDA(cudaStreamSynchronize(g->stream));
+                }
+                ttc_free(g);
+                TTC_CUDA(cudaEventRecord(e1, s));
+                TTC_CUDA(cudaEventSynchronize(e1));
+                TTC_CUDA(cudaEventElapsedTime(&el, e0, e1));
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                if (rc != TTC_OK) return rc;
+            }
+            if (ms) ms[i] = el;
+            if (i == 0 || el < best) {
+                best = el;
+                best_c = ttc_tune_candidates[i];
+            }
+        }
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto cache = tune_load();
+            Shape sh;
+            sh.light_per_sm = (int)best_c;
+            sh.heavy_per_sm = 0;
+            cache[light_key(st)] = sh;
+            tune_store(cache);
+            g_light_mem = cache;
+            g_light_loaded = true;
+        }
+        *chosen = best_c;
+        return TTC_OK;
+    } catch (const Failure &f) {
+        set_last_error(f.message);
+        return f.status;
+    } catch (...) {
+        set_last_error("unexpected internal failure");
+        return TTC_ERR_INTERNAL;
+    }
+}

@@ -15,7 +15,9 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_build", "libttc.so")
+# TTC_LIB selects another build of the library (the one with device index
+# checks, build.build(debug_bounds=True)); the default is the in-tree build
+LIB_PATH = os.environ.get("TTC_LIB") or os.path.join(HERE, "_build", "libttc.so")
 NUM_TYPES = 8
 
 OK, PENDING = 0, 1
@@ -35,7 +37,8 @@ EXPORTS = ["ttc_load", "ttc_load_ex", "ttc_free", "ttc_graph_info", "ttc_count",
            "ttc_serve_pause", "ttc_serve_set_reserve",
            "ttc_server_info", "ttc_last_error", "ttc_version", "ttc_debug_fail_alloc_after",
            "ttc_debug_launch_count", "ttc_set_profiling", "ttc_profile_read", "ttc_count_noalloc",
-           "ttc_release_cached", "ttc_memory_info", "ttc_count_grid", "ttc_count_shard"]
+           "ttc_release_cached", "ttc_memory_info", "ttc_count_grid", "ttc_count_shard", "ttc_tune_light"]
+TUNE_CANDIDATES = (17, 33, 65, 129, 257, 1025)  # ttc_tune_candidates in ttc.h
 
 
 class TTCError(RuntimeError):
@@ -57,7 +60,7 @@ class GraphStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in
                 ("n", "m", "m_self_loops", "m_s", "tau", "kappa", "sigma_max", "peel_rounds", "work_bytes",
                  "enum_elems", "tau_light", "tau_heavy", "device_bytes", "work_bytes_heavy", "tau_huge", "tau_hwarp", "tau_hcta", "light_pairs")] + \
-               [("key_bits", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+               [("key_bits", ctypes.c_uint32), ("light_max_pairs", ctypes.c_uint32)]
 
 
 class KernelTime(ctypes.Structure):
@@ -95,6 +98,7 @@ def lib():
             "ttc_count_batch": ([p, p, u32, p], ctypes.c_int),
             "ttc_count_batch_async": ([p, p, u32, p, p], ctypes.c_int),
             "ttc_count_shard": ([p, p, u32, u32, u32, p], ctypes.c_int),
+            "ttc_tune_light": ([p, p, p, u64, p, p, u32, p, p], ctypes.c_int),
             "ttc_count_multi": ([p, p, u32, p], ctypes.c_int),
             "ttc_count_sample": ([p, p, u64, u64, u64, p, p, p], ctypes.c_int),
             "ttc_server_create": ([p], p),
@@ -210,7 +214,7 @@ class Graph:
     def info(self) -> dict:
         s = GraphStats()
         check(lib().ttc_graph_info(self.handle, ctypes.byref(s)))
-        return {f: getattr(s, f) for f, _ in GraphStats._fields_ if f != "reserved"}
+        return {f: getattr(s, f) for f, _ in GraphStats._fields_}
 
     def count(self, delta) -> np.ndarray:
         d, dp = _deltas(delta)
@@ -263,6 +267,21 @@ class Graph:
         check(lib().ttc_count_sample(self.handle, dp, first, stride, cap, tri.ctypes.data, out.ctypes.data,
                                      ctypes.byref(n)))
         return tri[:n.value], out[:n.value]
+
+
+def tune_light(src, dst, t, probe_deltas, stream=None, orientation=ORIENT_DEGENERACY, labeling=LABEL_HEAVIEST_VW):
+    """ttc_tune_light: times load + count of the probe queries at each light
+    threshold in TUNE_CANDIDATES, caches the fastest for graphs of this
+    shape and returns (chosen threshold, {candidate: ms})."""
+    ptrs, m, flags, keep = _edge_ptrs(src, dst, t)
+    opts = LoadOpts(flags, orientation, labeling, 0, 0, stream)
+    d, dp = _deltas(probe_deltas)
+    chosen = ctypes.c_uint32()
+    ms = (ctypes.c_float * len(TUNE_CANDIDATES))()
+    check(lib().ttc_tune_light(ptrs[0], ptrs[1], ptrs[2], m, ctypes.byref(opts), dp, d.shape[0],
+                               ctypes.byref(chosen), ms))
+    del keep
+    return int(chosen.value), {c: float(v) for c, v in zip(TUNE_CANDIDATES, ms)}
 
 
 def count_multi(graphs, deltas) -> np.ndarray:
