@@ -175,7 +175,7 @@ ttc_status ttc_load_ex(const uint32_t *src, const uint32_t *dst, const int64_t *
  * it.  opts->light_max_pairs must be 0.  Processes that must bin a graph
  * identically (ttc_count_shard) should pass one explicit threshold. */
 #define TTC_TUNE_CANDIDATES 6
-static const uint32_t ttc_tune_candidates[TTC_TUNE_CANDIDATES] = {17, 33, 65, 129, 257, 1025};
+static const uint32_t ttc_tune_candidates[TTC_TUNE_CANDIDATES] = {17, 65, 257, 1025, 4097, 16385};
 ttc_status ttc_tune_light(const uint32_t *src, const uint32_t *dst, const int64_t *t, uint64_t m,
                           const ttc_load_opts *opts, const ttc_delta *probe, uint32_t k, uint32_t *chosen,
                           float *ms);

@@ -38,7 +38,7 @@ EXPORTS = ["ttc_load", "ttc_load_ex", "ttc_free", "ttc_graph_info", "ttc_count",
            "ttc_server_info", "ttc_last_error", "ttc_version", "ttc_debug_fail_alloc_after",
            "ttc_debug_launch_count", "ttc_set_profiling", "ttc_profile_read", "ttc_count_noalloc",
            "ttc_release_cached", "ttc_memory_info", "ttc_count_grid", "ttc_count_shard", "ttc_tune_light"]
-TUNE_CANDIDATES = (17, 33, 65, 129, 257, 1025)  # ttc_tune_candidates in ttc.h
+TUNE_CANDIDATES = (17, 65, 257, 1025, 4097, 16385)  # ttc_tune_candidates in ttc.h
 
 
 class TTCError(RuntimeError):
