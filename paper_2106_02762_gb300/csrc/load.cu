@@ -403,9 +403,12 @@ struct PeelCtl {
     int k;                 // level at the hand-off
     unsigned int rem_n;    // vertices left at the hand-off
     unsigned int rem_in_b; // the remaining list is in remB (else remA)
-    unsigned int pad;
-    unsigned int bar_count, bar_gen;  // grid barrier of the grid-wide stage
-    unsigned int core_alive;          // vertices the cluster stage hands to one CTA
+    unsigned int core_alive;  // vertices the cluster stage hands to one CTA
+    // grid barrier of the grid-wide stage: the arrival counter and the
+    // generation word sit on cache lines of their own, so the waiting CTAs'
+    // polls do not queue behind the arrivals
+    alignas(128) unsigned int bar_count;
+    alignas(128) unsigned int bar_gen;
 };
 
 constexpr uint64_t MASK40 = (uint64_t(1) << 40) - 1;
@@ -499,6 +502,13 @@ __device__ __forceinline__ void flush_frontier(PeelSlot *sl, uint32_t *front, ui
 // through an arrival counter and a generation word in device memory.  The
 // wait is bounded; a CTA that gives up reports failure so the kernel stops.
 constexpr uint32_t GRID_BAR_SPIN = 1u << 24;
+constexpr unsigned GRID_BAR_SLEEP_NS = 32;
+
+__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int *p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
 
 struct GridSync {
     uint32_t gen = 0;
@@ -517,12 +527,12 @@ struct GridSync {
                 atomicExch(&ctl->bar_gen, gen + 1);
             } else {
                 uint32_t spins = 0;
-                while (atomicAdd(&ctl->bar_gen, 0u) == gen) {
+                while (ld_acquire_gpu(&ctl->bar_gen) == gen) {
                     if (++spins > GRID_BAR_SPIN) {
                         ok = 0;
                         break;
                     }
-                    __nanosleep(64);
+                    __nanosleep(GRID_BAR_SLEEP_NS);
                 }
             }
             __threadfence();
@@ -856,13 +866,9 @@ __global__ void __launch_bounds__(256)
 // owner's next frontier.  Only counts cross the cluster barrier: pushes are
 // tallied per CTA in a slot that rotates over three rounds, so a slot is
 // read by every CTA between the barriers that end round r and r + 1 and is
-// zeroed in round r + 2.  One CTA alone needs no tally: its frontier counts
-// rotate over three slots (round r's frontier in slot r mod 3, its pushes in
-// slot r + 1 mod 3, slot r + 2 mod 3 zeroed during round r, once every
-// thread read it as round r - 1's count), so a round ends on one barrier
-// that also tells whether anything was pushed.  Continues from level ctl->k
-// and round ctl->rounds; writes level[] of the core vertices and the final
-// rounds and kappa.
+// zeroed in round r + 2.  Continues from level ctl->k and round
+// ctl->rounds; writes level[] of the core vertices it removes and hands the
+// last (at most stop_n) to peel_tail_kernel.
 constexpr int CORE_THREADS = 1024;      // per CTA of the cluster (measured: more threads per round beat fewer idle warps)
 constexpr int CORE_TAIL_THREADS = 1024;  // the one-CTA run of the last PEEL_TAIL vertices
 constexpr uint32_t PEEL_TAIL = 8192;     // the cluster hands the last this many to one CTA
@@ -873,31 +879,22 @@ constexpr uint32_t CORE_MAX_CLUSTER = 16;
 // level of `per` owned vertices (u32 each)
 inline size_t core_smem_bytes(uint32_t per) { return (size_t)per * 6 * 4; }
 
-// CLUSTER = false: one CTA owns every vertex (plain shared memory, block
-// barriers); CLUSTER = true: `per` (a power of two) vertices per CTA.
-template <bool CLUSTER>
-__global__ void __launch_bounds__(CORE_TAIL_THREADS, 1)
+// `per` (a power of two) vertices per CTA.
+__global__ void __launch_bounds__(CORE_THREADS, 1)
     peel_core_kernel(const uint32_t *rem, uint32_t R, uint32_t per, const uint32_t *coff, const uint32_t *cadj,
                      uint32_t *level, int *deg, uint32_t stop_n, uint32_t *alive_out, PeelCtl *ctl) {
     cg::cluster_group cl = cg::this_cluster();
-    const uint32_t crank = CLUSTER ? cl.block_rank() : 0u, csize = CLUSTER ? cl.num_blocks() : 1u;
-    const uint32_t per_lg = CLUSTER ? (uint32_t)(__ffs(per) - 1) : 0u;
+    const uint32_t crank = cl.block_rank(), csize = cl.num_blocks();
+    const uint32_t per_lg = (uint32_t)(__ffs(per) - 1);
     // shared memory of the CTA that owns a vertex
-    auto at = [&](auto *p, uint32_t own) {
-        if constexpr (CLUSTER) return cl.map_shared_rank(p, own);
-        else return p;
-    };
-    auto csync = [&]() {
-        if constexpr (CLUSTER) cl.sync();
-        else __syncthreads();
-    };
+    auto at = [&](auto *p, uint32_t own) { return cl.map_shared_rank(p, own); };
+    auto csync = [&]() { cl.sync(); };
     const uint32_t tid = threadIdx.x, lane = tid & 31, nthr = blockDim.x;
     extern __shared__ __align__(16) uint32_t core_smem[];
     uint32_t *s_deg = core_smem, *s_ab = s_deg + per, *s_na = s_ab + per;
     uint32_t *s_front = s_na + per;  // [2][per]
     uint32_t *s_lev = s_front + 2 * per;
-    __shared__ unsigned int s_fcnt[3];                 // entries in my frontier buffers (by round parity;
-                                                       // one CTA alone: by round mod 3)
+    __shared__ unsigned int s_fcnt[2];                 // entries in my frontier buffers, by round parity
     __shared__ unsigned int s_tot[3];                  // the cluster's pushes, per round mod 3
     __shared__ unsigned int s_peer[2];                 // this CTA's pushes, by round parity
     __shared__ int s_mins[CORE_MAX_CLUSTER];           // each CTA's smallest remaining degree
@@ -914,7 +911,7 @@ __global__ void __launch_bounds__(CORE_TAIL_THREADS, 1)
         s_lev[i] = UNSET;
     }
     if (tid == 0) {
-        s_fcnt[0] = s_fcnt[1] = s_fcnt[2] = 0;
+        s_fcnt[0] = s_fcnt[1] = 0;
         s_tot[0] = s_tot[1] = s_tot[2] = 0;
         s_peer[0] = s_peer[1] = 0;
         s_min = INT_MAX;
@@ -981,7 +978,7 @@ __global__ void __launch_bounds__(CORE_TAIL_THREADS, 1)
             for (uint32_t i = tid; i < my_n; i += nthr) {
                 if (s_lev[i] == UNSET && (int)s_deg[i] <= k) {
                     s_lev[i] = round;
-                    s_front[cur * per + atomicAdd(&s_fcnt[CLUSTER ? cur : round % 3], 1u)] = i;
+                    s_front[cur * per + atomicAdd(&s_fcnt[cur], 1u)] = i;
                 }
             }
             // every CTA has collected before any CTA decrements its
@@ -993,17 +990,12 @@ __global__ void __launch_bounds__(CORE_TAIL_THREADS, 1)
         }
         // relaxation of this CTA's frontier (round `round`)
         const uint32_t nxt = cur ^ 1, slot = round % 3;
-        const uint32_t fn = s_fcnt[CLUSTER ? cur : slot];
-        const uint32_t push_slot = CLUSTER ? nxt : (round + 1) % 3;
+        const uint32_t fn = s_fcnt[cur];
         const uint32_t *F = s_front + cur * per;
         const uint32_t par = round & 1;
-        // the tally slot (one CTA: the count slot) of round - 2: every CTA
-        // read it before the barrier that ended round - 1
-        if (tid == 0) {
-            if constexpr (CLUSTER) s_tot[(round + 1) % 3] = 0;
-            else s_fcnt[(round + 2) % 3] = 0;
-        }
-        bool pushed_any = false;
+        // the tally slot of round - 2: every CTA read it before the barrier
+        // that ended round - 1
+        if (tid == 0) s_tot[(round + 1) % 3] = 0;
         // one warp per frontier vertex, its lanes over the adjacency,
         // CORE_RUN entries a lane per step with their loads in flight together
         const uint32_t wid = tid >> 5, nwarp = nthr >> 5;
@@ -1023,8 +1015,8 @@ __global__ void __launch_bounds__(CORE_TAIL_THREADS, 1)
                 uint32_t own[CORE_RUN], idx[CORE_RUN];
 #pragma unroll
                 for (int j = 0; j < CORE_RUN; j++) {
-                    own[j] = CLUSTER && live[j] ? wv[j] >> per_lg : 0u;
-                    idx[j] = live[j] ? (CLUSTER ? wv[j] & (per - 1) : wv[j]) : 0u;
+                    own[j] = live[j] ? wv[j] >> per_lg : 0u;
+                    idx[j] = live[j] ? wv[j] & (per - 1) : 0u;
                 }
                 uint32_t old[CORE_RUN];
 #pragma unroll
@@ -1034,28 +1026,22 @@ __global__ void __launch_bounds__(CORE_TAIL_THREADS, 1)
                 for (int j = 0; j < CORE_RUN; j++) {
                     if (live[j] && (int)old[j] == k + 1) {
                         at(s_lev, own[j])[idx[j]] = round + 1;
-                        const uint32_t slot_at = atomicAdd(at(s_fcnt, own[j]) + push_slot, 1u);
+                        const uint32_t slot_at = atomicAdd(at(s_fcnt, own[j]) + nxt, 1u);
                         at(s_front, own[j])[nxt * per + slot_at] = idx[j];
-                        if constexpr (CLUSTER) atomicAdd(&s_peer[par], 1u);
-                        pushed_any = true;
+                        atomicAdd(&s_peer[par], 1u);
                     }
                 }
             }
         }
-        uint32_t pushed;
-        if constexpr (CLUSTER) {
-            __syncthreads();
-            if (tid == 0) s_fcnt[cur] = 0;  // consumed; others push into it only after the barrier
-            // add this CTA's pushes to every CTA's tally of this round before
-            // the barrier, so that after it each CTA reads the total locally
-            if (tid < csize && s_peer[par]) atomicAdd(at(s_tot, tid) + slot, s_peer[par]);
-            cl.sync();
-            pushed = s_tot[slot];
-            // read above, before this barrier; counted into again two rounds on
-            if (tid == 0) s_peer[par] = 0;
-        } else {
-            pushed = __syncthreads_or(pushed_any) ? 1u : 0u;
-        }
+        __syncthreads();
+        if (tid == 0) s_fcnt[cur] = 0;  // consumed; others push into it only after the barrier
+        // add this CTA's pushes to every CTA's tally of this round before
+        // the barrier, so that after it each CTA reads the total locally
+        if (tid < csize && s_peer[par]) atomicAdd(at(s_tot, tid) + slot, s_peer[par]);
+        cl.sync();
+        const uint32_t pushed = s_tot[slot];
+        // read above, before this barrier; counted into again two rounds on
+        if (tid == 0) s_peer[par] = 0;
         round++;
         cur = nxt;
         need_level = pushed == 0;
@@ -1075,6 +1061,209 @@ __global__ void __launch_bounds__(CORE_TAIL_THREADS, 1)
     csync();  // no CTA leaves while another may still read its shared memory
 }
 
+// The last R <= PEEL_TAIL vertices, peeled by one CTA (Sec. 3, the same
+// level-synchronous rule).  Shared memory holds each vertex's remaining
+// degree, level and adjacency start (coff, R + 1 entries), and two frontier
+// buffers of (vertex, offset of its first chunk among the round's chunks),
+// where a chunk is PEEL_CHUNK consecutive adjacency entries of one vertex.
+// A push reserves its frontier slot and its chunks with one packed 64-bit
+// shared-memory add ((vertices << 40) | chunks), so the offsets are an
+// exclusive prefix of the chunk counts in slot order.  A round deals the
+// frontier's chunks to the warps (chunk c to warp c mod 32; its vertex by a
+// warp-uniform binary search over the offsets), so a hub in the frontier is
+// spread over many warps instead of stepping through its list on one, and a
+// round costs about one dependent L2 load.  The round's packed counts rotate
+// over three slots (read in round r, pushed into in round r - 1, zeroed in
+// round r + 1, which starts after the barrier that ends r), so a round ends
+// on one barrier.  The per-vertex arrays are padded to a multiple of four
+// and scanned with 16-byte shared-memory loads at each new level.
+constexpr uint32_t PEEL_CHUNK = 32 * CORE_RUN;
+
+__host__ __device__ inline uint32_t tail_pad(uint32_t R) { return (R + 3) & ~3u; }
+// degree, level, coff (+4), two u32 offset buffers, two u16 vertex buffers
+inline size_t tail_smem_bytes(uint32_t R) { return ((size_t)6 * tail_pad(R) + 4) * 4; }
+
+// Warp-collective (every lane calls it): lane appends its vertices v[j] with
+// bit j of pm set (chunk counts ch[j]) to the frontier whose packed count is
+// *pk, in j order.
+template <int N>
+__device__ __forceinline__ void tail_push(uint32_t pm, const uint32_t (&v)[N], const uint32_t (&ch)[N],
+                                          unsigned long long *pk, uint16_t *fv, uint32_t *fo, uint32_t lane) {
+    const unsigned bal = __ballot_sync(0xffffffffu, pm != 0);
+    if (!bal) return;
+    uint64_t own = (uint64_t)__popc(pm) << 40;
+#pragma unroll
+    for (int j = 0; j < N; j++)
+        if (pm >> j & 1) own += ch[j];
+    uint64_t mine;
+    if (__popc(bal) == 1) {
+        if (!pm) return;
+        mine = atomicAdd(pk, (unsigned long long)own);
+    } else {
+        uint64_t x = own;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= (uint32_t)o) x += y;
+        }
+        uint64_t base = 0;
+        if (lane == 31) base = atomicAdd(pk, (unsigned long long)x);
+        base = __shfl_sync(0xffffffffu, base, 31);
+        if (!pm) return;
+        mine = base + x - own;
+    }
+    uint32_t fi = (uint32_t)(mine >> 40), off = (uint32_t)(mine & MASK40);
+#pragma unroll
+    for (int j = 0; j < N; j++)
+        if (pm >> j & 1) {
+            fv[fi] = (uint16_t)v[j];
+            fo[fi] = off;
+            fi++;
+            off += ch[j];
+        }
+}
+
+__device__ __forceinline__ uint32_t tail_chunks(const uint32_t *s_coff, uint32_t v) {
+    return (s_coff[v + 1] - s_coff[v] + PEEL_CHUNK - 1) / PEEL_CHUNK;
+}
+
+__global__ void __launch_bounds__(CORE_TAIL_THREADS, 1)
+    peel_tail_kernel(const uint32_t *rem, uint32_t R, const uint32_t *coff, const uint32_t *cadj,
+                     uint32_t *level, PeelCtl *ctl) {
+    extern __shared__ __align__(16) uint32_t tail_smem[];
+    const uint32_t Rp = tail_pad(R);
+    uint32_t *s_deg = tail_smem, *s_lev = s_deg + Rp, *s_coff = s_lev + Rp;  // s_coff: R + 1 used
+    uint32_t *s_fo = s_coff + Rp + 4;                                        // [2][Rp] chunk offsets
+    uint16_t *s_fv = reinterpret_cast<uint16_t *>(s_fo + 2 * Rp);            // [2][Rp] vertices
+    __shared__ unsigned long long s_fpack[3];
+    __shared__ int s_min;
+    const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nthr = blockDim.x, nwarp = nthr >> 5;
+    // s_coff[i] for i >= R is coff[R] (padding vertices have no entries);
+    // each entry has one writer
+    for (uint32_t i = tid; i <= Rp; i += nthr) {
+        const uint32_t c = coff[min(i, R)];
+        s_coff[i] = c;
+        if (i < Rp) {
+            s_deg[i] = i < R ? coff[i + 1] - c : 0u;
+            s_lev[i] = i < R ? UNSET : 0u;  // padding counts as removed
+        }
+    }
+    if (tid == 0) {
+        s_fpack[0] = s_fpack[1] = s_fpack[2] = 0;
+        s_min = INT_MAX;
+    }
+    int k = __ldcg(&ctl->k);
+    const uint32_t round0 = __ldcg(&ctl->rounds);
+    uint32_t kappa = __ldcg(&ctl->kappa);
+    uint32_t round = 0;
+    bool need_level = true, ok = true;
+    const uint4 *deg4 = reinterpret_cast<const uint4 *>(s_deg), *lev4 = reinterpret_cast<const uint4 *>(s_lev);
+    __syncthreads();
+    for (;;) {
+        const uint32_t slot = round % 3, buf = round & 1;
+        if (need_level) {
+            // new level: the smallest remaining degree, then every remaining
+            // vertex of degree <= k joins this round's frontier
+            int my = INT_MAX;
+            for (uint32_t i4 = tid; i4 < Rp / 4; i4 += nthr) {
+                const uint4 d = deg4[i4], l = lev4[i4];
+                if (l.x == UNSET) my = min(my, (int)d.x);
+                if (l.y == UNSET) my = min(my, (int)d.y);
+                if (l.z == UNSET) my = min(my, (int)d.z);
+                if (l.w == UNSET) my = min(my, (int)d.w);
+            }
+#pragma unroll
+            for (int o = 16; o; o >>= 1) my = min(my, __shfl_xor_sync(0xffffffffu, my, o));
+            if (lane == 0 && my != INT_MAX) atomicMin(&s_min, my);
+            __syncthreads();
+            const int g = s_min;
+            if (g == INT_MAX) break;  // nothing left (uniform)
+            k = max(k, g);
+            kappa = max(kappa, (uint32_t)k);
+            for (uint32_t b0 = 0; b0 < Rp / 4; b0 += nthr) {  // uniform trip count: the push is warp-collective
+                const uint32_t i4 = b0 + tid;
+                uint32_t v[4], ch[4], pm = 0;
+                if (i4 < Rp / 4) {
+                    const uint4 d = deg4[i4], l = lev4[i4];
+                    const uint32_t dd[4] = {d.x, d.y, d.z, d.w}, ll[4] = {l.x, l.y, l.z, l.w};
+#pragma unroll
+                    for (int c = 0; c < 4; c++) {
+                        v[c] = 4 * i4 + c;
+                        ch[c] = 0;
+                        if (ll[c] == UNSET && (int)dd[c] <= k) {
+                            s_lev[v[c]] = round;
+                            ch[c] = tail_chunks(s_coff, v[c]);
+                            pm |= 1u << c;
+                        }
+                    }
+                }
+                tail_push(pm, v, ch, &s_fpack[slot], s_fv + buf * Rp, s_fo + buf * Rp, lane);
+            }
+            __syncthreads();
+            if (tid == 0) s_min = INT_MAX;  // every thread read it before the barrier above
+            need_level = false;
+        }
+        // relaxation of round `round`: chunk c belongs to the last frontier
+        // slot whose offset is <= c
+        const unsigned long long fp = s_fpack[slot];
+        const uint32_t fn = (uint32_t)(fp >> 40), nch = (uint32_t)(fp & MASK40);
+        if (tid == 0) s_fpack[(round + 2) % 3] = 0;  // read in round - 1, pushed into in round + 1
+        const uint16_t *FV = s_fv + buf * Rp;
+        const uint32_t *FO = s_fo + buf * Rp;
+        uint16_t *NV = s_fv + (buf ^ 1) * Rp;
+        uint32_t *NO = s_fo + (buf ^ 1) * Rp;
+        unsigned long long *npk = &s_fpack[(round + 1) % 3];
+        for (uint32_t c = wid; c < nch; c += nwarp) {  // warp-uniform
+            uint32_t lo = 0, hi = fn;
+            while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (FO[mid] <= c) lo = mid; else hi = mid;
+            }
+            const uint32_t fv = FV[lo], ab = s_coff[fv], na = s_coff[fv + 1] - ab;
+            const uint32_t e0 = (c - FO[lo]) * PEEL_CHUNK;
+            uint32_t w[CORE_RUN];
+            bool live[CORE_RUN];
+#pragma unroll
+            for (int j = 0; j < CORE_RUN; j++) {
+                const uint32_t e = e0 + (uint32_t)j * 32 + lane;
+                live[j] = e < na;
+                w[j] = live[j] ? cadj[ab + e] : 0u;
+            }
+            // no level check: a removed vertex already has degree <= k, so
+            // a decrement returns k + 1 only for a remaining vertex, once
+            uint32_t old[CORE_RUN];
+#pragma unroll
+            for (int j = 0; j < CORE_RUN; j++) old[j] = live[j] ? atomicSub(s_deg + w[j], 1u) : 0u;
+            uint32_t pch[CORE_RUN], pm = 0;
+#pragma unroll
+            for (int j = 0; j < CORE_RUN; j++) {
+                pch[j] = 0;
+                if (live[j] && (int)old[j] == k + 1) {
+                    s_lev[w[j]] = round + 1;
+                    pch[j] = tail_chunks(s_coff, w[j]);
+                    pm |= 1u << j;
+                }
+            }
+            tail_push(pm, w, pch, npk, NV, NO, lane);
+        }
+        __syncthreads();
+        const bool pushed = *npk != 0;
+        round++;
+        need_level = !pushed;
+        if (round > R + 1) {  // cannot happen: every round removes a vertex
+            ok = false;
+            break;
+        }
+    }
+    for (uint32_t i = tid; i < R; i += nthr)
+        if (s_lev[i] != UNSET) level[rem[i]] = round0 + s_lev[i];
+    if (tid == 0) {
+        ctl->rounds = round0 + round;
+        ctl->kappa = kappa;
+        ctl->handoff = 0;
+        if (!ok) ctl->error = 1;
+    }
+}
 
 __device__ __forceinline__ uint32_t mix32(uint64_t x) {
     // splitmix64 finaliser, used only to draw a random vertex order
@@ -1728,10 +1917,10 @@ int core_cluster_size() {
     static int best = 0;
     if (best) return best;
     best = -1;
-    cudaFuncSetAttribute(peel_core_kernel<true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (cudaFuncSetAttribute(peel_core_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)core_smem_bytes(PEEL_TAIL)) != cudaSuccess ||
-        cudaFuncSetAttribute(peel_core_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(peel_core_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (cudaFuncSetAttribute(peel_tail_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tail_smem_bytes(PEEL_TAIL)) != cudaSuccess ||
+        cudaFuncSetAttribute(peel_core_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)core_smem_bytes(CORE_PER_MAX)) != cudaSuccess) {
         cudaGetLastError();
         return best;
@@ -1750,7 +1939,7 @@ int core_cluster_size() {
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         int clusters = 0;
-        if (cudaOccupancyMaxActiveClusters(&clusters, peel_core_kernel<true>, &cfg) == cudaSuccess && clusters >= 1) {
+        if (cudaOccupancyMaxActiveClusters(&clusters, peel_core_kernel, &cfg) == cudaSuccess && clusters >= 1) {
             best = c;
             break;
         }
@@ -1978,7 +2167,7 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
     g->heavy_wide = st.sigma_max >= 65536;
 
     prof_end(g, s);
-    prof_begin(g, s, "load:peel");
+    prof_begin(g, s, "load:peel_adj");
     // ---- a3: ordering
     DevBuf<uint32_t> level(n, s);
     TTC_CUDA(cudaMemsetAsync(level.get(), 0xff, n * 4, s));
@@ -1989,6 +2178,8 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
         TTC_CUDA(cudaMemcpyAsync(cursor.get(), adj_off.get(), (n + 1) * 4, cudaMemcpyDeviceToDevice, s));
         adj_fill_kernel<<<grid_for(ms), TPB, 0, s>>>(g->pair_vtx.get(), ms, cursor.get(), adj.get());
         TTC_LAUNCH_CHECK();
+        prof_end(g, s);
+        prof_begin(g, s, "load:peel_grid");
         DevBuf<int> pdeg(n, s);
         TTC_CUDA(cudaMemcpyAsync(pdeg.get(), deg.get(), n * 4, cudaMemcpyDeviceToDevice, s));
         DevBuf<uint32_t> remA(n, s), remB(n, s), frontA(n, s), frontB(n, s), foffA(n, s), foffB(n, s);
@@ -2021,10 +2212,12 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
         }
         PeelCtl out = read_scalar(ctl.get(), s);
         if (out.error) fail(TTC_ERR_INTERNAL, "k-core peel did not finish");
+        prof_end(g, s);
+        prof_begin(g, s, "load:peel_core");
         if (out.handoff) {
             // stage 2, the core: the remaining vertices get local ids and their
             // induced adjacency; one cluster peels them down to PEEL_TAIL
-            // vertices, one CTA the rest (same kernel, one CTA, more threads)
+            // vertices (peel_core_kernel), one CTA the rest (peel_tail_kernel)
             uint32_t R = out.rem_n;
             const uint32_t *rem = out.rem_in_b ? remB.get() : remA.get();
             uint32_t *lid = frontA.get(), *tail_list = frontB.get();  // free after the first stage
@@ -2047,15 +2240,21 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
                 TTC_LAUNCH_CHECK();
                 const int cluster = core_cluster_size();
                 if (cluster <= 0) fail(TTC_ERR_CUDA, "no thread-block cluster of 8 or 16 CTAs fits this device");
-                const uint32_t ncta = one_cta ? 1u : (uint32_t)cluster;
-                uint32_t per = R;  // one CTA owns all; a cluster CTA a power of two
-                if (!one_cta) {
-                    per = 1;
-                    while (per * ncta < R) per <<= 1;
+                if (one_cta) {
+                    peel_tail_kernel<<<1, CORE_TAIL_THREADS, tail_smem_bytes(R), s>>>(
+                        rem, R, coff.get(), cadj.get(), level.get(), ctl.get());
+                    TTC_LAUNCH_CHECK();
+                    note_launch();
+                    out = read_scalar(ctl.get(), s);
+                    if (out.error) fail(TTC_ERR_INTERNAL, "k-core peel of the core did not finish");
+                    break;
                 }
+                const uint32_t ncta = (uint32_t)cluster;
+                uint32_t per = 1;  // vertices a cluster CTA owns: a power of two
+                while (per * ncta < R) per <<= 1;
                 cudaLaunchConfig_t cfg = {};
                 cfg.gridDim = dim3(ncta);
-                cfg.blockDim = dim3(one_cta ? CORE_TAIL_THREADS : CORE_THREADS);
+                cfg.blockDim = dim3(CORE_THREADS);
                 cfg.dynamicSmemBytes = core_smem_bytes(per);
                 cfg.stream = s;
                 cudaLaunchAttribute attr[1];
@@ -2064,16 +2263,15 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
                 attr[0].val.clusterDim.y = 1;
                 attr[0].val.clusterDim.z = 1;
                 cfg.attrs = attr;
-                cfg.numAttrs = one_cta ? 0 : 1;
-                TTC_CUDA(cudaLaunchKernelEx(&cfg, one_cta ? peel_core_kernel<false> : peel_core_kernel<true>, rem, R,
-                                            per, (const uint32_t *)coff.get(), (const uint32_t *)cadj.get(),
-                                            level.get(), pdeg.get(), one_cta ? 0u : PEEL_TAIL, tail_list,
-                                            ctl.get()));
+                cfg.numAttrs = 1;
+                TTC_CUDA(cudaLaunchKernelEx(&cfg, peel_core_kernel, rem, R, per, (const uint32_t *)coff.get(),
+                                            (const uint32_t *)cadj.get(), level.get(), pdeg.get(), PEEL_TAIL,
+                                            tail_list, ctl.get()));
                 note_launch();
                 out = read_scalar(ctl.get(), s);
                 if (out.error) fail(TTC_ERR_INTERNAL, "k-core peel of the core did not finish");
                 if (!out.handoff) break;
-                if (one_cta || out.rem_n > PEEL_TAIL || out.core_alive != out.rem_n)
+                if (out.rem_n > PEEL_TAIL || out.core_alive != out.rem_n)
                     fail(TTC_ERR_INTERNAL, "k-core peel: inconsistent hand-off");
                 R = out.rem_n;
                 rem = tail_list;
