@@ -254,7 +254,7 @@ __global__ void seg_sort_small_kernel(int64_t *key, const uint32_t *poff, const 
 
 // Size classes of the pairs above SEG_TINY_CAP edges: class 0 = 9..32 edges,
 // class c = 1..9 = (2^(c+4), 2^(c+5)] edges, class 10 = longer than
-// SEG_BIG_CAP (sorted by the whole-array fallback instead).
+// SEG_BIG_CAP (sorted together by radix sorts instead).
 constexpr int SEG_CLASSES = 11;
 
 __device__ __forceinline__ int seg_class(uint32_t len) {
@@ -281,6 +281,51 @@ __global__ void seg_classify_kernel(const uint32_t *poff, uint32_t ms, unsigned 
         if (c >= 0 && (int)lane == leader) base = atomicAdd(&cursor[c], (unsigned int)__popc(peers));
         base = __shfl_sync(0xffffffffu, base, leader);
         if (FILL && c >= 0) list[base + __popc(peers & ((1u << lane) - 1))] = (uint32_t)p;
+    }
+}
+
+// Pairs too long for the in-place sorts (nb of them, pair r listed in
+// list[r]): their starts and lengths, for the long-pair sort below.
+__global__ void long_pair_list_kernel(const uint32_t *list, uint32_t nb, const uint32_t *poff, uint32_t *start,
+                                      uint64_t *len) {
+    GRID_STRIDE(r, (size_t)nb) {
+        const uint32_t p = list[r];
+        start[r] = poff[p];
+        len[r] = poff[p + 1] - poff[p];
+    }
+}
+
+// Long pair of element j of their concatenation (pre: exclusive prefix of
+// their lengths).
+__device__ __forceinline__ uint32_t long_pair_of(const uint64_t *pre, uint32_t nb, uint64_t j) {
+    uint32_t lo = 0, hi = nb;  // last r with pre[r] <= j
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (pre[mid] <= j) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// The long pairs' keys are gathered with each pair's rank, sorted by key and
+// then stably by rank, and written back into the same slots.
+__global__ void long_pair_gather_kernel(const int64_t *key, const uint32_t *start, const uint64_t *pre, uint32_t nb,
+                                        uint64_t total, uint64_t *gk, uint32_t *gr) {
+    GRID_STRIDE(j, total) {
+        const uint32_t r = long_pair_of(pre, nb, j);
+        gk[j] = (uint64_t)key[start[r] + (j - pre[r])];
+        gr[j] = r;
+    }
+}
+
+__global__ void long_pair_rank_kernel(const uint32_t *gr, uint64_t total, uint64_t *rk) {
+    GRID_STRIDE(j, total) rk[j] = gr[j];
+}
+
+__global__ void long_pair_scatter_kernel(const uint64_t *gk, const uint32_t *start, const uint64_t *pre, uint32_t nb,
+                                         uint64_t total, int64_t *key) {
+    GRID_STRIDE(j, total) {
+        const uint32_t r = long_pair_of(pre, nb, j);
+        key[start[r] + (j - pre[r])] = (int64_t)gk[j];
     }
 }
 
@@ -2129,7 +2174,7 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
         TTC_CUDA(cudaMemcpyAsync(g->poff.get() + ms, &mm32, 4, cudaMemcpyHostToDevice, s));
         TTC_CUDA(cudaStreamSynchronize(s));
     }
-    pid.reset(); head.reset();
+    pid.reset(); head.reset(); pkey.reset();
     // ---- a5: each pair's list in key order and its dir-0 prefix.  Nothing
     // before the count reads them, so they run on a side stream that
     // overlaps the peel, orientation and enumeration, and join at the end.
@@ -2516,22 +2561,42 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
     st.tau_hwarp = n_hw;
     st.tau_hcta = n_hc;
     st.tau_huge = n_huge;
-    // join the side stream; a pair longer than the in-place sort's largest
-    // class sends the whole array through a stable time sort and a second
-    // pair sort instead, and the dir-0 prefix is taken again
+    // join the side stream; the pairs longer than the in-place sort's largest
+    // class are sorted together (by key, then stably by pair), and the dir-0
+    // prefix is taken again
     side.join();
     if (seg_sort_after) {
-        const unsigned int too_long = read_scalar(cls.get() + SEG_CLASSES - 1, s);
-        if (too_long) {
-            radix_sort_u64_u64_range(reinterpret_cast<uint64_t *>(g->key.get()), pkey.get(), m, g->shift,
-                                     g->shift + span_bits, s);
-            radix_sort_u64_u64(pkey.get(), reinterpret_cast<uint64_t *>(g->key.get()), m, bits_for(n * n - 1), s);
+        unsigned int lp[2];  // count and list base of the pairs too long for the in-place sorts
+        TTC_CUDA(cudaMemcpyAsync(&lp[0], cls.get() + SEG_CLASSES - 1, 4, cudaMemcpyDeviceToHost, s));
+        TTC_CUDA(cudaMemcpyAsync(&lp[1], cls.get() + 2 * SEG_CLASSES - 1, 4, cudaMemcpyDeviceToHost, s));
+        TTC_CUDA(cudaStreamSynchronize(s));
+        if (lp[0]) {
+            const uint32_t nb = lp[0];
+            DevBuf<uint32_t> start(nb, s);
+            DevBuf<uint64_t> len(nb, s), pre((size_t)nb + 1, s);
+            long_pair_list_kernel<<<grid_for(nb), TPB, 0, s>>>(lists.get() + lp[1], nb, g->poff.get(), start.get(),
+                                                               len.get());
+            TTC_LAUNCH_CHECK();
+            exclusive_scan_u64(len.get(), pre.get(), nb, s);
+            const uint64_t total = read_scalar(pre.get() + nb, s);
+            DevBuf<uint64_t> gk(total, s), rk(total, s);
+            DevBuf<uint32_t> gr(total, s);
+            long_pair_gather_kernel<<<grid_for(total), TPB, 0, s>>>(g->key.get(), start.get(), pre.get(), nb, total,
+                                                                    gk.get(), gr.get());
+            TTC_LAUNCH_CHECK();
+            radix_sort_u64_u32(gk.get(), gr.get(), total, (int)st.key_bits, s);
+            long_pair_rank_kernel<<<grid_for(total), TPB, 0, s>>>(gr.get(), total, rk.get());
+            TTC_LAUNCH_CHECK();
+            radix_sort_u64_u64(rk.get(), gk.get(), total, bits_for(nb - 1), s);
+            long_pair_scatter_kernel<<<grid_for(total), TPB, 0, s>>>(gk.get(), start.get(), pre.get(), nb, total,
+                                                                     g->key.get());
+            TTC_LAUNCH_CHECK();
             dir0_flags_kernel<<<grid_for(m), TPB, 0, s>>>(g->key.get(), m, dflag.get());
             TTC_LAUNCH_CHECK();
             exclusive_scan_flags(dflag.get(), g->fwd.get(), m, s);
         }
     }
-    cls.reset(); lists.reset(); dflag.reset(); pkey.reset();
+    cls.reset(); lists.reset(); dflag.reset();
     set_view(g, s);
     prof_end(g, s);
     TTC_CUDA(cudaStreamSynchronize(s));
