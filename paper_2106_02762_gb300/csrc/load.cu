@@ -167,22 +167,45 @@ __global__ void dir0_flags_kernel(const int64_t *key, size_t m, uint8_t *f) {
     GRID_STRIDE(i, m) f[i] = (key[i] & 1) == 0;
 }
 
-__global__ void pair_sizes_kernel(const uint32_t *poff, size_t ms, const uint2 *pv, unsigned int *deg,
-                                  unsigned int *sigma_max) {
+// Static degrees.  The pairs are sorted by (lo, hi), so the pairs of one
+// lower endpoint u are the run [lo_first[u], lo_first[u] + lo_cnt[u]): its
+// two ends are found where lo changes (plain stores, no atomics, even for a
+// hub), and only the higher endpoints are counted with atomics (hi_cnt).
+// Also the longest pair (sigma_max).
+__global__ void pair_sizes_kernel(const uint32_t *poff, size_t ms, const uint2 *pv, uint32_t *lo_first,
+                                  unsigned int *hi_cnt, unsigned int *sigma_max) {
     unsigned int mx = 0;
     GRID_STRIDE(p, ms) {
         mx = max(mx, poff[p + 1] - poff[p]);
-        atomicAdd(&deg[pv[p].x], 1u);
-        atomicAdd(&deg[pv[p].y], 1u);
+        const uint2 e = pv[p];
+        if (p == 0 || pv[p - 1].x != e.x) lo_first[e.x] = (uint32_t)p;
+        atomicAdd(&hi_cnt[e.y], 1u);
     }
     for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if ((threadIdx.x & 31) == 0) atomicMax(sigma_max, mx);
 }
 
-__global__ void adj_fill_kernel(const uint2 *pv, size_t ms, uint32_t *cursor, uint32_t *adj) {
+// deg = lo_cnt + hi_cnt, with lo_cnt written at each run's end.
+__global__ void lo_runs_kernel(size_t ms, const uint2 *pv, const uint32_t *lo_first, unsigned int *lo_cnt) {
     GRID_STRIDE(p, ms) {
-        adj[atomicAdd(&cursor[pv[p].x], 1u)] = pv[p].y;
-        adj[atomicAdd(&cursor[pv[p].y], 1u)] = pv[p].x;
+        const uint32_t x = pv[p].x;
+        if (p + 1 == ms || pv[p + 1].x != x) lo_cnt[x] = (uint32_t)p + 1 - lo_first[x];
+    }
+}
+
+__global__ void deg_sum_kernel(size_t n, const unsigned int *lo_cnt, const unsigned int *hi_cnt, unsigned int *deg) {
+    GRID_STRIDE(v, n) deg[v] = lo_cnt[v] + hi_cnt[v];
+}
+
+// Adjacency lists: u's higher neighbours first, in pair order at fixed
+// places (coalesced, no atomics), then its lower neighbours through a cursor
+// (hi_cur, zeroed).
+__global__ void adj_fill_kernel(const uint2 *pv, size_t ms, const uint32_t *adj_off, const uint32_t *lo_first,
+                                const unsigned int *lo_cnt, unsigned int *hi_cur, uint32_t *adj) {
+    GRID_STRIDE(p, ms) {
+        const uint2 e = pv[p];
+        adj[adj_off[e.x] + ((uint32_t)p - lo_first[e.x])] = e.y;
+        adj[adj_off[e.y] + lo_cnt[e.y] + atomicAdd(&hi_cur[e.y], 1u)] = e.x;
     }
 }
 
@@ -2203,10 +2226,17 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
     prof_end(g, s);
     prof_begin(g, s, "load:degrees");
     // ---- static graph: undirected CSR, degrees
-    DevBuf<unsigned int> deg(n, s), smax(1, s);
-    TTC_CUDA(cudaMemsetAsync(deg.get(), 0, n * 4, s));
+    DevBuf<unsigned int> deg(n, s), smax(1, s), lo_cnt(n, s), hi_cnt(n, s);
+    DevBuf<uint32_t> lo_first(n, s);
+    TTC_CUDA(cudaMemsetAsync(lo_cnt.get(), 0, n * 4, s));
+    TTC_CUDA(cudaMemsetAsync(hi_cnt.get(), 0, n * 4, s));
     TTC_CUDA(cudaMemsetAsync(smax.get(), 0, 4, s));
-    pair_sizes_kernel<<<grid_for(ms), TPB, 0, s>>>(g->poff.get(), ms, g->pair_vtx.get(), deg.get(), smax.get());
+    pair_sizes_kernel<<<grid_for(ms), TPB, 0, s>>>(g->poff.get(), ms, g->pair_vtx.get(), lo_first.get(), hi_cnt.get(),
+                                                   smax.get());
+    TTC_LAUNCH_CHECK();
+    lo_runs_kernel<<<grid_for(ms), TPB, 0, s>>>(ms, g->pair_vtx.get(), lo_first.get(), lo_cnt.get());
+    TTC_LAUNCH_CHECK();
+    deg_sum_kernel<<<grid_for(n), TPB, 0, s>>>(n, lo_cnt.get(), hi_cnt.get(), deg.get());
     TTC_LAUNCH_CHECK();
     st.sigma_max = read_scalar(smax.get(), s);
     g->heavy_wide = st.sigma_max >= 65536;
@@ -2218,11 +2248,13 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
     TTC_CUDA(cudaMemsetAsync(level.get(), 0xff, n * 4, s));
     if (opt.orientation == TTC_ORIENT_DEGENERACY) {
         if (2ull * ms >= (uint64_t(1) << 32)) fail(TTC_ERR_RANGE, "too many static edges for the peel");
-        DevBuf<uint32_t> adj_off(n + 1, s), adj(2 * (size_t)ms, s), cursor(n + 1, s);
+        DevBuf<uint32_t> adj_off(n + 1, s), adj(2 * (size_t)ms, s);
         exclusive_scan_u32(deg.get(), adj_off.get(), n, s);
-        TTC_CUDA(cudaMemcpyAsync(cursor.get(), adj_off.get(), (n + 1) * 4, cudaMemcpyDeviceToDevice, s));
-        adj_fill_kernel<<<grid_for(ms), TPB, 0, s>>>(g->pair_vtx.get(), ms, cursor.get(), adj.get());
+        TTC_CUDA(cudaMemsetAsync(hi_cnt.get(), 0, n * 4, s));  // now the cursors of the lower neighbours
+        adj_fill_kernel<<<grid_for(ms), TPB, 0, s>>>(g->pair_vtx.get(), ms, adj_off.get(), lo_first.get(),
+                                                     lo_cnt.get(), hi_cnt.get(), adj.get());
         TTC_LAUNCH_CHECK();
+        lo_first.reset(); lo_cnt.reset(); hi_cnt.reset();
         prof_end(g, s);
         prof_begin(g, s, "load:peel_grid");
         DevBuf<int> pdeg(n, s);
