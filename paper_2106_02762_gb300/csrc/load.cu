@@ -566,6 +566,24 @@ __device__ __forceinline__ void flush_frontier(PeelSlot *sl, uint32_t *front, ui
     }
 }
 
+// Last index fi in [0, fn) with foff[fi] <= x, for a non-decreasing foff
+// with foff[0] = 0 <= x, by one warp (every lane calls it): each round the
+// lanes probe 32 evenly spaced places and keep the stretch between the last
+// one at or below x and the next, so fn offsets take about log32 fn
+// dependent device-memory loads instead of log2 fn.
+__device__ __forceinline__ uint32_t warp_last_le(const uint32_t *foff, uint32_t fn, uint32_t x, uint32_t lane) {
+    uint32_t lo = 0, hi = fn;  // the answer is in [lo, hi); foff[lo] <= x
+    while (hi - lo > 32) {
+        const uint32_t step = (hi - lo + 31) / 32;
+        const uint32_t pos = lo + lane * step;
+        const unsigned bal = __ballot_sync(0xffffffffu, pos < hi && __ldcg(foff + pos) <= x);
+        lo += (31 - __clz(bal)) * step;  // lane 0 probes lo itself, so bal != 0
+        hi = min(hi, lo + step);
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, lo + lane < hi && __ldcg(foff + lo + lane) <= x);
+    return lo + (31 - __clz(bal));
+}
+
 // Phase barrier of the grid-wide peel: every CTA of a cooperative launch,
 // through an arrival counter and a generation word in device memory.  The
 // wait is bounded; a CTA that gives up reports failure so the kernel stops.
@@ -637,6 +655,7 @@ __global__ void __launch_bounds__(PEEL_THREADS)
     uint32_t *s_foff = peel_smem, *s_front = peel_smem + PEEL_CACHE;
     uint32_t *s_ab = peel_smem + 2 * PEEL_CACHE, *s_off = s_ab + PEEL_STAGE;
     __shared__ PeelStage stg;
+    __shared__ uint32_t s_slice[2];  // frontier slots of a CTA's first and last edge
     if (threadIdx.x == 0) {
         stg.cnt = 0;
         stg.cut = ~0ull;
@@ -766,45 +785,56 @@ __global__ void __launch_bounds__(PEEL_THREADS)
             fn = (uint32_t)(f >> 40);
             fe = (uint32_t)(f & MASK40);
         }
-        // relaxation: remove the frontier (round `round`).  Each thread takes
-        // PEEL_RUN consecutive edges and issues their loads and atomics as
-        // independent batches, so one round costs a few memory latencies.
+        // relaxation: remove the frontier (round `round`).  The round's
+        // edges are dealt to the CTAs in equal contiguous ranges (every SM
+        // takes part however small the round), a CTA stages the slice of the
+        // frontier that covers its range in shared memory (two warp-parallel
+        // searches of the offsets), and each thread takes PEEL_RUN
+        // consecutive edges, finds their vertex in the slice and issues
+        // their loads and atomics as independent batches.
         PeelSlot *sl = &ctl->slot[ph % 3];
-        // small frontiers are copied into every CTA's shared memory first, so
-        // the per-edge searches below cost no device-memory latency
-        const bool cached = fn <= PEEL_CACHE;
-        if (cached) {
-            for (uint32_t i = threadIdx.x; i < fn; i += blockDim.x) {
-                s_foff[i] = __ldcg(foff + i);
-                s_front[i] = __ldcg(front + i);
+        const uint32_t cper = (fe + gridDim.x - 1) / gridDim.x;
+        const uint32_t cb = min(fe, blockIdx.x * cper), ce = min(fe, cb + cper);
+        for (uint32_t sb = cb; sb < ce; sb += blockDim.x * PEEL_RUN) {  // uniform per CTA
+            const uint32_t se = min(ce, sb + blockDim.x * PEEL_RUN);
+            if (threadIdx.x < 64) {
+                const uint32_t fi = warp_last_le(foff, fn, threadIdx.x < 32 ? sb : se - 1, lane);
+                if (lane == 0) s_slice[threadIdx.x >> 5] = fi;
             }
             __syncthreads();
-        }
-        auto ld_foff = [&](uint32_t i) { return cached ? s_foff[i] : __ldcg(foff + i); };
-        auto ld_front = [&](uint32_t i) { return cached ? s_front[i] : __ldcg(front + i); };
-        for (uint32_t e0 = tid * PEEL_RUN; e0 - tid * PEEL_RUN < fe; e0 += nthr * PEEL_RUN) {
-            // the loop bound keeps every lane of a warp iterating together
+            const uint32_t f0 = s_slice[0], nsl = s_slice[1] - f0 + 1;
+            const bool cached = nsl <= PEEL_CACHE;
+            if (cached)
+                for (uint32_t i = threadIdx.x; i < nsl; i += blockDim.x) {
+                    s_foff[i] = __ldcg(foff + f0 + i);
+                    s_front[i] = __ldcg(front + f0 + i);
+                }
+            __syncthreads();
+            const uint32_t fb = cached ? f0 : 0u, fc = cached ? nsl : fn;  // the slice searched
+            auto ld_foff = [&](uint32_t i) { return cached ? s_foff[i] : __ldcg(foff + i); };
+            auto ld_front = [&](uint32_t i) { return cached ? s_front[i] : __ldcg(front + i); };
+            const uint32_t e0 = sb + threadIdx.x * PEEL_RUN;
             uint32_t wv[PEEL_RUN];
             bool live[PEEL_RUN];
-            if (e0 < fe) {
-                uint32_t lo = 0, hi = fn;  // last fi with foff[fi] <= e0
+            if (e0 < se) {
+                uint32_t lo = 0, hi = fc;  // last slot of the slice with offset <= e0
                 while (hi - lo > 1) {
                     const uint32_t mid = (lo + hi) >> 1;
                     if (ld_foff(mid) <= e0) lo = mid; else hi = mid;
                 }
                 uint32_t fi = lo;
                 uint32_t fbeg = ld_foff(fi);
-                uint32_t fend = fi + 1 < fn ? ld_foff(fi + 1) : fe;
+                uint32_t fend = fb + fi + 1 < fn ? (fi + 1 < fc ? ld_foff(fi + 1) : __ldcg(foff + fb + fi + 1)) : fe;
                 uint32_t base = ld_front(fi);
 #pragma unroll
                 for (int j = 0; j < PEEL_RUN; j++) {
                     const uint32_t e = e0 + j;
-                    live[j] = e < fe;
+                    live[j] = e < se;
                     if (live[j]) {
-                        while (e >= fend) {
+                        while (e >= fend) {  // the next vertex (inside the slice: e < se)
                             fi++;
                             fbeg = fend;
-                            fend = fi + 1 < fn ? ld_foff(fi + 1) : fe;
+                            fend = fb + fi + 1 < fn ? (fi + 1 < fc ? ld_foff(fi + 1) : __ldcg(foff + fb + fi + 1)) : fe;
                             base = ld_front(fi);
                         }
                         wv[j] = adj[base + (e - fbeg)];
@@ -830,6 +860,7 @@ __global__ void __launch_bounds__(PEEL_THREADS)
                 }
                 push_frontier(push, ab, na, sl, front_next, foff_next, lane, &stg, s_ab, s_off);
             }
+            __syncthreads();  // the slice is read before the next one is staged
         }
         flush_frontier(sl, front_next, foff_next, &stg, s_ab, s_off);
         const PeelSlot *r = end_phase();
