@@ -568,9 +568,14 @@ def run_ours(args):
     # the light threshold, tuned on this graph (rank 0; every rank then loads
     # with the same explicit value, so all hold the same bins)
     chosen, tune_ms = 0, None
+    caps, caps_ms = (0, 0), None
     if rank == 0:
         chosen, tune_ms = ttc.tune_light(d_src, d_dst, d_t, step_deltas, stream=sptr)
+        # then the prefix-sum path's class caps at that threshold
+        caps, caps_ms = ttc.tune_heavy(d_src, d_dst, d_t, step_deltas, light_max_pairs=chosen, stream=sptr)
     chosen = int(allreduce_max(float(chosen), ws, dev))
+    caps = (int(allreduce_max(float(caps[0]), ws, dev)), int(allreduce_max(float(caps[1]), ws, dev)))
+    bins = dict(light_max_pairs=chosen, heavy_warp_cap=caps[0], heavy_cta_cap=caps[1])
 
     # on N GPUs every rank loads the same graph and counts its shard of the
     # triangle list; the ranks' counts are summed (the one exchange)
@@ -581,12 +586,12 @@ def run_ours(args):
         return shard.count_sharded(g, step_deltas, rank, ws, device=dev)
 
     def step_device():
-        g = ttc.Graph(d_src, d_dst, d_t, stream=sptr, light_max_pairs=chosen)
+        g = ttc.Graph(d_src, d_dst, d_t, stream=sptr, **bins)
         return g, count(g)
 
     def step_host():
         g = ttc.Graph(h_src.numpy().view(np.uint32), h_dst.numpy().view(np.uint32), h_t.numpy(), stream=sptr,
-                      light_max_pairs=chosen)
+                      **bins)
         return g, count(g)
 
     # warm-up
@@ -629,7 +634,7 @@ def run_ours(args):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        g = ttc.Graph(d_src, d_dst, d_t, stream=sptr, light_max_pairs=chosen)
+        g = ttc.Graph(d_src, d_dst, d_t, stream=sptr, **bins)
         e1.record(stream)
         e1.synchronize()
         load_ms.append(e0.elapsed_time(e1))
@@ -640,7 +645,7 @@ def run_ours(args):
     # recorded by the library on the graph's stream
     torch.cuda.synchronize()
     w = time.perf_counter()
-    g = ttc.Graph(d_src, d_dst, d_t, stream=sptr, profile_load=True, light_max_pairs=chosen)
+    g = ttc.Graph(d_src, d_dst, d_t, stream=sptr, profile_load=True, **bins)
     load_wall = time.perf_counter() - w
     load_phases = {k: v for k, v in g.profile()}
     info = g.info()
@@ -684,7 +689,7 @@ def run_ours(args):
         e1 = torch.cuda.Event(enable_timing=True)
         e2 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        gs = ttc.Graph(d_src, d_dst, d_t, stream=sptr, streamed=True, light_max_pairs=chosen)
+        gs = ttc.Graph(d_src, d_dst, d_t, stream=sptr, streamed=True, **bins)
         e1.record(stream)
         out_s = gs.count_batch(step_deltas)
         e2.record(stream)
@@ -774,6 +779,10 @@ def run_ours(args):
                            "kernels_ms": {k: v * 1e3 for k, v in kern_step.items()}},
             "light_threshold": {"chosen": chosen, "candidates_ms": tune_ms,
                                 "note": "ttc_tune_light: load + the step's batch at each threshold"},
+            "heavy_caps": {"chosen": list(caps),
+                           "candidates_ms": {"%d/%d" % wc: v for wc, v in caps_ms.items()} if caps_ms else None,
+                           "note": "ttc_tune_heavy at the chosen light threshold: the prefix-sum path's "
+                                   "one-warp and one-CTA caps (edges of A plus B)"},
             "load_ms": load_s * 1e3,
             "load_edges_per_s": m / load_s,
             "load_phases_ms": {"wall": load_wall * 1e3, **load_phases},

@@ -122,8 +122,21 @@ typedef struct {
     uint32_t labeling;         /* TTC_LABEL_* */
     uint32_t light_max_pairs;  /* triangles with sigma_A * sigma_B below this use the
                                   one-thread-per-triangle path, the others the
-                                  prefix-sum path (1 = all prefix-sum); 0 = default;
-                                  values above 2^20 count as 2^20 */
+                                  prefix-sum path (1 = all prefix-sum); 0 = the
+                                  tuned value for graphs of this shape
+                                  (ttc_tune_light), else the default; values
+                                  above 2^20 count as 2^20 */
+    uint32_t heavy_warp_cap;   /* prefix-sum-path triangles whose two enumerated
+                                  lists hold at most this many edges together are
+                                  counted by one warp each; 0 = tuned
+                                  (ttc_tune_heavy), else the kernel's capacity
+                                  (128 edges, 64 when a pair holds 2^16 edges or
+                                  more); larger values count as the capacity */
+    uint32_t heavy_cta_cap;    /* the others up to this many edges by one CTA
+                                  each, the rest by the flat path; 0 = tuned,
+                                  else the capacity (2048, 1024 when a pair holds
+                                  2^16 edges or more); clamped to
+                                  [heavy_warp_cap, capacity] */
     uint64_t seed;             /* TTC_ORIENT_RANDOM permutation seed */
     void *stream;              /* cudaStream_t to adopt; NULL = create one */
 } ttc_load_opts;
@@ -151,6 +164,8 @@ typedef struct {
                                 sigma_A * sigma_B (the (a, b) pairs that path visits) */
     uint32_t key_bits;       /* bits of the packed per-edge key */
     uint32_t light_max_pairs; /* the light threshold the load used (given, tuned or default) */
+    uint32_t heavy_warp_cap;  /* the one-warp class's cap the load used (edges of A plus B) */
+    uint32_t heavy_cta_cap;   /* the one-CTA class's cap the load used */
 } ttc_graph_stats;
 
 /* Build the device-resident graph (Alg. 1 steps up to the triangle list:
@@ -167,7 +182,8 @@ ttc_status ttc_load_ex(const uint32_t *src, const uint32_t *dst, const int64_t *
  * form of Algs. 2-4; the paper has no such split).  Loads the graph once per
  * candidate threshold (ttc_tune_candidates), times load plus one
  * ttc_count_batch of the k probe queries (host arrays) with CUDA events on
- * opts->stream, and keeps the fastest: *chosen receives it, ms (may be NULL)
+ * opts->stream (the faster of two timed runs after an untimed one), and
+ * keeps the fastest: *chosen receives it, ms (may be NULL)
  * the time of each candidate.  The choice is cached for graphs of the same
  * shape (bit lengths of m, m_s, largest multiplicity and kappa) on a GPU
  * with the same number of SMs, in the JSON file $TTC_TUNE_CACHE (default
@@ -179,6 +195,25 @@ static const uint32_t ttc_tune_candidates[TTC_TUNE_CANDIDATES] = {17, 65, 257, 1
 ttc_status ttc_tune_light(const uint32_t *src, const uint32_t *dst, const int64_t *t, uint64_t m,
                           const ttc_load_opts *opts, const ttc_delta *probe, uint32_t k, uint32_t *chosen,
                           float *ms);
+
+/* Tuning of the prefix-sum path's split into its three classes (one warp,
+ * one CTA, flat; this library's, not the paper's) at the light threshold
+ * opts->light_max_pairs (0: tuned or default).  Loads the graph once per
+ * (warp cap, CTA cap) pair of ttc_tune_heavy_candidates (capped as in
+ * ttc_load_opts), times load plus one ttc_count_batch of the k probe
+ * queries (the fastest of three timed runs after an untimed one), and keeps
+ * the fastest, the first candidate (the kernels' capacities) unless another
+ * is more than 1% faster: *warp_cap and *cta_cap receive the caps the loads
+ * used, ms (may be NULL) the time of each candidate.  With no prefix-sum-path triangle it stops after the
+ * first.  The choice is cached like the light threshold's (per shape, SM
+ * count and light threshold); ttc_load_ex with both caps 0 then uses it.
+ * opts->heavy_warp_cap and opts->heavy_cta_cap must be 0. */
+#define TTC_TUNE_HEAVY_CANDIDATES 6
+static const uint32_t ttc_tune_heavy_candidates[TTC_TUNE_HEAVY_CANDIDATES][2] = {
+    {128, 2048}, {64, 2048}, {32, 2048}, {128, 1024}, {64, 1024}, {128, 512}};
+ttc_status ttc_tune_heavy(const uint32_t *src, const uint32_t *dst, const int64_t *t, uint64_t m,
+                          const ttc_load_opts *opts, const ttc_delta *probe, uint32_t k, uint32_t *warp_cap,
+                          uint32_t *cta_cap, float *ms);
 
 /* Release a graph and all of its device memory.  NULL is a no-op. */
 void ttc_free(ttc_graph *g);

@@ -106,6 +106,7 @@ namespace ttc {
 
 struct LoadOptions {
     uint32_t flags = 0, orientation = 0, labeling = 0, light_max_pairs = 0;
+    uint32_t heavy_warp_cap = 0, heavy_cta_cap = 0;
     uint64_t seed = 0;
 };
 
@@ -184,6 +185,9 @@ uint32_t default_light_max_pairs();
 // multi.cu: the light threshold ttc_tune_light chose for graphs of this
 // shape on the current GPU (the tune cache), else default_light_max_pairs().
 uint32_t tuned_light_max(const ttc_graph_stats &st);
+// The heavy-class caps tuned for graphs of this shape at light threshold
+// `light` (ttc_tune_heavy), if any.
+bool tuned_heavy_caps(const ttc_graph_stats &st, uint32_t light, uint32_t *warp_cap, uint32_t *cta_cap);
 
 // A build with -DTTC_DEBUG_BOUNDS=1 checks the count kernels' indices on
 // the device (count_dev.cuh); this returns and clears the device word those

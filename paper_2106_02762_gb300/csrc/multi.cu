@@ -111,6 +111,16 @@ std::string light_key(const ttc_graph_stats &st) {
     return b;
 }
 
+// The heavy-class caps are tuned for a shape and the light threshold in use
+// (which decides the heavy triangles): "heavy|...|l<threshold>" keys as
+// [warp cap, CTA cap].
+std::string heavy_key(const ttc_graph_stats &st, uint32_t light) {
+    char b[160];
+    snprintf(b, sizeof b, "heavy|sm%d|m%d|s%d|x%d|k%d|l%u", sm_count(), bits_for(st.m), bits_for(st.m_s),
+             bits_for(st.sigma_max), bits_for(st.kappa), light);
+    return std::string(b);
+}
+
 // ---------------------------------------------------------------- plans
 struct Plan {
     std::vector<ttc_graph *> graphs;
@@ -342,6 +352,57 @@ uint32_t tuned_light_max(const ttc_graph_stats &st) {
     return it != g_light_mem.end() ? (uint32_t)it->second.light_per_sm : default_light_max_pairs();
 }
 
+bool tuned_heavy_caps(const ttc_graph_stats &st, uint32_t light, uint32_t *warp_cap, uint32_t *cta_cap) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (!g_light_loaded) {
+        g_light_mem = tune_load();
+        g_light_loaded = true;
+    }
+    const auto it = g_light_mem.find(heavy_key(st, light));
+    if (it == g_light_mem.end()) return false;
+    *warp_cap = (uint32_t)it->second.light_per_sm;
+    *cta_cap = (uint32_t)it->second.heavy_per_sm;
+    return true;
+}
+
+namespace {
+
+// Load plus one batched count of the probe queries, timed with CUDA events
+// on the options' stream: one untimed run (first-use work), then the
+// fastest of `timed` runs; st gets the graph's statistics.
+ttc_status time_load_count(const uint32_t *src, const uint32_t *dst, const int64_t *t, uint64_t m,
+                           const ttc_load_opts &o, const ttc_delta *probe, uint32_t k, int timed, float *best,
+                           ttc_graph_stats *st) {
+    std::vector<uint64_t> out(8 * (size_t)(k ? k : 1));
+    for (int rep = 0; rep <= timed; rep++) {
+        float ms = 0.f;
+        float *el = &ms;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        TTC_CUDA(cudaEventCreate(&e0));
+        TTC_CUDA(cudaEventCreate(&e1));
+        cudaStream_t s = static_cast<cudaStream_t>(o.stream);
+        TTC_CUDA(cudaEventRecord(e0, s));
+        ttc_graph *g = nullptr;
+        ttc_status rc = ttc_load_ex(src, dst, t, m, &o, &g);
+        if (rc == TTC_OK && k) rc = ttc_count_batch(g, probe, k, out.data());
+        if (rc == TTC_OK) {
+            *st = g->st;
+            TTC_CUDA(cudaStreamSynchronize(g->stream));
+        }
+        ttc_free(g);
+        TTC_CUDA(cudaEventRecord(e1, s));
+        TTC_CUDA(cudaEventSynchronize(e1));
+        TTC_CUDA(cudaEventElapsedTime(el, e0, e1));
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (rc != TTC_OK) return rc;
+        if (rep == 1 || (rep > 1 && ms < *best)) *best = ms;
+    }
+    return TTC_OK;
+}
+
+}  // namespace
+
 }  // namespace ttc
 
 extern "C" ttc_status ttc_tune_light(const uint32_t *src, const uint32_t *dst, const int64_t *t, uint64_t m,
@@ -357,35 +418,14 @@ extern "C" ttc_status ttc_tune_light(const uint32_t *src, const uint32_t *dst, c
     }
     try {
         ttc_load_opts o = opts ? *opts : ttc_load_opts{};
-        std::vector<uint64_t> out(8 * (size_t)(k ? k : 1));
         float best = 0.f;
         uint32_t best_c = default_light_max_pairs();
         ttc_graph_stats st{};
         for (uint32_t i = 0; i < TTC_TUNE_CANDIDATES; i++) {
             o.light_max_pairs = ttc_tune_candidates[i];
-            // one untimed load and count (first-use work), then a timed one
             float el = 0.f;
-            for (int rep = 0; rep < 2; rep++) {
-                cudaEvent_t e0 = nullptr, e1 = nullptr;
-                TTC_CUDA(cudaEventCreate(&e0));
-                TTC_CUDA(cudaEventCreate(&e1));
-                cudaStream_t s = static_cast<cudaStream_t>(o.stream);
-                TTC_CUDA(cudaEventRecord(e0, s));
-                ttc_graph *g = nullptr;
-                ttc_status rc = ttc_load_ex(src, dst, t, m, &o, &g);
-                if (rc == TTC_OK && k) rc = ttc_count_batch(g, probe, k, out.data());
-                if (rc == TTC_OK) {
-                    st = g->st;
-                    TTC_CUDA(cudaStreamSynchronize(g->stream));
-                }
-                ttc_free(g);
-                TTC_CUDA(cudaEventRecord(e1, s));
-                TTC_CUDA(cudaEventSynchronize(e1));
-                TTC_CUDA(cudaEventElapsedTime(&el, e0, e1));
-                cudaEventDestroy(e0);
-                cudaEventDestroy(e1);
-                if (rc != TTC_OK) return rc;
-            }
+            const ttc_status rc = time_load_count(src, dst, t, m, o, probe, k, 2, &el, &st);
+            if (rc != TTC_OK) return rc;
             if (ms) ms[i] = el;
             if (i == 0 || el < best) {
                 best = el;
@@ -404,6 +444,68 @@ extern "C" ttc_status ttc_tune_light(const uint32_t *src, const uint32_t *dst, c
             g_light_loaded = true;
         }
         *chosen = best_c;
+        return TTC_OK;
+    } catch (const Failure &f) {
+        set_last_error(f.message);
+        return f.status;
+    } catch (...) {
+        set_last_error("unexpected internal failure");
+        return TTC_ERR_INTERNAL;
+    }
+}
+
+extern "C" ttc_status ttc_tune_heavy(const uint32_t *src, const uint32_t *dst, const int64_t *t, uint64_t m,
+                                     const ttc_load_opts *opts, const ttc_delta *probe, uint32_t k,
+                                     uint32_t *warp_cap, uint32_t *cta_cap, float *ms) {
+    if (!warp_cap || !cta_cap || (k && !probe)) {
+        set_last_error("NULL argument");
+        return TTC_ERR_INVALID;
+    }
+    if (opts && (opts->heavy_warp_cap || opts->heavy_cta_cap)) {
+        set_last_error("ttc_tune_heavy chooses the heavy caps itself: pass 0");
+        return TTC_ERR_INVALID;
+    }
+    try {
+        ttc_load_opts o = opts ? *opts : ttc_load_opts{};
+        float best = 0.f;
+        uint32_t bw = 0, bc = 0, dw = 0, dc = 0;
+        ttc_graph_stats st{};
+        for (uint32_t i = 0; i < TTC_TUNE_HEAVY_CANDIDATES; i++) {
+            o.heavy_warp_cap = ttc_tune_heavy_candidates[i][0];
+            o.heavy_cta_cap = ttc_tune_heavy_candidates[i][1];
+            float el = 0.f;
+            const ttc_status rc = time_load_count(src, dst, t, m, o, probe, k, 3, &el, &st);
+            if (rc != TTC_OK) return rc;
+            if (ms) ms[i] = el;
+            // another pair replaces the first (the kernels' capacities) only
+            // when it is faster by more than 1%, not by timing noise
+            if (i == 0) {
+                dw = st.heavy_warp_cap;
+                dc = st.heavy_cta_cap;
+            }
+            if (i == 0 || el < best * (bw == dw && bc == dc ? 0.99f : 1.0f)) {
+                best = el;
+                bw = st.heavy_warp_cap;
+                bc = st.heavy_cta_cap;
+            }
+            if (!st.tau_heavy) {  // no heavy triangle: every candidate counts the same
+                for (uint32_t j = i + 1; ms && j < TTC_TUNE_HEAVY_CANDIDATES; j++) ms[j] = el;
+                break;
+            }
+        }
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto cache = tune_load();
+            Shape sh;
+            sh.light_per_sm = (int)bw;
+            sh.heavy_per_sm = (int)bc;
+            cache[heavy_key(st, st.light_max_pairs)] = sh;
+            tune_store(cache);
+            g_light_mem = cache;
+            g_light_loaded = true;
+        }
+        *warp_cap = bw;
+        *cta_cap = bc;
         return TTC_OK;
     } catch (const Failure &f) {
         set_last_error(f.message);

@@ -37,8 +37,10 @@ EXPORTS = ["ttc_load", "ttc_load_ex", "ttc_free", "ttc_graph_info", "ttc_count",
            "ttc_serve_pause", "ttc_serve_set_reserve",
            "ttc_server_info", "ttc_last_error", "ttc_version", "ttc_debug_fail_alloc_after",
            "ttc_debug_launch_count", "ttc_set_profiling", "ttc_profile_read", "ttc_count_noalloc",
-           "ttc_release_cached", "ttc_memory_info", "ttc_count_grid", "ttc_count_shard", "ttc_tune_light"]
+           "ttc_release_cached", "ttc_memory_info", "ttc_count_grid", "ttc_count_shard", "ttc_tune_light", "ttc_tune_heavy"]
 TUNE_CANDIDATES = (17, 65, 257, 1025, 4097, 16385)  # ttc_tune_candidates in ttc.h
+# ttc_tune_heavy_candidates in ttc.h: (warp cap, CTA cap)
+TUNE_HEAVY_CANDIDATES = ((128, 2048), (64, 2048), (32, 2048), (128, 1024), (64, 1024), (128, 512))
 
 
 class TTCError(RuntimeError):
@@ -53,14 +55,16 @@ class Delta(ctypes.Structure):
 
 class LoadOpts(ctypes.Structure):
     _fields_ = [("flags", ctypes.c_uint32), ("orientation", ctypes.c_uint32), ("labeling", ctypes.c_uint32),
-                ("light_max_pairs", ctypes.c_uint32), ("seed", ctypes.c_uint64), ("stream", ctypes.c_void_p)]
+                ("light_max_pairs", ctypes.c_uint32), ("heavy_warp_cap", ctypes.c_uint32),
+                ("heavy_cta_cap", ctypes.c_uint32), ("seed", ctypes.c_uint64), ("stream", ctypes.c_void_p)]
 
 
 class GraphStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in
                 ("n", "m", "m_self_loops", "m_s", "tau", "kappa", "sigma_max", "peel_rounds", "work_bytes",
                  "enum_elems", "tau_light", "tau_heavy", "device_bytes", "work_bytes_heavy", "tau_huge", "tau_hwarp", "tau_hcta", "light_pairs")] + \
-               [("key_bits", ctypes.c_uint32), ("light_max_pairs", ctypes.c_uint32)]
+               [("key_bits", ctypes.c_uint32), ("light_max_pairs", ctypes.c_uint32),
+                ("heavy_warp_cap", ctypes.c_uint32), ("heavy_cta_cap", ctypes.c_uint32)]
 
 
 class KernelTime(ctypes.Structure):
@@ -99,6 +103,7 @@ def lib():
             "ttc_count_batch_async": ([p, p, u32, p, p], ctypes.c_int),
             "ttc_count_shard": ([p, p, u32, u32, u32, p], ctypes.c_int),
             "ttc_tune_light": ([p, p, p, u64, p, p, u32, p, p], ctypes.c_int),
+            "ttc_tune_heavy": ([p, p, p, u64, p, p, u32, p, p, p], ctypes.c_int),
             "ttc_count_multi": ([p, p, u32, p], ctypes.c_int),
             "ttc_count_sample": ([p, p, u64, u64, u64, p, p, p], ctypes.c_int),
             "ttc_server_create": ([p], p),
@@ -176,7 +181,8 @@ class Graph:
     """A device-resident temporal graph (``ttc_load_ex``)."""
 
     def __init__(self, src, dst, t, orientation=ORIENT_DEGENERACY, labeling=LABEL_HEAVIEST_VW,
-                 light_max_pairs=0, seed=0, stream=None, profile_load=False, streamed=False, strict_time=False):
+                 light_max_pairs=0, seed=0, stream=None, profile_load=False, streamed=False, strict_time=False,
+                 heavy_warp_cap=0, heavy_cta_cap=0):
         """streamed: TTC_LOAD_STREAM (no light-triangle list; every count
         enumerates the triangles again and counts light ones as it finds them).
         strict_time: TTC_LOAD_STRICT_TIME (count a triple only if its three
@@ -188,7 +194,7 @@ class Graph:
             flags |= LOAD_STREAM
         if strict_time:
             flags |= LOAD_STRICT_TIME
-        opts = LoadOpts(flags, orientation, labeling, light_max_pairs, seed, stream)
+        opts = LoadOpts(flags, orientation, labeling, light_max_pairs, heavy_warp_cap, heavy_cta_cap, seed, stream)
         h = ctypes.c_void_p()
         check(lib().ttc_load_ex(ptrs[0], ptrs[1], ptrs[2], m, ctypes.byref(opts), ctypes.byref(h)))
         self._h = h
@@ -274,7 +280,7 @@ def tune_light(src, dst, t, probe_deltas, stream=None, orientation=ORIENT_DEGENE
     threshold in TUNE_CANDIDATES, caches the fastest for graphs of this
     shape and returns (chosen threshold, {candidate: ms})."""
     ptrs, m, flags, keep = _edge_ptrs(src, dst, t)
-    opts = LoadOpts(flags, orientation, labeling, 0, 0, stream)
+    opts = LoadOpts(flags, orientation, labeling, 0, 0, 0, 0, stream)
     d, dp = _deltas(probe_deltas)
     chosen = ctypes.c_uint32()
     ms = (ctypes.c_float * len(TUNE_CANDIDATES))()
@@ -282,6 +288,23 @@ def tune_light(src, dst, t, probe_deltas, stream=None, orientation=ORIENT_DEGENE
                                ctypes.byref(chosen), ms))
     del keep
     return int(chosen.value), {c: float(v) for c, v in zip(TUNE_CANDIDATES, ms)}
+
+
+def tune_heavy(src, dst, t, probe_deltas, light_max_pairs=0, stream=None, orientation=ORIENT_DEGENERACY,
+               labeling=LABEL_HEAVIEST_VW):
+    """ttc_tune_heavy: times load + count of the probe queries at each (warp
+    cap, CTA cap) of TUNE_HEAVY_CANDIDATES at the given light threshold,
+    caches the fastest and returns ((warp cap, CTA cap) the loads used,
+    {candidate: ms})."""
+    ptrs, m, flags, keep = _edge_ptrs(src, dst, t)
+    opts = LoadOpts(flags, orientation, labeling, light_max_pairs, 0, 0, 0, stream)
+    d, dp = _deltas(probe_deltas)
+    w, c = ctypes.c_uint32(), ctypes.c_uint32()
+    ms = (ctypes.c_float * len(TUNE_HEAVY_CANDIDATES))()
+    check(lib().ttc_tune_heavy(ptrs[0], ptrs[1], ptrs[2], m, ctypes.byref(opts), dp, d.shape[0],
+                               ctypes.byref(w), ctypes.byref(c), ms))
+    del keep
+    return (int(w.value), int(c.value)), {cand: float(v) for cand, v in zip(TUNE_HEAVY_CANDIDATES, ms)}
 
 
 def count_multi(graphs, deltas) -> np.ndarray:
