@@ -276,6 +276,23 @@ ttc_status ttc_count_batch_async(ttc_graph *g, const ttc_delta *d_dev, uint32_t 
  * handles and replayed afterwards. */
 ttc_status ttc_count_multi(ttc_graph *const *g, const ttc_delta *d, uint32_t G, uint64_t *out);
 
+/* Streaming many-graph count, for collections of graphs that need not fit
+ * in device memory together (the paper has no counterpart).  Graph i is the
+ * host arrays (src[i], dst[i], t[i]) of m[i] edges, counted under d[i].  The
+ * graphs are loaded in order (ttc_load_ex with opts, which may be NULL;
+ * TTC_LOAD_DEVICE_INPUT and TTC_LOAD_STREAM are refused) and gathered into
+ * batches: a graph joins the current batch while the batch's device
+ * footprint (ttc_graph_stats.device_bytes) stays within budget_bytes
+ * (0: half of the device memory free at the call), else the batch is counted
+ * by one ttc_count_multi launch and freed first.  So device memory holds at
+ * most one batch plus the graph being loaded; a graph larger than the budget
+ * forms a batch of its own.  out: G * 8 counts (host); *batches (may be
+ * NULL) receives the number of batches.  On an error the graphs loaded so
+ * far are freed. */
+ttc_status ttc_count_stream(const uint32_t *const *src, const uint32_t *const *dst, const int64_t *const *t,
+                            const uint64_t *m, const ttc_delta *d, uint32_t G, const ttc_load_opts *opts,
+                            uint64_t budget_bytes, uint64_t *out, uint32_t *batches);
+
 /* Sampled per-triangle counts, for checking against a slow reference at full
  * size: every `stride`-th static triangle of the graph's own list, starting
  * at `first`, is counted under d by the same kernels as ttc_count.  Writes up

@@ -515,3 +515,64 @@ extern "C" ttc_status ttc_tune_heavy(const uint32_t *src, const uint32_t *dst, c
         return TTC_ERR_INTERNAL;
     }
 }
+
+extern "C" ttc_status ttc_count_stream(const uint32_t *const *src, const uint32_t *const *dst,
+                                       const int64_t *const *t, const uint64_t *m, const ttc_delta *d, uint32_t G,
+                                       const ttc_load_opts *opts, uint64_t budget_bytes, uint64_t *out,
+                                       uint32_t *batches) {
+    if (G && (!src || !dst || !t || !m || !d || !out)) {
+        set_last_error("NULL argument");
+        return TTC_ERR_INVALID;
+    }
+    if (opts && (opts->flags & (TTC_LOAD_DEVICE_INPUT | TTC_LOAD_STREAM))) {
+        set_last_error("ttc_count_stream loads host arrays into listed graphs: "
+                       "TTC_LOAD_DEVICE_INPUT and TTC_LOAD_STREAM are refused");
+        return TTC_ERR_INVALID;
+    }
+    std::vector<ttc_graph *> batch;
+    uint32_t first = 0, nb = 0;  // first graph of the current batch
+    auto release = [&]() {
+        for (ttc_graph *g : batch) ttc_free(g);
+        batch.clear();
+    };
+    auto flush = [&]() -> ttc_status {
+        if (batch.empty()) return TTC_OK;
+        const ttc_status rc = ttc_count_multi(batch.data(), d + first, (uint32_t)batch.size(), out + 8 * (size_t)first);
+        release();
+        nb++;
+        return rc;
+    };
+    uint64_t budget = budget_bytes, bytes = 0;
+    if (!budget) {
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+            cudaGetLastError();
+            set_last_error("cudaMemGetInfo failed");
+            return TTC_ERR_CUDA;
+        }
+        budget = fr / 2;
+    }
+    for (uint32_t i = 0; i < G; i++) {
+        ttc_graph *g = nullptr;
+        ttc_status rc = ttc_load_ex(src[i], dst[i], t[i], m[i], opts, &g);
+        if (rc != TTC_OK) {
+            release();
+            return rc;
+        }
+        const uint64_t b = g->st.device_bytes;
+        if (!batch.empty() && bytes + b > budget) {
+            rc = flush();
+            if (rc != TTC_OK) {
+                ttc_free(g);
+                return rc;
+            }
+            first = i;
+            bytes = 0;
+        }
+        batch.push_back(g);
+        bytes += b;
+    }
+    const ttc_status rc = flush();
+    if (batches) *batches = nb;
+    return rc;
+}

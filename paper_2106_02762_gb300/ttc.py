@@ -37,7 +37,8 @@ EXPORTS = ["ttc_load", "ttc_load_ex", "ttc_free", "ttc_graph_info", "ttc_count",
            "ttc_serve_pause", "ttc_serve_set_reserve",
            "ttc_server_info", "ttc_last_error", "ttc_version", "ttc_debug_fail_alloc_after",
            "ttc_debug_launch_count", "ttc_set_profiling", "ttc_profile_read", "ttc_count_noalloc",
-           "ttc_release_cached", "ttc_memory_info", "ttc_count_grid", "ttc_count_shard", "ttc_tune_light", "ttc_tune_heavy"]
+           "ttc_release_cached", "ttc_memory_info", "ttc_count_grid", "ttc_count_shard", "ttc_tune_light", "ttc_tune_heavy",
+           "ttc_count_stream"]
 TUNE_CANDIDATES = (17, 65, 257, 1025, 4097, 16385)  # ttc_tune_candidates in ttc.h
 # ttc_tune_heavy_candidates in ttc.h: (warp cap, CTA cap)
 TUNE_HEAVY_CANDIDATES = ((128, 2048), (64, 2048), (32, 2048), (128, 1024), (64, 1024), (128, 512))
@@ -104,6 +105,7 @@ def lib():
             "ttc_count_shard": ([p, p, u32, u32, u32, p], ctypes.c_int),
             "ttc_tune_light": ([p, p, p, u64, p, p, u32, p, p], ctypes.c_int),
             "ttc_tune_heavy": ([p, p, p, u64, p, p, u32, p, p, p], ctypes.c_int),
+            "ttc_count_stream": ([p, p, p, p, p, u32, p, u64, p, p], ctypes.c_int),
             "ttc_count_multi": ([p, p, u32, p], ctypes.c_int),
             "ttc_count_sample": ([p, p, u64, u64, u64, p, p, p], ctypes.c_int),
             "ttc_server_create": ([p], p),
@@ -305,6 +307,36 @@ def tune_heavy(src, dst, t, probe_deltas, light_max_pairs=0, stream=None, orient
                                ctypes.byref(w), ctypes.byref(c), ms))
     del keep
     return (int(w.value), int(c.value)), {cand: float(v) for cand, v in zip(TUNE_HEAVY_CANDIDATES, ms)}
+
+
+def count_stream(edge_lists, deltas, budget_bytes=0, orientation=ORIENT_DEGENERACY, labeling=LABEL_HEAVIEST_VW,
+                 light_max_pairs=0):
+    """ttc_count_stream: counts many graphs given as host (src, dst, t)
+    arrays, loaded in order into batches whose device footprint stays within
+    budget_bytes (0: half of the free device memory), one ttc_count_multi
+    launch per batch.  Returns (counts [G, 8], number of batches)."""
+    G = len(edge_lists)
+    d, dp = _deltas(deltas)
+    if d.shape[0] != G:
+        raise ValueError("one delta-triple per graph")
+    keep, ms = [], []
+    ps = [(ctypes.c_void_p * G)() for _ in range(3)]
+    for i, (src, dst, t) in enumerate(edge_lists):
+        if _is_torch(src):
+            raise ValueError("count_stream takes host arrays")
+        ptrs, m, _, k = _edge_ptrs(src, dst, t)
+        for j in range(3):
+            ps[j][i] = ptrs[j]
+        ms.append(m)
+        keep.append(k)
+    m_arr = np.asarray(ms, dtype=np.uint64)
+    opts = LoadOpts(0, orientation, labeling, light_max_pairs, 0, 0, 0, None)
+    out = np.zeros((G, NUM_TYPES), dtype=np.uint64)
+    nb = ctypes.c_uint32(0)
+    check(lib().ttc_count_stream(ps[0], ps[1], ps[2], m_arr.ctypes.data, dp, G, ctypes.byref(opts),
+                                 int(budget_bytes), out.ctypes.data, ctypes.byref(nb)))
+    del keep
+    return out, int(nb.value)
 
 
 def count_multi(graphs, deltas) -> np.ndarray:

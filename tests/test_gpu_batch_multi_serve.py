@@ -69,6 +69,39 @@ def test_count_multi_matches_oracle_and_replays():
         h.free()
 
 
+def test_count_stream_batches_within_budget():
+    # the streaming many-graph count: graphs loaded from host arrays in
+    # order, counted batch by batch under a device-memory budget; results
+    # equal the oracle's whatever the batching
+    gs = _small_graphs() + [_heavy_triangle_graph() + ((2000, 900, 1500),)]
+    edges = [(s, d, t) for s, d, t, _ in gs]
+    deltas = [q for *_, q in gs]
+    want = np.stack([oracle.count(s, d, t, [q])[0] for s, d, t, q in gs])
+    one = [ttc.Graph(*e) for e in edges]
+    sizes = [g.info()["device_bytes"] for g in one]
+    for g in one:
+        g.free()
+    got, nb = ttc.count_stream(edges, deltas)  # half the free memory: one batch
+    assert (got == want).all() and nb == 1
+    budget = max(sizes)  # the largest alone, the others a few a batch
+    got, nb = ttc.count_stream(edges, deltas, budget_bytes=budget)
+    assert (got == want).all()
+    # the batches follow the rule: a graph joins while the batch stays within
+    # the budget
+    expect, run = 1, 0
+    for b in sizes:
+        if run and run + b > budget:
+            expect, run = expect + 1, 0
+        run += b
+    assert nb == expect > 1
+    got, nb = ttc.count_stream(edges, deltas, budget_bytes=1)  # one graph a batch
+    assert (got == want).all() and nb == len(edges)
+    got, nb = ttc.count_stream(edges, deltas, budget_bytes=1, light_max_pairs=1)  # every triangle heavy
+    assert (got == want).all()
+    with pytest.raises(ValueError):
+        ttc.count_stream(edges, deltas[:-1])
+
+
 @pytest.mark.slow
 def test_many_graph_workload_sample_matches_oracle():
     # a seeded sample of 64 of the 4096 graphs of the many-graphs workload
