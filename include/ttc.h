@@ -301,6 +301,22 @@ ttc_status ttc_count_stream(const uint32_t *const *src, const uint32_t *const *d
 ttc_status ttc_count_sample(ttc_graph *g, const ttc_delta *d, uint64_t first, uint64_t stride,
                             uint64_t cap, uint32_t *tri, uint64_t *out, uint64_t *written);
 
+/* Participation counts (analytics on Def. 1's counts; the paper has no
+ * counterpart).  vertex[v], v < n: the number of delta-temporal triangles
+ * (all eight types) that have v as a vertex.  pair[p], p < m_s: the number
+ * that use an edge of static pair p, pairs numbered as ttc_graph_pairs
+ * lists them.  Either output (host) may be NULL.  Each static triangle's
+ * count comes from the same kernels as ttc_count_sample and is added to its
+ * three vertices and its three pairs, so sum(vertex) = sum(pair) = 3 times
+ * ttc_count's total.  TTC_ERR_OVERFLOW if a sum passes 2^64; refused
+ * (TTC_ERR_INVALID) for a TTC_LOAD_STREAM handle. */
+ttc_status ttc_count_participation(ttc_graph *g, const ttc_delta *d, uint64_t *vertex, uint64_t *pair);
+
+/* The static pairs (vertex pairs with at least one edge) in the library's
+ * pair order: lohi[2 p], lohi[2 p + 1] = the lower and the higher vertex id
+ * of pair p, for p < m_s (host). */
+ttc_status ttc_graph_pairs(ttc_graph *g, uint32_t *lohi);
+
 /* No-allocation variant of ttc_count (the paper has no counterpart; this is
  * an interface convenience).  For callers that cannot allocate device memory
  * when they count: beside a framework allocator that owns the device's

@@ -560,4 +560,41 @@ ttc_status ttc_count_sample(ttc_graph *g, const ttc_delta *d, uint64_t first, ui
     TTC_API_END
 }
 
+ttc_status ttc_count_participation(ttc_graph *g, const ttc_delta *d, uint64_t *vertex, uint64_t *pair) {
+    if (!g || !d) {
+        set_last_error("NULL argument");
+        return TTC_ERR_INVALID;
+    }
+    if (g->streamed) {
+        set_last_error("the graph was loaded with TTC_LOAD_STREAM: it keeps no triangle list");
+        return TTC_ERR_INVALID;
+    }
+    TTC_API_BEGIN
+    int64_t hq[3];
+    normalise(*d, hq);
+    std::lock_guard<std::mutex> lock(g->mu);
+    TTC_CUDA(cudaSetDevice(g->device));
+    DevBuf<int64_t> dq(3, g->stream);
+    TTC_CUDA(cudaMemcpyAsync(dq.get(), hq, 24, cudaMemcpyHostToDevice, g->stream));
+    count_participation(g, dq.get(), vertex, pair);
+    return TTC_OK;
+    TTC_API_END
+}
+
+ttc_status ttc_graph_pairs(ttc_graph *g, uint32_t *lohi) {
+    if (!g || (g->st.m_s && !lohi)) {
+        set_last_error("NULL argument");
+        return TTC_ERR_INVALID;
+    }
+    TTC_API_BEGIN
+    std::lock_guard<std::mutex> lock(g->mu);
+    TTC_CUDA(cudaSetDevice(g->device));
+    if (g->st.m_s) {
+        TTC_CUDA(cudaMemcpyAsync(lohi, g->pair_vtx.get(), g->st.m_s * 8, cudaMemcpyDeviceToHost, g->stream));
+        TTC_CUDA(cudaStreamSynchronize(g->stream));
+    }
+    return TTC_OK;
+    TTC_API_END
+}
+
 }  // extern "C"

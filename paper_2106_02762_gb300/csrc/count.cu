@@ -1302,58 +1302,47 @@ unsigned int take_bounds_word() {
 #endif
 }
 
-// ---------------------------------------------------------------- sampled output
-void count_sample(ttc_graph *g, const int64_t *dq, uint64_t first, uint64_t stride, uint64_t cap,
-                  uint32_t *tri_vtx_host, unsigned long long *out_host, uint64_t *written) {
-    cudaStream_t s = g->stream;
-    const uint64_t tau = g->st.tau, nl = g->st.tau_light;
-    std::vector<uint64_t> all;
-    for (uint64_t i = 0, ti = first; i < cap && ti < tau; i++, ti += stride) all.push_back(ti);
-    *written = all.size();
-    if (all.empty()) return;
+// ---------------------------------------------------------------- per-triangle output
+namespace {
+
+// Per-triangle counts under dq of the triangles listed, in ascending order,
+// in `all` (host ids into the graph's triangle list): d_out (device,
+// zeroed, 8 per listed triangle in list order).  The ids fall in the bins
+// in order (light, one-warp, one-CTA, flat), so each bin's share is one
+// run of the list and its kernels write their rows in list order.
+void count_ids(ttc_graph *g, const int64_t *dq, const std::vector<uint64_t> &all, unsigned long long *d_out,
+               unsigned long long *flag, cudaStream_t s) {
     const uint64_t n = all.size();
-    DevBuf<uint64_t> d_all(n, s), d_idx(n, s);
-    DevBuf<uint32_t> d_vtx(3 * n, s);
-    DevBuf<unsigned long long> d_out(8 * n, s);
-    TTC_CUDA(cudaMemcpyAsync(d_all.get(), all.data(), n * 8, cudaMemcpyHostToDevice, s));
-    TTC_CUDA(cudaMemsetAsync(d_out.get(), 0, 8 * n * 8, s));
-    record_vertices_kernel<<<ceil_div(n, 256), 256, 0, s>>>(g->tri.get(), g->pair_vtx.get(), d_all.get(), n,
-                                                            d_vtx.get());
-    TTC_LAUNCH_CHECK();
-    // split by bin: light, heavy (one warp / one CTA each), huge (flat)
-    const uint64_t nw = g->st.tau_hwarp, nc = g->st.tau_hcta;
-    std::vector<uint64_t> li, hw, hc, hh, slot(n);
+    if (!n) return;
+    const uint64_t nl = g->st.tau_light, nw = g->st.tau_hwarp, nc = g->st.tau_hcta;
+    // d_idx: light ids, bin-relative heavy ids, absolute huge ids
+    std::vector<uint64_t> order(n);
+    uint64_t nlc = 0, nwc = 0, ncc = 0;
     for (uint64_t i = 0; i < n; i++) {
-        if (all[i] < nl) li.push_back(i);
-        else if (all[i] < nl + nw) hw.push_back(i);
-        else if (all[i] < nl + nw + nc) hc.push_back(i);
-        else hh.push_back(i);
+        const uint64_t ti = all[i];
+        if (ti < nl) { order[i] = ti; nlc++; }
+        else if (ti < nl + nw) { order[i] = ti - nl; nwc++; }
+        else if (ti < nl + nw + nc) { order[i] = ti - nl - nw; ncc++; }
+        else order[i] = ti;
     }
-    std::vector<uint64_t> order;  // d_idx: light ids, bin-relative heavy ids, absolute huge ids
-    for (uint64_t i : li) { slot[i] = order.size(); order.push_back(all[i]); }
-    for (uint64_t i : hw) { slot[i] = order.size(); order.push_back(all[i] - nl); }
-    for (uint64_t i : hc) { slot[i] = order.size(); order.push_back(all[i] - nl - nw); }
-    for (uint64_t i : hh) { slot[i] = order.size(); order.push_back(all[i]); }
+    const uint64_t nfc = nwc + ncc, nhc = n - nlc - nfc;
+    DevBuf<uint64_t> d_idx(n, s);
     TTC_CUDA(cudaMemcpyAsync(d_idx.get(), order.data(), n * 8, cudaMemcpyHostToDevice, s));
-    const uint64_t nlc = li.size(), nwc = hw.size(), ncc = hc.size(), nhc = hh.size();
-    const uint64_t nfc = nwc + ncc;
-    DevBuf<unsigned long long> flag(1, s);
-    TTC_CUDA(cudaMemsetAsync(flag.get(), 0, 8, s));
     if (nlc) {
         if (g->strict)
             light_kernel<2, 1, true><<<light_grid((nlc + 31) / 32), LIGHT_THREADS, 0, s>>>(
-                g->view.get(), g->prefix.get(), 1, dq, 1, d_out.get(), flag.get(), d_idx.get(), nlc);
+                g->view.get(), g->prefix.get(), 1, dq, 1, d_out, flag, d_idx.get(), nlc);
         else
             light_kernel<2, 1, false><<<light_grid((nlc + 31) / 32), LIGHT_THREADS, 0, s>>>(
-                g->view.get(), g->prefix.get(), 1, dq, 1, d_out.get(), flag.get(), d_idx.get(), nlc);
+                g->view.get(), g->prefix.get(), 1, dq, 1, d_out, flag, d_idx.get(), nlc);
         TTC_LAUNCH_CHECK();
     }
     if (nwc)
-        launch_warp_any<2>(heavy_kind(g->heavy_wide, g->strict), g->view.get(), g->prefix.get() + 2, 1, nwc, dq, 1, d_out.get() + 8 * nlc,
-                           flag.get(), d_idx.get() + nlc, nwc, s);
+        launch_warp_any<2>(heavy_kind(g->heavy_wide, g->strict), g->view.get(), g->prefix.get() + 2, 1, nwc, dq, 1,
+                           d_out + 8 * nlc, flag, d_idx.get() + nlc, nwc, s);
     if (ncc)
         launch_fused_any<2>(heavy_kind(g->heavy_wide, g->strict), g->view.get(), g->prefix.get() + 4, 1, ncc, dq, 1,
-                            d_out.get() + 8 * (nlc + nwc), flag.get(), d_idx.get() + nlc + nwc, ncc, s);
+                            d_out + 8 * (nlc + nwc), flag, d_idx.get() + nlc + nwc, ncc, s);
     if (nhc) {
         DevBuf<uint4> sub(nhc, s);
         DevBuf<uint64_t> sizes(nhc, s), eoff(nhc + 1, s);
@@ -1373,18 +1362,102 @@ void count_sample(ttc_graph *g, const int64_t *dq, uint64_t first, uint64_t stri
         const size_t bytes = ((size_t)total + 4 * nhc) * 8 * (g->heavy_wide ? 8 : 4);
         DevBuf<uint8_t> pre(bytes, s);
         ha.pre = pre.get();
-        ha.per_tri = d_out.get() + 8 * (nlc + nfc);
+        ha.per_tri = d_out + 8 * (nlc + nfc);
         ProfOff off;
-        if (g->heavy_wide) run_huge<unsigned long long>(g, ha, dq, nullptr, flag.get(), s);
-        else run_huge<uint32_t>(g, ha, dq, nullptr, flag.get(), s);
+        if (g->heavy_wide) run_huge<unsigned long long>(g, ha, dq, nullptr, flag, s);
+        else run_huge<uint32_t>(g, ha, dq, nullptr, flag, s);
     }
-    std::vector<unsigned long long> h(8 * n);
-    std::vector<uint32_t> hv(3 * n);
-    TTC_CUDA(cudaMemcpyAsync(h.data(), d_out.get(), 8 * n * 8, cudaMemcpyDeviceToHost, s));
-    TTC_CUDA(cudaMemcpyAsync(hv.data(), d_vtx.get(), 3 * n * 4, cudaMemcpyDeviceToHost, s));
+}
+
+// Adds each listed triangle's count (all eight types; triangles c0 ..
+// c0 + cnt - 1 of the list, their rows in out) to its three vertices and its
+// three pairs; a sum past 2^64 sets the overflow flag.
+__global__ void participation_kernel(const uint4 *tri, const uint2 *pv, uint64_t c0, uint64_t cnt,
+                                     const unsigned long long *out, unsigned long long *vertex,
+                                     unsigned long long *pair, unsigned long long *flag) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        unsigned long long tot = 0;
+        bool ovf = false;
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            const unsigned long long x = out[8 * i + k];
+            ovf |= tot + x < tot;
+            tot += x;
+        }
+        if (!tot) continue;
+        const uint4 r = tri[c0 + i];
+        const uint2 a = pv[r.x], b = pv[r.y];
+        const uint32_t u = (a.x == b.x || a.x == b.y) ? a.x : a.y;
+        const uint32_t vtx[3] = {u, a.x == u ? a.y : a.x, b.x == u ? b.y : b.x};
+        if (vertex)
+#pragma unroll
+            for (int k = 0; k < 3; k++) ovf |= atomicAdd(vertex + vtx[k], tot) + tot < tot;
+        if (pair) {
+            const uint32_t ps[3] = {r.x, r.y, r.z};
+#pragma unroll
+            for (int k = 0; k < 3; k++) ovf |= atomicAdd(pair + ps[k], tot) + tot < tot;
+        }
+        if (ovf) atomicOr(flag, 1ull);
+    }
+}
+
+}  // namespace
+
+void count_sample(ttc_graph *g, const int64_t *dq, uint64_t first, uint64_t stride, uint64_t cap,
+                  uint32_t *tri_vtx_host, unsigned long long *out_host, uint64_t *written) {
+    cudaStream_t s = g->stream;
+    const uint64_t tau = g->st.tau;
+    std::vector<uint64_t> all;
+    for (uint64_t i = 0, ti = first; i < cap && ti < tau; i++, ti += stride) all.push_back(ti);
+    *written = all.size();
+    if (all.empty()) return;
+    const uint64_t n = all.size();
+    DevBuf<uint64_t> d_all(n, s);
+    DevBuf<uint32_t> d_vtx(3 * n, s);
+    DevBuf<unsigned long long> d_out(8 * n, s), flag(1, s);
+    TTC_CUDA(cudaMemcpyAsync(d_all.get(), all.data(), n * 8, cudaMemcpyHostToDevice, s));
+    TTC_CUDA(cudaMemsetAsync(d_out.get(), 0, 8 * n * 8, s));
+    TTC_CUDA(cudaMemsetAsync(flag.get(), 0, 8, s));
+    record_vertices_kernel<<<ceil_div(n, 256), 256, 0, s>>>(g->tri.get(), g->pair_vtx.get(), d_all.get(), n,
+                                                            d_vtx.get());
+    TTC_LAUNCH_CHECK();
+    count_ids(g, dq, all, d_out.get(), flag.get(), s);
+    TTC_CUDA(cudaMemcpyAsync(out_host, d_out.get(), 8 * n * 8, cudaMemcpyDeviceToHost, s));
+    TTC_CUDA(cudaMemcpyAsync(tri_vtx_host, d_vtx.get(), 3 * n * 4, cudaMemcpyDeviceToHost, s));
     TTC_CUDA(cudaStreamSynchronize(s));
-    for (uint64_t i = 0; i < n; i++) memcpy(out_host + 8 * i, &h[8 * slot[i]], 64);
-    memcpy(tri_vtx_host, hv.data(), 3 * n * 4);
+}
+
+void count_participation(ttc_graph *g, const int64_t *dq, uint64_t *vertex_host, uint64_t *pair_host) {
+    cudaStream_t s = g->stream;
+    const uint64_t tau = g->st.tau, n = g->st.n, ms = g->st.m_s;
+    DevBuf<unsigned long long> vc(vertex_host ? (n ? n : 1) : 1, s), pc(pair_host ? (ms ? ms : 1) : 1, s), flag(1, s);
+    if (vertex_host) TTC_CUDA(cudaMemsetAsync(vc.get(), 0, n * 8, s));
+    if (pair_host) TTC_CUDA(cudaMemsetAsync(pc.get(), 0, ms * 8, s));
+    TTC_CUDA(cudaMemsetAsync(flag.get(), 0, 8, s));
+    // triangles in chunks, each counted per triangle and added to its
+    // vertices and pairs
+    const uint64_t chunk = uint64_t(1) << 22;
+    DevBuf<unsigned long long> d_out(8 * std::min<uint64_t>(chunk, tau ? tau : 1), s);
+    std::vector<uint64_t> ids;
+    for (uint64_t c0 = 0; c0 < tau; c0 += chunk) {
+        const uint64_t cnt = std::min(chunk, tau - c0);
+        ids.resize(cnt);
+        for (uint64_t i = 0; i < cnt; i++) ids[i] = c0 + i;
+        TTC_CUDA(cudaMemsetAsync(d_out.get(), 0, 8 * cnt * 8, s));
+        count_ids(g, dq, ids, d_out.get(), flag.get(), s);
+        participation_kernel<<<ceil_div(cnt, 256), 256, 0, s>>>(g->tri.get(), g->pair_vtx.get(), c0, cnt,
+                                                                d_out.get(), vertex_host ? vc.get() : nullptr,
+                                                                pair_host ? pc.get() : nullptr, flag.get());
+        TTC_LAUNCH_CHECK();
+        TTC_CUDA(cudaStreamSynchronize(s));  // ids is rewritten for the next chunk
+    }
+    unsigned long long f = 0;
+    TTC_CUDA(cudaMemcpyAsync(&f, flag.get(), 8, cudaMemcpyDeviceToHost, s));
+    if (vertex_host && n) TTC_CUDA(cudaMemcpyAsync(vertex_host, vc.get(), n * 8, cudaMemcpyDeviceToHost, s));
+    if (pair_host && ms) TTC_CUDA(cudaMemcpyAsync(pair_host, pc.get(), ms * 8, cudaMemcpyDeviceToHost, s));
+    TTC_CUDA(cudaStreamSynchronize(s));
+    check_count_flag(f);
 }
 
 // ---------------------------------------------------------------- many graphs

@@ -157,6 +157,7 @@ void count_one_into(ttc_graph *g, const int64_t *dq, unsigned long long *acc, vo
 
 // count.cu: per-triangle counts of a strided sample of the triangle list.
 // (host outputs; the sampled triangles run through the same light/heavy code)
+void count_participation(ttc_graph *g, const int64_t *dq, uint64_t *vertex_host, uint64_t *pair_host);
 void count_sample(ttc_graph *g, const int64_t *dq, uint64_t first, uint64_t stride, uint64_t cap,
                   uint32_t *tri_vtx_host, unsigned long long *out_host, uint64_t *written);
 

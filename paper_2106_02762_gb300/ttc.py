@@ -38,7 +38,7 @@ EXPORTS = ["ttc_load", "ttc_load_ex", "ttc_free", "ttc_graph_info", "ttc_count",
            "ttc_server_info", "ttc_last_error", "ttc_version", "ttc_debug_fail_alloc_after",
            "ttc_debug_launch_count", "ttc_set_profiling", "ttc_profile_read", "ttc_count_noalloc",
            "ttc_release_cached", "ttc_memory_info", "ttc_count_grid", "ttc_count_shard", "ttc_tune_light", "ttc_tune_heavy",
-           "ttc_count_stream"]
+           "ttc_count_stream", "ttc_count_participation", "ttc_graph_pairs"]
 TUNE_CANDIDATES = (17, 65, 257, 1025, 4097, 16385)  # ttc_tune_candidates in ttc.h
 # ttc_tune_heavy_candidates in ttc.h: (warp cap, CTA cap)
 TUNE_HEAVY_CANDIDATES = ((128, 2048), (64, 2048), (32, 2048), (128, 1024), (64, 1024), (128, 512))
@@ -106,6 +106,8 @@ def lib():
             "ttc_tune_light": ([p, p, p, u64, p, p, u32, p, p], ctypes.c_int),
             "ttc_tune_heavy": ([p, p, p, u64, p, p, u32, p, p, p], ctypes.c_int),
             "ttc_count_stream": ([p, p, p, p, p, u32, p, u64, p, p], ctypes.c_int),
+            "ttc_count_participation": ([p, p, p, p], ctypes.c_int),
+            "ttc_graph_pairs": ([p, p], ctypes.c_int),
             "ttc_count_multi": ([p, p, u32, p], ctypes.c_int),
             "ttc_count_sample": ([p, p, u64, u64, u64, p, p, p], ctypes.c_int),
             "ttc_server_create": ([p], p),
@@ -266,6 +268,24 @@ class Graph:
         check(lib().ttc_count_grid(self.handle, int(d13), a.ctypes.data, a.size, b.ctypes.data, b.size,
                                    out.ctypes.data, cyc.ctypes.data))
         return out, cyc
+
+    def participation(self, delta):
+        """ttc_count_participation: (per-vertex counts [n], per-pair counts
+        [m_s]) of the delta-temporal triangles (all types) each vertex and
+        each static pair (in pairs() order) belongs to."""
+        d, dp = _deltas(delta)
+        info = self.info()
+        vert = np.zeros(info["n"], dtype=np.uint64)
+        pair = np.zeros(info["m_s"], dtype=np.uint64)
+        check(lib().ttc_count_participation(self.handle, dp, vert.ctypes.data if vert.size else None,
+                                            pair.ctypes.data if pair.size else None))
+        return vert, pair
+
+    def pairs(self) -> np.ndarray:
+        """ttc_graph_pairs: the static pairs (lo, hi) in the library's pair order, [m_s, 2]."""
+        out = np.zeros((self.info()["m_s"], 2), dtype=np.uint32)
+        check(lib().ttc_graph_pairs(self.handle, out.ctypes.data if out.size else None))
+        return out
 
     def sample(self, delta, first: int, stride: int, cap: int):
         d, dp = _deltas(delta)
