@@ -273,7 +273,9 @@ ttc_status ttc_count_batch_async(ttc_graph *g, const ttc_delta *d_dev, uint32_t 
 /* Many graphs in one launch: graph q is counted under d[q]; out is a host
  * array of G * 8 counts.  All graphs must live on the current device.  The
  * launch is captured into a CUDA graph on first use for a given set of
- * handles and replayed afterwards. */
+ * handles and replayed afterwards.  Graphs loaded with TTC_LOAD_STREAM keep
+ * no triangle list to share: they are counted one by one (as ttc_count)
+ * after the shared launch of the others. */
 ttc_status ttc_count_multi(ttc_graph *const *g, const ttc_delta *d, uint32_t G, uint64_t *out);
 
 /* Streaming many-graph count, for collections of graphs that need not fit

@@ -8,6 +8,7 @@
 #include <new>
 #include <set>
 #include <tuple>
+#include <vector>
 
 #include <nvtx3/nvToolsExt.h>
 
@@ -527,13 +528,34 @@ ttc_status ttc_count_multi(ttc_graph *const *g, const ttc_delta *d, uint32_t G, 
         set_last_error("NULL argument");
         return TTC_ERR_INVALID;
     }
-    for (uint32_t i = 0; i < G; i++)
-        if (g[i] && g[i]->streamed) {
-            set_last_error("a graph was loaded with TTC_LOAD_STREAM (no triangle list to share)");
-            return TTC_ERR_INVALID;
-        }
     TTC_API_BEGIN
-    count_multi(g, d, G, out);
+    // graphs loaded with TTC_LOAD_STREAM keep no triangle list to share:
+    // the listed ones run in the shared launch, the streamed ones one by one
+    std::vector<ttc_graph *> listed;
+    std::vector<ttc_delta> ld;
+    std::vector<uint32_t> where, streamed;
+    for (uint32_t i = 0; i < G; i++) {
+        if (g[i] && g[i]->streamed) {
+            streamed.push_back(i);
+        } else {
+            listed.push_back(g[i]);
+            ld.push_back(d[i]);
+            where.push_back(i);
+        }
+    }
+    if (streamed.empty()) {
+        count_multi(g, d, G, out);
+        return TTC_OK;
+    }
+    if (!listed.empty()) {
+        std::vector<uint64_t> lo(8 * listed.size());
+        count_multi(listed.data(), ld.data(), (uint32_t)listed.size(), lo.data());
+        for (size_t j = 0; j < where.size(); j++) memcpy(out + 8 * (size_t)where[j], &lo[8 * j], 64);
+    }
+    for (uint32_t i : streamed) {
+        const ttc_status rc = run_queries(g[i], d + i, 1, out + 8 * (size_t)i);
+        if (rc != TTC_OK) return rc;
+    }
     return TTC_OK;
     TTC_API_END
 }

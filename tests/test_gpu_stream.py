@@ -96,13 +96,27 @@ def test_streamed_matches_listed_handle_on_power_law():
     ref.free()
 
 
+def test_streamed_handles_in_many_graph_counts():
+    # a many-graph call mixing streamed and listed handles: the listed ones
+    # share one launch, the streamed ones are counted alone; all equal the
+    # oracle
+    graphs = [synth.tiny_plain(), synth.random_tiny(3, 20, 300, 50), synth.large_plain(scale=0.002)]
+    deltas = [(3600, 1800, 1800), (12, 7, 9), synth.LARGE_PLAIN_DELTA]
+    want = np.stack([oracle.count(s, d, t, [q])[0] for (s, d, t), q in zip(graphs, deltas)])
+    for mask in ((True, False, True), (True, True, True), (False, True, False)):
+        hs = [ttc.Graph(*e, streamed=st) for e, st in zip(graphs, mask)]
+        assert (ttc.count_multi(hs, deltas) == want).all(), mask
+        for h in hs:
+            h.free()
+
+
 def test_streamed_handle_refuses_list_entry_points():
     s, d, t = synth.tiny_plain()
     g = ttc.Graph(s, d, t, streamed=True)
     with pytest.raises(ttc.TTCError):
-        ttc.count_multi([g], [(3600, 1800, 1800)])
-    with pytest.raises(ttc.TTCError):
         g.sample((3600, 1800, 1800), 0, 1, 4)
+    with pytest.raises(ttc.TTCError):
+        g.participation((3600, 1800, 1800))
     q = np.asarray((3600, 1800, 1800), dtype=np.int64)
     out = np.zeros(8, dtype=np.uint64)
     assert ttc.lib().ttc_count_noalloc(g.handle, q.ctypes.data, out.ctypes.data, None) == -1  # TTC_ERR_INVALID
