@@ -111,10 +111,28 @@ __global__ void __launch_bounds__(LIGHT_THREADS, 4)
         for (int j = 0; j < 8; j++) s_acc[j][threadIdx.x] = 0;
         if ((threadIdx.x & 31) < 8) s_wide[threadIdx.x >> 5][threadIdx.x & 31] = 0;
     }
+    // MODE 1 without thread slots: the queries in descending d13 order (ties
+    // by index), so that a pair stops at the first query whose d13 is below
+    // its time gap (every later one would skip it too; a query whose windows
+    // cover the time span has d13 >= span >= any gap, so it comes first)
+    Query *s_qs = reinterpret_cast<Query *>(s_t);
+    uint32_t *s_qi = reinterpret_cast<uint32_t *>(s_qs + nq);
     if constexpr (MODE == 1) {
         for (uint32_t i = threadIdx.x; i < nq * 8; i += blockDim.x) s_bacc[i] = 0;
-        if (tslots)
+        if (tslots) {
             for (uint32_t i = 0; i < LIGHT_QT * 8; i++) s_t[i * LIGHT_THREADS + threadIdx.x] = 0;
+        } else {
+            for (uint32_t i = threadIdx.x; i < nq; i += blockDim.x) {
+                const int64_t di = dq[3 * i];
+                uint32_t r = 0;
+                for (uint32_t j = 0; j < nq; j++) {
+                    const int64_t dj = dq[3 * j];
+                    r += (dj > di || (dj == di && j < i)) ? 1u : 0u;
+                }
+                s_qs[r] = load_query(dq, i);
+                s_qi[r] = i;
+            }
+        }
         __syncthreads();
     }
 
@@ -280,10 +298,12 @@ __global__ void __launch_bounds__(LIGHT_THREADS, 4)
                         light_pair<MODE != 1>(C, f, MODE == 1 ? wt.q[w][ql] : Q0, a_first, rx, ry, code, accq);
                     }
                 } else {
-                    for (uint32_t q = q_beg; q < q_end; q++) {
-                        const Query Q = load_query(dq, q);
+                    const int64_t gap = ry - rx;
+                    for (uint32_t r = 0; r < nq && s_qs[r].d13 >= gap; r++) {
+                        const uint32_t q = s_qi[r];
+                        if (q < q_beg || q >= q_end) continue;
                         auto accq = [&](int type, uint32_t n) { shared_add(&s_bacc[q * 8 + type], n, ovf); };
-                        light_pair<false>(C, f, Q, a_first, rx, ry, code, accq);
+                        light_pair<false>(C, f, s_qs[r], a_first, rx, ry, code, accq);
                     }
                 }
             });
@@ -1184,7 +1204,8 @@ void count_light_records(ttc_graph *g, const GraphView *gv, const uint64_t *ligh
         const uint32_t groups = (uint32_t)std::min<uint64_t>(nq, (want_items + chunks - 1) / chunks);
         const uint32_t qpw = (nq + groups - 1) / groups;
         prof_begin(g, s, "light_batch");
-        const size_t smem = nq * 64 + (qpw <= LIGHT_QT ? (size_t)LIGHT_QT * 8 * LIGHT_THREADS * 4 : 0);
+        const size_t smem = nq * 64 + (qpw <= LIGHT_QT ? (size_t)LIGHT_QT * 8 * LIGHT_THREADS * 4
+                                                       : (size_t)nq * (sizeof(Query) + 4));
         {
             const size_t most = MAX_BATCH_SMEM_Q * 64 + LIGHT_QT * 8 * LIGHT_THREADS * 4;
             ensure_smem((const void *)light_kernel<1, LIGHT_BATCH_R, false>, most);
