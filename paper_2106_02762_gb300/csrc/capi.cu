@@ -249,6 +249,12 @@ void graph_destroy(ttc_graph *g) {
     g->s_out_off.reset(); g->s_in_off.reset();
     // every buffer is freed on the graph's stream, so before that stream goes
     if (s) cudaStreamSynchronize(s);
+    if (g->side) {
+        cudaStreamSynchronize(g->side);
+        cudaStreamDestroy(g->side);
+        cudaEventDestroy(g->side_fork);
+        cudaEventDestroy(g->side_join);
+    }
     if (g->own_stream && s) cudaStreamDestroy(s);
     delete g;
 }

@@ -44,6 +44,11 @@ struct ttc_graph {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    // the count's heavy bins run on a second stream beside the light bin
+    // (created at the first count; forked from and joined to the count's
+    // stream by the two events)
+    cudaStream_t side = nullptr;
+    cudaEvent_t side_fork = nullptr, side_join = nullptr;
     ttc_graph_stats st{};
     uint32_t labeling = 0;
     uint32_t light_max_pairs = 0;
