@@ -339,6 +339,23 @@ __device__ __forceinline__ void phase1_values(const CL &C, const KeyFmt &f, cons
     out[6] = m0; out[7] = pm - m0;
 }
 
+// Phase 1 without L(e), which does not depend on the query: the batched
+// kernels take it (and its prefix sums) from the batch's first query and
+// search only h, R and M for the others (slots 2 and 3 of out untouched).
+template <typename CL>
+__device__ __forceinline__ void phase1_values_hrm(const CL &C, const KeyFmt &f, const Query &q, int64_t ke,
+                                                  uint32_t out[8]) {
+    const int64_t re = ke >> f.shift;
+    const int64_t bd[3] = {le_bound(f, re + q.d13), lt_bound(f, re - q.d23), lt_bound(f, re - q.d13)};
+    uint32_t ps[3];
+    search_n<3>(C, bd, ps);
+    const uint32_t ph = ps[0], pr = ps[1], pm = ps[2];
+    const uint32_t h0 = C.d0(ph), r0 = C.d0(pr), m0 = C.d0(pm);
+    out[0] = h0; out[1] = ph - h0;
+    out[4] = r0; out[5] = pr - r0;
+    out[6] = m0; out[7] = pm - m0;
+}
+
 // Phase 2 for an enumerated edge e with O the other enumerated list.
 // pref(dO, s, c) = prefix over O's own-direction-dO edges, first c of them,
 // of phase-1 slot s.  add(dO, dC, pi if e is on A, pi if e is on B, n).
@@ -602,16 +619,26 @@ __global__ void __launch_bounds__(HEAVY_THREADS)
                 const uint32_t dz0 = z ? s_d0[e] - a0 : s_d0[e];
                 const uint32_t rank = de ? j - dz0 : dz0;
                 uint32_t v[8];
-                if (c_staged) phase1_values(Cs, f, Q, ke, v);
-                else phase1_values(C, f, Q, ke, v);
                 const uint32_t at = sbase[2 * z + de] + rank + 1;
+                if (q == 0) {
+                    if (c_staged) phase1_values(Cs, f, Q, ke, v);
+                    else phase1_values(C, f, Q, ke, v);
 #pragma unroll
-                for (int s = 0; s < 8; s++) s_pre[s * ES + at] = v[s];
+                    for (int s = 0; s < 8; s++) s_pre[s * ES + at] = v[s];
+                } else {  // L(e) and its prefix sums are the first query's
+                    if (c_staged) phase1_values_hrm(Cs, f, Q, ke, v);
+                    else phase1_values_hrm(C, f, Q, ke, v);
+#pragma unroll
+                    for (int s = 0; s < 8; s++)
+                        if (s != 2 && s != 3) s_pre[s * ES + at] = v[s];
+                }
             }
             __syncthreads();
             // inclusive scans: 4 segments x 8 slots, one warp per (segment, slot)
+            // (slots 2 and 3, L(e), only for the first query)
             for (uint32_t p = threadIdx.x >> 5; p < 32; p += HEAVY_WARPS) {
                 const uint32_t seg = p & 3, s = p >> 2, lane = threadIdx.x & 31;
+                if (q > 0 && (s == 2 || s == 3)) continue;  // warp-uniform
                 P *base = s_pre + s * ES + sbase[seg] + 1;
                 P carry = 0;
                 for (uint32_t c0 = 0; c0 < slen[seg]; c0 += 32) {
@@ -787,20 +814,31 @@ __global__ void __launch_bounds__(HEAVY_THREADS)
                 const uint32_t dz0 = z ? s_d0[e] - a0 : s_d0[e];
                 const uint32_t rank = de ? j - dz0 : dz0;
                 uint32_t v[8];
-                if (c_staged) phase1_values(Cs, f, Q, ke, v);
-                else phase1_values(C, f, Q, ke, v);
                 const uint32_t at = sbase[2 * z + de] + rank + 1;
+                if (q == 0) {
+                    if (c_staged) phase1_values(Cs, f, Q, ke, v);
+                    else phase1_values(C, f, Q, ke, v);
 #pragma unroll
-                for (int s = 0; s < 8; s++) s_pre[s * ES + at] = v[s];
+                    for (int s = 0; s < 8; s++) s_pre[s * ES + at] = v[s];
+                } else {  // L(e) and its prefix sums are the first query's
+                    if (c_staged) phase1_values_hrm(Cs, f, Q, ke, v);
+                    else phase1_values_hrm(C, f, Q, ke, v);
+#pragma unroll
+                    for (int s = 0; s < 8; s++)
+                        if (s != 2 && s != 3) s_pre[s * ES + at] = v[s];
+                }
             }
             __syncwarp();
-            {  // inclusive scans: lane p scans (segment p & 3, slot p >> 2)
+            {  // inclusive scans: lane p scans (segment p & 3, slot p >> 2);
+               // slots 2 and 3, L(e), only for the first query
                 const uint32_t seg = lane & 3, s = lane >> 2;
-                P *base = s_pre + s * ES + sbase[seg] + 1;
-                P run = 0;
-                for (uint32_t i = 0; i < slen[seg]; i++) {
-                    run += base[i];
-                    base[i] = run;
+                if (q == 0 || (s != 2 && s != 3)) {
+                    P *base = s_pre + s * ES + sbase[seg] + 1;
+                    P run = 0;
+                    for (uint32_t i = 0; i < slen[seg]; i++) {
+                        run += base[i];
+                        base[i] = run;
+                    }
                 }
             }
             __syncwarp();
