@@ -301,7 +301,7 @@ __global__ void __launch_bounds__(LIGHT_THREADS, 4)
                     const int64_t gap = ry - rx;
                     for (uint32_t r = 0; r < nq && s_qs[r].d13 >= gap; r++) {
                         const uint32_t q = s_qi[r];
-                        if (q < q_beg || q >= q_end) continue;
+                        if (q - q_beg >= q_end - q_beg) continue;  // outside [q_beg, q_end)
                         auto accq = [&](int type, uint32_t n) { shared_add(&s_bacc[q * 8 + type], n, ovf); };
                         light_pair<false>(C, f, s_qs[r], a_first, rx, ry, code, accq);
                     }
@@ -880,7 +880,15 @@ struct HugeArgs {
     uint64_t nh, total;
     void *pre;                          // prefix entries: 8 values each
     unsigned long long *per_tri;        // sample mode: per-record outputs
+    // queries of one pass: query q's prefix entries start at entry
+    // q * qstride (qstride = total + 4 nh) and its counts at out + 8 q
+    uint32_t nq = 1;
+    uint64_t qstride = 0;
 };
+
+// Scratch one batched pass of the flat path may take for its queries'
+// prefix entries (a single query always gets its own).
+constexpr size_t HUGE_PASS_BYTES = size_t(64) << 20;
 
 // Locates enumerated edge e: the last triangle h with eoff[h] <= e.
 __device__ __forceinline__ uint64_t find_tri(const uint64_t *__restrict__ eoff, uint64_t nh, uint64_t e) {
@@ -921,11 +929,14 @@ __device__ __forceinline__ uint64_t seg_base(const HugeTri &t, uint32_t z, uint3
 
 template <typename P, bool ST>
 __global__ void __launch_bounds__(HEAVY_THREADS) huge_phase1(HugeArgs a, const int64_t *dq) {
-    const Query q = load_query(dq, 0);
     const KeyFmt f{a.gv.shift, a.gv.span, ST};
-    P *pre = static_cast<P *>(a.pre);
-    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < a.total;
-         e += (uint64_t)gridDim.x * blockDim.x) {
+    // over (enumerated edge, query) of the pass
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < a.total * a.nq;
+         x += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t qi = (uint32_t)(x / a.total);
+        const uint64_t e = x - (uint64_t)qi * a.total;
+        const Query q = load_query(dq, qi);
+        P *pre = static_cast<P *>(a.pre) + 8 * a.qstride * qi;
         const uint64_t h = find_tri(a.eoff, a.nh, e);
         const HugeTri t = huge_tri(a, h);
         uint32_t j = (uint32_t)(e - __ldg(a.eoff + h));
@@ -948,11 +959,13 @@ __global__ void __launch_bounds__(HEAVY_THREADS) huge_phase1(HugeArgs a, const i
 // One warp per segment; 4 segments per huge triangle.
 template <typename P>
 __global__ void __launch_bounds__(HEAVY_THREADS) huge_scan(HugeArgs a) {
-    P *pre = static_cast<P *>(a.pre);
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
-    for (uint64_t sidx = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); sidx < 4 * a.nh;
-         sidx += warps) {
+    for (uint64_t x = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); x < 4 * a.nh * a.nq;
+         x += warps) {
+        const uint32_t qi = (uint32_t)(x / (4 * a.nh));
+        const uint64_t sidx = x - (uint64_t)qi * 4 * a.nh;
+        P *pre = static_cast<P *>(a.pre) + 8 * a.qstride * qi;
         const uint64_t h = sidx >> 2;
         const uint32_t z = (uint32_t)((sidx >> 1) & 1);
         const uint32_t d = (uint32_t)(sidx & 1);
@@ -994,8 +1007,42 @@ __global__ void __launch_bounds__(HEAVY_THREADS)
 #pragma unroll
     for (int j = 0; j < 8; j++) s_acc[j][threadIdx.x] = 0;
     unsigned ovf = 0;
-    const Query q = load_query(dq, 0);
     const KeyFmt f{a.gv.shift, a.gv.span, ST};
+    if (a.nq > 1) {
+        // several queries: over (enumerated edge, query), each count added
+        // to its query's row with a carry-checked device atomic
+        for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < a.total * a.nq;
+             x += (uint64_t)gridDim.x * blockDim.x) {
+            const uint32_t qi = (uint32_t)(x / a.total);
+            const uint64_t e = x - (uint64_t)qi * a.total;
+            const Query q = load_query(dq, qi);
+            const P *pre = static_cast<const P *>(a.pre) + 8 * a.qstride * qi;
+            const uint64_t h = find_tri(a.eoff, a.nh, e);
+            const HugeTri t = huge_tri(a, h);
+            uint32_t j = (uint32_t)(e - __ldg(a.eoff + h));
+            const uint32_t z = j >= t.A.n;
+            if (z) j -= t.A.n;
+            const GList &Z = z ? t.B : t.A;
+            const GList &O = z ? t.A : t.B;
+            const uint32_t oz = 1 - z;
+            const int64_t ke = __ldg(Z.key + Z.b + j);
+            const uint32_t de = (uint32_t)(ke & 1) ^ Z.flip;
+            auto pref = [&](uint32_t dO, int s, uint32_t c) -> unsigned long long {
+                return (unsigned long long)pre[8 * (seg_base(t, oz, dO) + c) + s];
+            };
+            auto add = [&](uint32_t dO, uint32_t dC, int pia, int pib, unsigned long long n) {
+                if (!n) return;
+                const uint32_t dA = z ? dO : de, dB = z ? de : dO;
+                const int type = type_of(z ? pib : pia, dA, dB, dC);
+                const unsigned long long old = atomicAdd(out + 8 * (size_t)qi + type, n);
+                if (old + n < old) ovf = 1;
+            };
+            phase2_edge(O, t.C, f, q, ke, pref, add);
+        }
+        if (ovf) atomicOr(flag, 1ull);
+        return;
+    }
+    const Query q = load_query(dq, 0);
     const P *pre = static_cast<const P *>(a.pre);
     const uint64_t iters = (a.total + (uint64_t)gridDim.x * blockDim.x - 1) / ((uint64_t)gridDim.x * blockDim.x);
     for (uint64_t it = 0; it < iters; it++) {  // uniform trip count (warp_flush needs full warps)
@@ -1137,6 +1184,7 @@ struct BinViews {
     const uint64_t *light_pre, *hw_pre, *hc_pre;  // {0, 32-record chunks}, {0, n_hw}, {0, n_hc}
     uint64_t n_light, n_hw, n_hc;
     HugeArgs huge;                                 // huge.nh = 0: none
+    uint32_t huge_qcap = 1;                        // queries one pass of the flat path takes
 };
 
 // One query (acc[8] + flag) or a batch of k (acc[k][8] + flag at acc[8 k])
@@ -1187,9 +1235,14 @@ void count_bins(ttc_graph *g, const BinViews &b, const int64_t *dq, uint32_t k, 
         }
     }
     if (b.huge.nh) {
-        for (uint32_t q = 0; q < k; q++) {
-            if (g->heavy_wide) run_huge<unsigned long long>(g, b.huge, dq + 3 * q, acc + 8 * (size_t)q, flag, s);
-            else run_huge<uint32_t>(g, b.huge, dq + 3 * q, acc + 8 * (size_t)q, flag, s);
+        // the flat path in passes of up to huge_qcap queries (one launch per
+        // phase each; the scratch holds that many queries' prefix entries)
+        for (uint32_t q0 = 0; q0 < k; q0 += b.huge_qcap) {
+            HugeArgs ha = b.huge;
+            ha.nq = std::min(b.huge_qcap, k - q0);
+            ha.qstride = ha.total + 4 * ha.nh;
+            if (g->heavy_wide) run_huge<unsigned long long>(g, ha, dq + 3 * (size_t)q0, acc + 8 * (size_t)q0, flag, s);
+            else run_huge<uint32_t>(g, ha, dq + 3 * (size_t)q0, acc + 8 * (size_t)q0, flag, s);
         }
     }
     if (fork) {
@@ -1210,6 +1263,7 @@ void count_graph(ttc_graph *g, const int64_t *dq, uint32_t k, unsigned long long
     b.n_hw = g->st.tau_hwarp;
     b.n_hc = g->st.tau_hcta;
     if (g->st.tau_huge) b.huge = huge_args(g, scratch);
+    b.huge_qcap = huge_pass_queries(g, k);
     count_bins(g, b, dq, k, acc, s);
 }
 
@@ -1289,9 +1343,17 @@ size_t heavy_scratch_bytes(const ttc_graph *g) {
     return g->st.tau_huge ? entries * 8 * (g->heavy_wide ? 8 : 4) : 0;
 }
 
+// Queries one batched pass of the flat path takes: all k while their prefix
+// entries fit HUGE_PASS_BYTES, else as many as do (at least one).
+uint32_t huge_pass_queries(const ttc_graph *g, uint32_t k) {
+    const size_t one = heavy_scratch_bytes(g);
+    if (k <= 1 || !one) return 1;
+    return (uint32_t)std::min<size_t>(k, std::max<size_t>(1, HUGE_PASS_BYTES / one));
+}
+
 void count_queue(ttc_graph *g, const int64_t *dq, uint32_t k, unsigned long long *acc, cudaStream_t s) {
     void *scratch = nullptr;
-    const size_t bytes = heavy_scratch_bytes(g);
+    const size_t bytes = heavy_scratch_bytes(g) * huge_pass_queries(g, k);
     if (bytes) {
         if (g->scratch.count < bytes) g->scratch.alloc(bytes, s);
         scratch = g->scratch.get();
@@ -1353,9 +1415,10 @@ void count_queue_shard(ttc_graph *g, const int64_t *dq, uint32_t k, unsigned lon
         if (g->shard_eoff.count < nh + 1) g->shard_eoff.alloc(g->st.tau_huge + 1, s);
         TTC_CUDA(cudaMemcpyAsync(g->shard_eoff.get(), eo.data(), (nh + 1) * 8, cudaMemcpyHostToDevice, s));
         TTC_CUDA(cudaStreamSynchronize(s));  // eo is about to go out of scope
-        const size_t bytes = heavy_scratch_bytes(g);
+        const size_t bytes = heavy_scratch_bytes(g) * huge_pass_queries(g, k);
         if (g->scratch.count < bytes) g->scratch.alloc(bytes, s);
         b.huge = huge_args(g, g->scratch.get());
+        b.huge_qcap = huge_pass_queries(g, k);
         b.huge.tri += lo[3];
         b.huge.eoff = g->shard_eoff.get();
         b.huge.nh = nh;

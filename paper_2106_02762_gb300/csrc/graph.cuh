@@ -158,6 +158,9 @@ void count_light_records(ttc_graph *g, const GraphView *view, const uint64_t *pr
 // caller) and the heavy-path prefix scratch of heavy_scratch_bytes(g) bytes.
 // Allocates nothing.
 size_t heavy_scratch_bytes(const ttc_graph *g);
+// Queries one batched pass of the flat heavy path takes out of k (its
+// scratch is that many times heavy_scratch_bytes(g)).
+uint32_t huge_pass_queries(const ttc_graph *g, uint32_t k);
 void count_one_into(ttc_graph *g, const int64_t *dq, unsigned long long *acc, void *scratch, cudaStream_t s);
 
 // count.cu: per-triangle counts of a strided sample of the triangle list.
