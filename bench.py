@@ -800,6 +800,9 @@ def run_ours(args):
                                 "kernels_ms": {k: v * 1e3 for k, v in kern_unb.items()}},
             "step_count": {"deltas": [list(q) for q in step_deltas], "ms": b_s * 1e3,
                            "kernels_ms": {k: v * 1e3 for k, v in kern_step.items()}},
+            "kernels_ms_note": "CUDA events around each kernel on the stream it runs on; a count runs its heavy "
+                               "bins on a side stream beside the light kernel, so their times include waiting for "
+                               "the SM slots the light kernel holds, and the query's ms is less than the sum",
             "light_threshold": {"chosen": chosen, "candidates_ms": tune_ms,
                                 "note": "ttc_tune_light: load + the step's batch at each threshold"},
             "heavy_caps": {"chosen": list(caps),
