@@ -234,7 +234,9 @@ ttc_status ttc_graph_info(const ttc_graph *g, ttc_graph_stats *s);
 ttc_status ttc_count(ttc_graph *g, const ttc_delta *d, uint64_t out[TTC_NUM_TYPES]);
 
 /* k queries in one pass over the triangles.  d[k] host array; out is a host
- * array of k * 8 counts, row q for d[q]. */
+ * array of k * 8 counts, row q for d[q].  The flat heavy path takes the
+ * queries in passes whose prefix scratch stays within 64 MB
+ * ($TTC_HUGE_PASS_BYTES, environment, replaces that cap). */
 ttc_status ttc_count_batch(ttc_graph *g, const ttc_delta *d, uint32_t k, uint64_t *out);
 
 /* One shard of ttc_count_batch, for counting one graph on several GPUs (or

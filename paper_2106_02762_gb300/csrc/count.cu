@@ -38,6 +38,7 @@
 // Deltas arrive normalised (d12, d23 <= d13 <= d12 + d23); all counts are
 // unsigned 64-bit sums with carry detection.
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -1345,10 +1346,14 @@ size_t heavy_scratch_bytes(const ttc_graph *g) {
 
 // Queries one batched pass of the flat path takes: all k while their prefix
 // entries fit HUGE_PASS_BYTES, else as many as do (at least one).
+// ($TTC_HUGE_PASS_BYTES, when set, replaces the cap.)
 uint32_t huge_pass_queries(const ttc_graph *g, uint32_t k) {
     const size_t one = heavy_scratch_bytes(g);
     if (k <= 1 || !one) return 1;
-    return (uint32_t)std::min<size_t>(k, std::max<size_t>(1, HUGE_PASS_BYTES / one));
+    const char *e = getenv("TTC_HUGE_PASS_BYTES");
+    const long long v = e ? atoll(e) : 0;
+    const size_t cap = v > 0 ? (size_t)v : HUGE_PASS_BYTES;
+    return (uint32_t)std::min<size_t>(k, std::max<size_t>(1, cap / one));
 }
 
 void count_queue(ttc_graph *g, const int64_t *dq, uint32_t k, unsigned long long *acc, cudaStream_t s) {

@@ -69,6 +69,25 @@ def test_count_multi_matches_oracle_and_replays():
         h.free()
 
 
+def test_batched_flat_path_in_passes(monkeypatch):
+    # a batch on a graph whose heavy triangles take the flat path, with the
+    # pass cap of that path set so that a pass takes one query, two queries,
+    # or all of them: every split equals the oracle
+    s, d, t = _heavy_triangle_graph()
+    g = ttc.Graph(s, d, t, light_max_pairs=1)  # every triangle on the prefix-sum path
+    assert g.info()["tau_huge"] >= 1
+    deltas = [(BIG, BIG, BIG), (2000, 900, 1500), (500, 300, 400), (3000, 3000, 0), (0, 0, 0), (9000, 100, 8900),
+              (1200, 1200, 1200)]
+    want = oracle.count(s, d, t, deltas)
+    for cap in ("1", "200000", None):  # about 96 KB of prefix entries a query here
+        if cap is None:
+            monkeypatch.delenv("TTC_HUGE_PASS_BYTES", raising=False)
+        else:
+            monkeypatch.setenv("TTC_HUGE_PASS_BYTES", cap)
+        assert (g.count_batch(deltas) == want).all(), cap
+    g.free()
+
+
 def test_count_stream_batches_within_budget():
     # the streaming many-graph count: graphs loaded from host arrays in
     # order, counted batch by batch under a device-memory budget; results
