@@ -17,7 +17,10 @@
  * Conventions shared by every entry point:
  *   - Inputs are owned by the caller and only read during the call.  Unless a
  *     flag says otherwise, pointers are host pointers; they are copied to the
- *     device before the call returns.
+ *     device before the call returns.  A load's edge arrays that are
+ *     page-locked (cudaMallocHost, cudaHostAlloc or cudaHostRegister under
+ *     the current device) are read by the load's first kernel directly, over
+ *     the host link, which also writes the device copies.
  *   - Outputs are caller-allocated and written only when the call returns
  *     TTC_OK.
  *   - A ttc_graph owns all of its device memory until ttc_free().  It is

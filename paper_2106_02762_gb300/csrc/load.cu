@@ -50,24 +50,51 @@ struct IngestStats {
     long long tmin, tmax;  // over the kept edges
 };
 
-__global__ void ingest_check_kernel(const uint32_t *src, const uint32_t *dst, const int64_t *t, size_t m,
-                                    uint8_t *keep, IngestStats *st) {
+// Validates the input edges and flags self-loops.  src/dst/t may be device
+// memory or page-locked host memory mapped into the device's address space;
+// in the second case the kernel also writes the device copies (src_copy,
+// dst_copy, t_copy non-null), so the input crosses the host link once.  Each
+// thread loads INGEST_UNROLL elements before using any, so that many reads
+// are in flight (host reads have a long latency).
+constexpr int INGEST_UNROLL = 4;
+__global__ void ingest_check_kernel(const uint32_t *__restrict__ src, const uint32_t *__restrict__ dst,
+                                    const int64_t *__restrict__ t, size_t m, uint8_t *__restrict__ keep,
+                                    IngestStats *st, uint32_t *__restrict__ src_copy, uint32_t *__restrict__ dst_copy,
+                                    int64_t *__restrict__ t_copy) {
     const int64_t TLIM = (int64_t)1 << 62;
     unsigned int my_max = 0, bad_id = 0, bad_t = 0;
     unsigned long long loops = 0;
     long long lo = LLONG_MAX, hi = LLONG_MIN;
-    GRID_STRIDE(i, m) {
-        const uint32_t a = src[i], b = dst[i];
-        const int64_t tt = t[i];
-        keep[i] = a != b;
-        loops += a == b;
-        if (a != b) {
-            lo = min(lo, (long long)tt);
-            hi = max(hi, (long long)tt);
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < m; i0 += INGEST_UNROLL * stride) {
+        uint32_t a[INGEST_UNROLL], b[INGEST_UNROLL];
+        int64_t tt[INGEST_UNROLL];
+#pragma unroll
+        for (int k = 0; k < INGEST_UNROLL; k++) {
+            const size_t i = i0 + k * stride;
+            a[k] = i < m ? src[i] : 0u;
+            b[k] = i < m ? dst[i] : 0u;
+            tt[k] = i < m ? t[i] : 0;
         }
-        my_max = max(my_max, max(a, b));
-        bad_id |= (a >> 31) | (b >> 31);
-        bad_t |= (tt < -TLIM) | (tt > TLIM);
+#pragma unroll
+        for (int k = 0; k < INGEST_UNROLL; k++) {
+            const size_t i = i0 + k * stride;
+            if (i >= m) break;
+            if (src_copy) {
+                src_copy[i] = a[k];
+                dst_copy[i] = b[k];
+                t_copy[i] = tt[k];
+            }
+            keep[i] = a[k] != b[k];
+            loops += a[k] == b[k];
+            if (a[k] != b[k]) {
+                lo = min(lo, (long long)tt[k]);
+                hi = max(hi, (long long)tt[k]);
+            }
+            my_max = max(my_max, max(a[k], b[k]));
+            bad_id |= (a[k] >> 31) | (b[k] >> 31);
+            bad_t |= (tt[k] < -TLIM) | (tt[k] > TLIM);
+        }
     }
     for (int o = 16; o; o >>= 1) {
         my_max = max(my_max, __shfl_xor_sync(0xffffffffu, my_max, o));
@@ -85,6 +112,25 @@ __global__ void ingest_check_kernel(const uint32_t *src, const uint32_t *dst, co
         if (lo != LLONG_MAX) atomicMin(&st->tmin, lo);
         if (hi != LLONG_MIN) atomicMax(&st->tmax, hi);
     }
+}
+
+// The device address of page-locked host memory (cudaMallocHost,
+// cudaHostAlloc, cudaHostRegister) allocated under the current device, which
+// kernels read directly over the host link; nullptr for pageable memory, for
+// another device's allocation, or when p is not aligned to `align` bytes.
+const void *mapped_host(const void *p, size_t align) {
+    if (!p || reinterpret_cast<uintptr_t>(p) % align) return nullptr;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();  // the failed query leaves a (non-sticky) error behind
+        return nullptr;
+    }
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost && a.device == dev ? a.devicePointer : nullptr;
 }
 
 // kept edges in input order: eidx = original index, tk = timestamp
@@ -2099,11 +2145,28 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
     DevBuf<int64_t> t_buf;
     const uint32_t *src = src_in, *dst = dst_in;
     const int64_t *t = t_in;
+    // what the ingest kernel reads, and where it writes the device copies
+    // (page-locked host input only)
+    const uint32_t *in_src = src_in, *in_dst = dst_in;
+    const int64_t *in_t = t_in;
+    uint32_t *copy_src = nullptr, *copy_dst = nullptr;
+    int64_t *copy_t = nullptr;
     if (!(opt.flags & TTC_LOAD_DEVICE_INPUT) && m0) {
         src_buf.alloc(m0, s); dst_buf.alloc(m0, s); t_buf.alloc(m0, s);
-        TTC_CUDA(cudaMemcpyAsync(src_buf.get(), src_in, m0 * 4, cudaMemcpyHostToDevice, s));
-        TTC_CUDA(cudaMemcpyAsync(dst_buf.get(), dst_in, m0 * 4, cudaMemcpyHostToDevice, s));
-        TTC_CUDA(cudaMemcpyAsync(t_buf.get(), t_in, m0 * 8, cudaMemcpyHostToDevice, s));
+        const void *hs = mapped_host(src_in, 4);
+        const void *hd = mapped_host(dst_in, 4);
+        const void *ht = mapped_host(t_in, 8);
+        if (hs && hd && ht) {
+            in_src = static_cast<const uint32_t *>(hs);
+            in_dst = static_cast<const uint32_t *>(hd);
+            in_t = static_cast<const int64_t *>(ht);
+            copy_src = src_buf.get(); copy_dst = dst_buf.get(); copy_t = t_buf.get();
+        } else {
+            TTC_CUDA(cudaMemcpyAsync(src_buf.get(), src_in, m0 * 4, cudaMemcpyHostToDevice, s));
+            TTC_CUDA(cudaMemcpyAsync(dst_buf.get(), dst_in, m0 * 4, cudaMemcpyHostToDevice, s));
+            TTC_CUDA(cudaMemcpyAsync(t_buf.get(), t_in, m0 * 8, cudaMemcpyHostToDevice, s));
+            in_src = src_buf.get(); in_dst = dst_buf.get(); in_t = t_buf.get();
+        }
         src = src_buf.get(); dst = dst_buf.get(); t = t_buf.get();
     }
     DevBuf<IngestStats> ist(1, s);
@@ -2115,7 +2178,8 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
     }
     DevBuf<uint8_t> keep(m0 + 1, s);
     if (m0) {
-        ingest_check_kernel<<<grid_for(m0), TPB, 0, s>>>(src, dst, t, m0, keep.get(), ist.get());
+        ingest_check_kernel<<<grid_for(m0), TPB, 0, s>>>(in_src, in_dst, in_t, m0, keep.get(), ist.get(), copy_src,
+                                                        copy_dst, copy_t);
         TTC_LAUNCH_CHECK();
     }
     const IngestStats is = read_scalar(ist.get(), s);

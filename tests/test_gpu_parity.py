@@ -351,6 +351,56 @@ def test_device_input_tensors():
     assert (out.cpu().numpy().astype(np.uint64) == want).all()
 
 
+def test_page_locked_host_input():
+    """Page-locked host arrays are read by the ingest kernel itself, over the
+    host link, which also writes the device copies; pageable arrays are
+    copied first.  Every form loads the same graph: a scaled power-law graph
+    with self-loops mixed in (so the kept edges are compacted) and a length
+    that fills no whole round of the ingest's grid."""
+    import torch
+    s, d, t = synth.large_plain(scale=0.004)
+    rng = np.random.default_rng(17)
+    k = 1001
+    loops = rng.integers(0, int(s.max()) + 1, size=k).astype(np.uint32)
+    s = np.concatenate([s, loops])
+    d = np.concatenate([d, loops])
+    t = np.concatenate([t, rng.integers(0, 1 << 30, size=k).astype(np.int64)])
+    perm = rng.permutation(s.size)
+    s, d, t = s[perm], d[perm], t[perm]
+    deltas = [synth.LARGE_PLAIN_DELTA, synth.LARGE_PLAIN_DELTA_UNBOUNDED]
+    want = oracle.count(s, d, t, deltas)
+
+    def pinned(a):
+        h = torch.from_numpy(a.view(np.int32) if a.dtype == np.uint32 else a).pin_memory()
+        return h, (h.numpy().view(np.uint32) if a.dtype == np.uint32 else h.numpy())
+
+    (hs, ps), (hd, pd), (ht, pt) = pinned(s), pinned(d), pinned(t)
+    dev = tuple(torch.from_numpy(a.view(np.int32) if a.dtype == np.uint32 else a).cuda() for a in (s, d, t))
+    keys = ("m", "m_self_loops", "m_s", "tau", "kappa", "sigma_max", "work_bytes", "tau_light")
+    infos = []
+    for form in ((ps, pd, pt), (ps, pd, t), (s, d, t), dev):
+        g = ttc.Graph(*form)
+        try:
+            assert (g.count_batch(deltas) == want).all()
+            infos.append({key: g.info()[key] for key in keys})
+        finally:
+            g.free()
+    assert infos[0]["m_self_loops"] == k
+    assert all(i == infos[0] for i in infos)
+
+    # the direct read still rejects out-of-range ids and timestamps
+    bad = ps.copy()
+    hb = torch.from_numpy(bad.view(np.int32)).pin_memory()
+    hb[7] = -1  # id 2^32 - 1
+    with pytest.raises(ttc.TTCError, match="RANGE"):
+        ttc.Graph(hb.numpy().view(np.uint32), pd, pt)
+    tb = torch.from_numpy(t.copy()).pin_memory()
+    tb[11] = (1 << 62) + 1
+    with pytest.raises(ttc.TTCError, match="RANGE"):
+        ttc.Graph(ps, pd, tb.numpy())
+    del hs, hd, ht
+
+
 def test_invalid_inputs_rejected():
     s, d, t = _edges([(0, 1, 0), (1, 2, 1), (0, 2, 2)])
     with pytest.raises(ttc.TTCError, match="RANGE"):
