@@ -293,9 +293,10 @@ ttc_status ttc_count_multi(ttc_graph *const *g, const ttc_delta *d, uint32_t G, 
  * (0: half of the device memory free at the call), else the batch is counted
  * by one ttc_count_multi launch and freed first.  So device memory holds at
  * most one batch plus the graph being loaded; a graph larger than the budget
- * forms a batch of its own.  out: G * 8 counts (host); *batches (may be
- * NULL) receives the number of batches.  On an error the graphs loaded so
- * far are freed. */
+ * forms a batch of its own.  A load that fails with TTC_ERR_NOMEM while a
+ * batch is resident is tried once more after that batch is counted and
+ * freed.  out: G * 8 counts (host); *batches (may be NULL) receives the
+ * number of batches.  On an error the graphs loaded so far are freed. */
 ttc_status ttc_count_stream(const uint32_t *const *src, const uint32_t *const *dst, const int64_t *const *t,
                             const uint64_t *m, const ttc_delta *d, uint32_t G, const ttc_load_opts *opts,
                             uint64_t budget_bytes, uint64_t *out, uint32_t *batches);

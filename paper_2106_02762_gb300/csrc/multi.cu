@@ -555,6 +555,15 @@ extern "C" ttc_status ttc_count_stream(const uint32_t *const *src, const uint32_
     for (uint32_t i = 0; i < G; i++) {
         ttc_graph *g = nullptr;
         ttc_status rc = ttc_load_ex(src[i], dst[i], t[i], m[i], opts, &g);
+        if (rc == TTC_ERR_NOMEM && !batch.empty()) {
+            // the resident batch may be what left too little room: count and
+            // free it, then load the graph again into the memory it held
+            rc = flush();
+            if (rc != TTC_OK) return rc;
+            first = i;
+            bytes = 0;
+            rc = ttc_load_ex(src[i], dst[i], t[i], m[i], opts, &g);
+        }
         if (rc != TTC_OK) {
             release();
             return rc;

@@ -121,6 +121,41 @@ def test_count_stream_batches_within_budget():
         ttc.count_stream(edges, deltas[:-1])
 
 
+def test_count_stream_retries_a_load_after_freeing_the_batch():
+    # A load that runs out of device memory while a batch is resident is
+    # tried again once that batch is counted and freed.  The injected failure
+    # (the n-th device allocation of the call) lands in turn in the first
+    # graph's load (an error: no batch to free), a later graph's load (the
+    # retry: one batch more, same counts) and the count (an error); every
+    # outcome leaves no device memory behind.
+    import torch
+    gs = _small_graphs(count=3)
+    edges = [(s, d, t) for s, d, t, _ in gs]
+    deltas = [q for *_, q in gs]
+    want = np.stack([oracle.count(s, d, t, [q])[0] for s, d, t, q in gs])
+    got, nb = ttc.count_stream(edges, deltas)
+    assert (got == want).all() and nb == 1
+    torch.cuda.synchronize()
+    used0 = ttc.memory_info()["pool_used"]
+    outcomes = set()
+    for n in range(1, 5000):
+        ttc.debug_fail_alloc_after(n)
+        try:
+            got, nb = ttc.count_stream(edges, deltas)
+            outcomes.add(nb)
+            assert (got == want).all()
+        except ttc.TTCError as e:
+            assert e.status == -3
+            outcomes.add("error")
+        finally:
+            ttc.debug_fail_alloc_after(0)
+        torch.cuda.synchronize()
+        assert ttc.memory_info()["pool_used"] == used0, n
+        if 1 in outcomes:  # n is past the call's last allocation
+            break
+    assert outcomes == {"error", 1, 2}
+
+
 @pytest.mark.slow
 def test_many_graph_workload_sample_matches_oracle():
     # a seeded sample of 64 of the 4096 graphs of the many-graphs workload
