@@ -518,7 +518,7 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "light_kernel_dram_unbounded_power
 def light_traffic(ttc):
     """DRAM bytes (read + write) of one light-kernel launch on the full
     power-law workload, from the one-pass ncu capture summarised in
-    profiles/; None when that capture was taken on other count-kernel source
+    profiles/; None when that capture was taken on other light-kernel source
     than the library built here (the version string carries its hash)."""
     try:
         fields = dict(line.split(":", 1) for line in open(TRAFFIC_FILE) if ":" in line)
@@ -591,14 +591,15 @@ def run_ours(args):
     # the light threshold, tuned on this graph (rank 0; every rank then loads
     # with the same explicit value, so all hold the same bins)
     chosen, tune_ms = 0, None
-    caps, caps_ms = (0, 0), None
+    caps, caps_ms = (0, 0, 0), None
     if rank == 0:
         chosen, tune_ms = ttc.tune_light(d_src, d_dst, d_t, step_deltas, stream=sptr)
-        # then the prefix-sum path's class caps at that threshold
+        # then the prefix-sum path's class caps and the one-CTA class's search
+        # form at that threshold
         caps, caps_ms = ttc.tune_heavy(d_src, d_dst, d_t, step_deltas, light_max_pairs=chosen, stream=sptr)
     chosen = int(allreduce_max(float(chosen), ws, dev))
-    caps = (int(allreduce_max(float(caps[0]), ws, dev)), int(allreduce_max(float(caps[1]), ws, dev)))
-    bins = dict(light_max_pairs=chosen, heavy_warp_cap=caps[0], heavy_cta_cap=caps[1])
+    caps = tuple(int(allreduce_max(float(x), ws, dev)) for x in caps)
+    bins = dict(light_max_pairs=chosen, heavy_warp_cap=caps[0], heavy_cta_cap=caps[1], heavy_merge=caps[2])
 
     # on N GPUs every rank loads the same graph and counts its shard of the
     # triangle list; the ranks' counts are summed (the one exchange)
@@ -806,9 +807,11 @@ def run_ours(args):
             "light_threshold": {"chosen": chosen, "candidates_ms": tune_ms,
                                 "note": "ttc_tune_light: load + the step's batch at each threshold"},
             "heavy_caps": {"chosen": list(caps),
-                           "candidates_ms": {"%d/%d" % wc: v for wc, v in caps_ms.items()} if caps_ms else None,
+                           "candidates_ms": {"%d/%d/%s" % (w, c, "merge" if mg == ttc.HEAVY_MERGE else "binary"): v
+                                             for (w, c, mg), v in caps_ms.items()} if caps_ms else None,
                            "note": "ttc_tune_heavy at the chosen light threshold: the prefix-sum path's "
-                                   "one-warp and one-CTA caps (edges of A plus B)"},
+                                   "one-warp and one-CTA caps (edges of A plus B) and the one-CTA class's "
+                                   "search form (1 binary, 2 two-pointer)"},
             "load_ms": load_s * 1e3,
             "load_edges_per_s": m / load_s,
             "load_phases_ms": {"wall": load_wall * 1e3, **load_phases},

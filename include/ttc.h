@@ -119,6 +119,17 @@ typedef enum {
 #define TTC_LABEL_HEAVIEST_VW 0u  /* default */
 #define TTC_LABEL_SOURCE 1u       /* the paper's labelling */
 
+/* How the one-CTA class of the prefix-sum path finds the window ends of
+ * Algs. 2-4 (this library's choice; both give identical counts). */
+#define TTC_HEAVY_BINARY 1u  /* a binary search per bound and enumerated edge (default) */
+#define TTC_HEAVY_MERGE 2u   /* the two-pointer form: along a key-sorted list every
+                                bound only grows, so a thread takes a run of
+                                consecutive edges, binary-searches the first and
+                                steps forward from there for the rest; used for the
+                                triangles whose C list is staged in shared memory and
+                                holds at most sigma_A + sigma_B edges, binary
+                                searches elsewhere (and in the many-graph launch) */
+
 typedef struct {
     uint32_t flags;            /* TTC_LOAD_* */
     uint32_t orientation;      /* TTC_ORIENT_* */
@@ -140,6 +151,8 @@ typedef struct {
                                   else the capacity (2048, 1024 when a pair holds
                                   2^16 edges or more); clamped to
                                   [heavy_warp_cap, capacity] */
+    uint32_t heavy_merge;      /* TTC_HEAVY_BINARY or TTC_HEAVY_MERGE; 0 = tuned
+                                  (ttc_tune_heavy), else TTC_HEAVY_BINARY */
     uint64_t seed;             /* TTC_ORIENT_RANDOM permutation seed */
     void *stream;              /* cudaStream_t to adopt; NULL = create one */
 } ttc_load_opts;
@@ -169,6 +182,7 @@ typedef struct {
     uint32_t light_max_pairs; /* the light threshold the load used (given, tuned or default) */
     uint32_t heavy_warp_cap;  /* the one-warp class's cap the load used (edges of A plus B) */
     uint32_t heavy_cta_cap;   /* the one-CTA class's cap the load used */
+    uint32_t heavy_merge;     /* the one-CTA class's search form (TTC_HEAVY_*) */
 } ttc_graph_stats;
 
 /* Build the device-resident graph (Alg. 1 steps up to the triangle list:
@@ -200,23 +214,28 @@ ttc_status ttc_tune_light(const uint32_t *src, const uint32_t *dst, const int64_
                           float *ms);
 
 /* Tuning of the prefix-sum path's split into its three classes (one warp,
- * one CTA, flat; this library's, not the paper's) at the light threshold
- * opts->light_max_pairs (0: tuned or default).  Loads the graph once per
- * (warp cap, CTA cap) pair of ttc_tune_heavy_candidates (capped as in
- * ttc_load_opts), times load plus one ttc_count_batch of the k probe
- * queries (the fastest of three timed runs after an untimed one), and keeps
- * the fastest, the first candidate (the kernels' capacities) unless another
- * is more than 1% faster: *warp_cap and *cta_cap receive the caps the loads
- * used, ms (may be NULL) the time of each candidate.  With no prefix-sum-path triangle it stops after the
- * first.  The choice is cached like the light threshold's (per shape, SM
- * count and light threshold); ttc_load_ex with both caps 0 then uses it.
- * opts->heavy_warp_cap and opts->heavy_cta_cap must be 0. */
-#define TTC_TUNE_HEAVY_CANDIDATES 6
-static const uint32_t ttc_tune_heavy_candidates[TTC_TUNE_HEAVY_CANDIDATES][2] = {
-    {128, 2048}, {64, 2048}, {32, 2048}, {128, 1024}, {64, 1024}, {128, 512}};
+ * one CTA, flat; this library's, not the paper's) and of the one-CTA class's
+ * search form, at the light threshold opts->light_max_pairs (0: tuned or
+ * default).  Loads the graph once per (warp cap, CTA cap, search form) of
+ * ttc_tune_heavy_candidates (caps capped as in ttc_load_opts), times load
+ * plus one ttc_count_batch of the k probe queries (the fastest of three
+ * timed runs after an untimed one), and keeps the fastest, the first
+ * candidate (the kernels' capacities, binary searches) unless another is
+ * more than 1% faster: *warp_cap, *cta_cap and *merge receive what the loads
+ * used, ms (may be NULL) the time of each candidate.  With no
+ * prefix-sum-path triangle it stops after the first.  The choice is cached
+ * like the light threshold's (per shape, SM count and light threshold);
+ * ttc_load_ex with both caps 0 then uses the caps, with heavy_merge 0 the
+ * search form.  opts->heavy_warp_cap, opts->heavy_cta_cap and
+ * opts->heavy_merge must be 0. */
+#define TTC_TUNE_HEAVY_CANDIDATES 8
+static const uint32_t ttc_tune_heavy_candidates[TTC_TUNE_HEAVY_CANDIDATES][3] = {
+    {128, 2048, TTC_HEAVY_BINARY}, {64, 2048, TTC_HEAVY_BINARY},  {32, 2048, TTC_HEAVY_BINARY},
+    {128, 1024, TTC_HEAVY_BINARY}, {64, 1024, TTC_HEAVY_BINARY},  {128, 512, TTC_HEAVY_BINARY},
+    {128, 2048, TTC_HEAVY_MERGE},  {64, 2048, TTC_HEAVY_MERGE}};
 ttc_status ttc_tune_heavy(const uint32_t *src, const uint32_t *dst, const int64_t *t, uint64_t m,
                           const ttc_load_opts *opts, const ttc_delta *probe, uint32_t k, uint32_t *warp_cap,
-                          uint32_t *cta_cap, float *ms);
+                          uint32_t *cta_cap, uint32_t *merge, float *ms);
 
 /* Release a graph and all of its device memory.  NULL is a no-op. */
 void ttc_free(ttc_graph *g);

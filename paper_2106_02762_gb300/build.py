@@ -36,15 +36,34 @@ def _headers():
     return max((os.path.getmtime(h) for h in hs), default=0.0)
 
 
-def count_source_hash() -> str:
-    """Short hash of the count kernels' source (csrc/count.cu, csrc/count_dev.cuh
-    and the shared headers); profiles taken with ncu record it, so a stale
-    profile can be told from a current one."""
+# The light kernel's sources: count.cu up to its heavy-bin section (the file's
+# head and the light bin), graph.cuh up to the host-side graph handle (the
+# key format, TriRec and GraphView, which the kernels read), and the device
+# helpers in full.
+_LIGHT_SOURCES = [("count.cu", "// ---------------------------------------------------------------- heavy: per-edge math"),
+                  ("count_dev.cuh", None), ("graph.cuh", "struct ttc_graph {"), ("common.cuh", None)]
+
+
+def count_source_hash(read=None) -> str:
+    """Short hash of the light count kernel's source (the parts listed in
+    _LIGHT_SOURCES); the ncu profile of that kernel records it, so a stale
+    profile can be told from a current one while changes elsewhere (the
+    heavy bins, host code) leave it valid.  read(name) -> bytes overrides the
+    source files (to hash another revision)."""
     import hashlib
     h = hashlib.sha1()
-    for f in ["count.cu", "count_dev.cuh", "graph.cuh", "common.cuh"]:
-        with open(os.path.join(CSRC, f), "rb") as fh:
-            h.update(fh.read())
+    for f, stop in _LIGHT_SOURCES:
+        if read is not None:
+            data = read(f)
+        else:
+            with open(os.path.join(CSRC, f), "rb") as fh:
+                data = fh.read()
+        if stop is not None:
+            cut = data.find(stop.encode())
+            if cut < 0:
+                raise RuntimeError("%s: marker %r not found" % (f, stop))
+            data = data[:cut]
+        h.update(data)
     return h.hexdigest()[:12]
 
 

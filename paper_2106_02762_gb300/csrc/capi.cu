@@ -385,7 +385,9 @@ ttc_status ttc_load_ex(const uint32_t *src, const uint32_t *dst, const int64_t *
         lo.light_max_pairs = opts->light_max_pairs;
         lo.heavy_warp_cap = opts->heavy_warp_cap;
         lo.heavy_cta_cap = opts->heavy_cta_cap;
+        lo.heavy_merge = opts->heavy_merge;
         lo.seed = opts->seed;
+        if (lo.heavy_merge > TTC_HEAVY_MERGE) fail(TTC_ERR_INVALID, "unknown heavy_merge %u", lo.heavy_merge);
         if (lo.flags & ~(TTC_LOAD_DEVICE_INPUT | TTC_LOAD_PROFILE | TTC_LOAD_STREAM | TTC_LOAD_STRICT_TIME))
             fail(TTC_ERR_INVALID, "unknown load flags 0x%x", lo.flags);
     }

@@ -321,17 +321,57 @@ __global__ void __launch_bounds__(LIGHT_THREADS, 4)
 }
 
 // ---------------------------------------------------------------- heavy: per-edge math
+// Searches of the two phases, binary or two-pointer.  Along one enumerated
+// list in key order every bound the phases look up in C or in the other
+// list is a non-decreasing function of the edge's time or key (t_e plus a
+// constant window end, or the key itself), so each answer #{keys < bound}
+// only moves forward from one edge to the next.  The two-pointer form gives
+// a thread a contiguous run of edges of one list: the first edge's bounds
+// are binary-searched, every later edge's are found by stepping forward from
+// the previous answers.  The answers are the same either way, so the prefix
+// sums of Algs. 2-4 read at them are too.
+template <int N>
+struct Cursor {
+    uint32_t pos[N];
+    bool valid;  // pos holds the answers for the previous edge of the same list
+};
+
+__device__ __forceinline__ int64_t list_key(const SList &l, uint32_t i) { return l.key[i]; }
+__device__ __forceinline__ int64_t list_key(const GList &l, uint32_t i) { return __ldg(l.key + l.b + i); }
+
+// res[i] = #{keys < bd[i]} in l; with a cursor, stepped forward from its
+// answers when it holds some (the bounds must not be below the previous
+// ones), and left holding these answers.
+template <int N, typename L>
+__device__ __forceinline__ void find_n(const L &l, const int64_t (&bd)[N], uint32_t (&res)[N], Cursor<N> *cur) {
+    if (cur && cur->valid) {
+#pragma unroll
+        for (int i = 0; i < N; i++) {
+            uint32_t p = cur->pos[i];
+            while (p < l.n && list_key(l, p) < bd[i]) p++;
+            res[i] = p;
+        }
+    } else {
+        search_n<N>(l, bd, res);
+    }
+    if (cur) {
+#pragma unroll
+        for (int i = 0; i < N; i++) cur->pos[i] = res[i];
+        cur->valid = true;
+    }
+}
+
 // Phase 1 for an enumerated edge e (key ke): the values h, L, R, M against C,
 // each split by C's direction: out[2 s + dC].
 template <typename CL>
 __device__ __forceinline__ void phase1_values(const CL &C, const KeyFmt &f, const Query &q, int64_t ke,
-                                              uint32_t out[8]) {
+                                              uint32_t out[8], Cursor<4> *cur = nullptr) {
     const int64_t re = ke >> f.shift;
     // L(e): C's edges before e, by key or (strict) by time
     const int64_t bd[4] = {le_bound(f, re + q.d13), f.strict ? lt_bound(f, re) : key_bound(ke),
                            lt_bound(f, re - q.d23), lt_bound(f, re - q.d13)};
     uint32_t ps[4];
-    search_n<4>(C, bd, ps);
+    find_n<4>(C, bd, ps, cur);
     const uint32_t ph = ps[0], pl = ps[1], pr = ps[2], pm = ps[3];
     const uint32_t h0 = C.d0(ph), l0 = C.d0(pl), r0 = C.d0(pr), m0 = C.d0(pm);
     out[0] = h0; out[1] = ph - h0;
@@ -345,11 +385,11 @@ __device__ __forceinline__ void phase1_values(const CL &C, const KeyFmt &f, cons
 // search only h, R and M for the others (slots 2 and 3 of out untouched).
 template <typename CL>
 __device__ __forceinline__ void phase1_values_hrm(const CL &C, const KeyFmt &f, const Query &q, int64_t ke,
-                                                  uint32_t out[8]) {
+                                                  uint32_t out[8], Cursor<3> *cur = nullptr) {
     const int64_t re = ke >> f.shift;
     const int64_t bd[3] = {le_bound(f, re + q.d13), lt_bound(f, re - q.d23), lt_bound(f, re - q.d13)};
     uint32_t ps[3];
-    search_n<3>(C, bd, ps);
+    find_n<3>(C, bd, ps, cur);
     const uint32_t ph = ps[0], pr = ps[1], pm = ps[2];
     const uint32_t h0 = C.d0(ph), r0 = C.d0(pr), m0 = C.d0(pm);
     out[0] = h0; out[1] = ph - h0;
@@ -360,9 +400,10 @@ __device__ __forceinline__ void phase1_values_hrm(const CL &C, const KeyFmt &f, 
 // Phase 2 for an enumerated edge e with O the other enumerated list.
 // pref(dO, s, c) = prefix over O's own-direction-dO edges, first c of them,
 // of phase-1 slot s.  add(dO, dC, pi if e is on A, pi if e is on B, n).
+// cc, co: cursors of the two-pointer form for the searches in C and in O.
 template <typename OL, typename CL, typename PF, typename ADD>
 __device__ __forceinline__ void phase2_edge(const OL &O, const CL &C, const KeyFmt &f, const Query &q, int64_t ke,
-                                            PF &&pref, ADD &&add) {
+                                            PF &&pref, ADD &&add, Cursor<4> *cc = nullptr, Cursor<8> *co = nullptr) {
     const int64_t re = ke >> f.shift;
     // searches in C (split by C's direction).  C's edges not after e (Ka)
     // and before e (Kb): the same key position, or (strict) those with
@@ -370,7 +411,7 @@ __device__ __forceinline__ void phase2_edge(const OL &O, const CL &C, const KeyF
     const int64_t bc[4] = {f.strict ? le_bound(f, re) : key_bound(ke), le_bound(f, re + q.d23),
                            le_bound(f, re + q.d12), lt_bound(f, re - q.d12)};
     uint32_t pc[4];
-    search_n<4>(C, bc, pc);
+    find_n<4>(C, bc, pc, cc);
     const uint32_t posCa = pc[0], pH = pc[1], pG = pc[2], pLo = pc[3];
     const uint32_t posCb = f.strict ? C.below(lt_bound(f, re)) : posCa;
     const uint32_t Ka0 = C.d0(posCa), H0 = C.d0(pH), G0 = C.d0(pG), Lo0 = C.d0(pLo);
@@ -387,7 +428,7 @@ __device__ __forceinline__ void phase2_edge(const OL &O, const CL &C, const KeyF
                            le_bound(f, re + q.d13 - q.d12),
                            le_bound(f, re + q.d23)};
     uint32_t po[8];
-    search_n<8>(O, bo, po);
+    find_n<8>(O, bo, po, co);
     // O's edges before e end at posOb, those after e start at posOa: one
     // key position, or (strict) t < t_e and t <= t_e
     const uint32_t posOa = po[0], posOb = f.strict ? O.below(lt_bound(f, re)) : posOa;
@@ -492,12 +533,14 @@ __device__ __forceinline__ uint32_t block_excl_scan_u32(uint32_t v, uint32_t *tm
 
 // One CTA per heavy triangle of the CTA class, over a table of graphs.  MODE
 // as light_kernel; heavy_pre[g] = first CTA-class record of graph g in the
-// global index space (G + 1 entries).
+// global index space (G + 1 entries).  merge: take the two-pointer form for
+// the triangles whose C is staged and holds at most as many edges as A and B
+// together (the bounds then move little from one edge to the next).
 template <typename P, int MODE, bool ST>
 __global__ void __launch_bounds__(HEAVY_THREADS)
     heavy_fused_kernel(const GraphView *__restrict__ gvs, const uint64_t *__restrict__ heavy_pre, uint32_t G,
                        const int64_t *dq, uint32_t nq, unsigned long long *out, unsigned long long *flag,
-                       const uint64_t *idx, uint64_t nidx) {
+                       const uint64_t *idx, uint64_t nidx, uint32_t merge) {
     using Cap = FusedCap<P>;
     constexpr uint32_t CAP = Cap::CAP, ES = Cap::ES;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -608,12 +651,21 @@ __global__ void __launch_bounds__(HEAVY_THREADS)
         // first prefix entry of each own-direction segment: A0, A1, B0, B1
         const uint32_t sbase[4] = {0, a0 + 1, na + 2, na + 2 + b0 + 1};
         const uint32_t slen[4] = {a0, na - a0, b0, nb - b0};
+        // the two-pointer form (block-uniform): each thread takes its
+        // contiguous run beg .. end of A ++ B; otherwise the edges are dealt
+        // out thread-strided and every bound is binary-searched
+        const bool walk = merge && c_staged && C.n <= ne;
+        const uint32_t e_first = walk ? beg : threadIdx.x, e_last = walk ? end : ne;
+        const uint32_t e_step = walk ? 1u : (uint32_t)HEAVY_THREADS;
         for (uint32_t q = 0; q < (MODE == 1 ? nq : 1u); q++) {
             const Query Q = load_query(dq, MODE == 0 ? g : q);
             // phase 1 (and the zero entry of each segment)
             if (threadIdx.x < 32) s_pre[(threadIdx.x >> 2) * ES + sbase[threadIdx.x & 3]] = 0;
-            for (uint32_t e = threadIdx.x; e < ne; e += HEAVY_THREADS) {
+            Cursor<4> c1{};
+            Cursor<3> c1h{};
+            for (uint32_t e = e_first; e < e_last; e += e_step) {
                 const uint32_t z = e >= na;
+                if (e == na) c1.valid = c1h.valid = false;  // B's list: its bounds start over
                 const uint32_t j = z ? e - na : e;
                 const int64_t ke = key_at(e);
                 const uint32_t de = (uint32_t)(ke & 1) ^ (z ? B.flip : A.flip);
@@ -622,12 +674,12 @@ __global__ void __launch_bounds__(HEAVY_THREADS)
                 uint32_t v[8];
                 const uint32_t at = sbase[2 * z + de] + rank + 1;
                 if (q == 0) {
-                    if (c_staged) phase1_values(Cs, f, Q, ke, v);
+                    if (c_staged) phase1_values(Cs, f, Q, ke, v, walk ? &c1 : nullptr);
                     else phase1_values(C, f, Q, ke, v);
 #pragma unroll
                     for (int s = 0; s < 8; s++) s_pre[s * ES + at] = v[s];
                 } else {  // L(e) and its prefix sums are the first query's
-                    if (c_staged) phase1_values_hrm(Cs, f, Q, ke, v);
+                    if (c_staged) phase1_values_hrm(Cs, f, Q, ke, v, walk ? &c1h : nullptr);
                     else phase1_values_hrm(C, f, Q, ke, v);
 #pragma unroll
                     for (int s = 0; s < 8; s++)
@@ -657,8 +709,11 @@ __global__ void __launch_bounds__(HEAVY_THREADS)
             }
             __syncthreads();
             // phase 2
-            for (uint32_t e = threadIdx.x; e < ne; e += HEAVY_THREADS) {
+            Cursor<4> cc{};
+            Cursor<8> co{};
+            for (uint32_t e = e_first; e < e_last; e += e_step) {
                 const uint32_t z = e >= na;
+                if (e == na) cc.valid = co.valid = false;  // e moves to B, O to A: bounds start over
                 const int64_t ke = key_at(e);
                 const uint32_t de = (uint32_t)(ke & 1) ^ (z ? B.flip : A.flip);
                 // O = the other list, staged: keys and its own dir-0 prefix
@@ -675,7 +730,7 @@ __global__ void __launch_bounds__(HEAVY_THREADS)
                     else if constexpr (MODE == 1) shared_add(&s_tail[q * 8 + type], n, ovf);
                     else atomicAdd(out + 8 * h + type, n);
                 };
-                if (c_staged) phase2_edge(O, Cs, f, Q, ke, pref, add);
+                if (c_staged) phase2_edge(O, Cs, f, Q, ke, pref, add, walk ? &cc : nullptr, walk ? &co : nullptr);
                 else phase2_edge(O, C, f, Q, ke, pref, add);
             }
             __syncthreads();
@@ -1123,10 +1178,10 @@ unsigned heavy_grid(uint64_t items, int per_sm = 2) {
 template <typename P, int MODE, bool ST>
 void launch_fused(const GraphView *gvs, const uint64_t *heavy_pre, uint32_t G, uint64_t items, const int64_t *dq,
                   uint32_t nq, unsigned long long *out, unsigned long long *flag, const uint64_t *idx,
-                  uint64_t nidx, cudaStream_t s, int per_sm = 2) {
+                  uint64_t nidx, cudaStream_t s, int per_sm, uint32_t merge) {
     ensure_smem((const void *)heavy_fused_kernel<P, MODE, ST>, FusedCap<P>::bytes(1, MAX_BATCH_SMEM_Q));
     heavy_fused_kernel<P, MODE, ST><<<heavy_grid(items, per_sm), HEAVY_THREADS, FusedCap<P>::bytes(MODE, nq), s>>>(
-        gvs, heavy_pre, G, dq, nq, out, flag, idx, nidx);
+        gvs, heavy_pre, G, dq, nq, out, flag, idx, nidx, merge);
     TTC_LAUNCH_CHECK();
 }
 
@@ -1143,8 +1198,11 @@ void launch_warp(const GraphView *gvs, const uint64_t *hw_pre, uint32_t G, uint6
     TTC_LAUNCH_CHECK();
 }
 
-// kind: bit 0 = 64-bit prefix sums (wide lists), bit 1 = strict time order
-inline int heavy_kind(int wide, bool strict) { return (wide ? 1 : 0) | (strict ? 2 : 0); }
+// kind: bit 0 = 64-bit prefix sums (wide lists), bit 1 = strict time order,
+// bit 2 = the one-CTA class takes the two-pointer form where it applies
+inline int heavy_kind(int wide, bool strict, bool merge = false) {
+    return (wide ? 1 : 0) | (strict ? 2 : 0) | (merge ? 4 : 0);
+}
 
 template <int MODE>
 void launch_warp_any(int kind, const GraphView *gvs, const uint64_t *hw_pre, uint32_t G, uint64_t items,
@@ -1164,15 +1222,16 @@ template <int MODE>
 void launch_fused_any(int kind, const GraphView *gvs, const uint64_t *heavy_pre, uint32_t G, uint64_t items,
                       const int64_t *dq, uint32_t nq, unsigned long long *out, unsigned long long *flag,
                       const uint64_t *idx, uint64_t nidx, cudaStream_t s, int per_sm = 2) {
+    const uint32_t merge = (kind & 4) ? 1u : 0u;
     switch (kind & 3) {
-        case 0: launch_fused<uint32_t, MODE, false>(gvs, heavy_pre, G, items, dq, nq, out, flag, idx, nidx, s, per_sm);
-            break;
+        case 0: launch_fused<uint32_t, MODE, false>(gvs, heavy_pre, G, items, dq, nq, out, flag, idx, nidx, s, per_sm,
+                                                    merge); break;
         case 1: launch_fused<unsigned long long, MODE, false>(gvs, heavy_pre, G, items, dq, nq, out, flag, idx, nidx, s,
-                                                              per_sm); break;
-        case 2: launch_fused<uint32_t, MODE, true>(gvs, heavy_pre, G, items, dq, nq, out, flag, idx, nidx, s, per_sm);
-            break;
+                                                              per_sm, merge); break;
+        case 2: launch_fused<uint32_t, MODE, true>(gvs, heavy_pre, G, items, dq, nq, out, flag, idx, nidx, s, per_sm,
+                                                   merge); break;
         default: launch_fused<unsigned long long, MODE, true>(gvs, heavy_pre, G, items, dq, nq, out, flag, idx, nidx, s,
-                                                              per_sm);
+                                                              per_sm, merge);
     }
 }
 
@@ -1228,10 +1287,10 @@ void count_bins(ttc_graph *g, const BinViews &b, const int64_t *dq, uint32_t k, 
         }
         if (nc) {
             prof_begin(g, s, mode ? "heavy_cta_batch" : "heavy_cta");
-            if (mode) launch_fused_any<1>(heavy_kind(g->heavy_wide, g->strict), b.hc_view, b.hc_pre, 1, nc,
-                                          dq + 3 * (size_t)q0, nq, acc + 8 * (size_t)q0, flag, nullptr, 0, s);
-            else launch_fused_any<0>(heavy_kind(g->heavy_wide, g->strict), b.hc_view, b.hc_pre, 1, nc, dq, 1, acc,
-                                     flag, nullptr, 0, s);
+            const int kc = heavy_kind(g->heavy_wide, g->strict, g->st.heavy_merge == TTC_HEAVY_MERGE);
+            if (mode) launch_fused_any<1>(kc, b.hc_view, b.hc_pre, 1, nc, dq + 3 * (size_t)q0, nq, acc + 8 * (size_t)q0,
+                                          flag, nullptr, 0, s);
+            else launch_fused_any<0>(kc, b.hc_view, b.hc_pre, 1, nc, dq, 1, acc, flag, nullptr, 0, s);
             prof_end(g, s);
         }
     }
@@ -1491,8 +1550,9 @@ void count_ids(ttc_graph *g, const int64_t *dq, const std::vector<uint64_t> &all
         launch_warp_any<2>(heavy_kind(g->heavy_wide, g->strict), g->view.get(), g->prefix.get() + 2, 1, nwc, dq, 1,
                            d_out + 8 * nlc, flag, d_idx.get() + nlc, nwc, s);
     if (ncc)
-        launch_fused_any<2>(heavy_kind(g->heavy_wide, g->strict), g->view.get(), g->prefix.get() + 4, 1, ncc, dq, 1,
-                            d_out + 8 * (nlc + nwc), flag, d_idx.get() + nlc + nwc, ncc, s);
+        launch_fused_any<2>(heavy_kind(g->heavy_wide, g->strict, g->st.heavy_merge == TTC_HEAVY_MERGE), g->view.get(),
+                            g->prefix.get() + 4, 1, ncc, dq, 1, d_out + 8 * (nlc + nwc), flag, d_idx.get() + nlc + nwc,
+                            ncc, s);
     if (nhc) {
         DevBuf<uint4> sub(nhc, s);
         DevBuf<uint64_t> sizes(nhc, s), eoff(nhc + 1, s);

@@ -111,7 +111,7 @@ namespace ttc {
 
 struct LoadOptions {
     uint32_t flags = 0, orientation = 0, labeling = 0, light_max_pairs = 0;
-    uint32_t heavy_warp_cap = 0, heavy_cta_cap = 0;
+    uint32_t heavy_warp_cap = 0, heavy_cta_cap = 0, heavy_merge = 0;
     uint64_t seed = 0;
 };
 
@@ -195,8 +195,10 @@ uint32_t default_light_max_pairs();
 // shape on the current GPU (the tune cache), else default_light_max_pairs().
 uint32_t tuned_light_max(const ttc_graph_stats &st);
 // The heavy-class caps tuned for graphs of this shape at light threshold
-// `light` (ttc_tune_heavy), if any.
-bool tuned_heavy_caps(const ttc_graph_stats &st, uint32_t light, uint32_t *warp_cap, uint32_t *cta_cap);
+// `light` (ttc_tune_heavy), if any, and the one-CTA class's search form
+// (TTC_HEAVY_*, 0 when the entry records none).
+bool tuned_heavy_caps(const ttc_graph_stats &st, uint32_t light, uint32_t *warp_cap, uint32_t *cta_cap,
+                      uint32_t *merge);
 
 // A build with -DTTC_DEBUG_BOUNDS=1 checks the count kernels' indices on
 // the device (count_dev.cuh); this returns and clears the device word those

@@ -2652,14 +2652,17 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
     st.light_pairs = hws[3];
     // heavy records in three classes by size (one warp, one CTA, flat),
     // stably partitioned so each class is contiguous; the huge class last
-    // the classes' caps: given, else tuned for graphs of this shape at this
-    // light threshold, else the kernels' capacities
+    // the classes' caps and the one-CTA class's search form: given, else
+    // tuned for graphs of this shape at this light threshold, else the
+    // kernels' capacities and binary searches
     uint32_t wcap = warp_capacity(g->heavy_wide), ccap = fused_capacity(g->heavy_wide);
+    uint32_t merge = opt.heavy_merge;
     {
-        uint32_t tw = opt.heavy_warp_cap, tc = opt.heavy_cta_cap, aw = 0, ac = 0;
-        if ((!tw || !tc) && tuned_heavy_caps(st, g->light_max_pairs, &aw, &ac)) {
+        uint32_t tw = opt.heavy_warp_cap, tc = opt.heavy_cta_cap, aw = 0, ac = 0, am = 0;
+        if ((!tw || !tc || !merge) && tuned_heavy_caps(st, g->light_max_pairs, &aw, &ac, &am)) {
             if (!tw) tw = aw;
             if (!tc) tc = ac;
+            if (!merge) merge = am;
         }
         if (tw) wcap = std::min(wcap, tw);
         if (tc) ccap = std::min(ccap, tc);
@@ -2667,6 +2670,7 @@ void build_graph(ttc_graph *g, const uint32_t *src_in, const uint32_t *dst_in, c
     }
     st.heavy_warp_cap = wcap;
     st.heavy_cta_cap = ccap;
+    st.heavy_merge = merge ? merge : TTC_HEAVY_BINARY;
     uint64_t n_huge = 0, n_hw = 0, n_hc = 0;
     if (nh) {
         DevBuf<uint8_t> f0(nh, s), f1(nh, s), f2(nh, s);

@@ -41,6 +41,7 @@ namespace {
 
 struct Shape {
     int light_per_sm = 8, heavy_per_sm = 2;
+    int extra = 0;  // heavy-caps entries: the one-CTA class's search form (0 = none recorded)
 };
 
 // ---------------------------------------------------------------- tune cache
@@ -53,7 +54,8 @@ std::string tune_path() {
     return std::string(home && *home ? home : "/tmp") + "/.cache/ttc/tune.json";
 }
 
-// The cache is a flat JSON object {"key": [light, heavy], ...}.
+// The cache is a flat JSON object {"key": [light, heavy], ...}; an entry may
+// carry a third number (Shape::extra).
 std::map<std::string, Shape> tune_load() {
     std::map<std::string, Shape> m;
     std::ifstream f(tune_path());
@@ -69,8 +71,9 @@ std::map<std::string, Shape> tune_load() {
         const size_t a = s.find('[', j), b = s.find(']', j);
         if (a == std::string::npos || b == std::string::npos) break;
         Shape sh;
-        if (sscanf(s.c_str() + a + 1, "%d , %d", &sh.light_per_sm, &sh.heavy_per_sm) == 2 && sh.light_per_sm > 0 &&
-            (sh.heavy_per_sm > 0 || key.rfind("light|", 0) == 0))
+        const int got = sscanf(s.c_str() + a + 1, "%d , %d , %d", &sh.light_per_sm, &sh.heavy_per_sm, &sh.extra);
+        if (got < 3) sh.extra = 0;
+        if (got >= 2 && sh.light_per_sm > 0 && (sh.heavy_per_sm > 0 || key.rfind("light|", 0) == 0))
             m[key] = sh;
         i = b + 1;
     }
@@ -89,7 +92,9 @@ void tune_store(const std::map<std::string, Shape> &m) {
     bool first = true;
     for (auto &kv : m) {
         f << (first ? "\n" : ",\n") << "  \"" << kv.first << "\": [" << kv.second.light_per_sm << ", "
-          << kv.second.heavy_per_sm << "]";
+          << kv.second.heavy_per_sm;
+        if (kv.second.extra) f << ", " << kv.second.extra;
+        f << "]";
         first = false;
     }
     f << "\n}\n";
@@ -352,7 +357,8 @@ uint32_t tuned_light_max(const ttc_graph_stats &st) {
     return it != g_light_mem.end() ? (uint32_t)it->second.light_per_sm : default_light_max_pairs();
 }
 
-bool tuned_heavy_caps(const ttc_graph_stats &st, uint32_t light, uint32_t *warp_cap, uint32_t *cta_cap) {
+bool tuned_heavy_caps(const ttc_graph_stats &st, uint32_t light, uint32_t *warp_cap, uint32_t *cta_cap,
+                      uint32_t *merge) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     if (!g_light_loaded) {
         g_light_mem = tune_load();
@@ -362,6 +368,8 @@ bool tuned_heavy_caps(const ttc_graph_stats &st, uint32_t light, uint32_t *warp_
     if (it == g_light_mem.end()) return false;
     *warp_cap = (uint32_t)it->second.light_per_sm;
     *cta_cap = (uint32_t)it->second.heavy_per_sm;
+    const int x = it->second.extra;
+    *merge = x == (int)TTC_HEAVY_BINARY || x == (int)TTC_HEAVY_MERGE ? (uint32_t)x : 0u;
     return true;
 }
 
@@ -456,37 +464,41 @@ extern "C" ttc_status ttc_tune_light(const uint32_t *src, const uint32_t *dst, c
 
 extern "C" ttc_status ttc_tune_heavy(const uint32_t *src, const uint32_t *dst, const int64_t *t, uint64_t m,
                                      const ttc_load_opts *opts, const ttc_delta *probe, uint32_t k,
-                                     uint32_t *warp_cap, uint32_t *cta_cap, float *ms) {
-    if (!warp_cap || !cta_cap || (k && !probe)) {
+                                     uint32_t *warp_cap, uint32_t *cta_cap, uint32_t *merge, float *ms) {
+    if (!warp_cap || !cta_cap || !merge || (k && !probe)) {
         set_last_error("NULL argument");
         return TTC_ERR_INVALID;
     }
-    if (opts && (opts->heavy_warp_cap || opts->heavy_cta_cap)) {
-        set_last_error("ttc_tune_heavy chooses the heavy caps itself: pass 0");
+    if (opts && (opts->heavy_warp_cap || opts->heavy_cta_cap || opts->heavy_merge)) {
+        set_last_error("ttc_tune_heavy chooses the heavy caps and search form itself: pass 0");
         return TTC_ERR_INVALID;
     }
     try {
         ttc_load_opts o = opts ? *opts : ttc_load_opts{};
         float best = 0.f;
-        uint32_t bw = 0, bc = 0, dw = 0, dc = 0;
+        uint32_t bw = 0, bc = 0, bm = 0, dw = 0, dc = 0, dm = 0;
         ttc_graph_stats st{};
         for (uint32_t i = 0; i < TTC_TUNE_HEAVY_CANDIDATES; i++) {
             o.heavy_warp_cap = ttc_tune_heavy_candidates[i][0];
             o.heavy_cta_cap = ttc_tune_heavy_candidates[i][1];
+            o.heavy_merge = ttc_tune_heavy_candidates[i][2];
             float el = 0.f;
             const ttc_status rc = time_load_count(src, dst, t, m, o, probe, k, 3, &el, &st);
             if (rc != TTC_OK) return rc;
             if (ms) ms[i] = el;
-            // another pair replaces the first (the kernels' capacities) only
-            // when it is faster by more than 1%, not by timing noise
+            // another candidate replaces the first (the kernels' capacities,
+            // binary searches) only when it is faster by more than 1%, not by
+            // timing noise
             if (i == 0) {
                 dw = st.heavy_warp_cap;
                 dc = st.heavy_cta_cap;
+                dm = st.heavy_merge;
             }
-            if (i == 0 || el < best * (bw == dw && bc == dc ? 0.99f : 1.0f)) {
+            if (i == 0 || el < best * (bw == dw && bc == dc && bm == dm ? 0.99f : 1.0f)) {
                 best = el;
                 bw = st.heavy_warp_cap;
                 bc = st.heavy_cta_cap;
+                bm = st.heavy_merge;
             }
             if (!st.tau_heavy) {  // no heavy triangle: every candidate counts the same
                 for (uint32_t j = i + 1; ms && j < TTC_TUNE_HEAVY_CANDIDATES; j++) ms[j] = el;
@@ -499,6 +511,7 @@ extern "C" ttc_status ttc_tune_heavy(const uint32_t *src, const uint32_t *dst, c
             Shape sh;
             sh.light_per_sm = (int)bw;
             sh.heavy_per_sm = (int)bc;
+            sh.extra = (int)bm;
             cache[heavy_key(st, st.light_max_pairs)] = sh;
             tune_store(cache);
             g_light_mem = cache;
@@ -506,6 +519,7 @@ extern "C" ttc_status ttc_tune_heavy(const uint32_t *src, const uint32_t *dst, c
         }
         *warp_cap = bw;
         *cta_cap = bc;
+        *merge = bm;
         return TTC_OK;
     } catch (const Failure &f) {
         set_last_error(f.message);

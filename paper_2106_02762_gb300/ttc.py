@@ -30,6 +30,7 @@ LOAD_STREAM = 4
 LOAD_STRICT_TIME = 8
 ORIENT_DEGENERACY, ORIENT_ID, ORIENT_DEGREE, ORIENT_RANDOM = 0, 1, 2, 3
 LABEL_HEAVIEST_VW, LABEL_SOURCE = 0, 1
+HEAVY_BINARY, HEAVY_MERGE = 1, 2  # the one-CTA class's search form (TTC_HEAVY_*)
 
 EXPORTS = ["ttc_load", "ttc_load_ex", "ttc_free", "ttc_graph_info", "ttc_count", "ttc_count_batch",
            "ttc_count_batch_async", "ttc_count_multi", "ttc_count_sample", "ttc_server_create",
@@ -40,8 +41,10 @@ EXPORTS = ["ttc_load", "ttc_load_ex", "ttc_free", "ttc_graph_info", "ttc_count",
            "ttc_release_cached", "ttc_memory_info", "ttc_count_grid", "ttc_count_shard", "ttc_tune_light", "ttc_tune_heavy",
            "ttc_count_stream", "ttc_count_participation", "ttc_graph_pairs"]
 TUNE_CANDIDATES = (17, 65, 257, 1025, 4097, 16385)  # ttc_tune_candidates in ttc.h
-# ttc_tune_heavy_candidates in ttc.h: (warp cap, CTA cap)
-TUNE_HEAVY_CANDIDATES = ((128, 2048), (64, 2048), (32, 2048), (128, 1024), (64, 1024), (128, 512))
+# ttc_tune_heavy_candidates in ttc.h: (warp cap, CTA cap, search form)
+TUNE_HEAVY_CANDIDATES = ((128, 2048, HEAVY_BINARY), (64, 2048, HEAVY_BINARY), (32, 2048, HEAVY_BINARY),
+                         (128, 1024, HEAVY_BINARY), (64, 1024, HEAVY_BINARY), (128, 512, HEAVY_BINARY),
+                         (128, 2048, HEAVY_MERGE), (64, 2048, HEAVY_MERGE))
 
 
 class TTCError(RuntimeError):
@@ -57,7 +60,8 @@ class Delta(ctypes.Structure):
 class LoadOpts(ctypes.Structure):
     _fields_ = [("flags", ctypes.c_uint32), ("orientation", ctypes.c_uint32), ("labeling", ctypes.c_uint32),
                 ("light_max_pairs", ctypes.c_uint32), ("heavy_warp_cap", ctypes.c_uint32),
-                ("heavy_cta_cap", ctypes.c_uint32), ("seed", ctypes.c_uint64), ("stream", ctypes.c_void_p)]
+                ("heavy_cta_cap", ctypes.c_uint32), ("heavy_merge", ctypes.c_uint32), ("seed", ctypes.c_uint64),
+                ("stream", ctypes.c_void_p)]
 
 
 class GraphStats(ctypes.Structure):
@@ -65,7 +69,8 @@ class GraphStats(ctypes.Structure):
                 ("n", "m", "m_self_loops", "m_s", "tau", "kappa", "sigma_max", "peel_rounds", "work_bytes",
                  "enum_elems", "tau_light", "tau_heavy", "device_bytes", "work_bytes_heavy", "tau_huge", "tau_hwarp", "tau_hcta", "light_pairs")] + \
                [("key_bits", ctypes.c_uint32), ("light_max_pairs", ctypes.c_uint32),
-                ("heavy_warp_cap", ctypes.c_uint32), ("heavy_cta_cap", ctypes.c_uint32)]
+                ("heavy_warp_cap", ctypes.c_uint32), ("heavy_cta_cap", ctypes.c_uint32),
+                ("heavy_merge", ctypes.c_uint32)]
 
 
 class KernelTime(ctypes.Structure):
@@ -104,7 +109,7 @@ def lib():
             "ttc_count_batch_async": ([p, p, u32, p, p], ctypes.c_int),
             "ttc_count_shard": ([p, p, u32, u32, u32, p], ctypes.c_int),
             "ttc_tune_light": ([p, p, p, u64, p, p, u32, p, p], ctypes.c_int),
-            "ttc_tune_heavy": ([p, p, p, u64, p, p, u32, p, p, p], ctypes.c_int),
+            "ttc_tune_heavy": ([p, p, p, u64, p, p, u32, p, p, p, p], ctypes.c_int),
             "ttc_count_stream": ([p, p, p, p, p, u32, p, u64, p, p], ctypes.c_int),
             "ttc_count_participation": ([p, p, p, p], ctypes.c_int),
             "ttc_graph_pairs": ([p, p], ctypes.c_int),
@@ -186,11 +191,12 @@ class Graph:
 
     def __init__(self, src, dst, t, orientation=ORIENT_DEGENERACY, labeling=LABEL_HEAVIEST_VW,
                  light_max_pairs=0, seed=0, stream=None, profile_load=False, streamed=False, strict_time=False,
-                 heavy_warp_cap=0, heavy_cta_cap=0):
+                 heavy_warp_cap=0, heavy_cta_cap=0, heavy_merge=0):
         """streamed: TTC_LOAD_STREAM (no light-triangle list; every count
         enumerates the triangles again and counts light ones as it finds them).
         strict_time: TTC_LOAD_STRICT_TIME (count a triple only if its three
-        timestamps strictly increase)."""
+        timestamps strictly increase).  heavy_merge: HEAVY_BINARY or
+        HEAVY_MERGE for the one-CTA class (0: tuned, else binary)."""
         ptrs, m, flags, keep = _edge_ptrs(src, dst, t)
         if profile_load:
             flags |= LOAD_PROFILE
@@ -198,7 +204,9 @@ class Graph:
             flags |= LOAD_STREAM
         if strict_time:
             flags |= LOAD_STRICT_TIME
-        opts = LoadOpts(flags, orientation, labeling, light_max_pairs, heavy_warp_cap, heavy_cta_cap, seed, stream)
+        opts = LoadOpts(flags=flags, orientation=orientation, labeling=labeling, light_max_pairs=light_max_pairs,
+                        heavy_warp_cap=heavy_warp_cap, heavy_cta_cap=heavy_cta_cap, heavy_merge=heavy_merge,
+                        seed=seed, stream=stream)
         h = ctypes.c_void_p()
         check(lib().ttc_load_ex(ptrs[0], ptrs[1], ptrs[2], m, ctypes.byref(opts), ctypes.byref(h)))
         self._h = h
@@ -302,7 +310,7 @@ def tune_light(src, dst, t, probe_deltas, stream=None, orientation=ORIENT_DEGENE
     threshold in TUNE_CANDIDATES, caches the fastest for graphs of this
     shape and returns (chosen threshold, {candidate: ms})."""
     ptrs, m, flags, keep = _edge_ptrs(src, dst, t)
-    opts = LoadOpts(flags, orientation, labeling, 0, 0, 0, 0, stream)
+    opts = LoadOpts(flags=flags, orientation=orientation, labeling=labeling, stream=stream)
     d, dp = _deltas(probe_deltas)
     chosen = ctypes.c_uint32()
     ms = (ctypes.c_float * len(TUNE_CANDIDATES))()
@@ -315,18 +323,20 @@ def tune_light(src, dst, t, probe_deltas, stream=None, orientation=ORIENT_DEGENE
 def tune_heavy(src, dst, t, probe_deltas, light_max_pairs=0, stream=None, orientation=ORIENT_DEGENERACY,
                labeling=LABEL_HEAVIEST_VW):
     """ttc_tune_heavy: times load + count of the probe queries at each (warp
-    cap, CTA cap) of TUNE_HEAVY_CANDIDATES at the given light threshold,
-    caches the fastest and returns ((warp cap, CTA cap) the loads used,
-    {candidate: ms})."""
+    cap, CTA cap, search form) of TUNE_HEAVY_CANDIDATES at the given light
+    threshold, caches the fastest and returns ((warp cap, CTA cap, search
+    form) the loads used, {candidate: ms})."""
     ptrs, m, flags, keep = _edge_ptrs(src, dst, t)
-    opts = LoadOpts(flags, orientation, labeling, light_max_pairs, 0, 0, 0, stream)
+    opts = LoadOpts(flags=flags, orientation=orientation, labeling=labeling, light_max_pairs=light_max_pairs,
+                    stream=stream)
     d, dp = _deltas(probe_deltas)
-    w, c = ctypes.c_uint32(), ctypes.c_uint32()
+    w, c, mg = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
     ms = (ctypes.c_float * len(TUNE_HEAVY_CANDIDATES))()
     check(lib().ttc_tune_heavy(ptrs[0], ptrs[1], ptrs[2], m, ctypes.byref(opts), dp, d.shape[0],
-                               ctypes.byref(w), ctypes.byref(c), ms))
+                               ctypes.byref(w), ctypes.byref(c), ctypes.byref(mg), ms))
     del keep
-    return (int(w.value), int(c.value)), {cand: float(v) for cand, v in zip(TUNE_HEAVY_CANDIDATES, ms)}
+    return ((int(w.value), int(c.value), int(mg.value)),
+            {cand: float(v) for cand, v in zip(TUNE_HEAVY_CANDIDATES, ms)})
 
 
 def count_stream(edge_lists, deltas, budget_bytes=0, orientation=ORIENT_DEGENERACY, labeling=LABEL_HEAVIEST_VW,
@@ -350,7 +360,7 @@ def count_stream(edge_lists, deltas, budget_bytes=0, orientation=ORIENT_DEGENERA
         ms.append(m)
         keep.append(k)
     m_arr = np.asarray(ms, dtype=np.uint64)
-    opts = LoadOpts(0, orientation, labeling, light_max_pairs, 0, 0, 0, None)
+    opts = LoadOpts(orientation=orientation, labeling=labeling, light_max_pairs=light_max_pairs)
     out = np.zeros((G, NUM_TYPES), dtype=np.uint64)
     nb = ctypes.c_uint32(0)
     check(lib().ttc_count_stream(ps[0], ps[1], ps[2], m_arr.ctypes.data, dp, G, ctypes.byref(opts),

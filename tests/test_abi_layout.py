@@ -71,8 +71,8 @@ def probe(tmp_path_factory):
             lines.append('  printf("%s %s %%zu %%zu\\n", offsetof(%s, %s), sizeof(((%s *)0)->%s));'
                          % (cname, f, cname, f, cname, f))
     lines.append('  for (int i = 0; i < TTC_TUNE_CANDIDATES; i++) printf("light %u\\n", ttc_tune_candidates[i]);')
-    lines.append('  for (int i = 0; i < TTC_TUNE_HEAVY_CANDIDATES; i++) printf("heavy %u %u\\n", '
-                 'ttc_tune_heavy_candidates[i][0], ttc_tune_heavy_candidates[i][1]);')
+    lines.append('  for (int i = 0; i < TTC_TUNE_HEAVY_CANDIDATES; i++) printf("heavy %u %u %u\\n", '
+                 'ttc_tune_heavy_candidates[i][0], ttc_tune_heavy_candidates[i][1], ttc_tune_heavy_candidates[i][2]);')
     for name in header_constants():
         lines.append('  printf("const %s %%lld\\n", (long long)%s);' % (name, name))
     lines += ["  return 0;", "}"]
@@ -105,7 +105,7 @@ def test_struct_layout_matches_header(probe, cname):
 
 def test_tuner_candidates_match_header(probe):
     light = tuple(int(r[1]) for r in probe if r[0] == "light")
-    heavy = tuple((int(r[1]), int(r[2])) for r in probe if r[0] == "heavy")
+    heavy = tuple((int(r[1]), int(r[2]), int(r[3])) for r in probe if r[0] == "heavy")
     assert light == ttc.TUNE_CANDIDATES
     assert heavy == ttc.TUNE_HEAVY_CANDIDATES
 
@@ -117,8 +117,8 @@ def test_constants_match_header(probe):
     for name, code in status.items():
         assert ttc.STATUS[code] == name[len("TTC_ERR_"):], name
     assert (consts["TTC_OK"], consts["TTC_PENDING"]) == (ttc.OK, ttc.PENDING)
-    mirrored = [k for k in consts if k.startswith(("TTC_LOAD_", "TTC_ORIENT_", "TTC_LABEL_"))]
-    assert len(mirrored) == 10
+    mirrored = [k for k in consts if k.startswith(("TTC_LOAD_", "TTC_ORIENT_", "TTC_LABEL_", "TTC_HEAVY_"))]
+    assert len(mirrored) == 12
     for name in mirrored + ["TTC_NUM_TYPES"]:
         assert getattr(ttc, name[len("TTC_"):]) == consts[name], name
     assert consts["TTC_TUNE_CANDIDATES"] == len(ttc.TUNE_CANDIDATES)

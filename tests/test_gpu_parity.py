@@ -59,6 +59,50 @@ def test_random_tiny_every_path():
         _check(s, d, t, deltas, seed=seed, **opts)
 
 
+def test_two_pointer_form_matches_oracle_and_binary_form():
+    # Every triangle on the prefix-sum path's one-CTA class (light threshold
+    # 1, warp cap 1).  With HEAVY_MERGE that class takes the two-pointer form
+    # for the triangles whose C is staged and holds at most sigma_A + sigma_B
+    # edges (under the default labelling C is the heaviest pair, so most
+    # do).  Counts equal the oracle's for single queries and batches, both
+    # labellings and the strict reading; the per-triangle kernel
+    # (participation counts) agrees with the binary-search form.
+    rng = np.random.default_rng(29)
+    opts = dict(light_max_pairs=ALL_HEAVY, heavy_warp_cap=1, heavy_merge=ttc.HEAVY_MERGE)
+    for seed in range(48):
+        n = int(rng.integers(3, 10))
+        m = int(rng.integers(3, 80))
+        tr = int(rng.integers(1, 30))
+        s, d, t = synth.random_tiny(7000 + seed, n, m, tr)
+        deltas = _menu(rng, tr)
+        strict = seed % 3 == 2
+        lab = ttc.LABEL_SOURCE if seed % 4 == 1 else ttc.LABEL_HEAVIEST_VW
+        want = oracle.count(s, d, t, deltas, strict=strict)
+        g = ttc.Graph(s, d, t, labeling=lab, strict_time=strict, **opts)
+        try:
+            info = g.info()
+            assert info["heavy_merge"] == ttc.HEAVY_MERGE and info["tau_hwarp"] == 0
+            assert (g.count_batch(deltas) == want).all(), seed
+            for q in range(3):
+                assert (g.count(deltas[q]) == want[q]).all(), (seed, q)
+        finally:
+            g.free()
+    s, d, t = synth.large_plain(scale=0.002)
+    deltas = [synth.LARGE_PLAIN_DELTA, synth.LARGE_PLAIN_DELTA_UNBOUNDED, (3600, 600, 3000)]
+    want = oracle.count(s, d, t, deltas)
+    merged = ttc.Graph(s, d, t, **opts)
+    binary = ttc.Graph(s, d, t, light_max_pairs=ALL_HEAVY, heavy_warp_cap=1, heavy_merge=ttc.HEAVY_BINARY)
+    try:
+        assert merged.info()["tau_hcta"] > 0 and binary.info()["heavy_merge"] == ttc.HEAVY_BINARY
+        assert (merged.count_batch(deltas) == want).all()
+        assert (merged.count(deltas[1]) == want[1]).all()
+        for a, b in zip(merged.participation(deltas[0]), binary.participation(deltas[0])):
+            assert (a == b).all()
+    finally:
+        merged.free()
+        binary.free()
+
+
 def test_tiny_plain_workload():
     s, d, t = synth.tiny_plain()
     deltas = [synth.TINY_PLAIN_DELTA, (BIG, BIG, BIG), (100_000, 60_000, 50_000)]

@@ -46,31 +46,31 @@ def test_tuned_heavy_caps_are_used_and_counts_agree():
     # caps move triangles between its one-warp, one-CTA and flat classes
     s, d, t = synth.large_plain(scale=0.003)
     probe = [synth.LARGE_PLAIN_DELTA, (BIG, BIG, BIG)]
-    (w, c), ms = ttc.tune_heavy(s, d, t, probe, light_max_pairs=17)
+    (w, c, mg), ms = ttc.tune_heavy(s, d, t, probe, light_max_pairs=17)
     assert set(ms) == set(ttc.TUNE_HEAVY_CANDIDATES) and all(v > 0 for v in ms.values())
-    # the first candidate (the capacities) stays unless another is more
-    # than 1% faster
+    # the first candidate (the capacities, binary searches) stays unless
+    # another is more than 1% faster
     first = ttc.TUNE_HEAVY_CANDIDATES[0]
     best = min(ms, key=ms.get)
     if ms[best] >= 0.99 * ms[first]:
         best = first
-    assert (w, c) == (min(best[0], 128), min(max(best[1], best[0]), 2048))
-    tuned = ttc.Graph(s, d, t, light_max_pairs=17)  # caps 0: the tuned ones
+    assert (w, c, mg) == (min(best[0], 128), min(max(best[1], best[0]), 2048), best[2])
+    tuned = ttc.Graph(s, d, t, light_max_pairs=17)  # caps and search form 0: the tuned ones
     info = tuned.info()
-    assert (info["heavy_warp_cap"], info["heavy_cta_cap"]) == (w, c)
+    assert (info["heavy_warp_cap"], info["heavy_cta_cap"], info["heavy_merge"]) == (w, c, mg)
     assert info["tau_heavy"] > 0
     deltas = probe + [(200000, 150000, 120000), (3600, 600, 3000)]
     want = oracle.count(s, d, t, deltas)
     assert (tuned.count_batch(deltas) == want).all()
     tuned.free()
     classes = {}
-    for cw, cc in ttc.TUNE_HEAVY_CANDIDATES + ((1, 1), (1, 64)):
-        g = ttc.Graph(s, d, t, light_max_pairs=17, heavy_warp_cap=cw, heavy_cta_cap=cc)
+    for cw, cc, cm in ttc.TUNE_HEAVY_CANDIDATES + ((1, 1, ttc.HEAVY_BINARY), (1, 64, ttc.HEAVY_MERGE)):
+        g = ttc.Graph(s, d, t, light_max_pairs=17, heavy_warp_cap=cw, heavy_cta_cap=cc, heavy_merge=cm)
         i = g.info()
-        assert (i["heavy_warp_cap"], i["heavy_cta_cap"]) == (min(cw, 128), min(max(cc, cw), 2048))
+        assert (i["heavy_warp_cap"], i["heavy_cta_cap"], i["heavy_merge"]) == (min(cw, 128), min(max(cc, cw), 2048), cm)
         assert i["tau_hwarp"] + i["tau_hcta"] + i["tau_huge"] == i["tau_heavy"] == info["tau_heavy"]
         classes[(cw, cc)] = (i["tau_hwarp"], i["tau_hcta"], i["tau_huge"])
-        assert (g.count_batch(deltas) == want).all(), (cw, cc)
+        assert (g.count_batch(deltas) == want).all(), (cw, cc, cm)
         g.free()
     # smaller caps move triangles to the larger classes, never back
     assert classes[(1, 1)][2] == info["tau_heavy"]
