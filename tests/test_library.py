@@ -55,3 +55,32 @@ def test_missing_library_fails_loudly(monkeypatch):
     monkeypatch.setattr(ttc, "LIB_PATH", "/nonexistent/libttc.so")
     with pytest.raises(RuntimeError, match="not built"):
         ttc.lib()
+
+
+def test_count_hash_tracks_the_light_kernel_sources_only():
+    # the hash that ties the light kernel's DRAM capture to its source moves
+    # with the light bin and the device headers, not with the heavy bins or
+    # the host-side handle
+    from paper_2106_02762_gb300 import build
+    files = {f: open(os.path.join(build.CSRC, f), "rb").read() for f, _ in build._LIGHT_SOURCES}
+
+    def hashed(edit=None):
+        return build.count_source_hash(lambda f: edit(f, files[f]) if edit else files[f])
+
+    def after(name, marker, text):
+        def edit(f, data):
+            if f != name:
+                return data
+            i = data.index(marker.encode()) + len(marker)
+            return data[:i] + text + data[i:]
+        return edit
+
+    base = hashed()
+    assert base == build.count_source_hash()
+    heavy = "// ---------------------------------------------------------------- heavy: per-edge math"
+    assert hashed(after("count.cu", heavy, b"\n// a heavy-bin change\n")) == base
+    assert hashed(after("graph.cuh", "struct ttc_graph {", b"\n    int host_side_field;\n")) == base
+    light = "// ---------------------------------------------------------------- light bin"
+    assert hashed(after("count.cu", light, b"\n// a light-bin change\n")) != base
+    assert hashed(after("graph.cuh", "struct GraphView {", b"\n    int device_field;\n")) != base
+    assert hashed(lambda f, d: d + b"\n" if f == "count_dev.cuh" else d) != base
